@@ -1,0 +1,360 @@
+#!/usr/bin/env python
+"""Benchmark of the compression hot path on GB300.
+
+One step = fz_compress + fz_decompress of a 512^3 float32 Gaussian random
+field (Kolmogorov spectrum, seed 2 + rank) at a value-range-relative bound of
+1e-4 with first-order Lorenzo and code radius 512 -- the paper's Nyx-shaped
+workload (Table 2) with synthetic data.  The field (512 MiB) is larger than
+L2, so no flush is needed between timed steps.
+
+Printed (rank 0, one JSON line): round-trip throughput on the input basis
+(input bytes / (compress + decompress device time)), per-direction GB/s and
+fractions of the HBM roofline, compression ratio, the dominant kernel's
+roofline entry (CUDA-event stage timing inside the library), an end-to-end
+number through the C ABI with host buffers and copies, the CPU oracle timed
+on a bounded slab of the same field, and the SM clocks sampled during the
+timed region.
+
+``--impl reference`` times the CPU oracle instead (rank 0 only), each step a
+bounded slab of the same workload.
+
+Multi-GPU (torchrun): every rank compresses its own field (weak scaling, no
+collective on the data path); the time is the maximum over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import ctypes as C
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+import torch
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+
+WORKLOAD = "3D FP32 512^3 Gaussian random field (k^-5/3), REL 1e-4, Lorenzo-1, radius 512"
+METRIC = "compress/decompress GB/s vs HBM peak at REL 1e-4; CR learned vs plain"
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during a region."""
+
+    FIELDS = ("uuid,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device: int):
+        self.uuid = None
+        try:
+            self.uuid = str(torch.cuda.get_device_properties(device).uuid)
+        except Exception:
+            pass
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            if self.uuid and self.uuid not in parts[0] and parts[0] not in self.uuid:
+                continue
+            rows.append(parts)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def cpu_baseline(field_gpu: torch.Tensor, slab_z: int, eb: float):
+    """The CPU oracle, as it stands, on a z-slab of the same field."""
+    import oracle
+    x = field_gpu[:slab_z].contiguous().cpu().numpy()
+    t0 = time.perf_counter()
+    buf = oracle.compress(x, eb)
+    t1 = time.perf_counter()
+    oracle.decompress(buf)
+    t2 = time.perf_counter()
+    gbs = x.nbytes / (t2 - t0) / 1e9
+    return {"value": round(gbs, 4), "unit": "GB/s", "cores": 1, "kind": "oracle",
+            "sample": f"{x.shape[2]}x{x.shape[1]}x{x.shape[0]} slab of the field ({x.nbytes >> 20} MiB), "
+                      f"compress {t1 - t0:.2f} s + decompress {t2 - t1:.2f} s, single thread",
+            "compress_gbs": round(x.nbytes / (t1 - t0) / 1e9, 4), "decompress_gbs": round(x.nbytes / (t2 - t1) / 1e9, 4)}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    import oracle
+    oracle.build()
+    dev = "cuda" if torch.cuda.is_available() else "cpu"
+    field = synth.grf3d(args.size, seed=2, device=dev)
+    slab = max(1, args.ref_slab)
+    x = field[:slab].contiguous().cpu().numpy()
+    for _ in range(args.warmup):
+        oracle.decompress(oracle.compress(x, args.eb))
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.decompress(oracle.compress(x, args.eb))
+    dt = time.perf_counter() - t0
+    v = args.steps * x.nbytes / dt / 1e9
+    out = {"impl": "reference", "metric": METRIC, "value": round(v, 4), "unit": "GB/s", "n_gpus": world,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(dt / args.steps * 1e3, 3),
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+           "config": {"workload": WORKLOAD, "sample": f"{args.size}x{args.size}x{slab} slab per step"},
+           "cpu_baseline": {"value": round(v, 4), "unit": "GB/s", "cores": 1, "kind": "oracle",
+                            "sample": f"{args.size}x{args.size}x{slab} slab ({x.nbytes >> 20} MiB) per step"},
+           "e2e": {"value": round(v, 4), "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def run_fz(args, rank, world, local_rank):
+    import paper_2509_20563_gb300 as fz
+    from paper_2509_20563_gb300 import build as fzbuild
+    fzbuild.build()
+    L = fz.lib()
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    N = args.size ** 3
+    x = synth.grf3d(args.size, seed=2 + rank, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    sp = C.c_void_p(stream.cuda_stream)
+    ctx = fz.Context(local_rank)
+    assert L.fz_ctx_set_profiling(ctx.handle, 1) == 0
+    bound = fz.compress_bound(x.shape)
+    buf = torch.empty(bound, dtype=torch.uint8, device=dev)
+    y = torch.empty_like(x)
+    dims = fz._dims(x.shape)
+    pipe = fz._pipeline("lorenzo1", 512)
+    nbytes = C.c_uint64()
+    hdr = C.create_string_buffer(256)
+
+    def compress():
+        st = L.fz_compress(ctx.handle, C.c_void_p(x.data_ptr()), 3, dims, 1, args.eb, C.byref(pipe),
+                           C.c_void_p(buf.data_ptr()), bound, C.byref(nbytes), hdr, sp)
+        if st:
+            raise fz.FzError(st, "fz_compress")
+
+    def decompress():
+        st = L.fz_decompress(ctx.handle, C.c_void_p(buf.data_ptr()), nbytes.value, hdr, C.c_void_p(y.data_ptr()),
+                             N, sp)
+        if st:
+            raise fz.FzError(st, "fz_decompress")
+
+    # correctness of this very configuration before timing
+    compress()
+    decompress()
+    rng = float(x.max()) - float(x.min())
+    eb_abs = args.eb * rng
+    max_err = float((y.double() - x.double()).abs().max())
+    assert max_err <= eb_abs, (max_err, eb_abs)
+    S = nbytes.value
+    fh = fz.stream_info(hdr.raw)
+    for _ in range(args.warmup):
+        compress()
+        decompress()
+    prof = fz_profile_t()
+    stages_c, stages_d = {}, {}
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
+           torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    clocks = Clocks(local_rank)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize(dev)
+    clocks.start()
+    launches0 = _launches(L, ctx)
+    for i in range(args.steps):
+        ev[i][0].record(stream)
+        compress()
+        ev[i][1].record(stream)
+        decompress()
+        ev[i][2].record(stream)
+        assert L.fz_ctx_get_profile(ctx.handle, C.byref(prof)) == 0
+        for k in range(prof.n_compress):
+            stages_c.setdefault(prof.compress_names[k].decode(), []).append(prof.compress_ms[k])
+        for k in range(prof.n_decompress):
+            stages_d.setdefault(prof.decompress_names[k].decode(), []).append(prof.decompress_ms[k])
+    torch.cuda.synchronize(dev)
+    launches = _launches(L, ctx) - launches0
+    if world > 1:
+        torch.distributed.barrier()
+    clk = clocks.stop()
+    tc = [a.elapsed_time(b) for a, b, _ in ev]
+    td = [b.elapsed_time(c) for _, b, c in ev]
+    tot_ms = sum(tc) + sum(td)
+    if world > 1:
+        t = torch.tensor([tot_ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        tot_ms = float(t.item())
+    peak, peak_kind = _peaks()
+    mc, md = statistics.mean(tc), statistics.mean(td)
+    comp_gbs = 4 * N / (mc * 1e-3) / 1e9
+    dec_gbs = 4 * N / (md * 1e-3) / 1e9
+    comp_forced = 12 * N + S       # range read + quant read + codes write + codes read + stream
+    dec_forced = S + 4 * N
+    # per-kernel algorithmic bytes per launch
+    n_blocks = N // 512
+    hd = np.frombuffer(hdr.raw, dtype=np.uint8)
+    n_out = int(np.frombuffer(hdr.raw[112:120], np.uint64)[0])
+    n_exc = int(np.frombuffer(hdr.raw[120:128], np.uint64)[0])
+    total_bits = int(np.frombuffer(hdr.raw[128:136], np.uint64)[0])
+    alg = {"range": 4 * N, "quant": 4 * N + 2 * N + 4 * n_blocks + 8 * (n_out + n_exc),
+           "encode": 2 * N + total_bits // 8 + 4 * n_blocks,
+           "decode": S + 4 * N}
+    kern = {k: statistics.mean(v) for k, v in {**stages_c, **stages_d}.items() if k in alg}
+    dom = max(kern, key=kern.get)
+    ach = alg[dom] / (kern[dom] * 1e-3) / 1e9
+    value = args.steps * world * 4 * N / (tot_ms * 1e-3) / 1e9
+    res = {"metric": METRIC, "value": round(value, 2), "unit": "GB/s", "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": round(tot_ms / args.steps, 4), "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+           "config": {"workload": WORKLOAD, "dims": [args.size] * 3, "eb_mode": "rel", "eb": args.eb,
+                      "predictor": "lorenzo1", "radius": 512, "l2": "input 512 MiB > L2, no flush",
+                      "parallelism": f"replicas x{world}"},
+           "compress_gbs": round(comp_gbs, 2), "decompress_gbs": round(dec_gbs, 2),
+           "compress_roofline_frac": round(comp_forced / (mc * 1e-3) / 1e9 / peak, 4),
+           "decompress_roofline_frac": round(dec_forced / (md * 1e-3) / 1e9 / peak, 4),
+           "roofline_basis": "forced HBM bytes: compress 12N+S, decompress S+4N; peak = MEASURED_PEAKS hbm_gbs "
+                             f"({peak_kind})",
+           "cr": round(4 * N / S, 4), "stream_bytes": S, "n_outliers": n_out, "n_exceptions": n_exc,
+           "max_err_over_eb": round(max_err / eb_abs, 6),
+           "stages_ms": {**{f"c.{k}": round(statistics.mean(v), 4) for k, v in stages_c.items()},
+                         **{f"d.{k}": round(statistics.mean(v), 4) for k, v in stages_d.items()}},
+           "roofline": {"kernel": dom, "bound": "hbm", "achieved": round(ach, 1), "peak": peak, "unit": "GB/s",
+                        "frac": round(ach / peak, 4), "traffic": args.traffic,
+                        "algorithmic_bytes": alg[dom], "peak_kind": peak_kind},
+           "gpu_launches": int(launches), "clocks": clk}
+    # end to end through the C ABI with host buffers: H2D input, compress, D2H stream,
+    # H2D stream, decompress, D2H reconstruction -- copies inside the timed region
+    if args.e2e_steps > 0:
+        hx = torch.empty(x.shape, dtype=torch.float32, pin_memory=True)
+        hx.copy_(x)
+        hs = torch.empty(bound, dtype=torch.uint8, pin_memory=True)
+        hy = torch.empty(x.shape, dtype=torch.float32, pin_memory=True)
+        xd = torch.empty_like(x)
+        bd = torch.empty_like(buf)
+
+        def e2e_step():
+            xd.copy_(hx, non_blocking=True)
+            st = L.fz_compress(ctx.handle, C.c_void_p(xd.data_ptr()), 3, dims, 1, args.eb, C.byref(pipe),
+                               C.c_void_p(buf.data_ptr()), bound, C.byref(nbytes), hdr, sp)
+            assert st == 0
+            nb = nbytes.value
+            hs[:nb].copy_(buf[:nb], non_blocking=True)
+            bd[:nb].copy_(hs[:nb], non_blocking=True)
+            st = L.fz_decompress(ctx.handle, C.c_void_p(bd.data_ptr()), nb, hdr, C.c_void_p(y.data_ptr()), N, sp)
+            assert st == 0
+            hy.copy_(y, non_blocking=True)
+            return nb
+
+        for _ in range(2):
+            e2e_step()
+        torch.cuda.synchronize(dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        if world > 1:
+            torch.distributed.barrier()
+        e0.record(stream)
+        for _ in range(args.e2e_steps):
+            nb = e2e_step()
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        ems = e0.elapsed_time(e1)
+        if world > 1:
+            t = torch.tensor([ems], device=dev)
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            ems = float(t.item())
+        res["e2e"] = {"value": round(args.e2e_steps * world * 4 * N / (ems * 1e-3) / 1e9, 2), "unit": "GB/s",
+                      "h2d_bytes_per_step": 4 * N + nb, "d2h_bytes_per_step": nb + 4 * N,
+                      "steps": args.e2e_steps}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        res["cpu_baseline"] = cpu_baseline(x, args.cpu_slab, args.eb)
+    if rank == 0:
+        print(json.dumps(res), flush=True)
+    ctx.close()
+
+
+class fz_profile_t(C.Structure):
+    _fields_ = [("n_compress", C.c_uint32), ("n_decompress", C.c_uint32),
+                ("compress_names", (C.c_char * 16) * 12), ("compress_ms", C.c_float * 12),
+                ("decompress_names", (C.c_char * 16) * 12), ("decompress_ms", C.c_float * 12),
+                ("launches", C.c_uint64)]
+
+
+def _launches(L, ctx):
+    p = fz_profile_t()
+    L.fz_ctx_get_profile(ctx.handle, C.byref(p))
+    return p.launches
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="fz", choices=["fz", "reference"])
+    ap.add_argument("--size", type=int, default=512)
+    ap.add_argument("--eb", type=float, default=1e-4)
+    ap.add_argument("--e2e-steps", type=int, default=5)
+    ap.add_argument("--cpu-slab", type=int, default=160, help="z-slab of the field the CPU oracle times")
+    ap.add_argument("--ref-slab", type=int, default=16, help="z-slab per step for --impl reference")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--traffic", type=float, default=None, help="ncu dram bytes per launch of the dominant kernel")
+    args = ap.parse_args()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        if args.impl == "reference":
+            if rank != 0:
+                return
+        else:
+            torch.distributed.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+    else:
+        run_fz(args, rank, world, local_rank)
+    if world > 1 and args.impl != "reference":
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

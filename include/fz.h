@@ -1,0 +1,206 @@
+/*
+ * fz.h -- C ABI of the GB300 error-bounded compression library (libfz.so).
+ *
+ * The library implements the data-parallel hot path of the FZMod-Default
+ * pipeline of FZModules (§3.3): value-range preprocessing (§3.2), Lorenzo
+ * dual-quant prediction with a fixed code radius and outliers (§3.1), a
+ * histogram of the quantization codes (§3.2), a canonical Huffman codebook and
+ * a chunked Huffman encoder (§3.1-§3.2), and the inverse path (decode, outlier
+ * scatter, inverse Lorenzo, dequantization; §3.3.1).  Every stage runs as a
+ * CUDA kernel for sm_103a; the host code only validates arguments, sizes the
+ * workspace and launches.
+ *
+ * Conventions for every entry point:
+ *   - Pointers named d_* are device pointers on the context's device; h_* are
+ *     host pointers.  The caller owns all buffers it passes.  The context owns
+ *     its workspace (device scratch), which grows on demand.
+ *   - Fields are float32, C order with x fastest: dims[0] = nx (fastest),
+ *     dims[1] = ny, dims[2] = nz.  Unused trailing dims must be 1 or are
+ *     ignored beyond ndim.  1 <= ndim <= 3, every dim >= 1, N = prod(dims) <
+ *     2^32.
+ *   - Every call returns an fz_status and never throws.  Argument errors are
+ *     detected before any launch.  On an error the contents of the output
+ *     buffer are unspecified.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream).  Calls that return sizes or device-detected errors
+ *     synchronize that stream before returning.
+ *   - A context may be used by one host thread at a time; distinct contexts
+ *     are independent.
+ */
+#ifndef FZ_H
+#define FZ_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  FZ_OK = 0,
+  FZ_EINVAL = 1,        /* bad argument (null pointer, bad dims, eb <= 0 or not finite, ...) */
+  FZ_ENOMEM = 2,        /* device workspace could not be allocated */
+  FZ_ECUDA = 3,         /* a CUDA runtime call failed */
+  FZ_EBUFFER = 4,       /* output buffer too small */
+  FZ_ECORRUPT = 5,      /* compressed stream failed validation */
+  FZ_ETIMEOUT = 6,      /* a bounded device-side wait expired */
+  FZ_EUNSUPPORTED = 7   /* valid request this build does not implement */
+} fz_status;
+
+typedef enum {
+  FZ_EB_ABS = 0,        /* eb is the absolute bound */
+  FZ_EB_REL = 1         /* eb is relative to the value range (max - min over finite values), §3.2, §4.2 */
+} fz_eb_mode;
+
+typedef enum {
+  FZ_PRED_LORENZO1 = 0, /* first-order Lorenzo, 1D/2D/3D (cuSZ, §3.1) */
+  FZ_PRED_LORENZO2 = 1, /* second-order Lorenzo, 1D/2D/3D */
+  FZ_PRED_INTERP_LIN = 2,
+  FZ_PRED_INTERP_CUBIC = 3,
+  FZ_SEL_MLP = 16,      /* per-block predictor picked by the learned selector */
+  FZ_SEL_EXHAUSTIVE = 17/* per-block predictor picked by exhaustive trial */
+} fz_predictor;
+
+/* Pipeline description.  Zero-initialise and set struct_size = sizeof(fz_pipeline).
+ * A NULL pipeline pointer means: first-order Lorenzo, radius 512. */
+typedef struct {
+  uint32_t struct_size;
+  uint32_t predictor;          /* fz_predictor */
+  uint32_t radius;             /* code radius R, 2..512; 0 selects 512 */
+  uint32_t reserved;
+  const void *selector_weights;/* device pointer to a selector weight blob (FZ_SEL_MLP only) */
+} fz_pipeline;
+
+/* The 256-byte little-endian stream header.  Sections follow at 16-byte
+ * aligned offsets: lens u8[2R], [predictor ids], anchors i32[n_blocks],
+ * chunk_bits u32[n_chunks], outlier index u32[n_out], outlier residual
+ * i32[n_out], exception index u32[n_exc], exception bits u32[n_exc], then the
+ * MSB-first bitstream in u32 words.  A RAW stream is the header followed by
+ * the N input floats; a CONST stream is the header followed by one float
+ * (padded to 16 bytes).  For RAW and CONST streams only magic, version,
+ * flags, ndim, eb_mode, dims, eb and total_bytes are set; the rest is 0. */
+typedef struct {
+  uint32_t magic;              /* 'F','Z','G','B' */
+  uint16_t version;            /* 1 */
+  uint16_t flags;              /* FZ_FLAG_* */
+  uint32_t ndim;
+  uint32_t eb_mode;
+  uint64_t dims[3];
+  double eb;                   /* as requested */
+  double eb_abs;               /* absolute bound used */
+  uint32_t ebx2_bits;          /* float32 quantization bin width */
+  uint32_t inv2eb_bits;        /* float32 reciprocal of the bin width */
+  uint32_t ebchk_bits;         /* float32 per-value check bound */
+  uint32_t radius;
+  uint32_t block[3];
+  uint32_t predictor;          /* fz_predictor used for every block, or FZ_SEL_* when ids are stored */
+  uint32_t chunk;              /* symbols per Huffman chunk (= block size) */
+  uint32_t reserved0;
+  uint64_t n_blocks, n_chunks, n_out, n_exc, total_bits;
+  uint64_t off_lens, off_ids, off_anchors, off_chunk_bits, off_out_idx, off_out_val,
+      off_exc_idx, off_exc_val, off_bits, total_bytes;
+  uint8_t pad[40];
+} fz_header;
+
+#define FZ_MAGIC 0x42475A46u
+#define FZ_HEADER_BYTES 256u
+#define FZ_FLAG_RAW 1u
+#define FZ_FLAG_CONST 2u
+#define FZ_FLAG_IDS 4u
+
+typedef struct fz_ctx fz_ctx;
+
+/* Create a context bound to CUDA device `device` (its workspace is allocated
+ * lazily by the first call that needs it).  *out receives the handle. */
+fz_status fz_ctx_create(int device, fz_ctx **out);
+
+/* Free the context and its workspace.  Safe on NULL. */
+fz_status fz_ctx_destroy(fz_ctx *ctx);
+
+/* Bytes of output space fz_compress may need: 256 + 4N rounded up to 16.
+ * Returns 0 for invalid dims. */
+uint64_t fz_compress_bound(uint32_t ndim, const uint64_t dims[3]);
+
+/* Compress the float32 field d_in into the stream d_out (FZMod-Default,
+ * §3.3): REL range (§3.2) -> prequantization and Lorenzo prediction with
+ * radius-R codes, anchors and outliers (§3.1) -> code histogram (§3.2) ->
+ * canonical Huffman codebook -> chunked encode.  d_out must be 16-byte
+ * aligned, must not overlap d_in, and out_cap must be >= 256 + 4N.  On
+ * success *out_bytes (host) receives the stream length; if h_header is not
+ * NULL the 256-byte header is also copied to it (host).  The call
+ * synchronizes `stream`.  Errors: FZ_EINVAL, FZ_EBUFFER, FZ_EUNSUPPORTED,
+ * FZ_ENOMEM, FZ_ECUDA, FZ_ETIMEOUT. */
+fz_status fz_compress(fz_ctx *ctx, const float *d_in, uint32_t ndim, const uint64_t dims[3],
+                      uint32_t eb_mode, double eb, const fz_pipeline *pipe, void *d_out,
+                      uint64_t out_cap, uint64_t *out_bytes, void *h_header, void *stream);
+
+/* Reconstruct the field from the stream d_in (in_bytes long, 16-byte
+ * aligned) into d_out (out_cap_values floats, >= N): Huffman decode per
+ * chunk, outlier scatter, anchor restore, inverse Lorenzo prefix sums,
+ * dequantization, exception overwrite, all in one fused kernel (§3.3.1).
+ * h_header may point to a host copy of the stream's first 256 bytes (saves
+ * one device-to-host copy); NULL makes the call read it from d_in.  The call
+ * synchronizes `stream`.  Errors: FZ_EINVAL, FZ_EBUFFER, FZ_ECORRUPT,
+ * FZ_EUNSUPPORTED, FZ_ENOMEM, FZ_ECUDA. */
+fz_status fz_decompress(fz_ctx *ctx, const void *d_in, uint64_t in_bytes, const void *h_header,
+                        float *d_out, uint64_t out_cap_values, void *stream);
+
+/* Parse a host copy of a stream header: dimensionality, dims, absolute
+ * bound and flags.  Any output pointer may be NULL.  FZ_ECORRUPT on a bad
+ * header. */
+fz_status fz_stream_info(const void *h_header, uint64_t header_bytes, uint32_t *ndim, uint64_t dims[3],
+                         double *eb_abs, uint32_t *flags);
+
+/* Stage entry point (prediction + quantization module, §3.1-§3.2): runs the
+ * REL range and constants, prequantization, Lorenzo prediction and code
+ * histogram on d_in and writes the block-major code stream d_codes
+ * (u16[n_blocks*block_size]), the anchors d_anchors (i32[n_blocks]) and the
+ * histogram d_hist (u64[2R]); *n_out and *n_exc (host) receive the outlier
+ * and exception counts and *eb_abs the absolute bound.  Synchronizes
+ * `stream`. */
+fz_status fz_lorenzo_quantize(fz_ctx *ctx, const float *d_in, uint32_t ndim, const uint64_t dims[3],
+                              uint32_t eb_mode, double eb, const fz_pipeline *pipe, uint16_t *d_codes,
+                              int32_t *d_anchors, uint64_t *d_hist, uint64_t *n_out, uint64_t *n_exc,
+                              double *eb_abs, void *stream);
+
+/* Stage entry point (Huffman codebook module, §3.2): from the histogram
+ * d_hist (u64[nsym], nsym <= 1024, at least one nonzero count) compute the
+ * code lengths d_lens (u8[nsym], two-queue Huffman, ties to the leaf,
+ * 24-bit limit by count halving) and the canonical codewords d_codes
+ * (u32[nsym], RFC 1951 order).  Synchronizes `stream`; FZ_EINVAL if no
+ * count is nonzero. */
+fz_status fz_huffman_codebook(fz_ctx *ctx, const uint64_t *d_hist, uint32_t nsym, uint8_t *d_lens,
+                              uint32_t *d_codes, void *stream);
+
+/* Per-stage timing of the last fz_compress and fz_decompress on a context.
+ * When profiling is enabled, each call records a CUDA event on its stream
+ * before the first and after every stage launch; a stage time is the
+ * elapsed time between consecutive events.  `launches` counts the kernel
+ * launches the context has issued since it was created (always counted). */
+#define FZ_MAX_STAGES 12
+typedef struct {
+  uint32_t n_compress, n_decompress;      /* stages recorded for the last call of each kind */
+  char compress_names[FZ_MAX_STAGES][16];
+  float compress_ms[FZ_MAX_STAGES];
+  char decompress_names[FZ_MAX_STAGES][16];
+  float decompress_ms[FZ_MAX_STAGES];
+  uint64_t launches;
+} fz_profile;
+
+/* Turn stage timing on (enable != 0) or off.  Host-only bookkeeping; the
+ * events are created on the context's device. */
+fz_status fz_ctx_set_profiling(fz_ctx *ctx, int enable);
+
+/* Copy the stage times of the last calls into *out (synchronizes on the
+ * recorded events). */
+fz_status fz_ctx_get_profile(fz_ctx *ctx, fz_profile *out);
+
+/* Human-readable name of a status code (static string). */
+const char *fz_status_str(fz_status s);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FZ_H */

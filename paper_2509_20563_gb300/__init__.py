@@ -1,0 +1,234 @@
+"""GB300-native error-bounded lossy compression (FZMod-Default hot path).
+
+Thin Python binding of ``libfz.so`` (the C ABI declared in ``include/fz.h``).
+Every stage of compression and decompression runs in the library's CUDA
+kernels; this module only marshals arguments: torch supplies device memory
+and the current CUDA stream.  If the library has not been built the binding
+raises instead of falling back to anything else.
+
+The raw C entry points are available under their C names (``fz_compress``,
+``fz_decompress``, ...) through :func:`lib`; :func:`compress` and
+:func:`decompress` wrap them for torch tensors.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+import torch
+
+__all__ = ["lib", "Context", "compress", "decompress", "lorenzo_quantize", "huffman_codebook", "stream_info",
+           "FzError", "HEADER_BYTES"]
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libfz.so")
+HEADER_BYTES = 256
+
+STATUS = {0: "FZ_OK", 1: "FZ_EINVAL", 2: "FZ_ENOMEM", 3: "FZ_ECUDA", 4: "FZ_EBUFFER", 5: "FZ_ECORRUPT",
+          6: "FZ_ETIMEOUT", 7: "FZ_EUNSUPPORTED"}
+PREDICTORS = {"lorenzo1": 0, "lorenzo2": 1, "interp_linear": 2, "interp_cubic": 3, "mlp": 16, "exhaustive": 17}
+
+_lock = threading.Lock()
+_lib = None
+
+
+class FzError(RuntimeError):
+    def __init__(self, code: int, what: str):
+        super().__init__(f"{what}: {STATUS.get(code, code)}")
+        self.code = code
+
+
+class Pipeline(C.Structure):
+    _fields_ = [("struct_size", C.c_uint32), ("predictor", C.c_uint32), ("radius", C.c_uint32),
+                ("reserved", C.c_uint32), ("selector_weights", C.c_void_p)]
+
+
+_u64p = C.POINTER(C.c_uint64)
+_vp = C.c_void_p
+
+
+def _declare(L):
+    L.fz_status_str.restype = C.c_char_p
+    L.fz_status_str.argtypes = [C.c_int]
+    L.fz_ctx_create.argtypes = [C.c_int, C.POINTER(C.c_void_p)]
+    L.fz_ctx_destroy.argtypes = [_vp]
+    L.fz_compress_bound.restype = C.c_uint64
+    L.fz_compress_bound.argtypes = [C.c_uint32, _u64p]
+    L.fz_compress.argtypes = [_vp, _vp, C.c_uint32, _u64p, C.c_uint32, C.c_double, C.POINTER(Pipeline), _vp,
+                              C.c_uint64, _u64p, _vp, _vp]
+    L.fz_decompress.argtypes = [_vp, _vp, C.c_uint64, _vp, _vp, C.c_uint64, _vp]
+    L.fz_stream_info.argtypes = [_vp, C.c_uint64, C.POINTER(C.c_uint32), _u64p, C.POINTER(C.c_double),
+                                 C.POINTER(C.c_uint32)]
+    L.fz_lorenzo_quantize.argtypes = [_vp, _vp, C.c_uint32, _u64p, C.c_uint32, C.c_double, C.POINTER(Pipeline),
+                                      _vp, _vp, _vp, _u64p, _u64p, C.POINTER(C.c_double), _vp]
+    L.fz_huffman_codebook.argtypes = [_vp, _vp, C.c_uint32, _vp, _vp, _vp]
+    for name in ("fz_ctx_create", "fz_ctx_destroy", "fz_compress", "fz_decompress", "fz_stream_info",
+                 "fz_lorenzo_quantize", "fz_huffman_codebook"):
+        getattr(L, name).restype = C.c_int
+
+
+def lib():
+    """The loaded libfz.so (raises if it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise RuntimeError(f"libfz.so is not built ({LIB_PATH}); run paper_2509_20563_gb300.build.build()")
+            L = C.CDLL(LIB_PATH)
+            _declare(L)
+            _lib = L
+    return _lib
+
+
+def _check(st: int, what: str):
+    if st != 0:
+        raise FzError(st, what)
+
+
+class Context:
+    """Owns an fz_ctx (device workspace) for one CUDA device."""
+
+    def __init__(self, device: int = 0):
+        h = C.c_void_p()
+        _check(lib().fz_ctx_create(int(device), C.byref(h)), "fz_ctx_create")
+        self.handle = h
+        self.device = int(device)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib().fz_ctx_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+_ctxs: dict[int, Context] = {}
+
+
+def _ctx(device: int) -> Context:
+    with _lock:
+        c = _ctxs.get(device)
+    if c is None:
+        c = Context(device)
+        with _lock:
+            _ctxs[device] = c
+    return c
+
+
+def _dims(shape):
+    d = (C.c_uint64 * 3)(1, 1, 1)
+    for a, s in enumerate(reversed(shape)):
+        d[a] = int(s)
+    return d
+
+
+def _pipeline(predictor="lorenzo1", radius=512, selector_weights=None) -> Pipeline:
+    p = Pipeline()
+    p.struct_size = C.sizeof(Pipeline)
+    p.predictor = PREDICTORS[predictor] if isinstance(predictor, str) else int(predictor)
+    p.radius = int(radius)
+    p.selector_weights = selector_weights.data_ptr() if selector_weights is not None else None
+    return p
+
+
+def _stream(stream):
+    s = torch.cuda.current_stream() if stream is None else stream
+    return C.c_void_p(s.cuda_stream)
+
+
+def compress_bound(shape) -> int:
+    return int(lib().fz_compress_bound(len(shape), _dims(shape)))
+
+
+def compress(x: torch.Tensor, eb: float, mode: str = "rel", predictor="lorenzo1", radius: int = 512,
+             out: torch.Tensor | None = None, stream=None, selector_weights=None) -> torch.Tensor:
+    """Compress a contiguous float32 CUDA tensor (1-3 dims, last axis fastest).
+    Returns a uint8 CUDA tensor holding exactly the stream; its host header
+    copy is attached as ``.fz_header`` (bytes)."""
+    if not (x.is_cuda and x.dtype == torch.float32 and x.is_contiguous()):
+        raise ValueError("compress expects a contiguous float32 CUDA tensor")
+    if not 1 <= x.dim() <= 3:
+        raise ValueError("1 to 3 dimensions")
+    bound = compress_bound(x.shape)
+    if out is None:
+        out = torch.empty(bound, dtype=torch.uint8, device=x.device)
+    nbytes = C.c_uint64()
+    hdr = C.create_string_buffer(HEADER_BYTES)
+    pipe = _pipeline(predictor, radius, selector_weights)
+    st = lib().fz_compress(_ctx(x.device.index or 0).handle, C.c_void_p(x.data_ptr()), x.dim(), _dims(x.shape),
+                           1 if mode == "rel" else 0, float(eb), C.byref(pipe), C.c_void_p(out.data_ptr()),
+                           out.numel(), C.byref(nbytes), hdr, _stream(stream))
+    _check(st, "fz_compress")
+    res = out[: nbytes.value]
+    res.fz_header = hdr.raw
+    return res
+
+
+def stream_info(header: bytes):
+    ndim, dims, eb_abs, flags = C.c_uint32(), (C.c_uint64 * 3)(), C.c_double(), C.c_uint32()
+    buf = C.create_string_buffer(bytes(header[:HEADER_BYTES]), HEADER_BYTES)
+    _check(lib().fz_stream_info(buf, HEADER_BYTES, C.byref(ndim), dims, C.byref(eb_abs), C.byref(flags)),
+           "fz_stream_info")
+    shape = tuple(int(dims[a]) for a in range(ndim.value))[::-1]
+    return shape, eb_abs.value, flags.value
+
+
+def decompress(buf: torch.Tensor, out: torch.Tensor | None = None, header: bytes | None = None,
+               stream=None) -> torch.Tensor:
+    """Reconstruct the float32 field from a compressed stream on the GPU."""
+    if not (buf.is_cuda and buf.dtype == torch.uint8):
+        raise ValueError("decompress expects a uint8 CUDA tensor")
+    header = header if header is not None else getattr(buf, "fz_header", None)
+    if header is None:
+        header = bytes(buf[:HEADER_BYTES].cpu().numpy())
+    shape, _, _ = stream_info(header)
+    n = 1
+    for s in shape:
+        n *= s
+    if out is None:
+        out = torch.empty(shape, dtype=torch.float32, device=buf.device)
+    hb = C.create_string_buffer(bytes(header[:HEADER_BYTES]), HEADER_BYTES)
+    st = lib().fz_decompress(_ctx(buf.device.index or 0).handle, C.c_void_p(buf.data_ptr()), buf.numel(), hb,
+                             C.c_void_p(out.data_ptr()), out.numel(), _stream(stream))
+    _check(st, "fz_decompress")
+    return out
+
+
+def lorenzo_quantize(x: torch.Tensor, eb: float, mode: str = "rel", predictor="lorenzo1", radius: int = 512,
+                     stream=None):
+    """Stage call: (codes u16 block-major, anchors i32, hist u64, n_out, n_exc, eb_abs)."""
+    ndim = x.dim()
+    blk = {1: (1024,), 2: (32, 32), 3: (8, 8, 8)}[ndim]
+    nb = 1
+    for s, b in zip(x.shape, blk):
+        nb *= -(-s // b)
+    bs = 1
+    for b in blk:
+        bs *= b
+    codes = torch.empty(nb * bs, dtype=torch.int16, device=x.device)
+    anchors = torch.empty(nb, dtype=torch.int32, device=x.device)
+    hist = torch.zeros(2 * radius, dtype=torch.int64, device=x.device)
+    no, ne, eba = C.c_uint64(), C.c_uint64(), C.c_double()
+    pipe = _pipeline(predictor, radius)
+    st = lib().fz_lorenzo_quantize(_ctx(x.device.index or 0).handle, C.c_void_p(x.data_ptr()), ndim, _dims(x.shape),
+                                   1 if mode == "rel" else 0, float(eb), C.byref(pipe), C.c_void_p(codes.data_ptr()),
+                                   C.c_void_p(anchors.data_ptr()), C.c_void_p(hist.data_ptr()), C.byref(no),
+                                   C.byref(ne), C.byref(eba), _stream(stream))
+    _check(st, "fz_lorenzo_quantize")
+    return codes, anchors, hist, no.value, ne.value, eba.value
+
+
+def huffman_codebook(hist: torch.Tensor, stream=None):
+    """Stage call: (lengths u8, canonical codewords u32 as int32) for a u64 histogram."""
+    nsym = hist.numel()
+    lens = torch.empty(nsym, dtype=torch.uint8, device=hist.device)
+    codes = torch.empty(nsym, dtype=torch.int32, device=hist.device)
+    st = lib().fz_huffman_codebook(_ctx(hist.device.index or 0).handle, C.c_void_p(hist.data_ptr()), nsym,
+                                   C.c_void_p(lens.data_ptr()), C.c_void_p(codes.data_ptr()), _stream(stream))
+    _check(st, "fz_huffman_codebook")
+    return lens, codes

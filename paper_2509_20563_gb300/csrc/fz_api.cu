@@ -1,0 +1,475 @@
+// fz_api.cu -- the C ABI of libfz.so: argument validation, workspace sizing,
+// launch order of the stage kernels and the final status read-back.  No
+// stage of the compression path runs on the host.
+#include <string.h>
+
+#include <new>
+
+#include "fz_internal.cuh"
+
+struct fz_ctx {
+  int device = 0;
+  int sm_count = 0;
+  void *ws = nullptr;
+  size_t ws_bytes = 0;
+  void *h_pinned = nullptr;  // host mirror of the call's result block
+  // stage profiling (CUDA events on the call's stream)
+  bool profiling = false;
+  cudaEvent_t cev[FZ_MAX_STAGES + 1] = {};
+  cudaEvent_t dev_[FZ_MAX_STAGES + 1] = {};
+  const char *cname[FZ_MAX_STAGES] = {};
+  const char *dname[FZ_MAX_STAGES] = {};
+  uint32_t nc = 0, nd = 0;
+  uint64_t launches = 0;
+};
+
+namespace {
+// Records stage boundaries of one call when profiling is on.
+struct StageClock {
+  fz_ctx *ctx;
+  cudaStream_t s;
+  bool dec;
+  uint32_t n = 0;
+  StageClock(fz_ctx *c, cudaStream_t st, bool decompress) : ctx(c), s(st), dec(decompress) {
+    if (ctx->profiling) cudaEventRecord(dec ? ctx->dev_[0] : ctx->cev[0], s);
+    (dec ? ctx->nd : ctx->nc) = 0;
+  }
+  void mark(const char *name, int kernels) {
+    ctx->launches += (uint64_t)kernels;
+    if (!ctx->profiling || n >= FZ_MAX_STAGES) return;
+    cudaEventRecord(dec ? ctx->dev_[n + 1] : ctx->cev[n + 1], s);
+    (dec ? ctx->dname : ctx->cname)[n] = name;
+    ++n;
+    (dec ? ctx->nd : ctx->nc) = n;
+  }
+};
+}  // namespace
+
+namespace fz {
+namespace {
+
+constexpr size_t kAlign = 256;
+inline size_t up(size_t v) { return (v + kAlign - 1) & ~(kAlign - 1); }
+
+fz_status from_cuda(cudaError_t e) {
+  if (e == cudaSuccess) return FZ_OK;
+  if (e == cudaErrorMemoryAllocation) return FZ_ENOMEM;
+  return FZ_ECUDA;
+}
+
+// Validate ndim/dims; fills N.
+bool valid_dims(uint32_t ndim, const uint64_t *dims, uint64_t *n) {
+  if (!dims || ndim < 1 || ndim > 3) return false;
+  uint64_t v = 1;
+  for (uint32_t a = 0; a < ndim; ++a) {
+    if (dims[a] == 0 || dims[a] >= (1ull << 32)) return false;
+    v *= dims[a];
+    if (v >= (1ull << 32)) return false;
+  }
+  *n = v;
+  return true;
+}
+
+fz_status ensure_ws(fz_ctx *ctx, size_t bytes) {
+  if (ctx->ws_bytes >= bytes) return FZ_OK;
+  if (ctx->ws) {
+    cudaFree(ctx->ws);
+    ctx->ws = nullptr;
+    ctx->ws_bytes = 0;
+  }
+  size_t want = bytes + bytes / 8;  // headroom so similar sizes do not reallocate
+  cudaError_t e = cudaMalloc(&ctx->ws, want);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    e = cudaMalloc(&ctx->ws, bytes);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      ctx->ws = nullptr;
+      return FZ_ENOMEM;
+    }
+    want = bytes;
+  }
+  ctx->ws_bytes = want;
+  return FZ_OK;
+}
+
+fz_status ensure_pinned(fz_ctx *ctx) {
+  if (ctx->h_pinned) return FZ_OK;
+  cudaError_t e = cudaMallocHost(&ctx->h_pinned, sizeof(Result) + 64);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    ctx->h_pinned = nullptr;
+    return FZ_ENOMEM;
+  }
+  return FZ_OK;
+}
+
+// Carve the compress workspace out of the context allocation.
+size_t layout_compress(const Geom &g, char *base, CompressWs &ws) {
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    char *p = base ? base + off : nullptr;
+    off += up(bytes);
+    return p;
+  };
+  const uint64_t n_etiles = (g.n_blocks + kEncWarps - 1) / kEncWarps;
+  ws.ctl = reinterpret_cast<Ctl *>(take(sizeof(Ctl)));
+  ws.qstatus = reinterpret_cast<uint64_t *>(take(8 * g.n_qtiles));
+  ws.estatus = reinterpret_cast<uint64_t *>(take(8 * n_etiles));
+  ws.zero_bytes = off;
+  ws.cap_list = g.n / 8;
+  const uint64_t cap = ws.cap_list + 1;
+  ws.codes = reinterpret_cast<uint16_t *>(take(2 * g.npad));
+  ws.anchors = reinterpret_cast<int32_t *>(take(4 * g.n_blocks));
+  ws.out_idx = reinterpret_cast<uint32_t *>(take(4 * cap));
+  ws.out_val = reinterpret_cast<int32_t *>(take(4 * cap));
+  ws.exc_idx = reinterpret_cast<uint32_t *>(take(4 * cap));
+  ws.exc_val = reinterpret_cast<uint32_t *>(take(4 * cap));
+  return off;
+}
+
+struct Req {
+  uint32_t pred, R;
+};
+
+fz_status parse_pipe(const fz_pipeline *pipe, Req &r) {
+  r.pred = FZ_PRED_LORENZO1;
+  r.R = 512;
+  if (pipe) {
+    if (pipe->struct_size < sizeof(uint32_t) * 3) return FZ_EINVAL;
+    r.pred = pipe->predictor;
+    if (pipe->radius) r.R = pipe->radius;
+  }
+  if (r.R < 2 || r.R > 512) return FZ_EINVAL;
+  if (r.pred != FZ_PRED_LORENZO1 && r.pred != FZ_PRED_LORENZO2) {
+    if (r.pred == FZ_PRED_INTERP_LIN || r.pred == FZ_PRED_INTERP_CUBIC || r.pred == FZ_SEL_MLP ||
+        r.pred == FZ_SEL_EXHAUSTIVE)
+      return FZ_EUNSUPPORTED;
+    return FZ_EINVAL;
+  }
+  return FZ_OK;
+}
+
+// Run range + quantization into `ws` (shared by compress and the stage call).
+fz_status run_front(fz_ctx *ctx, const float *d_in, const Geom &g, uint32_t eb_mode, double eb, const Req &r,
+                    const CompressWs &ws, cudaStream_t st, StageClock &clk) {
+  cudaError_t e = cudaMemsetAsync(ws.ctl, 0, ws.zero_bytes, st);
+  if (e != cudaSuccess) return from_cuda(e);
+  clk.mark("memset", 0);
+  e = launch_range(d_in, g, eb_mode, eb, ws.ctl, st);
+  if (e != cudaSuccess) return from_cuda(e);
+  clk.mark("range", 1);
+  e = launch_quant(d_in, g, r.R, r.pred, ws, st, ctx->sm_count);
+  clk.mark("quant", 1);
+  return from_cuda(e);
+}
+
+bool overlaps(const void *a, uint64_t na, const void *b, uint64_t nb) {
+  uintptr_t x = (uintptr_t)a, y = (uintptr_t)b;
+  return x < y + nb && y < x + na;
+}
+
+// Host-side validation of a stream header against the stream length.
+fz_status check_header(const fz_header &h, uint64_t in_bytes, Geom &g) {
+  if (h.magic != FZ_MAGIC || h.version != 1) return FZ_ECORRUPT;
+  uint64_t n;
+  if (!valid_dims(h.ndim, h.dims, &n)) return FZ_ECORRUPT;
+  for (uint32_t a = h.ndim; a < 3; ++a)
+    if (h.dims[a] != 1) return FZ_ECORRUPT;
+  if (h.total_bytes > in_bytes || h.total_bytes < FZ_HEADER_BYTES) return FZ_ECORRUPT;
+  make_geom(h.ndim, h.dims, g);
+  if (h.flags == FZ_FLAG_RAW) return h.total_bytes == FZ_HEADER_BYTES + 4 * n ? FZ_OK : FZ_ECORRUPT;
+  if (h.flags == FZ_FLAG_CONST) return h.total_bytes == FZ_HEADER_BYTES + 16 ? FZ_OK : FZ_ECORRUPT;
+  if (h.flags != 0) return FZ_EUNSUPPORTED;
+  if (h.radius < 2 || h.radius > 512) return FZ_ECORRUPT;
+  if (h.predictor != FZ_PRED_LORENZO1 && h.predictor != FZ_PRED_LORENZO2) return FZ_EUNSUPPORTED;
+  if (h.block[0] != g.bx || h.block[1] != g.by || h.block[2] != g.bz || h.chunk != g.bsize) return FZ_ECORRUPT;
+  if (h.n_blocks != g.n_blocks || h.n_chunks != g.n_blocks) return FZ_ECORRUPT;
+  if (h.n_out > n || h.n_exc > n || h.total_bits > 24ull * g.npad) return FZ_ECORRUPT;
+  const uint64_t secs[9][2] = {{h.off_lens, 2ull * h.radius},        {h.off_anchors, 4 * h.n_blocks},
+                               {h.off_chunk_bits, 4 * h.n_chunks},   {h.off_out_idx, 4 * h.n_out},
+                               {h.off_out_val, 4 * h.n_out},         {h.off_exc_idx, 4 * h.n_exc},
+                               {h.off_exc_val, 4 * h.n_exc},         {h.off_bits, 4 * ((h.total_bits + 31) / 32)},
+                               {h.total_bytes, 0}};
+  if (h.off_lens != FZ_HEADER_BYTES) return FZ_ECORRUPT;
+  for (int i = 0; i < 8; ++i) {
+    if (secs[i][0] & 15u) return FZ_ECORRUPT;
+    if (secs[i][0] + secs[i][1] > secs[i + 1][0]) return FZ_ECORRUPT;
+  }
+  return FZ_OK;
+}
+
+}  // namespace
+}  // namespace fz
+
+using namespace fz;
+
+extern "C" {
+
+const char *fz_status_str(fz_status s) {
+  switch (s) {
+    case FZ_OK: return "ok";
+    case FZ_EINVAL: return "invalid argument";
+    case FZ_ENOMEM: return "out of device memory";
+    case FZ_ECUDA: return "CUDA error";
+    case FZ_EBUFFER: return "output buffer too small";
+    case FZ_ECORRUPT: return "corrupt stream";
+    case FZ_ETIMEOUT: return "device wait timed out";
+    case FZ_EUNSUPPORTED: return "unsupported";
+  }
+  return "unknown status";
+}
+
+fz_status fz_ctx_create(int device, fz_ctx **out) {
+  if (!out) return FZ_EINVAL;
+  *out = nullptr;
+  int n = 0;
+  if (cudaGetDeviceCount(&n) != cudaSuccess) { cudaGetLastError(); return FZ_ECUDA; }
+  if (device < 0 || device >= n) return FZ_EINVAL;
+  fz_ctx *c = new (std::nothrow) fz_ctx();
+  if (!c) return FZ_ENOMEM;
+  c->device = device;
+  if (cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) {
+    delete c;
+    return FZ_ECUDA;
+  }
+  *out = c;
+  return FZ_OK;
+}
+
+fz_status fz_ctx_set_profiling(fz_ctx *ctx, int enable) {
+  if (!ctx) return FZ_EINVAL;
+  if (enable && !ctx->cev[0]) {
+    if (cudaSetDevice(ctx->device) != cudaSuccess) return FZ_ECUDA;
+    for (int i = 0; i <= FZ_MAX_STAGES; ++i) {
+      if (cudaEventCreate(&ctx->cev[i]) != cudaSuccess || cudaEventCreate(&ctx->dev_[i]) != cudaSuccess)
+        return FZ_ECUDA;
+    }
+  }
+  ctx->profiling = enable != 0;
+  return FZ_OK;
+}
+
+fz_status fz_ctx_get_profile(fz_ctx *ctx, fz_profile *out) {
+  if (!ctx || !out) return FZ_EINVAL;
+  memset(out, 0, sizeof(*out));
+  out->launches = ctx->launches;
+  if (!ctx->profiling) return FZ_OK;
+  if (cudaSetDevice(ctx->device) != cudaSuccess) return FZ_ECUDA;
+  for (int kind = 0; kind < 2; ++kind) {
+    const uint32_t n = kind ? ctx->nd : ctx->nc;
+    cudaEvent_t *ev = kind ? ctx->dev_ : ctx->cev;
+    if (n == 0) continue;
+    if (cudaEventSynchronize(ev[n]) != cudaSuccess) return FZ_ECUDA;
+    for (uint32_t i = 0; i < n; ++i) {
+      float ms = 0.f;
+      if (cudaEventElapsedTime(&ms, ev[i], ev[i + 1]) != cudaSuccess) return FZ_ECUDA;
+      const char *nm = kind ? ctx->dname[i] : ctx->cname[i];
+      char *dst = kind ? out->decompress_names[i] : out->compress_names[i];
+      strncpy(dst, nm ? nm : "", 15);
+      (kind ? out->decompress_ms : out->compress_ms)[i] = ms;
+    }
+    (kind ? out->n_decompress : out->n_compress) = n;
+  }
+  return FZ_OK;
+}
+
+fz_status fz_ctx_destroy(fz_ctx *ctx) {
+  if (!ctx) return FZ_OK;
+  int prev = 0;
+  cudaGetDevice(&prev);
+  cudaSetDevice(ctx->device);
+  for (int i = 0; i <= FZ_MAX_STAGES; ++i) {
+    if (ctx->cev[i]) cudaEventDestroy(ctx->cev[i]);
+    if (ctx->dev_[i]) cudaEventDestroy(ctx->dev_[i]);
+  }
+  if (ctx->ws) cudaFree(ctx->ws);
+  if (ctx->h_pinned) cudaFreeHost(ctx->h_pinned);
+  cudaSetDevice(prev);
+  delete ctx;
+  return FZ_OK;
+}
+
+uint64_t fz_compress_bound(uint32_t ndim, const uint64_t dims[3]) {
+  uint64_t n;
+  if (!valid_dims(ndim, dims, &n)) return 0;
+  return align16(FZ_HEADER_BYTES + 4 * n);
+}
+
+fz_status fz_stream_info(const void *h_header, uint64_t header_bytes, uint32_t *ndim, uint64_t dims[3],
+                         double *eb_abs, uint32_t *flags) {
+  if (!h_header || header_bytes < FZ_HEADER_BYTES) return FZ_EINVAL;
+  fz_header h;
+  memcpy(&h, h_header, sizeof(h));
+  uint64_t n;
+  if (h.magic != FZ_MAGIC || h.version != 1 || !valid_dims(h.ndim, h.dims, &n)) return FZ_ECORRUPT;
+  if (ndim) *ndim = h.ndim;
+  if (dims) for (int a = 0; a < 3; ++a) dims[a] = h.dims[a];
+  if (eb_abs) *eb_abs = h.eb_abs;
+  if (flags) *flags = h.flags;
+  return FZ_OK;
+}
+
+fz_status fz_compress(fz_ctx *ctx, const float *d_in, uint32_t ndim, const uint64_t dims[3], uint32_t eb_mode,
+                      double eb, const fz_pipeline *pipe, void *d_out, uint64_t out_cap, uint64_t *out_bytes,
+                      void *h_header, void *stream) {
+  if (!ctx || !d_in || !d_out || !out_bytes) return FZ_EINVAL;
+  uint64_t n;
+  if (!valid_dims(ndim, dims, &n)) return FZ_EINVAL;
+  if (eb_mode > FZ_EB_REL || !(eb > 0.0) || !(eb < __builtin_inf())) return FZ_EINVAL;
+  if (((uintptr_t)d_out & 15u) || ((uintptr_t)d_in & 3u)) return FZ_EINVAL;
+  Req r;
+  fz_status st = parse_pipe(pipe, r);
+  if (st) return st;
+  if (out_cap < FZ_HEADER_BYTES + 4 * n) return FZ_EBUFFER;
+  if (overlaps(d_in, 4 * n, d_out, out_cap)) return FZ_EINVAL;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  if (cudaSetDevice(ctx->device) != cudaSuccess) return FZ_ECUDA;
+  uint64_t d3[3] = {dims[0], ndim >= 2 ? dims[1] : 1, ndim >= 3 ? dims[2] : 1};
+  Geom g;
+  make_geom(ndim, d3, g);
+  CompressWs ws;
+  size_t need = layout_compress(g, nullptr, ws);
+  if ((st = ensure_ws(ctx, need)) || (st = ensure_pinned(ctx))) return st;
+  layout_compress(g, reinterpret_cast<char *>(ctx->ws), ws);
+  StageClock clk(ctx, s, false);
+  if ((st = run_front(ctx, d_in, g, eb_mode, eb, r, ws, s, clk))) return st;
+  uint8_t *out = reinterpret_cast<uint8_t *>(d_out);
+  cudaError_t e = launch_codebook(g, r.R, r.pred, eb_mode, eb, ws, s);
+  clk.mark("codebook", 1);
+  if (e == cudaSuccess) { e = launch_encode(g, ws, out, s); clk.mark("encode", 1); }
+  if (e == cudaSuccess) { e = launch_assemble(d_in, g, r.R, ws, out, s, ctx->sm_count); clk.mark("assemble", 1); }
+  if (e == cudaSuccess) e = cudaMemcpyAsync(ctx->h_pinned, &ws.ctl->res, sizeof(Result), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return from_cuda(e);
+  const Result *res = reinterpret_cast<const Result *>(ctx->h_pinned);
+  if (res->err) return (fz_status)res->err;
+  *out_bytes = res->total_bytes;
+  if (h_header) memcpy(h_header, &res->hdr, FZ_HEADER_BYTES);
+  return FZ_OK;
+}
+
+fz_status fz_decompress(fz_ctx *ctx, const void *d_in, uint64_t in_bytes, const void *h_header, float *d_out,
+                        uint64_t out_cap_values, void *stream) {
+  if (!ctx || !d_in || !d_out || in_bytes < FZ_HEADER_BYTES) return FZ_EINVAL;
+  if (((uintptr_t)d_in & 15u) || ((uintptr_t)d_out & 3u)) return FZ_EINVAL;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  if (cudaSetDevice(ctx->device) != cudaSuccess) return FZ_ECUDA;
+  fz_status st = ensure_pinned(ctx);
+  if (st) return st;
+  fz_header h;
+  if (h_header) {
+    memcpy(&h, h_header, sizeof(h));
+  } else {
+    cudaError_t e = cudaMemcpyAsync(ctx->h_pinned, d_in, FZ_HEADER_BYTES, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return from_cuda(e);
+    memcpy(&h, ctx->h_pinned, sizeof(h));
+  }
+  Geom g;
+  if ((st = check_header(h, in_bytes, g))) return st;
+  if (out_cap_values < g.n) return FZ_EBUFFER;
+  if (overlaps(d_in, in_bytes, d_out, 4 * g.n)) return FZ_EINVAL;
+  const uint8_t *in = reinterpret_cast<const uint8_t *>(d_in);
+  cudaError_t e = cudaSuccess;
+  if (h.flags == FZ_FLAG_RAW) {
+    e = cudaMemcpyAsync(d_out, in + FZ_HEADER_BYTES, 4 * g.n, cudaMemcpyDeviceToDevice, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    return from_cuda(e);
+  }
+  if (h.flags == FZ_FLAG_CONST) {
+    uint32_t bits = 0;
+    e = cudaMemcpyAsync(ctx->h_pinned, in + FZ_HEADER_BYTES, 4, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return from_cuda(e);
+    memcpy(&bits, ctx->h_pinned, 4);
+    e = launch_fill(d_out, g.n, bits, s, ctx->sm_count);
+    ctx->launches += 1;
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    return from_cuda(e);
+  }
+  const uint64_t n_groups = (h.n_chunks + kDecThreads - 1) / kDecThreads;
+  size_t off = 0;
+  auto take = [&](size_t bytes) { size_t o = off; off += up(bytes); return o; };
+  const size_t o_err = take(16), o_lut = take(4u << kLutBits), o_ltab = take(4 * (75 + kMaxSym)),
+               o_gsum = take(8 * n_groups);
+  if ((st = ensure_ws(ctx, off))) return st;
+  char *base = reinterpret_cast<char *>(ctx->ws);
+  DecodeWs ws;
+  ws.err = reinterpret_cast<uint32_t *>(base + o_err);
+  ws.lut = reinterpret_cast<uint32_t *>(base + o_lut);
+  ws.ltab = reinterpret_cast<uint32_t *>(base + o_ltab);
+  ws.gsum = reinterpret_cast<uint64_t *>(base + o_gsum);
+  StageClock clk(ctx, s, true);
+  e = cudaMemsetAsync(ws.err, 0, 16, s);
+  if (e == cudaSuccess) { e = launch_decode_prep(in, h, ws, s); clk.mark("dec_prep", 2); }
+  if (e == cudaSuccess) { e = launch_decode_main(in, h, d_out, ws, s); clk.mark("decode", 1); }
+  if (e == cudaSuccess) e = cudaMemcpyAsync(ctx->h_pinned, ws.err, 4, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return from_cuda(e);
+  uint32_t err;
+  memcpy(&err, ctx->h_pinned, 4);
+  return (fz_status)err;
+}
+
+fz_status fz_lorenzo_quantize(fz_ctx *ctx, const float *d_in, uint32_t ndim, const uint64_t dims[3],
+                              uint32_t eb_mode, double eb, const fz_pipeline *pipe, uint16_t *d_codes,
+                              int32_t *d_anchors, uint64_t *d_hist, uint64_t *n_out, uint64_t *n_exc,
+                              double *eb_abs, void *stream) {
+  if (!ctx || !d_in || !d_codes || !d_anchors || !d_hist || !n_out || !n_exc || !eb_abs) return FZ_EINVAL;
+  uint64_t n;
+  if (!valid_dims(ndim, dims, &n)) return FZ_EINVAL;
+  if (eb_mode > FZ_EB_REL || !(eb > 0.0) || !(eb < __builtin_inf())) return FZ_EINVAL;
+  if (((uintptr_t)d_codes & 15u) || ((uintptr_t)d_in & 3u) || ((uintptr_t)d_anchors & 3u)) return FZ_EINVAL;
+  Req r;
+  fz_status st = parse_pipe(pipe, r);
+  if (st) return st;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  if (cudaSetDevice(ctx->device) != cudaSuccess) return FZ_ECUDA;
+  uint64_t d3[3] = {dims[0], ndim >= 2 ? dims[1] : 1, ndim >= 3 ? dims[2] : 1};
+  Geom g;
+  make_geom(ndim, d3, g);
+  CompressWs ws;
+  size_t need = layout_compress(g, nullptr, ws);
+  if ((st = ensure_ws(ctx, need)) || (st = ensure_pinned(ctx))) return st;
+  layout_compress(g, reinterpret_cast<char *>(ctx->ws), ws);
+  ws.codes = d_codes;
+  ws.anchors = d_anchors;
+  StageClock clk(ctx, s, false);
+  if ((st = run_front(ctx, d_in, g, eb_mode, eb, r, ws, s, clk))) return st;
+  cudaError_t e = cudaMemcpyAsync(d_hist, ws.ctl->hist, 8ull * 2 * r.R, cudaMemcpyDeviceToDevice, s);
+  // gather the scalar results: counts, bound and error word
+  struct Small { unsigned long long n_out, n_exc; double eb_abs; uint32_t err, mode; };
+  Small *hs = reinterpret_cast<Small *>(ctx->h_pinned);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&hs->n_out, &ws.ctl->n_out, 16, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&hs->eb_abs, &ws.ctl->eb_abs, 8, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&hs->err, &ws.ctl->res.err, 4, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return from_cuda(e);
+  if (hs->err) return (fz_status)hs->err;
+  *n_out = hs->n_out;
+  *n_exc = hs->n_exc;
+  *eb_abs = hs->eb_abs;
+  return FZ_OK;
+}
+
+fz_status fz_huffman_codebook(fz_ctx *ctx, const uint64_t *d_hist, uint32_t nsym, uint8_t *d_lens,
+                              uint32_t *d_codes, void *stream) {
+  if (!ctx || !d_hist || !d_lens || !d_codes || nsym == 0 || nsym > (uint32_t)kMaxSym) return FZ_EINVAL;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  if (cudaSetDevice(ctx->device) != cudaSuccess) return FZ_ECUDA;
+  fz_status st = ensure_ws(ctx, up(sizeof(Ctl)));
+  if (st) return st;
+  Ctl *ctl = reinterpret_cast<Ctl *>(ctx->ws);
+  if ((st = ensure_pinned(ctx))) return st;
+  cudaError_t e = cudaMemsetAsync(&ctl->res.err, 0, 4, s);
+  if (e == cudaSuccess) { e = launch_codebook_only(d_hist, nsym, d_lens, d_codes, ctl, s); ctx->launches += 1; }
+  if (e == cudaSuccess) e = cudaMemcpyAsync(ctx->h_pinned, &ctl->res.err, 4, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return from_cuda(e);
+  uint32_t err;
+  memcpy(&err, ctx->h_pinned, 4);
+  return (fz_status)err;
+}
+
+}  // extern "C"

@@ -1,0 +1,289 @@
+// fz_codebook.cu -- Huffman codebook module (FZModules §3.2: the Huffman
+// encoder is fed by the histogram of quantization codes) and the stream
+// layout decision.  One CTA of 1024 threads:
+//   1. bitonic sort of (count, symbol) keys of the used symbols;
+//   2. two-queue Huffman merge (one thread; ties take the leaf);
+//   3. node depths by pointer jumping (log rounds, all threads);
+//   4. 24-bit length limit by halving counts and rebuilding;
+//   5. canonical codewords in RFC 1951 order via warp ballots;
+//   6. total bit count, section offsets, raw-fallback rule and the header.
+#include "fz_internal.cuh"
+
+namespace fz {
+
+namespace {
+
+constexpr int kCbThreads = 1024;
+
+struct CbSmem {
+  unsigned long long key[kMaxSym];
+  unsigned long long cnt[kMaxSym];
+  unsigned long long lw[kMaxSym];   // sorted leaf weights
+  unsigned long long iw[kMaxSym];   // internal node weights
+  uint16_t lsym[kMaxSym];           // sorted leaf symbols
+  int16_t lpar[kMaxSym], ipar[kMaxSym];
+  int16_t dep[2][kMaxSym], anc[2][kMaxSym];
+  uint8_t len[kMaxSym];
+  uint32_t wcnt[32][kLmax + 1];
+  uint32_t next_code[kLmax + 2];
+  uint32_t m, maxlen;
+  unsigned long long total_bits;
+};
+
+// Code lengths (into s.len) and canonical codewords (into code[]) for the
+// counts in s.cnt[0..nsym).  Returns false if no symbol is used.
+__device__ bool build_codebook(CbSmem &s, uint32_t nsym, uint32_t *code_out) {
+  const int t = threadIdx.x;
+  for (int iter = 0; iter < 64; ++iter) {
+    // ---- 1. sort keys (count << 10 | symbol); unused symbols sort last
+    s.key[t] = (t < (int)nsym && s.cnt[t]) ? ((s.cnt[t] << 10) | (unsigned long long)t) : ~0ull;
+    if (t == 0) { s.m = 0; s.maxlen = 0; }
+    s.len[t] = 0;
+    __syncthreads();
+    for (int k = 2; k <= kMaxSym; k <<= 1) {
+      for (int j = k >> 1; j > 0; j >>= 1) {
+        int ixj = t ^ j;
+        if (ixj > t) {
+          bool asc = (t & k) == 0;
+          unsigned long long a = s.key[t], b = s.key[ixj];
+          if ((a > b) == asc) { s.key[t] = b; s.key[ixj] = a; }
+        }
+        __syncthreads();
+      }
+    }
+    if (s.key[t] != ~0ull) atomicAdd(&s.m, 1u);
+    __syncthreads();
+    const uint32_t m = s.m;
+    if (m == 0) return false;
+    if ((uint32_t)t < m) {
+      s.lsym[t] = (uint16_t)(s.key[t] & 1023u);
+      s.lw[t] = s.key[t] >> 10;
+    }
+    __syncthreads();
+    if (m == 1) {
+      if (t == 0) { s.len[s.lsym[0]] = 1; s.maxlen = 1; }
+      __syncthreads();
+      break;
+    }
+    // ---- 2. two-queue merge (serial); internal node k = merge number k
+    if (t == 0) {
+      uint32_t li = 0, ih = 0;
+      unsigned long long lf = s.lw[0], inf = 0;
+      for (uint32_t k = 0; k + 1 < m; ++k) {
+        unsigned long long sum = 0;
+#pragma unroll
+        for (int take = 0; take < 2; ++take) {
+          bool have_i = ih < k;
+          bool leaf = li < m && (!have_i || lf <= inf);
+          if (leaf) {
+            sum += lf;
+            s.lpar[li] = (int16_t)k;
+            ++li;
+            lf = li < m ? s.lw[li] : 0ull;
+          } else {
+            sum += inf;
+            s.ipar[ih] = (int16_t)k;
+            ++ih;
+            inf = ih < k ? s.iw[ih] : 0ull;
+          }
+        }
+        s.iw[k] = sum;
+        if (ih == k) inf = sum;
+      }
+    }
+    __syncthreads();
+    // ---- 3. depth of every internal node by pointer jumping
+    const int root = (int)m - 2;
+    if (t < (int)m - 1) {
+      s.dep[0][t] = (t == root) ? 0 : 1;
+      s.anc[0][t] = (t == root) ? (int16_t)root : s.ipar[t];
+    }
+    __syncthreads();
+    int cur = 0;
+    for (int r = 0; (1 << r) < (int)m; ++r) {
+      if (t < (int)m - 1) {
+        int a = s.anc[cur][t];
+        s.dep[cur ^ 1][t] = s.dep[cur][t] + s.dep[cur][a];
+        s.anc[cur ^ 1][t] = s.anc[cur][a];
+      }
+      __syncthreads();
+      cur ^= 1;
+    }
+    if ((uint32_t)t < m) {
+      int l = s.dep[cur][s.lpar[t]] + 1;
+      s.len[s.lsym[t]] = (uint8_t)(l > 255 ? 255 : l);
+      atomicMax(&s.maxlen, (uint32_t)l);
+    }
+    __syncthreads();
+    if (s.maxlen <= (uint32_t)kLmax) break;
+    // ---- 4. length limit: halve the counts and rebuild
+    if (t < (int)nsym && s.cnt[t]) s.cnt[t] = (s.cnt[t] + 1) >> 1;
+    __syncthreads();
+  }
+  // ---- 5. canonical codewords (RFC 1951 order)
+  const int lane = t & 31, warp = t >> 5;
+  const int L = (t < (int)nsym) ? s.len[t] : 0;
+  if (t < 32 * (kLmax + 1)) (&s.wcnt[0][0])[t] = 0;
+  __syncthreads();
+  uint32_t rank = 0;
+#pragma unroll 1
+  for (int l = 1; l <= kLmax; ++l) {
+    uint32_t b = __ballot_sync(0xffffffffu, L == l);
+    if (L == l) rank = __popc(b & ((1u << lane) - 1));
+    if (lane == 0) s.wcnt[warp][l] = __popc(b);
+  }
+  __syncthreads();
+  if (t >= 1 && t <= kLmax) {  // exclusive prefix over warps for length t
+    uint32_t acc = 0;
+    for (int w = 0; w < 32; ++w) { uint32_t v = s.wcnt[w][t]; s.wcnt[w][t] = acc; acc += v; }
+    s.wcnt[0][0] = 0;
+    // total per length stored in next_code temporarily via a second pass below
+    s.next_code[t] = acc;
+  }
+  __syncthreads();
+  if (t == 0) {
+    uint32_t bl[kLmax + 1];
+    bl[0] = 0;
+    for (int l = 1; l <= kLmax; ++l) bl[l] = s.next_code[l];
+    uint32_t c = 0;
+    for (int l = 1; l <= kLmax; ++l) {
+      c = (c + bl[l - 1]) << 1;
+      s.next_code[l] = c;
+    }
+  }
+  __syncthreads();
+  if (t < (int)nsym) code_out[t] = L ? (s.next_code[L] + s.wcnt[warp][L] + rank) : 0u;
+  return true;
+}
+
+__device__ void write_min_header(fz_header &h, uint16_t flags, const Geom &g, uint32_t eb_mode, double eb,
+                                 uint64_t total) {
+  uint8_t *p = reinterpret_cast<uint8_t *>(&h);
+  for (int i = 0; i < (int)sizeof(fz_header); ++i) p[i] = 0;
+  h.magic = FZ_MAGIC;
+  h.version = 1;
+  h.flags = flags;
+  h.ndim = g.ndim;
+  h.eb_mode = eb_mode;
+  h.dims[0] = g.nx; h.dims[1] = g.ny; h.dims[2] = g.nz;
+  h.eb = eb;
+  h.total_bytes = total;
+}
+
+__global__ void __launch_bounds__(kCbThreads) k_codebook(Geom g, uint32_t R, uint32_t pred, uint32_t eb_mode,
+                                                          double eb, CompressWs ws) {
+  extern __shared__ __align__(16) unsigned char cb_smem[];
+  CbSmem &s = *reinterpret_cast<CbSmem *>(cb_smem);
+  __shared__ uint32_t s_mode;
+  Ctl *ctl = ws.ctl;
+  const int t = threadIdx.x;
+  const uint32_t nsym = 2 * R;
+  if (t == 0) {
+    uint32_t mode = ctl->mode;
+    if (mode == kModeNormal && ctl->n_out + ctl->n_exc > ws.cap_list) mode = kModeRaw;
+    s_mode = mode;
+    s.total_bits = 0;
+  }
+  __syncthreads();
+  uint32_t mode = s_mode;
+  if (mode == kModeNormal) {
+    s.cnt[t] = t < (int)nsym ? ctl->hist[t] : 0ull;
+    __syncthreads();
+    bool ok = build_codebook(s, nsym, ctl->enc);
+    __syncthreads();
+    if (!ok) {
+      if (t == 0) set_err(ctl, FZ_ECORRUPT);
+      return;
+    }
+    if (t < (int)nsym) {
+      uint32_t L = s.len[t];
+      ctl->lens[t] = (uint8_t)L;
+      ctl->enc[t] = (L << 24) | ctl->enc[t];
+      unsigned long long b = ctl->hist[t] * (unsigned long long)L;
+      if (b) atomicAdd(&s.total_bits, b);
+    }
+    __syncthreads();
+  }
+  if (t != 0) return;
+  fz_header &h = ctl->res.hdr;
+  const uint64_t N = g.n;
+  if (mode == kModeNormal) {
+    const uint64_t nb = g.n_blocks, nch = g.n_blocks;
+    const uint64_t n_out = ctl->n_out, n_exc = ctl->n_exc, tb = s.total_bits;
+    const uint64_t off_lens = FZ_HEADER_BYTES;
+    const uint64_t off_anch = align16(off_lens + nsym);
+    const uint64_t off_cb = align16(off_anch + 4 * nb);
+    const uint64_t off_oidx = align16(off_cb + 4 * nch);
+    const uint64_t off_oval = align16(off_oidx + 4 * n_out);
+    const uint64_t off_eidx = align16(off_oval + 4 * n_out);
+    const uint64_t off_eval = align16(off_eidx + 4 * n_exc);
+    const uint64_t off_bits = align16(off_eval + 4 * n_exc);
+    const uint64_t total = align16(off_bits + 4 * ((tb + 31) / 32));
+    if (total > FZ_HEADER_BYTES + 4 * N) {
+      mode = kModeRaw;
+    } else {
+      write_min_header(h, 0, g, eb_mode, eb, total);
+      h.eb_abs = ctl->eb_abs;
+      h.ebx2_bits = __float_as_uint(ctl->ebx2);
+      h.inv2eb_bits = __float_as_uint(ctl->inv2eb);
+      h.ebchk_bits = __float_as_uint(ctl->eb_chk);
+      h.radius = R;
+      h.block[0] = g.bx; h.block[1] = g.by; h.block[2] = g.bz;
+      h.predictor = pred;
+      h.chunk = g.bsize;
+      h.n_blocks = nb; h.n_chunks = nch; h.n_out = n_out; h.n_exc = n_exc; h.total_bits = tb;
+      h.off_lens = off_lens; h.off_ids = 0; h.off_anchors = off_anch; h.off_chunk_bits = off_cb;
+      h.off_out_idx = off_oidx; h.off_out_val = off_oval; h.off_exc_idx = off_eidx; h.off_exc_val = off_eval;
+      h.off_bits = off_bits;
+      ctl->total_bits = tb;
+    }
+  }
+  if (mode == kModeRaw) write_min_header(h, FZ_FLAG_RAW, g, eb_mode, eb, FZ_HEADER_BYTES + 4 * N);
+  if (mode == kModeConst) write_min_header(h, FZ_FLAG_CONST, g, eb_mode, eb, FZ_HEADER_BYTES + 16);
+  ctl->mode = mode;
+  ctl->res.mode = mode;
+  ctl->res.total_bytes = h.total_bytes;
+  ctl->res.n_out = ctl->n_out;
+  ctl->res.n_exc = ctl->n_exc;
+}
+
+__global__ void __launch_bounds__(kCbThreads) k_codebook_only(const uint64_t *hist, uint32_t nsym, uint8_t *lens,
+                                                               uint32_t *codes, Ctl *ctl) {
+  extern __shared__ __align__(16) unsigned char cb_smem[];
+  CbSmem &s = *reinterpret_cast<CbSmem *>(cb_smem);
+  const int t = threadIdx.x;
+  s.cnt[t] = t < (int)nsym ? hist[t] : 0ull;
+  __syncthreads();
+  bool ok = build_codebook(s, nsym, codes);
+  __syncthreads();
+  if (!ok) {
+    if (t == 0) set_err(ctl, FZ_EINVAL);
+    return;
+  }
+  if (t < (int)nsym) lens[t] = s.len[t];
+}
+
+}  // namespace
+
+cudaError_t launch_codebook(const Geom &g, uint32_t R, uint32_t pred, uint32_t eb_mode, double eb,
+                            const CompressWs &ws, cudaStream_t st) {
+  static bool attr_set = false;  // the attribute is per function; setting it twice is harmless
+  if (!attr_set) {
+    cudaError_t e = cudaFuncSetAttribute(k_codebook, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(CbSmem));
+    if (e != cudaSuccess) return e;
+    attr_set = true;
+  }
+  k_codebook<<<1, kCbThreads, sizeof(CbSmem), st>>>(g, R, pred, eb_mode, eb, ws);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_codebook_only(const uint64_t *hist, uint32_t nsym, uint8_t *lens, uint32_t *codes, Ctl *ctl,
+                                 cudaStream_t st) {
+  cudaError_t e =
+      cudaFuncSetAttribute(k_codebook_only, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(CbSmem));
+  if (e != cudaSuccess) return e;
+  k_codebook_only<<<1, kCbThreads, sizeof(CbSmem), st>>>(hist, nsym, lens, codes, ctl);
+  return cudaGetLastError();
+}
+
+}  // namespace fz

@@ -1,0 +1,216 @@
+// fz_internal.cuh -- device-side data structures shared by the kernels of
+// libfz.so: the per-call control block, the workspace layout, block/tile
+// geometry, bounded decoupled look-back and small device helpers.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/fz.h"
+
+namespace fz {
+
+constexpr int kMaxSym = 1024;      // 2R <= 1024 (R <= 512)
+constexpr int kLmax = 24;          // longest Huffman codeword
+constexpr int kLutBits = 12;       // first-level decode table width
+constexpr int kTileElems = 4096;   // elements per quantization tile
+constexpr int kQuantThreads = 256; // 8 warps per quantization tile
+constexpr int kEncWarps = 8;       // chunks per encode tile (one warp per chunk)
+constexpr int kDecThreads = 128;   // chunks per decode CTA (one thread per chunk)
+
+enum Mode : uint32_t { kModeNormal = 0, kModeConst = 1, kModeRaw = 2 };
+
+// Block geometry: block shape per dimensionality (1D 1024, 2D 32x32,
+// 3D 8x8x8) and the field extents, x fastest.
+struct Geom {
+  uint32_t ndim;
+  uint32_t nx, ny, nz;     // extents (unused axes 1)
+  uint32_t bx, by, bz;     // block extents
+  uint32_t nbx, nby, nbz;  // blocks per axis
+  uint32_t bsize;          // elements per block
+  uint64_t n;              // nx*ny*nz
+  uint64_t n_blocks;
+  uint64_t npad;           // n_blocks * bsize
+  // quantization tiles: NB consecutive blocks along x
+  uint32_t tile_nb;        // blocks per tile along x
+  uint32_t tiles_x;        // tiles per block-row
+  uint64_t n_qtiles;
+};
+
+inline __host__ __device__ void make_geom(uint32_t ndim, const uint64_t dims[3], Geom &g) {
+  g.ndim = ndim;
+  g.nx = (uint32_t)dims[0];
+  g.ny = ndim >= 2 ? (uint32_t)dims[1] : 1u;
+  g.nz = ndim >= 3 ? (uint32_t)dims[2] : 1u;
+  if (ndim == 1) { g.bx = 1024; g.by = 1; g.bz = 1; g.tile_nb = 4; }
+  else if (ndim == 2) { g.bx = 32; g.by = 32; g.bz = 1; g.tile_nb = 4; }
+  else { g.bx = 8; g.by = 8; g.bz = 8; g.tile_nb = 8; }
+  g.nbx = (g.nx + g.bx - 1) / g.bx;
+  g.nby = (g.ny + g.by - 1) / g.by;
+  g.nbz = (g.nz + g.bz - 1) / g.bz;
+  g.bsize = g.bx * g.by * g.bz;
+  g.n = (uint64_t)g.nx * g.ny * g.nz;
+  g.n_blocks = (uint64_t)g.nbx * g.nby * g.nbz;
+  g.npad = g.n_blocks * g.bsize;
+  g.tiles_x = (g.nbx + g.tile_nb - 1) / g.tile_nb;
+  g.n_qtiles = (uint64_t)g.tiles_x * g.nby * g.nbz;
+}
+
+// Per-call control block.  Zeroed by one memset at the start of each
+// compress; every field is designed so that zero is the right initial value.
+struct Result {
+  uint64_t total_bytes;
+  uint32_t err;            // first fz_status reported by a kernel (0 = none)
+  uint32_t mode;
+  uint64_t n_out, n_exc;
+  fz_header hdr;           // the stream header as written
+};
+
+struct Ctl {
+  unsigned long long hist[kMaxSym];
+  // REL range: max of inverted ordered keys for the minimum, max of ordered
+  // keys for the maximum, and the same on raw bit patterns.
+  unsigned int lo_nkey, hi_key, bits_nmin, bits_max, any_finite, range_done;
+  unsigned int quant_ticket, encode_ticket;
+  unsigned long long n_out, n_exc;
+  // constants (written by the range tail or the ABS constants kernel)
+  double eb_abs;
+  float ebx2, inv2eb, eb_chk;
+  uint32_t mode;           // Mode after the range stage
+  uint32_t const_bits;
+  uint32_t pad0;
+  // codebook results
+  uint32_t enc[kMaxSym];   // (len << 24) | codeword
+  uint8_t lens[kMaxSym];
+  uint64_t total_bits;
+  Result res;
+};
+
+// ---------------------------------------------------------------- errors
+__device__ __forceinline__ void set_err(Ctl *ctl, uint32_t code) { atomicCAS(&ctl->res.err, 0u, code); }
+
+// ---------------------------------------------------------------- ordered float keys
+// Monotone map from float bit patterns to unsigned keys (for atomic min/max).
+__device__ __forceinline__ uint32_t fkey(float f) {
+  uint32_t u = __float_as_uint(f);
+  return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+__device__ __forceinline__ float fkey_inv(uint32_t k) {
+  uint32_t u = (k & 0x80000000u) ? (k & 0x7fffffffu) : ~k;
+  return __uint_as_float(u);
+}
+
+// ---------------------------------------------------------------- constants
+// eb_abs -> bin width ebx2 (rounded down), its reciprocal (nearest), and the
+// per-value check bound (rounded down); each step one IEEE operation.
+__device__ __forceinline__ void device_constants(double eb_abs, float &ebx2, float &inv2eb, float &eb_chk) {
+  double w = __dmul_rn(2.0, eb_abs);
+  w = __dmul_rn(w, 1.0 - 0x1p-12);
+  ebx2 = __double2float_rd(w);
+  double inv = __ddiv_rn(1.0, (double)ebx2);
+  inv2eb = __double2float_rn(inv);
+  double c = __dmul_rn(eb_abs, 1.0 - 0x1p-23);
+  eb_chk = __double2float_rd(c);
+}
+
+// ---------------------------------------------------------------- bounded decoupled look-back
+// Status word per tile: bits 63..62 = 1 (aggregate) or 2 (inclusive prefix),
+// low 62 bits = value.  Tiles are numbered in the order they are claimed from
+// a ticket counter, so every predecessor is resident or finished and the wait
+// always ends; the clock bound only guards against a corrupted state.
+constexpr uint64_t kLbFlagAgg = 1ull << 62;
+constexpr uint64_t kLbFlagInc = 2ull << 62;
+constexpr uint64_t kLbMask = (1ull << 62) - 1;
+constexpr long long kSpinCycles = 4000000000ll;  // about two seconds at 2 GHz
+
+__device__ __forceinline__ uint64_t ld_volatile_u64(const uint64_t *p) {
+  return *(const volatile uint64_t *)p;
+}
+__device__ __forceinline__ void st_status(uint64_t *p, uint64_t v) {
+  atomicExch((unsigned long long *)p, (unsigned long long)v);
+}
+
+// Combine two packed values.  `packed2` packs two 31-bit saturating counters.
+template <bool kPacked2>
+__device__ __forceinline__ uint64_t lb_add(uint64_t a, uint64_t b) {
+  if (!kPacked2) return (a + b) & kLbMask;
+  const uint64_t m = (1ull << 31) - 1;
+  uint64_t lo = (a & m) + (b & m), hi = ((a >> 31) & m) + ((b >> 31) & m);
+  lo = lo > m ? m : lo;
+  hi = hi > m ? m : hi;
+  return lo | (hi << 31);
+}
+
+// Called by one thread of the tile.  Returns the exclusive prefix.
+template <bool kPacked2>
+__device__ uint64_t lookback(uint64_t *status, uint64_t tile, uint64_t agg, Ctl *ctl) {
+  if (tile == 0) {
+    st_status(&status[0], kLbFlagInc | agg);
+    return 0;
+  }
+  st_status(&status[tile], kLbFlagAgg | agg);
+  uint64_t excl = 0;
+  int64_t j = (int64_t)tile - 1;
+  long long t0 = clock64();
+  while (j >= 0) {
+    uint64_t v = ld_volatile_u64(&status[j]);
+    if ((v >> 62) == 0) {
+      if (clock64() - t0 > kSpinCycles) {
+        set_err(ctl, FZ_ETIMEOUT);
+        break;
+      }
+      __nanosleep(32);
+      continue;
+    }
+    excl = lb_add<kPacked2>(excl, v & kLbMask);
+    if ((v >> 62) == 2) break;
+    j--;
+  }
+  st_status(&status[tile], kLbFlagInc | lb_add<kPacked2>(excl, agg));
+  return excl;
+}
+
+inline __host__ __device__ uint64_t align16(uint64_t v) { return (v + 15u) & ~(uint64_t)15u; }
+
+// ---------------------------------------------------------------- workspace layout
+// Device scratch owned by the context for one compress call.
+struct CompressWs {
+  Ctl *ctl;
+  uint64_t *qstatus;       // look-back status per quantization tile
+  uint64_t *estatus;       // look-back status per encode tile
+  size_t zero_bytes;       // bytes from ctl to the end of estatus (memset per call)
+  uint16_t *codes;         // npad block-major codes
+  int32_t *anchors;        // n_blocks
+  uint32_t *out_idx;       // cap_list
+  int32_t *out_val;
+  uint32_t *exc_idx;
+  uint32_t *exc_val;
+  uint64_t cap_list;       // floor(N/8)
+};
+
+}  // namespace fz
+
+// Host-side launchers (defined in the .cu files).
+namespace fz {
+cudaError_t launch_range(const float *x, const Geom &g, uint32_t eb_mode, double eb, Ctl *ctl, cudaStream_t s);
+cudaError_t launch_quant(const float *x, const Geom &g, uint32_t R, uint32_t pred, const CompressWs &ws,
+                         cudaStream_t s, int sm_count);
+cudaError_t launch_codebook(const Geom &g, uint32_t R, uint32_t pred, uint32_t eb_mode, double eb,
+                            const CompressWs &ws, cudaStream_t s);
+cudaError_t launch_encode(const Geom &g, const CompressWs &ws, uint8_t *d_out, cudaStream_t s);
+cudaError_t launch_assemble(const float *x, const Geom &g, uint32_t R, const CompressWs &ws, uint8_t *d_out,
+                            cudaStream_t s, int sm_count);
+cudaError_t launch_codebook_only(const uint64_t *hist, uint32_t nsym, uint8_t *lens, uint32_t *codes,
+                                 Ctl *ctl, cudaStream_t s);
+
+struct DecodeWs {
+  uint32_t *lut;           // 1 << kLutBits entries: (len << 16) | sym, len 0 = long code
+  uint32_t *ltab;          // long-code tables: first[25], count[25], base[25], sorted syms[1024]
+  uint64_t *gsum;          // per decode group: sum of chunk bits, then exclusive offset
+  uint32_t *err;           // device error word
+};
+cudaError_t launch_decode_prep(const uint8_t *d_in, const fz_header &h, const DecodeWs &ws, cudaStream_t s);
+cudaError_t launch_decode_main(const uint8_t *d_in, const fz_header &h, float *d_out, const DecodeWs &ws,
+                               cudaStream_t s);
+cudaError_t launch_fill(float *out, uint64_t n, uint32_t bits, cudaStream_t s, int sm_count);
+}  // namespace fz

@@ -1,0 +1,245 @@
+"""GPU parity: the CUDA path through the C ABI against the CPU oracle.
+
+The stream format is fully determined by the method's readings (rounding,
+block order, Huffman tie-break, bit order), so the GPU stream must equal the
+oracle's byte for byte and the reconstructions must be bit-identical.  Sizes
+span several quantization/encode/decode tiles and ragged tails; the last
+tests run the full workload sizes of the benchmark.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+fz = None
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    global fz
+    from paper_2509_20563_gb300 import build
+    build.build()
+    import paper_2509_20563_gb300 as m
+    m.lib()
+    fz = m
+
+
+def _bits(a):
+    return np.ascontiguousarray(a, dtype=np.float32).view(np.uint32)
+
+
+def _eb_abs(x, eb, mode):
+    if mode == "abs":
+        return eb
+    f = x[np.isfinite(x)]
+    return eb * (float(f.max()) - float(f.min()))
+
+
+def _roundtrip_check(x, eb, mode="rel", predictor="lorenzo1", radius=512):
+    k = 2 if predictor == "lorenzo2" else 1
+    ref = oracle.compress(x, eb, mode, lorenzo_k=k, radius=radius)
+    xd = torch.from_numpy(np.ascontiguousarray(x)).cuda()
+    buf = fz.compress(xd, eb, mode, predictor=predictor, radius=radius)
+    got = buf.cpu().numpy()
+    assert got.size == ref.size, (got.size, ref.size)
+    if not np.array_equal(got, ref):
+        diff = np.nonzero(got != ref)[0]
+        raise AssertionError(f"stream differs at {diff.size} bytes, first at {diff[0]}")
+    y = fz.decompress(buf).cpu().numpy()
+    yref = oracle.decompress(ref)
+    assert y.shape == x.shape
+    assert np.array_equal(_bits(y), _bits(yref))
+    # the GPU decoder also reads the oracle's stream (cross-decode)
+    y2 = fz.decompress(torch.from_numpy(ref).cuda()).cpu().numpy()
+    assert np.array_equal(_bits(y2), _bits(yref))
+    eba = _eb_abs(x, eb, mode)
+    fin = np.isfinite(x)
+    assert (np.abs(x[fin].astype(np.float64) - y[fin].astype(np.float64)) <= eba).all()
+    assert np.array_equal(_bits(x[~fin]), _bits(y[~fin]))
+    return got
+
+
+SHAPES = [(1,), (37,), (1024,), (5000,), (20000,), (1, 1), (61, 45), (100, 100), (33, 300), (1, 1, 1),
+          (8, 8, 8), (17, 9, 33), (40, 37, 70), (16, 64, 130)]
+
+
+@pytest.mark.parametrize("shape", SHAPES)
+@pytest.mark.parametrize("predictor", ["lorenzo1", "lorenzo2"])
+def test_stream_bit_exact_shapes(shape, predictor):
+    x = synth.smooth_nd(shape, seed=sum(shape)).numpy()
+    _roundtrip_check(x, 1e-3, "rel", predictor)
+
+
+@pytest.mark.parametrize("eb,mode,radius", [(1e-2, "rel", 512), (1e-4, "rel", 512), (1e-5, "rel", 512),
+                                            (0.05, "abs", 512), (1e-3, "rel", 64), (1e-3, "rel", 2)])
+def test_stream_bit_exact_bounds_and_radius(eb, mode, radius):
+    x = synth.blobs3d((40, 48, 56), seed=11).numpy()
+    _roundtrip_check(x, eb, mode, radius=radius)
+
+
+def test_workload_generators_small():
+    _roundtrip_check(synth.blobs3d().numpy(), 1e-3)                                  # 64^3, REL 1e-3
+    _roundtrip_check(synth.grf3d(64, device="cpu").numpy(), 1e-4)
+    _roundtrip_check(synth.hacc1d(1 << 20, device="cpu").numpy(), 1e-4)
+    _roundtrip_check(synth.cesm2d(180, 360).numpy(), 1e-3)
+
+
+def test_special_values():
+    x = synth.smooth_nd((30, 40, 20), 5).numpy()
+    x[3, 4, 5] = np.nan
+    x[10, 10, 10] = np.inf
+    x[20, 1, 0] = -np.inf
+    x[0, 0, 0] = 3e38
+    _roundtrip_check(x, 1e-3)
+    # constant field -> CONST stream
+    got = _roundtrip_check(np.full((10, 11), 3.25, np.float32), 1e-3)
+    assert got.size == 272
+    # all NaN with identical bits -> CONST; mixed zeros of both signs -> RAW
+    _roundtrip_check(np.full(100, np.nan, np.float32), 1e-3)
+    z = np.zeros(64, np.float32)
+    z[::2] = -0.0
+    _roundtrip_check(z, 1e-3)
+    # white noise at a tiny bound -> RAW fallback
+    w = np.random.default_rng(0).standard_normal((50, 60)).astype(np.float32)
+    got = _roundtrip_check(w, 1e-7)
+    assert got.size == 256 + 4 * w.size
+
+
+def test_deterministic():
+    x = torch.from_numpy(synth.grf3d(64, device="cpu").numpy()).cuda()
+    a = fz.compress(x, 1e-4).cpu().numpy()
+    b = fz.compress(x, 1e-4).cpu().numpy()
+    assert np.array_equal(a, b)
+
+
+@pytest.mark.parametrize("shape", [(5000,), (61, 45), (17, 9, 33), (64, 64, 64)])
+def test_quantize_stage_matches_oracle(shape):
+    x = synth.smooth_nd(shape, seed=3).numpy()
+    x.ravel()[::101] += 3.0  # outliers
+    ndim = len(shape)
+    codes, anchors, hist, n_out, n_exc, eb_abs = fz.lorenzo_quantize(torch.from_numpy(x).cuda(), 1e-3, "rel")
+    assert eb_abs == _eb_abs(x, 1e-3, "rel")
+    ebx2, inv2eb, eb_chk = oracle.constants(eb_abs)
+    rc, ra, rh, rno, rne = oracle.quantize_stage(x, ndim, shape[::-1], inv2eb, ebx2, eb_chk, 1, 512)
+    assert np.array_equal(codes.cpu().numpy().view(np.uint16), rc)
+    assert np.array_equal(anchors.cpu().numpy(), ra)
+    assert np.array_equal(hist.cpu().numpy().astype(np.uint64), rh)
+    assert (n_out, n_exc) == (rno, rne)
+    assert n_out > 0
+
+
+def _codebook_case(counts):
+    h = torch.from_numpy(counts.astype(np.int64)).cuda()
+    lens, codes = fz.huffman_codebook(h)
+    rl = oracle.huffman_lengths(counts.astype(np.uint64))
+    assert np.array_equal(lens.cpu().numpy(), rl)
+    rcode = oracle.canonical_codes(rl)
+    assert np.array_equal(codes.cpu().numpy().view(np.uint32), rcode)
+
+
+@pytest.mark.parametrize("seed", range(8))
+def test_codebook_matches_oracle(seed):
+    rng = np.random.default_rng(seed)
+    nsym = int(rng.choice([2, 3, 17, 256, 1000, 1024]))
+    c = rng.geometric(rng.uniform(0.001, 0.3), size=nsym).astype(np.int64)
+    c[rng.random(nsym) < 0.2] = 0
+    if (c > 0).sum() == 0:
+        c[0] = 1
+    _codebook_case(c)
+
+
+def test_codebook_edge_cases():
+    c = np.zeros(1024, np.int64)
+    c[512] = 10 ** 9
+    _codebook_case(c)  # single used symbol
+    fib = [1, 1]
+    while len(fib) < 45:
+        fib.append(fib[-1] + fib[-2])
+    c = np.zeros(1024, np.int64)
+    c[100:145] = fib
+    _codebook_case(c)  # forces the 24-bit length limit
+    c = np.ones(1024, np.int64)
+    _codebook_case(c)  # all equal weights: ties everywhere
+
+
+def test_corrupt_streams_are_rejected_without_fault():
+    x = synth.blobs3d((32, 32, 32), seed=2).numpy()
+    buf = fz.compress(torch.from_numpy(x).cuda(), 1e-3)
+    host = buf.cpu().numpy()
+    hdr = host[:256].tobytes()
+    # header corruption
+    bad = bytearray(hdr)
+    bad[0] ^= 0xFF
+    with pytest.raises(fz.FzError) as e:
+        fz.decompress(buf, header=bytes(bad))
+    assert e.value.code == 5
+    # over-subscribed code-length table
+    t = host.copy()
+    t[256:256 + 1024] = 1
+    with pytest.raises(fz.FzError):
+        fz.decompress(torch.from_numpy(t).cuda(), header=hdr)
+    # random bit flips in the payload: either a clean error or some output
+    rng = np.random.default_rng(1)
+    for _ in range(20):
+        t = host.copy()
+        i = int(rng.integers(1280, t.size))
+        t[i] ^= np.uint8(1 << int(rng.integers(0, 8)))
+        try:
+            fz.decompress(torch.from_numpy(t).cuda(), header=hdr)
+        except fz.FzError as err:
+            assert err.code == 5
+    # truncated stream length
+    with pytest.raises(fz.FzError):
+        fz.decompress(buf[:1000].clone(), header=hdr)
+    torch.cuda.synchronize()
+
+
+def test_bad_arguments():
+    x = torch.zeros(100, device="cuda")
+    with pytest.raises(fz.FzError) as e:
+        fz.compress(x, -1.0)
+    assert e.value.code == 1
+    with pytest.raises(fz.FzError) as e:
+        fz.compress(x, 1e-3, out=torch.empty(100, dtype=torch.uint8, device="cuda"))
+    assert e.value.code == 4
+    with pytest.raises(fz.FzError) as e:
+        fz.compress(x, 1e-3, predictor="interp_cubic", radius=512)
+    assert e.value.code == 7
+
+
+# ---------------------------------------------------------------- full workload sizes
+def _full_check(x, eb):
+    """GPU stream == oracle stream on the full field; bound on every value."""
+    xd = x.cuda() if not x.is_cuda else x
+    buf = fz.compress(xd, eb)
+    y = fz.decompress(buf)
+    f = xd[torch.isfinite(xd)]
+    eba = eb * (float(f.max()) - float(f.min()))
+    assert float((y.double() - xd.double()).abs().max()) <= eba
+    xh = xd.cpu().numpy()
+    ref = oracle.compress(xh, eb)
+    got = buf.cpu().numpy()
+    assert got.size == ref.size and np.array_equal(got, ref)
+    return got.size
+
+
+def test_full_512cubed_grf_rel1e4():
+    x = synth.grf3d(512, seed=2, device="cuda")
+    n = _full_check(x, 1e-4)
+    assert n < x.numel() * 4
+
+
+def test_full_hacc_1d_rel():
+    x = synth.hacc1d(synth.HACC_N, seed=3, device="cuda")
+    for eb in (1e-2, 1e-4):
+        _full_check(x, eb)
+
+
+def test_full_cesm_2d_rel():
+    x = synth.cesm2d(1800, 3600, seed=4)
+    for eb in (1e-2, 1e-3, 1e-4):
+        _full_check(x, eb)
