@@ -32,7 +32,7 @@
 #define ORC_ECORRUPT 5
 #define ORC_EUNSUPPORTED 7
 
-#define ORC_LMAX 24
+#define ORC_LMAX 14
 #define ORC_MAXSYM 1024
 
 /* ------------------------------------------------------------------------ */
@@ -270,8 +270,9 @@ static int leaf_cmp(const void *a, const void *b) {
  * nonzero count, sorted by (count, symbol).  Each of the m-1 merges takes, two
  * times, the front of the leaf queue if its weight is <= the front of the
  * internal queue, else the internal front.  A leaf's length is its depth.  A
- * single used symbol gets length 1.  If the longest code exceeds 24 bits every
- * nonzero count c becomes (c+1)>>1 and the lengths are rebuilt. */
+ * single used symbol gets length 1.  If the longest code exceeds 14 bits
+ * (ORC_LMAX) every nonzero count c becomes (c+1)>>1 and the lengths are
+ * rebuilt. */
 int orc_huffman_lengths(const uint64_t *counts_in, uint32_t nsym, uint8_t *len) {
   if (nsym == 0 || nsym > ORC_MAXSYM) return ORC_EINVAL;
   uint64_t cnt[ORC_MAXSYM];
@@ -317,14 +318,14 @@ int orc_huffman_lengths(const uint64_t *counts_in, uint32_t nsym, uint8_t *len) 
 /* Canonical codes from lengths, in the order of RFC 1951 §3.2.2: count codes
  * per length, first code of each length, then numerically consecutive codes
  * within a length in symbol order.  Returns ORC_ECORRUPT when the lengths
- * over-subscribe the code space (Kraft sum > 1) or exceed 24. */
+ * over-subscribe the code space (Kraft sum > 1) or exceed 14 bits. */
 int orc_canonical_codes(const uint8_t *len, uint32_t nsym, uint32_t *code) {
   uint32_t bl_count[ORC_LMAX + 1] = {0}, next_code[ORC_LMAX + 2] = {0};
   for (uint32_t s = 0; s < nsym; s++) {
     if (len[s] > ORC_LMAX) return ORC_ECORRUPT;
     if (len[s]) bl_count[len[s]]++;
   }
-  uint64_t kraft = 0; /* in units of 2^-24 */
+  uint64_t kraft = 0; /* in units of 2^-ORC_LMAX */
   for (int l = 1; l <= ORC_LMAX; l++) kraft += (uint64_t)bl_count[l] << (ORC_LMAX - l);
   if (kraft > ((uint64_t)1 << ORC_LMAX)) return ORC_ECORRUPT;
   uint32_t c = 0;
@@ -631,7 +632,7 @@ done:
 /* Step 11: decompress                                                       */
 /* ------------------------------------------------------------------------ */
 
-/* Decode one canonical codeword starting at bit p by walking lengths 1..24:
+/* Decode one canonical codeword starting at bit p by walking lengths 1..14:
  * the first length l whose l-bit prefix v satisfies first[l] <= v < first[l] +
  * count[l] identifies symbol sorted[base[l] + v - first[l]]. */
 static int decode_one(const uint32_t *w, uint64_t nbits_total, uint64_t *p, const uint32_t *first,
