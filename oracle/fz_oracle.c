@@ -266,53 +266,54 @@ static int leaf_cmp(const void *a, const void *b) {
   return x->s < y->s ? -1 : (x->s > y->s);
 }
 
-/* Huffman code lengths by the two-queue method.  Leaves: symbols with a
- * nonzero count, sorted by (count, symbol).  Each of the m-1 merges takes, two
- * times, the front of the leaf queue if its weight is <= the front of the
- * internal queue, else the internal front.  A leaf's length is its depth.  A
- * single used symbol gets length 1.  If the longest code exceeds 14 bits
- * (ORC_LMAX) every nonzero count c becomes (c+1)>>1 and the lengths are
- * rebuilt. */
+/* Code lengths of the Huffman code of the histogram, limited to ORC_LMAX
+ * bits: the optimal prefix code among those whose lengths are all <= 14,
+ * computed by the package-merge algorithm of Larmore and Hirschberg (when the
+ * plain Huffman code already fits in 14 bits this is a Huffman code).
+ *   Leaves: the used symbols sorted by (count, symbol).
+ *   Level L = 14 holds the leaves.  Level l < L holds the leaves merged with
+ *   the packages of level l+1 (sums of its consecutive item pairs; an odd
+ *   last item is dropped), ordered by weight, a leaf before a package of
+ *   equal weight.
+ *   The first 2m-2 items of level 1 are selected.  At each level, of the
+ *   selected items a_l are leaves and the others packages, which select the
+ *   first 2(m_l - a_l) items of the next level.
+ *   The length of the i-th leaf is the number of levels where i < a_l.
+ * A single used symbol gets length 1. */
 int orc_huffman_lengths(const uint64_t *counts_in, uint32_t nsym, uint8_t *len) {
   if (nsym == 0 || nsym > ORC_MAXSYM) return ORC_EINVAL;
-  uint64_t cnt[ORC_MAXSYM];
-  memcpy(cnt, counts_in, nsym * sizeof(uint64_t));
   leaf_t leaf[ORC_MAXSYM];
-  uint64_t iw[ORC_MAXSYM];
-  int32_t iparent[ORC_MAXSYM], lparent[ORC_MAXSYM], depth[ORC_MAXSYM];
-  for (;;) {
-    memset(len, 0, nsym);
-    uint32_t m = 0;
-    for (uint32_t s = 0; s < nsym; s++)
-      if (cnt[s]) { leaf[m].w = cnt[s]; leaf[m].s = s; m++; }
-    if (m == 0) return ORC_EINVAL;
-    if (m == 1) { len[leaf[0].s] = 1; return ORC_OK; }
-    qsort(leaf, m, sizeof(leaf_t), leaf_cmp);
-    uint32_t li = 0, ih = 0;  /* queue fronts; internal nodes 0..k-1 exist */
-    for (uint32_t k = 0; k + 1 < m; k++) {
-      uint64_t wsum = 0;
-      for (int take = 0; take < 2; take++) {
-        int from_leaf;
-        if (li < m && (ih >= k || leaf[li].w <= iw[ih])) from_leaf = 1;
-        else from_leaf = 0;
-        if (from_leaf) { wsum += leaf[li].w; lparent[li] = (int32_t)k; li++; }
-        else { wsum += iw[ih]; iparent[ih] = (int32_t)k; ih++; }
-      }
-      iw[k] = wsum;
+  memset(len, 0, nsym);
+  uint32_t m = 0;
+  for (uint32_t s = 0; s < nsym; s++)
+    if (counts_in[s]) { leaf[m].w = counts_in[s]; leaf[m].s = s; m++; }
+  if (m == 0) return ORC_EINVAL;
+  if (m == 1) { len[leaf[0].s] = 1; return ORC_OK; }
+  qsort(leaf, m, sizeof(leaf_t), leaf_cmp);
+  static uint64_t cur[2 * ORC_MAXSYM], nxt[2 * ORC_MAXSYM], pk[ORC_MAXSYM];
+  static uint8_t isleaf[ORC_LMAX + 1][2 * ORC_MAXSYM];
+  uint32_t n_cur = m;
+  for (uint32_t i = 0; i < m; i++) { cur[i] = leaf[i].w; isleaf[ORC_LMAX][i] = 1; }
+  for (int l = ORC_LMAX - 1; l >= 1; l--) {
+    uint32_t np = n_cur / 2;
+    for (uint32_t j = 0; j < np; j++) pk[j] = cur[2 * j] + cur[2 * j + 1];
+    uint32_t i = 0, j = 0, k = 0;
+    while (i < m || j < np) {
+      if (j >= np || (i < m && leaf[i].w <= pk[j])) { nxt[k] = leaf[i].w; isleaf[l][k] = 1; i++; }
+      else { nxt[k] = pk[j]; isleaf[l][k] = 0; j++; }
+      k++;
     }
-    uint32_t root = m - 2;
-    depth[root] = 0;
-    for (int32_t k = (int32_t)root - 1; k >= 0; k--) depth[k] = depth[iparent[k]] + 1;
-    int maxl = 0;
-    for (uint32_t i = 0; i < m; i++) {
-      int l = depth[lparent[i]] + 1;
-      len[leaf[i].s] = (uint8_t)(l > 255 ? 255 : l);
-      if (l > maxl) maxl = l;
-    }
-    if (maxl <= ORC_LMAX) return ORC_OK;
-    for (uint32_t s = 0; s < nsym; s++)
-      if (cnt[s]) cnt[s] = (cnt[s] + 1) >> 1;
+    n_cur = k;
+    memcpy(cur, nxt, n_cur * sizeof(uint64_t));
   }
+  uint32_t sel = 2 * m - 2;
+  for (int l = 1; l <= ORC_LMAX && sel > 0; l++) {
+    uint32_t a = 0;
+    for (uint32_t k = 0; k < sel; k++) a += isleaf[l][k];
+    for (uint32_t i = 0; i < a; i++) len[leaf[i].s]++;
+    sel = 2 * (sel - a);
+  }
+  return ORC_OK;
 }
 
 /* Canonical codes from lengths, in the order of RFC 1951 §3.2.2: count codes

@@ -233,6 +233,50 @@ def test_huffman_exhaustive_small(seed):
     assert int((counts * ln).sum()) == best
 
 
+def _dp_limited_optimum(counts, lmax=14):
+    """Independent exact optimum over prefix codes with depth <= lmax: fill
+    depths top-down with the heaviest symbols first (optimal lengths are
+    monotone in weight); avail = free nodes at the current depth."""
+    import functools
+    w = sorted((int(c) for c in counts if c > 0), reverse=True)
+    n = len(w)
+    if n == 1:
+        return w[0]
+    pre = [0]
+    for v in w:
+        pre.append(pre[-1] + v)
+
+    @functools.lru_cache(maxsize=None)
+    def best(i, d, avail):
+        if i == n:
+            return 0
+        if d > lmax or avail == 0:
+            return float("inf")
+        avail = min(avail, n - i)
+        out = float("inf")
+        for k in range(0, avail + 1):
+            rest = best(i + k, d + 1, min(2 * (avail - k), n - i - k)) if i + k < n else 0
+            out = min(out, (pre[i + k] - pre[i]) * d + rest)
+        return out
+
+    return best(0, 1, 2)
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_length_limited_code_is_optimal_dp(seed):
+    rng = np.random.default_rng(500 + seed)
+    n = int(rng.integers(16, 23))
+    fib = [1, 1]
+    while len(fib) < n:
+        fib.append(fib[-1] + fib[-2])
+    counts = np.array(fib, np.uint64) * np.uint64(rng.integers(1, 4))
+    counts = counts[rng.permutation(n)]
+    ln = oracle.huffman_lengths(counts)
+    assert ln.max() <= 14 and _heap_huffman_maxlen([int(c) for c in counts]) > 14  # the limit binds
+    assert sum(Fraction(1, 2 ** int(l)) for l in ln) <= 1
+    assert int((counts * ln).sum()) == _dp_limited_optimum(counts)
+
+
 def test_huffman_single_symbol_and_length_limit():
     c = np.zeros(1024, np.uint64)
     c[512] = 1000
