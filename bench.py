@@ -210,9 +210,9 @@ def run_fz(args, rank, world, local_rank):
         ev[i][2].record(stream)
         assert L.fz_ctx_get_profile(ctx.handle, C.byref(prof)) == 0
         for k in range(prof.n_compress):
-            stages_c.setdefault(prof.compress_names[k].decode(), []).append(prof.compress_ms[k])
+            stages_c.setdefault(prof.compress_names[k].value.decode(), []).append(prof.compress_ms[k])
         for k in range(prof.n_decompress):
-            stages_d.setdefault(prof.decompress_names[k].decode(), []).append(prof.decompress_ms[k])
+            stages_d.setdefault(prof.decompress_names[k].value.decode(), []).append(prof.decompress_ms[k])
     torch.cuda.synchronize(dev)
     launches = _launches(L, ctx) - launches0
     if world > 1:

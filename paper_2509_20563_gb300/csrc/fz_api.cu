@@ -114,7 +114,8 @@ size_t layout_compress(const Geom &g, char *base, CompressWs &ws) {
   };
   const uint64_t n_etiles = (g.n_blocks + kEncWarps - 1) / kEncWarps;
   ws.ctl = reinterpret_cast<Ctl *>(take(sizeof(Ctl)));
-  ws.qstatus = reinterpret_cast<uint64_t *>(take(8 * g.n_qtiles));
+  ws.tinfo = reinterpret_cast<uint4 *>(take(16 * g.n_qtiles));
+  ws.tgroup = reinterpret_cast<uint2 *>(take(8 * ((g.n_qtiles + kTileGroup - 1) / kTileGroup)));
   ws.estatus = reinterpret_cast<uint64_t *>(take(8 * n_etiles));
   ws.zero_bytes = off;
   ws.cap_list = g.n / 8;
@@ -185,7 +186,7 @@ fz_status check_header(const fz_header &h, uint64_t in_bytes, Geom &g) {
   if (h.predictor != FZ_PRED_LORENZO1 && h.predictor != FZ_PRED_LORENZO2) return FZ_EUNSUPPORTED;
   if (h.block[0] != g.bx || h.block[1] != g.by || h.block[2] != g.bz || h.chunk != g.bsize) return FZ_ECORRUPT;
   if (h.n_blocks != g.n_blocks || h.n_chunks != g.n_blocks) return FZ_ECORRUPT;
-  if (h.n_out > n || h.n_exc > n || h.total_bits > 24ull * g.npad) return FZ_ECORRUPT;
+  if (h.n_out > n || h.n_exc > n || h.total_bits > (uint64_t)kLmax * g.npad) return FZ_ECORRUPT;
   const uint64_t secs[9][2] = {{h.off_lens, 2ull * h.radius},        {h.off_anchors, 4 * h.n_blocks},
                                {h.off_chunk_bits, 4 * h.n_chunks},   {h.off_out_idx, 4 * h.n_out},
                                {h.off_out_val, 4 * h.n_out},         {h.off_exc_idx, 4 * h.n_exc},
@@ -337,7 +338,7 @@ fz_status fz_compress(fz_ctx *ctx, const float *d_in, uint32_t ndim, const uint6
   uint8_t *out = reinterpret_cast<uint8_t *>(d_out);
   cudaError_t e = launch_codebook(g, r.R, r.pred, eb_mode, eb, ws, s);
   clk.mark("codebook", 1);
-  if (e == cudaSuccess) { e = launch_encode(g, ws, out, s); clk.mark("encode", 1); }
+  if (e == cudaSuccess) { e = launch_encode(g, ws, out, s, ctx->sm_count); clk.mark("encode", 1); }
   if (e == cudaSuccess) { e = launch_assemble(d_in, g, r.R, ws, out, s, ctx->sm_count); clk.mark("assemble", 1); }
   if (e == cudaSuccess) e = cudaMemcpyAsync(ctx->h_pinned, &ws.ctl->res, sizeof(Result), cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
@@ -391,19 +392,17 @@ fz_status fz_decompress(fz_ctx *ctx, const void *d_in, uint64_t in_bytes, const 
   const uint64_t n_groups = (h.n_chunks + kDecThreads - 1) / kDecThreads;
   size_t off = 0;
   auto take = [&](size_t bytes) { size_t o = off; off += up(bytes); return o; };
-  const size_t o_err = take(16), o_lut = take(4u << kLutBits), o_ltab = take(4 * (75 + kMaxSym)),
-               o_gsum = take(8 * n_groups);
+  const size_t o_err = take(16), o_lut = take(2u << kLutBits), o_gsum = take(8 * n_groups);
   if ((st = ensure_ws(ctx, off))) return st;
   char *base = reinterpret_cast<char *>(ctx->ws);
   DecodeWs ws;
   ws.err = reinterpret_cast<uint32_t *>(base + o_err);
-  ws.lut = reinterpret_cast<uint32_t *>(base + o_lut);
-  ws.ltab = reinterpret_cast<uint32_t *>(base + o_ltab);
+  ws.lut = reinterpret_cast<uint16_t *>(base + o_lut);
   ws.gsum = reinterpret_cast<uint64_t *>(base + o_gsum);
   StageClock clk(ctx, s, true);
   e = cudaMemsetAsync(ws.err, 0, 16, s);
   if (e == cudaSuccess) { e = launch_decode_prep(in, h, ws, s); clk.mark("dec_prep", 2); }
-  if (e == cudaSuccess) { e = launch_decode_main(in, h, d_out, ws, s); clk.mark("decode", 1); }
+  if (e == cudaSuccess) { e = launch_decode_main(in, h, d_out, ws, s, ctx->sm_count); clk.mark("decode", 1); }
   if (e == cudaSuccess) e = cudaMemcpyAsync(ctx->h_pinned, ws.err, 4, cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) return from_cuda(e);

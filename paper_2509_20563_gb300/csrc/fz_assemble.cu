@@ -1,9 +1,10 @@
-// fz_assemble.cu -- stream assembly: copies the header, the code-length
-// table, anchors, outliers and exceptions from the workspace into their
-// 16-byte aligned sections of the output and zeroes the alignment gaps (the
-// chunk bit lengths and the bitstream were written in place by the encoder).
-// For a RAW stream it copies the input floats; for a CONST stream it writes
-// the single value.
+// fz_assemble.cu -- stream assembly: the header, the code-length table and
+// the anchors are copied into their 16-byte aligned sections, the outliers
+// and exceptions are gathered from the quantizer's per-tile scratch slots
+// into code-stream order, and the alignment gaps are zeroed (the chunk bit
+// lengths and the bitstream were written in place by the encoder).  For a
+// RAW stream the input floats are copied; for a CONST stream the single
+// value is written.
 #include "fz_internal.cuh"
 
 namespace fz {
@@ -11,6 +12,7 @@ namespace fz {
 namespace {
 
 constexpr int kAsmThreads = 256;
+constexpr int kTilesPerThread = kTileGroup / kAsmThreads;
 
 // Grid-stride byte copy using the widest access both pointers allow.
 __device__ void copy_bytes(uint8_t *dst, const uint8_t *src, uint64_t n, uint64_t tid, uint64_t nth) {
@@ -35,8 +37,32 @@ __device__ void zero_gap(uint8_t *out, uint64_t from, uint64_t to) {
   for (uint64_t i = from; i < to; ++i) out[i] = 0;
 }
 
+// Block-wide exclusive scan of one value per thread; returns the block total.
+__device__ uint2 block_exscan2(uint2 v, uint2 &excl, uint2 *sw) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  uint2 inc = v;
+#pragma unroll
+  for (int off = 1; off < 32; off <<= 1) {
+    const uint32_t a = __shfl_up_sync(0xffffffffu, inc.x, off), b = __shfl_up_sync(0xffffffffu, inc.y, off);
+    if (lane >= off) { inc.x += a; inc.y += b; }
+  }
+  if (lane == 31) sw[warp] = inc;
+  __syncthreads();
+  uint2 wpre = make_uint2(0, 0), tot = make_uint2(0, 0);
+  for (int w = 0; w < kAsmThreads / 32; ++w) {
+    if (w < warp) { wpre.x += sw[w].x; wpre.y += sw[w].y; }
+    tot.x += sw[w].x;
+    tot.y += sw[w].y;
+  }
+  excl = make_uint2(wpre.x + inc.x - v.x, wpre.y + inc.y - v.y);
+  __syncthreads();
+  return tot;
+}
+
 __global__ void __launch_bounds__(kAsmThreads) k_assemble(const float *__restrict__ x, Geom g, uint32_t R,
                                                            CompressWs ws, uint8_t *d_out) {
+  __shared__ uint2 sw[kAsmThreads / 32];
+  __shared__ unsigned long long s_ob, s_eb;
   const Ctl *ctl = ws.ctl;
   const uint32_t mode = ctl->mode;
   const fz_header &h = ctl->res.hdr;
@@ -56,10 +82,6 @@ __global__ void __launch_bounds__(kAsmThreads) k_assemble(const float *__restric
   const uint64_t nb = h.n_blocks, n_out = h.n_out, n_exc = h.n_exc;
   copy_bytes(d_out + h.off_lens, ctl->lens, nsym, tid, nth);
   copy_bytes(d_out + h.off_anchors, reinterpret_cast<const uint8_t *>(ws.anchors), 4 * nb, tid, nth);
-  copy_bytes(d_out + h.off_out_idx, reinterpret_cast<const uint8_t *>(ws.out_idx), 4 * n_out, tid, nth);
-  copy_bytes(d_out + h.off_out_val, reinterpret_cast<const uint8_t *>(ws.out_val), 4 * n_out, tid, nth);
-  copy_bytes(d_out + h.off_exc_idx, reinterpret_cast<const uint8_t *>(ws.exc_idx), 4 * n_exc, tid, nth);
-  copy_bytes(d_out + h.off_exc_val, reinterpret_cast<const uint8_t *>(ws.exc_val), 4 * n_exc, tid, nth);
   if (tid == 0) {
     zero_gap(d_out, h.off_lens + nsym, h.off_anchors);
     zero_gap(d_out, h.off_anchors + 4 * nb, h.off_chunk_bits);
@@ -70,16 +92,66 @@ __global__ void __launch_bounds__(kAsmThreads) k_assemble(const float *__restric
     zero_gap(d_out, h.off_exc_val + 4 * n_exc, h.off_bits);
     zero_gap(d_out, h.off_bits + 4 * ((h.total_bits + 31) / 32), h.total_bytes);
   }
+  if ((n_out | n_exc) == 0) return;
+  // ---- ordered gather: one CTA per group of kTileGroup tiles
+  uint32_t *oidx = reinterpret_cast<uint32_t *>(d_out + h.off_out_idx);
+  int32_t *oval = reinterpret_cast<int32_t *>(d_out + h.off_out_val);
+  uint32_t *eidx = reinterpret_cast<uint32_t *>(d_out + h.off_exc_idx);
+  uint32_t *eval = reinterpret_cast<uint32_t *>(d_out + h.off_exc_val);
+  const uint64_t n_tg = (g.n_qtiles + kTileGroup - 1) / kTileGroup;
+  for (uint64_t grp = blockIdx.x; grp < n_tg; grp += gridDim.x) {
+    // totals of the earlier groups
+    unsigned long long po = 0, pe = 0;
+    for (uint64_t q = threadIdx.x; q < grp; q += kAsmThreads) { po += ws.tgroup[q].x; pe += ws.tgroup[q].y; }
+    for (int off = 16; off > 0; off >>= 1) {
+      po += __shfl_down_sync(0xffffffffu, po, off);
+      pe += __shfl_down_sync(0xffffffffu, pe, off);
+    }
+    if (threadIdx.x == 0) { s_ob = 0; s_eb = 0; }
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) { atomicAdd(&s_ob, po); atomicAdd(&s_eb, pe); }
+    __syncthreads();
+    const unsigned long long ob = s_ob, eb = s_eb;
+    // this thread's tiles
+    const uint64_t t0 = grp * kTileGroup + (uint64_t)threadIdx.x * kTilesPerThread;
+    uint4 ti[kTilesPerThread];
+    uint2 mine = make_uint2(0, 0);
+#pragma unroll
+    for (int k = 0; k < kTilesPerThread; ++k) {
+      ti[k] = (t0 + k < g.n_qtiles) ? ws.tinfo[t0 + k] : make_uint4(0, 0, 0, 0);
+      mine.x += ti[k].x;
+      mine.y += ti[k].y;
+    }
+    uint2 excl;
+    block_exscan2(mine, excl, sw);
+    unsigned long long o = ob + excl.x, e = eb + excl.y;
+#pragma unroll
+    for (int k = 0; k < kTilesPerThread; ++k) {
+      for (uint32_t i = 0; i < ti[k].x; ++i) {
+        const uint64_t src = (uint64_t)ti[k].z + i;
+        if (src < ws.cap_list && o + i < n_out) { oidx[o + i] = ws.out_idx[src]; oval[o + i] = ws.out_val[src]; }
+      }
+      for (uint32_t i = 0; i < ti[k].y; ++i) {
+        const uint64_t src = (uint64_t)ti[k].w + i;
+        if (src < ws.cap_list && e + i < n_exc) { eidx[e + i] = ws.exc_idx[src]; eval[e + i] = ws.exc_val[src]; }
+      }
+      o += ti[k].x;
+      e += ti[k].y;
+    }
+    __syncthreads();
+  }
 }
 
 }  // namespace
 
 cudaError_t launch_assemble(const float *x, const Geom &g, uint32_t R, const CompressWs &ws, uint8_t *d_out,
                             cudaStream_t s, int sm_count) {
-  // the grid covers the raw-copy worst case; idle threads exit quickly
+  // the grid covers the raw-copy worst case and the tile groups; idle threads exit quickly
   uint64_t want = (4 * g.n / 16 + kAsmThreads - 1) / kAsmThreads;
   uint64_t grid = (uint64_t)sm_count * 8;
   if (want < grid) grid = want;
+  const uint64_t n_tg = (g.n_qtiles + kTileGroup - 1) / kTileGroup;
+  if (grid < n_tg) grid = n_tg < (uint64_t)sm_count * 8 ? n_tg : (uint64_t)sm_count * 8;
   if (grid < 2) grid = 2;
   k_assemble<<<(unsigned)grid, kAsmThreads, 0, s>>>(x, g, R, ws, d_out);
   return cudaGetLastError();

@@ -2,11 +2,12 @@
 // encoder is fed by the histogram of quantization codes) and the stream
 // layout decision.  One CTA of 1024 threads:
 //   1. bitonic sort of (count, symbol) keys of the used symbols;
-//   2. two-queue Huffman merge (one thread; ties take the leaf);
-//   3. node depths by pointer jumping (log rounds, all threads);
-//   4. 24-bit length limit by halving counts and rebuilding;
-//   5. canonical codewords in RFC 1951 order via warp ballots;
-//   6. total bit count, section offsets, raw-fallback rule and the header.
+//   2. package-merge for the optimal code with lengths <= 14 (a Huffman code
+//      whenever the unlimited one fits): 13 levels, each a parallel merge of
+//      the sorted leaves with the packages of the level below;
+//   3. selection of 2m-2 items and code lengths from the per-level counts;
+//   4. canonical codewords in RFC 1951 order via warp ballots;
+//   5. total bit count, section offsets, raw-fallback rule and the header.
 #include "fz_internal.cuh"
 
 namespace fz {
@@ -18,110 +19,117 @@ constexpr int kCbThreads = 1024;
 struct CbSmem {
   unsigned long long key[kMaxSym];
   unsigned long long cnt[kMaxSym];
-  unsigned long long lw[kMaxSym];   // sorted leaf weights
-  unsigned long long iw[kMaxSym];   // internal node weights
-  uint16_t lsym[kMaxSym];           // sorted leaf symbols
-  int16_t lpar[kMaxSym], ipar[kMaxSym];
-  int16_t dep[2][kMaxSym], anc[2][kMaxSym];
+  unsigned long long lw[kMaxSym];          // sorted leaf weights
+  unsigned long long S[2][2 * kMaxSym];    // items of the current / next level
+  unsigned long long pk[kMaxSym];          // packages of the current level
+  uint32_t flags[kLmax + 1][2 * kMaxSym / 32];  // per level: is-leaf bit per item
+  uint32_t a[kLmax + 1];                   // selected leaves per level
+  uint16_t lsym[kMaxSym];                  // sorted leaf symbols
   uint8_t len[kMaxSym];
   uint32_t wcnt[32][kLmax + 1];
   uint32_t next_code[kLmax + 2];
-  uint32_t m, maxlen;
   unsigned long long total_bits;
 };
 
+// Number of elements of the sorted array a[0..n) that are < v (strict) or
+// <= v (!strict).
+__device__ __forceinline__ uint32_t rank_of(const unsigned long long *a, uint32_t n, unsigned long long v,
+                                            bool strict) {
+  uint32_t lo = 0, hi = n;
+  while (lo < hi) {
+    const uint32_t mid = (lo + hi) >> 1;
+    const bool before = strict ? (a[mid] < v) : (a[mid] <= v);
+    if (before) lo = mid + 1; else hi = mid;
+  }
+  return lo;
+}
+
 // Code lengths (into s.len) and canonical codewords (into code[]) for the
-// counts in s.cnt[0..nsym).  Returns false if no symbol is used.
+// counts in s.cnt[0..nsym): the optimal prefix code with lengths <= 14
+// (package-merge), leaves in (count, symbol) order, a leaf before a package
+// of equal weight.  Each level's merge is parallel: every leaf and every
+// package finds its merged position by binary search in the other list.
+// Returns false if no symbol is used.
 __device__ bool build_codebook(CbSmem &s, uint32_t nsym, uint32_t *code_out) {
-  const int t = threadIdx.x;
-  for (int iter = 0; iter < 64; ++iter) {
-    // ---- 1. sort keys (count << 10 | symbol); unused symbols sort last
-    s.key[t] = (t < (int)nsym && s.cnt[t]) ? ((s.cnt[t] << 10) | (unsigned long long)t) : ~0ull;
-    if (t == 0) { s.m = 0; s.maxlen = 0; }
-    s.len[t] = 0;
+  const int t = threadIdx.x, lane = t & 31;
+  // ---- 1. sort keys (count << 10 | symbol); unused symbols sort last
+  s.key[t] = (t < (int)nsym && s.cnt[t]) ? ((s.cnt[t] << 10) | (unsigned long long)t) : ~0ull;
+  s.len[t] = 0;
+  __syncthreads();
+  for (int k = 2; k <= kMaxSym; k <<= 1) {
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      const int ixj = t ^ j;
+      if (ixj > t) {
+        const bool asc = (t & k) == 0;
+        const unsigned long long a = s.key[t], b = s.key[ixj];
+        if ((a > b) == asc) { s.key[t] = b; s.key[ixj] = a; }
+      }
+      __syncthreads();
+    }
+  }
+  const uint32_t m = (uint32_t)__syncthreads_count(s.key[t] != ~0ull);
+  if (m == 0) return false;
+  if ((uint32_t)t < m) {
+    s.lsym[t] = (uint16_t)(s.key[t] & 1023u);
+    s.lw[t] = s.key[t] >> 10;
+  }
+  __syncthreads();
+  if (m == 1) {
+    if (t == 0) s.len[s.lsym[0]] = 1;
     __syncthreads();
-    for (int k = 2; k <= kMaxSym; k <<= 1) {
-      for (int j = k >> 1; j > 0; j >>= 1) {
-        int ixj = t ^ j;
-        if (ixj > t) {
-          bool asc = (t & k) == 0;
-          unsigned long long a = s.key[t], b = s.key[ixj];
-          if ((a > b) == asc) { s.key[t] = b; s.key[ixj] = a; }
+  } else {
+    // ---- 2. package-merge, level kLmax (leaves only) down to level 1
+    for (int i = t; i < (kLmax + 1) * (2 * kMaxSym / 32); i += kCbThreads) (&s.flags[0][0])[i] = 0;
+    if ((uint32_t)t < m) s.S[0][t] = s.lw[t];
+    __syncthreads();
+    if ((uint32_t)t < m) atomicOr(&s.flags[kLmax][t >> 5], 1u << (t & 31));
+    uint32_t n_cur = m;
+    int cb = 0;
+    for (int l = kLmax - 1; l >= 1; --l) {
+      const uint32_t np = n_cur >> 1;
+      if ((uint32_t)t < np) s.pk[t] = s.S[cb][2 * t] + s.S[cb][2 * t + 1];
+      __syncthreads();
+      if ((uint32_t)t < m) {
+        const uint32_t pos = (uint32_t)t + rank_of(s.pk, np, s.lw[t], true);
+        s.S[cb ^ 1][pos] = s.lw[t];
+        atomicOr(&s.flags[l][pos >> 5], 1u << (pos & 31));
+      }
+      if ((uint32_t)t < np) {
+        const uint32_t pos = (uint32_t)t + rank_of(s.lw, m, s.pk[t], false);
+        s.S[cb ^ 1][pos] = s.pk[t];
+      }
+      __syncthreads();
+      n_cur = m + np;
+      cb ^= 1;
+    }
+    // ---- 3. selection: 2m-2 items at level 1; a_l leaves per level
+    if (t < 32) {
+      uint32_t sel = 2 * m - 2;
+      for (int l = 1; l <= kLmax; ++l) {
+        uint32_t c = 0;
+        for (int w = lane; w < 2 * kMaxSym / 32; w += 32) {
+          const uint32_t lo = (uint32_t)w * 32;
+          if (lo >= sel) break;
+          uint32_t bits = s.flags[l][w];
+          if (sel - lo < 32) bits &= (1u << (sel - lo)) - 1u;
+          c += __popc(bits);
         }
-        __syncthreads();
+        c = __reduce_add_sync(0xffffffffu, c);
+        if (lane == 0) s.a[l] = c;
+        sel = 2 * (sel - c);
       }
     }
-    if (s.key[t] != ~0ull) atomicAdd(&s.m, 1u);
     __syncthreads();
-    const uint32_t m = s.m;
-    if (m == 0) return false;
     if ((uint32_t)t < m) {
-      s.lsym[t] = (uint16_t)(s.key[t] & 1023u);
-      s.lw[t] = s.key[t] >> 10;
-    }
-    __syncthreads();
-    if (m == 1) {
-      if (t == 0) { s.len[s.lsym[0]] = 1; s.maxlen = 1; }
-      __syncthreads();
-      break;
-    }
-    // ---- 2. two-queue merge (serial); internal node k = merge number k
-    if (t == 0) {
-      uint32_t li = 0, ih = 0;
-      unsigned long long lf = s.lw[0], inf = 0;
-      for (uint32_t k = 0; k + 1 < m; ++k) {
-        unsigned long long sum = 0;
+      uint32_t L = 0;
 #pragma unroll
-        for (int take = 0; take < 2; ++take) {
-          bool have_i = ih < k;
-          bool leaf = li < m && (!have_i || lf <= inf);
-          if (leaf) {
-            sum += lf;
-            s.lpar[li] = (int16_t)k;
-            ++li;
-            lf = li < m ? s.lw[li] : 0ull;
-          } else {
-            sum += inf;
-            s.ipar[ih] = (int16_t)k;
-            ++ih;
-            inf = ih < k ? s.iw[ih] : 0ull;
-          }
-        }
-        s.iw[k] = sum;
-        if (ih == k) inf = sum;
-      }
+      for (int l = 1; l <= kLmax; ++l) L += (uint32_t)t < s.a[l];
+      s.len[s.lsym[t]] = (uint8_t)L;
     }
-    __syncthreads();
-    // ---- 3. depth of every internal node by pointer jumping
-    const int root = (int)m - 2;
-    if (t < (int)m - 1) {
-      s.dep[0][t] = (t == root) ? 0 : 1;
-      s.anc[0][t] = (t == root) ? (int16_t)root : s.ipar[t];
-    }
-    __syncthreads();
-    int cur = 0;
-    for (int r = 0; (1 << r) < (int)m; ++r) {
-      if (t < (int)m - 1) {
-        int a = s.anc[cur][t];
-        s.dep[cur ^ 1][t] = s.dep[cur][t] + s.dep[cur][a];
-        s.anc[cur ^ 1][t] = s.anc[cur][a];
-      }
-      __syncthreads();
-      cur ^= 1;
-    }
-    if ((uint32_t)t < m) {
-      int l = s.dep[cur][s.lpar[t]] + 1;
-      s.len[s.lsym[t]] = (uint8_t)(l > 255 ? 255 : l);
-      atomicMax(&s.maxlen, (uint32_t)l);
-    }
-    __syncthreads();
-    if (s.maxlen <= (uint32_t)kLmax) break;
-    // ---- 4. length limit: halve the counts and rebuild
-    if (t < (int)nsym && s.cnt[t]) s.cnt[t] = (s.cnt[t] + 1) >> 1;
     __syncthreads();
   }
-  // ---- 5. canonical codewords (RFC 1951 order)
-  const int lane = t & 31, warp = t >> 5;
+  // ---- 4. canonical codewords (RFC 1951 order)
+  const int warp = t >> 5;
   const int L = (t < (int)nsym) ? s.len[t] : 0;
   if (t < 32 * (kLmax + 1)) (&s.wcnt[0][0])[t] = 0;
   __syncthreads();
@@ -195,12 +203,20 @@ __global__ void __launch_bounds__(kCbThreads) k_codebook(Geom g, uint32_t R, uin
       if (t == 0) set_err(ctl, FZ_ECORRUPT);
       return;
     }
+    unsigned long long b = 0;
     if (t < (int)nsym) {
       uint32_t L = s.len[t];
       ctl->lens[t] = (uint8_t)L;
       ctl->enc[t] = (L << 24) | ctl->enc[t];
-      unsigned long long b = ctl->hist[t] * (unsigned long long)L;
-      if (b) atomicAdd(&s.total_bits, b);
+      b = ctl->hist[t] * (unsigned long long)L;
+    }
+    for (int off = 16; off > 0; off >>= 1) b += __shfl_down_sync(0xffffffffu, b, off);
+    if ((t & 31) == 0) s.key[t >> 5] = b;  // the sort keys are no longer needed
+    __syncthreads();
+    if (t < 32) {
+      unsigned long long v = s.key[t];
+      for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
+      if (t == 0) s.total_bits = v;
     }
     __syncthreads();
   }

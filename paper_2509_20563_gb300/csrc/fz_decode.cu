@@ -2,19 +2,25 @@
 // decode, outlier scatter, anchor restore, inverse Lorenzo and
 // dequantization fused in one kernel.  The paper overlaps a CPU Huffman
 // decode with a GPU outlier scatter; here both happen in the same GPU
-// thread, which decodes one chunk (= one block) straight into registers:
-// the inverse Lorenzo is an inclusive prefix sum along x (a running sum),
-// then along y (per-column sums), then along z (per-(x,y) plane sums), so
-// a thread never needs the decoded codes in memory.  Every output row is
-// written as soon as it is complete: a warp covers 32 consecutive blocks
-// along x, so its rows form long contiguous runs in HBM.
+// thread, which decodes one chunk (= one block) symbol by symbol and never
+// stores the codes: the inverse Lorenzo is an inclusive prefix sum along x (a
+// running sum in a register), then along y (per-column sums), then along z
+// (per-(x,y) plane sums, kept in a per-thread column of shared memory), and
+// every output row is written as soon as it is complete.  A warp covers 32
+// consecutive blocks along x, so its rows form long contiguous runs in HBM.
+// The loop body is one row of symbols, small enough for the instruction
+// cache.
+//
+// The code-length limit of the format (14 bits) equals the width of the
+// shared-memory decode table, so every codeword resolves with one lookup
+// and the decode loop has no data-dependent branch.
 //
 // Kernels:
-//   k_dec_gsum  -- per group of 128 chunks, the sum of their bit lengths
+//   k_dec_gsum  -- per group of 256 chunks, the sum of their bit lengths
 //   k_dec_prep  -- one CTA: canonical codes from the length table, the
-//                  first-level decode table (12 bits), long-code tables,
-//                  and the exclusive scan of the group sums
-//   k_decode    -- one thread per chunk
+//                  16384-entry decode table, and the exclusive scan of the
+//                  group sums
+//   k_decode    -- persistent; one thread per chunk of the current group
 #include <string.h>
 
 #include "fz_internal.cuh"
@@ -24,7 +30,9 @@ namespace fz {
 namespace {
 
 constexpr int kPrepThreads = 1024;
-constexpr int kLtFirst = 0, kLtCount = 25, kLtBase = 50, kLtSorted = 75, kLtWords = 75 + kMaxSym;
+constexpr int kLutSize = 1 << kLutBits;
+// decode-table entry: bit 15 valid, bits 10..13 length-1, bits 0..9 symbol
+constexpr uint16_t kLutValid = 0x8000u;
 
 __device__ __forceinline__ void dec_err(uint32_t *err, uint32_t code) { atomicCAS(err, 0u, code); }
 
@@ -33,13 +41,15 @@ __global__ void k_dec_gsum(const uint32_t *__restrict__ chunk_bits, uint64_t n_c
   const uint64_t gidx = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (gidx >= n_groups) return;
-  const uint64_t c0 = gidx * kDecThreads + 4 * lane;
+  constexpr int kPerLane = kDecThreads / 32;  // 8
+  const uint64_t c0 = gidx * kDecThreads + kPerLane * lane;
   unsigned long long s = 0;
-  if (c0 + 3 < n_chunks) {
-    uint4 v = *reinterpret_cast<const uint4 *>(chunk_bits + c0);
-    s = (unsigned long long)v.x + v.y + v.z + v.w;
+  if (c0 + kPerLane - 1 < n_chunks) {
+    const uint4 v = *reinterpret_cast<const uint4 *>(chunk_bits + c0);
+    const uint4 w = *reinterpret_cast<const uint4 *>(chunk_bits + c0 + 4);
+    s = (unsigned long long)v.x + v.y + v.z + v.w + w.x + w.y + w.z + w.w;
   } else {
-    for (uint64_t c = c0; c < n_chunks && c < c0 + 4; ++c) s += chunk_bits[c];
+    for (uint64_t c = c0; c < n_chunks && c < c0 + kPerLane; ++c) s += chunk_bits[c];
   }
   for (int off = 16; off > 0; off >>= 1) s += __shfl_down_sync(0xffffffffu, s, off);
   if (lane == 0) gsum[gidx] = s;
@@ -47,30 +57,20 @@ __global__ void k_dec_gsum(const uint32_t *__restrict__ chunk_bits, uint64_t n_c
 
 __global__ void __launch_bounds__(kPrepThreads) k_dec_prep(const uint8_t *__restrict__ lens_in, uint32_t nsym,
                                                             uint64_t *gsum, uint64_t n_groups,
-                                                            uint64_t total_bits, uint32_t *lut, uint32_t *ltab,
-                                                            uint32_t *err) {
-  __shared__ uint32_t bl[kLmax + 1], first[kLmax + 1], basel[kLmax + 1];
+                                                            uint64_t total_bits, uint16_t *lut, uint32_t *err) {
+  __shared__ uint32_t first[kLmax + 1], cnt[kLmax + 1], basel[kLmax + 1];
   __shared__ uint32_t wcnt[32][kLmax + 1];
-  __shared__ unsigned long long kraft;
+  __shared__ uint32_t wk[32];
+  __shared__ uint16_t sorted[kMaxSym];
   __shared__ unsigned long long wsum[32];
-  __shared__ int bad;
   const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
-  if (t <= kLmax) bl[t] = 0;
-  if (t == 0) { kraft = 0; bad = 0; }
-  if (t < 32 * (kLmax + 1)) (&wcnt[0][0])[t] = 0;
-  for (int i = t; i < (1 << kLutBits); i += kPrepThreads) lut[i] = 0;
-  __syncthreads();
   int L = t < (int)nsym ? lens_in[t] : 0;
-  if (L > kLmax) { bad = 1; L = 0; }
-  if (L) {
-    atomicAdd(&bl[L], 1u);
-    atomicAdd(&kraft, 1ull << (kLmax - L));
-  }
-  __syncthreads();
-  if (bad || kraft == 0 || kraft > (1ull << kLmax)) {
-    if (t == 0) dec_err(err, FZ_ECORRUPT);
-    return;
-  }
+  const bool badlen = L > kLmax;
+  if (badlen) L = 0;
+  // Kraft sum in units of 2^-14 (fits 32 bits for 1024 symbols)
+  uint32_t k = L ? (1u << (kLmax - L)) : 0u;
+  k = __reduce_add_sync(0xffffffffu, k);
+  const bool wbad = __any_sync(0xffffffffu, badlen);
   uint32_t rank = 0;
 #pragma unroll 1
   for (int l = 1; l <= kLmax; ++l) {
@@ -78,34 +78,52 @@ __global__ void __launch_bounds__(kPrepThreads) k_dec_prep(const uint8_t *__rest
     if (L == l) rank = __popc(b & ((1u << lane) - 1));
     if (lane == 0) wcnt[warp][l] = __popc(b);
   }
+  if (lane == 0) wk[warp] = wbad ? 0xffffffffu : k;
   __syncthreads();
-  if (t >= 1 && t <= kLmax) {
+  if (t >= 1 && t <= kLmax) {  // per-length counts and warp prefixes
     uint32_t acc = 0;
     for (int w = 0; w < 32; ++w) { uint32_t v = wcnt[w][t]; wcnt[w][t] = acc; acc += v; }
+    cnt[t] = acc;
   }
-  if (t == 0) {
-    uint32_t c = 0, b = 0;
-    for (int l = 1; l <= kLmax; ++l) {
-      c = (c + (l > 1 ? bl[l - 1] : 0u)) << 1;
-      first[l] = c;
-      basel[l] = b;
-      b += bl[l];
-      ltab[kLtFirst + l] = c;
-      ltab[kLtCount + l] = bl[l];
-      ltab[kLtBase + l] = basel[l];
+  if (t == 32) {
+    unsigned long long kraft = 0;
+    bool bad = false;
+    for (int w = 0; w < 32; ++w) {
+      if (wk[w] == 0xffffffffu) bad = true;
+      else kraft += wk[w];
     }
-    ltab[kLtFirst] = ltab[kLtCount] = ltab[kLtBase] = 0;
+    first[0] = (bad || kraft == 0 || kraft > (1ull << kLmax)) ? 1u : 0u;  // status flag
   }
   __syncthreads();
-  if (L) {
-    const uint32_t r = wcnt[warp][L] + rank;
-    const uint32_t code = first[L] + r;
-    ltab[kLtSorted + basel[L] + r] = (uint32_t)t;
-    if (L <= kLutBits) {
-      const uint32_t e = ((uint32_t)L << 16) | (uint32_t)t;
-      const uint32_t lo = code << (kLutBits - L), cnt = 1u << (kLutBits - L);
-      for (uint32_t i = 0; i < cnt; ++i) lut[lo + i] = e;
+  if (first[0]) {
+    if (t == 0) dec_err(err, FZ_ECORRUPT);
+    return;
+  }
+  __syncthreads();
+  if (t == 0) {
+    uint32_t c = 0, b = 0;
+    cnt[0] = 0;
+    first[0] = 0;
+    for (int l = 1; l <= kLmax; ++l) {
+      c = (c + cnt[l - 1]) << 1;
+      first[l] = c;
+      basel[l] = b;
+      b += cnt[l];
     }
+  }
+  __syncthreads();
+  if (L) sorted[basel[L] + wcnt[warp][L] + rank] = (uint16_t)t;
+  __syncthreads();
+  // every table entry: the codeword whose left-aligned range contains it
+  for (int e = t; e < kLutSize; e += kPrepThreads) {
+    uint16_t v = 0;
+#pragma unroll
+    for (int l = 1; l <= kLmax; ++l) {
+      const uint32_t c = (uint32_t)e >> (kLmax - l);
+      if (cnt[l] && c >= first[l] && c - first[l] < cnt[l])
+        v = (uint16_t)(kLutValid | ((l - 1) << 10) | sorted[basel[l] + c - first[l]]);
+    }
+    lut[e] = v;
   }
   // exclusive scan of the group bit sums (in place)
   const uint64_t per = (n_groups + kPrepThreads - 1) / kPrepThreads;
@@ -139,68 +157,67 @@ __global__ void __launch_bounds__(kPrepThreads) k_dec_prep(const uint8_t *__rest
 
 struct DecParams {
   const uint32_t *words;
-  uint64_t n_words;
+  uint64_t n_words;       // bitstream words
   const uint32_t *chunk_bits;
   const int32_t *anchors;
   const uint32_t *out_idx;
   const int32_t *out_val;
   const uint32_t *exc_idx;
   const uint32_t *exc_val;
-  uint64_t n_out, n_exc, n_chunks;
+  uint64_t n_out, n_exc, n_chunks, n_groups;
   const uint64_t *goff;
-  const uint32_t *lut;
-  const uint32_t *ltab;
+  const uint16_t *lut;
   uint32_t *err;
   float *out;
   float ebx2;
   int32_t R;
 };
 
+// MSB-first bit reader over one chunk.  A 64-bit buffer holds the next
+// bits; when fewer than 32 remain it takes the next stream word.  That word
+// and the one after it are loaded two refills ahead, and every step is
+// predicated rather than branched, so lanes that consume bits at different
+// rates never diverge.
 struct BitReader {
   const uint32_t *W;
-  uint64_t nw, wi;
+  uint64_t nw, wi;  // words available; index of the word after pend1
+  uint32_t pend0, pend1;
   unsigned long long buf;
   int nb;
   uint32_t used;
   __device__ __forceinline__ uint32_t ld(uint64_t i) const { return i < nw ? __ldg(W + i) : 0u; }
   __device__ __forceinline__ void init(const uint32_t *w, uint64_t n, uint64_t bitpos) {
-    W = w; nw = n; wi = bitpos >> 5;
+    W = w;
+    nw = n;
+    const uint64_t sw = bitpos >> 5;
     const int sk = (int)(bitpos & 31u);
-    buf = (((unsigned long long)ld(wi) << 32) | ld(wi + 1)) << sk;
+    buf = (((unsigned long long)ld(sw) << 32) | ld(sw + 1)) << sk;
     nb = 64 - sk;
-    wi += 2;
+    pend0 = ld(sw + 2);
+    pend1 = ld(sw + 3);
+    wi = sw + 4;
     used = 0;
+  }
+  __device__ __forceinline__ uint32_t next(const uint16_t *slut, bool &bad) {
+    const bool need = nb < 32;
+    buf |= need ? ((unsigned long long)pend0 << (32 - nb)) : 0ull;
+    nb += need ? 32 : 0;
+    const uint32_t fresh = (need && wi < nw) ? __ldg(W + wi) : 0u;
+    pend0 = need ? pend1 : pend0;
+    pend1 = need ? fresh : pend1;
+    wi += need ? 1 : 0;
+    const uint32_t e = slut[buf >> (64 - kLutBits)];
+    const uint32_t L = ((e >> 10) & 15u) + 1u;
+    bad |= !(e & kLutValid);
+    buf <<= L;
+    nb -= (int)L;
+    used += L;
+    return e & 1023u;
   }
 };
 
-__device__ __noinline__ uint32_t decode_long(unsigned long long buf, const uint32_t *slt, const uint16_t *ssorted,
-                                             uint32_t &L) {
-  for (int l = kLutBits + 1; l <= kLmax; ++l) {
-    const uint32_t v = (uint32_t)(buf >> (64 - l));
-    const uint32_t d = v - slt[kLtFirst + l];
-    if (d < slt[kLtCount + l]) { L = (uint32_t)l; return ssorted[slt[kLtBase + l] + d]; }
-  }
-  L = 0;
-  return 0xffffffffu;
-}
-
-__device__ __forceinline__ uint32_t next_sym(BitReader &br, const uint32_t *slut, const uint32_t *slt,
-                                             const uint16_t *ssorted, bool &bad) {
-  if (br.nb < 32) {
-    br.buf |= (unsigned long long)br.ld(br.wi) << (32 - br.nb);
-    ++br.wi;
-    br.nb += 32;
-  }
-  const uint32_t e = slut[br.buf >> (64 - kLutBits)];
-  uint32_t L = e >> 16, sym = e & 0xffffu;
-  if (L == 0) {
-    sym = decode_long(br.buf, slt, ssorted, L);
-    if (L == 0) { bad = true; L = 1; sym = 0xffffffffu; }
-  }
-  br.buf <<= L;
-  br.nb -= (int)L;
-  br.used += L;
-  return sym;
+__device__ __forceinline__ void prefetch_l2(const void *p) {
+  asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
 }
 
 __device__ __forceinline__ uint64_t lower_bound_u32(const uint32_t *a, uint64_t n, uint32_t key) {
@@ -212,41 +229,51 @@ __device__ __forceinline__ uint64_t lower_bound_u32(const uint32_t *a, uint64_t 
   return lo;
 }
 
-// Per-thread state for outliers and exceptions of one block.
+// Outliers and exceptions of one block (both lists ascend by code-stream
+// position).  The rare paths are out of line to keep the unrolled decode
+// loop small.
 struct Side {
   uint64_t oc, ec;
   uint32_t next_e;
-  __device__ __forceinline__ int32_t outlier(const DecParams &p, uint32_t pos0, uint32_t pos, bool &bad) {
-    if (oc == ~0ull) oc = lower_bound_u32(p.out_idx, p.n_out, pos0);
-    if (oc < p.n_out && __ldg(p.out_idx + oc) == pos) return __ldg(p.out_val + oc++);
-    bad = true;
-    return 0;
-  }
-  __device__ __forceinline__ void init_exc(const DecParams &p, uint32_t pos0) {
-    oc = ~0ull;
-    next_e = 0xffffffffu;
-    ec = 0;
-    if (p.n_exc) {
-      ec = lower_bound_u32(p.exc_idx, p.n_exc, pos0);
-      if (ec < p.n_exc) next_e = __ldg(p.exc_idx + ec);
-    }
-  }
-  __device__ __forceinline__ float exc(const DecParams &p, uint32_t pos, float v) {
-    if (pos != next_e) return v;
-    float r = __uint_as_float(__ldg(p.exc_val + ec));
-    ++ec;
-    next_e = ec < p.n_exc ? __ldg(p.exc_idx + ec) : 0xffffffffu;
-    return r;
-  }
 };
 
-// Residual of the next symbol: code - R, the outlier value for code 0.
-__device__ __forceinline__ int32_t next_delta(BitReader &br, const uint32_t *slut, const uint32_t *slt,
-                                              const uint16_t *ssorted, const DecParams &p, Side &sd,
+__device__ __noinline__ int32_t fetch_outlier(const DecParams &p, Side &sd, uint32_t pos0, uint32_t pos,
+                                              bool &bad) {
+  if (sd.oc == ~0ull) sd.oc = lower_bound_u32(p.out_idx, p.n_out, pos0);
+  if (sd.oc < p.n_out && __ldg(p.out_idx + sd.oc) == pos) return __ldg(p.out_val + sd.oc++);
+  bad = true;
+  return 0;
+}
+
+__device__ __noinline__ float fetch_exception(const DecParams &p, Side &sd) {
+  const float r = __uint_as_float(__ldg(p.exc_val + sd.ec));
+  ++sd.ec;
+  sd.next_e = sd.ec < p.n_exc ? __ldg(p.exc_idx + sd.ec) : 0xffffffffu;
+  return r;
+}
+
+__device__ __forceinline__ void init_side(const DecParams &p, Side &sd, uint32_t pos0) {
+  sd.oc = ~0ull;
+  sd.ec = 0;
+  sd.next_e = 0xffffffffu;
+  if (p.n_exc) {
+    sd.ec = lower_bound_u32(p.exc_idx, p.n_exc, pos0);
+    if (sd.ec < p.n_exc) sd.next_e = __ldg(p.exc_idx + sd.ec);
+  }
+}
+
+// Residual of the next symbol: code - R, or the stored outlier for code 0.
+__device__ __forceinline__ int32_t next_delta(BitReader &br, const uint16_t *slut, const DecParams &p, Side &sd,
                                               uint32_t pos0, uint32_t pos, bool &bad) {
-  const uint32_t sym = next_sym(br, slut, slt, ssorted, bad);
-  if (sym == 0) return sd.outlier(p, pos0, pos, bad);
+  const uint32_t sym = br.next(slut, bad);
+  if (sym == 0) return fetch_outlier(p, sd, pos0, pos, bad);
   return (int32_t)sym - p.R;
+}
+
+__device__ __forceinline__ float value(const DecParams &p, Side &sd, uint32_t pos, int32_t q) {
+  float v = __fmul_rn(__int2float_rn(q), p.ebx2);
+  if (pos == sd.next_e) v = fetch_exception(p, sd);
+  return v;
 }
 
 __device__ __forceinline__ void store4(float *out, uint64_t f, bool vec, const float *o) {
@@ -258,48 +285,38 @@ __device__ __forceinline__ void store4(float *out, uint64_t f, bool vec, const f
   }
 }
 
+// Per-thread prefix state that does not fit registers lives in shared
+// memory, one column per thread ([i][thread] layout, conflict-free):
+// 3D: the plane sums P (64 per order), 2D: the column sums Y (32 per order).
 template <int NDIM, int K>
-__global__ void __launch_bounds__(kDecThreads) k_decode(DecParams p, Geom g) {
-  __shared__ uint32_t slut[1 << kLutBits];
-  __shared__ uint32_t slt[kLtSorted];
-  __shared__ uint16_t ssorted[kMaxSym];
-  __shared__ unsigned long long swarp[kDecThreads / 32];
-  const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
-  for (int i = t; i < (1 << kLutBits); i += kDecThreads) slut[i] = __ldg(p.lut + i);
-  for (int i = t; i < kLtSorted; i += kDecThreads) slt[i] = __ldg(p.ltab + i);
-  for (int i = t; i < kMaxSym; i += kDecThreads) ssorted[i] = (uint16_t)__ldg(p.ltab + kLtSorted + i);
-  const uint64_t j = (uint64_t)blockIdx.x * kDecThreads + t;
-  const bool valid = j < p.n_chunks;
-  const uint32_t cb = valid ? __ldg(p.chunk_bits + j) : 0u;
-  unsigned long long incl = cb;
-  for (int off = 1; off < 32; off <<= 1) {
-    unsigned long long v = __shfl_up_sync(0xffffffffu, incl, off);
-    if (lane >= off) incl += v;
-  }
-  if (lane == 31) swarp[warp] = incl;
-  __syncthreads();
-  unsigned long long start = p.goff[blockIdx.x] + incl - cb;
-  for (int w = 0; w < warp; ++w) start += swarp[w];
-  if (!valid) return;
+struct DecState {
+  static constexpr int kWords = NDIM == 3 ? 64 * K : (NDIM == 2 ? 32 * K : 0);
+};
 
+template <int NDIM, int K>
+constexpr size_t dec_smem_bytes() {
+  return sizeof(uint16_t) * kLutSize + sizeof(int32_t) * (size_t)DecState<NDIM, K>::kWords * kDecThreads;
+}
+
+template <int NDIM, int K>
+__device__ __forceinline__ void decode_chunk(const DecParams &p, const Geom &g, const uint16_t *slut,
+                                             int32_t *st, uint64_t j, uint64_t start, bool vecbase) {
+  constexpr int T = kDecThreads;
   bool bad = false;
   BitReader br;
   br.init(p.words, p.n_words, start);
   const uint32_t pos0 = (uint32_t)(j * g.bsize);
   Side sd;
-  sd.init_exc(p, pos0);
+  init_side(p, sd, pos0);
   const int32_t anchor = __ldg(p.anchors + j);
-  const float ebx2 = p.ebx2;
   const uint32_t bxi = (uint32_t)(j % g.nbx);
   const uint64_t jr = j / g.nbx;
   const uint32_t byi = (uint32_t)(jr % g.nby), bzi = (uint32_t)(jr / g.nby);
   const uint32_t X0 = bxi * g.bx, Y0 = byi * g.by, Z0 = bzi * g.bz;
-  const bool vecbase = ((g.nx & 3u) == 0) && (((uintptr_t)p.out & 15u) == 0);
+  for (int i = 0; i < DecState<NDIM, K>::kWords; ++i) st[i * T] = 0;
 
   if (NDIM == 3) {
-    int32_t P1[64], P2[64];
-#pragma unroll
-    for (int i = 0; i < 64; ++i) { P1[i] = 0; P2[i] = 0; }
+    // st[(y*8+x)*T]: plane sums of order 1; st[(64+y*8+x)*T]: order 2
     const bool xfull = X0 + 8 <= g.nx;
 #pragma unroll 1
     for (int z = 0; z < 8; ++z) {
@@ -307,23 +324,29 @@ __global__ void __launch_bounds__(kDecThreads) k_decode(DecParams p, Geom g) {
 #pragma unroll
       for (int i = 0; i < 8; ++i) { Y1[i] = 0; Y2[i] = 0; }
       const bool zin = Z0 + z < g.nz;
-#pragma unroll
+#pragma unroll 1
       for (int y = 0; y < 8; ++y) {
         int32_t r1 = 0, r2 = 0;
         float o[8];
+        int32_t *row = st + (y * 8) * T;
 #pragma unroll
         for (int x = 0; x < 8; ++x) {
           const uint32_t pos = pos0 + (uint32_t)(z * 64 + y * 8 + x);
-          int32_t d = next_delta(br, slut, slt, ssorted, p, sd, pos0, pos, bad);
-          if (y == 0 && x == 0) d += (z == 0) ? anchor : 0;
+          int32_t d = next_delta(br, slut, p, sd, pos0, pos, bad);
+          if (x == 0) d += (y == 0 && z == 0) ? anchor : 0;
           int32_t q;
           if (K == 1) {
-            r1 += d; Y1[x] += r1; P1[y * 8 + x] += Y1[x]; q = P1[y * 8 + x];
+            r1 += d; Y1[x] += r1;
+            q = row[x * T] + Y1[x];
+            row[x * T] = q;
           } else {
             r1 += d; r2 += r1; Y1[x] += r2; Y2[x] += Y1[x];
-            P1[y * 8 + x] += Y2[x]; P2[y * 8 + x] += P1[y * 8 + x]; q = P2[y * 8 + x];
+            const int32_t p1 = row[x * T] + Y2[x];
+            row[x * T] = p1;
+            q = row[(64 + x) * T] + p1;
+            row[(64 + x) * T] = q;
           }
-          o[x] = sd.exc(p, pos, __fmul_rn(__int2float_rn(q), ebx2));
+          o[x] = value(p, sd, pos, q);
         }
         if (zin && Y0 + y < g.ny) {
           const uint64_t f = ((uint64_t)(Z0 + z) * g.ny + (Y0 + y)) * g.nx + X0;
@@ -339,72 +362,134 @@ __global__ void __launch_bounds__(kDecThreads) k_decode(DecParams p, Geom g) {
       }
     }
   } else if (NDIM == 2) {
-    int32_t Y1[32], Y2[32];
-#pragma unroll
-    for (int i = 0; i < 32; ++i) { Y1[i] = 0; Y2[i] = 0; }
+    // st[x*T]: column sums of order 1; st[(32+x)*T]: order 2
     const bool xfull = X0 + 32 <= g.nx;
 #pragma unroll 1
     for (int y = 0; y < 32; ++y) {
       int32_t r1 = 0, r2 = 0;
       const bool yin = Y0 + y < g.ny;
       const uint64_t f = ((uint64_t)(Y0 + y)) * g.nx + X0;
+#pragma unroll 1
+      for (int x8 = 0; x8 < 4; ++x8) {
+        float o[8];
+        int32_t *col = st + (x8 * 8) * T;
 #pragma unroll
-      for (int x4 = 0; x4 < 8; ++x4) {
-        float o[4];
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          const int x = 4 * x4 + u;
-          const uint32_t pos = pos0 + (uint32_t)(y * 32 + x);
-          int32_t d = next_delta(br, slut, slt, ssorted, p, sd, pos0, pos, bad);
-          if (x == 0) d += (y == 0) ? anchor : 0;
+        for (int u = 0; u < 8; ++u) {
+          const uint32_t pos = pos0 + (uint32_t)(y * 32 + x8 * 8 + u);
+          int32_t d = next_delta(br, slut, p, sd, pos0, pos, bad);
+          if (u == 0) d += (x8 == 0 && y == 0) ? anchor : 0;
           int32_t q;
-          if (K == 1) { r1 += d; Y1[x] += r1; q = Y1[x]; }
-          else { r1 += d; r2 += r1; Y1[x] += r2; Y2[x] += Y1[x]; q = Y2[x]; }
-          o[u] = sd.exc(p, pos, __fmul_rn(__int2float_rn(q), ebx2));
+          if (K == 1) {
+            r1 += d;
+            q = col[u * T] + r1;
+            col[u * T] = q;
+          } else {
+            r1 += d; r2 += r1;
+            const int32_t y1 = col[u * T] + r2;
+            col[u * T] = y1;
+            q = col[(32 + u) * T] + y1;
+            col[(32 + u) * T] = q;
+          }
+          o[u] = value(p, sd, pos, q);
         }
         if (yin) {
-          if (xfull) store4(p.out, f + 4 * x4, vecbase, o);
-          else {
+          const uint64_t fx = f + 8 * x8;
+          if (xfull) {
+            store4(p.out, fx, vecbase, o);
+            store4(p.out, fx + 4, vecbase, o + 4);
+          } else {
 #pragma unroll
-            for (int u = 0; u < 4; ++u)
-              if (X0 + 4 * x4 + u < g.nx) p.out[f + 4 * x4 + u] = o[u];
+            for (int u = 0; u < 8; ++u)
+              if (X0 + 8 * x8 + u < g.nx) p.out[fx + u] = o[u];
           }
         }
       }
     }
   } else {
+    // the anchor enters the first running sum once, as the origin residual
     int32_t r1 = anchor, r2 = 0;
     const uint64_t f0 = (uint64_t)X0;
     const bool full = X0 + 1024 <= g.nx;
-#pragma unroll 2
-    for (int x4 = 0; x4 < 256; ++x4) {
-      float o[4];
+#pragma unroll 1
+    for (int x8 = 0; x8 < 128; ++x8) {
+      float o[8];
 #pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        const uint32_t pos = pos0 + (uint32_t)(4 * x4 + u);
-        int32_t d = next_delta(br, slut, slt, ssorted, p, sd, pos0, pos, bad);
+      for (int u = 0; u < 8; ++u) {
+        const uint32_t pos = pos0 + (uint32_t)(8 * x8 + u);
+        int32_t d = next_delta(br, slut, p, sd, pos0, pos, bad);
         int32_t q;
         if (K == 1) { r1 += d; q = r1; }
-        else {
-          // anchor enters the first running sum once, as the origin residual
-          r1 += d; r2 += r1; q = r2;
-        }
-        o[u] = sd.exc(p, pos, __fmul_rn(__int2float_rn(q), ebx2));
+        else { r1 += d; r2 += r1; q = r2; }
+        o[u] = value(p, sd, pos, q);
       }
-      if (full) store4(p.out, f0 + 4 * x4, vecbase, o);
-      else {
+      if (full) {
+        store4(p.out, f0 + 8 * x8, vecbase, o);
+        store4(p.out, f0 + 8 * x8 + 4, vecbase, o + 4);
+      } else {
 #pragma unroll
-        for (int u = 0; u < 4; ++u)
-          if (X0 + 4 * x4 + u < g.nx) p.out[f0 + 4 * x4 + u] = o[u];
+        for (int u = 0; u < 8; ++u)
+          if (X0 + 8 * x8 + u < g.nx) p.out[f0 + 8 * x8 + u] = o[u];
       }
     }
   }
-  if (br.used != cb || bad) dec_err(p.err, FZ_ECORRUPT);
+  if (br.used != __ldg(p.chunk_bits + j) || bad) dec_err(p.err, FZ_ECORRUPT);
 }
 
 template <int NDIM, int K>
-void launch_dec_t(const DecParams &p, const Geom &g, uint64_t n_groups, cudaStream_t s) {
-  k_decode<NDIM, K><<<(unsigned)n_groups, kDecThreads, 0, s>>>(p, g);
+__global__ void __launch_bounds__(kDecThreads) k_decode(DecParams p, Geom g) {
+  extern __shared__ __align__(16) unsigned char d_smem[];
+  uint16_t *slut = reinterpret_cast<uint16_t *>(d_smem);
+  int32_t *sstate = reinterpret_cast<int32_t *>(d_smem + sizeof(uint16_t) * kLutSize);
+  __shared__ unsigned long long swarp[kDecThreads / 32];
+  const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+  {
+    const uint4 *src = reinterpret_cast<const uint4 *>(p.lut);
+    uint4 *dst = reinterpret_cast<uint4 *>(slut);
+    for (int i = t; i < kLutSize / 8; i += kDecThreads) dst[i] = __ldg(src + i);
+  }
+  const bool vecbase = ((g.nx & 3u) == 0) && (((uintptr_t)p.out & 15u) == 0);
+  for (uint64_t grp = blockIdx.x; grp < p.n_groups; grp += gridDim.x) {
+    {
+      // pull the next group's bitstream (one contiguous range) into L2
+      const uint64_t ng = grp + gridDim.x;
+      if (ng < p.n_groups) {
+        const uint64_t w0 = p.goff[ng] >> 5;
+        const uint64_t w1 = ng + 1 < p.n_groups ? (p.goff[ng + 1] + 31) >> 5 : p.n_words;
+        for (uint64_t w = w0 + 32 * (uint64_t)t; w < w1 && w < p.n_words; w += 32 * (uint64_t)kDecThreads)
+          prefetch_l2(p.words + w);
+      }
+    }
+    const uint64_t j = grp * kDecThreads + t;
+    const bool valid = j < p.n_chunks;
+    const uint32_t cb = valid ? __ldg(p.chunk_bits + j) : 0u;
+    unsigned long long incl = cb;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+      const unsigned long long v = __shfl_up_sync(0xffffffffu, incl, off);
+      if (lane >= off) incl += v;
+    }
+    __syncthreads();  // the table is in place and swarp is free again
+    if (lane == 31) swarp[warp] = incl;
+    __syncthreads();
+    unsigned long long start = p.goff[grp] + incl - cb;
+    for (int w = 0; w < warp; ++w) start += swarp[w];
+    if (valid) decode_chunk<NDIM, K>(p, g, slut, sstate + t, j, start, vecbase);
+  }
+}
+
+template <int NDIM, int K>
+cudaError_t launch_dec_t(const DecParams &p, const Geom &g, int sm_count, cudaStream_t s) {
+  const int smem = (int)dec_smem_bytes<NDIM, K>();
+  cudaError_t e = cudaFuncSetAttribute(k_decode<NDIM, K>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e != cudaSuccess) return e;
+  int per_sm = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_decode<NDIM, K>, kDecThreads, smem);
+  if (e != cudaSuccess) return e;
+  if (per_sm < 1) per_sm = 1;
+  uint64_t grid = (uint64_t)sm_count * per_sm;
+  if (grid > p.n_groups) grid = p.n_groups;
+  k_decode<NDIM, K><<<(unsigned)grid, kDecThreads, smem, s>>>(p, g);
+  return cudaGetLastError();
 }
 
 }  // namespace
@@ -418,21 +503,18 @@ cudaError_t launch_decode_prep(const uint8_t *d_in, const fz_header &h, const De
     k_dec_gsum<<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(cbits, n_chunks, n_groups, ws.gsum);
   }
   k_dec_prep<<<1, kPrepThreads, 0, s>>>(d_in + h.off_lens, 2 * h.radius, ws.gsum, n_groups, h.total_bits, ws.lut,
-                                        ws.ltab, ws.err);
+                                        ws.err);
   return cudaGetLastError();
 }
 
 cudaError_t launch_decode_main(const uint8_t *d_in, const fz_header &h, float *d_out, const DecodeWs &ws,
-                               cudaStream_t s) {
+                               cudaStream_t s, int sm_count) {
   Geom g;
   make_geom(h.ndim, h.dims, g);
-  const uint64_t n_chunks = h.n_chunks;
-  const uint64_t n_groups = (n_chunks + kDecThreads - 1) / kDecThreads;
-  const uint32_t *cbits = reinterpret_cast<const uint32_t *>(d_in + h.off_chunk_bits);
   DecParams p;
   p.words = reinterpret_cast<const uint32_t *>(d_in + h.off_bits);
   p.n_words = (h.total_bits + 31) / 32;
-  p.chunk_bits = cbits;
+  p.chunk_bits = reinterpret_cast<const uint32_t *>(d_in + h.off_chunk_bits);
   p.anchors = reinterpret_cast<const int32_t *>(d_in + h.off_anchors);
   p.out_idx = reinterpret_cast<const uint32_t *>(d_in + h.off_out_idx);
   p.out_val = reinterpret_cast<const int32_t *>(d_in + h.off_out_val);
@@ -440,26 +522,22 @@ cudaError_t launch_decode_main(const uint8_t *d_in, const fz_header &h, float *d
   p.exc_val = reinterpret_cast<const uint32_t *>(d_in + h.off_exc_val);
   p.n_out = h.n_out;
   p.n_exc = h.n_exc;
-  p.n_chunks = n_chunks;
+  p.n_chunks = h.n_chunks;
+  p.n_groups = (h.n_chunks + kDecThreads - 1) / kDecThreads;
   p.goff = ws.gsum;
   p.lut = ws.lut;
-  p.ltab = ws.ltab;
   p.err = ws.err;
   p.out = d_out;
   memcpy(&p.ebx2, &h.ebx2_bits, 4);
   p.R = (int32_t)h.radius;
   const bool k2 = h.predictor == FZ_PRED_LORENZO2;
   switch (g.ndim) {
-    case 1: k2 ? launch_dec_t<1, 2>(p, g, n_groups, s) : launch_dec_t<1, 1>(p, g, n_groups, s); break;
-    case 2: k2 ? launch_dec_t<2, 2>(p, g, n_groups, s) : launch_dec_t<2, 1>(p, g, n_groups, s); break;
-    default: k2 ? launch_dec_t<3, 2>(p, g, n_groups, s) : launch_dec_t<3, 1>(p, g, n_groups, s); break;
+    case 1: return k2 ? launch_dec_t<1, 2>(p, g, sm_count, s) : launch_dec_t<1, 1>(p, g, sm_count, s);
+    case 2: return k2 ? launch_dec_t<2, 2>(p, g, sm_count, s) : launch_dec_t<2, 1>(p, g, sm_count, s);
+    default: return k2 ? launch_dec_t<3, 2>(p, g, sm_count, s) : launch_dec_t<3, 1>(p, g, sm_count, s);
   }
-  return cudaGetLastError();
 }
 
-}  // namespace fz
-
-namespace fz {
 namespace {
 __global__ void k_fill(float *out, uint64_t n, uint32_t bits) {
   const float v = __uint_as_float(bits);
@@ -476,4 +554,5 @@ cudaError_t launch_fill(float *out, uint64_t n, uint32_t bits, cudaStream_t s, i
   k_fill<<<(unsigned)grid, 256, 0, s>>>(out, n, bits);
   return cudaGetLastError();
 }
+
 }  // namespace fz

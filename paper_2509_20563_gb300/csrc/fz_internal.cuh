@@ -11,12 +11,13 @@
 namespace fz {
 
 constexpr int kMaxSym = 1024;      // 2R <= 1024 (R <= 512)
-constexpr int kLmax = 24;          // longest Huffman codeword
-constexpr int kLutBits = 12;       // first-level decode table width
+constexpr int kLmax = 14;          // longest Huffman codeword (length limit of the format)
+constexpr int kLutBits = 14;       // decode table width: every codeword resolves in one lookup
 constexpr int kTileElems = 4096;   // elements per quantization tile
 constexpr int kQuantThreads = 256; // 8 warps per quantization tile
 constexpr int kEncWarps = 8;       // chunks per encode tile (one warp per chunk)
-constexpr int kDecThreads = 128;   // chunks per decode CTA (one thread per chunk)
+constexpr int kDecThreads = 256;   // chunks per decode CTA (one thread per chunk)
+constexpr int kTileGroup = 1024;   // quantization tiles per outlier-offset group
 
 enum Mode : uint32_t { kModeNormal = 0, kModeConst = 1, kModeRaw = 2 };
 
@@ -71,8 +72,8 @@ struct Ctl {
   // REL range: max of inverted ordered keys for the minimum, max of ordered
   // keys for the maximum, and the same on raw bit patterns.
   unsigned int lo_nkey, hi_key, bits_nmin, bits_max, any_finite, range_done;
-  unsigned int quant_ticket, encode_ticket;
-  unsigned long long n_out, n_exc;
+  unsigned int encode_ticket, pad_t;
+  unsigned long long n_out, n_exc;   // totals; also the append cursors of the scratch lists
   // constants (written by the range tail or the ABS constants kernel)
   double eb_abs;
   float ebx2, inv2eb, eb_chk;
@@ -141,14 +142,17 @@ __device__ __forceinline__ uint64_t lb_add(uint64_t a, uint64_t b) {
   return lo | (hi << 31);
 }
 
-// Called by one thread of the tile.  Returns the exclusive prefix.
+// Publishes the tile's aggregate (tile 0 publishes its inclusive prefix).
+__device__ __forceinline__ void lookback_publish(uint64_t *status, uint64_t tile, uint64_t agg) {
+  st_status(&status[tile], (tile == 0 ? kLbFlagInc : kLbFlagAgg) | agg);
+}
+
+// After lookback_publish: walks back to the nearest inclusive prefix, then
+// publishes this tile's inclusive prefix.  Called by one thread of the tile;
+// returns the exclusive prefix.
 template <bool kPacked2>
-__device__ uint64_t lookback(uint64_t *status, uint64_t tile, uint64_t agg, Ctl *ctl) {
-  if (tile == 0) {
-    st_status(&status[0], kLbFlagInc | agg);
-    return 0;
-  }
-  st_status(&status[tile], kLbFlagAgg | agg);
+__device__ uint64_t lookback_resolve(uint64_t *status, uint64_t tile, uint64_t agg, Ctl *ctl) {
+  if (tile == 0) return 0;
   uint64_t excl = 0;
   int64_t j = (int64_t)tile - 1;
   long long t0 = clock64();
@@ -170,18 +174,62 @@ __device__ uint64_t lookback(uint64_t *status, uint64_t tile, uint64_t agg, Ctl 
   return excl;
 }
 
+// Warp-cooperative variant of lookback_resolve (non-packed values): the 32
+// lanes read 32 predecessors at once, so the walk back costs one round of
+// loads per 32 tiles.  All lanes of the warp must call it; returns the
+// exclusive prefix in every lane.
+__device__ __forceinline__ uint64_t lookback_resolve_warp(uint64_t *status, uint64_t tile, uint64_t agg,
+                                                          Ctl *ctl) {
+  const int lane = threadIdx.x & 31;
+  if (tile == 0) return 0;
+  uint64_t excl = 0;
+  int64_t hi = (int64_t)tile - 1;  // highest predecessor not yet summed
+  long long t0 = clock64();
+  bool timed_out = false;
+  while (hi >= 0) {
+    const int64_t j = hi - lane;
+    uint64_t v = j >= 0 ? ld_volatile_u64(&status[j]) : (kLbFlagInc | 0ull);
+    uint32_t flag = (uint32_t)(v >> 62);
+    // the nearest inclusive prefix in the window (lowest lane index with flag 2)
+    const uint32_t inc_mask = __ballot_sync(0xffffffffu, flag == 2);
+    const int stop = inc_mask ? __ffs(inc_mask) - 1 : 31;
+    const uint32_t missing = __ballot_sync(0xffffffffu, flag == 0 && lane <= stop);
+    if (missing) {
+      if (clock64() - t0 > kSpinCycles) { timed_out = true; break; }
+      __nanosleep(32);
+      continue;
+    }
+    uint64_t part = lane <= stop ? (v & kLbMask) : 0ull;
+    for (int off = 16; off > 0; off >>= 1) part += __shfl_down_sync(0xffffffffu, part, off);
+    part = __shfl_sync(0xffffffffu, part, 0);
+    excl = (excl + part) & kLbMask;
+    if (inc_mask) break;
+    hi -= 32;
+  }
+  if (timed_out && lane == 0) set_err(ctl, FZ_ETIMEOUT);
+  if (lane == 0) st_status(&status[tile], kLbFlagInc | ((excl + agg) & kLbMask));
+  return excl;
+}
+
+template <bool kPacked2>
+__device__ __forceinline__ uint64_t lookback(uint64_t *status, uint64_t tile, uint64_t agg, Ctl *ctl) {
+  lookback_publish(status, tile, agg);
+  return lookback_resolve<kPacked2>(status, tile, agg, ctl);
+}
+
 inline __host__ __device__ uint64_t align16(uint64_t v) { return (v + 15u) & ~(uint64_t)15u; }
 
 // ---------------------------------------------------------------- workspace layout
 // Device scratch owned by the context for one compress call.
 struct CompressWs {
   Ctl *ctl;
-  uint64_t *qstatus;       // look-back status per quantization tile
+  uint4 *tinfo;            // per quantization tile: n_out, n_exc, first outlier slot, first exception slot
+  uint2 *tgroup;           // per group of kTileGroup tiles: outlier and exception counts
   uint64_t *estatus;       // look-back status per encode tile
   size_t zero_bytes;       // bytes from ctl to the end of estatus (memset per call)
   uint16_t *codes;         // npad block-major codes
   int32_t *anchors;        // n_blocks
-  uint32_t *out_idx;       // cap_list
+  uint32_t *out_idx;       // cap_list entries, grouped by tile (tile order given by tinfo)
   int32_t *out_val;
   uint32_t *exc_idx;
   uint32_t *exc_val;
@@ -197,20 +245,19 @@ cudaError_t launch_quant(const float *x, const Geom &g, uint32_t R, uint32_t pre
                          cudaStream_t s, int sm_count);
 cudaError_t launch_codebook(const Geom &g, uint32_t R, uint32_t pred, uint32_t eb_mode, double eb,
                             const CompressWs &ws, cudaStream_t s);
-cudaError_t launch_encode(const Geom &g, const CompressWs &ws, uint8_t *d_out, cudaStream_t s);
+cudaError_t launch_encode(const Geom &g, const CompressWs &ws, uint8_t *d_out, cudaStream_t s, int sm_count);
 cudaError_t launch_assemble(const float *x, const Geom &g, uint32_t R, const CompressWs &ws, uint8_t *d_out,
                             cudaStream_t s, int sm_count);
 cudaError_t launch_codebook_only(const uint64_t *hist, uint32_t nsym, uint8_t *lens, uint32_t *codes,
                                  Ctl *ctl, cudaStream_t s);
 
 struct DecodeWs {
-  uint32_t *lut;           // 1 << kLutBits entries: (len << 16) | sym, len 0 = long code
-  uint32_t *ltab;          // long-code tables: first[25], count[25], base[25], sorted syms[1024]
+  uint16_t *lut;           // 1 << kLutBits entries: valid bit, length-1, symbol
   uint64_t *gsum;          // per decode group: sum of chunk bits, then exclusive offset
   uint32_t *err;           // device error word
 };
 cudaError_t launch_decode_prep(const uint8_t *d_in, const fz_header &h, const DecodeWs &ws, cudaStream_t s);
 cudaError_t launch_decode_main(const uint8_t *d_in, const fz_header &h, float *d_out, const DecodeWs &ws,
-                               cudaStream_t s);
+                               cudaStream_t s, int sm_count);
 cudaError_t launch_fill(float *out, uint64_t n, uint32_t bits, cudaStream_t s, int sm_count);
 }  // namespace fz

@@ -1,13 +1,22 @@
 // fz_quant.cu -- prediction + quantization module (FZModules §3.1-§3.2).
 //
-// One persistent kernel does, per tile of 4096 values (a run of consecutive
-// blocks along x): coalesced 16-byte loads of the field into shared memory
-// with FP32 prequantization (q = rint(x * inv2eb), per-value bound check ->
-// exceptions), the block-local Lorenzo residual read back from shared memory,
-// radius-R codes written in block-major order, anchors at block origins, the
-// code histogram in shared memory, and ordered compaction of outliers and
-// exceptions whose global offsets come from a bounded decoupled look-back
-// over tiles.  HBM traffic: 4 bytes read and 2 bytes written per value.
+// One persistent kernel walks the tiles of 4096 values (runs of consecutive
+// blocks along x) in a static schedule; the loads of the next tile are in
+// flight while the current one is processed.  Per tile:
+//   * FP32 prequantization q = rint(x * inv2eb) with the per-value bound
+//     check (exceptions), straight from registers;
+//   * the block-local Lorenzo residual, written as successive differences
+//     (1 - S_x)^k, (1 - S_y)^k, (1 - S_z)^k with zero padding at the block
+//     origin.  In 3D each warp owns one z-plane of the tile, each thread a
+//     4x4 patch, so the x and y differences stay in registers (warp
+//     shuffles for the patch borders) and only the z difference goes
+//     through shared memory.  1D and 2D tiles difference in shared memory;
+//   * radius-R codes in block-major order, anchors at block origins, the
+//     code histogram in shared memory;
+//   * outliers and exceptions, compacted in code-stream order inside the
+//     tile and appended to a scratch list at a slot taken with one atomic per
+//     tile; the assembler later lays the tiles out in order.
+// HBM traffic: 4 bytes read and 2 bytes written per value.
 #include "fz_internal.cuh"
 
 namespace fz {
@@ -29,14 +38,16 @@ struct TileShape<3> {
   static constexpr int BX = 8, BY = 8, BZ = 8, NB = 8, TX = 64, ROWS = 64, WPB = 1;
 };
 
+// q = rint(x * inv2eb) (binary32, half to even); an exception when |t| is
+// not below 2^23 (this also catches NaN and infinities, q forced to 0) or
+// when q * ebx2 misses x by more than eb_chk (q kept).
 __device__ __forceinline__ int32_t prequant(float x, float inv2eb, float ebx2, float eb_chk, bool &exc) {
-  if (!isfinite(x)) { exc = true; return 0; }
-  float t = __fmul_rn(x, inv2eb);
-  if (!(fabsf(t) < 8388608.0f)) { exc = true; return 0; }
-  int32_t q = __float2int_rn(t);
-  float r = __fmul_rn(__int2float_rn(q), ebx2);
-  float d = fabsf(__fsub_rn(x, r));
-  exc = d > eb_chk;
+  const float t = __fmul_rn(x, inv2eb);
+  const bool ok = fabsf(t) < 8388608.0f;
+  const int32_t q = ok ? __float2int_rn(t) : 0;
+  const float r = __fmul_rn(__int2float_rn(q), ebx2);
+  const float d = fabsf(__fsub_rn(x, r));
+  exc = !ok || d > eb_chk;
   return q;
 }
 
@@ -46,194 +57,406 @@ __device__ __forceinline__ int lz_coef(int o) {
   return o == 1 ? -2 : 1;
 }
 
-// Lorenzo-K residual of the point at (row, col) of the shared tile; terms that
-// fall before the block origin along any axis are zero.
-template <int NDIM, int K, int TXP>
-__device__ __forceinline__ int32_t lorenzo_residual(const int32_t *sq, int row, int col, int px, int py, int pz) {
+struct QuantConst {
+  float inv2eb, ebx2, eb_chk;
+  int32_t R;
+};
+
+// Code of residual d at a position; marks outliers.  Out-of-domain
+// positions and block origins get R.
+__device__ __forceinline__ uint32_t make_code(int32_t d, int32_t R, bool in, bool origin, bool &outl) {
+  const uint32_t c = (uint32_t)(d + R);
+  const bool o = (c - 1u) >= (uint32_t)(2 * R - 1);
+  const bool keep = in && !origin;
+  outl = keep && o;
+  return keep ? (o ? 0u : c) : (uint32_t)R;
+}
+
+// Tile coordinates.
+struct TileXY {
+  uint32_t tx, by, bz, x0, y0, z0;
+};
+template <int NDIM>
+__device__ __forceinline__ TileXY tile_xy(const Geom &g, uint64_t tile) {
   using S = TileShape<NDIM>;
+  TileXY t;
+  t.tx = (uint32_t)(tile % g.tiles_x);
+  const uint64_t rest = tile / g.tiles_x;
+  t.by = (uint32_t)(rest % g.nby);
+  t.bz = (uint32_t)(rest / g.nby);
+  t.x0 = t.tx * S::NB * S::BX;
+  t.y0 = t.by * S::BY;
+  t.z0 = t.bz * S::BZ;
+  return t;
+}
+
+// Per-thread element mapping of a tile for the loads: 4 float4 per thread.
+// 3D: warp = z-plane, lanes 0-15 rows 0-3, lanes 16-31 rows 4-7, 4 columns
+// each.  1D/2D: float4 index tid + 256 j in row-major tile order.
+template <int NDIM>
+__device__ __forceinline__ void elem_rc(int tid, int j, int &row, int &col) {
+  using S = TileShape<NDIM>;
+  if (NDIM == 3) {
+    const int warp = tid >> 5, lane = tid & 31;
+    row = warp * 8 + (lane >> 4) * 4 + j;
+    col = (lane & 15) * 4;
+  } else {
+    const int e = 4 * (tid + kQuantThreads * j);
+    row = e / S::TX;
+    col = e % S::TX;
+  }
+}
+
+template <int NDIM>
+__device__ __forceinline__ void load_tile(const float *__restrict__ x, const Geom &g, const TileXY &t, int tid,
+                                          bool vec_ok, float4 (&v)[4]) {
+  using S = TileShape<NDIM>;
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    int row, col;
+    elem_rc<NDIM>(tid, j, row, col);
+    const uint32_t X = t.x0 + col, Y = t.y0 + (row % S::BY), Z = t.z0 + row / S::BY;
+    const bool inrow = Y < g.ny && Z < g.nz;
+    const uint64_t fi = ((uint64_t)Z * g.ny + Y) * g.nx + X;
+    if (inrow && vec_ok && X < g.nx) {
+      v[j] = __ldcs(reinterpret_cast<const float4 *>(x + fi));
+    } else {
+      float a[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) a[u] = (inrow && X + u < g.nx) ? x[fi + u] : 0.0f;
+      v[j] = make_float4(a[0], a[1], a[2], a[3]);
+    }
+  }
+}
+
+// Shared memory of one CTA.
+template <int NDIM>
+struct QuantSmem {
+  static constexpr int TXP = TileShape<NDIM>::TX + 8;
+  int32_t sq[2][TileShape<NDIM>::ROWS * TXP];  // double-buffered q (1D/2D) or x/y-differenced q (3D)
+  uint8_t sexc[2][kTileElems];                 // exception flags, tile row-major
+  uint32_t shist[kMaxSym];
+  uint32_t wout[8], wexc[8];
+  uint32_t oslot, eslot;  // this tile's first entries in the scratch lists
+};
+
+// Residual at (row, col) of the shared tile for the ordered-compaction pass
+// and for 1D/2D codes.  3D tiles hold x/y-differenced values: only the z
+// difference remains.  1D/2D tiles hold q: the full difference is taken.
+template <int NDIM, int K>
+__device__ __forceinline__ int32_t smem_residual(const int32_t *sq, int row, int col, int px, int py, int pz) {
+  using S = TileShape<NDIM>;
+  constexpr int TXP = S::TX + 8;
   int32_t s = 0;
+  if (NDIM == 3) {
 #pragma unroll
-  for (int oz = 0; oz <= (NDIM >= 3 ? K : 0); ++oz)
+    for (int oz = 0; oz <= K; ++oz)
+      if (pz >= oz) s += lz_coef<K>(oz) * sq[(row - 8 * oz) * TXP + col];
+    return s;
+  }
 #pragma unroll
-    for (int oy = 0; oy <= (NDIM >= 2 ? K : 0); ++oy)
+  for (int oy = 0; oy <= (NDIM >= 2 ? K : 0); ++oy)
 #pragma unroll
-      for (int ox = 0; ox <= K; ++ox) {
-        int c = lz_coef<K>(ox);
-        if (NDIM >= 2) c *= lz_coef<K>(oy);
-        if (NDIM >= 3) c *= lz_coef<K>(oz);
-        bool ok = px >= ox && py >= oy && pz >= oz;
-        int32_t v = ok ? sq[(row - oy - S::BY * oz) * TXP + col - ox] : 0;
-        s += c * v;
-      }
+    for (int ox = 0; ox <= K; ++ox) {
+      int c = lz_coef<K>(ox);
+      if (NDIM >= 2) c *= lz_coef<K>(oy);
+      const bool ok = px >= ox && py >= oy;
+      s += ok ? c * sq[(row - oy) * TXP + col - ox] : 0;
+    }
   return s;
 }
 
-template <int NDIM, int K>
-__global__ void __launch_bounds__(kQuantThreads) k_quant(const float *__restrict__ x, Geom g, uint32_t R,
-                                                          CompressWs ws) {
+// Phase A of a tile: prequantize this thread's 16 values, difference them
+// along x and y in registers (3D), and store them to the shared tile.
+template <int NDIM, int K, bool INTERIOR>
+__device__ __forceinline__ void tile_front(const Geom &g, const TileXY &t, const float4 (&v)[4],
+                                           const QuantConst &qc, int32_t *sq, uint8_t *sexc, int32_t (&q)[4][4],
+                                           uint32_t (&exf)[4]) {
   using S = TileShape<NDIM>;
   constexpr int TXP = S::TX + 8;
+  const int tid = threadIdx.x, lane = tid & 31;
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    int row, col;
+    elem_rc<NDIM>(tid, j, row, col);
+    const uint32_t X = t.x0 + col, Y = t.y0 + (row % S::BY), Z = t.z0 + row / S::BY;
+    const bool inrow = INTERIOR || (Y < g.ny && Z < g.nz);
+    const float a[4] = {v[j].x, v[j].y, v[j].z, v[j].w};
+    exf[j] = 0;
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const bool in = INTERIOR || (inrow && X + u < g.nx);
+      bool ee;
+      const int32_t qq = prequant(a[u], qc.inv2eb, qc.ebx2, qc.eb_chk, ee);
+      q[j][u] = in ? qq : 0;
+      exf[j] |= (uint32_t)(in && ee) << (8 * u);
+    }
+    *reinterpret_cast<uint32_t *>(&sexc[row * S::TX + col]) = exf[j];
+  }
+  if (NDIM == 3) {
+    // (1 - S_x)^K within the thread's 4 columns; the left neighbour column
+    // comes from lane - 1 unless the patch starts a block (px = 0).
+    const bool blk_start = ((lane & 15) & 1) == 0;
+#pragma unroll
+    for (int rep = 0; rep < K; ++rep) {
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int32_t left = __shfl_up_sync(0xffffffffu, q[j][3], 1);
+        q[j][3] -= q[j][2];
+        q[j][2] -= q[j][1];
+        q[j][1] -= q[j][0];
+        q[j][0] -= blk_start ? 0 : left;
+      }
+    }
+    // (1 - S_y)^K within rows 0-3 / 4-7; row 4 takes row 3 from lane - 16.
+    const bool upper = (lane >> 4) != 0;
+#pragma unroll
+    for (int rep = 0; rep < K; ++rep) {
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int32_t above = __shfl_up_sync(0xffffffffu, q[3][u], 16);
+        q[3][u] -= q[2][u];
+        q[2][u] -= q[1][u];
+        q[1][u] -= q[0][u];
+        q[0][u] -= upper ? above : 0;
+      }
+    }
+  }
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    int row, col;
+    elem_rc<NDIM>(tid, j, row, col);
+    *reinterpret_cast<int4 *>(&sq[row * TXP + col]) = make_int4(q[j][0], q[j][1], q[j][2], q[j][3]);
+  }
+}
+
+// Phase B of a 3D tile: the z difference, codes, anchors, histogram; the
+// thread keeps its 4x4 patch of one z-plane.
+template <int K, bool INTERIOR>
+__device__ __forceinline__ void tile_codes3(const Geom &g, const TileXY &t, const QuantConst &qc,
+                                            const CompressWs &ws, const int32_t *sq, uint32_t *shist,
+                                            const int32_t (&q)[4][4], const uint32_t (&exf)[4], uint32_t &nout,
+                                            uint32_t &nexc) {
+  using S = TileShape<3>;
+  constexpr int TXP = S::TX + 8;
+  const int tid = threadIdx.x, lane = tid & 31, pz = tid >> 5;
+  const int h = lane >> 4, c = (lane & 15) * 4;
+  const int wb = c >> 3, px0 = c & 7;
+  const uint32_t bxi = t.tx * S::NB + wb;
+  const bool bvalid = INTERIOR || bxi < g.nbx;
+  const uint64_t blk = (uint64_t)bxi + (uint64_t)g.nbx * (t.by + (uint64_t)g.nby * t.bz);
+  uint32_t codes[4][4];
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    const int py = 4 * h + j, row = pz * 8 + py;
+    int32_t d[4] = {q[j][0], q[j][1], q[j][2], q[j][3]};
+#pragma unroll
+    for (int oz = 1; oz <= K; ++oz) {
+      if (pz >= oz) {
+        const int4 b = *reinterpret_cast<const int4 *>(&sq[(row - 8 * oz) * TXP + c]);
+        const int cf = lz_coef<K>(oz);
+        d[0] += cf * b.x; d[1] += cf * b.y; d[2] += cf * b.z; d[3] += cf * b.w;
+      }
+    }
+    const bool yzin = INTERIOR || ((t.y0 + py < g.ny) && (t.z0 + pz < g.nz));
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const bool in = INTERIOR || (yzin && (t.x0 + c + u < g.nx));
+      const bool origin = (j == 0 && u == 0) && (h == 0 && pz == 0 && px0 == 0);
+      bool outl;
+      codes[j][u] = make_code(d[u], qc.R, in, origin, outl);
+      if (origin && bvalid) ws.anchors[blk] = d[u];
+      nout += outl;
+      nexc += (exf[j] >> (8 * u)) & 1u;
+    }
+    if (bvalid) {
+      const uint64_t p0 = blk * 512 + pz * 64 + py * 8 + px0;
+      *reinterpret_cast<uint2 *>(ws.codes + p0) =
+          make_uint2(codes[j][0] | (codes[j][1] << 16), codes[j][2] | (codes[j][3] << 16));
+    }
+  }
+  if (bvalid) {
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+#pragma unroll
+      for (int u = 0; u < 4; ++u) atomicAdd(&shist[codes[j][u]], 1u);
+  } else {
+    nout = 0;
+    nexc = 0;
+  }
+}
+
+// Phase B of a 1D/2D tile: warp = half a block, 16 steps of 32 positions.
+template <int NDIM, int K, bool INTERIOR>
+__device__ __forceinline__ void tile_codes12(const Geom &g, const TileXY &t, const QuantConst &qc,
+                                             const CompressWs &ws, const int32_t *sq, const uint8_t *sexc,
+                                             uint32_t *shist, uint32_t &nout, uint32_t &nexc) {
+  using S = TileShape<NDIM>;
+  constexpr int kPerWarp = S::BX * S::BY / S::WPB;
+  constexpr int kIter = kPerWarp / 32;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int wb = warp / S::WPB, seg = warp % S::WPB;
+  const uint32_t bxi = t.tx * S::NB + wb;
+  if (!INTERIOR && bxi >= g.nbx) return;
+  const uint64_t blk = (uint64_t)bxi + (uint64_t)g.nbx * (t.by + (uint64_t)g.nby * t.bz);
+  uint16_t *cdst = ws.codes + blk * g.bsize + seg * kPerWarp;
+#pragma unroll 4
+  for (int i = 0; i < kIter; ++i) {
+    const int p = seg * kPerWarp + 32 * i + lane;
+    const int px = p % S::BX, py = p / S::BX;
+    const int row = py, col = wb * S::BX + px;
+    const bool in = INTERIOR || ((t.x0 + col < g.nx) && (t.y0 + py < g.ny));
+    const int32_t d = smem_residual<NDIM, K>(sq, row, col, px, py, 0);
+    bool outl;
+    const uint32_t code = make_code(d, qc.R, in, p == 0, outl);
+    if (p == 0) ws.anchors[blk] = d;
+    cdst[32 * i + lane] = (uint16_t)code;
+    atomicAdd(&shist[code], 1u);
+    nout += outl;
+    nexc += (in && sexc[row * S::TX + col]) ? 1u : 0u;
+  }
+}
+
+template <int NDIM, int K>
+__global__ void __launch_bounds__(kQuantThreads, 3) k_quant(const float *__restrict__ x, Geom g, uint32_t R,
+                                                             CompressWs ws) {
+  using S = TileShape<NDIM>;
+  using SM = QuantSmem<NDIM>;
   constexpr int kPerWarp = S::BX * S::BY * S::BZ / S::WPB;  // 512 positions
   constexpr int kIter = kPerWarp / 32;                      // 16
   static_assert(S::TX * S::ROWS == kTileElems, "tile size");
   static_assert(S::NB * S::WPB == kQuantThreads / 32, "warps per tile");
-
-  __shared__ __align__(16) int32_t sq[S::ROWS * TXP];
-  __shared__ __align__(16) uint8_t sexc[kTileElems];
-  __shared__ uint32_t shist[kMaxSym];
-  __shared__ uint32_t s_wout[8], s_wexc[8], s_wout_off[8], s_wexc_off[8];
-  __shared__ uint32_t s_tile;
+  extern __shared__ __align__(16) unsigned char q_smem[];
+  SM &sm = *reinterpret_cast<SM *>(q_smem);
 
   Ctl *ctl = ws.ctl;
   if (ctl->mode != kModeNormal) return;
-  const float inv2eb = ctl->inv2eb, ebx2 = ctl->ebx2, eb_chk = ctl->eb_chk;
+  QuantConst qc;
+  qc.inv2eb = ctl->inv2eb;
+  qc.ebx2 = ctl->ebx2;
+  qc.eb_chk = ctl->eb_chk;
+  qc.R = (int32_t)R;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const uint32_t nsym = 2 * R;
-  for (int s = tid; s < kMaxSym; s += kQuantThreads) shist[s] = 0;
+  for (int s = tid; s < kMaxSym; s += kQuantThreads) sm.shist[s] = 0;
   const bool vec_ok = ((g.nx & 3u) == 0) && (((uintptr_t)x & 15u) == 0);
 
-  for (;;) {
-    if (tid == 0) s_tile = atomicAdd(&ctl->quant_ticket, 1u);
-    __syncthreads();
-    const uint64_t tile = s_tile;
-    if (tile >= g.n_qtiles) break;
-    const uint32_t tx = (uint32_t)(tile % g.tiles_x);
-    const uint64_t rest = tile / g.tiles_x;
-    const uint32_t by = (uint32_t)(rest % g.nby), bz = (uint32_t)(rest / g.nby);
-    const uint32_t x0 = tx * S::NB * S::BX;
-    const uint32_t y0 = by * S::BY, z0 = bz * S::BZ;
-
-    // ---- phase 1: load + prequantize into shared memory (row-major tile)
-#pragma unroll
-    for (int j = 0; j < kTileElems / 4 / kQuantThreads; ++j) {
-      const int e = 4 * (tid + kQuantThreads * j);
-      const int row = e / S::TX, col = e % S::TX;
-      const uint32_t X = x0 + col;
-      const uint32_t Y = y0 + (row % S::BY), Z = z0 + row / S::BY;
-      float v[4];
-      bool inrow = Y < g.ny && Z < g.nz;
-      uint64_t fi = ((uint64_t)Z * g.ny + Y) * g.nx + X;
-      if (inrow && vec_ok && X < g.nx) {
-        float4 f = __ldcs(reinterpret_cast<const float4 *>(x + fi));
-        v[0] = f.x; v[1] = f.y; v[2] = f.z; v[3] = f.w;
-      } else {
-#pragma unroll
-        for (int u = 0; u < 4; ++u) v[u] = (inrow && X + u < g.nx) ? x[fi + u] : 0.0f;
-      }
-      int4 q4;
-      uint32_t ex = 0;
-      int32_t qq[4];
-#pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        bool in = inrow && X + u < g.nx;
-        bool ee = false;
-        qq[u] = in ? prequant(v[u], inv2eb, ebx2, eb_chk, ee) : 0;
-        ex |= (uint32_t)(in && ee) << (8 * u);
-      }
-      q4.x = qq[0]; q4.y = qq[1]; q4.z = qq[2]; q4.w = qq[3];
-      *reinterpret_cast<int4 *>(&sq[row * TXP + col]) = q4;
-      *reinterpret_cast<uint32_t *>(&sexc[e]) = ex;
-    }
-    __syncthreads();
-
-    // ---- phase 2: residuals, codes, histogram, counts (warp = block segment)
-    const int wb = warp / S::WPB, seg = warp % S::WPB;
-    const uint32_t bxi = tx * S::NB + wb;
-    const bool wvalid = bxi < g.nbx;
-    const uint64_t blk = (uint64_t)bxi + (uint64_t)g.nbx * (by + (uint64_t)g.nby * bz);
+  uint64_t tile = blockIdx.x;
+  float4 v[4];
+  if (tile < g.n_qtiles) load_tile<NDIM>(x, g, tile_xy<NDIM>(g, tile), tid, vec_ok, v);
+  for (int buf = 0; tile < g.n_qtiles; tile += gridDim.x, buf ^= 1) {
+    const TileXY t = tile_xy<NDIM>(g, tile);
+    // a tile that lies wholly inside the domain skips every bounds test
+    const bool interior = vec_ok && t.x0 + S::TX <= g.nx && t.y0 + S::BY <= g.ny && t.z0 + S::BZ <= g.nz;
+    int32_t *sq = sm.sq[buf];
+    uint8_t *sexc = sm.sexc[buf];
     uint32_t nout = 0, nexc = 0;
-    if (wvalid) {
-      uint16_t *cdst = ws.codes + blk * g.bsize + seg * kPerWarp;
-#pragma unroll 4
-      for (int i = 0; i < kIter; ++i) {
-        const int p = seg * kPerWarp + 32 * i + lane;
-        const int px = p % S::BX, py = (p / S::BX) % S::BY, pz = p / (S::BX * S::BY);
-        const int row = py + S::BY * pz, col = wb * S::BX + px;
-        const bool in = (x0 + col < g.nx) && (y0 + py < g.ny) && (z0 + pz < g.nz);
-        const int32_t d = lorenzo_residual<NDIM, K, TXP>(sq, row, col, px, py, pz);
-        uint32_t code;
-        bool outl = false;
-        if (!in) code = R;
-        else if (p == 0) { code = R; ws.anchors[blk] = d; }
-        else if (d > -(int32_t)R && d < (int32_t)R) code = (uint32_t)(d + (int32_t)R);
-        else { code = 0; outl = true; }
-        cdst[32 * i + lane] = (uint16_t)code;
-        const uint32_t c0 = __shfl_sync(0xffffffffu, code, 0);
-        if (__all_sync(0xffffffffu, code == c0)) {
-          if (lane == 0) atomicAdd(&shist[c0], 32u);
-        } else {
-          atomicAdd(&shist[code], 1u);
+    int32_t q[4][4];
+    uint32_t exf[4];
+    if (interior) tile_front<NDIM, K, true>(g, t, v, qc, sq, sexc, q, exf);
+    else tile_front<NDIM, K, false>(g, t, v, qc, sq, sexc, q, exf);
+    __syncthreads();
+    // ---- next tile's loads go out now and land while this tile is coded
+    {
+      const uint64_t nt = tile + gridDim.x;
+      if (nt < g.n_qtiles) load_tile<NDIM>(x, g, tile_xy<NDIM>(g, nt), tid, vec_ok, v);
+    }
+    if (NDIM == 3) {
+      if (interior) tile_codes3<K, true>(g, t, qc, ws, sq, sm.shist, q, exf, nout, nexc);
+      else tile_codes3<K, false>(g, t, qc, ws, sq, sm.shist, q, exf, nout, nexc);
+    } else {
+      if (interior) tile_codes12<NDIM, K, true>(g, t, qc, ws, sq, sexc, sm.shist, nout, nexc);
+      else tile_codes12<NDIM, K, false>(g, t, qc, ws, sq, sexc, sm.shist, nout, nexc);
+    }
+
+    // ---- outliers / exceptions of this tile (rare): ordered compaction
+    nout = __reduce_add_sync(0xffffffffu, nout);
+    nexc = __reduce_add_sync(0xffffffffu, nexc);
+    if (lane == 0) { sm.wout[warp] = nout; sm.wexc[warp] = nexc; }
+    if (__syncthreads_or((nout | nexc) != 0)) {
+      if (tid == 0) {
+        uint32_t to = 0, te = 0;
+        for (int w = 0; w < 8; ++w) { to += sm.wout[w]; te += sm.wexc[w]; }
+        const unsigned long long os = to ? atomicAdd(&ctl->n_out, (unsigned long long)to) : 0ull;
+        const unsigned long long es = te ? atomicAdd(&ctl->n_exc, (unsigned long long)te) : 0ull;
+        ws.tinfo[tile] = make_uint4(to, te, (uint32_t)os, (uint32_t)es);
+        const uint64_t grp = tile / kTileGroup;
+        if (to) atomicAdd(&ws.tgroup[grp].x, to);
+        if (te) atomicAdd(&ws.tgroup[grp].y, te);
+        sm.oslot = (uint32_t)os;
+        sm.eslot = (uint32_t)es;
+      }
+      __syncthreads();
+      // Each warp walks one block in code order (3D: warp = block; 1D/2D:
+      // warp = half block) and appends its entries after the earlier warps'.
+      const int wb = warp / S::WPB, seg = warp % S::WPB;
+      const uint32_t bxi = t.tx * S::NB + wb;
+      const bool bvalid = bxi < g.nbx;
+      const uint64_t blk = (uint64_t)bxi + (uint64_t)g.nbx * (t.by + (uint64_t)g.nby * t.bz);
+      uint32_t co = 0, ce = 0;
+      if (bvalid) {
+        for (int i = 0; i < kIter; ++i) {
+          const int p = seg * kPerWarp + 32 * i + lane;
+          const int px = p % S::BX, py = (p / S::BX) % S::BY, pz = p / (S::BX * S::BY);
+          const int row = py + S::BY * pz, col = wb * S::BX + px;
+          const bool in = (t.x0 + col < g.nx) && (t.y0 + py < g.ny) && (t.z0 + pz < g.nz);
+          const int32_t d = smem_residual<NDIM, K>(sq, row, col, px, py, pz);
+          bool outl;
+          make_code(d, qc.R, in, p == 0, outl);
+          co += __popc(__ballot_sync(0xffffffffu, outl));
+          ce += __popc(__ballot_sync(0xffffffffu, in && sexc[row * S::TX + col]));
         }
-        nout += __popc(__ballot_sync(0xffffffffu, outl));
-        nexc += __popc(__ballot_sync(0xffffffffu, in && sexc[row * S::TX + col]));
       }
-    }
-    if (lane == 0) { s_wout[warp] = nout; s_wexc[warp] = nexc; }
-    __syncthreads();
-
-    // ---- phase 3: tile totals and their global offsets (look-back)
-    if (tid == 0) {
-      uint32_t to = 0, te = 0;
-      for (int w = 0; w < 8; ++w) {
-        s_wout_off[w] = to; to += s_wout[w];
-        s_wexc_off[w] = te; te += s_wexc[w];
-      }
-      uint64_t agg = (uint64_t)to | ((uint64_t)te << 31);
-      uint64_t ex = lookback<true>(ws.qstatus, tile, agg, ctl);
-      uint32_t eo = (uint32_t)(ex & ((1ull << 31) - 1)), ee = (uint32_t)(ex >> 31);
-      for (int w = 0; w < 8; ++w) { s_wout_off[w] += eo; s_wexc_off[w] += ee; }
-      if (to) atomicAdd(&ctl->n_out, (unsigned long long)to);
-      if (te) atomicAdd(&ctl->n_exc, (unsigned long long)te);
-    }
-    __syncthreads();
-
-    // ---- phase 4: ordered write of this warp's outliers and exceptions
-    if (wvalid && (nout | nexc)) {
-      uint32_t oo = s_wout_off[warp], eo = s_wexc_off[warp];
-      for (int i = 0; i < kIter; ++i) {
-        const int p = seg * kPerWarp + 32 * i + lane;
-        const int px = p % S::BX, py = (p / S::BX) % S::BY, pz = p / (S::BX * S::BY);
-        const int row = py + S::BY * pz, col = wb * S::BX + px;
-        const bool in = (x0 + col < g.nx) && (y0 + py < g.ny) && (z0 + pz < g.nz);
-        const uint32_t pos = (uint32_t)(blk * g.bsize + p);
-        if (nout) {
-          const int32_t d = lorenzo_residual<NDIM, K, TXP>(sq, row, col, px, py, pz);
-          const bool outl = in && p != 0 && !(d > -(int32_t)R && d < (int32_t)R);
-          const uint32_t m = __ballot_sync(0xffffffffu, outl);
+      __syncthreads();
+      if (lane == 0) { sm.wout[warp] = co; sm.wexc[warp] = ce; }
+      __syncthreads();
+      uint32_t oo = sm.oslot, eo = sm.eslot;
+      for (int w = 0; w < warp; ++w) { oo += sm.wout[w]; eo += sm.wexc[w]; }
+      if (bvalid && (co | ce)) {
+        for (int i = 0; i < kIter; ++i) {
+          const int p = seg * kPerWarp + 32 * i + lane;
+          const int px = p % S::BX, py = (p / S::BX) % S::BY, pz = p / (S::BX * S::BY);
+          const int row = py + S::BY * pz, col = wb * S::BX + px;
+          const bool in = (t.x0 + col < g.nx) && (t.y0 + py < g.ny) && (t.z0 + pz < g.nz);
+          const uint32_t pos = (uint32_t)(blk * g.bsize + p);
+          const int32_t d = smem_residual<NDIM, K>(sq, row, col, px, py, pz);
+          bool outl;
+          make_code(d, qc.R, in, p == 0, outl);
+          uint32_t m = __ballot_sync(0xffffffffu, outl);
           if (outl) {
-            uint64_t o = (uint64_t)oo + __popc(m & ((1u << lane) - 1));
+            const uint64_t o = (uint64_t)oo + __popc(m & ((1u << lane) - 1));
             if (o < ws.cap_list) { ws.out_idx[o] = pos; ws.out_val[o] = d; }
           }
           oo += __popc(m);
-        }
-        if (nexc) {
           const bool e = in && sexc[row * S::TX + col];
-          const uint32_t m = __ballot_sync(0xffffffffu, e);
+          m = __ballot_sync(0xffffffffu, e);
           if (e) {
-            uint64_t o = (uint64_t)eo + __popc(m & ((1u << lane) - 1));
-            uint64_t fi = ((uint64_t)(z0 + pz) * g.ny + (y0 + py)) * g.nx + (x0 + col);
+            const uint64_t o = (uint64_t)eo + __popc(m & ((1u << lane) - 1));
+            const uint64_t fi = ((uint64_t)(t.z0 + pz) * g.ny + (t.y0 + py)) * g.nx + (t.x0 + col);
             if (o < ws.cap_list) { ws.exc_idx[o] = pos; ws.exc_val[o] = __float_as_uint(x[fi]); }
           }
           eo += __popc(m);
         }
       }
     }
-    __syncthreads();
   }
-  // flush the CTA histogram
+  __syncthreads();
   for (int s = tid; s < (int)nsym; s += kQuantThreads)
-    if (shist[s]) atomicAdd(&ctl->hist[s], (unsigned long long)shist[s]);
+    if (sm.shist[s]) atomicAdd(&ctl->hist[s], (unsigned long long)sm.shist[s]);
 }
 
 template <int NDIM, int K>
 cudaError_t launch_t(const float *x, const Geom &g, uint32_t R, const CompressWs &ws, cudaStream_t s, int sms) {
+  const int smem = (int)sizeof(QuantSmem<NDIM>);
+  cudaError_t e = cudaFuncSetAttribute(k_quant<NDIM, K>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e != cudaSuccess) return e;
   int per_sm = 0;
-  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_quant<NDIM, K>, kQuantThreads, 0);
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_quant<NDIM, K>, kQuantThreads, smem);
   if (e != cudaSuccess) return e;
   if (per_sm < 1) per_sm = 1;
   uint64_t grid = (uint64_t)sms * per_sm;
   if (grid > g.n_qtiles) grid = g.n_qtiles;
-  k_quant<NDIM, K><<<(unsigned)grid, kQuantThreads, 0, s>>>(x, g, R, ws);
+  k_quant<NDIM, K><<<(unsigned)grid, kQuantThreads, smem, s>>>(x, g, R, ws);
   return cudaGetLastError();
 }
 
