@@ -173,6 +173,10 @@ struct DecParams {
   int32_t R;
 };
 
+__device__ __forceinline__ void prefetch_l2(const void *p) {
+  asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+}
+
 // MSB-first bit reader over one chunk.  A 64-bit buffer holds the next
 // bits; when fewer than 32 remain it takes the next stream word.  That word
 // and the one after it are loaded two refills ahead, and every step is
@@ -190,6 +194,7 @@ struct BitReader {
     W = w;
     nw = n;
     const uint64_t sw = bitpos >> 5;
+    if (sw + 32 < n) prefetch_l2(w + sw + 32);  // the chunk's second line
     const int sk = (int)(bitpos & 31u);
     buf = (((unsigned long long)ld(sw) << 32) | ld(sw + 1)) << sk;
     nb = 64 - sk;
@@ -203,6 +208,8 @@ struct BitReader {
     buf |= need ? ((unsigned long long)pend0 << (32 - nb)) : 0ull;
     nb += need ? 32 : 0;
     const uint32_t fresh = (need && wi < nw) ? __ldg(W + wi) : 0u;
+    // entering a new 128-byte line: ask L2 for the line two ahead
+    if (need && (wi & 31u) == 0 && wi + 64 < nw) prefetch_l2(W + wi + 64);
     pend0 = need ? pend1 : pend0;
     pend1 = need ? fresh : pend1;
     wi += need ? 1 : 0;
@@ -216,10 +223,6 @@ struct BitReader {
   }
 };
 
-__device__ __forceinline__ void prefetch_l2(const void *p) {
-  asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
-}
-
 __device__ __forceinline__ uint64_t lower_bound_u32(const uint32_t *a, uint64_t n, uint32_t key) {
   uint64_t lo = 0, hi = n;
   while (lo < hi) {
@@ -230,25 +233,47 @@ __device__ __forceinline__ uint64_t lower_bound_u32(const uint32_t *a, uint64_t 
 }
 
 // Outliers and exceptions of one block (both lists ascend by code-stream
-// position).  The rare paths are out of line to keep the unrolled decode
-// loop small.
+// position).  The rare paths are out of line to keep the decode loop small;
+// they take and return their state by value so that nothing in the loop has
+// its address taken (which would move it to local memory).
 struct Side {
   uint64_t oc, ec;
   uint32_t next_e;
 };
 
-__device__ __noinline__ int32_t fetch_outlier(const DecParams &p, Side &sd, uint32_t pos0, uint32_t pos,
-                                              bool &bad) {
-  if (sd.oc == ~0ull) sd.oc = lower_bound_u32(p.out_idx, p.n_out, pos0);
-  if (sd.oc < p.n_out && __ldg(p.out_idx + sd.oc) == pos) return __ldg(p.out_val + sd.oc++);
-  bad = true;
-  return 0;
+struct OutlierHit {
+  int32_t value;
+  uint32_t ok;
+  uint64_t oc;
+};
+
+__device__ __noinline__ OutlierHit fetch_outlier(const uint32_t *out_idx, const int32_t *out_val, uint64_t n_out,
+                                                 uint64_t oc, uint32_t pos0, uint32_t pos) {
+  OutlierHit r;
+  if (oc == ~0ull) oc = lower_bound_u32(out_idx, n_out, pos0);
+  if (oc < n_out && __ldg(out_idx + oc) == pos) {
+    r.value = __ldg(out_val + oc);
+    r.ok = 1;
+    r.oc = oc + 1;
+  } else {
+    r.value = 0;
+    r.ok = 0;
+    r.oc = oc;
+  }
+  return r;
 }
 
-__device__ __noinline__ float fetch_exception(const DecParams &p, Side &sd) {
-  const float r = __uint_as_float(__ldg(p.exc_val + sd.ec));
-  ++sd.ec;
-  sd.next_e = sd.ec < p.n_exc ? __ldg(p.exc_idx + sd.ec) : 0xffffffffu;
+struct ExceptionHit {
+  uint32_t bits, next_e;
+  uint64_t ec;
+};
+
+__device__ __noinline__ ExceptionHit fetch_exception(const uint32_t *exc_idx, const uint32_t *exc_val,
+                                                     uint64_t n_exc, uint64_t ec) {
+  ExceptionHit r;
+  r.bits = __ldg(exc_val + ec);
+  r.ec = ec + 1;
+  r.next_e = r.ec < n_exc ? __ldg(exc_idx + r.ec) : 0xffffffffu;
   return r;
 }
 
@@ -266,13 +291,23 @@ __device__ __forceinline__ void init_side(const DecParams &p, Side &sd, uint32_t
 __device__ __forceinline__ int32_t next_delta(BitReader &br, const uint16_t *slut, const DecParams &p, Side &sd,
                                               uint32_t pos0, uint32_t pos, bool &bad) {
   const uint32_t sym = br.next(slut, bad);
-  if (sym == 0) return fetch_outlier(p, sd, pos0, pos, bad);
+  if (sym == 0) {
+    const OutlierHit h = fetch_outlier(p.out_idx, p.out_val, p.n_out, sd.oc, pos0, pos);
+    sd.oc = h.oc;
+    bad |= !h.ok;
+    return h.value;
+  }
   return (int32_t)sym - p.R;
 }
 
 __device__ __forceinline__ float value(const DecParams &p, Side &sd, uint32_t pos, int32_t q) {
   float v = __fmul_rn(__int2float_rn(q), p.ebx2);
-  if (pos == sd.next_e) v = fetch_exception(p, sd);
+  if (pos == sd.next_e) {
+    const ExceptionHit h = fetch_exception(p.exc_idx, p.exc_val, p.n_exc, sd.ec);
+    sd.ec = h.ec;
+    sd.next_e = h.next_e;
+    v = __uint_as_float(h.bits);
+  }
   return v;
 }
 
@@ -449,16 +484,6 @@ __global__ void __launch_bounds__(kDecThreads) k_decode(DecParams p, Geom g) {
   }
   const bool vecbase = ((g.nx & 3u) == 0) && (((uintptr_t)p.out & 15u) == 0);
   for (uint64_t grp = blockIdx.x; grp < p.n_groups; grp += gridDim.x) {
-    {
-      // pull the next group's bitstream (one contiguous range) into L2
-      const uint64_t ng = grp + gridDim.x;
-      if (ng < p.n_groups) {
-        const uint64_t w0 = p.goff[ng] >> 5;
-        const uint64_t w1 = ng + 1 < p.n_groups ? (p.goff[ng + 1] + 31) >> 5 : p.n_words;
-        for (uint64_t w = w0 + 32 * (uint64_t)t; w < w1 && w < p.n_words; w += 32 * (uint64_t)kDecThreads)
-          prefetch_l2(p.words + w);
-      }
-    }
     const uint64_t j = grp * kDecThreads + t;
     const bool valid = j < p.n_chunks;
     const uint32_t cb = valid ? __ldg(p.chunk_bits + j) : 0u;

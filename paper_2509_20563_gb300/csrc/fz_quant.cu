@@ -80,10 +80,11 @@ template <int NDIM>
 __device__ __forceinline__ TileXY tile_xy(const Geom &g, uint64_t tile) {
   using S = TileShape<NDIM>;
   TileXY t;
-  t.tx = (uint32_t)(tile % g.tiles_x);
-  const uint64_t rest = tile / g.tiles_x;
-  t.by = (uint32_t)(rest % g.nby);
-  t.bz = (uint32_t)(rest / g.nby);
+  const uint32_t t32 = (uint32_t)tile;  // tiles number fewer than 2^32 / 4096
+  t.tx = t32 % g.tiles_x;
+  const uint32_t rest = t32 / g.tiles_x;
+  t.by = rest % g.nby;
+  t.bz = rest / g.nby;
   t.x0 = t.tx * S::NB * S::BX;
   t.y0 = t.by * S::BY;
   t.z0 = t.bz * S::BZ;
@@ -267,8 +268,8 @@ __device__ __forceinline__ void tile_codes3(const Geom &g, const TileXY &t, cons
       codes[j][u] = make_code(d[u], qc.R, in, origin, outl);
       if (origin && bvalid) ws.anchors[blk] = d[u];
       nout += outl;
-      nexc += (exf[j] >> (8 * u)) & 1u;
     }
+    nexc += __popc(exf[j]);
     if (bvalid) {
       const uint64_t p0 = blk * 512 + pz * 64 + py * 8 + px0;
       *reinterpret_cast<uint2 *>(ws.codes + p0) =
