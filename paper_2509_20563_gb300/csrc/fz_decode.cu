@@ -177,49 +177,70 @@ __device__ __forceinline__ void prefetch_l2(const void *p) {
   asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
 }
 
-// MSB-first bit reader over one chunk.  A 64-bit buffer holds the next
-// bits; when fewer than 32 remain it takes the next stream word.  That word
-// and the one after it are loaded two refills ahead, and every step is
-// predicated rather than branched, so lanes that consume bits at different
-// rates never diverge.
+__device__ __forceinline__ void cp_async4(uint32_t *dst_smem, const uint32_t *src, bool valid) {
+  const uint32_t d = (uint32_t)__cvta_generic_to_shared(dst_smem);
+  const int n = valid ? 4 : 0;  // zero-fill past the end of the bitstream
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(d), "l"(src), "r"(n) : "memory");
+  asm volatile("cp.async.commit_group;\n" ::: "memory");
+}
+__device__ __forceinline__ void cp_async_wait3() { asm volatile("cp.async.wait_group 3;\n" ::: "memory"); }
+
+constexpr int kRing = 4;  // stream words in flight per thread
+
+// MSB-first bit reader over one chunk, all 32-bit: a window of two stream
+// words (a, b) and a bit offset into a; the next 32 bits are one funnel shift
+// away.  When the offset passes 32 the window slides by a word.  The words
+// ahead of the window wait in a per-thread ring in shared memory, filled by
+// asynchronous copies issued four slides early, so a slide never waits on
+// memory and no register is ever read while its load is in flight.  Words
+// past the end of the bitstream read as zero.
 struct BitReader {
-  const uint32_t *W;
-  uint64_t nw, wi;  // words available; index of the word after pend1
-  uint32_t pend0, pend1;
-  unsigned long long buf;
-  int nb;
-  uint32_t used;
-  __device__ __forceinline__ uint32_t ld(uint64_t i) const { return i < nw ? __ldg(W + i) : 0u; }
-  __device__ __forceinline__ void init(const uint32_t *w, uint64_t n, uint64_t bitpos) {
-    W = w;
-    nw = n;
+  const uint32_t *W;   // the chunk's first word
+  uint32_t nw;         // words from W to the end of the bitstream
+  uint32_t wi;         // next word to fetch into the ring, relative to W
+  uint32_t *ring;      // this thread's ring: ring[k * kDecThreads]
+  uint32_t rd;         // next ring slot to read
+  uint32_t a, b;
+  uint32_t off;        // bits of a already consumed (0..31)
+  uint32_t vall;       // AND of all table entries used (valid bit check)
+  __device__ __forceinline__ uint32_t ld(uint32_t i) const { return i < nw ? __ldg(W + i) : 0u; }
+  __device__ __forceinline__ void init(const uint32_t *words, uint64_t n_words, uint64_t bitpos, uint32_t bits,
+                                       uint32_t *ring_col) {
     const uint64_t sw = bitpos >> 5;
-    if (sw + 32 < n) prefetch_l2(w + sw + 32);  // the chunk's second line
-    const int sk = (int)(bitpos & 31u);
-    buf = (((unsigned long long)ld(sw) << 32) | ld(sw + 1)) << sk;
-    nb = 64 - sk;
-    pend0 = ld(sw + 2);
-    pend1 = ld(sw + 3);
-    wi = sw + 4;
-    used = 0;
+    W = words + sw;
+    nw = (uint32_t)(n_words > sw ? (n_words - sw < 0xffffffffull ? n_words - sw : 0xffffffffull) : 0);
+    off = (uint32_t)(bitpos & 31u);
+    ring = ring_col;
+    a = ld(0);
+    b = ld(1);
+#pragma unroll
+    for (int k = 0; k < kRing; ++k) cp_async4(ring + k * kDecThreads, W + (2 + k < nw ? 2 + k : 0), 2 + k < nw);
+    wi = 2 + kRing;
+    rd = 0;
+    vall = 0xffffffffu;
+    // the whole chunk (a few 128-byte lines) is pulled into L2 up front
+    const uint32_t cw = (off + bits + 31) / 32 + 2;
+    for (uint32_t i = 32; i < cw && i < nw; i += 32) prefetch_l2(W + i);
   }
-  __device__ __forceinline__ uint32_t next(const uint16_t *slut, bool &bad) {
-    const bool need = nb < 32;
-    buf |= need ? ((unsigned long long)pend0 << (32 - nb)) : 0ull;
-    nb += need ? 32 : 0;
-    const uint32_t fresh = (need && wi < nw) ? __ldg(W + wi) : 0u;
-    // entering a new 128-byte line: ask L2 for the line two ahead
-    if (need && (wi & 31u) == 0 && wi + 64 < nw) prefetch_l2(W + wi + 64);
-    pend0 = need ? pend1 : pend0;
-    pend1 = need ? fresh : pend1;
-    wi += need ? 1 : 0;
-    const uint32_t e = slut[buf >> (64 - kLutBits)];
-    const uint32_t L = ((e >> 10) & 15u) + 1u;
-    bad |= !(e & kLutValid);
-    buf <<= L;
-    nb -= (int)L;
-    used += L;
+  __device__ __forceinline__ uint32_t next(const uint16_t *slut) {
+    const uint32_t win = __funnelshift_l(b, a, off);
+    const uint32_t e = slut[win >> (32 - kLutBits)];
+    vall &= e;
+    off += ((e >> 10) & 15u) + 1u;
+    if (off >= 32) {
+      off -= 32;
+      cp_async_wait3();
+      a = b;
+      b = ring[rd * kDecThreads];
+      cp_async4(ring + rd * kDecThreads, W + (wi < nw ? wi : 0), wi < nw);
+      rd = (rd + 1) & (kRing - 1);
+      ++wi;
+    }
     return e & 1023u;
+  }
+  // bits consumed since init, given the starting offset
+  __device__ __forceinline__ uint32_t consumed(uint32_t start_off) const {
+    return (wi - 2 - kRing) * 32 + off - start_off;
   }
 };
 
@@ -290,7 +311,7 @@ __device__ __forceinline__ void init_side(const DecParams &p, Side &sd, uint32_t
 // Residual of the next symbol: code - R, or the stored outlier for code 0.
 __device__ __forceinline__ int32_t next_delta(BitReader &br, const uint16_t *slut, const DecParams &p, Side &sd,
                                               uint32_t pos0, uint32_t pos, bool &bad) {
-  const uint32_t sym = br.next(slut, bad);
+  const uint32_t sym = br.next(slut);
   if (sym == 0) {
     const OutlierHit h = fetch_outlier(p.out_idx, p.out_val, p.n_out, sd.oc, pos0, pos);
     sd.oc = h.oc;
@@ -300,9 +321,10 @@ __device__ __forceinline__ int32_t next_delta(BitReader &br, const uint16_t *slu
   return (int32_t)sym - p.R;
 }
 
+template <bool EXC>
 __device__ __forceinline__ float value(const DecParams &p, Side &sd, uint32_t pos, int32_t q) {
   float v = __fmul_rn(__int2float_rn(q), p.ebx2);
-  if (pos == sd.next_e) {
+  if (EXC && pos == sd.next_e) {
     const ExceptionHit h = fetch_exception(p.exc_idx, p.exc_val, p.n_exc, sd.ec);
     sd.ec = h.ec;
     sd.next_e = h.next_e;
@@ -330,16 +352,19 @@ struct DecState {
 
 template <int NDIM, int K>
 constexpr size_t dec_smem_bytes() {
-  return sizeof(uint16_t) * kLutSize + sizeof(int32_t) * (size_t)DecState<NDIM, K>::kWords * kDecThreads;
+  return sizeof(uint16_t) * kLutSize +
+         sizeof(int32_t) * (size_t)(DecState<NDIM, K>::kWords + kRing) * kDecThreads;
 }
 
-template <int NDIM, int K>
+template <int NDIM, int K, bool EXC>
 __device__ __forceinline__ void decode_chunk(const DecParams &p, const Geom &g, const uint16_t *slut,
-                                             int32_t *st, uint64_t j, uint64_t start, bool vecbase) {
+                                             int32_t *st, uint32_t *ring, uint64_t j, uint64_t start, bool vecbase) {
   constexpr int T = kDecThreads;
   bool bad = false;
   BitReader br;
-  br.init(p.words, p.n_words, start);
+  const uint32_t cbits = __ldg(p.chunk_bits + j);
+  br.init(p.words, p.n_words, start, cbits, ring);
+  const uint32_t start_off = br.off;
   const uint32_t pos0 = (uint32_t)(j * g.bsize);
   Side sd;
   init_side(p, sd, pos0);
@@ -381,7 +406,7 @@ __device__ __forceinline__ void decode_chunk(const DecParams &p, const Geom &g, 
             q = row[(64 + x) * T] + p1;
             row[(64 + x) * T] = q;
           }
-          o[x] = value(p, sd, pos, q);
+          o[x] = value<EXC>(p, sd, pos, q);
         }
         if (zin && Y0 + y < g.ny) {
           const uint64_t f = ((uint64_t)(Z0 + z) * g.ny + (Y0 + y)) * g.nx + X0;
@@ -425,7 +450,7 @@ __device__ __forceinline__ void decode_chunk(const DecParams &p, const Geom &g, 
             q = col[(32 + u) * T] + y1;
             col[(32 + u) * T] = q;
           }
-          o[u] = value(p, sd, pos, q);
+          o[u] = value<EXC>(p, sd, pos, q);
         }
         if (yin) {
           const uint64_t fx = f + 8 * x8;
@@ -455,7 +480,7 @@ __device__ __forceinline__ void decode_chunk(const DecParams &p, const Geom &g, 
         int32_t q;
         if (K == 1) { r1 += d; q = r1; }
         else { r1 += d; r2 += r1; q = r2; }
-        o[u] = value(p, sd, pos, q);
+        o[u] = value<EXC>(p, sd, pos, q);
       }
       if (full) {
         store4(p.out, f0 + 8 * x8, vecbase, o);
@@ -467,7 +492,9 @@ __device__ __forceinline__ void decode_chunk(const DecParams &p, const Geom &g, 
       }
     }
   }
-  if (br.used != __ldg(p.chunk_bits + j) || bad) dec_err(p.err, FZ_ECORRUPT);
+  asm volatile("cp.async.wait_all;\n" ::: "memory");  // the ring is reused by the next chunk
+  if (br.consumed(start_off) != cbits || bad || !(br.vall & kLutValid))
+    dec_err(p.err, FZ_ECORRUPT);
 }
 
 template <int NDIM, int K>
@@ -475,6 +502,7 @@ __global__ void __launch_bounds__(kDecThreads) k_decode(DecParams p, Geom g) {
   extern __shared__ __align__(16) unsigned char d_smem[];
   uint16_t *slut = reinterpret_cast<uint16_t *>(d_smem);
   int32_t *sstate = reinterpret_cast<int32_t *>(d_smem + sizeof(uint16_t) * kLutSize);
+  uint32_t *sring = reinterpret_cast<uint32_t *>(sstate + DecState<NDIM, K>::kWords * kDecThreads);
   __shared__ unsigned long long swarp[kDecThreads / 32];
   const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
   {
@@ -498,7 +526,10 @@ __global__ void __launch_bounds__(kDecThreads) k_decode(DecParams p, Geom g) {
     __syncthreads();
     unsigned long long start = p.goff[grp] + incl - cb;
     for (int w = 0; w < warp; ++w) start += swarp[w];
-    if (valid) decode_chunk<NDIM, K>(p, g, slut, sstate + t, j, start, vecbase);
+    if (valid) {
+      if (p.n_exc) decode_chunk<NDIM, K, true>(p, g, slut, sstate + t, sring + t, j, start, vecbase);
+      else decode_chunk<NDIM, K, false>(p, g, slut, sstate + t, sring + t, j, start, vecbase);
+    }
   }
 }
 
