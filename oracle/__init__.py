@@ -1,9 +1,8 @@
 """CPU oracle of the compression path (test infrastructure only).
 
 Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline legs of
-``bench.py`` import this package.  It compiles ``fz_oracle.c`` (and, for the
-learned selector, ``fz_oracle_mlp.c``) with gcc into ``oracle/_build`` and
-wraps the C functions with ctypes and numpy.  Nothing here touches the CUDA
+``bench.py`` import this package.  It compiles ``fz_oracle.c`` with gcc into
+``oracle/_build`` and wraps the C functions with ctypes and numpy.  Nothing here touches the CUDA
 library, and the CUDA library never loads this one.
 
 The C sources are built with ``-O2 -ffp-contract=off -fno-fast-math`` so that
@@ -28,13 +27,9 @@ _lib = None
 OK, EINVAL, ENOMEM, EBUFFER, ECORRUPT, EUNSUPPORTED = 0, 1, 2, 4, 5, 7
 
 
-def _extra_sources():
-    return [s for s in ("fz_oracle_mlp.c",) if os.path.exists(os.path.join(_HERE, s))]
-
-
 def build(force: bool = False) -> str:
     """Compile the oracle shared library (gcc, plain C11); returns its path."""
-    srcs = [os.path.join(_HERE, s) for s in _SOURCES + _extra_sources()]
+    srcs = [os.path.join(_HERE, s) for s in _SOURCES]
     os.makedirs(_BUILD, exist_ok=True)
     if not force and os.path.exists(_LIB):
         lib_t = os.path.getmtime(_LIB)
@@ -91,9 +86,25 @@ def _declare(L):
                                      C.c_uint32, u16p, i32p, u64p, u64p, u64p]
     L.orc_encode.argtypes = [u16p, C.c_uint64, C.c_uint64, u8p, C.c_uint32, u32p, C.c_uint64, u32p, u64p]
     L.orc_decode.argtypes = [u32p, C.c_uint64, u8p, C.c_uint32, C.c_uint64, u16p]
-    if hasattr(L, "orc_mlp_forward"):
-        from . import mlp as _mlp  # noqa: F401  (declares its own symbols)
-        _mlp._declare(L)
+    L.orc_compress_pred.argtypes = [f32p, C.c_uint32, u64p, C.c_uint32, C.c_double, C.c_uint32, C.c_uint32,
+                                    u16p, u8p, C.c_uint64, u64p]
+    L.orc_interp_block.argtypes = [C.c_int, C.c_int, u8p, i32p, u8p, i64p]
+    L.orc_interp_block.restype = None
+    L.orc_block_costs.argtypes = [i32p, u8p, i32p, u8p, C.c_uint32, u64p]
+    L.orc_log2fix.argtypes = [C.c_uint64]
+    L.orc_log2fix.restype = C.c_float
+    L.orc_f32_to_bf16.argtypes = [C.c_float]
+    L.orc_f32_to_bf16.restype = C.c_uint16
+    L.orc_bf16_to_f32.argtypes = [C.c_uint16]
+    L.orc_bf16_to_f32.restype = C.c_float
+    L.orc_block_features.argtypes = [i32p, u8p, i32p, u8p, C.c_uint32, u64p, u16p]
+    L.orc_block_features.restype = None
+    L.orc_mlp_infer.argtypes = [u16p, u16p, f32p]
+    L.orc_mlp_loss_grad.argtypes = [u16p, u16p, u8p, C.c_uint64, C.POINTER(C.c_double)]
+    L.orc_mlp_loss_grad.restype = C.c_double
+    L.orc_mlp_loss_double.argtypes = [C.POINTER(C.c_double), u16p, u8p, C.c_uint64]
+    L.orc_mlp_loss_double.restype = C.c_double
+    L.orc_field_blocks.argtypes = [f32p, u64p, C.c_uint32, C.c_double, C.c_uint32, u8p, u64p, u16p]
 
 
 def _p(a, t):
@@ -221,8 +232,14 @@ def compress_bound(shape) -> int:
     return int(lib().orc_compress_bound(len(shape), _p(d, u64p)))
 
 
-def compress(x: np.ndarray, eb: float, mode: str = "rel", lorenzo_k: int = 1, radius: int = 512) -> np.ndarray:
-    """Compress a C-order float32 array (last axis fastest = the format's x)."""
+PRED_IDS = {"lorenzo1": 0, "lorenzo2": 1, "interp_linear": 2, "interp_cubic": 3, "mlp": 16, "exhaustive": 17}
+
+
+def compress(x: np.ndarray, eb: float, mode: str = "rel", lorenzo_k: int = 1, radius: int = 512,
+             predictor=None, weights: np.ndarray | None = None) -> np.ndarray:
+    """Compress a C-order float32 array (last axis fastest = the format's x).
+    ``predictor`` (name or id) overrides ``lorenzo_k``; ``weights`` are the
+    selector network's bfloat16 bits for predictor "mlp"."""
     x = np.ascontiguousarray(x, dtype=np.float32)
     shape = x.shape
     ndim = len(shape)
@@ -230,10 +247,102 @@ def compress(x: np.ndarray, eb: float, mode: str = "rel", lorenzo_k: int = 1, ra
     cap = int(lib().orc_compress_bound(ndim, _p(d, u64p))) + 4096
     out = np.zeros(cap, np.uint8)
     nb = C.c_uint64()
-    st = lib().orc_compress(_p(x, f32p), ndim, _p(d, u64p), 1 if mode == "rel" else 0, float(eb), lorenzo_k,
-                            radius, _p(out, u8p), cap, C.byref(nb))
+    pred = lorenzo_k - 1 if predictor is None else (PRED_IDS[predictor] if isinstance(predictor, str) else predictor)
+    wp = None
+    if weights is not None:
+        weights = np.ascontiguousarray(weights, dtype=np.uint16)
+        wp = _p(weights, u16p)
+    st = lib().orc_compress_pred(_p(x, f32p), ndim, _p(d, u64p), 1 if mode == "rel" else 0, float(eb), pred,
+                                 radius, wp, _p(out, u8p), cap, C.byref(nb))
     _chk(st, "compress")
     return out[: nb.value].copy()
+
+
+# ---------------------------------------------------------------- selector
+NFEAT, NHID, NPRED = 32, 64, 4
+NW = NHID * NFEAT + NHID + NPRED * NHID + NPRED
+
+
+def interp_block(cubic: bool, inverse: bool, values, inb=None, corner_q=None, corner_in=None):
+    v = np.ascontiguousarray(values, dtype=np.int64).ravel().copy()
+    inb = np.ones(512, np.uint8) if inb is None else np.ascontiguousarray(inb, dtype=np.uint8).ravel()
+    cq = np.zeros(8, np.int32) if corner_q is None else np.ascontiguousarray(corner_q, dtype=np.int32)
+    ci = np.zeros(8, np.uint8) if corner_in is None else np.ascontiguousarray(corner_in, dtype=np.uint8)
+    lib().orc_interp_block(int(cubic), int(inverse), _p(inb, u8p), _p(cq, i32p), _p(ci, u8p), _p(v, i64p))
+    return v
+
+
+def block_costs(qb, inb=None, corner_q=None, corner_in=None, R=512):
+    qb = np.ascontiguousarray(qb, dtype=np.int32).ravel()
+    inb = np.ones(512, np.uint8) if inb is None else np.ascontiguousarray(inb, dtype=np.uint8).ravel()
+    cq = np.zeros(8, np.int32) if corner_q is None else np.ascontiguousarray(corner_q, dtype=np.int32)
+    ci = np.zeros(8, np.uint8) if corner_in is None else np.ascontiguousarray(corner_in, dtype=np.uint8)
+    c = np.zeros(NPRED, np.uint64)
+    best = lib().orc_block_costs(_p(qb, i32p), _p(inb, u8p), _p(cq, i32p), _p(ci, u8p), R, _p(c, u64p))
+    return best, c
+
+
+def log2fix(s: int) -> float:
+    return lib().orc_log2fix(int(s))
+
+
+def f32_to_bf16(f: float) -> int:
+    return int(lib().orc_f32_to_bf16(float(f)))
+
+
+def bf16_to_f32(h: int) -> float:
+    return lib().orc_bf16_to_f32(int(h))
+
+
+def block_features(qb, inb=None, corner_q=None, corner_in=None, R=512):
+    qb = np.ascontiguousarray(qb, dtype=np.int32).ravel()
+    inb = np.ones(512, np.uint8) if inb is None else np.ascontiguousarray(inb, dtype=np.uint8).ravel()
+    cq = np.zeros(8, np.int32) if corner_q is None else np.ascontiguousarray(corner_q, dtype=np.int32)
+    ci = np.zeros(8, np.uint8) if corner_in is None else np.ascontiguousarray(corner_in, dtype=np.uint8)
+    stat = np.zeros(NFEAT, np.uint64)
+    feat = np.zeros(NFEAT, np.uint16)
+    lib().orc_block_features(_p(qb, i32p), _p(inb, u8p), _p(cq, i32p), _p(ci, u8p), R, _p(stat, u64p),
+                             _p(feat, u16p))
+    return stat, feat
+
+
+def mlp_infer(weights, feat):
+    w = np.ascontiguousarray(weights, dtype=np.uint16)
+    f = np.ascontiguousarray(feat, dtype=np.uint16)
+    lg = np.zeros(NPRED, np.float32)
+    best = lib().orc_mlp_infer(_p(w, u16p), _p(f, u16p), _p(lg, f32p))
+    return best, lg
+
+
+def mlp_loss_grad(weights, feat, labels):
+    w = np.ascontiguousarray(weights, dtype=np.uint16)
+    f = np.ascontiguousarray(feat, dtype=np.uint16)
+    lb = np.ascontiguousarray(labels, dtype=np.uint8)
+    g = np.zeros(NW, np.float64)
+    loss = lib().orc_mlp_loss_grad(_p(w, u16p), _p(f, u16p), _p(lb, u8p), lb.size,
+                                   g.ctypes.data_as(C.POINTER(C.c_double)))
+    return loss, g
+
+
+def mlp_loss_double(W, feat, labels):
+    W = np.ascontiguousarray(W, dtype=np.float64)
+    f = np.ascontiguousarray(feat, dtype=np.uint16)
+    lb = np.ascontiguousarray(labels, dtype=np.uint8)
+    return lib().orc_mlp_loss_double(W.ctypes.data_as(C.POINTER(C.c_double)), _p(f, u16p), _p(lb, u8p), lb.size)
+
+
+def field_blocks(x: np.ndarray, eb: float, mode: str = "rel", radius: int = 512):
+    """Exhaustive-trial labels, trial costs and bfloat16 features of every
+    block of a 3D field (nz, ny, nx)."""
+    x = np.ascontiguousarray(x, dtype=np.float32)
+    d = _dims3(x.shape[::-1])
+    nb = int(np.prod([-(-s // 8) for s in x.shape]))
+    lab = np.zeros(nb, np.uint8)
+    costs = np.zeros((nb, NPRED), np.uint64)
+    feat = np.zeros((nb, NFEAT), np.uint16)
+    _chk(lib().orc_field_blocks(_p(x, f32p), _p(d, u64p), 1 if mode == "rel" else 0, float(eb), radius,
+                                _p(lab, u8p), _p(costs, u64p), _p(feat, u16p)), "field_blocks")
+    return lab, costs, feat
 
 
 def decompress(buf: np.ndarray) -> np.ndarray:

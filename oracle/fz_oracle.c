@@ -410,6 +410,396 @@ static void put_min_header(uint8_t *h, uint16_t flags, uint32_t ndim, uint32_t e
 }
 
 /* ------------------------------------------------------------------------ */
+/* Per-block predictor selection (3D, 8x8x8 blocks): interpolation           */
+/* predictors, exhaustive trial, block features and the selector MLP         */
+/* (the auto-selection of modules named as future work in §5; the dynamic   */
+/* module selection of §3.3.1)                                               */
+/* ------------------------------------------------------------------------ */
+
+static int check_args(uint32_t ndim, const uint64_t dims[3], uint64_t *n);
+
+#define ORC_NPRED 4
+#define ORC_NFEAT 32
+#define ORC_HID 64
+
+/* Corner c = cx + 2 cy + 4 cz of a block: the point o + 8 (cx, cy, cz). */
+static int corner_of(int x, int y, int z) {
+  if ((x != 0 && x != 8) || (y != 0 && y != 8) || (z != 0 && z != 8)) return -1;
+  return (x >> 3) + 2 * (y >> 3) + 4 * (z >> 3);
+}
+
+/* Value and availability of a point of the block's neighbourhood during the
+ * interpolation: in-block points (in the domain) and in-domain corners. */
+static int interp_get(const int64_t *vb, const uint8_t *inb, const int32_t cq[8], const uint8_t cin[8], int x, int y,
+                      int z, int64_t *v) {
+  if (x >= 0 && y >= 0 && z >= 0 && x < 8 && y < 8 && z < 8) {
+    int i = (z * 8 + y) * 8 + x;
+    if (!inb[i]) return 0;
+    *v = vb[i];
+    return 1;
+  }
+  int c = corner_of(x, y, z);
+  if (c < 0 || !cin[c]) return 0;
+  *v = cq[c];
+  return 1;
+}
+
+/* Interpolation predictor of one 8x8x8 block on the integer field q, open
+ * loop.  Known first: the block origin (its anchor) and the in-domain
+ * corners o + {0,8}^3.  Levels s = 4, 2, 1; within a level, passes along x,
+ * then y, then z; the pass along axis a predicts the points whose a
+ * coordinate is s mod 2s, whose earlier coordinates are 0 mod s and whose
+ * later coordinates are 0 mod 2s.  With neighbours p +- s and p +- 3s along
+ * a: the cubic form (-q[-3] + 9 q[-1] + 9 q[+1] - q[+3] + 8) >> 4 when
+ * `cubic` and all four are available, else the linear form
+ * (q[-1] + q[+1] + 1) >> 1 when both near neighbours are, else q[-1].  The
+ * residual is q - prediction (at the origin: q itself, the anchor).  When
+ * `inverse` is set, v holds residuals on entry and q on exit. */
+void orc_interp_block(int cubic, int inverse, const uint8_t *inb, const int32_t cq[8], const uint8_t cin[8],
+                      int64_t *v) {
+  /* w: q values.  Forward: all of q (the traversal only ever reads points
+   * of earlier levels or passes).  Inverse: filled in traversal order,
+   * starting from the origin, whose residual is q itself. */
+  int64_t *w = (int64_t *)malloc(512 * sizeof(int64_t));
+  if (!w) return;
+  for (int i = 0; i < 512; i++) w[i] = inverse ? 0 : v[i];
+  if (inverse) w[0] = v[0];
+  for (int s = 4; s >= 1; s >>= 1)
+    for (int a = 0; a < 3; a++)
+      for (int z = 0; z < 8; z++)
+        for (int y = 0; y < 8; y++)
+          for (int x = 0; x < 8; x++) {
+            int c[3] = {x, y, z};
+            int ok = (c[a] % (2 * s)) == s;
+            for (int b = 0; b < 3 && ok; b++) {
+              if (b < a && c[b] % s != 0) ok = 0;
+              if (b > a && c[b] % (2 * s) != 0) ok = 0;
+            }
+            if (!ok) continue;
+            int i = (z * 8 + y) * 8 + x;
+            if (!inb[i]) continue;
+            int64_t vm1, vp1, vm3, vp3;
+            int d[3] = {0, 0, 0};
+            d[a] = s;
+            int am1 = interp_get(w, inb, cq, cin, x - d[0], y - d[1], z - d[2], &vm1);
+            int ap1 = interp_get(w, inb, cq, cin, x + d[0], y + d[1], z + d[2], &vp1);
+            int am3 = interp_get(w, inb, cq, cin, x - 3 * d[0], y - 3 * d[1], z - 3 * d[2], &vm3);
+            int ap3 = interp_get(w, inb, cq, cin, x + 3 * d[0], y + 3 * d[1], z + 3 * d[2], &vp3);
+            int64_t pred;
+            if (cubic && am3 && am1 && ap1 && ap3) pred = (-vm3 + 9 * vm1 + 9 * vp1 - vp3 + 8) >> 4;
+            else if (am1 && ap1) pred = (vm1 + vp1 + 1) >> 1;
+            else pred = vm1; /* p - s is in the block and the domain whenever p is */
+            if (inverse) w[i] = v[i] + pred;  /* reconstruct q */
+            else v[i] = w[i] - pred;          /* residual; w keeps q */
+          }
+  if (inverse) for (int i = 0; i < 512; i++) v[i] = inb[i] ? w[i] : 0;
+  free(w);
+}
+
+/* Residuals of predictor pid (0 Lorenzo-1, 1 Lorenzo-2, 2 interpolation
+ * linear, 3 interpolation cubic) for one block; qb in block order. */
+static void block_residual(int pid, uint32_t ndim, const uint32_t b[3], const int32_t *qb, const uint8_t *inb,
+                           const int32_t cq[8], const uint8_t cin[8], int64_t *delta) {
+  if (pid < 2) {
+    orc_lorenzo_block(pid + 1, ndim, b, qb, inb, delta);
+    return;
+  }
+  for (int i = 0; i < 512; i++) delta[i] = inb[i] ? qb[i] : 0;
+  orc_interp_block(pid == 3, 0, inb, cq, cin, delta);
+}
+
+/* q values at the 8 corners o + {0,8}^3 of block blk and whether each lies
+ * in the domain. */
+static void block_corners(const grid_t *g, uint64_t blk, const int32_t *q, int32_t cq[8], uint8_t cin[8]) {
+  uint64_t bxi = blk % g->nb[0], byi = (blk / g->nb[0]) % g->nb[1], bzi = blk / (g->nb[0] * g->nb[1]);
+  for (int c = 0; c < 8; c++) {
+    uint64_t X = (bxi + (c & 1)) * 8, Y = (byi + ((c >> 1) & 1)) * 8, Z = (bzi + (c >> 2)) * 8;
+    cin[c] = (uint8_t)(X < g->d[0] && Y < g->d[1] && Z < g->d[2]);
+    cq[c] = cin[c] ? q[(Z * g->d[1] + Y) * g->d[0] + X] : 0;
+  }
+}
+
+/* Trial cost of a residual: 1 + 2 floor(log2(|d| + 1)) bits inside the code
+ * range (an Elias-gamma-like size), 96 bits for an outlier. */
+static uint64_t trial_bits(int64_t d, uint32_t R) {
+  uint64_t a = (uint64_t)(d < 0 ? -d : d);
+  if (a >= R) return 96;
+  uint64_t v = a + 1, e = 0;
+  while (v >>= 1) e++;
+  return 1 + 2 * e;
+}
+
+/* Exhaustive trial: cost of every predictor over the block's in-domain
+ * points except the origin; returns the argmin (ties: lowest id). */
+int orc_block_costs(const int32_t *qb, const uint8_t *inb, const int32_t cq[8], const uint8_t cin[8], uint32_t R,
+                    uint64_t cost[ORC_NPRED]) {
+  static const uint32_t b3[3] = {8, 8, 8};
+  int64_t delta[512];
+  int best = 0;
+  for (int k = 0; k < ORC_NPRED; k++) {
+    block_residual(k, 3, b3, qb, inb, cq, cin, delta);
+    uint64_t c = 0;
+    for (int i = 1; i < 512; i++)
+      if (inb[i]) c += trial_bits(delta[i], R);
+    cost[k] = c;
+    if (c < cost[best]) best = k;
+  }
+  return best;
+}
+
+/* log2fix(s) = e + m/16 with e = floor(log2(s+1)) and m the 4 bits of s+1
+ * below its leading one (zero-filled when s+1 has fewer bits); exact in
+ * binary32. */
+float orc_log2fix(uint64_t s) {
+  uint64_t v = s + 1;
+  int e = 63;
+  while (!((v >> e) & 1)) e--;
+  uint64_t m = e >= 4 ? (v >> (e - 4)) & 15u : (v << (4 - e)) & 15u;
+  return (float)e + (float)m / 16.0f;
+}
+
+/* binary32 -> bfloat16 bits, round to nearest, ties to even (finite input). */
+uint16_t orc_f32_to_bf16(float f) {
+  uint32_t u = f2u(f);
+  uint32_t lsb = (u >> 16) & 1u;
+  u += 0x7fffu + lsb;
+  return (uint16_t)(u >> 16);
+}
+float orc_bf16_to_f32(uint16_t h) { return u2f((uint32_t)h << 16); }
+
+static uint64_t uabs64(int64_t v) { return (uint64_t)(v < 0 ? -v : v); }
+
+/* The 32 block statistics (all integers >= 0) behind the selector's inputs:
+ *  0-7   sum and max of |residual| of predictors 0..3 on the 64 points with
+ *        all-odd in-block coordinates
+ *  8-10  sum |q(p) - q(p - e_a)|               (first differences, a = x,y,z)
+ *  11-13 sum |second differences|, 14-16 sum |third differences| per axis
+ *  17-19 sum |mixed differences| for (x,y), (x,z), (y,z)
+ *  20-22 sign changes between consecutive first differences per axis
+ *  23    sum |q - mean| (mean = floor(sum q / n))
+ *  24    max q - min q
+ *  25    outliers of Lorenzo-1 on the odd sub-lattice
+ *  26-28 availability of the +x, +y, +z corner anchors
+ *  29    in-domain points, 30 |anchor|, 31 sum |q(p) - q(p - 2 e_x)|
+ * A difference is taken where all the points it uses lie in the block and
+ * the domain.  Then feature = bf16(log2fix(statistic)). */
+void orc_block_features(const int32_t *qb, const uint8_t *inb, const int32_t cq[8], const uint8_t cin[8], uint32_t R,
+                        uint64_t stat[ORC_NFEAT], uint16_t feat[ORC_NFEAT]) {
+  static const uint32_t b3[3] = {8, 8, 8};
+  int64_t delta[512];
+  memset(stat, 0, ORC_NFEAT * sizeof(uint64_t));
+  for (int k = 0; k < ORC_NPRED; k++) {
+    block_residual(k, 3, b3, qb, inb, cq, cin, delta);
+    for (int z = 1; z < 8; z += 2)
+      for (int y = 1; y < 8; y += 2)
+        for (int x = 1; x < 8; x += 2) {
+          int i = (z * 8 + y) * 8 + x;
+          if (!inb[i]) continue;
+          uint64_t a = uabs64(delta[i]);
+          stat[2 * k] += a;
+          if (a > stat[2 * k + 1]) stat[2 * k + 1] = a;
+          if (k == 0 && a >= R) stat[25]++;
+        }
+  }
+  int64_t sum = 0, mn = 0, mx = 0;
+  uint64_t n = 0;
+  for (int i = 0; i < 512; i++)
+    if (inb[i]) {
+      if (n == 0) { mn = qb[i]; mx = qb[i]; }
+      if (qb[i] < mn) mn = qb[i];
+      if (qb[i] > mx) mx = qb[i];
+      sum += qb[i];
+      n++;
+    }
+  for (int z = 0; z < 8; z++)
+    for (int y = 0; y < 8; y++)
+      for (int x = 0; x < 8; x++) {
+        int c[3] = {x, y, z};
+        int i = (z * 8 + y) * 8 + x;
+        if (!inb[i]) continue;
+        int st[3] = {1, 8, 64};
+        for (int a = 0; a < 3; a++) {
+          if (c[a] >= 1 && inb[i - st[a]]) {
+            int64_t d1 = (int64_t)qb[i] - qb[i - st[a]];
+            stat[8 + a] += uabs64(d1);
+            if (c[a] >= 2 && inb[i - 2 * st[a]]) {
+              int64_t d1p = (int64_t)qb[i - st[a]] - qb[i - 2 * st[a]];
+              stat[11 + a] += uabs64(d1 - d1p);
+              if ((d1 > 0 && d1p < 0) || (d1 < 0 && d1p > 0)) stat[20 + a]++;
+              if (c[a] >= 3 && inb[i - 3 * st[a]]) {
+                int64_t d1pp = (int64_t)qb[i - 2 * st[a]] - qb[i - 3 * st[a]];
+                stat[14 + a] += uabs64(d1 - 2 * d1p + d1pp);
+              }
+            }
+          }
+        }
+        int pairs[3][2] = {{0, 1}, {0, 2}, {1, 2}};
+        for (int pr = 0; pr < 3; pr++) {
+          int a = pairs[pr][0], bb = pairs[pr][1];
+          if (c[a] >= 1 && c[bb] >= 1 && inb[i - st[a]] && inb[i - st[bb]] && inb[i - st[a] - st[bb]]) {
+            int64_t m = (int64_t)qb[i] - qb[i - st[a]] - qb[i - st[bb]] + qb[i - st[a] - st[bb]];
+            stat[17 + pr] += uabs64(m);
+          }
+        }
+        if (x >= 2 && inb[i - 2]) stat[31] += uabs64((int64_t)qb[i] - qb[i - 2]);
+      }
+  int64_t mean = sum / (int64_t)n;
+  if ((sum % (int64_t)n) != 0 && sum < 0) mean -= 1; /* floor */
+  for (int i = 0; i < 512; i++)
+    if (inb[i]) stat[23] += uabs64((int64_t)qb[i] - mean);
+  stat[24] = (uint64_t)(mx - mn);
+  stat[26] = cin[1];
+  stat[27] = cin[2];
+  stat[28] = cin[4];
+  stat[29] = n;
+  stat[30] = uabs64(qb[0]);
+  for (int f = 0; f < ORC_NFEAT; f++) feat[f] = orc_f32_to_bf16(orc_log2fix(stat[f]));
+}
+
+/* Selector network weights, all bfloat16 bits: W1[64][32], b1[64],
+ * W2[4][64], b2[4] (2372 values). */
+#define ORC_W1 0
+#define ORC_B1 (ORC_W1 + ORC_HID * ORC_NFEAT)
+#define ORC_W2 (ORC_B1 + ORC_HID)
+#define ORC_B2 (ORC_W2 + ORC_NPRED * ORC_HID)
+#define ORC_NW (ORC_B2 + ORC_NPRED)
+
+/* Inference: h_j = bf16(max(0, fma chain over k of W1[j][k] f[k] starting
+ * from b1[j])), logits_i = fma chain over j of W2[i][j] h_j starting from
+ * b2[i]; binary32 fmaf in index order; argmax with ties to the lowest id. */
+int orc_mlp_infer(const uint16_t *w, const uint16_t feat[ORC_NFEAT], float logits[ORC_NPRED]) {
+  float h[ORC_HID];
+  for (int j = 0; j < ORC_HID; j++) {
+    float acc = orc_bf16_to_f32(w[ORC_B1 + j]);
+    for (int k = 0; k < ORC_NFEAT; k++)
+      acc = fmaf(orc_bf16_to_f32(w[ORC_W1 + j * ORC_NFEAT + k]), orc_bf16_to_f32(feat[k]), acc);
+    if (!(acc > 0.0f)) acc = 0.0f;
+    h[j] = orc_bf16_to_f32(orc_f32_to_bf16(acc));
+  }
+  int best = 0;
+  for (int i = 0; i < ORC_NPRED; i++) {
+    float acc = orc_bf16_to_f32(w[ORC_B2 + i]);
+    for (int j = 0; j < ORC_HID; j++) acc = fmaf(orc_bf16_to_f32(w[ORC_W2 + i * ORC_HID + j]), h[j], acc);
+    logits[i] = acc;
+    if (acc > logits[best]) best = i;
+  }
+  return best;
+}
+
+/* Training objective in double: z = b1 + W1 f, h = max(0, z),
+ * logits = b2 + W2 h, loss = mean over the minibatch of -log softmax(logits)
+ * at the label; analytic gradients with respect to all parameters (the
+ * weights are the bfloat16 values, as doubles).  grad has ORC_NW entries. */
+double orc_mlp_loss_grad(const uint16_t *w, const uint16_t *feat, const uint8_t *label, uint64_t nb, double *grad) {
+  double W[ORC_NW];
+  for (int i = 0; i < ORC_NW; i++) W[i] = (double)orc_bf16_to_f32(w[i]);
+  if (grad) memset(grad, 0, ORC_NW * sizeof(double));
+  double loss = 0.0;
+  for (uint64_t s = 0; s < nb; s++) {
+    const uint16_t *f16 = feat + s * ORC_NFEAT;
+    double f[ORC_NFEAT], z[ORC_HID], h[ORC_HID], lg[ORC_NPRED], p[ORC_NPRED];
+    for (int k = 0; k < ORC_NFEAT; k++) f[k] = (double)orc_bf16_to_f32(f16[k]);
+    for (int j = 0; j < ORC_HID; j++) {
+      double acc = W[ORC_B1 + j];
+      for (int k = 0; k < ORC_NFEAT; k++) acc += W[ORC_W1 + j * ORC_NFEAT + k] * f[k];
+      z[j] = acc;
+      h[j] = acc > 0.0 ? acc : 0.0;
+    }
+    double mxl = -1e300;
+    for (int i = 0; i < ORC_NPRED; i++) {
+      double acc = W[ORC_B2 + i];
+      for (int j = 0; j < ORC_HID; j++) acc += W[ORC_W2 + i * ORC_HID + j] * h[j];
+      lg[i] = acc;
+      if (acc > mxl) mxl = acc;
+    }
+    double den = 0.0;
+    for (int i = 0; i < ORC_NPRED; i++) { p[i] = exp(lg[i] - mxl); den += p[i]; }
+    for (int i = 0; i < ORC_NPRED; i++) p[i] /= den;
+    loss += -log(p[label[s]]);
+    if (!grad) continue;
+    double dl[ORC_NPRED], dh[ORC_HID];
+    for (int i = 0; i < ORC_NPRED; i++) dl[i] = (p[i] - (i == label[s] ? 1.0 : 0.0)) / (double)nb;
+    for (int i = 0; i < ORC_NPRED; i++) {
+      grad[ORC_B2 + i] += dl[i];
+      for (int j = 0; j < ORC_HID; j++) grad[ORC_W2 + i * ORC_HID + j] += dl[i] * h[j];
+    }
+    for (int j = 0; j < ORC_HID; j++) {
+      double a = 0.0;
+      for (int i = 0; i < ORC_NPRED; i++) a += W[ORC_W2 + i * ORC_HID + j] * dl[i];
+      dh[j] = z[j] > 0.0 ? a : 0.0;
+      grad[ORC_B1 + j] += dh[j];
+      for (int k = 0; k < ORC_NFEAT; k++) grad[ORC_W1 + j * ORC_NFEAT + k] += dh[j] * f[k];
+    }
+  }
+  return loss / (double)nb;
+}
+
+/* The same loss with the weights given as doubles (for finite differences). */
+double orc_mlp_loss_double(const double *W, const uint16_t *feat, const uint8_t *label, uint64_t nb) {
+  double loss = 0.0;
+  for (uint64_t s = 0; s < nb; s++) {
+    const uint16_t *f16 = feat + s * ORC_NFEAT;
+    double f[ORC_NFEAT], h[ORC_HID], lg[ORC_NPRED];
+    for (int k = 0; k < ORC_NFEAT; k++) f[k] = (double)orc_bf16_to_f32(f16[k]);
+    for (int j = 0; j < ORC_HID; j++) {
+      double acc = W[ORC_B1 + j];
+      for (int k = 0; k < ORC_NFEAT; k++) acc += W[ORC_W1 + j * ORC_NFEAT + k] * f[k];
+      h[j] = acc > 0.0 ? acc : 0.0;
+    }
+    double mxl = -1e300, den = 0.0;
+    for (int i = 0; i < ORC_NPRED; i++) {
+      double acc = W[ORC_B2 + i];
+      for (int j = 0; j < ORC_HID; j++) acc += W[ORC_W2 + i * ORC_HID + j] * h[j];
+      lg[i] = acc;
+      if (acc > mxl) mxl = acc;
+    }
+    for (int i = 0; i < ORC_NPRED; i++) den += exp(lg[i] - mxl);
+    loss += -(lg[label[s]] - mxl - log(den));
+  }
+  return loss / (double)nb;
+}
+
+/* Labels and features of every block of a 3D field (for training and for
+ * the stage tests): exhaustive-trial label, the 4 trial costs and the 32
+ * bfloat16 features. */
+int orc_field_blocks(const float *x, const uint64_t dims[3], uint32_t eb_mode, double eb, uint32_t R, uint8_t *label,
+                     uint64_t *costs, uint16_t *feat) {
+  uint64_t n;
+  int st = check_args(3, dims, &n);
+  if (st) return st;
+  double eb_abs = eb;
+  if (eb_mode == 1) {
+    float lo, hi;
+    int same;
+    if (!orc_range(x, n, &lo, &hi, &same) || hi == lo) return ORC_EUNSUPPORTED;
+    eb_abs = eb * ((double)hi - (double)lo);
+  }
+  float ebx2, inv2eb, eb_chk;
+  orc_constants(eb_abs, &ebx2, &inv2eb, &eb_chk);
+  int32_t *q = (int32_t *)malloc(n * 4);
+  uint8_t *exc = (uint8_t *)malloc(n);
+  if (!q || !exc) { free(q); free(exc); return ORC_ENOMEM; }
+  orc_prequant(x, n, inv2eb, ebx2, eb_chk, q, exc);
+  grid_t g;
+  make_grid(3, dims, &g);
+  int32_t qb[512], cq[8];
+  uint8_t inb[512], cin[8];
+  uint64_t fidx[512], stat[ORC_NFEAT];
+  for (uint64_t blk = 0; blk < g.n_blocks; blk++) {
+    gather_block(&g, blk, q, qb, inb, fidx);
+    block_corners(&g, blk, q, cq, cin);
+    uint64_t c[ORC_NPRED];
+    int best = orc_block_costs(qb, inb, cq, cin, R, c);
+    if (label) label[blk] = (uint8_t)best;
+    if (costs) memcpy(costs + blk * ORC_NPRED, c, sizeof(c));
+    if (feat) orc_block_features(qb, inb, cq, cin, R, stat, feat + blk * ORC_NFEAT);
+  }
+  free(q);
+  free(exc);
+  return ORC_OK;
+}
+
+/* ------------------------------------------------------------------------ */
 /* Whole pipeline: compress                                                  */
 /* ------------------------------------------------------------------------ */
 
@@ -441,17 +831,25 @@ static int write_raw(const float *x, uint64_t n, uint32_t ndim, uint32_t ebmode,
   return ORC_OK;
 }
 
-/* Compress x (field order, x fastest) with Lorenzo order `lorenzo_k` (1 or 2)
- * and radius R.  eb_mode 0 = ABS, 1 = REL (value range over finite values).
- * Output is the complete stream. */
-int orc_compress(const float *x, uint32_t ndim, const uint64_t dims[3], uint32_t eb_mode, double eb,
-                 uint32_t lorenzo_k, uint32_t R, uint8_t *out, uint64_t cap, uint64_t *out_bytes) {
+/* Compress x (field order, x fastest) with predictor `pred` (0 Lorenzo-1,
+ * 1 Lorenzo-2 in any dimension; 2 interpolation linear, 3 interpolation
+ * cubic, 16 per-block choice by the selector network with bfloat16 weights
+ * `w`, 17 per-block choice by exhaustive trial, 3D only) and radius R.
+ * eb_mode 0 = ABS, 1 = REL (value range over finite values).  Output is the
+ * complete stream; with a per-block choice it carries the 2-bit predictor id
+ * of every block. */
+int orc_compress_pred(const float *x, uint32_t ndim, const uint64_t dims[3], uint32_t eb_mode, double eb,
+                      uint32_t pred, uint32_t R, const uint16_t *w, uint8_t *out, uint64_t cap,
+                      uint64_t *out_bytes) {
   uint64_t n;
   int st = check_args(ndim, dims, &n);
   if (st) return st;
   if (!(eb > 0.0) || !isfinite(eb) || eb_mode > 1) return ORC_EINVAL;
-  if (lorenzo_k < 1 || lorenzo_k > 2) return ORC_EUNSUPPORTED;
+  if (!(pred <= 3 || pred == 16 || pred == 17)) return ORC_EINVAL;
+  if (pred >= 2 && ndim != 3) return ORC_EUNSUPPORTED;
+  if (pred == 16 && !w) return ORC_EINVAL;
   if (R < 2 || R > 512) return ORC_EINVAL;
+  const int sel = pred >= 16;
   uint64_t dd[3] = {1, 1, 1};
   for (uint32_t a = 0; a < ndim; a++) dd[a] = dims[a];
 
@@ -499,17 +897,33 @@ int orc_compress(const float *x, uint32_t ndim, const uint64_t dims[3], uint32_t
   uint8_t *inb = (uint8_t *)malloc(g.bsize);
   uint64_t *fidx = (uint64_t *)malloc(g.bsize * 8);
   int64_t *delta = (int64_t *)malloc(g.bsize * 8);
+  uint8_t *ids = (uint8_t *)calloc(g.n_blocks / 4 + 1, 1);
   uint64_t hist[ORC_MAXSYM];
   memset(hist, 0, sizeof(hist));
   uint64_t n_out = 0, n_exc = 0;
   int overflow = 0;
-  if (!codes || !anchors || !oidx || !oval || !eidx || !eval || !qb || !inb || !fidx || !delta) {
+  if (!codes || !anchors || !oidx || !oval || !eidx || !eval || !qb || !inb || !fidx || !delta || !ids) {
     st = ORC_ENOMEM;
     goto done;
   }
   for (uint64_t blk = 0; blk < g.n_blocks; blk++) {
     gather_block(&g, blk, q, qb, inb, fidx);
-    orc_lorenzo_block((int)lorenzo_k, ndim, g.b, qb, inb, delta);
+    int32_t cq[8];
+    uint8_t cin[8];
+    int pid = (int)pred;
+    if (ndim == 3) block_corners(&g, blk, q, cq, cin);
+    if (pred == 17) {
+      uint64_t c[ORC_NPRED];
+      pid = orc_block_costs(qb, inb, cq, cin, R, c);
+    } else if (pred == 16) {
+      uint64_t stat[ORC_NFEAT];
+      uint16_t feat[ORC_NFEAT];
+      float lg[ORC_NPRED];
+      orc_block_features(qb, inb, cq, cin, R, stat, feat);
+      pid = orc_mlp_infer(w, feat, lg);
+    }
+    if (sel) ids[blk >> 2] |= (uint8_t)(pid << (2 * (blk & 3)));
+    block_residual(pid, ndim, g.b, qb, inb, cq, cin, delta);
     for (uint64_t i = 0; i < g.bsize; i++) {
       uint64_t pos = blk * g.bsize + i;
       uint16_t c;
@@ -550,7 +964,8 @@ int orc_compress(const float *x, uint32_t ndim, const uint64_t dims[3], uint32_t
   uint64_t n_chunks = g.n_blocks, C = g.bsize;
   uint64_t off_lens = HDR;
   uint64_t off_ids = align16(off_lens + nsym);
-  uint64_t off_anch = off_ids;
+  uint64_t ids_bytes = sel ? (g.n_blocks + 3) / 4 : 0;
+  uint64_t off_anch = align16(off_ids + ids_bytes);
   uint64_t off_cb = align16(off_anch + 4 * g.n_blocks);
   uint64_t off_oidx = align16(off_cb + 4 * n_chunks);
   uint64_t off_oval = align16(off_oidx + 4 * n_out);
@@ -568,7 +983,7 @@ int orc_compress(const float *x, uint32_t ndim, const uint64_t dims[3], uint32_t
   uint8_t *h = out;
   put_u32(h + H_MAGIC, MAGIC);
   put_u16(h + H_VERSION, 1);
-  put_u16(h + H_FLAGS, 0);
+  put_u16(h + H_FLAGS, sel ? F_IDS : 0);
   put_u32(h + H_NDIM, ndim);
   put_u32(h + H_EBMODE, eb_mode);
   for (int a = 0; a < 3; a++) put_u64(h + H_DIMS + 8 * a, dd[a]);
@@ -579,7 +994,7 @@ int orc_compress(const float *x, uint32_t ndim, const uint64_t dims[3], uint32_t
   put_u32(h + H_EBCHK, f2u(eb_chk));
   put_u32(h + H_RADIUS, R);
   for (int a = 0; a < 3; a++) put_u32(h + H_BLOCK + 4 * a, g.b[a]);
-  put_u32(h + H_PRED, lorenzo_k - 1);
+  put_u32(h + H_PRED, pred);
   put_u32(h + H_CHUNK, (uint32_t)C);
   put_u64(h + H_NBLOCKS, g.n_blocks);
   put_u64(h + H_NCHUNKS, n_chunks);
@@ -587,7 +1002,7 @@ int orc_compress(const float *x, uint32_t ndim, const uint64_t dims[3], uint32_t
   put_u64(h + H_NEXC, n_exc);
   put_u64(h + H_TBITS, total_bits);
   put_u64(h + H_OFF_LENS, off_lens);
-  put_u64(h + H_OFF_IDS, 0);
+  put_u64(h + H_OFF_IDS, sel ? off_ids : 0);
   put_u64(h + H_OFF_ANCH, off_anch);
   put_u64(h + H_OFF_CBITS, off_cb);
   put_u64(h + H_OFF_OIDX, off_oidx);
@@ -597,6 +1012,7 @@ int orc_compress(const float *x, uint32_t ndim, const uint64_t dims[3], uint32_t
   put_u64(h + H_OFF_BITS, off_bits);
   put_u64(h + H_TOTAL, total);
   memcpy(out + off_lens, len, nsym);
+  if (sel) memcpy(out + off_ids, ids, ids_bytes);
   for (uint64_t b = 0; b < g.n_blocks; b++) put_u32(out + off_anch + 4 * b, (uint32_t)anchors[b]);
   for (uint64_t i = 0; i < n_out; i++) {
     put_u32(out + off_oidx + 4 * i, oidx[i]);
@@ -625,8 +1041,15 @@ int orc_compress(const float *x, uint32_t ndim, const uint64_t dims[3], uint32_t
   st = ORC_OK;
 done:
   free(q); free(exc); free(codes); free(anchors); free(oidx); free(oval); free(eidx); free(eval);
-  free(qb); free(inb); free(fidx); free(delta);
+  free(qb); free(inb); free(fidx); free(delta); free(ids);
   return st;
+}
+
+/* Lorenzo order k (1 or 2) for every block. */
+int orc_compress(const float *x, uint32_t ndim, const uint64_t dims[3], uint32_t eb_mode, double eb,
+                 uint32_t lorenzo_k, uint32_t R, uint8_t *out, uint64_t cap, uint64_t *out_bytes) {
+  if (lorenzo_k < 1 || lorenzo_k > 2) return ORC_EUNSUPPORTED;
+  return orc_compress_pred(x, ndim, dims, eb_mode, eb, lorenzo_k - 1, R, NULL, out, cap, out_bytes);
 }
 
 /* ------------------------------------------------------------------------ */
@@ -678,12 +1101,16 @@ int orc_decompress(const uint8_t *in, uint64_t in_bytes, float *out, uint64_t ou
     for (uint64_t i = 0; i < n; i++) out[i] = v;
     return ORC_OK;
   }
-  if (flags != 0) return ORC_EUNSUPPORTED;
+  if (flags != 0 && flags != F_IDS) return ORC_EUNSUPPORTED;
   grid_t g;
   make_grid(ndim, dims, &g);
   uint32_t R = get_u32(in + H_RADIUS), nsym = 2 * R;
   uint32_t pred = get_u32(in + H_PRED);
-  if (R < 2 || R > 512 || pred > 1) return ORC_ECORRUPT;
+  const int sel = flags == F_IDS;
+  if (R < 2 || R > 512) return ORC_ECORRUPT;
+  if (sel != (pred == 16 || pred == 17) || !(pred <= 3 || pred == 16 || pred == 17)) return ORC_ECORRUPT;
+  if (pred >= 2 && ndim != 3) return ORC_ECORRUPT;
+  uint64_t o_ids = get_u64(in + H_OFF_IDS);
   for (int a = 0; a < 3; a++)
     if (get_u32(in + H_BLOCK + 4 * a) != g.b[a]) return ORC_ECORRUPT;
   float ebx2 = u2f(get_u32(in + H_EBX2));
@@ -696,6 +1123,7 @@ int orc_decompress(const uint8_t *in, uint64_t in_bytes, float *out, uint64_t ou
   uint64_t o_oi = get_u64(in + H_OFF_OIDX), o_ov = get_u64(in + H_OFF_OVAL), o_ei = get_u64(in + H_OFF_EIDX);
   uint64_t o_ev = get_u64(in + H_OFF_EVAL), o_bits = get_u64(in + H_OFF_BITS);
   uint64_t n_words = (tbits + 31) / 32;
+  if (sel && o_ids + (nb + 3) / 4 > total) return ORC_ECORRUPT;
   if (o_len + nsym > total || o_anch + 4 * nb > total || o_cb + 4 * nch > total || o_oi + 4 * n_out > total ||
       o_ov + 4 * n_out > total || o_ei + 4 * n_exc > total || o_ev + 4 * n_exc > total ||
       o_bits + 4 * n_words > total)
@@ -745,7 +1173,21 @@ int orc_decompress(const uint8_t *in, uint64_t in_bytes, float *out, uint64_t ou
     }
     if (p != p_end) { st = ORC_ECORRUPT; goto ddone; }
     v[0] += (int32_t)get_u32(in + o_anch + 4 * blk);
-    orc_lorenzo_block_inverse((int)pred + 1, ndim, g.b, v);
+    int pid = sel ? (in[o_ids + (blk >> 2)] >> (2 * (blk & 3))) & 3 : (int)pred;
+    if (pid < 2) {
+      orc_lorenzo_block_inverse(pid + 1, ndim, g.b, v);
+    } else {
+      /* corner anchors: origins of the neighbouring blocks */
+      int32_t cq[8];
+      uint8_t cin[8];
+      uint64_t bxi = blk % g.nb[0], byi = (blk / g.nb[0]) % g.nb[1], bzi = blk / (g.nb[0] * g.nb[1]);
+      for (int c = 0; c < 8; c++) {
+        uint64_t X = bxi + (c & 1), Y = byi + ((c >> 1) & 1), Z = bzi + (c >> 2);
+        cin[c] = (uint8_t)(X < g.nb[0] && Y < g.nb[1] && Z < g.nb[2]);
+        cq[c] = cin[c] ? (int32_t)get_u32(in + o_anch + 4 * ((Z * g.nb[1] + Y) * g.nb[0] + X)) : 0;
+      }
+      orc_interp_block(pid == 3, 1, inb, cq, cin, v);
+    }
     for (uint64_t i = 0; i < g.bsize; i++) {
       if (!inb[i]) continue;
       uint64_t pos = blk * g.bsize + i;

@@ -205,3 +205,43 @@ def smooth_nd(shape, seed: int = 0) -> torch.Tensor:
         f += rng.uniform(0.2, 1.0) * np.sin(arg)
     f += 1e-3 * rng.standard_normal(shape)
     return torch.from_numpy(f.astype(np.float32))
+
+
+# --------------------------------------------------------------------------
+# 3D: stitched field for the learned predictor selector
+# --------------------------------------------------------------------------
+def stitched3d(n: int = 512, seed: int = 200, region: int = 64, device=None) -> torch.Tensor:
+    """n^3 field made of region^3 cubes, each (by seed) smooth (40%: Gaussian
+    random field with a k^-4 spectrum), oscillatory (40%: a sinusoid with
+    random direction, wavelength U[4,16] cells, amplitude 1, over a weak
+    smooth background) or noisy (20%: uniform U[-a, a] with a U[0.05, 0.5]).
+    Amplitudes are comparable so that one value-range bound fits all three."""
+    dev = _dev(device)
+    g = _gen(seed, dev)
+    f64 = torch.float64
+    smooth = grf3d(n, seed=seed * 7 + 1, slope=4.0 - 2.0, device=dev).to(f64)  # shell spectrum k^-2 -> P(k) ~ k^-4
+    smooth = smooth / smooth.abs().max()
+    nr = n // region
+    out = torch.empty((n, n, n), dtype=f64, device=dev)
+    ax = torch.arange(region, device=dev, dtype=f64)
+    zz, yy, xx = torch.meshgrid(ax, ax, ax, indexing="ij")
+    for rz in range(nr):
+        for ry in range(nr):
+            for rx in range(nr):
+                sl = (slice(rz * region, (rz + 1) * region), slice(ry * region, (ry + 1) * region),
+                      slice(rx * region, (rx + 1) * region))
+                u = float(torch.rand(1, generator=g, device=dev, dtype=f64))
+                base = smooth[sl]
+                if u < 0.4:
+                    out[sl] = base
+                elif u < 0.8:
+                    d = torch.randn(3, generator=g, device=dev, dtype=f64)
+                    d = d / d.norm()
+                    lam = 4.0 + 12.0 * float(torch.rand(1, generator=g, device=dev, dtype=f64))
+                    ph = 2.0 * math.pi * float(torch.rand(1, generator=g, device=dev, dtype=f64))
+                    out[sl] = torch.sin(2.0 * math.pi * (d[0] * (xx + rx * region) + d[1] * (yy + ry * region)
+                                                         + d[2] * (zz + rz * region)) / lam + ph) + 0.1 * base
+                else:
+                    a = 0.05 + 0.45 * float(torch.rand(1, generator=g, device=dev, dtype=f64))
+                    out[sl] = a * (2.0 * torch.rand(base.shape, generator=g, device=dev, dtype=f64) - 1.0)
+    return out.to(torch.float32)

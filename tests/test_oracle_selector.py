@@ -1,0 +1,215 @@
+"""Pins of the oracle's per-block predictor selection: interpolation
+predictors, trial costs, block features, the selector network's exact
+inference and its training gradients."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import synth
+
+
+def _block_coords():
+    z, y, x = np.meshgrid(np.arange(8), np.arange(8), np.arange(8), indexing="ij")
+    return x.ravel(), y.ravel(), z.ravel()
+
+
+def _corners(fn):
+    cq = np.zeros(8, np.int32)
+    for c in range(8):
+        cq[c] = fn(8 * (c & 1), 8 * ((c >> 1) & 1), 8 * (c >> 2))
+    return cq
+
+
+def _level_axis(x, y, z):
+    """Level s and pass axis of a non-origin block point (the traversal
+    order: levels 4, 2, 1; passes x, y, z)."""
+    c = (x, y, z)
+    for s in (4, 2, 1):
+        if all(v % s == 0 for v in c):
+            ax = max(a for a in range(3) if (c[a] // s) % 2 == 1)
+            return s, ax
+    raise AssertionError
+
+
+def _avail(c, ax, off):
+    p = list(c)
+    p[ax] += off
+    if all(0 <= v < 8 for v in p):
+        return True
+    return all(v in (0, 8) for v in p)
+
+
+def test_interp_linear_exact_on_affine_fields():
+    fn = lambda x, y, z: 3 * x - 2 * y + 5 * z + 7
+    x, y, z = _block_coords()
+    q = fn(x, y, z)
+    d = oracle.interp_block(False, False, q, corner_q=_corners(fn), corner_in=np.ones(8, np.uint8))
+    assert d[0] == q[0]  # the origin keeps q (the anchor)
+    checked = 0
+    for i in range(1, 512):
+        s, ax = _level_axis(x[i], y[i], z[i])
+        c = (x[i], y[i], z[i])
+        if _avail(c, ax, -s) and _avail(c, ax, s):
+            assert d[i] == 0, (c, d[i])
+            checked += 1
+    assert checked > 200
+
+
+def test_interp_cubic_exact_on_cubic_polynomials():
+    for ax in range(3):
+        fn = lambda x, y, z, ax=ax: (x, y, z)[ax] ** 3 - 4 * (x, y, z)[ax] ** 2 + 11
+        x, y, z = _block_coords()
+        q = fn(x, y, z)
+        d = oracle.interp_block(True, False, q, corner_q=_corners(fn), corner_in=np.ones(8, np.uint8))
+        hits = 0
+        for i in range(1, 512):
+            s, a = _level_axis(x[i], y[i], z[i])
+            c = (x[i], y[i], z[i])
+            if a == ax and all(_avail(c, a, o) for o in (-3 * s, -s, s, 3 * s)):
+                assert d[i] == 0
+                hits += 1
+        assert hits > 0
+
+
+@pytest.mark.parametrize("cubic", [False, True])
+@pytest.mark.parametrize("seed", range(4))
+def test_interp_inverse_roundtrip(cubic, seed):
+    rng = np.random.default_rng(seed)
+    q = rng.integers(-(2 ** 22), 2 ** 22, 512).astype(np.int32)
+    inb = np.ones((8, 8, 8), np.uint8)
+    if seed % 2:  # a ragged block at the domain edge
+        inb[5:, :, :] = 0
+        inb[:, :, 6:] = 0
+    inb = inb.ravel()
+    cin = rng.integers(0, 2, 8).astype(np.uint8)
+    cin[0] = 1
+    cq = rng.integers(-1000, 1000, 8).astype(np.int32)
+    qm = np.where(inb > 0, q, 0)
+    d = oracle.interp_block(cubic, False, qm, inb, cq, cin)
+    r = oracle.interp_block(cubic, True, d, inb, cq, cin)
+    assert np.array_equal(r[inb > 0], qm[inb > 0].astype(np.int64))
+
+
+def test_trial_costs_and_labels():
+    # constant block: Lorenzo-1 and both interpolations leave zeros -> 511
+    # one-bit codes and the first id wins; Lorenzo-2's zero padding leaves
+    # nonzero residuals next to the block faces
+    best, c = oracle.block_costs(np.full(512, 40, np.int32), corner_q=np.full(8, 40, np.int32),
+                                 corner_in=np.ones(8, np.uint8))
+    assert best == 0 and c[0] == c[2] == c[3] == 511 and c[1] > 511
+    # a single huge spike: outliers cost 96 bits
+    q = np.zeros(512, np.int32)
+    q[511] = 10 ** 6
+    _, c = oracle.block_costs(q)
+    assert c[0] == 510 + 96
+    # the label of every block of a field is the argmin of its costs (ties -> lowest)
+    x = synth.stitched3d(64, seed=3, region=32, device="cpu").numpy()
+    lab, costs, _ = oracle.field_blocks(x, 1e-4)
+    assert np.array_equal(lab, np.argmin(costs, axis=1))
+
+
+def test_log2fix_definition():
+    cases = {0: 0.0, 1: 1.0, 2: 1.5, 3: 2.0, 6: 2.75, 15: 4.0, 16: 4.0625, 31: 5.0, 47: 5.5,
+             (1 << 20) - 1: 20.0, (1 << 40) + (1 << 36) - 1: 40.0625}
+    for s_, v in cases.items():
+        assert oracle.log2fix(s_) == v, (s_, oracle.log2fix(s_), v)
+
+
+def test_bf16_round_to_nearest_even():
+    assert oracle.f32_to_bf16(1.0) == 0x3F80
+    assert oracle.f32_to_bf16(1.0 + 2 ** -8) == 0x3F80       # tie -> even
+    assert oracle.f32_to_bf16(1.0 + 3 * 2 ** -8) == 0x3F82   # tie -> even
+    rng = np.random.default_rng(0)
+    v = (rng.standard_normal(2000) * 10.0 ** rng.uniform(-3, 3, 2000)).astype(np.float32)
+    ref = torch.from_numpy(v).to(torch.bfloat16).view(torch.int16).numpy().view(np.uint16)
+    got = np.array([oracle.f32_to_bf16(float(a)) for a in v], np.uint16)
+    assert np.array_equal(got, ref)
+
+
+def test_features_closed_forms():
+    st, ft = oracle.block_features(np.full(512, 9, np.int32), corner_q=np.full(8, 9, np.int32),
+                                   corner_in=np.ones(8, np.uint8))
+    # every statistic vanishes except Lorenzo-2's (zero padding at the faces)
+    assert st[[0, 1, 4, 5, 6, 7]].sum() == 0 and st[2] > 0
+    assert st[8:26].sum() == 0 and st[29] == 512 and st[30] == 9 and st[31] == 0
+    assert st[26:29].tolist() == [1, 1, 1]
+    x, y, z = _block_coords()
+    st, _ = oracle.block_features(x.astype(np.int32))  # ramp along x, no corners
+    assert st[8] == 7 * 64 and st[9] == 0 and st[10] == 0
+    assert st[11] == 0 and st[14] == 0 and st[20:23].sum() == 0
+    assert st[23] == 64 * (3 + 2 + 1 + 0 + 1 + 2 + 3 + 4) and st[24] == 7
+    assert st[31] == 2 * 6 * 64 and st[26:29].tolist() == [0, 0, 0]
+    # features are bf16(log2fix(stat))
+    for v, f in zip(st, _):
+        assert f == oracle.f32_to_bf16(oracle.log2fix(int(v)))
+
+
+def _rand_weights(rng):
+    w = (rng.standard_normal(oracle.NW) * 0.3).astype(np.float32)
+    return torch.from_numpy(w).to(torch.bfloat16).view(torch.int16).numpy().view(np.uint16)
+
+
+def _bf(a):
+    return torch.from_numpy(np.ascontiguousarray(a).view(np.int16)).view(torch.bfloat16).float().double().numpy()
+
+
+def test_mlp_inference_matches_double_forward():
+    rng = np.random.default_rng(3)
+    w = _rand_weights(rng)
+    W = _bf(w)
+    n1, n2 = oracle.NHID * oracle.NFEAT, oracle.NHID
+    agree = 0
+    for _ in range(200):
+        f32 = rng.uniform(0, 20, oracle.NFEAT).astype(np.float32)
+        f = torch.from_numpy(f32).to(torch.bfloat16).view(torch.int16).numpy().view(np.uint16)
+        best, lg = oracle.mlp_infer(w, f)
+        fd = _bf(f)
+        h = np.maximum(W[:n1].reshape(64, 32) @ fd + W[n1:n1 + n2], 0)
+        lgd = W[n1 + n2:n1 + n2 + 256].reshape(4, 64) @ h + W[-4:]
+        srt = np.sort(lgd)
+        if srt[-1] - srt[-2] > 1e-2 * max(1.0, abs(srt[-1])):
+            assert best == int(np.argmax(lgd))
+            agree += 1
+        assert np.allclose(lg, lgd, rtol=2e-2, atol=2e-2 * np.abs(lgd).max())
+    assert agree > 150
+
+
+def test_mlp_gradient_matches_finite_differences():
+    rng = np.random.default_rng(11)
+    w = _rand_weights(rng)
+    nb = 64
+    f32 = rng.uniform(0, 10, (nb, oracle.NFEAT)).astype(np.float32)
+    feat = torch.from_numpy(f32).to(torch.bfloat16).view(torch.int16).numpy().view(np.uint16)
+    lab = rng.integers(0, 4, nb).astype(np.uint8)
+    loss, g = oracle.mlp_loss_grad(w, feat, lab)
+    W = _bf(w)
+    assert abs(oracle.mlp_loss_double(W, feat, lab) - loss) < 1e-12
+    idx = rng.choice(oracle.NW, 60, replace=False)
+    for i in idx:
+        e = 1e-6
+        Wp, Wm = W.copy(), W.copy()
+        Wp[i] += e
+        Wm[i] -= e
+        fd = (oracle.mlp_loss_double(Wp, feat, lab) - oracle.mlp_loss_double(Wm, feat, lab)) / (2 * e)
+        assert abs(fd - g[i]) <= 1e-6 + 1e-4 * abs(fd), (i, fd, g[i])
+
+
+def test_selector_streams_roundtrip_and_ids():
+    x = synth.stitched3d(64, seed=5, region=32, device="cpu").numpy()
+    eb = 1e-4
+    eb_abs = eb * (float(x.max()) - float(x.min()))
+    lab, _, _ = oracle.field_blocks(x, eb)
+    for pred in ("interp_linear", "interp_cubic", "exhaustive"):
+        buf = oracle.compress(x, eb, predictor=pred)
+        y = oracle.decompress(buf)
+        assert (np.abs(x.astype(np.float64) - y) <= eb_abs).all()
+    buf = oracle.compress(x, eb, predictor="exhaustive")
+    off_ids = int(np.frombuffer(buf[144:152].tobytes(), np.uint64)[0])
+    ids = np.unpackbits(buf[off_ids:off_ids + (lab.size + 3) // 4][:, None], axis=1, bitorder="little")
+    ids = (ids.reshape(-1, 4, 2) * np.array([1, 2])).sum(-1).ravel()[: lab.size]
+    assert np.array_equal(ids, lab)
+    # random weights: any choice keeps the bound
+    w = _rand_weights(np.random.default_rng(0))
+    y = oracle.decompress(oracle.compress(x, eb, predictor="mlp", weights=w))
+    assert (np.abs(x.astype(np.float64) - y) <= eb_abs).all()
