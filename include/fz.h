@@ -173,6 +173,46 @@ fz_status fz_lorenzo_quantize(fz_ctx *ctx, const float *d_in, uint32_t ndim, con
 fz_status fz_huffman_codebook(fz_ctx *ctx, const uint64_t *d_hist, uint32_t nsym, uint8_t *d_lens,
                               uint32_t *d_codes, void *stream);
 
+/* ---- per-block predictor selection (3D): FZ_PRED_INTERP_*, FZ_SEL_* ----
+ * The auto-selection of modules named as future work in FZModules §5 and the
+ * dynamic module selection of §3.3.1.  Four predictors per 8x8x8 block:
+ * 0 Lorenzo-1, 1 Lorenzo-2, 2 interpolation linear, 3 interpolation cubic
+ * (levels 4, 2, 1 over the block with the corner anchors o + {0,8}^3).
+ * FZ_SEL_EXHAUSTIVE picks per block the predictor with the smallest trial
+ * cost (sum over the block of 1 + 2 floor(log2(|d|+1)) bits for codes, 96
+ * for outliers); FZ_SEL_MLP picks the argmax of a 32 -> 64 (ReLU) -> 4
+ * network over 32 block statistics (log2fix, bfloat16), with bfloat16
+ * weights given as fz_pipeline.selector_weights: a device array of
+ * FZ_SELECTOR_WEIGHTS uint16 bfloat16 values in the order W1[64][32], b1[64],
+ * W2[4][64], b2[4].  Streams then carry a 2-bit id per block. */
+#define FZ_SELECTOR_WEIGHTS 2372
+#define FZ_SELECTOR_FEATURES 32
+
+/* Stage entry point (label generation for the selector): for every block
+ * of the 3D field d_in, the exhaustive-trial label d_labels (u8[n_blocks]),
+ * optionally the four trial costs d_costs (u32[n_blocks][4]) and the 32
+ * bfloat16 features d_features (u16[n_blocks][32]).  eb_mode/eb/radius as
+ * for fz_compress.  Synchronizes `stream`; FZ_EUNSUPPORTED for a constant
+ * field. */
+fz_status fz_block_report(fz_ctx *ctx, const float *d_in, const uint64_t dims[3], uint32_t eb_mode, double eb,
+                          uint32_t radius, uint8_t *d_labels, uint32_t *d_costs, uint16_t *d_features,
+                          void *stream);
+
+/* Selector training, gradient: mean softmax cross-entropy of n samples
+ * (features u16[n][32] bfloat16, labels u8[n]) under the bfloat16 rounding
+ * of the float32 master weights d_weights (FZ_SELECTOR_WEIGHTS values);
+ * writes the gradient with respect to the master weights to d_grad
+ * (float32, same layout) and, if h_loss is not NULL, the loss (host; the
+ * call then synchronizes `stream`).  Deterministic (fixed reduction order). */
+fz_status fz_mlp_grad(fz_ctx *ctx, const float *d_weights, const uint16_t *d_features, const uint8_t *d_labels,
+                      uint32_t n, float *d_grad, float *h_loss, void *stream);
+
+/* Selector training, Adam step number `step` (from 1) on the float32 master
+ * weights with moment buffers d_m, d_v; also writes their bfloat16 copy to
+ * d_weights_bf16 when it is not NULL.  Does not synchronize. */
+fz_status fz_mlp_adam(fz_ctx *ctx, float *d_weights, const float *d_grad, float *d_m, float *d_v, uint32_t step,
+                      float lr, float beta1, float beta2, float eps, uint16_t *d_weights_bf16, void *stream);
+
 /* Per-stage timing of the last fz_compress and fz_decompress on a context.
  * When profiling is enabled, each call records a CUDA event on its stream
  * before the first and after every stage launch; a stage time is the

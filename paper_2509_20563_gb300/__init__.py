@@ -19,11 +19,13 @@ import threading
 import torch
 
 __all__ = ["lib", "Context", "compress", "decompress", "lorenzo_quantize", "huffman_codebook", "stream_info",
-           "FzError", "HEADER_BYTES"]
+           "block_report", "mlp_grad", "mlp_adam", "FzError", "HEADER_BYTES", "SELECTOR_WEIGHTS"]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_build", "libfz.so")
 HEADER_BYTES = 256
+SELECTOR_WEIGHTS = 2372  # W1[64][32], b1[64], W2[4][64], b2[4]
+SELECTOR_FEATURES = 32
 
 STATUS = {0: "FZ_OK", 1: "FZ_EINVAL", 2: "FZ_ENOMEM", 3: "FZ_ECUDA", 4: "FZ_EBUFFER", 5: "FZ_ECORRUPT",
           6: "FZ_ETIMEOUT", 7: "FZ_EUNSUPPORTED"}
@@ -63,8 +65,15 @@ def _declare(L):
     L.fz_lorenzo_quantize.argtypes = [_vp, _vp, C.c_uint32, _u64p, C.c_uint32, C.c_double, C.POINTER(Pipeline),
                                       _vp, _vp, _vp, _u64p, _u64p, C.POINTER(C.c_double), _vp]
     L.fz_huffman_codebook.argtypes = [_vp, _vp, C.c_uint32, _vp, _vp, _vp]
+    L.fz_block_report.argtypes = [_vp, _vp, _u64p, C.c_uint32, C.c_double, C.c_uint32, _vp, _vp, _vp, _vp]
+    L.fz_mlp_grad.argtypes = [_vp, _vp, _vp, _vp, C.c_uint32, _vp, C.POINTER(C.c_float), _vp]
+    L.fz_mlp_adam.argtypes = [_vp, _vp, _vp, _vp, _vp, C.c_uint32, C.c_float, C.c_float, C.c_float, C.c_float,
+                              _vp, _vp]
+    L.fz_ctx_set_profiling.argtypes = [_vp, C.c_int]
+    L.fz_ctx_get_profile.argtypes = [_vp, _vp]
     for name in ("fz_ctx_create", "fz_ctx_destroy", "fz_compress", "fz_decompress", "fz_stream_info",
-                 "fz_lorenzo_quantize", "fz_huffman_codebook"):
+                 "fz_lorenzo_quantize", "fz_huffman_codebook", "fz_block_report", "fz_mlp_grad", "fz_mlp_adam",
+                 "fz_ctx_set_profiling", "fz_ctx_get_profile"):
         getattr(L, name).restype = C.c_int
 
 
@@ -232,3 +241,46 @@ def huffman_codebook(hist: torch.Tensor, stream=None):
                                    C.c_void_p(lens.data_ptr()), C.c_void_p(codes.data_ptr()), _stream(stream))
     _check(st, "fz_huffman_codebook")
     return lens, codes
+
+
+# ---------------------------------------------------------------- selector
+def block_report(x: torch.Tensor, eb: float, mode: str = "rel", radius: int = 512, costs: bool = True,
+                 features: bool = True, stream=None):
+    """Per-block exhaustive-trial labels (u8), trial costs (int32 [nb, 4])
+    and bfloat16 features (int16 bits [nb, 32]) of a 3D float32 CUDA field."""
+    if x.dim() != 3:
+        raise ValueError("block_report needs a 3D field")
+    nb = 1
+    for s_ in x.shape:
+        nb *= -(-s_ // 8)
+    lab = torch.empty(nb, dtype=torch.uint8, device=x.device)
+    cst = torch.empty((nb, 4), dtype=torch.int32, device=x.device) if costs else None
+    fea = torch.empty((nb, SELECTOR_FEATURES), dtype=torch.int16, device=x.device) if features else None
+    st = lib().fz_block_report(_ctx(x.device.index or 0).handle, C.c_void_p(x.data_ptr()), _dims(x.shape),
+                               1 if mode == "rel" else 0, float(eb), int(radius), C.c_void_p(lab.data_ptr()),
+                               C.c_void_p(cst.data_ptr()) if cst is not None else None,
+                               C.c_void_p(fea.data_ptr()) if fea is not None else None, _stream(stream))
+    _check(st, "fz_block_report")
+    return lab, cst, fea
+
+
+def mlp_grad(w: torch.Tensor, feat: torch.Tensor, labels: torch.Tensor, grad: torch.Tensor | None = None,
+             want_loss: bool = True, stream=None):
+    """Gradient (float32 [2372]) and loss of the selector objective."""
+    if grad is None:
+        grad = torch.empty(SELECTOR_WEIGHTS, dtype=torch.float32, device=w.device)
+    loss = C.c_float()
+    st = lib().fz_mlp_grad(_ctx(w.device.index or 0).handle, C.c_void_p(w.data_ptr()), C.c_void_p(feat.data_ptr()),
+                           C.c_void_p(labels.data_ptr()), labels.numel(), C.c_void_p(grad.data_ptr()),
+                           C.byref(loss) if want_loss else None, _stream(stream))
+    _check(st, "fz_mlp_grad")
+    return grad, (loss.value if want_loss else None)
+
+
+def mlp_adam(w, grad, m, v, step: int, lr: float, beta1: float = 0.9, beta2: float = 0.999, eps: float = 1e-8,
+             w_bf16: torch.Tensor | None = None, stream=None):
+    st = lib().fz_mlp_adam(_ctx(w.device.index or 0).handle, C.c_void_p(w.data_ptr()), C.c_void_p(grad.data_ptr()),
+                           C.c_void_p(m.data_ptr()), C.c_void_p(v.data_ptr()), int(step), float(lr), float(beta1),
+                           float(beta2), float(eps), C.c_void_p(w_bf16.data_ptr()) if w_bf16 is not None else None,
+                           _stream(stream))
+    _check(st, "fz_mlp_adam")

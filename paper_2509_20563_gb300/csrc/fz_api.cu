@@ -126,29 +126,37 @@ size_t layout_compress(const Geom &g, char *base, CompressWs &ws) {
   ws.out_val = reinterpret_cast<int32_t *>(take(4 * cap));
   ws.exc_idx = reinterpret_cast<uint32_t *>(take(4 * cap));
   ws.exc_val = reinterpret_cast<uint32_t *>(take(4 * cap));
+  ws.ids = reinterpret_cast<uint8_t *>(take(g.n_blocks));
   return off;
 }
 
 struct Req {
   uint32_t pred, R;
+  const uint16_t *weights;
 };
 
-fz_status parse_pipe(const fz_pipeline *pipe, Req &r) {
+fz_status parse_pipe(const fz_pipeline *pipe, uint32_t ndim, Req &r) {
   r.pred = FZ_PRED_LORENZO1;
   r.R = 512;
+  r.weights = nullptr;
   if (pipe) {
     if (pipe->struct_size < sizeof(uint32_t) * 3) return FZ_EINVAL;
     r.pred = pipe->predictor;
     if (pipe->radius) r.R = pipe->radius;
+    if (pipe->struct_size >= sizeof(fz_pipeline)) r.weights = reinterpret_cast<const uint16_t *>(pipe->selector_weights);
   }
   if (r.R < 2 || r.R > 512) return FZ_EINVAL;
-  if (r.pred != FZ_PRED_LORENZO1 && r.pred != FZ_PRED_LORENZO2) {
-    if (r.pred == FZ_PRED_INTERP_LIN || r.pred == FZ_PRED_INTERP_CUBIC || r.pred == FZ_SEL_MLP ||
-        r.pred == FZ_SEL_EXHAUSTIVE)
-      return FZ_EUNSUPPORTED;
-    return FZ_EINVAL;
+  switch (r.pred) {
+    case FZ_PRED_LORENZO1:
+    case FZ_PRED_LORENZO2: return FZ_OK;
+    case FZ_PRED_INTERP_LIN:
+    case FZ_PRED_INTERP_CUBIC:
+    case FZ_SEL_EXHAUSTIVE: return ndim == 3 ? FZ_OK : FZ_EUNSUPPORTED;
+    case FZ_SEL_MLP:
+      if (ndim != 3) return FZ_EUNSUPPORTED;
+      return r.weights ? FZ_OK : FZ_EINVAL;
+    default: return FZ_EINVAL;
   }
-  return FZ_OK;
 }
 
 // Run range + quantization into `ws` (shared by compress and the stage call).
@@ -160,7 +168,8 @@ fz_status run_front(fz_ctx *ctx, const float *d_in, const Geom &g, uint32_t eb_m
   e = launch_range(d_in, g, eb_mode, eb, ws.ctl, st);
   if (e != cudaSuccess) return from_cuda(e);
   clk.mark("range", 1);
-  e = launch_quant(d_in, g, r.R, r.pred, ws, st, ctx->sm_count);
+  if (r.pred <= FZ_PRED_LORENZO2) e = launch_quant(d_in, g, r.R, r.pred, ws, st, ctx->sm_count);
+  else e = launch_selquant(d_in, g, r.R, r.pred, ws, r.weights, st, ctx->sm_count);
   clk.mark("quant", 1);
   return from_cuda(e);
 }
@@ -181,13 +190,20 @@ fz_status check_header(const fz_header &h, uint64_t in_bytes, Geom &g) {
   make_geom(h.ndim, h.dims, g);
   if (h.flags == FZ_FLAG_RAW) return h.total_bytes == FZ_HEADER_BYTES + 4 * n ? FZ_OK : FZ_ECORRUPT;
   if (h.flags == FZ_FLAG_CONST) return h.total_bytes == FZ_HEADER_BYTES + 16 ? FZ_OK : FZ_ECORRUPT;
-  if (h.flags != 0) return FZ_EUNSUPPORTED;
+  if (h.flags != 0 && h.flags != FZ_FLAG_IDS) return FZ_EUNSUPPORTED;
   if (h.radius < 2 || h.radius > 512) return FZ_ECORRUPT;
-  if (h.predictor != FZ_PRED_LORENZO1 && h.predictor != FZ_PRED_LORENZO2) return FZ_EUNSUPPORTED;
+  const bool sel = h.predictor == FZ_SEL_MLP || h.predictor == FZ_SEL_EXHAUSTIVE;
+  if (!(h.predictor <= FZ_PRED_INTERP_CUBIC || sel)) return FZ_ECORRUPT;
+  if (sel != (h.flags == FZ_FLAG_IDS)) return FZ_ECORRUPT;
+  if (h.predictor > FZ_PRED_LORENZO2 && h.ndim != 3) return FZ_ECORRUPT;
+  if (sel && (h.off_ids < FZ_HEADER_BYTES + 2ull * h.radius || (h.off_ids & 15u) ||
+              h.off_ids + (h.n_blocks + 3) / 4 > h.off_anchors))
+    return FZ_ECORRUPT;
   if (h.block[0] != g.bx || h.block[1] != g.by || h.block[2] != g.bz || h.chunk != g.bsize) return FZ_ECORRUPT;
   if (h.n_blocks != g.n_blocks || h.n_chunks != g.n_blocks) return FZ_ECORRUPT;
   if (h.n_out > n || h.n_exc > n || h.total_bits > (uint64_t)kLmax * g.npad) return FZ_ECORRUPT;
-  const uint64_t secs[9][2] = {{h.off_lens, 2ull * h.radius},        {h.off_anchors, 4 * h.n_blocks},
+  const uint64_t secs[9][2] = {{h.off_lens, sel ? h.off_ids - h.off_lens : 2ull * h.radius},
+                               {h.off_anchors, 4 * h.n_blocks},
                                {h.off_chunk_bits, 4 * h.n_chunks},   {h.off_out_idx, 4 * h.n_out},
                                {h.off_out_val, 4 * h.n_out},         {h.off_exc_idx, 4 * h.n_exc},
                                {h.off_exc_val, 4 * h.n_exc},         {h.off_bits, 4 * ((h.total_bits + 31) / 32)},
@@ -320,7 +336,7 @@ fz_status fz_compress(fz_ctx *ctx, const float *d_in, uint32_t ndim, const uint6
   if (eb_mode > FZ_EB_REL || !(eb > 0.0) || !(eb < __builtin_inf())) return FZ_EINVAL;
   if (((uintptr_t)d_out & 15u) || ((uintptr_t)d_in & 3u)) return FZ_EINVAL;
   Req r;
-  fz_status st = parse_pipe(pipe, r);
+  fz_status st = parse_pipe(pipe, ndim, r);
   if (st) return st;
   if (out_cap < FZ_HEADER_BYTES + 4 * n) return FZ_EBUFFER;
   if (overlaps(d_in, 4 * n, d_out, out_cap)) return FZ_EINVAL;
@@ -392,7 +408,9 @@ fz_status fz_decompress(fz_ctx *ctx, const void *d_in, uint64_t in_bytes, const 
   const uint64_t n_groups = (h.n_chunks + kDecThreads - 1) / kDecThreads;
   size_t off = 0;
   auto take = [&](size_t bytes) { size_t o = off; off += up(bytes); return o; };
-  const size_t o_err = take(16), o_lut = take(2u << kLutBits), o_gsum = take(8 * n_groups);
+  const bool selpath = h.predictor > FZ_PRED_LORENZO2;
+  const size_t o_err = take(16), o_lut = take(2u << kLutBits), o_gsum = take(8 * n_groups),
+               o_codes = selpath ? take(2 * g.npad) : 0;
   if ((st = ensure_ws(ctx, off))) return st;
   char *base = reinterpret_cast<char *>(ctx->ws);
   DecodeWs ws;
@@ -402,7 +420,15 @@ fz_status fz_decompress(fz_ctx *ctx, const void *d_in, uint64_t in_bytes, const 
   StageClock clk(ctx, s, true);
   e = cudaMemsetAsync(ws.err, 0, 16, s);
   if (e == cudaSuccess) { e = launch_decode_prep(in, h, ws, s); clk.mark("dec_prep", 2); }
-  if (e == cudaSuccess) { e = launch_decode_main(in, h, d_out, ws, s, ctx->sm_count); clk.mark("decode", 1); }
+  if (e == cudaSuccess) {
+    if (selpath) {
+      e = launch_sel_decode(in, h, d_out, ws, reinterpret_cast<uint16_t *>(base + o_codes), s, ctx->sm_count);
+      clk.mark("decode", 2);
+    } else {
+      e = launch_decode_main(in, h, d_out, ws, s, ctx->sm_count);
+      clk.mark("decode", 1);
+    }
+  }
   if (e == cudaSuccess) e = cudaMemcpyAsync(ctx->h_pinned, ws.err, 4, cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) return from_cuda(e);
@@ -421,7 +447,7 @@ fz_status fz_lorenzo_quantize(fz_ctx *ctx, const float *d_in, uint32_t ndim, con
   if (eb_mode > FZ_EB_REL || !(eb > 0.0) || !(eb < __builtin_inf())) return FZ_EINVAL;
   if (((uintptr_t)d_codes & 15u) || ((uintptr_t)d_in & 3u) || ((uintptr_t)d_anchors & 3u)) return FZ_EINVAL;
   Req r;
-  fz_status st = parse_pipe(pipe, r);
+  fz_status st = parse_pipe(pipe, ndim, r);
   if (st) return st;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   if (cudaSetDevice(ctx->device) != cudaSuccess) return FZ_ECUDA;
@@ -469,6 +495,67 @@ fz_status fz_huffman_codebook(fz_ctx *ctx, const uint64_t *d_hist, uint32_t nsym
   uint32_t err;
   memcpy(&err, ctx->h_pinned, 4);
   return (fz_status)err;
+}
+
+fz_status fz_block_report(fz_ctx *ctx, const float *d_in, const uint64_t dims[3], uint32_t eb_mode, double eb,
+                          uint32_t radius, uint8_t *d_labels, uint32_t *d_costs, uint16_t *d_features,
+                          void *stream) {
+  if (!ctx || !d_in || !d_labels) return FZ_EINVAL;
+  uint64_t n;
+  if (!valid_dims(3, dims, &n)) return FZ_EINVAL;
+  if (eb_mode > FZ_EB_REL || !(eb > 0.0) || !(eb < __builtin_inf())) return FZ_EINVAL;
+  const uint32_t R = radius ? radius : 512;
+  if (R < 2 || R > 512 || ((uintptr_t)d_in & 3u)) return FZ_EINVAL;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  if (cudaSetDevice(ctx->device) != cudaSuccess) return FZ_ECUDA;
+  Geom g;
+  make_geom(3, dims, g);
+  CompressWs ws;
+  size_t need = layout_compress(g, nullptr, ws);
+  fz_status st;
+  if ((st = ensure_ws(ctx, need)) || (st = ensure_pinned(ctx))) return st;
+  layout_compress(g, reinterpret_cast<char *>(ctx->ws), ws);
+  cudaError_t e = cudaMemsetAsync(ws.ctl, 0, ws.zero_bytes, s);
+  if (e == cudaSuccess) e = launch_range(d_in, g, eb_mode, eb, ws.ctl, s);
+  if (e == cudaSuccess) e = launch_select_report(d_in, g, R, ws, d_labels, d_costs, d_features, s, ctx->sm_count);
+  ctx->launches += 2;
+  struct Small { uint32_t err, mode; };
+  Small *hs = reinterpret_cast<Small *>(ctx->h_pinned);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&hs->err, &ws.ctl->res.err, 4, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&hs->mode, &ws.ctl->mode, 4, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return from_cuda(e);
+  if (hs->err) return (fz_status)hs->err;
+  return hs->mode == kModeNormal ? FZ_OK : FZ_EUNSUPPORTED;
+}
+
+fz_status fz_mlp_grad(fz_ctx *ctx, const float *d_weights, const uint16_t *d_features, const uint8_t *d_labels,
+                      uint32_t n, float *d_grad, float *h_loss, void *stream) {
+  if (!ctx || !d_weights || !d_features || !d_labels || !d_grad || n == 0) return FZ_EINVAL;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  if (cudaSetDevice(ctx->device) != cudaSuccess) return FZ_ECUDA;
+  const size_t part = up(sizeof(float) * mlp_partial_floats(n));
+  fz_status st;
+  if ((st = ensure_ws(ctx, part + up(16))) || (st = ensure_pinned(ctx))) return st;
+  float *partial = reinterpret_cast<float *>(ctx->ws);
+  float *dloss = reinterpret_cast<float *>(reinterpret_cast<char *>(ctx->ws) + part);
+  cudaError_t e = launch_mlp_grad(d_weights, d_features, d_labels, n, partial, d_grad, dloss, s);
+  ctx->launches += 2;
+  if (h_loss) {
+    if (e == cudaSuccess) e = cudaMemcpyAsync(ctx->h_pinned, dloss, 4, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e == cudaSuccess) memcpy(h_loss, ctx->h_pinned, 4);
+  }
+  return from_cuda(e);
+}
+
+fz_status fz_mlp_adam(fz_ctx *ctx, float *d_weights, const float *d_grad, float *d_m, float *d_v, uint32_t step,
+                      float lr, float beta1, float beta2, float eps, uint16_t *d_weights_bf16, void *stream) {
+  if (!ctx || !d_weights || !d_grad || !d_m || !d_v || step == 0) return FZ_EINVAL;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  if (cudaSetDevice(ctx->device) != cudaSuccess) return FZ_ECUDA;
+  ctx->launches += 1;
+  return from_cuda(launch_adam(d_weights, d_grad, d_m, d_v, d_weights_bf16, step, lr, beta1, beta2, eps, s));
 }
 
 }  // extern "C"

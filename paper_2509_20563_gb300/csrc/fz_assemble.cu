@@ -82,8 +82,21 @@ __global__ void __launch_bounds__(kAsmThreads) k_assemble(const float *__restric
   const uint64_t nb = h.n_blocks, n_out = h.n_out, n_exc = h.n_exc;
   copy_bytes(d_out + h.off_lens, ctl->lens, nsym, tid, nth);
   copy_bytes(d_out + h.off_anchors, reinterpret_cast<const uint8_t *>(ws.anchors), 4 * nb, tid, nth);
+  uint64_t lens_end = h.off_lens + nsym;
+  if (h.flags & FZ_FLAG_IDS) {
+    // 2-bit predictor ids, four blocks per byte, first block in the low bits
+    const uint64_t nbytes = (nb + 3) / 4;
+    for (uint64_t i = tid; i < nbytes; i += nth) {
+      uint8_t v = 0;
+      for (int k = 0; k < 4; ++k)
+        if (4 * i + k < nb) v |= (uint8_t)((ws.ids[4 * i + k] & 3u) << (2 * k));
+      d_out[h.off_ids + i] = v;
+    }
+    if (tid == 0) zero_gap(d_out, lens_end, h.off_ids);
+    lens_end = h.off_ids + nbytes;
+  }
   if (tid == 0) {
-    zero_gap(d_out, h.off_lens + nsym, h.off_anchors);
+    zero_gap(d_out, lens_end, h.off_anchors);
     zero_gap(d_out, h.off_anchors + 4 * nb, h.off_chunk_bits);
     zero_gap(d_out, h.off_chunk_bits + 4 * h.n_chunks, h.off_out_idx);
     zero_gap(d_out, h.off_out_idx + 4 * n_out, h.off_out_val);

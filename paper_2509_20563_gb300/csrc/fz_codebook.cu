@@ -226,8 +226,10 @@ __global__ void __launch_bounds__(kCbThreads) k_codebook(Geom g, uint32_t R, uin
   if (mode == kModeNormal) {
     const uint64_t nb = g.n_blocks, nch = g.n_blocks;
     const uint64_t n_out = ctl->n_out, n_exc = ctl->n_exc, tb = s.total_bits;
+    const bool sel = pred == FZ_SEL_MLP || pred == FZ_SEL_EXHAUSTIVE;
     const uint64_t off_lens = FZ_HEADER_BYTES;
-    const uint64_t off_anch = align16(off_lens + nsym);
+    const uint64_t off_ids = align16(off_lens + nsym);
+    const uint64_t off_anch = align16(off_ids + (sel ? (nb + 3) / 4 : 0));
     const uint64_t off_cb = align16(off_anch + 4 * nb);
     const uint64_t off_oidx = align16(off_cb + 4 * nch);
     const uint64_t off_oval = align16(off_oidx + 4 * n_out);
@@ -238,7 +240,7 @@ __global__ void __launch_bounds__(kCbThreads) k_codebook(Geom g, uint32_t R, uin
     if (total > FZ_HEADER_BYTES + 4 * N) {
       mode = kModeRaw;
     } else {
-      write_min_header(h, 0, g, eb_mode, eb, total);
+      write_min_header(h, sel ? FZ_FLAG_IDS : 0, g, eb_mode, eb, total);
       h.eb_abs = ctl->eb_abs;
       h.ebx2_bits = __float_as_uint(ctl->ebx2);
       h.inv2eb_bits = __float_as_uint(ctl->inv2eb);
@@ -248,7 +250,7 @@ __global__ void __launch_bounds__(kCbThreads) k_codebook(Geom g, uint32_t R, uin
       h.predictor = pred;
       h.chunk = g.bsize;
       h.n_blocks = nb; h.n_chunks = nch; h.n_out = n_out; h.n_exc = n_exc; h.total_bits = tb;
-      h.off_lens = off_lens; h.off_ids = 0; h.off_anchors = off_anch; h.off_chunk_bits = off_cb;
+      h.off_lens = off_lens; h.off_ids = sel ? off_ids : 0; h.off_anchors = off_anch; h.off_chunk_bits = off_cb;
       h.off_out_idx = off_oidx; h.off_out_val = off_oval; h.off_exc_idx = off_eidx; h.off_exc_val = off_eval;
       h.off_bits = off_bits;
       ctl->total_bits = tb;

@@ -219,6 +219,33 @@ __device__ __forceinline__ uint64_t lookback(uint64_t *status, uint64_t tile, ui
 
 inline __host__ __device__ uint64_t align16(uint64_t v) { return (v + 15u) & ~(uint64_t)15u; }
 
+// q = rint(x * inv2eb) (binary32, half to even); an exception when |t| is
+// not below 2^23 (this also catches NaN and infinities, q forced to 0) or
+// when q * ebx2 misses x by more than eb_chk (q kept).
+__device__ __forceinline__ int32_t prequant(float x, float inv2eb, float ebx2, float eb_chk, bool &exc) {
+  const float t = __fmul_rn(x, inv2eb);
+  const bool ok = fabsf(t) < 8388608.0f;
+  const int32_t q = ok ? __float2int_rn(t) : 0;
+  const float r = __fmul_rn(__int2float_rn(q), ebx2);
+  const float d = fabsf(__fsub_rn(x, r));
+  exc = !ok || d > eb_chk;
+  return q;
+}
+
+// Selector network shape: 32 block features -> 64 hidden (ReLU) -> 4
+// predictor logits.  Parameter order in every weight array: W1[64][32],
+// b1[64], W2[4][64], b2[4].
+constexpr int kNFeat = 32, kNHid = 64, kNPred = 4;
+constexpr int kOffW1 = 0, kOffB1 = kNHid * kNFeat, kOffW2 = kOffB1 + kNHid, kOffB2 = kOffW2 + kNPred * kNHid;
+constexpr int kNWeights = kOffB2 + kNPred;  // 2372
+
+__device__ __forceinline__ uint16_t f32_to_bf16_rne(float f) {
+  uint32_t u = __float_as_uint(f);
+  u += 0x7fffu + ((u >> 16) & 1u);
+  return (uint16_t)(u >> 16);
+}
+__device__ __forceinline__ float bf16_to_f32(uint16_t h) { return __uint_as_float((uint32_t)h << 16); }
+
 // ---------------------------------------------------------------- workspace layout
 // Device scratch owned by the context for one compress call.
 struct CompressWs {
@@ -234,6 +261,7 @@ struct CompressWs {
   uint32_t *exc_idx;
   uint32_t *exc_val;
   uint64_t cap_list;       // floor(N/8)
+  uint8_t *ids;            // per block: predictor id (per-block selection only)
 };
 
 }  // namespace fz
@@ -260,4 +288,15 @@ cudaError_t launch_decode_prep(const uint8_t *d_in, const fz_header &h, const De
 cudaError_t launch_decode_main(const uint8_t *d_in, const fz_header &h, float *d_out, const DecodeWs &ws,
                                cudaStream_t s, int sm_count);
 cudaError_t launch_fill(float *out, uint64_t n, uint32_t bits, cudaStream_t s, int sm_count);
+cudaError_t launch_selquant(const float *x, const Geom &g, uint32_t R, uint32_t pred, const CompressWs &ws,
+                            const uint16_t *weights, cudaStream_t s, int sm_count);
+cudaError_t launch_select_report(const float *x, const Geom &g, uint32_t R, const CompressWs &ws, uint8_t *labels,
+                                 uint32_t *costs, uint16_t *feat, cudaStream_t s, int sm_count);
+cudaError_t launch_sel_decode(const uint8_t *d_in, const fz_header &h, float *d_out, const DecodeWs &ws,
+                              uint16_t *codes, cudaStream_t s, int sm_count);
+cudaError_t launch_mlp_grad(const float *w, const uint16_t *feat, const uint8_t *labels, uint32_t n,
+                            float *partial, float *grad, float *loss, cudaStream_t s);
+cudaError_t launch_adam(float *w, const float *grad, float *m, float *v, uint16_t *w_bf16, uint32_t step, float lr,
+                        float beta1, float beta2, float eps, cudaStream_t s);
+size_t mlp_partial_floats(uint32_t n);
 }  // namespace fz

@@ -38,19 +38,6 @@ struct TileShape<3> {
   static constexpr int BX = 8, BY = 8, BZ = 8, NB = 8, TX = 64, ROWS = 64, WPB = 1;
 };
 
-// q = rint(x * inv2eb) (binary32, half to even); an exception when |t| is
-// not below 2^23 (this also catches NaN and infinities, q forced to 0) or
-// when q * ebx2 misses x by more than eb_chk (q kept).
-__device__ __forceinline__ int32_t prequant(float x, float inv2eb, float ebx2, float eb_chk, bool &exc) {
-  const float t = __fmul_rn(x, inv2eb);
-  const bool ok = fabsf(t) < 8388608.0f;
-  const int32_t q = ok ? __float2int_rn(t) : 0;
-  const float r = __fmul_rn(__int2float_rn(q), ebx2);
-  const float d = fabsf(__fsub_rn(x, r));
-  exc = !ok || d > eb_chk;
-  return q;
-}
-
 template <int K>
 __device__ __forceinline__ int lz_coef(int o) {
   if (K == 1) return o == 0 ? 1 : -1;

@@ -1,0 +1,839 @@
+// fz_select.cu -- per-block predictor selection for 3D fields (the
+// auto-selection of modules that FZModules names as future work in §5, and
+// the dynamic module selection of §3.3.1), built on the prediction +
+// quantization module of §3.1.
+//
+// Each 8x8x8 block is predicted by one of four predictors: Lorenzo order 1
+// or 2, or in-block interpolation (linear or cubic; levels 4, 2, 1 with the
+// corner anchors o + {0,8}^3).  The choice comes from an exhaustive trial
+// (the predictor with the smallest trial cost) or from a small network
+// (32 block statistics -> 64 hidden -> 4 logits, bfloat16 weights, binary32
+// fmaf accumulation in a fixed order).  The 2-bit choice of every block goes
+// into the stream.
+//
+// Kernels:
+//   k_selquant   -- one warp per block of a 4096-value tile: prequantize,
+//                   gather the corner anchors, choose the predictor (or only
+//                   report labels, trial costs and features), then codes,
+//                   anchors, histogram and ordered outliers/exceptions like
+//                   the plain quantizer
+//   k_dec_codes  -- one thread per chunk: Huffman decode into a code buffer
+//   k_sel_recon  -- one warp per block: outlier scatter, anchor, inverse of
+//                   the block's predictor, dequantization, exceptions
+#include <string.h>
+
+#include "fz_decode_common.cuh"
+
+namespace fz {
+
+namespace {
+
+constexpr int kTX = 64, kTXP = 72, kRows = 64;  // tile: 8 blocks along x, rows (y, z)
+constexpr int kSelThreads = 256;
+
+enum SelMode : int { kSelFixed = 0, kSelExhaustive = 1, kSelNet = 2, kSelReport = 3 };
+
+// Per-warp view of one block inside the shared tile.
+struct BlockView {
+  const int32_t *sq;   // tile q, row (py + 8 pz), column (8 wb + px)
+  const int32_t *cq;   // q at the 8 corners o + 8 (cx, cy, cz), index cx + 2 cy + 4 cz
+  uint32_t cin;        // corner availability bits
+  int wb;              // block within the tile
+  uint32_t xlim, ylim, zlim;  // in-domain extent of the block (1..8 per axis)
+  __device__ __forceinline__ bool in(int px, int py, int pz) const {
+    return (uint32_t)px < xlim && (uint32_t)py < ylim && (uint32_t)pz < zlim;
+  }
+  __device__ __forceinline__ int32_t at(int px, int py, int pz) const {
+    return sq[(py + 8 * pz) * kTXP + 8 * wb + px];
+  }
+  // value and availability of a neighbourhood point during interpolation
+  __device__ __forceinline__ bool get(int x, int y, int z, int64_t &v) const {
+    if (x >= 0 && y >= 0 && z >= 0 && x < 8 && y < 8 && z < 8) {
+      if (!in(x, y, z)) return false;
+      v = at(x, y, z);
+      return true;
+    }
+    if ((x != 0 && x != 8) || (y != 0 && y != 8) || (z != 0 && z != 8)) return false;
+    const int c = (x >> 3) + 2 * (y >> 3) + 4 * (z >> 3);
+    if (!((cin >> c) & 1u)) return false;
+    v = cq[c];
+    return true;
+  }
+};
+
+template <int K>
+__device__ __forceinline__ int lzc(int o) {
+  if (K == 1) return o == 0 ? 1 : -1;
+  return o == 1 ? -2 : 1;
+}
+
+// Lorenzo-K residual (zero outside the block; the lower neighbours of an
+// in-domain point are in the domain).
+template <int K>
+__device__ __forceinline__ int32_t res_lorenzo(const BlockView &b, int px, int py, int pz) {
+  int32_t s = 0;
+#pragma unroll
+  for (int oz = 0; oz <= K; ++oz)
+#pragma unroll
+    for (int oy = 0; oy <= K; ++oy)
+#pragma unroll
+      for (int ox = 0; ox <= K; ++ox)
+        if (px >= ox && py >= oy && pz >= oz) s += lzc<K>(ox) * lzc<K>(oy) * lzc<K>(oz) * b.at(px - ox, py - oy, pz - oz);
+  return s;
+}
+
+// Level and pass axis of a non-origin block point.
+__device__ __forceinline__ void level_axis(int px, int py, int pz, int &s, int &a) {
+  const int v = px | py | pz;
+  s = (v & 1) ? 1 : ((v & 2) ? 2 : 4);
+  a = ((pz / s) & 1) ? 2 : (((py / s) & 1) ? 1 : 0);
+}
+
+// Interpolation prediction of a non-origin point from the values `b`
+// exposes (q during compression, reconstructed q during decompression).
+__device__ __forceinline__ int64_t interp_pred(const BlockView &b, bool cubic, int px, int py, int pz) {
+  int s, a;
+  level_axis(px, py, pz, s, a);
+  const int dx = a == 0 ? s : 0, dy = a == 1 ? s : 0, dz = a == 2 ? s : 0;
+  int64_t vm1 = 0, vp1 = 0, vm3 = 0, vp3 = 0;
+  const bool am1 = b.get(px - dx, py - dy, pz - dz, vm1);
+  const bool ap1 = b.get(px + dx, py + dy, pz + dz, vp1);
+  if (cubic) {
+    const bool am3 = b.get(px - 3 * dx, py - 3 * dy, pz - 3 * dz, vm3);
+    const bool ap3 = b.get(px + 3 * dx, py + 3 * dy, pz + 3 * dz, vp3);
+    if (am3 && am1 && ap1 && ap3) return (-vm3 + 9 * vm1 + 9 * vp1 - vp3 + 8) >> 4;
+  }
+  if (am1 && ap1) return (vm1 + vp1 + 1) >> 1;
+  return vm1;
+}
+
+// Residual of predictor pid at an in-domain point (the origin keeps q).
+__device__ __forceinline__ int32_t residual(const BlockView &b, int pid, int px, int py, int pz) {
+  if ((px | py | pz) == 0) return b.at(0, 0, 0);
+  switch (pid) {
+    case 0: return res_lorenzo<1>(b, px, py, pz);
+    case 1: return res_lorenzo<2>(b, px, py, pz);
+    default: return (int32_t)((int64_t)b.at(px, py, pz) - interp_pred(b, pid == 3, px, py, pz));
+  }
+}
+
+__device__ __forceinline__ uint32_t trial_bits(int32_t d, uint32_t R) {
+  const uint32_t a = (uint32_t)(d < 0 ? -d : d);
+  if (a >= R) return 96u;
+  return 1u + 2u * (31u - (uint32_t)__clz((int)(a + 1)));
+}
+
+__device__ __forceinline__ unsigned long long warp_sum64(unsigned long long v) {
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+  return v;
+}
+__device__ __forceinline__ unsigned long long warp_max64(unsigned long long v) {
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    const unsigned long long o = __shfl_xor_sync(0xffffffffu, v, off);
+    v = o > v ? o : v;
+  }
+  return v;
+}
+__device__ __forceinline__ long long warp_min_s64(long long v) {
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    const long long o = __shfl_xor_sync(0xffffffffu, v, off);
+    v = o < v ? o : v;
+  }
+  return v;
+}
+__device__ __forceinline__ long long warp_max_s64(long long v) {
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    const long long o = __shfl_xor_sync(0xffffffffu, v, off);
+    v = o > v ? o : v;
+  }
+  return v;
+}
+__device__ __forceinline__ unsigned long long uabs64(long long v) {
+  return (unsigned long long)(v < 0 ? -v : v);
+}
+
+// Trial costs of the four predictors (every lane gets all four).
+__device__ void block_costs(const BlockView &b, uint32_t R, uint32_t cost[kNPred]) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int k = 0; k < kNPred; ++k) {
+    uint32_t c = 0;
+    for (int i = 0; i < 16; ++i) {
+      const int p = 32 * i + lane;
+      const int px = p & 7, py = (p >> 3) & 7, pz = p >> 6;
+      if (p == 0 || !b.in(px, py, pz)) continue;
+      c += trial_bits(residual(b, k, px, py, pz), R);
+    }
+    cost[k] = (uint32_t)warp_sum64(c);
+  }
+}
+
+__device__ __forceinline__ float log2fix(unsigned long long s) {
+  const unsigned long long v = s + 1;
+  const int e = 63 - __clzll((long long)v);
+  const unsigned long long m = e >= 4 ? (v >> (e - 4)) & 15ull : (v << (4 - e)) & 15ull;
+  return __fadd_rn((float)e, (float)m * 0.0625f);
+}
+
+// The 32 block statistics (see the selector's definition: sums and maxima
+// of predictor residuals on the 64 all-odd points, difference sums, sign
+// changes, spread, corner availability, size, anchor) -> bfloat16 features.
+// Returns this lane's feature (lane f holds feature f).
+__device__ uint16_t block_feature(const BlockView &b, uint32_t R) {
+  const int lane = threadIdx.x & 31;
+  unsigned long long st[kNFeat];
+#pragma unroll
+  for (int f = 0; f < kNFeat; ++f) st[f] = 0;
+  // predictor residuals on the odd sub-lattice: points lane and lane + 32
+#pragma unroll
+  for (int k = 0; k < kNPred; ++k) {
+    unsigned long long sum = 0, mx = 0, outl = 0;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int o = lane + 32 * h;
+      const int px = 2 * (o & 3) + 1, py = 2 * ((o >> 2) & 3) + 1, pz = 2 * (o >> 4) + 1;
+      if (!b.in(px, py, pz)) continue;
+      const unsigned long long a = uabs64(residual(b, k, px, py, pz));
+      sum += a;
+      mx = a > mx ? a : mx;
+      outl += a >= R ? 1 : 0;
+    }
+    st[2 * k] = warp_sum64(sum);
+    st[2 * k + 1] = warp_max64(mx);
+    if (k == 0) st[25] = warp_sum64(outl);
+  }
+  long long qsum = 0, qmn = 0x7fffffffffffffffll, qmx = -0x7fffffffffffffffll - 1;
+  unsigned long long n = 0;
+  unsigned long long d1[3] = {0, 0, 0}, d2[3] = {0, 0, 0}, d3[3] = {0, 0, 0}, mix[3] = {0, 0, 0}, sc[3] = {0, 0, 0};
+  unsigned long long x2 = 0;
+  for (int i = 0; i < 16; ++i) {
+    const int p = 32 * i + lane;
+    const int c[3] = {p & 7, (p >> 3) & 7, p >> 6};
+    if (!b.in(c[0], c[1], c[2])) continue;
+    const long long q = b.at(c[0], c[1], c[2]);
+    qsum += q;
+    qmn = q < qmn ? q : qmn;
+    qmx = q > qmx ? q : qmx;
+    ++n;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      int e[3] = {0, 0, 0};
+      e[a] = 1;
+      if (c[a] >= 1) {
+        const long long q1 = b.at(c[0] - e[0], c[1] - e[1], c[2] - e[2]);
+        const long long dd1 = q - q1;
+        d1[a] += uabs64(dd1);
+        if (c[a] >= 2) {
+          const long long q2 = b.at(c[0] - 2 * e[0], c[1] - 2 * e[1], c[2] - 2 * e[2]);
+          const long long dd1p = q1 - q2;
+          d2[a] += uabs64(dd1 - dd1p);
+          sc[a] += ((dd1 > 0 && dd1p < 0) || (dd1 < 0 && dd1p > 0)) ? 1 : 0;
+          if (c[a] >= 3) {
+            const long long q3 = b.at(c[0] - 3 * e[0], c[1] - 3 * e[1], c[2] - 3 * e[2]);
+            d3[a] += uabs64(dd1 - 2 * dd1p + (q2 - q3));
+          }
+        }
+      }
+    }
+    const int pa[3] = {0, 0, 1}, pb[3] = {1, 2, 2};
+#pragma unroll
+    for (int pr = 0; pr < 3; ++pr) {
+      const int a = pa[pr], bb = pb[pr];
+      if (c[a] >= 1 && c[bb] >= 1) {
+        int ea[3] = {0, 0, 0}, eb[3] = {0, 0, 0};
+        ea[a] = 1;
+        eb[bb] = 1;
+        const long long m = q - b.at(c[0] - ea[0], c[1] - ea[1], c[2] - ea[2]) -
+                            b.at(c[0] - eb[0], c[1] - eb[1], c[2] - eb[2]) +
+                            b.at(c[0] - ea[0] - eb[0], c[1] - ea[1] - eb[1], c[2] - ea[2] - eb[2]);
+        mix[pr] += uabs64(m);
+      }
+    }
+    if (c[0] >= 2) x2 += uabs64(q - b.at(c[0] - 2, c[1], c[2]));
+  }
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    st[8 + a] = warp_sum64(d1[a]);
+    st[11 + a] = warp_sum64(d2[a]);
+    st[14 + a] = warp_sum64(d3[a]);
+    st[17 + a] = warp_sum64(mix[a]);
+    st[20 + a] = warp_sum64(sc[a]);
+  }
+  st[31] = warp_sum64(x2);
+  const long long total = (long long)warp_sum64((unsigned long long)qsum);
+  const long long nn = (long long)warp_sum64(n);
+  long long mean = total / nn;
+  if ((total % nn) != 0 && total < 0) mean -= 1;
+  unsigned long long dev = 0;
+  for (int i = 0; i < 16; ++i) {
+    const int p = 32 * i + lane;
+    const int px = p & 7, py = (p >> 3) & 7, pz = p >> 6;
+    if (b.in(px, py, pz)) dev += uabs64((long long)b.at(px, py, pz) - mean);
+  }
+  st[23] = warp_sum64(dev);
+  st[24] = (unsigned long long)(warp_max_s64(qmx) - warp_min_s64(qmn));
+  st[26] = (b.cin >> 1) & 1u;
+  st[27] = (b.cin >> 2) & 1u;
+  st[28] = (b.cin >> 4) & 1u;
+  st[29] = (unsigned long long)nn;
+  st[30] = uabs64(b.at(0, 0, 0));
+  unsigned long long mine = 0;
+#pragma unroll
+  for (int f = 0; f < kNFeat; ++f) mine = (lane == f) ? st[f] : mine;
+  return f32_to_bf16_rne(log2fix(mine));
+}
+
+// Exact network inference: lane l computes hidden units l and l + 32,
+// lanes 0..3 the logits, each with fmaf in index order.  Returns the
+// argmax (ties to the lowest id) in every lane.
+__device__ int mlp_choose(const float *w, uint16_t feat_lane) {
+  const int lane = threadIdx.x & 31;
+  const float f = bf16_to_f32(feat_lane);
+  float h[2];
+#pragma unroll
+  for (int u = 0; u < 2; ++u) {
+    const int j = lane + 32 * u;
+    float acc = w[kOffB1 + j];
+#pragma unroll 8
+    for (int k = 0; k < kNFeat; ++k) acc = __fmaf_rn(w[kOffW1 + j * kNFeat + k], __shfl_sync(0xffffffffu, f, k), acc);
+    acc = acc > 0.0f ? acc : 0.0f;
+    h[u] = bf16_to_f32(f32_to_bf16_rne(acc));
+  }
+  float lg = 0.0f;
+  {
+    const int i = lane < kNPred ? lane : 0;
+    float acc = w[kOffB2 + i];
+    for (int j = 0; j < kNHid; ++j) {
+      const float hj = __shfl_sync(0xffffffffu, h[j >> 5], j & 31);
+      acc = __fmaf_rn(w[kOffW2 + i * kNHid + j], hj, acc);
+    }
+    lg = acc;
+  }
+  int best = 0;
+  float bv = __shfl_sync(0xffffffffu, lg, 0);
+#pragma unroll
+  for (int i = 1; i < kNPred; ++i) {
+    const float v = __shfl_sync(0xffffffffu, lg, i);
+    if (v > bv) { bv = v; best = i; }
+  }
+  return best;
+}
+
+struct SelOut {
+  uint8_t *labels;            // report mode: exhaustive label per block
+  uint32_t *costs;            // report mode: 4 trial costs per block (may be null)
+  uint16_t *feat;             // report mode: 32 bfloat16 features per block (may be null)
+  const uint16_t *weights;    // network mode: bfloat16 weights
+};
+
+struct SelSmem {
+  int32_t sq[kRows * kTXP];
+  uint8_t sexc[kTileElems];
+  uint32_t shist[kMaxSym];
+  int32_t cq[8][8];
+  uint32_t cin[8];
+  float w[kNWeights];
+  uint32_t wout[8], wexc[8];
+  uint32_t oslot, eslot;
+  int pid[8];
+};
+
+template <int MODE>
+__global__ void __launch_bounds__(kSelThreads) k_selquant(const float *__restrict__ x, Geom g, uint32_t R,
+                                                           uint32_t fixed_pid, CompressWs ws, SelOut so) {
+  extern __shared__ __align__(16) unsigned char sel_smem[];
+  SelSmem &sm = *reinterpret_cast<SelSmem *>(sel_smem);
+  Ctl *ctl = ws.ctl;
+  if (ctl->mode != kModeNormal) return;
+  const float inv2eb = ctl->inv2eb, ebx2 = ctl->ebx2, eb_chk = ctl->eb_chk;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  for (int s = tid; s < kMaxSym; s += kSelThreads) sm.shist[s] = 0;
+  if (MODE == kSelNet)
+    for (int i = tid; i < kNWeights; i += kSelThreads) sm.w[i] = bf16_to_f32(so.weights[i]);
+  __syncthreads();
+
+  for (uint64_t tile = blockIdx.x; tile < g.n_qtiles; tile += gridDim.x) {
+    const uint32_t t32 = (uint32_t)tile;
+    const uint32_t tx = t32 % g.tiles_x, rest = t32 / g.tiles_x;
+    const uint32_t by = rest % g.nby, bz = rest / g.nby;
+    const uint32_t x0 = tx * kTX, y0 = by * 8, z0 = bz * 8;
+    // ---- load + prequantize the tile (row-major, 4 values per thread per step)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int e = 4 * (tid + kSelThreads * j);
+      const int row = e / kTX, col = e % kTX;
+      const uint32_t X = x0 + col, Y = y0 + (row & 7), Z = z0 + (row >> 3);
+      const bool inrow = Y < g.ny && Z < g.nz;
+      const uint64_t fi = ((uint64_t)Z * g.ny + Y) * g.nx + X;
+      uint32_t ex = 0;
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const bool in = inrow && X + u < g.nx;
+        bool ee = false;
+        const int32_t q = in ? prequant(x[fi + u], inv2eb, ebx2, eb_chk, ee) : 0;
+        sm.sq[row * kTXP + col + u] = q;
+        ex |= (uint32_t)(in && ee) << (8 * u);
+      }
+      *reinterpret_cast<uint32_t *>(&sm.sexc[e]) = ex;
+    }
+    // ---- corner anchors of every block: q at o + 8 (cx, cy, cz)
+    {
+      const int wb = warp, c = lane;
+      if (c < 8) {
+        const uint64_t X = (uint64_t)x0 + 8 * wb + 8 * (c & 1), Y = y0 + 8 * ((c >> 1) & 1), Z = z0 + 8 * (c >> 2);
+        const bool in = X < g.nx && Y < g.ny && Z < g.nz;
+        bool ee;
+        sm.cq[wb][c] = in ? prequant(x[(Z * g.ny + Y) * g.nx + X], inv2eb, ebx2, eb_chk, ee) : 0;
+        const uint32_t bits = __ballot_sync(0x000000ffu, in);
+        if (c == 0) sm.cin[wb] = bits & 0xffu;
+      }
+    }
+    __syncthreads();
+
+    // ---- one warp per block: choose, then codes
+    const int wb = warp;
+    const uint32_t bxi = tx * 8 + wb;
+    const bool bvalid = bxi < g.nbx;
+    const uint64_t blk = (uint64_t)bxi + (uint64_t)g.nbx * (by + (uint64_t)g.nby * bz);
+    BlockView b;
+    b.sq = sm.sq;
+    b.cq = sm.cq[wb];
+    b.cin = sm.cin[wb];
+    b.wb = wb;
+    b.xlim = g.nx - x0 - 8 * wb < 8 ? g.nx - x0 - 8 * wb : 8;
+    b.ylim = g.ny - y0 < 8 ? g.ny - y0 : 8;
+    b.zlim = g.nz - z0 < 8 ? g.nz - z0 : 8;
+    uint32_t nout = 0, nexc = 0;
+    if (bvalid) {
+      int pid = (int)fixed_pid;
+      if (MODE == kSelExhaustive || MODE == kSelReport) {
+        uint32_t cost[kNPred];
+        block_costs(b, R, cost);
+        pid = 0;
+#pragma unroll
+        for (int k = 1; k < kNPred; ++k)
+          if (cost[k] < cost[pid]) pid = k;
+        if (MODE == kSelReport) {
+          if (lane == 0) so.labels[blk] = (uint8_t)pid;
+          if (so.costs && lane < kNPred) so.costs[blk * kNPred + lane] = cost[lane];
+        }
+      }
+      if (MODE == kSelNet || (MODE == kSelReport && so.feat)) {
+        const uint16_t f = block_feature(b, R);
+        if (MODE == kSelReport) so.feat[blk * kNFeat + lane] = f;
+        else pid = mlp_choose(sm.w, f);
+      }
+      if (MODE != kSelReport) {
+        if (lane == 0) { ws.ids[blk] = (uint8_t)pid; sm.pid[wb] = pid; }
+        uint16_t *cdst = ws.codes + blk * 512;
+        for (int i = 0; i < 16; ++i) {
+          const int p = 32 * i + lane;
+          const int px = p & 7, py = (p >> 3) & 7, pz = p >> 6;
+          const bool in = b.in(px, py, pz);
+          uint32_t code = R;
+          if (in) {
+            const int32_t d = residual(b, pid, px, py, pz);
+            if (p == 0) ws.anchors[blk] = d;
+            else {
+              const uint32_t c = (uint32_t)(d + (int32_t)R);
+              const bool o = (c - 1u) >= 2u * R - 1u;
+              code = o ? 0u : c;
+              nout += o;
+            }
+            nexc += sm.sexc[(py + 8 * pz) * kTX + 8 * wb + px] ? 1u : 0u;
+          }
+          cdst[p] = (uint16_t)code;
+          atomicAdd(&sm.shist[code], 1u);
+        }
+      }
+    }
+    if (MODE == kSelReport) {
+      __syncthreads();
+      continue;
+    }
+    // ---- ordered outliers / exceptions (warp = block, position order)
+    nout = __reduce_add_sync(0xffffffffu, nout);
+    nexc = __reduce_add_sync(0xffffffffu, nexc);
+    if (lane == 0) { sm.wout[warp] = nout; sm.wexc[warp] = nexc; }
+    if (__syncthreads_or((nout | nexc) != 0)) {
+      if (tid == 0) {
+        uint32_t to = 0, te = 0;
+        for (int w = 0; w < 8; ++w) { to += sm.wout[w]; te += sm.wexc[w]; }
+        const unsigned long long os = to ? atomicAdd(&ctl->n_out, (unsigned long long)to) : 0ull;
+        const unsigned long long es = te ? atomicAdd(&ctl->n_exc, (unsigned long long)te) : 0ull;
+        ws.tinfo[tile] = make_uint4(to, te, (uint32_t)os, (uint32_t)es);
+        const uint64_t grp = tile / kTileGroup;
+        if (to) atomicAdd(&ws.tgroup[grp].x, to);
+        if (te) atomicAdd(&ws.tgroup[grp].y, te);
+        sm.oslot = (uint32_t)os;
+        sm.eslot = (uint32_t)es;
+      }
+      __syncthreads();
+      uint32_t oo = sm.oslot, eo = sm.eslot;
+      for (int w = 0; w < warp; ++w) { oo += sm.wout[w]; eo += sm.wexc[w]; }
+      if (bvalid && (nout | nexc)) {
+        const int pid = sm.pid[wb];
+        for (int i = 0; i < 16; ++i) {
+          const int p = 32 * i + lane;
+          const int px = p & 7, py = (p >> 3) & 7, pz = p >> 6;
+          const bool in = b.in(px, py, pz);
+          const uint32_t pos = (uint32_t)(blk * 512 + p);
+          int32_t d = 0;
+          bool outl = false;
+          if (in && p != 0) {
+            d = residual(b, pid, px, py, pz);
+            const uint32_t c = (uint32_t)(d + (int32_t)R);
+            outl = (c - 1u) >= 2u * R - 1u;
+          }
+          uint32_t m = __ballot_sync(0xffffffffu, outl);
+          if (outl) {
+            const uint64_t o = (uint64_t)oo + __popc(m & ((1u << lane) - 1));
+            if (o < ws.cap_list) { ws.out_idx[o] = pos; ws.out_val[o] = d; }
+          }
+          oo += __popc(m);
+          const bool e = in && sm.sexc[(py + 8 * pz) * kTX + 8 * wb + px];
+          m = __ballot_sync(0xffffffffu, e);
+          if (e) {
+            const uint64_t o = (uint64_t)eo + __popc(m & ((1u << lane) - 1));
+            const uint64_t fi = ((uint64_t)(z0 + pz) * g.ny + (y0 + py)) * g.nx + (x0 + 8 * wb + px);
+            if (o < ws.cap_list) { ws.exc_idx[o] = pos; ws.exc_val[o] = __float_as_uint(x[fi]); }
+          }
+          eo += __popc(m);
+        }
+      }
+    }
+    __syncthreads();
+  }
+  for (int s = tid; s < (int)(2 * R); s += kSelThreads)
+    if (sm.shist[s]) atomicAdd(&ctl->hist[s], (unsigned long long)sm.shist[s]);
+}
+
+template <int MODE>
+cudaError_t launch_sel_t(const float *x, const Geom &g, uint32_t R, uint32_t pid, const CompressWs &ws,
+                         const SelOut &so, cudaStream_t s, int sms) {
+  const int smem = (int)sizeof(SelSmem);
+  cudaError_t e = cudaFuncSetAttribute(k_selquant<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e != cudaSuccess) return e;
+  int per_sm = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_selquant<MODE>, kSelThreads, smem);
+  if (e != cudaSuccess) return e;
+  if (per_sm < 1) per_sm = 1;
+  uint64_t grid = (uint64_t)sms * per_sm;
+  if (grid > g.n_qtiles) grid = g.n_qtiles;
+  k_selquant<MODE><<<(unsigned)grid, kSelThreads, smem, s>>>(x, g, R, pid, ws, so);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- decoding
+struct SelDecParams {
+  const uint32_t *words;
+  uint64_t n_words;
+  const uint32_t *chunk_bits;
+  const uint64_t *goff;
+  uint64_t n_chunks, n_groups;
+  const uint16_t *lut;
+  uint16_t *codes;
+  uint32_t *err;
+};
+
+__device__ __forceinline__ void sel_err(uint32_t *err, uint32_t code) { atomicCAS(err, 0u, code); }
+
+// Phase 1: one thread per chunk (= block), codes written row by row.
+__global__ void __launch_bounds__(kDecThreads) k_dec_codes(SelDecParams p) {
+  extern __shared__ __align__(16) unsigned char dc_smem[];
+  uint16_t *slut = reinterpret_cast<uint16_t *>(dc_smem);
+  uint32_t *sring = reinterpret_cast<uint32_t *>(dc_smem + sizeof(uint16_t) * kLutSize);
+  __shared__ unsigned long long swarp[kDecThreads / 32];
+  const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+  {
+    const uint4 *src = reinterpret_cast<const uint4 *>(p.lut);
+    uint4 *dst = reinterpret_cast<uint4 *>(slut);
+    for (int i = t; i < kLutSize / 8; i += kDecThreads) dst[i] = __ldg(src + i);
+  }
+  for (uint64_t grp = blockIdx.x; grp < p.n_groups; grp += gridDim.x) {
+    const uint64_t j = grp * kDecThreads + t;
+    const bool valid = j < p.n_chunks;
+    const uint32_t cb = valid ? __ldg(p.chunk_bits + j) : 0u;
+    unsigned long long incl = cb;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+      const unsigned long long v = __shfl_up_sync(0xffffffffu, incl, off);
+      if (lane >= off) incl += v;
+    }
+    __syncthreads();
+    if (lane == 31) swarp[warp] = incl;
+    __syncthreads();
+    unsigned long long start = p.goff[grp] + incl - cb;
+    for (int w = 0; w < warp; ++w) start += swarp[w];
+    if (!valid) continue;
+    BitReader br;
+    br.init(p.words, p.n_words, start, cb, sring + t);
+    const uint32_t start_off = br.off;
+    uint4 *dst = reinterpret_cast<uint4 *>(p.codes + j * 512);
+#pragma unroll 1
+    for (int r = 0; r < 64; ++r) {
+      uint32_t c[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) c[u] = br.next(slut);
+      dst[r] = make_uint4(c[0] | (c[1] << 16), c[2] | (c[3] << 16), c[4] | (c[5] << 16), c[6] | (c[7] << 16));
+    }
+    asm volatile("cp.async.wait_all;\n" ::: "memory");
+    if (br.consumed(start_off) != cb || !(br.vall & kLutValid)) sel_err(p.err, FZ_ECORRUPT);
+  }
+}
+
+struct ReconParams {
+  const uint16_t *codes;
+  const int32_t *anchors;
+  const uint8_t *ids;       // packed 2-bit ids, or null for a fixed predictor
+  uint32_t fixed_pid;
+  const uint32_t *out_idx;
+  const int32_t *out_val;
+  const uint32_t *exc_idx;
+  const uint32_t *exc_val;
+  uint64_t n_out, n_exc;
+  float *out;
+  float ebx2;
+  int32_t R;
+  uint32_t *err;
+};
+
+__device__ __forceinline__ uint64_t lb_u32(const uint32_t *a, uint64_t n, uint32_t key) {
+  uint64_t lo = 0, hi = n;
+  while (lo < hi) {
+    const uint64_t mid = (lo + hi) >> 1;
+    if (__ldg(a + mid) < key) lo = mid + 1; else hi = mid;
+  }
+  return lo;
+}
+
+constexpr int kReconWarps = 8;
+
+// Phase 2: one warp per block.  The block's q is rebuilt in shared memory.
+__global__ void __launch_bounds__(kReconWarps * 32) k_sel_recon(ReconParams rp, Geom g) {
+  __shared__ int32_t sq[kReconWarps][512];
+  __shared__ int32_t scq[kReconWarps][8];
+  __shared__ uint32_t sov[kReconWarps][512];
+  __shared__ uint32_t smask[kReconWarps][16];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const uint64_t nwarps = (uint64_t)gridDim.x * kReconWarps;
+  for (uint64_t blk = (uint64_t)blockIdx.x * kReconWarps + w; blk < g.n_blocks; blk += nwarps) {
+    const uint32_t bxi = (uint32_t)(blk % g.nbx);
+    const uint64_t br_ = blk / g.nbx;
+    const uint32_t byi = (uint32_t)(br_ % g.nby), bzi = (uint32_t)(br_ / g.nby);
+    const uint32_t X0 = 8 * bxi, Y0 = 8 * byi, Z0 = 8 * bzi;
+    const uint32_t xl = g.nx - X0 < 8 ? g.nx - X0 : 8, yl = g.ny - Y0 < 8 ? g.ny - Y0 : 8,
+                   zl = g.nz - Z0 < 8 ? g.nz - Z0 : 8;
+    const uint32_t pos0 = (uint32_t)(blk * 512);
+    const int pid = rp.ids ? (rp.ids[blk >> 2] >> (2 * (blk & 3))) & 3 : (int)rp.fixed_pid;
+    // corner anchors (origins of the neighbouring blocks)
+    uint32_t cin = 0;
+    if (lane < 8) {
+      const uint64_t cx = bxi + (lane & 1), cy = byi + ((lane >> 1) & 1), cz = bzi + (lane >> 2);
+      const bool in = cx < g.nbx && cy < g.nby && cz < g.nbz;
+      scq[w][lane] = in ? __ldg(rp.anchors + (cz * g.nby + cy) * g.nbx + cx) : 0;
+    }
+    {
+      const uint64_t cx = bxi + (lane & 1), cy = byi + ((lane >> 1) & 1), cz = bzi + ((lane >> 2) & 1);
+      cin = __ballot_sync(0xffffffffu, lane < 8 && cx < g.nbx && cy < g.nby && cz < g.nbz) & 0xffu;
+    }
+    // residuals, with outliers scattered in position order
+    uint64_t obase = 0;
+    if (lane == 0 && rp.n_out) obase = lb_u32(rp.out_idx, rp.n_out, pos0);
+    obase = __shfl_sync(0xffffffffu, obase, 0);
+    bool bad = false;
+    uint32_t orank = 0;
+    for (int i = 0; i < 16; ++i) {
+      const int p = 32 * i + lane;
+      const uint32_t code = __ldg(rp.codes + pos0 + p);
+      const bool isout = code == 0;
+      const uint32_t m = __ballot_sync(0xffffffffu, isout);
+      int32_t d = (int32_t)code - rp.R;
+      if (isout) {
+        const uint64_t k = obase + orank + __popc(m & ((1u << lane) - 1));
+        if (k < rp.n_out && __ldg(rp.out_idx + k) == pos0 + p) d = __ldg(rp.out_val + k);
+        else { bad = true; d = 0; }
+      }
+      orank += __popc(m);
+      if (p == 0) d += __ldg(rp.anchors + blk);
+      sq[w][p] = d;
+      sov[w][p] = 0;
+    }
+    if (lane < 16) smask[w][lane] = 0;
+    __syncwarp();
+    BlockView b;
+    b.sq = nullptr;
+    b.cq = scq[w];
+    b.cin = cin;
+    b.wb = 0;
+    b.xlim = xl;
+    b.ylim = yl;
+    b.zlim = zl;
+    if (pid < 2) {
+      // K inclusive prefix sums along x, y, z (lanes own two lines each)
+      for (int rep = 0; rep <= pid; ++rep) {
+        for (int axis = 0; axis < 3; ++axis) {
+          const int stride = axis == 0 ? 1 : (axis == 1 ? 8 : 64);
+#pragma unroll
+          for (int h = 0; h < 2; ++h) {
+            const int line = lane + 32 * h;  // 64 lines of 8 along the axis
+            int base;
+            if (axis == 0) base = line * 8;
+            else if (axis == 1) base = (line & 7) + 64 * (line >> 3);
+            else base = line;
+            int32_t acc = 0;
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+              acc += sq[w][base + k * stride];
+              sq[w][base + k * stride] = acc;
+            }
+          }
+          __syncwarp();
+        }
+      }
+    } else {
+      // interpolation: passes in order, each pass's points are independent
+      const bool cubic = pid == 3;
+      for (int s = 4; s >= 1; s >>= 1)
+        for (int a = 0; a < 3; ++a) {
+          for (int i = 0; i < 16; ++i) {
+            const int p = 32 * i + lane;
+            const int c[3] = {p & 7, (p >> 3) & 7, p >> 6};
+            bool ok = p != 0 && (c[a] % (2 * s)) == s;
+#pragma unroll
+            for (int bb = 0; bb < 3; ++bb) {
+              if (bb < a && c[bb] % s != 0) ok = false;
+              if (bb > a && c[bb] % (2 * s) != 0) ok = false;
+            }
+            if (!ok || !b.in(c[0], c[1], c[2])) continue;
+            // predict from the reconstructed values of earlier passes
+            int sl, al;
+            level_axis(c[0], c[1], c[2], sl, al);
+            const int dx = al == 0 ? sl : 0, dy = al == 1 ? sl : 0, dz = al == 2 ? sl : 0;
+            auto get = [&](int xx, int yy, int zz, int64_t &val) -> bool {
+              if (xx >= 0 && yy >= 0 && zz >= 0 && xx < 8 && yy < 8 && zz < 8) {
+                if (!b.in(xx, yy, zz)) return false;
+                val = sq[w][(zz * 8 + yy) * 8 + xx];
+                return true;
+              }
+              if ((xx != 0 && xx != 8) || (yy != 0 && yy != 8) || (zz != 0 && zz != 8)) return false;
+              const int cc = (xx >> 3) + 2 * (yy >> 3) + 4 * (zz >> 3);
+              if (!((cin >> cc) & 1u)) return false;
+              val = scq[w][cc];
+              return true;
+            };
+            int64_t vm1 = 0, vp1 = 0, vm3 = 0, vp3 = 0, pred;
+            const bool am1 = get(c[0] - dx, c[1] - dy, c[2] - dz, vm1);
+            const bool ap1 = get(c[0] + dx, c[1] + dy, c[2] + dz, vp1);
+            const bool am3 = cubic && get(c[0] - 3 * dx, c[1] - 3 * dy, c[2] - 3 * dz, vm3);
+            const bool ap3 = cubic && get(c[0] + 3 * dx, c[1] + 3 * dy, c[2] + 3 * dz, vp3);
+            if (cubic && am3 && am1 && ap1 && ap3) pred = (-vm3 + 9 * vm1 + 9 * vp1 - vp3 + 8) >> 4;
+            else if (am1 && ap1) pred = (vm1 + vp1 + 1) >> 1;
+            else pred = vm1;
+            sq[w][p] = (int32_t)(sq[w][p] + pred);
+          }
+          __syncwarp();
+        }
+    }
+    // exceptions of this block into a per-warp override table
+    if (rp.n_exc) {
+      uint64_t e0 = 0, e1 = 0;
+      if (lane == 0) {
+        e0 = lb_u32(rp.exc_idx, rp.n_exc, pos0);
+        e1 = lb_u32(rp.exc_idx, rp.n_exc, pos0 + 512);
+      }
+      e0 = __shfl_sync(0xffffffffu, e0, 0);
+      e1 = __shfl_sync(0xffffffffu, e1, 0);
+      for (uint64_t k = e0 + lane; k < e1; k += 32) {
+        const uint32_t p = __ldg(rp.exc_idx + k) - pos0;
+        sov[w][p] = __ldg(rp.exc_val + k);
+        atomicOr(&smask[w][p >> 5], 1u << (p & 31));
+      }
+      __syncwarp();
+    }
+    // dequantize and store (lane i of step k: point 32 k + i)
+    for (int i = 0; i < 16; ++i) {
+      const int p = 32 * i + lane;
+      const int px = p & 7, py = (p >> 3) & 7, pz = p >> 6;
+      if (!b.in(px, py, pz)) continue;
+      float v = __fmul_rn(__int2float_rn(sq[w][p]), rp.ebx2);
+      if ((smask[w][p >> 5] >> (p & 31)) & 1u) v = __uint_as_float(sov[w][p]);
+      rp.out[((uint64_t)(Z0 + pz) * g.ny + (Y0 + py)) * g.nx + (X0 + px)] = v;
+    }
+    if (__any_sync(0xffffffffu, bad) && lane == 0) sel_err(rp.err, FZ_ECORRUPT);
+    __syncwarp();
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_selquant(const float *x, const Geom &g, uint32_t R, uint32_t pred, const CompressWs &ws,
+                            const uint16_t *weights, cudaStream_t s, int sm_count) {
+  SelOut so = {};
+  so.weights = weights;
+  switch (pred) {
+    case FZ_SEL_MLP: return launch_sel_t<kSelNet>(x, g, R, 0, ws, so, s, sm_count);
+    case FZ_SEL_EXHAUSTIVE: return launch_sel_t<kSelExhaustive>(x, g, R, 0, ws, so, s, sm_count);
+    default: return launch_sel_t<kSelFixed>(x, g, R, pred, ws, so, s, sm_count);
+  }
+}
+
+cudaError_t launch_select_report(const float *x, const Geom &g, uint32_t R, const CompressWs &ws, uint8_t *labels,
+                                 uint32_t *costs, uint16_t *feat, cudaStream_t s, int sm_count) {
+  SelOut so = {};
+  so.labels = labels;
+  so.costs = costs;
+  so.feat = feat;
+  return launch_sel_t<kSelReport>(x, g, R, 0, ws, so, s, sm_count);
+}
+
+cudaError_t launch_sel_decode(const uint8_t *d_in, const fz_header &h, float *d_out, const DecodeWs &ws,
+                              uint16_t *codes, cudaStream_t s, int sm_count) {
+  Geom g;
+  make_geom(h.ndim, h.dims, g);
+  SelDecParams p;
+  p.words = reinterpret_cast<const uint32_t *>(d_in + h.off_bits);
+  p.n_words = (h.total_bits + 31) / 32;
+  p.chunk_bits = reinterpret_cast<const uint32_t *>(d_in + h.off_chunk_bits);
+  p.goff = ws.gsum;
+  p.n_chunks = h.n_chunks;
+  p.n_groups = (h.n_chunks + kDecThreads - 1) / kDecThreads;
+  p.lut = ws.lut;
+  p.codes = codes;
+  p.err = ws.err;
+  const int smem = (int)(sizeof(uint16_t) * kLutSize + sizeof(uint32_t) * kRing * kDecThreads);
+  cudaError_t e = cudaFuncSetAttribute(k_dec_codes, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e != cudaSuccess) return e;
+  int per_sm = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_dec_codes, kDecThreads, smem);
+  if (e != cudaSuccess) return e;
+  uint64_t grid = (uint64_t)sm_count * (per_sm > 0 ? per_sm : 1);
+  if (grid > p.n_groups) grid = p.n_groups;
+  k_dec_codes<<<(unsigned)grid, kDecThreads, smem, s>>>(p);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  ReconParams rp;
+  rp.codes = codes;
+  rp.anchors = reinterpret_cast<const int32_t *>(d_in + h.off_anchors);
+  rp.ids = (h.flags & FZ_FLAG_IDS) ? d_in + h.off_ids : nullptr;
+  rp.fixed_pid = h.predictor;
+  rp.out_idx = reinterpret_cast<const uint32_t *>(d_in + h.off_out_idx);
+  rp.out_val = reinterpret_cast<const int32_t *>(d_in + h.off_out_val);
+  rp.exc_idx = reinterpret_cast<const uint32_t *>(d_in + h.off_exc_idx);
+  rp.exc_val = reinterpret_cast<const uint32_t *>(d_in + h.off_exc_val);
+  rp.n_out = h.n_out;
+  rp.n_exc = h.n_exc;
+  rp.out = d_out;
+  memcpy(&rp.ebx2, &h.ebx2_bits, 4);
+  rp.R = (int32_t)h.radius;
+  rp.err = ws.err;
+  uint64_t rgrid = (g.n_blocks + kReconWarps - 1) / kReconWarps;
+  if (rgrid > (uint64_t)sm_count * 16) rgrid = (uint64_t)sm_count * 16;
+  k_sel_recon<<<(unsigned)rgrid, kReconWarps * 32, 0, s>>>(rp, g);
+  return cudaGetLastError();
+}
+
+}  // namespace fz
