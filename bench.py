@@ -192,7 +192,7 @@ def run_fz(args, rank, world, local_rank):
     for _ in range(args.warmup):
         compress()
         decompress()
-    prof = fz_profile_t()
+    prof = fz.Profile()
     stages_c, stages_d = {}, {}
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
            torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
@@ -312,15 +312,9 @@ def run_fz(args, rank, world, local_rank):
     ctx.close()
 
 
-class fz_profile_t(C.Structure):
-    _fields_ = [("n_compress", C.c_uint32), ("n_decompress", C.c_uint32),
-                ("compress_names", (C.c_char * 16) * 12), ("compress_ms", C.c_float * 12),
-                ("decompress_names", (C.c_char * 16) * 12), ("decompress_ms", C.c_float * 12),
-                ("launches", C.c_uint64)]
-
-
 def _launches(L, ctx):
-    p = fz_profile_t()
+    import paper_2509_20563_gb300 as fz
+    p = fz.Profile()
     L.fz_ctx_get_profile(ctx.handle, C.byref(p))
     return p.launches
 

@@ -166,10 +166,11 @@ fz_status fz_lorenzo_quantize(fz_ctx *ctx, const float *d_in, uint32_t ndim, con
 
 /* Stage entry point (Huffman codebook module, §3.2): from the histogram
  * d_hist (u64[nsym], nsym <= 1024, at least one nonzero count) compute the
- * code lengths d_lens (u8[nsym], two-queue Huffman, ties to the leaf,
- * 24-bit limit by count halving) and the canonical codewords d_codes
- * (u32[nsym], RFC 1951 order).  Synchronizes `stream`; FZ_EINVAL if no
- * count is nonzero. */
+ * code lengths d_lens (u8[nsym]: the optimal prefix code with lengths <= 14
+ * found by package-merge, leaves ordered by (count, symbol), a leaf before a
+ * package of equal weight; a single used symbol gets length 1) and the
+ * canonical codewords d_codes (u32[nsym], RFC 1951 order).  Synchronizes
+ * `stream`; FZ_EINVAL if no count is nonzero. */
 fz_status fz_huffman_codebook(fz_ctx *ctx, const uint64_t *d_hist, uint32_t nsym, uint8_t *d_lens,
                               uint32_t *d_codes, void *stream);
 
@@ -217,7 +218,9 @@ fz_status fz_mlp_adam(fz_ctx *ctx, float *d_weights, const float *d_grad, float 
  * When profiling is enabled, each call records a CUDA event on its stream
  * before the first and after every stage launch; a stage time is the
  * elapsed time between consecutive events.  `launches` counts the kernel
- * launches the context has issued since it was created (always counted). */
+ * launches the context has issued since it was created (always counted);
+ * `batch_plans` and `batch_graphs` count the cached batch plans and those of
+ * them that run as an instantiated CUDA graph. */
 #define FZ_MAX_STAGES 12
 typedef struct {
   uint32_t n_compress, n_decompress;      /* stages recorded for the last call of each kind */
@@ -226,6 +229,7 @@ typedef struct {
   char decompress_names[FZ_MAX_STAGES][16];
   float decompress_ms[FZ_MAX_STAGES];
   uint64_t launches;
+  uint32_t batch_plans, batch_graphs;
 } fz_profile;
 
 /* Turn stage timing on (enable != 0) or off.  Host-only bookkeeping; the
@@ -238,6 +242,51 @@ fz_status fz_ctx_get_profile(fz_ctx *ctx, fz_profile *out);
 
 /* Human-readable name of a status code (static string). */
 const char *fz_status_str(fz_status s);
+
+/* ---- batched calls: many fields of uneven size in one pass ----
+ * The paper composes its pipelines from modules launched one field at a
+ * time (§3.3); these two calls are this library's batching of the same path.
+ * Each stage runs as one persistent kernel over a work queue spanning every
+ * field of the batch; the whole sequence is captured as a CUDA graph the
+ * first time a batch shape (count, dims, mode, radius, predictor, output
+ * buffer) is seen -- after an autotuner has timed candidate launch shapes --
+ * and replayed by later calls of the same shape.  Launch shapes never change
+ * the bytes: stream j is byte-identical to fz_compress of field j alone.
+ * Only Lorenzo predictors (FZ_PRED_LORENZO1/2) are batched; others give
+ * FZ_EUNSUPPORTED. */
+
+/* Worst-case packed output of a batch: the sum over fields of
+ * fz_compress_bound rounded up to 16 bytes.  dims holds 3 values per field
+ * (unused trailing dims ignored).  0 on invalid dims. */
+uint64_t fz_compress_batch_bound(uint32_t n, const uint32_t *ndim, const uint64_t *dims);
+
+/* Compress n fields (1 <= n <= 65535).  d_in: host array of n device
+ * pointers (float32, 4-byte aligned); ndim: n values; dims: 3n values; eb:
+ * n error bounds (all in mode eb_mode).  The streams are packed into d_out
+ * (device, 16-byte aligned, out_cap bytes), stream j starting at
+ * h_offsets[j] (a multiple of 16) and its length in its header
+ * (total_bytes); h_offsets[n] is the packed size (host array of n+1
+ * values).  FZ_EBUFFER if the packed streams do not fit out_cap (contents
+ * then unspecified).  Synchronizes `stream`.  The first call with a new
+ * batch shape runs the autotuner (a few extra passes over the batch). */
+fz_status fz_compress_batch(fz_ctx *ctx, uint32_t n, const float *const *d_in, const uint32_t *ndim,
+                            const uint64_t *dims, uint32_t eb_mode, const double *eb, const fz_pipeline *pipe,
+                            void *d_out, uint64_t out_cap, uint64_t *h_offsets, void *stream);
+
+/* Reconstruct n streams packed in d_in (device, 16-byte aligned) at the
+ * host offsets h_offsets[0..n] (stream j occupies [h_offsets[j],
+ * h_offsets[j+1]), as fz_compress_batch lays them out) into the n device
+ * arrays d_out[j] (host array of device pointers); out_cap_values (host, n
+ * values, may be NULL) bounds each output.  Reads the n headers to the host
+ * first.  Synchronizes `stream`. */
+fz_status fz_decompress_batch(fz_ctx *ctx, uint32_t n, const void *d_in, const uint64_t *h_offsets,
+                              float *const *d_out, const uint64_t *out_cap_values, void *stream);
+
+/* Batched-call options: autotune (default 1) times candidate launch shapes
+ * on the first call with a new batch shape; graphs (default 1) captures and
+ * replays the batch sequence as a CUDA graph (0 runs it eagerly every call).
+ * Clears the cached plans. */
+fz_status fz_ctx_set_batch_options(fz_ctx *ctx, int autotune, int graphs);
 
 #ifdef __cplusplus
 }

@@ -19,7 +19,8 @@ import threading
 import torch
 
 __all__ = ["lib", "Context", "compress", "decompress", "lorenzo_quantize", "huffman_codebook", "stream_info",
-           "block_report", "mlp_grad", "mlp_adam", "FzError", "HEADER_BYTES", "SELECTOR_WEIGHTS"]
+           "block_report", "mlp_grad", "mlp_adam", "compress_batch", "decompress_batch", "FzError", "HEADER_BYTES",
+           "SELECTOR_WEIGHTS"]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_build", "libfz.so")
@@ -69,11 +70,18 @@ def _declare(L):
     L.fz_mlp_grad.argtypes = [_vp, _vp, _vp, _vp, C.c_uint32, _vp, C.POINTER(C.c_float), _vp]
     L.fz_mlp_adam.argtypes = [_vp, _vp, _vp, _vp, _vp, C.c_uint32, C.c_float, C.c_float, C.c_float, C.c_float,
                               _vp, _vp]
+    L.fz_compress_batch_bound.restype = C.c_uint64
+    L.fz_compress_batch_bound.argtypes = [C.c_uint32, _vp, _vp]
+    L.fz_compress_batch.argtypes = [_vp, C.c_uint32, _vp, _vp, _vp, C.c_uint32, _vp, C.POINTER(Pipeline), _vp,
+                                    C.c_uint64, _vp, _vp]
+    L.fz_decompress_batch.argtypes = [_vp, C.c_uint32, _vp, _vp, _vp, _vp, _vp]
+    L.fz_ctx_set_batch_options.argtypes = [_vp, C.c_int, C.c_int]
     L.fz_ctx_set_profiling.argtypes = [_vp, C.c_int]
     L.fz_ctx_get_profile.argtypes = [_vp, _vp]
     for name in ("fz_ctx_create", "fz_ctx_destroy", "fz_compress", "fz_decompress", "fz_stream_info",
                  "fz_lorenzo_quantize", "fz_huffman_codebook", "fz_block_report", "fz_mlp_grad", "fz_mlp_adam",
-                 "fz_ctx_set_profiling", "fz_ctx_get_profile"):
+                 "fz_ctx_set_profiling", "fz_ctx_get_profile", "fz_compress_batch", "fz_decompress_batch",
+                 "fz_ctx_set_batch_options"):
         getattr(L, name).restype = C.c_int
 
 
@@ -206,6 +214,84 @@ def decompress(buf: torch.Tensor, out: torch.Tensor | None = None, header: bytes
                              C.c_void_p(out.data_ptr()), out.numel(), _stream(stream))
     _check(st, "fz_decompress")
     return out
+
+
+def _batch_shapes(xs):
+    n = len(xs)
+    ndim = (C.c_uint32 * n)()
+    dims = (C.c_uint64 * (3 * n))()
+    for j, x in enumerate(xs):
+        ndim[j] = x.dim()
+        d = _dims(x.shape)
+        for a in range(3):
+            dims[3 * j + a] = d[a]
+    return ndim, dims
+
+
+def compress_batch(xs, eb, mode: str = "rel", predictor="lorenzo1", radius: int = 512, out=None, stream=None,
+                   ctx: Context | None = None):
+    """Compress a list of contiguous float32 CUDA tensors (1-3 dims each) in
+    one batched call.  ``eb`` is one bound or one per field.  Returns the
+    packed uint8 buffer and the stream offsets (n+1 ints); stream j is
+    ``buf[off[j]:off[j] + its total_bytes]``, byte-identical to ``compress``
+    of field j."""
+    xs = list(xs)
+    n = len(xs)
+    if n == 0:
+        raise ValueError("empty batch")
+    for x in xs:
+        if not (x.is_cuda and x.dtype == torch.float32 and x.is_contiguous() and 1 <= x.dim() <= 3):
+            raise ValueError("compress_batch expects contiguous float32 CUDA tensors of 1 to 3 dims")
+    ndim, dims = _batch_shapes(xs)
+    bound = int(lib().fz_compress_batch_bound(n, ndim, dims))
+    if out is None:
+        out = torch.empty(bound, dtype=torch.uint8, device=xs[0].device)
+    ebs = [float(eb)] * n if isinstance(eb, (int, float)) else [float(e) for e in eb]
+    ptrs = (C.c_void_p * n)(*[x.data_ptr() for x in xs])
+    ebarr = (C.c_double * n)(*ebs)
+    offs = (C.c_uint64 * (n + 1))()
+    pipe = _pipeline(predictor, radius)
+    c = ctx if ctx is not None else _ctx(xs[0].device.index or 0)
+    st = lib().fz_compress_batch(c.handle, n, ptrs, ndim, dims, 1 if mode == "rel" else 0, ebarr, C.byref(pipe),
+                                 C.c_void_p(out.data_ptr()), out.numel(), offs, _stream(stream))
+    _check(st, "fz_compress_batch")
+    return out, [int(offs[j]) for j in range(n + 1)]
+
+
+def decompress_batch(buf: torch.Tensor, offsets, outs=None, stream=None, ctx: Context | None = None):
+    """Reconstruct every stream of a packed batch buffer; returns the list of
+    float32 CUDA tensors (shapes from the stream headers)."""
+    n = len(offsets) - 1
+    if outs is None:
+        host = [bytes(buf[offsets[j]: offsets[j] + HEADER_BYTES].cpu().numpy()) for j in range(n)]
+        outs = [torch.empty(stream_info(h)[0], dtype=torch.float32, device=buf.device) for h in host]
+    ptrs = (C.c_void_p * n)(*[o.data_ptr() for o in outs])
+    caps = (C.c_uint64 * n)(*[o.numel() for o in outs])
+    offs = (C.c_uint64 * (n + 1))(*[int(o) for o in offsets])
+    c = ctx if ctx is not None else _ctx(buf.device.index or 0)
+    st = lib().fz_decompress_batch(c.handle, n, C.c_void_p(buf.data_ptr()), offs, ptrs, caps, _stream(stream))
+    _check(st, "fz_decompress_batch")
+    return outs
+
+
+class Profile(C.Structure):
+    """fz_profile: per-stage times of the last calls, launch and plan counts."""
+    _fields_ = [("n_compress", C.c_uint32), ("n_decompress", C.c_uint32),
+                ("compress_names", (C.c_char * 16) * 12), ("compress_ms", C.c_float * 12),
+                ("decompress_names", (C.c_char * 16) * 12), ("decompress_ms", C.c_float * 12),
+                ("launches", C.c_uint64), ("batch_plans", C.c_uint32), ("batch_graphs", C.c_uint32)]
+
+
+def profile(device: int = 0, ctx: Context | None = None) -> Profile:
+    c = ctx if ctx is not None else _ctx(device)
+    p = Profile()
+    _check(lib().fz_ctx_get_profile(c.handle, C.byref(p)), "fz_ctx_get_profile")
+    return p
+
+
+def set_batch_options(autotune: bool = True, graphs: bool = True, device: int = 0, ctx: Context | None = None):
+    c = ctx if ctx is not None else _ctx(device)
+    _check(lib().fz_ctx_set_batch_options(c.handle, int(autotune), int(graphs)), "fz_ctx_set_batch_options")
 
 
 def lorenzo_quantize(x: torch.Tensor, eb: float, mode: str = "rel", predictor="lorenzo1", radius: int = 512,

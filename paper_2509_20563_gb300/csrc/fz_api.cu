@@ -5,23 +5,7 @@
 
 #include <new>
 
-#include "fz_internal.cuh"
-
-struct fz_ctx {
-  int device = 0;
-  int sm_count = 0;
-  void *ws = nullptr;
-  size_t ws_bytes = 0;
-  void *h_pinned = nullptr;  // host mirror of the call's result block
-  // stage profiling (CUDA events on the call's stream)
-  bool profiling = false;
-  cudaEvent_t cev[FZ_MAX_STAGES + 1] = {};
-  cudaEvent_t dev_[FZ_MAX_STAGES + 1] = {};
-  const char *cname[FZ_MAX_STAGES] = {};
-  const char *dname[FZ_MAX_STAGES] = {};
-  uint32_t nc = 0, nd = 0;
-  uint64_t launches = 0;
-};
+#include "fz_host.h"
 
 namespace {
 // Records stage boundaries of one call when profiling is on.
@@ -48,27 +32,8 @@ struct StageClock {
 namespace fz {
 namespace {
 
-constexpr size_t kAlign = 256;
-inline size_t up(size_t v) { return (v + kAlign - 1) & ~(kAlign - 1); }
 
-fz_status from_cuda(cudaError_t e) {
-  if (e == cudaSuccess) return FZ_OK;
-  if (e == cudaErrorMemoryAllocation) return FZ_ENOMEM;
-  return FZ_ECUDA;
-}
 
-// Validate ndim/dims; fills N.
-bool valid_dims(uint32_t ndim, const uint64_t *dims, uint64_t *n) {
-  if (!dims || ndim < 1 || ndim > 3) return false;
-  uint64_t v = 1;
-  for (uint32_t a = 0; a < ndim; ++a) {
-    if (dims[a] == 0 || dims[a] >= (1ull << 32)) return false;
-    v *= dims[a];
-    if (v >= (1ull << 32)) return false;
-  }
-  *n = v;
-  return true;
-}
 
 fz_status ensure_ws(fz_ctx *ctx, size_t bytes) {
   if (ctx->ws_bytes >= bytes) return FZ_OK;
@@ -104,30 +69,51 @@ fz_status ensure_pinned(fz_ctx *ctx) {
   return FZ_OK;
 }
 
-// Carve the compress workspace out of the context allocation.
-size_t layout_compress(const Geom &g, char *base, CompressWs &ws) {
-  size_t off = 0;
-  auto take = [&](size_t bytes) {
-    char *p = base ? base + off : nullptr;
-    off += up(bytes);
+}  // namespace
+
+// Carve the compress workspace out of two regions: the part zeroed at the
+// start of every call (control block, per-tile counts, look-back status) at
+// zbase, and the rest at rbase.  Returns the zeroed part's size and stores
+// the rest's in *rest_bytes.  Null bases only compute the sizes.
+size_t layout_compress_split(const Geom &g, char *zbase, char *rbase, CompressWs &ws, size_t *rest_bytes) {
+  size_t zo = 0, ro = 0;
+  auto ztake = [&](size_t bytes) {
+    char *p = zbase ? zbase + zo : nullptr;
+    zo += up(bytes);
+    return p;
+  };
+  auto rtake = [&](size_t bytes) {
+    char *p = rbase ? rbase + ro : nullptr;
+    ro += up(bytes);
     return p;
   };
   const uint64_t n_etiles = (g.n_blocks + kEncWarps - 1) / kEncWarps;
-  ws.ctl = reinterpret_cast<Ctl *>(take(sizeof(Ctl)));
-  ws.tinfo = reinterpret_cast<uint4 *>(take(16 * g.n_qtiles));
-  ws.tgroup = reinterpret_cast<uint2 *>(take(8 * ((g.n_qtiles + kTileGroup - 1) / kTileGroup)));
-  ws.estatus = reinterpret_cast<uint64_t *>(take(8 * n_etiles));
-  ws.zero_bytes = off;
+  ws.ctl = reinterpret_cast<Ctl *>(ztake(sizeof(Ctl)));
+  ws.tinfo = reinterpret_cast<uint4 *>(ztake(16 * g.n_qtiles));
+  ws.tgroup = reinterpret_cast<uint2 *>(ztake(8 * ((g.n_qtiles + kTileGroup - 1) / kTileGroup)));
+  ws.estatus = reinterpret_cast<uint64_t *>(ztake(8 * n_etiles));
+  ws.zero_bytes = zo;
   ws.cap_list = g.n / 8;
   const uint64_t cap = ws.cap_list + 1;
-  ws.codes = reinterpret_cast<uint16_t *>(take(2 * g.npad));
-  ws.anchors = reinterpret_cast<int32_t *>(take(4 * g.n_blocks));
-  ws.out_idx = reinterpret_cast<uint32_t *>(take(4 * cap));
-  ws.out_val = reinterpret_cast<int32_t *>(take(4 * cap));
-  ws.exc_idx = reinterpret_cast<uint32_t *>(take(4 * cap));
-  ws.exc_val = reinterpret_cast<uint32_t *>(take(4 * cap));
-  ws.ids = reinterpret_cast<uint8_t *>(take(g.n_blocks));
-  return off;
+  ws.codes = reinterpret_cast<uint16_t *>(rtake(2 * g.npad));
+  ws.anchors = reinterpret_cast<int32_t *>(rtake(4 * g.n_blocks));
+  ws.out_idx = reinterpret_cast<uint32_t *>(rtake(4 * cap));
+  ws.out_val = reinterpret_cast<int32_t *>(rtake(4 * cap));
+  ws.exc_idx = reinterpret_cast<uint32_t *>(rtake(4 * cap));
+  ws.exc_val = reinterpret_cast<uint32_t *>(rtake(4 * cap));
+  ws.ids = reinterpret_cast<uint8_t *>(rtake(g.n_blocks));
+  if (rest_bytes) *rest_bytes = ro;
+  return zo;
+}
+
+namespace {
+
+// Single-field layout: the zeroed part first, the rest right after it.
+size_t layout_compress(const Geom &g, char *base, CompressWs &ws) {
+  size_t rest = 0;
+  const size_t z = layout_compress_split(g, nullptr, nullptr, ws, &rest);
+  if (base) layout_compress_split(g, base, base + z, ws, nullptr);
+  return z + rest;
 }
 
 struct Req {
@@ -174,10 +160,8 @@ fz_status run_front(fz_ctx *ctx, const float *d_in, const Geom &g, uint32_t eb_m
   return from_cuda(e);
 }
 
-bool overlaps(const void *a, uint64_t na, const void *b, uint64_t nb) {
-  uintptr_t x = (uintptr_t)a, y = (uintptr_t)b;
-  return x < y + nb && y < x + na;
-}
+
+}  // namespace
 
 // Host-side validation of a stream header against the stream length.
 fz_status check_header(const fz_header &h, uint64_t in_bytes, Geom &g) {
@@ -216,7 +200,6 @@ fz_status check_header(const fz_header &h, uint64_t in_bytes, Geom &g) {
   return FZ_OK;
 }
 
-}  // namespace
 }  // namespace fz
 
 using namespace fz;
@@ -271,6 +254,9 @@ fz_status fz_ctx_get_profile(fz_ctx *ctx, fz_profile *out) {
   if (!ctx || !out) return FZ_EINVAL;
   memset(out, 0, sizeof(*out));
   out->launches = ctx->launches;
+  out->batch_plans = (uint32_t)ctx->plans.size();
+  out->batch_graphs = 0;
+  for (const BatchPlan *p : ctx->plans) out->batch_graphs += p->exec ? 1u : 0u;
   if (!ctx->profiling) return FZ_OK;
   if (cudaSetDevice(ctx->device) != cudaSuccess) return FZ_ECUDA;
   for (int kind = 0; kind < 2; ++kind) {
@@ -300,6 +286,10 @@ fz_status fz_ctx_destroy(fz_ctx *ctx) {
     if (ctx->cev[i]) cudaEventDestroy(ctx->cev[i]);
     if (ctx->dev_[i]) cudaEventDestroy(ctx->dev_[i]);
   }
+  destroy_batch_plans(ctx);
+  if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
+  if (ctx->bws) cudaFree(ctx->bws);
+  if (ctx->h_batch) cudaFreeHost(ctx->h_batch);
   if (ctx->ws) cudaFree(ctx->ws);
   if (ctx->h_pinned) cudaFreeHost(ctx->h_pinned);
   cudaSetDevice(prev);

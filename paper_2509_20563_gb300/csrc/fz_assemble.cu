@@ -59,15 +59,23 @@ __device__ uint2 block_exscan2(uint2 v, uint2 &excl, uint2 *sw) {
   return tot;
 }
 
-__global__ void __launch_bounds__(kAsmThreads) k_assemble(const float *__restrict__ x, Geom g, uint32_t R,
-                                                           CompressWs ws, uint8_t *d_out) {
-  __shared__ uint2 sw[kAsmThreads / 32];
-  __shared__ unsigned long long s_ob, s_eb;
+struct AsmSmem {
+  uint2 sw[kAsmThreads / 32];
+  unsigned long long ob, eb;
+};
+
+// Assembly of one field's stream by CTAs bid = 0..nblk-1 (all threads of
+// each CTA call it together).
+__device__ __forceinline__ void assemble_body(const float *__restrict__ x, const Geom &g, uint32_t R,
+                                              const CompressWs &ws, uint8_t *d_out, uint32_t bid, uint32_t nblk,
+                                              AsmSmem &sm) {
+  uint2 *sw = sm.sw;
+  unsigned long long &s_ob = sm.ob, &s_eb = sm.eb;
   const Ctl *ctl = ws.ctl;
   const uint32_t mode = ctl->mode;
   const fz_header &h = ctl->res.hdr;
-  const uint64_t tid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const uint64_t nth = (uint64_t)gridDim.x * blockDim.x;
+  const uint64_t tid = (uint64_t)bid * blockDim.x + threadIdx.x;
+  const uint64_t nth = (uint64_t)nblk * blockDim.x;
   const uint8_t *hb = reinterpret_cast<const uint8_t *>(&h);
   if (tid < FZ_HEADER_BYTES) d_out[tid] = hb[tid];
   if (mode == kModeRaw) {
@@ -112,7 +120,7 @@ __global__ void __launch_bounds__(kAsmThreads) k_assemble(const float *__restric
   uint32_t *eidx = reinterpret_cast<uint32_t *>(d_out + h.off_exc_idx);
   uint32_t *eval = reinterpret_cast<uint32_t *>(d_out + h.off_exc_val);
   const uint64_t n_tg = (g.n_qtiles + kTileGroup - 1) / kTileGroup;
-  for (uint64_t grp = blockIdx.x; grp < n_tg; grp += gridDim.x) {
+  for (uint64_t grp = bid; grp < n_tg; grp += nblk) {
     // totals of the earlier groups
     unsigned long long po = 0, pe = 0;
     for (uint64_t q = threadIdx.x; q < grp; q += kAsmThreads) { po += ws.tgroup[q].x; pe += ws.tgroup[q].y; }
@@ -155,7 +163,34 @@ __global__ void __launch_bounds__(kAsmThreads) k_assemble(const float *__restric
   }
 }
 
+__global__ void __launch_bounds__(kAsmThreads) k_assemble(const float *__restrict__ x, Geom g, uint32_t R,
+                                                           CompressWs ws, uint8_t *d_out) {
+  __shared__ AsmSmem sm;
+  assemble_body(x, g, R, ws, d_out, blockIdx.x, gridDim.x, sm);
+}
+
+// Batched variant: the whole grid assembles the fields one after another.
+__global__ void __launch_bounds__(kAsmThreads) k_assemble_batch(const BatchJob *__restrict__ jobs, uint32_t n,
+                                                                 uint8_t *d_out) {
+  __shared__ AsmSmem sm;
+  for (uint32_t j = 0; j < n; ++j) {
+    const BatchJob &J = jobs[j];
+    if (J.out_off == kNoOutput) continue;
+    assemble_body(J.x, J.g, J.R, J.ws, d_out + J.out_off, blockIdx.x, gridDim.x, sm);
+  }
+}
+
 }  // namespace
+
+cudaError_t launch_assemble_batch(const BatchJob *jobs, uint32_t n, uint8_t *d_out, uint64_t max_n, cudaStream_t s,
+                                  int sm_count) {
+  uint64_t grid = (uint64_t)sm_count * 4;
+  const uint64_t want = (4 * max_n / 16 + kAsmThreads - 1) / kAsmThreads;
+  if (want < grid) grid = want;
+  if (grid < 2) grid = 2;
+  k_assemble_batch<<<(unsigned)grid, kAsmThreads, 0, s>>>(jobs, n, d_out);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_assemble(const float *x, const Geom &g, uint32_t R, const CompressWs &ws, uint8_t *d_out,
                             cudaStream_t s, int sm_count) {

@@ -178,11 +178,10 @@ __device__ void write_min_header(fz_header &h, uint16_t flags, const Geom &g, ui
   h.total_bytes = total;
 }
 
-__global__ void __launch_bounds__(kCbThreads) k_codebook(Geom g, uint32_t R, uint32_t pred, uint32_t eb_mode,
-                                                          double eb, CompressWs ws) {
-  extern __shared__ __align__(16) unsigned char cb_smem[];
-  CbSmem &s = *reinterpret_cast<CbSmem *>(cb_smem);
-  __shared__ uint32_t s_mode;
+// The codebook, the layout decision and the header of one field; all
+// threads of the CTA call it together.
+__device__ __forceinline__ void codebook_body(const Geom &g, uint32_t R, uint32_t pred, uint32_t eb_mode, double eb,
+                                              const CompressWs &ws, CbSmem &s, uint32_t &s_mode) {
   Ctl *ctl = ws.ctl;
   const int t = threadIdx.x;
   const uint32_t nsym = 2 * R;
@@ -265,6 +264,72 @@ __global__ void __launch_bounds__(kCbThreads) k_codebook(Geom g, uint32_t R, uin
   ctl->res.n_exc = ctl->n_exc;
 }
 
+__global__ void __launch_bounds__(kCbThreads) k_codebook(Geom g, uint32_t R, uint32_t pred, uint32_t eb_mode,
+                                                          double eb, CompressWs ws) {
+  extern __shared__ __align__(16) unsigned char cb_smem[];
+  __shared__ uint32_t s_mode;
+  codebook_body(g, R, pred, eb_mode, eb, ws, *reinterpret_cast<CbSmem *>(cb_smem), s_mode);
+}
+
+// Batched variant: one CTA per field.
+__global__ void __launch_bounds__(kCbThreads) k_codebook_batch(const BatchJob *__restrict__ jobs) {
+  extern __shared__ __align__(16) unsigned char cb_smem[];
+  __shared__ uint32_t s_mode;
+  const BatchJob &J = jobs[blockIdx.x];
+  codebook_body(J.g, J.R, J.pred, J.eb_mode, J.eb, J.ws, *reinterpret_cast<CbSmem *>(cb_smem), s_mode);
+}
+
+// Packed placement of the batch's streams: each field's stream starts at a
+// 16-byte boundary, in field order.  One CTA; also decides whether the
+// packed output fits.
+__global__ void __launch_bounds__(kCbThreads) k_batch_offsets(BatchJob *jobs, uint32_t n, uint64_t out_cap,
+                                                               BatchCtl *bctl) {
+  __shared__ unsigned long long wsum[kCbThreads / 32];
+  const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+  const uint32_t per = (n + kCbThreads - 1) / kCbThreads;
+  const uint32_t j0 = t * per;
+  unsigned long long loc = 0;
+  for (uint32_t j = j0; j < j0 + per && j < n; ++j) loc += align16(jobs[j].ws.ctl->res.total_bytes);
+  unsigned long long incl = loc;
+  for (int off = 1; off < 32; off <<= 1) {
+    const unsigned long long v = __shfl_up_sync(0xffffffffu, incl, off);
+    if (lane >= off) incl += v;
+  }
+  if (lane == 31) wsum[warp] = incl;
+  __syncthreads();
+  unsigned long long total = 0, run = incl - loc;
+  for (int w = 0; w < kCbThreads / 32; ++w) {
+    if (w < warp) run += wsum[w];
+    total += wsum[w];
+  }
+  const bool fits = total <= out_cap;
+  for (uint32_t j = j0; j < j0 + per && j < n; ++j) {
+    jobs[j].out_off = fits ? run : kNoOutput;
+    run += align16(jobs[j].ws.ctl->res.total_bytes);
+  }
+  if (t == 0) {
+    bctl->total_bytes = total;
+    if (!fits) atomicCAS(&bctl->err, 0u, (uint32_t)FZ_EBUFFER);
+  }
+}
+
+// Per-field results and packed offsets, gathered for one copy to the host:
+// offsets[0..n) the stream starts, offsets[n] the packed size, offsets[n+1]
+// the batch-wide error word.
+__global__ void k_batch_results(const BatchJob *__restrict__ jobs, uint32_t n, const BatchCtl *bctl, Result *res,
+                                uint64_t *offsets) {
+  for (uint32_t j = blockIdx.x * blockDim.x + threadIdx.x; j < n + 2; j += gridDim.x * blockDim.x) {
+    if (j < n) {
+      res[j] = jobs[j].ws.ctl->res;
+      offsets[j] = jobs[j].out_off;
+    } else if (j == n) {
+      offsets[n] = bctl->total_bytes;
+    } else {
+      offsets[n + 1] = bctl->err;
+    }
+  }
+}
+
 __global__ void __launch_bounds__(kCbThreads) k_codebook_only(const uint64_t *hist, uint32_t nsym, uint8_t *lens,
                                                                uint32_t *codes, Ctl *ctl) {
   extern __shared__ __align__(16) unsigned char cb_smem[];
@@ -292,6 +357,25 @@ cudaError_t launch_codebook(const Geom &g, uint32_t R, uint32_t pred, uint32_t e
     attr_set = true;
   }
   k_codebook<<<1, kCbThreads, sizeof(CbSmem), st>>>(g, R, pred, eb_mode, eb, ws);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_codebook_batch(const BatchJob *jobs, uint32_t n, cudaStream_t st) {
+  cudaError_t e =
+      cudaFuncSetAttribute(k_codebook_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(CbSmem));
+  if (e != cudaSuccess) return e;
+  k_codebook_batch<<<n, kCbThreads, sizeof(CbSmem), st>>>(jobs);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_batch_offsets(BatchJob *jobs, uint32_t n, uint64_t out_cap, BatchCtl *bctl, cudaStream_t st) {
+  k_batch_offsets<<<1, kCbThreads, 0, st>>>(jobs, n, out_cap, bctl);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_batch_results(const BatchJob *jobs, uint32_t n, const BatchCtl *bctl, Result *res,
+                                 uint64_t *offsets, cudaStream_t st) {
+  k_batch_results<<<(n + 2 + 255) / 256, 256, 0, st>>>(jobs, n, bctl, res, offsets);
   return cudaGetLastError();
 }
 

@@ -52,9 +52,8 @@ __global__ void k_dec_gsum(const uint32_t *__restrict__ chunk_bits, uint64_t n_c
   if (lane == 0) gsum[gidx] = s;
 }
 
-__global__ void __launch_bounds__(kPrepThreads) k_dec_prep(const uint8_t *__restrict__ lens_in, uint32_t nsym,
-                                                            uint64_t *gsum, uint64_t n_groups,
-                                                            uint64_t total_bits, uint16_t *lut, uint32_t *err) {
+__device__ __forceinline__ void k_dec_prep_body(const uint8_t *__restrict__ lens_in, uint32_t nsym, uint64_t *gsum,
+                                                uint64_t n_groups, uint64_t total_bits, uint16_t *lut, uint32_t *err) {
   __shared__ uint32_t first[kLmax + 1], cnt[kLmax + 1], basel[kLmax + 1];
   __shared__ uint32_t wcnt[32][kLmax + 1];
   __shared__ uint32_t wk[32];
@@ -150,6 +149,12 @@ __global__ void __launch_bounds__(kPrepThreads) k_dec_prep(const uint8_t *__rest
     gsum[i] = run;
     run += v;
   }
+}
+
+__global__ void __launch_bounds__(kPrepThreads) k_dec_prep(const uint8_t *__restrict__ lens_in, uint32_t nsym,
+                                                            uint64_t *gsum, uint64_t n_groups,
+                                                            uint64_t total_bits, uint16_t *lut, uint32_t *err) {
+  k_dec_prep_body(lens_in, nsym, gsum, n_groups, total_bits, lut, err);
 }
 
 struct DecParams {
@@ -414,21 +419,15 @@ __device__ __forceinline__ void decode_chunk(const DecParams &p, const Geom &g, 
     dec_err(p.err, FZ_ECORRUPT);
 }
 
+// Decode groups grp, grp + step, ... below g_end of one field whose table
+// is in slut; all threads of the CTA call it together.
 template <int NDIM, int K>
-__global__ void __launch_bounds__(kDecThreads) k_decode(DecParams p, Geom g) {
-  extern __shared__ __align__(16) unsigned char d_smem[];
-  uint16_t *slut = reinterpret_cast<uint16_t *>(d_smem);
-  int32_t *sstate = reinterpret_cast<int32_t *>(d_smem + sizeof(uint16_t) * kLutSize);
-  uint32_t *sring = reinterpret_cast<uint32_t *>(sstate + DecState<NDIM, K>::kWords * kDecThreads);
-  __shared__ unsigned long long swarp[kDecThreads / 32];
+__device__ __forceinline__ void decode_groups(const DecParams &p, const Geom &g, const uint16_t *slut,
+                                              int32_t *sstate, uint32_t *sring, unsigned long long *swarp,
+                                              uint64_t grp, uint64_t g_end, uint64_t step) {
   const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
-  {
-    const uint4 *src = reinterpret_cast<const uint4 *>(p.lut);
-    uint4 *dst = reinterpret_cast<uint4 *>(slut);
-    for (int i = t; i < kLutSize / 8; i += kDecThreads) dst[i] = __ldg(src + i);
-  }
   const bool vecbase = ((g.nx & 3u) == 0) && (((uintptr_t)p.out & 15u) == 0);
-  for (uint64_t grp = blockIdx.x; grp < p.n_groups; grp += gridDim.x) {
+  for (; grp < g_end; grp += step) {
     const uint64_t j = grp * kDecThreads + t;
     const bool valid = j < p.n_chunks;
     const uint32_t cb = valid ? __ldg(p.chunk_bits + j) : 0u;
@@ -447,6 +446,88 @@ __global__ void __launch_bounds__(kDecThreads) k_decode(DecParams p, Geom g) {
       if (p.n_exc) decode_chunk<NDIM, K, true>(p, g, slut, sstate + t, sring + t, j, start, vecbase);
       else decode_chunk<NDIM, K, false>(p, g, slut, sstate + t, sring + t, j, start, vecbase);
     }
+  }
+}
+
+__device__ __forceinline__ void load_lut(uint16_t *slut, const uint16_t *lut) {
+  const uint4 *src = reinterpret_cast<const uint4 *>(lut);
+  uint4 *dst = reinterpret_cast<uint4 *>(slut);
+  for (int i = threadIdx.x; i < kLutSize / 8; i += kDecThreads) dst[i] = __ldg(src + i);
+}
+
+template <int NDIM, int K>
+__global__ void __launch_bounds__(kDecThreads) k_decode(DecParams p, Geom g) {
+  extern __shared__ __align__(16) unsigned char d_smem[];
+  uint16_t *slut = reinterpret_cast<uint16_t *>(d_smem);
+  int32_t *sstate = reinterpret_cast<int32_t *>(d_smem + sizeof(uint16_t) * kLutSize);
+  uint32_t *sring = reinterpret_cast<uint32_t *>(sstate + DecState<NDIM, K>::kWords * kDecThreads);
+  __shared__ unsigned long long swarp[kDecThreads / 32];
+  load_lut(slut, p.lut);
+  decode_groups<NDIM, K>(p, g, slut, sstate, sring, swarp, blockIdx.x, p.n_groups, gridDim.x);
+}
+
+// ---------------------------------------------------------------- batched decode
+// One field of a batched decompress (Huffman streams only).
+struct DecJob {
+  DecParams p;
+  Geom g;
+  const uint8_t *lens;
+  uint32_t nsym, pad;
+  uint64_t total_bits;
+  uint64_t group_base;  // first decode group in the job's class queue
+};
+
+// Group bit sums of every field: blockIdx.y = field.
+__global__ void k_dec_gsum_batch(const DecJob *__restrict__ jobs) {
+  const DecJob &J = jobs[blockIdx.y];
+  const uint64_t gidx = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (gidx >= J.p.n_groups) return;
+  const uint64_t c0 = gidx * kDecThreads + 8 * lane;
+  unsigned long long s = 0;
+  for (uint64_t c = c0; c < J.p.n_chunks && c < c0 + 8; ++c) s += J.p.chunk_bits[c];
+  for (int off = 16; off > 0; off >>= 1) s += __shfl_down_sync(0xffffffffu, s, off);
+  if (lane == 0) const_cast<uint64_t *>(J.p.goff)[gidx] = s;
+}
+
+// Decode tables and group offsets: one CTA per field.
+__global__ void __launch_bounds__(kPrepThreads) k_dec_prep_batch(const DecJob *__restrict__ jobs) {
+  const DecJob &J = jobs[blockIdx.x];
+  k_dec_prep_body(J.lens, J.nsym, const_cast<uint64_t *>(J.p.goff), J.p.n_groups, J.total_bits,
+                  const_cast<uint16_t *>(J.p.lut), J.p.err);
+}
+
+// The decode groups of every field of one class (dimensionality, Lorenzo
+// order) form one queue cut into equal contiguous ranges, one per CTA; the
+// decode table is reloaded when the CTA moves to another field.
+template <int NDIM, int K>
+__global__ void __launch_bounds__(kDecThreads) k_decode_batch(const DecJob *__restrict__ jobs,
+                                                               const uint32_t *__restrict__ members,
+                                                               uint32_t n_members, uint64_t total_groups) {
+  extern __shared__ __align__(16) unsigned char d_smem[];
+  uint16_t *slut = reinterpret_cast<uint16_t *>(d_smem);
+  int32_t *sstate = reinterpret_cast<int32_t *>(d_smem + sizeof(uint16_t) * kLutSize);
+  uint32_t *sring = reinterpret_cast<uint32_t *>(sstate + DecState<NDIM, K>::kWords * kDecThreads);
+  __shared__ unsigned long long swarp[kDecThreads / 32];
+  __shared__ DecParams sp;
+  __shared__ Geom sg;
+  const uint64_t lo = total_groups * blockIdx.x / gridDim.x, hi = total_groups * (blockIdx.x + 1) / gridDim.x;
+  uint32_t a = 0, b = n_members;
+  while (a < b) {
+    const uint32_t m = (a + b) >> 1;
+    const DecJob &J = jobs[members[m]];
+    if (J.group_base + J.p.n_groups <= lo) a = m + 1; else b = m;
+  }
+  for (uint64_t t = lo; t < hi && a < n_members; ++a) {
+    const DecJob &J = jobs[members[a]];
+    const uint64_t jb = J.group_base, je = jb + J.p.n_groups;
+    const uint64_t t0 = t > jb ? t : jb, t1 = hi < je ? hi : je;
+    __syncthreads();  // the previous field is done with the table and the staged parameters
+    if (threadIdx.x == 0) { sp = J.p; sg = J.g; }
+    load_lut(slut, J.p.lut);
+    __syncthreads();
+    if (t0 < t1) decode_groups<NDIM, K>(sp, sg, slut, sstate, sring, swarp, t0 - jb, t1 - jb, 1);
+    t = t1;
   }
 }
 
@@ -518,6 +599,128 @@ __global__ void k_fill(float *out, uint64_t n, uint32_t bits) {
     out[i] = v;
 }
 }  // namespace
+
+// ---------------------------------------------------------------- batched decode: host side
+namespace {
+// RAW and CONST fields of a batched decompress.
+struct PlainJob {
+  const uint8_t *src;  // the stream
+  float *out;
+  uint64_t n;
+  uint32_t is_const, pad;
+};
+
+__global__ void k_plain_batch(const PlainJob *__restrict__ jobs, uint32_t n) {
+  const uint64_t tid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x, nth = (uint64_t)gridDim.x * blockDim.x;
+  for (uint32_t j = 0; j < n; ++j) {
+    const PlainJob &J = jobs[j];
+    const uint8_t *src = J.src + FZ_HEADER_BYTES;
+    if (J.is_const) {
+      const float v = *reinterpret_cast<const float *>(src);
+      for (uint64_t i = tid; i < J.n; i += nth) J.out[i] = v;
+    } else {
+      const float *f = reinterpret_cast<const float *>(src);
+      for (uint64_t i = tid; i < J.n; i += nth) J.out[i] = f[i];
+    }
+  }
+}
+
+template <int NDIM, int K>
+cudaError_t launch_dec_batch_t(const DecJob *jobs, const uint32_t *members, uint32_t n_members,
+                               uint64_t total_groups, int per_sm, cudaStream_t s, int sms) {
+  const int smem = (int)dec_smem_bytes<NDIM, K>();
+  cudaError_t e = cudaFuncSetAttribute(k_decode_batch<NDIM, K>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e != cudaSuccess) return e;
+  int occ = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_decode_batch<NDIM, K>, kDecThreads, smem);
+  if (e != cudaSuccess) return e;
+  if (occ < 1) occ = 1;
+  if (per_sm < 1 || per_sm > occ) per_sm = occ;
+  uint64_t grid = (uint64_t)sms * per_sm;
+  if (grid > total_groups) grid = total_groups;
+  if (grid < 1) grid = 1;
+  k_decode_batch<NDIM, K><<<(unsigned)grid, kDecThreads, smem, s>>>(jobs, members, n_members, total_groups);
+  return cudaGetLastError();
+}
+}  // namespace
+
+size_t dec_job_bytes() { return sizeof(DecJob); }
+size_t plain_job_bytes() { return sizeof(PlainJob); }
+uint64_t dec_groups(const fz_header &h) { return (h.n_chunks + kDecThreads - 1) / kDecThreads; }
+
+void fill_dec_job(void *dst, const uint8_t *d_in, const fz_header &h, float *d_out, uint16_t *lut, uint64_t *gsum,
+                  uint32_t *err, uint64_t group_base) {
+  DecJob J;
+  memset(&J, 0, sizeof(J));
+  make_geom(h.ndim, h.dims, J.g);
+  DecParams &p = J.p;
+  p.words = reinterpret_cast<const uint32_t *>(d_in + h.off_bits);
+  p.n_words = (h.total_bits + 31) / 32;
+  p.chunk_bits = reinterpret_cast<const uint32_t *>(d_in + h.off_chunk_bits);
+  p.anchors = reinterpret_cast<const int32_t *>(d_in + h.off_anchors);
+  p.out_idx = reinterpret_cast<const uint32_t *>(d_in + h.off_out_idx);
+  p.out_val = reinterpret_cast<const int32_t *>(d_in + h.off_out_val);
+  p.exc_idx = reinterpret_cast<const uint32_t *>(d_in + h.off_exc_idx);
+  p.exc_val = reinterpret_cast<const uint32_t *>(d_in + h.off_exc_val);
+  p.n_out = h.n_out;
+  p.n_exc = h.n_exc;
+  p.n_chunks = h.n_chunks;
+  p.n_groups = dec_groups(h);
+  p.goff = gsum;
+  p.lut = lut;
+  p.err = err;
+  p.out = d_out;
+  memcpy(&p.ebx2, &h.ebx2_bits, 4);
+  p.R = (int32_t)h.radius;
+  J.lens = d_in + h.off_lens;
+  J.nsym = 2 * h.radius;
+  J.total_bits = h.total_bits;
+  J.group_base = group_base;
+  memcpy(dst, &J, sizeof(J));
+}
+
+void fill_plain_job(void *dst, const uint8_t *d_in, uint64_t n, bool is_const, float *d_out) {
+  PlainJob J;
+  memset(&J, 0, sizeof(J));
+  J.src = d_in;
+  J.out = d_out;
+  J.n = n;
+  J.is_const = is_const ? 1u : 0u;
+  memcpy(dst, &J, sizeof(J));
+}
+
+cudaError_t launch_decode_batch_prep(const void *jobs, uint32_t n, uint64_t max_groups, cudaStream_t s) {
+  const DecJob *J = reinterpret_cast<const DecJob *>(jobs);
+  const uint64_t gx = (max_groups * 32 + 255) / 256;
+  k_dec_gsum_batch<<<dim3((unsigned)gx, n), 256, 0, s>>>(J);
+  k_dec_prep_batch<<<n, kPrepThreads, 0, s>>>(J);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_decode_batch_main(int ndim, int k, const void *jobs, const uint32_t *members, uint32_t n_members,
+                                     uint64_t total_groups, int per_sm, cudaStream_t s, int sms) {
+  const DecJob *J = reinterpret_cast<const DecJob *>(jobs);
+  const bool k2 = k == 2;
+  switch (ndim) {
+    case 1:
+      return k2 ? launch_dec_batch_t<1, 2>(J, members, n_members, total_groups, per_sm, s, sms)
+                : launch_dec_batch_t<1, 1>(J, members, n_members, total_groups, per_sm, s, sms);
+    case 2:
+      return k2 ? launch_dec_batch_t<2, 2>(J, members, n_members, total_groups, per_sm, s, sms)
+                : launch_dec_batch_t<2, 1>(J, members, n_members, total_groups, per_sm, s, sms);
+    default:
+      return k2 ? launch_dec_batch_t<3, 2>(J, members, n_members, total_groups, per_sm, s, sms)
+                : launch_dec_batch_t<3, 1>(J, members, n_members, total_groups, per_sm, s, sms);
+  }
+}
+
+cudaError_t launch_plain_batch(const void *jobs, uint32_t n, uint64_t max_n, cudaStream_t s, int sms) {
+  uint64_t grid = (max_n + 255) / 256;
+  if (grid > (uint64_t)sms * 8) grid = (uint64_t)sms * 8;
+  if (grid < 1) grid = 1;
+  k_plain_batch<<<(unsigned)grid, 256, 0, s>>>(reinterpret_cast<const PlainJob *>(jobs), n);
+  return cudaGetLastError();
+}
 
 // CONST streams: every value is the stored one.
 cudaError_t launch_fill(float *out, uint64_t n, uint32_t bits, cudaStream_t s, int sm_count) {

@@ -24,140 +24,200 @@ namespace {
 constexpr int kEncThreads = kEncWarps * 32;
 
 template <int CH>
-__global__ void __launch_bounds__(kEncThreads) k_encode(Geom g, CompressWs ws, uint8_t *d_out) {
-  constexpr int PER = CH / 32;                                     // codes per lane (16 or 32)
-  constexpr int kMaxWords = (CH * kEncWarps * kLmax + 32) / 32 + 3;  // tile image + next-tile head
-  __shared__ uint32_t senc[kMaxSym];
-  __shared__ __align__(16) uint32_t lw[kMaxWords];
-  __shared__ uint32_t s_wtot[kEncWarps], s_woff[kEncWarps];
-  __shared__ uint32_t s_tile, s_tbits;
-  __shared__ unsigned long long s_base;
+struct EncSmem {
+  static constexpr int kMaxWords = (CH * kEncWarps * kLmax + 32) / 32 + 3;  // tile image + next-tile head
+  uint32_t senc[kMaxSym];
+  __align__(16) uint32_t lw[kMaxWords];
+  uint32_t wtot[kEncWarps], woff[kEncWarps];
+  uint32_t tile, tbits, job;
+  unsigned long long base;
+};
 
-  Ctl *ctl = ws.ctl;
-  if (ctl->mode != kModeNormal) return;
+// One encode tile (kEncWarps chunks) of one field whose codeword table is
+// in sm.senc; all threads of the CTA call it together.
+template <int CH>
+__device__ __forceinline__ void encode_tile(const CompressWs &ws, uint8_t *d_out, uint64_t n_chunks, uint64_t tile,
+                                            EncSmem<CH> &sm) {
+  constexpr int PER = CH / 32;  // codes per lane (16 or 32)
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  Ctl *ctl = ws.ctl;
   const fz_header &h = ctl->res.hdr;
   uint32_t *chunk_bits = reinterpret_cast<uint32_t *>(d_out + h.off_chunk_bits);
   uint32_t *words = reinterpret_cast<uint32_t *>(d_out + h.off_bits);
-  const uint64_t n_chunks = g.n_blocks;
   const uint64_t n_tiles = (n_chunks + kEncWarps - 1) / kEncWarps;
   const uint64_t wlimit = (ctl->total_bits + 31) / 32;
-  for (int s = tid; s < kMaxSym; s += kEncThreads) senc[s] = ctl->enc[s];
+  uint32_t *senc = sm.senc, *lw = sm.lw;
 
-  for (;;) {
-    if (tid == 0) s_tile = atomicAdd(&ctl->encode_ticket, 1u);
-    __syncthreads();
-    const uint64_t tile = s_tile;
-    if (tile >= n_tiles) break;
-
-    // ---- lane codes and bit counts
-    const uint64_t chunk = tile * kEncWarps + warp;
-    const bool valid = chunk < n_chunks;
-    uint32_t cw[PER];
-    uint32_t lbits = 0;
-    if (valid) {
-      const uint4 *src = reinterpret_cast<const uint4 *>(ws.codes + chunk * CH + lane * PER);
+  // ---- lane codes and bit counts
+  const uint64_t chunk = tile * kEncWarps + warp;
+  const bool valid = chunk < n_chunks;
+  uint32_t cw[PER];
+  uint32_t lbits = 0;
+  if (valid) {
+    const uint4 *src = reinterpret_cast<const uint4 *>(ws.codes + chunk * CH + lane * PER);
 #pragma unroll
-      for (int v = 0; v < PER / 8; ++v) {
-        const uint4 u = __ldcs(src + v);
-        const uint32_t w4[4] = {u.x, u.y, u.z, u.w};
+    for (int v = 0; v < PER / 8; ++v) {
+      const uint4 u = __ldcs(src + v);
+      const uint32_t w4[4] = {u.x, u.y, u.z, u.w};
 #pragma unroll
-        for (int k = 0; k < 4; ++k) {
-          cw[8 * v + 2 * k] = senc[w4[k] & 0xffffu];
-          cw[8 * v + 2 * k + 1] = senc[w4[k] >> 16];
-        }
+      for (int k = 0; k < 4; ++k) {
+        cw[8 * v + 2 * k] = senc[w4[k] & 0xffffu];
+        cw[8 * v + 2 * k + 1] = senc[w4[k] >> 16];
       }
+    }
 #pragma unroll
-      for (int k = 0; k < PER; ++k) lbits += cw[k] >> 24;
-    } else {
+    for (int k = 0; k < PER; ++k) lbits += cw[k] >> 24;
+  } else {
 #pragma unroll
-      for (int k = 0; k < PER; ++k) cw[k] = 0;
-    }
-    uint32_t incl = lbits;
+    for (int k = 0; k < PER; ++k) cw[k] = 0;
+  }
+  uint32_t incl = lbits;
 #pragma unroll
-    for (int off = 1; off < 32; off <<= 1) {
-      const uint32_t v = __shfl_up_sync(0xffffffffu, incl, off);
-      if (lane >= off) incl += v;
-    }
-    const uint32_t lane_off = incl - lbits;
-    if (lane == 31) {
-      s_wtot[warp] = incl;
-      if (valid) chunk_bits[chunk] = incl;
-    }
-    __syncthreads();
-    if (tid == 0) {
-      uint32_t acc = 0;
-      for (int w = 0; w < kEncWarps; ++w) { s_woff[w] = acc; acc += s_wtot[w]; }
-      s_tbits = acc;
-      lookback_publish(ws.estatus, tile, acc);
-    }
-    __syncthreads();
-    const uint32_t tbits = s_tbits;
-    const uint32_t nl = (tbits + 32 + 31) / 32 + 1;
-    for (uint32_t w = tid; w < nl; w += kEncThreads) lw[w] = 0;
-    __syncthreads();
+  for (int off = 1; off < 32; off <<= 1) {
+    const uint32_t v = __shfl_up_sync(0xffffffffu, incl, off);
+    if (lane >= off) incl += v;
+  }
+  const uint32_t lane_off = incl - lbits;
+  if (lane == 31) {
+    sm.wtot[warp] = incl;
+    if (valid) chunk_bits[chunk] = incl;
+  }
+  __syncthreads();
+  if (tid == 0) {
+    uint32_t acc = 0;
+    for (int w = 0; w < kEncWarps; ++w) { sm.woff[w] = acc; acc += sm.wtot[w]; }
+    sm.tbits = acc;
+    lookback_publish(ws.estatus, tile, acc);
+  }
+  __syncthreads();
+  const uint32_t tbits = sm.tbits;
+  const uint32_t nl = (tbits + 32 + 31) / 32 + 1;
+  for (uint32_t w = tid; w < nl; w += kEncThreads) lw[w] = 0;
+  __syncthreads();
 
-    // ---- pack this lane's codewords MSB-first at its tile-local bit offset
-    if (valid) {
-      const uint32_t rb = s_woff[warp] + lane_off;
-      uint32_t wi = rb >> 5;
-      int cnt = (int)(rb & 31u);
-      unsigned long long buf = 0;
+  // ---- pack this lane's codewords MSB-first at its tile-local bit offset
+  if (valid) {
+    const uint32_t rb = sm.woff[warp] + lane_off;
+    uint32_t wi = rb >> 5;
+    int cnt = (int)(rb & 31u);
+    unsigned long long buf = 0;
 #pragma unroll
-      for (int k = 0; k < PER; ++k) {
-        const uint32_t L = cw[k] >> 24, c = cw[k] & 0xffffffu;
-        buf |= (unsigned long long)c << (64 - cnt - (int)L);
-        cnt += (int)L;
-        if (cnt >= 32) {
-          atomicOr(&lw[wi], (uint32_t)(buf >> 32));
-          ++wi;
-          buf <<= 32;
-          cnt -= 32;
-        }
+    for (int k = 0; k < PER; ++k) {
+      const uint32_t L = cw[k] >> 24, c = cw[k] & 0xffffffu;
+      buf |= (unsigned long long)c << (64 - cnt - (int)L);
+      cnt += (int)L;
+      if (cnt >= 32) {
+        atomicOr(&lw[wi], (uint32_t)(buf >> 32));
+        ++wi;
+        buf <<= 32;
+        cnt -= 32;
       }
-      if (cnt > 0) atomicOr(&lw[wi], (uint32_t)(buf >> 32));
     }
-    __syncthreads();
+    if (cnt > 0) atomicOr(&lw[wi], (uint32_t)(buf >> 32));
+  }
+  __syncthreads();
 
-    if (warp == 0) {
-      // first 32 bits of the next tile, placed right after this tile's bits
-      if (tile + 1 < n_tiles) {
-        const uint32_t e = senc[ws.codes[(tile + 1) * kEncWarps * (uint64_t)CH + lane]];
-        const uint32_t L = e >> 24, c = e & 0xffffffu;
-        uint32_t p = L;
+  if (warp == 0) {
+    // first 32 bits of the next tile, placed right after this tile's bits
+    if (tile + 1 < n_tiles) {
+      const uint32_t e = senc[ws.codes[(tile + 1) * kEncWarps * (uint64_t)CH + lane]];
+      const uint32_t L = e >> 24, c = e & 0xffffffu;
+      uint32_t p = L;
 #pragma unroll
-        for (int off = 1; off < 32; off <<= 1) {
-          const uint32_t v = __shfl_up_sync(0xffffffffu, p, off);
-          if (lane >= off) p += v;
-        }
-        p -= L;
-        const uint32_t contrib = p < 32 ? (uint32_t)(((unsigned long long)c << (64 - p - L)) >> 32) : 0u;
-        const uint32_t head = __reduce_or_sync(0xffffffffu, contrib);
-        if (lane == 0) {
-          const uint32_t r = tbits & 31u, w0 = tbits >> 5;
-          lw[w0] |= head >> r;
-          if (r) lw[w0 + 1] |= head << (32 - r);
-        }
+      for (int off = 1; off < 32; off <<= 1) {
+        const uint32_t v = __shfl_up_sync(0xffffffffu, p, off);
+        if (lane >= off) p += v;
       }
-      const unsigned long long base = lookback_resolve_warp(ws.estatus, tile, tbits, ctl);
+      p -= L;
+      const uint32_t contrib = p < 32 ? (uint32_t)(((unsigned long long)c << (64 - p - L)) >> 32) : 0u;
+      const uint32_t head = __reduce_or_sync(0xffffffffu, contrib);
       if (lane == 0) {
-        s_base = base;
-        if (tile == n_tiles - 1 && base + tbits != ctl->total_bits) set_err(ctl, FZ_ECORRUPT);
+        const uint32_t r = tbits & 31u, w0 = tbits >> 5;
+        lw[w0] |= head >> r;
+        if (r) lw[w0 + 1] |= head << (32 - r);
+      }
+    }
+    const unsigned long long base = lookback_resolve_warp(ws.estatus, tile, tbits, ctl);
+    if (lane == 0) {
+      sm.base = base;
+      if (tile == n_tiles - 1 && base + tbits != ctl->total_bits) set_err(ctl, FZ_ECORRUPT);
+    }
+  }
+  __syncthreads();
+
+  // ---- write every word whose first bit lies in this tile (funnel shift
+  // by the offset's low bits; never past the bitstream section)
+  const unsigned long long base = sm.base;
+  const uint32_t r = (uint32_t)(base & 31u);
+  const uint64_t gw0 = base >> 5;
+  const uint32_t jmax = (uint32_t)(((base + tbits - 1) >> 5) - gw0);
+  if (tid == 0 && gw0 + jmax >= wlimit) set_err(ctl, FZ_ECORRUPT);
+  for (uint32_t j = (r ? 1u : 0u) + tid; j <= jmax; j += kEncThreads) {
+    const uint32_t v = r ? ((lw[j - 1] << (32 - r)) | (lw[j] >> r)) : lw[j];
+    if (gw0 + j < wlimit) words[gw0 + j] = v;
+  }
+}
+
+template <int CH>
+__global__ void __launch_bounds__(kEncThreads) k_encode(Geom g, CompressWs ws, uint8_t *d_out) {
+  __shared__ EncSmem<CH> sm;
+  Ctl *ctl = ws.ctl;
+  if (ctl->mode != kModeNormal) return;
+  const int tid = threadIdx.x;
+  const uint64_t n_tiles = (g.n_blocks + kEncWarps - 1) / kEncWarps;
+  for (int s = tid; s < kMaxSym; s += kEncThreads) sm.senc[s] = ctl->enc[s];
+  for (;;) {
+    if (tid == 0) sm.tile = atomicAdd(&ctl->encode_ticket, 1u);
+    __syncthreads();
+    const uint64_t tile = sm.tile;
+    if (tile >= n_tiles) break;
+    encode_tile<CH>(ws, d_out, g.n_blocks, tile, sm);
+  }
+}
+
+// Batched variant: the encode tiles of every field of one chunk-size class
+// form one ticket queue, in field order, so a field's tiles are claimed in
+// order and its look-back always ends.  The codeword table is reloaded when
+// a CTA moves to another field; fields without a Huffman section, or
+// without room in the packed output, are skipped.
+template <int CH>
+__global__ void __launch_bounds__(kEncThreads) k_encode_batch(const BatchJob *__restrict__ jobs,
+                                                               const uint32_t *__restrict__ members,
+                                                               uint32_t n_members, uint64_t total_tiles,
+                                                               uint32_t *ticket, uint8_t *d_out) {
+  __shared__ EncSmem<CH> sm;
+  const int tid = threadIdx.x;
+  uint32_t cur = 0xffffffffu;
+  for (;;) {
+    if (tid == 0) {
+      const uint32_t tk = atomicAdd(ticket, 1u);
+      sm.tile = tk;
+      if (tk < total_tiles) {
+        uint32_t a = 0, b = n_members;  // the member whose tiles contain tk
+        while (a < b) {
+          const uint32_t m = (a + b) >> 1;
+          const BatchJob &J = jobs[members[m]];
+          if (J.etile_base + (J.g.n_blocks + kEncWarps - 1) / kEncWarps <= tk) a = m + 1; else b = m;
+        }
+        sm.job = members[a];
       }
     }
     __syncthreads();
-
-    // ---- write every word whose first bit lies in this tile (funnel shift
-    // by the offset's low bits; never past the bitstream section)
-    const unsigned long long base = s_base;
-    const uint32_t r = (uint32_t)(base & 31u);
-    const uint64_t gw0 = base >> 5;
-    const uint32_t jmax = (uint32_t)(((base + tbits - 1) >> 5) - gw0);
-    if (tid == 0 && gw0 + jmax >= wlimit) set_err(ctl, FZ_ECORRUPT);
-    for (uint32_t j = (r ? 1u : 0u) + tid; j <= jmax; j += kEncThreads) {
-      const uint32_t v = r ? ((lw[j - 1] << (32 - r)) | (lw[j] >> r)) : lw[j];
-      if (gw0 + j < wlimit) words[gw0 + j] = v;
+    const uint64_t tk = sm.tile;
+    if (tk >= total_tiles) break;
+    const uint32_t j = sm.job;
+    const BatchJob &J = jobs[j];
+    if (J.ws.ctl->mode != kModeNormal || J.out_off == kNoOutput) {
+      __syncthreads();
+      continue;
     }
+    if (j != cur) {
+      for (int s = tid; s < kMaxSym; s += kEncThreads) sm.senc[s] = J.ws.ctl->enc[s];
+      cur = j;
+      __syncthreads();
+    }
+    encode_tile<CH>(J.ws, d_out + J.out_off, J.g.n_blocks, tk - J.etile_base, sm);
+    __syncthreads();
   }
 }
 
@@ -174,7 +234,29 @@ cudaError_t launch_t(const Geom &g, const CompressWs &ws, uint8_t *d_out, cudaSt
   return cudaGetLastError();
 }
 
+template <int CH>
+cudaError_t launch_batch_t(const BatchJob *jobs, const uint32_t *members, uint32_t n_members, uint64_t total_tiles,
+                           uint32_t *ticket, uint8_t *d_out, int per_sm, cudaStream_t s, int sms) {
+  int occ = 0;
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_encode_batch<CH>, kEncThreads, 0);
+  if (e != cudaSuccess) return e;
+  if (occ < 1) occ = 1;
+  if (per_sm < 1 || per_sm > occ) per_sm = occ;
+  uint64_t grid = (uint64_t)sms * per_sm;
+  if (grid > total_tiles) grid = total_tiles;
+  if (grid < 1) grid = 1;
+  k_encode_batch<CH><<<(unsigned)grid, kEncThreads, 0, s>>>(jobs, members, n_members, total_tiles, ticket, d_out);
+  return cudaGetLastError();
+}
+
 }  // namespace
+
+cudaError_t launch_encode_batch(int chunk, const BatchJob *jobs, const uint32_t *members, uint32_t n_members,
+                                uint64_t total_tiles, uint32_t *ticket, uint8_t *d_out, int per_sm, cudaStream_t s,
+                                int sm_count) {
+  if (chunk == 512) return launch_batch_t<512>(jobs, members, n_members, total_tiles, ticket, d_out, per_sm, s, sm_count);
+  return launch_batch_t<1024>(jobs, members, n_members, total_tiles, ticket, d_out, per_sm, s, sm_count);
+}
 
 cudaError_t launch_encode(const Geom &g, const CompressWs &ws, uint8_t *d_out, cudaStream_t s, int sm_count) {
   if (g.bsize == 512) return launch_t<512>(g, ws, d_out, s, sm_count);

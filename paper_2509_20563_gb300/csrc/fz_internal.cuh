@@ -264,6 +264,39 @@ struct CompressWs {
   uint8_t *ids;            // per block: predictor id (per-block selection only)
 };
 
+// ---------------------------------------------------------------- batched calls
+// One field of a batched compress.  The host fills everything except
+// out_off, which k_batch_offsets writes once every stream size is known.
+struct BatchJob {
+  const float *x;
+  Geom g;
+  CompressWs ws;
+  double eb;
+  uint32_t eb_mode, R, pred, pad;
+  uint64_t range_base, range_segs;  // the field's range segments in the batch-wide segment queue
+  uint64_t qtile_base;              // first quantization tile in its quantizer class queue
+  uint64_t etile_base;              // first encode tile in its chunk-size class queue
+  uint64_t out_off;                 // byte offset of the field's stream in the packed output
+};
+
+// Batch-wide control words (zeroed with the fields' control blocks).
+struct BatchCtl {
+  uint32_t ticket[2];               // encode tickets of the two chunk-size classes (512, 1024)
+  uint32_t err;
+  uint32_t pad;
+  uint64_t total_bytes;             // packed output bytes
+};
+
+constexpr uint64_t kNoOutput = ~0ull;  // out_off of every field when the packed output does not fit
+
+// Launch shape of the batched kernels, chosen by the autotuner.
+struct BatchTune {
+  int range_seg_log2;   // elements per range segment = 2^range_seg_log2
+  int quant_per_sm;     // quantizer CTAs per SM
+  int encode_per_sm;    // encoder CTAs per SM
+  int decode_per_sm;    // decoder CTAs per SM
+};
+
 }  // namespace fz
 
 // Host-side launchers (defined in the .cu files).
@@ -299,4 +332,30 @@ cudaError_t launch_mlp_grad(const float *w, const uint16_t *feat, const uint8_t 
 cudaError_t launch_adam(float *w, const float *grad, float *m, float *v, uint16_t *w_bf16, uint32_t step, float lr,
                         float beta1, float beta2, float eps, cudaStream_t s);
 size_t mlp_partial_floats(uint32_t n);
+
+// batched compress stages (fields of one call described by a device table)
+cudaError_t launch_range_batch(const BatchJob *jobs, uint32_t n, uint64_t total_segs, int seg_log2,
+                               cudaStream_t s, int sm_count);
+cudaError_t launch_quant_batch(int ndim, int k, const BatchJob *jobs, const uint32_t *members, uint32_t n_members,
+                               uint64_t total_tiles, int per_sm, cudaStream_t s, int sm_count);
+cudaError_t launch_codebook_batch(const BatchJob *jobs, uint32_t n, cudaStream_t s);
+cudaError_t launch_batch_offsets(BatchJob *jobs, uint32_t n, uint64_t out_cap, BatchCtl *bctl, cudaStream_t s);
+cudaError_t launch_encode_batch(int chunk, const BatchJob *jobs, const uint32_t *members, uint32_t n_members,
+                                uint64_t total_tiles, uint32_t *ticket, uint8_t *d_out, int per_sm, cudaStream_t s,
+                                int sm_count);
+cudaError_t launch_assemble_batch(const BatchJob *jobs, uint32_t n, uint8_t *d_out, uint64_t max_n, cudaStream_t s,
+                                  int sm_count);
+// batched decompress (the job tables are opaque to the API layer)
+size_t dec_job_bytes();
+size_t plain_job_bytes();
+uint64_t dec_groups(const fz_header &h);
+void fill_dec_job(void *dst, const uint8_t *d_in, const fz_header &h, float *d_out, uint16_t *lut, uint64_t *gsum,
+                  uint32_t *err, uint64_t group_base);
+void fill_plain_job(void *dst, const uint8_t *d_in, uint64_t n, bool is_const, float *d_out);
+cudaError_t launch_decode_batch_prep(const void *jobs, uint32_t n, uint64_t max_groups, cudaStream_t s);
+cudaError_t launch_decode_batch_main(int ndim, int k, const void *jobs, const uint32_t *members, uint32_t n_members,
+                                     uint64_t total_groups, int per_sm, cudaStream_t s, int sms);
+cudaError_t launch_plain_batch(const void *jobs, uint32_t n, uint64_t max_n, cudaStream_t s, int sms);
+cudaError_t launch_batch_results(const BatchJob *jobs, uint32_t n, const BatchCtl *bctl, Result *res,
+                                 uint64_t *offsets, cudaStream_t s);
 }  // namespace fz

@@ -305,17 +305,17 @@ __device__ __forceinline__ void tile_codes12(const Geom &g, const TileXY &t, con
   }
 }
 
+// The tiles tile, tile + step, ... below t_end of one field, then the
+// field's histogram flush.  All threads of the CTA call it together.
 template <int NDIM, int K>
-__global__ void __launch_bounds__(kQuantThreads, 3) k_quant(const float *__restrict__ x, Geom g, uint32_t R,
-                                                             CompressWs ws) {
+__device__ __forceinline__ void quant_tiles(const float *__restrict__ x, const Geom &g, uint32_t R,
+                                            const CompressWs &ws, uint64_t tile, uint64_t t_end, uint64_t t_step,
+                                            QuantSmem<NDIM> &sm) {
   using S = TileShape<NDIM>;
-  using SM = QuantSmem<NDIM>;
   constexpr int kPerWarp = S::BX * S::BY * S::BZ / S::WPB;  // 512 positions
   constexpr int kIter = kPerWarp / 32;                      // 16
   static_assert(S::TX * S::ROWS == kTileElems, "tile size");
   static_assert(S::NB * S::WPB == kQuantThreads / 32, "warps per tile");
-  extern __shared__ __align__(16) unsigned char q_smem[];
-  SM &sm = *reinterpret_cast<SM *>(q_smem);
 
   Ctl *ctl = ws.ctl;
   if (ctl->mode != kModeNormal) return;
@@ -329,10 +329,9 @@ __global__ void __launch_bounds__(kQuantThreads, 3) k_quant(const float *__restr
   for (int s = tid; s < kMaxSym; s += kQuantThreads) sm.shist[s] = 0;
   const bool vec_ok = ((g.nx & 3u) == 0) && (((uintptr_t)x & 15u) == 0);
 
-  uint64_t tile = blockIdx.x;
   float4 v[4];
-  if (tile < g.n_qtiles) load_tile<NDIM>(x, g, tile_xy<NDIM>(g, tile), tid, vec_ok, v);
-  for (int buf = 0; tile < g.n_qtiles; tile += gridDim.x, buf ^= 1) {
+  if (tile < t_end) load_tile<NDIM>(x, g, tile_xy<NDIM>(g, tile), tid, vec_ok, v);
+  for (int buf = 0; tile < t_end; tile += t_step, buf ^= 1) {
     const TileXY t = tile_xy<NDIM>(g, tile);
     // a tile that lies wholly inside the domain skips every bounds test
     const bool interior = vec_ok && t.x0 + S::TX <= g.nx && t.y0 + S::BY <= g.ny && t.z0 + S::BZ <= g.nz;
@@ -346,8 +345,8 @@ __global__ void __launch_bounds__(kQuantThreads, 3) k_quant(const float *__restr
     __syncthreads();
     // ---- next tile's loads go out now and land while this tile is coded
     {
-      const uint64_t nt = tile + gridDim.x;
-      if (nt < g.n_qtiles) load_tile<NDIM>(x, g, tile_xy<NDIM>(g, nt), tid, vec_ok, v);
+      const uint64_t nt = tile + t_step;
+      if (nt < t_end) load_tile<NDIM>(x, g, tile_xy<NDIM>(g, nt), tid, vec_ok, v);
     }
     if (NDIM == 3) {
       if (interior) tile_codes3<K, true>(g, t, qc, ws, sq, sm.shist, q, exf, nout, nexc);
@@ -434,6 +433,49 @@ __global__ void __launch_bounds__(kQuantThreads, 3) k_quant(const float *__restr
 }
 
 template <int NDIM, int K>
+__global__ void __launch_bounds__(kQuantThreads, 3) k_quant(const float *__restrict__ x, Geom g, uint32_t R,
+                                                             CompressWs ws) {
+  extern __shared__ __align__(16) unsigned char q_smem[];
+  QuantSmem<NDIM> &sm = *reinterpret_cast<QuantSmem<NDIM> *>(q_smem);
+  quant_tiles<NDIM, K>(x, g, R, ws, blockIdx.x, g.n_qtiles, gridDim.x, sm);
+}
+
+// Batched variant: the quantization tiles of every field of one class
+// (dimensionality, Lorenzo order) form one queue, cut into equal contiguous
+// ranges, one per CTA; a CTA runs the fields its range overlaps in turn
+// (field parameters staged in shared memory, the histogram flushed per
+// field).
+template <int NDIM, int K>
+__global__ void __launch_bounds__(kQuantThreads, 3) k_quant_batch(const BatchJob *__restrict__ jobs,
+                                                                   const uint32_t *__restrict__ members,
+                                                                   uint32_t n_members, uint64_t total_tiles) {
+  extern __shared__ __align__(16) unsigned char q_smem[];
+  QuantSmem<NDIM> &sm = *reinterpret_cast<QuantSmem<NDIM> *>(q_smem);
+  __shared__ Geom sg;
+  __shared__ CompressWs sws;
+  __shared__ const float *sx;
+  __shared__ uint32_t sR;
+  const uint64_t lo = total_tiles * blockIdx.x / gridDim.x, hi = total_tiles * (blockIdx.x + 1) / gridDim.x;
+  // first member whose tiles reach past lo
+  uint32_t a = 0, b = n_members;
+  while (a < b) {
+    const uint32_t m = (a + b) >> 1;
+    const BatchJob &J = jobs[members[m]];
+    if (J.qtile_base + J.g.n_qtiles <= lo) a = m + 1; else b = m;
+  }
+  for (uint64_t t = lo; t < hi && a < n_members; ++a) {
+    const BatchJob &J = jobs[members[a]];
+    const uint64_t jb = J.qtile_base, je = jb + J.g.n_qtiles;
+    const uint64_t t0 = t > jb ? t : jb, t1 = hi < je ? hi : je;
+    __syncthreads();  // the previous field's flush is done with the staged parameters
+    if (threadIdx.x == 0) { sg = J.g; sws = J.ws; sx = J.x; sR = J.R; }
+    __syncthreads();
+    if (t0 < t1) quant_tiles<NDIM, K>(sx, sg, sR, sws, t0 - jb, t1 - jb, 1, sm);
+    t = t1;
+  }
+}
+
+template <int NDIM, int K>
 cudaError_t launch_t(const float *x, const Geom &g, uint32_t R, const CompressWs &ws, cudaStream_t s, int sms) {
   const int smem = (int)sizeof(QuantSmem<NDIM>);
   cudaError_t e = cudaFuncSetAttribute(k_quant<NDIM, K>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
@@ -448,7 +490,41 @@ cudaError_t launch_t(const float *x, const Geom &g, uint32_t R, const CompressWs
   return cudaGetLastError();
 }
 
+template <int NDIM, int K>
+cudaError_t launch_batch_t(const BatchJob *jobs, const uint32_t *members, uint32_t n_members, uint64_t total_tiles,
+                           int per_sm, cudaStream_t s, int sms) {
+  const int smem = (int)sizeof(QuantSmem<NDIM>);
+  cudaError_t e = cudaFuncSetAttribute(k_quant_batch<NDIM, K>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e != cudaSuccess) return e;
+  int occ = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_quant_batch<NDIM, K>, kQuantThreads, smem);
+  if (e != cudaSuccess) return e;
+  if (occ < 1) occ = 1;
+  if (per_sm < 1 || per_sm > occ) per_sm = occ;
+  uint64_t grid = (uint64_t)sms * per_sm;
+  if (grid > total_tiles) grid = total_tiles;
+  if (grid < 1) grid = 1;
+  k_quant_batch<NDIM, K><<<(unsigned)grid, kQuantThreads, smem, s>>>(jobs, members, n_members, total_tiles);
+  return cudaGetLastError();
+}
+
 }  // namespace
+
+cudaError_t launch_quant_batch(int ndim, int k, const BatchJob *jobs, const uint32_t *members, uint32_t n_members,
+                               uint64_t total_tiles, int per_sm, cudaStream_t s, int sm_count) {
+  const bool k2 = k == 2;
+  switch (ndim) {
+    case 1:
+      return k2 ? launch_batch_t<1, 2>(jobs, members, n_members, total_tiles, per_sm, s, sm_count)
+                : launch_batch_t<1, 1>(jobs, members, n_members, total_tiles, per_sm, s, sm_count);
+    case 2:
+      return k2 ? launch_batch_t<2, 2>(jobs, members, n_members, total_tiles, per_sm, s, sm_count)
+                : launch_batch_t<2, 1>(jobs, members, n_members, total_tiles, per_sm, s, sm_count);
+    default:
+      return k2 ? launch_batch_t<3, 2>(jobs, members, n_members, total_tiles, per_sm, s, sm_count)
+                : launch_batch_t<3, 1>(jobs, members, n_members, total_tiles, per_sm, s, sm_count);
+  }
+}
 
 cudaError_t launch_quant(const float *x, const Geom &g, uint32_t R, uint32_t pred, const CompressWs &ws,
                          cudaStream_t s, int sm_count) {

@@ -121,7 +121,76 @@ __global__ void __launch_bounds__(kRangeThreads) k_range(const float *__restrict
 
 __global__ void k_constants_abs(Ctl *ctl, double eb) { range_tail(ctl, FZ_EB_ABS, eb); }
 
+// Batched variant: every REL field is cut into segments of 2^seg_log2
+// values (an ABS field is one empty segment), and the segments of all
+// fields form one queue.  The CTA that finishes a field's last segment runs
+// that field's tail.
+__global__ void __launch_bounds__(kRangeThreads) k_range_batch(const BatchJob *__restrict__ jobs, uint32_t n,
+                                                                uint64_t total_segs, int seg_log2) {
+  __shared__ Acc sh[kRangeThreads / 32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (uint64_t sgi = blockIdx.x; sgi < total_segs; sgi += gridDim.x) {
+    uint32_t a = 0, b = n;  // the field whose segments contain sgi
+    while (a < b) {
+      const uint32_t m = (a + b) >> 1;
+      if (jobs[m].range_base + jobs[m].range_segs <= sgi) a = m + 1; else b = m;
+    }
+    const BatchJob &J = jobs[a];
+    Acc acc;
+    acc.init();
+    if (J.eb_mode == FZ_EB_REL) {
+      const uint64_t lo = (sgi - J.range_base) << seg_log2;
+      uint64_t hi = lo + (1ull << seg_log2);
+      if (hi > J.g.n) hi = J.g.n;
+      const float *x = J.x;
+      if (((uintptr_t)x & 15u) == 0) {
+        const float4 *x4 = reinterpret_cast<const float4 *>(x);
+        const uint64_t a4 = lo / 4, b4 = hi / 4;  // lo is a multiple of 4
+        for (uint64_t i = a4 + threadIdx.x; i < b4; i += kRangeThreads) {
+          const float4 v = __ldcs(x4 + i);
+          acc.add(v.x); acc.add(v.y); acc.add(v.z); acc.add(v.w);
+        }
+        for (uint64_t j = b4 * 4 + threadIdx.x; j < hi; j += kRangeThreads) acc.add(x[j]);
+      } else {
+        for (uint64_t j = lo + threadIdx.x; j < hi; j += kRangeThreads) acc.add(x[j]);
+      }
+    }
+    for (int off = 16; off > 0; off >>= 1) acc.shfl_merge(off);
+    if (lane == 0) sh[warp] = acc;
+    __syncthreads();
+    if (warp == 0) {
+      acc.init();
+      if (lane < kRangeThreads / 32) acc = sh[lane];
+      for (int off = 16; off > 0; off >>= 1) acc.shfl_merge(off);
+      if (lane == 0) {
+        Ctl *ctl = J.ws.ctl;
+        atomicMax(&ctl->lo_nkey, acc.lo_nkey);
+        atomicMax(&ctl->hi_key, acc.hi_key);
+        atomicMax(&ctl->bits_nmin, acc.bits_nmin);
+        atomicMax(&ctl->bits_max, acc.bits_max);
+        if (acc.any) atomicOr(&ctl->any_finite, 1u);
+        __threadfence();
+        const unsigned int done = atomicAdd(&ctl->range_done, 1u);
+        if (done == J.range_segs - 1) {
+          __threadfence();
+          range_tail(ctl, J.eb_mode, J.eb);
+        }
+      }
+    }
+    __syncthreads();
+  }
+}
+
 }  // namespace
+
+cudaError_t launch_range_batch(const BatchJob *jobs, uint32_t n, uint64_t total_segs, int seg_log2, cudaStream_t s,
+                               int sm_count) {
+  uint64_t grid = (uint64_t)sm_count * 4;
+  if (grid > total_segs) grid = total_segs;
+  if (grid < 1) grid = 1;
+  k_range_batch<<<(unsigned)grid, kRangeThreads, 0, s>>>(jobs, n, total_segs, seg_log2);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_range(const float *x, const Geom &g, uint32_t eb_mode, double eb, Ctl *ctl, cudaStream_t s) {
   if (eb_mode == FZ_EB_ABS) {

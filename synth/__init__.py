@@ -245,3 +245,34 @@ def stitched3d(n: int = 512, seed: int = 200, region: int = 64, device=None) -> 
                     a = 0.05 + 0.45 * float(torch.rand(1, generator=g, device=dev, dtype=f64))
                     out[sl] = a * (2.0 * torch.rand(base.shape, generator=g, device=dev, dtype=f64) - 1.0)
     return out.to(torch.float32)
+
+
+# --------------------------------------------------------------------------
+# batched workload: many fields of uneven size
+# --------------------------------------------------------------------------
+def batch_fields(seed: int = 5, n3: int = 32, n2: int = 32, scale: float = 1.0, device=None):
+    """n3 3D cubes with side U{32..256} (blob/sinusoid fields, blob count
+    proportional to the volume: 32 per 64^3, between 8 and 512) and n2 2D
+    lat/lon fields with each side U{512..4096} (spherical-harmonic fields),
+    in a seeded random order.  ``scale`` shrinks every side (for tests).
+    Returns a list of float32 tensors on ``device``."""
+    rng = np.random.default_rng(seed)
+    dev = _dev(device)
+    specs = []
+    for _ in range(n3):
+        side = max(2, int(round(int(rng.integers(32, 257)) * scale)))
+        specs.append(("3d", side, int(rng.integers(1 << 30))))
+    for _ in range(n2):
+        ny = max(8, int(round(int(rng.integers(512, 4097)) * scale)))
+        nx = max(160, int(round(int(rng.integers(512, 4097)) * scale)))
+        specs.append(("2d", (ny, nx), int(rng.integers(1 << 30))))
+    order = rng.permutation(len(specs))
+    out = []
+    for i in order:
+        kind, size, s = specs[i]
+        if kind == "3d":
+            nb = int(min(512, max(8, round(32 * size ** 3 / 64 ** 3))))
+            out.append(blobs3d((size, size, size), seed=s, n_blobs=nb, device=dev).contiguous())
+        else:
+            out.append(cesm2d(size[0], size[1], seed=s).to(dev).contiguous())
+    return out

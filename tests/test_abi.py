@@ -71,3 +71,18 @@ def test_null_arguments_rejected_without_gpu(fzlib):
     nb = C.c_uint64()
     assert fzlib.fz_compress(None, None, 1, d, 1, 1e-3, None, None, 0, C.byref(nb), None, None) == 1
     assert fzlib.fz_decompress(None, None, 0, None, None, 0, None) == 1
+
+
+def test_batch_bound_and_argument_checks(fzlib):
+    ndim = (C.c_uint32 * 3)(3, 2, 1)
+    dims = (C.c_uint64 * 9)(10, 10, 10, 33, 65, 7, 100003, 9, 9)
+    want = sum((256 + 4 * n + 15) // 16 * 16 for n in (1000, 33 * 65, 100003))
+    assert fzlib.fz_compress_batch_bound(3, ndim, dims) == want
+    assert fzlib.fz_compress_batch_bound(0, ndim, dims) == 0
+    bad = (C.c_uint32 * 3)(3, 4, 1)
+    assert fzlib.fz_compress_batch_bound(3, bad, dims) == 0
+    # argument errors are reported before any device work
+    offs = (C.c_uint64 * 4)()
+    assert fzlib.fz_compress_batch(None, 3, None, ndim, dims, 1, None, None, None, 0, offs, None) == 1
+    assert fzlib.fz_decompress_batch(None, 0, None, offs, None, None, None) == 1
+    assert fzlib.fz_ctx_set_batch_options(None, 1, 1) == 1

@@ -1,0 +1,143 @@
+"""Batched compression: every stream of a batched call is byte-identical to
+the single-field call (and to the oracle), batched decompression matches
+single-field decompression bit for bit, and the cached graph replays
+correctly with new data of the same shapes."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+fz = None
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    global fz
+    from paper_2509_20563_gb300 import build
+    build.build()
+    import paper_2509_20563_gb300 as m
+    m.lib()
+    fz = m
+
+
+def _fields(seed=5):
+    fs = synth.batch_fields(seed=seed, n3=5, n2=5, scale=0.125, device="cpu")
+    nanf = synth.smooth_nd((17, 30, 24), 4).clone()
+    nanf[3, 4, 5] = float("nan")
+    nanf[9, 0, 23] = float("inf")
+    extra = [
+        synth.smooth_nd((100003,), 3),                 # 1D, ragged last block
+        torch.full((16, 16, 16), 1.5),                 # constant field
+        torch.rand(20, 20, 20, generator=torch.Generator().manual_seed(seed)),  # raw fallback at a tiny bound
+        nanf,                                          # exceptions
+        synth.smooth_nd((5,), 6),                      # tiny 1D
+        synth.smooth_nd((33, 65), 7),                  # 2D, ragged blocks
+    ]
+    fs = fs[:4] + extra[:3] + fs[4:8] + extra[3:] + fs[8:]
+    ebs = [1e-7 if f.shape == (20, 20, 20) else 1e-3 for f in fs]
+    return [f.contiguous() for f in fs], ebs
+
+
+def _check_batch(xs, ebs, mode="rel", predictor="lorenzo1", with_oracle=True):
+    xg = [x.cuda() for x in xs]
+    buf, offs = fz.compress_batch(xg, ebs, mode=mode, predictor=predictor)
+    assert len(offs) == len(xs) + 1
+    hb = buf[: offs[-1]].cpu().numpy()
+    singles = []
+    for j, (x, eb) in enumerate(zip(xs, ebs)):
+        one = fz.compress(xg[j], eb, mode=mode, predictor=predictor)
+        s = one.cpu().numpy()
+        assert offs[j] % 16 == 0
+        assert offs[j + 1] - offs[j] == (s.size + 15) // 16 * 16, j
+        assert np.array_equal(hb[offs[j]: offs[j] + s.size], s), j
+        if with_oracle:
+            ref = oracle.compress(x.numpy(), eb, mode=mode, lorenzo_k=2 if predictor == "lorenzo2" else 1)
+            assert np.array_equal(s, ref), j
+        singles.append(one)
+    ys = fz.decompress_batch(buf, offs)
+    for j, (x, eb) in enumerate(zip(xs, ebs)):
+        y1 = fz.decompress(singles[j])
+        assert ys[j].shape == x.shape
+        assert np.array_equal(ys[j].cpu().numpy().view(np.uint32), y1.cpu().numpy().view(np.uint32)), j
+        xn = x.numpy().astype(np.float64)
+        f = np.isfinite(xn)
+        if f.any() and mode == "rel":
+            eba = eb * (xn[f].max() - xn[f].min())
+        else:
+            eba = eb
+        assert (np.abs(xn[f] - ys[j].cpu().numpy()[f]) <= eba).all(), j
+    return buf, offs
+
+
+def test_batch_matches_single_calls_and_oracle():
+    xs, ebs = _fields()
+    _check_batch(xs, ebs)
+
+
+def test_batch_graph_replay_with_new_data():
+    xs, ebs = _fields()
+    _check_batch(xs, ebs, with_oracle=False)
+    # same shapes, new values and bounds: the cached graph runs with the new table
+    xs2 = [(x * 1.7 + 0.25).contiguous() for x in xs]
+    ebs2 = [e * 2 for e in ebs]
+    _check_batch(xs2, ebs2)
+    _check_batch(xs2, ebs2, with_oracle=False)
+    prof = fz.profile()
+    assert prof.batch_graphs >= 1 and prof.batch_graphs == prof.batch_plans
+
+
+@pytest.mark.parametrize("mode,predictor", [("abs", "lorenzo2"), ("rel", "lorenzo2"), ("abs", "lorenzo1")])
+def test_batch_modes(mode, predictor):
+    xs, ebs = _fields(seed=8)
+    if mode == "abs":
+        ebs = [1e-3 if e > 1e-6 else 1e-9 for e in ebs]
+    _check_batch(xs, ebs, mode=mode, predictor=predictor)
+
+
+def test_batch_options_do_not_change_bytes():
+    xs, ebs = _fields(seed=9)
+    xg = [x.cuda() for x in xs]
+    ref, ro = fz.compress_batch(xg, ebs)
+    ref = ref[: ro[-1]].cpu().numpy()
+    try:
+        for tune, graphs in [(False, False), (False, True), (True, False)]:
+            fz.set_batch_options(autotune=tune, graphs=graphs)
+            for _ in range(2):
+                buf, offs = fz.compress_batch(xg, ebs)
+                assert offs == ro
+                assert np.array_equal(buf[: offs[-1]].cpu().numpy(), ref)
+    finally:
+        fz.set_batch_options(True, True)
+
+
+def test_batch_output_too_small():
+    xs, ebs = _fields(seed=10)
+    xg = [x.cuda() for x in xs]
+    _, offs = fz.compress_batch(xg, ebs)
+    small = torch.zeros(offs[-1] - 16, dtype=torch.uint8, device="cuda")
+    with pytest.raises(fz.FzError) as e:
+        fz.compress_batch(xg, ebs, out=small)
+    assert e.value.code == 4
+    # the context stays usable
+    buf, offs2 = fz.compress_batch(xg, ebs)
+    assert offs2 == offs
+
+
+def test_batch_full_size_workload():
+    """The 64-field workload (32 cubes of side 32-256, 32 lat/lon fields of
+    side 512-4096) at REL 1e-4: every stream equals the single-field call and
+    every reconstruction is within the bound."""
+    xs = synth.batch_fields(seed=5, device="cuda")
+    assert len(xs) == 64
+    buf, offs = fz.compress_batch(xs, 1e-4)
+    ys = fz.decompress_batch(buf, offs)
+    for j, x in enumerate(xs):
+        one = fz.compress(x, 1e-4)
+        assert torch.equal(buf[offs[j]: offs[j] + one.numel()], one), j
+        eba = 1e-4 * (float(x.max()) - float(x.min()))
+        assert float((ys[j].double() - x.double()).abs().max()) <= eba, j
+        del one
