@@ -74,7 +74,7 @@ class Clocks:
             os.makedirs(os.path.dirname(self.path), exist_ok=True)
             self.f = open(self.path, "w")
             self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
-                                          "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+                                          "-lms", "100"], stdout=self.f, stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
 
@@ -305,11 +305,103 @@ def run_fz(args, rank, world, local_rank):
         res["e2e"] = {"value": round(args.e2e_steps * world * 4 * N / (ems * 1e-3) / 1e9, 2), "unit": "GB/s",
                       "h2d_bytes_per_step": 4 * N + nb, "d2h_bytes_per_step": nb + 4 * N,
                       "steps": args.e2e_steps}
+    if rank == 0 and world == 1 and not args.no_batch:
+        res["batch"] = bench_batch(fz, dev, stream, args)
+    if rank == 0 and world == 1 and not args.no_learned:
+        res["learned"] = bench_learned(fz, dev, args)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         res["cpu_baseline"] = cpu_baseline(x, args.cpu_slab, args.eb)
     if rank == 0:
         print(json.dumps(res), flush=True)
     ctx.close()
+
+
+def bench_batch(fz, dev, stream, args):
+    """64 fields of uneven size (32 cubes of side 32-256, 32 lat/lon fields of
+    side 512-4096) at REL 1e-4: one batched call (graph replay after the
+    first, autotuned call) against one fz_compress call per field; both
+    timed with CUDA events on the launching stream."""
+    xs = synth.batch_fields(seed=5, device=dev)
+    n_vals = sum(x.numel() for x in xs)
+    ctx = fz.Context(dev.index or 0)
+    buf, offs = fz.compress_batch(xs, args.eb, ctx=ctx)      # autotune + capture
+    for _ in range(2):
+        buf, offs = fz.compress_batch(xs, args.eb, out=buf, ctx=ctx)
+    ys = fz.decompress_batch(buf, offs, ctx=ctx)
+    for _ in range(2):
+        fz.decompress_batch(buf, offs, outs=ys, ctx=ctx)
+    S = offs[-1]
+    reps = 5
+
+    def timed(fn):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize(dev)
+        e0.record(stream)
+        for _ in range(reps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        return e0.elapsed_time(e1) / reps
+
+    t_bc = timed(lambda: fz.compress_batch(xs, args.eb, out=buf, ctx=ctx))
+    t_bd = timed(lambda: fz.decompress_batch(buf, offs, outs=ys, ctx=ctx))
+    outs = [torch.empty(fz.compress_bound(x.shape), dtype=torch.uint8, device=dev) for x in xs]
+    singles = [fz.compress(x, args.eb, out=o) for x, o in zip(xs, outs)]
+    t_sc = timed(lambda: [fz.compress(x, args.eb, out=o) for x, o in zip(xs, outs)])
+    recon = [torch.empty_like(x) for x in xs]
+    t_sd = timed(lambda: [fz.decompress(b, out=r) for b, r in zip(singles, recon)])
+    peak, _ = _peaks()
+    forced_c = 12 * n_vals + S
+    forced_d = 4 * n_vals + S
+    prof = fz.profile(ctx=ctx)
+    ctx.close()
+    gb = lambda t: round(4 * n_vals / (t * 1e-3) / 1e9, 2)
+    return {"workload": "64 fields: 32 cubes side U{32..256} + 32 lat/lon fields sides U{512..4096}, REL 1e-4",
+            "values": n_vals, "stream_bytes": S, "cr": round(4 * n_vals / S, 4),
+            "batch_compress_ms": round(t_bc, 4), "per_field_compress_ms": round(t_sc, 4),
+            "batch_decompress_ms": round(t_bd, 4), "per_field_decompress_ms": round(t_sd, 4),
+            "batch_compress_gbs": gb(t_bc), "per_field_compress_gbs": gb(t_sc),
+            "batch_decompress_gbs": gb(t_bd), "per_field_decompress_gbs": gb(t_sd),
+            "batch_compress_roofline_frac": round(forced_c / (t_bc * 1e-3) / 1e9 / peak, 4),
+            "batch_decompress_roofline_frac": round(forced_d / (t_bd * 1e-3) / 1e9 / peak, 4),
+            "speedup_compress": round(t_sc / t_bc, 3), "speedup_decompress": round(t_sd / t_bd, 3),
+            "graphs": int(prof.batch_graphs), "plans": int(prof.batch_plans)}
+
+
+def bench_learned(fz, dev, args):
+    """Selector network trained on the GPU (exhaustive-trial labels of 16
+    stitched 256^3 fields, seeds 100-115), then compression ratio and
+    throughput of plain Lorenzo-1, the exhaustive per-block trial and the
+    network on the unseen stitched 512^3 field (seed 200) at REL 1e-4."""
+    import paper_2509_20563_gb300.selector as sel
+    t0 = time.perf_counter()
+    fields = [synth.stitched3d(256, seed=100 + i, region=64, device=dev) for i in range(16)]
+    feat, lab = sel.collect(fields, args.eb)
+    del fields
+    w, wb, hist = sel.train(feat, lab, epochs=12, batch=4096, lr=3e-3, seed=0)
+    t_train = time.perf_counter() - t0
+    x = synth.stitched3d(512, seed=200, region=64, device=dev)
+    out = {"workload": "stitched 512^3 (smooth / oscillatory / noisy 64^3 regions), REL 1e-4, 8^3 blocks",
+           "train_seconds": round(t_train, 2), "train_blocks": int(lab.numel()), "final_loss": round(hist[-1], 4)}
+    N = x.numel()
+    for name, kw in [("plain", {"predictor": "lorenzo1"}), ("exhaustive", {"predictor": "exhaustive"}),
+                     ("mlp", {"predictor": "mlp", "selector_weights": wb})]:
+        buf = fz.compress(x, args.eb, **kw)
+        y = fz.decompress(buf)
+        err = float((y.double() - x.double()).abs().max()) / (args.eb * (float(x.max()) - float(x.min())))
+        ob = torch.empty(fz.compress_bound(x.shape), dtype=torch.uint8, device=dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(3):
+            fz.compress(x, args.eb, out=ob, **kw)
+        e1.record()
+        torch.cuda.synchronize(dev)
+        out[f"cr_{name}"] = round(4 * N / buf.numel(), 4)
+        out[f"compress_gbs_{name}"] = round(4 * N * 3 / (e0.elapsed_time(e1) * 1e-3) / 1e9, 2)
+        out[f"max_err_over_eb_{name}"] = round(err, 6)
+    out["mlp_vs_exhaustive"] = round(out["cr_mlp"] / out["cr_exhaustive"], 4)
+    out["mlp_vs_plain"] = round(out["cr_mlp"] / out["cr_plain"], 4)
+    return out
 
 
 def _launches(L, ctx):
@@ -322,7 +414,7 @@ def _launches(L, ctx):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=400)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="fz", choices=["fz", "reference"])
     ap.add_argument("--size", type=int, default=512)
@@ -331,6 +423,8 @@ def main():
     ap.add_argument("--cpu-slab", type=int, default=160, help="z-slab of the field the CPU oracle times")
     ap.add_argument("--ref-slab", type=int, default=16, help="z-slab per step for --impl reference")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batch", action="store_true", help="skip the 64-field batched workload")
+    ap.add_argument("--no-learned", action="store_true", help="skip the selector training and CR comparison")
     ap.add_argument("--traffic", type=float, default=None, help="ncu dram bytes per launch of the dominant kernel")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))

@@ -395,11 +395,11 @@ fz_status fz_decompress(fz_ctx *ctx, const void *d_in, uint64_t in_bytes, const 
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     return from_cuda(e);
   }
-  const uint64_t n_groups = (h.n_chunks + kDecThreads - 1) / kDecThreads;
+  const uint64_t n_units = dec_units_of(h.n_chunks);
   size_t off = 0;
   auto take = [&](size_t bytes) { size_t o = off; off += up(bytes); return o; };
   const bool selpath = h.predictor > FZ_PRED_LORENZO2;
-  const size_t o_err = take(16), o_lut = take(2u << kLutBits), o_gsum = take(8 * n_groups),
+  const size_t o_err = take(16), o_lut = take(2u << kLutBits), o_gsum = take(8 * n_units),
                o_codes = selpath ? take(2 * g.npad) : 0;
   if ((st = ensure_ws(ctx, off))) return st;
   char *base = reinterpret_cast<char *>(ctx->ws);

@@ -418,7 +418,7 @@ fz_status fz_decompress_batch(fz_ctx *ctx, uint32_t n, const void *d_in, const u
   std::vector<Geom> geo(n);
   std::vector<uint32_t> dec, plain;
   std::vector<uint32_t> mem[kQClasses];
-  uint64_t groups[kQClasses] = {}, max_groups = 0, max_plain = 0;
+  uint64_t units[kQClasses] = {}, max_units = 0, max_plain = 0;
   std::vector<uint64_t> key;
   key.push_back(1);
   key.push_back(n);
@@ -435,8 +435,8 @@ fz_status fz_decompress_batch(fz_ctx *ctx, uint32_t n, const void *d_in, const u
       if (h.predictor > FZ_PRED_LORENZO2) return FZ_EUNSUPPORTED;
       const int c = qclass(h.ndim, h.predictor == FZ_PRED_LORENZO2 ? 2 : 1);
       mem[c].push_back((uint32_t)dec.size());
-      groups[c] += dec_groups(h);
-      if (dec_groups(h) > max_groups) max_groups = dec_groups(h);
+      units[c] += dec_units(h);
+      if (dec_units(h) > max_units) max_units = dec_units(h);
       dec.push_back(j);
     }
     key.push_back(h.flags);
@@ -455,7 +455,7 @@ fz_status fz_decompress_batch(fz_ctx *ctx, uint32_t n, const void *d_in, const u
     o_lut[i] = dev;
     dev += up(2u << kLutBits);
     o_gsum[i] = dev;
-    dev += up(8 * dec_groups(hs[dec[i]]));
+    dev += up(8 * dec_units(hs[dec[i]]));
   }
   if ((st = ensure_batch_mem(ctx, dev, up(hdr_bytes) + up(tbl) + up(16)))) return st;
   char *dbase = reinterpret_cast<char *>(ctx->bws);
@@ -473,7 +473,7 @@ fz_status fz_decompress_batch(fz_ctx *ctx, uint32_t n, const void *d_in, const u
       const int c = qclass(h.ndim, h.predictor == FZ_PRED_LORENZO2 ? 2 : 1);
       fill_dec_job(htbl + djb * i, in + h_offsets[j], h, d_out[j], reinterpret_cast<uint16_t *>(dbase + o_lut[i]),
                    reinterpret_cast<uint64_t *>(dbase + o_gsum[i]), derr, gb[c]);
-      gb[c] += dec_groups(h);
+      gb[c] += dec_units(h);
     }
     for (uint32_t i = 0; i < np; ++i) {
       const uint32_t j = plain[i];
@@ -494,10 +494,10 @@ fz_status fz_decompress_batch(fz_ctx *ctx, uint32_t n, const void *d_in, const u
   auto enqueue = [&](const BatchTune &t, cudaStream_t q) -> cudaError_t {
     cudaError_t e2 = cudaMemsetAsync(derr, 0, 16, q);
     if (e2 == cudaSuccess) e2 = cudaMemcpyAsync(ddec, htbl, tbl, cudaMemcpyHostToDevice, q);
-    if (e2 == cudaSuccess && nd) e2 = launch_decode_batch_prep(ddec, nd, max_groups, q);
+    if (e2 == cudaSuccess && nd) e2 = launch_decode_batch_prep(ddec, nd, max_units, q);
     for (int c = 0; c < kQClasses && e2 == cudaSuccess; ++c) {
       if (mem[c].empty()) continue;
-      e2 = launch_decode_batch_main(c / 2 + 1, c % 2 + 1, ddec, dmem + moff[c], (uint32_t)mem[c].size(), groups[c],
+      e2 = launch_decode_batch_main(c / 2 + 1, c % 2 + 1, ddec, dmem + moff[c], (uint32_t)mem[c].size(), units[c],
                                     t.decode_per_sm, q, ctx->sm_count);
     }
     if (e2 == cudaSuccess && np) e2 = launch_plain_batch(dplain, np, max_plain, q, ctx->sm_count);

@@ -33,27 +33,20 @@ constexpr int kPrepThreads = 1024;
 
 __device__ __forceinline__ void dec_err(uint32_t *err, uint32_t code) { atomicCAS(err, 0u, code); }
 
-__global__ void k_dec_gsum(const uint32_t *__restrict__ chunk_bits, uint64_t n_chunks, uint64_t n_groups,
-                           uint64_t *gsum) {
-  const uint64_t gidx = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+// Bit length of every work unit (kDecUnit chunks): one warp per unit.
+__global__ void k_dec_gsum(const uint32_t *__restrict__ chunk_bits, uint64_t n_chunks, uint64_t n_units,
+                           uint64_t *usum) {
+  const uint64_t u = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
-  if (gidx >= n_groups) return;
-  constexpr int kPerLane = kDecThreads / 32;  // 8
-  const uint64_t c0 = gidx * kDecThreads + kPerLane * lane;
-  unsigned long long s = 0;
-  if (c0 + kPerLane - 1 < n_chunks) {
-    const uint4 v = *reinterpret_cast<const uint4 *>(chunk_bits + c0);
-    const uint4 w = *reinterpret_cast<const uint4 *>(chunk_bits + c0 + 4);
-    s = (unsigned long long)v.x + v.y + v.z + v.w + w.x + w.y + w.z + w.w;
-  } else {
-    for (uint64_t c = c0; c < n_chunks && c < c0 + kPerLane; ++c) s += chunk_bits[c];
-  }
-  for (int off = 16; off > 0; off >>= 1) s += __shfl_down_sync(0xffffffffu, s, off);
-  if (lane == 0) gsum[gidx] = s;
+  if (u >= n_units) return;
+  const uint64_t j = u * kDecUnit + lane;
+  uint32_t v = j < n_chunks ? __ldg(chunk_bits + j) : 0u;
+  v = __reduce_add_sync(0xffffffffu, v);
+  if (lane == 0) usum[u] = v;
 }
 
 __device__ __forceinline__ void k_dec_prep_body(const uint8_t *__restrict__ lens_in, uint32_t nsym, uint64_t *gsum,
-                                                uint64_t n_groups, uint64_t total_bits, uint16_t *lut, uint32_t *err) {
+                                                uint64_t n_units, uint64_t total_bits, uint16_t *lut, uint32_t *err) {
   __shared__ uint32_t first[kLmax + 1], cnt[kLmax + 1], basel[kLmax + 1];
   __shared__ uint32_t wcnt[32][kLmax + 1];
   __shared__ uint32_t wk[32];
@@ -117,15 +110,15 @@ __device__ __forceinline__ void k_dec_prep_body(const uint8_t *__restrict__ lens
     for (int l = 1; l <= kLmax; ++l) {
       const uint32_t c = (uint32_t)e >> (kLmax - l);
       if (cnt[l] && c >= first[l] && c - first[l] < cnt[l])
-        v = (uint16_t)(kLutValid | ((l - 1) << 10) | sorted[basel[l] + c - first[l]]);
+        v = (uint16_t)((l << kLutLenShift) | sorted[basel[l] + c - first[l]]);
     }
     lut[e] = v;
   }
-  // exclusive scan of the group bit sums (in place)
-  const uint64_t per = (n_groups + kPrepThreads - 1) / kPrepThreads;
+  // exclusive scan of the work units' bit sums (in place)
+  const uint64_t per = (n_units + kPrepThreads - 1) / kPrepThreads;
   const uint64_t g0 = (uint64_t)t * per;
   unsigned long long loc = 0;
-  for (uint64_t i = g0; i < g0 + per && i < n_groups; ++i) loc += gsum[i];
+  for (uint64_t i = g0; i < g0 + per && i < n_units; ++i) loc += gsum[i];
   unsigned long long incl = loc;
   for (int off = 1; off < 32; off <<= 1) {
     unsigned long long v = __shfl_up_sync(0xffffffffu, incl, off);
@@ -144,7 +137,7 @@ __device__ __forceinline__ void k_dec_prep_body(const uint8_t *__restrict__ lens
   }
   __syncthreads();
   unsigned long long run = wsum[warp] + incl - loc;
-  for (uint64_t i = g0; i < g0 + per && i < n_groups; ++i) {
+  for (uint64_t i = g0; i < g0 + per && i < n_units; ++i) {
     unsigned long long v = gsum[i];
     gsum[i] = run;
     run += v;
@@ -152,9 +145,9 @@ __device__ __forceinline__ void k_dec_prep_body(const uint8_t *__restrict__ lens
 }
 
 __global__ void __launch_bounds__(kPrepThreads) k_dec_prep(const uint8_t *__restrict__ lens_in, uint32_t nsym,
-                                                            uint64_t *gsum, uint64_t n_groups,
+                                                            uint64_t *gsum, uint64_t n_units,
                                                             uint64_t total_bits, uint16_t *lut, uint32_t *err) {
-  k_dec_prep_body(lens_in, nsym, gsum, n_groups, total_bits, lut, err);
+  k_dec_prep_body(lens_in, nsym, gsum, n_units, total_bits, lut, err);
 }
 
 struct DecParams {
@@ -166,10 +159,10 @@ struct DecParams {
   const int32_t *out_val;
   const uint32_t *exc_idx;
   const uint32_t *exc_val;
-  uint64_t n_out, n_exc, n_chunks, n_groups;
-  const uint64_t *goff;
+  uint64_t n_out, n_exc, n_chunks, n_units;
+  const uint64_t *goff;   // per work unit: first bit
   const uint16_t *lut;
-  uint32_t *err;
+  uint32_t *err;          // err[0] error word, err[1] work-unit counter
   float *out;
   float ebx2;
   int32_t R;
@@ -230,19 +223,6 @@ __device__ __forceinline__ void init_side(const DecParams &p, Side &sd, uint32_t
   }
 }
 
-// Residual of the next symbol: code - R, or the stored outlier for code 0.
-__device__ __forceinline__ int32_t next_delta(BitReader &br, const uint16_t *slut, const DecParams &p, Side &sd,
-                                              uint32_t pos0, uint32_t pos, bool &bad) {
-  const uint32_t sym = br.next(slut);
-  if (sym == 0) {
-    const OutlierHit h = fetch_outlier(p.out_idx, p.out_val, p.n_out, sd.oc, pos0, pos);
-    sd.oc = h.oc;
-    bad |= !h.ok;
-    return h.value;
-  }
-  return (int32_t)sym - p.R;
-}
-
 template <bool EXC>
 __device__ __forceinline__ float value(const DecParams &p, Side &sd, uint32_t pos, int32_t q) {
   float v = __fmul_rn(__int2float_rn(q), p.ebx2);
@@ -264,6 +244,20 @@ __device__ __forceinline__ void store4(float *out, uint64_t f, bool vec, const f
   }
 }
 
+// Eight consecutive outputs of a block row starting at field index f, of
+// which those below x_end (field x) exist.
+__device__ __forceinline__ void store8(float *out, uint64_t f, bool full, bool vec, uint32_t x0, uint32_t nx,
+                                       const float (&o)[8]) {
+  if (full) {
+    store4(out, f, vec, o);
+    store4(out, f + 4, vec, o + 4);
+  } else {
+#pragma unroll
+    for (int u = 0; u < 8; ++u)
+      if (x0 + u < nx) out[f + u] = o[u];
+  }
+}
+
 // Per-thread prefix state that does not fit registers lives in shared
 // memory, one column per thread ([i][thread] layout, conflict-free):
 // 3D: the plane sums P (64 per order), 2D: the column sums Y (32 per order).
@@ -272,19 +266,136 @@ struct DecState {
   static constexpr int kWords = NDIM == 3 ? 64 * K : (NDIM == 2 ? 32 * K : 0);
 };
 
+// Threads per decode CTA (one CTA per SM).  The decode table is shared by
+// all of them, and the rest of the SM's 256 KB of shared memory + L1 is
+// split between the per-thread state and L1, which must keep about one
+// 128-byte line of every thread's bitstream resident: the asynchronous word
+// copies then hit L1 instead of going to L2 one sector per word.
+#ifndef FZ_DEC_T3
+#define FZ_DEC_T3 448
+#endif
+template <int NDIM, int K>
+struct DecCta {
+  static constexpr int T = NDIM == 3 ? (K == 1 ? FZ_DEC_T3 : 288) : (NDIM == 2 ? (K == 1 ? 640 : 448) : 768);
+};
+
 template <int NDIM, int K>
 constexpr size_t dec_smem_bytes() {
   return sizeof(uint16_t) * kLutSize +
-         sizeof(int32_t) * (size_t)(DecState<NDIM, K>::kWords + kRing) * kDecThreads;
+         sizeof(int32_t) * (size_t)(DecState<NDIM, K>::kWords + kRing) * DecCta<NDIM, K>::T;
 }
 
-template <int NDIM, int K, bool EXC>
+// The stored residuals of the outliers among eight codes (code 0 decodes
+// to -R, which no in-range code gives).  Rare: out of the decode loop's
+// straight-line code.
+__device__ __forceinline__ void fix_outliers(const DecParams &p, Side &sd, uint32_t pos0, uint32_t pos,
+                                             int32_t (&d)[8], bool &bad) {
+#pragma unroll
+  for (int u = 0; u < 8; ++u) {
+    if (d[u] == -p.R) {
+      const OutlierHit h = fetch_outlier(p.out_idx, p.out_val, p.n_out, sd.oc, pos0, pos + u);
+      sd.oc = h.oc;
+      bad |= !h.ok;
+      d[u] = h.value;
+    }
+  }
+}
+
+// Prefix-sum state of the inverse Lorenzo for one chunk.
+struct Prefix {
+  int32_t r1, r2;          // running sums along x (orders 1, 2)
+  int32_t Y1[8], Y2[8];    // 3D: per-column sums along y within the plane
+};
+
+// Inverse Lorenzo, dequantization and store of group gi (eight codes) of a
+// chunk: 3D group = one x-row (z = gi / 8, y = gi % 8); 2D group = a quarter
+// row (y = gi / 4); 1D group = eight consecutive values.
+template <int NDIM, int K, bool EXC, int T>
+__device__ __forceinline__ void consume(const DecParams &p, const Geom &g, Side &sd, Prefix &s, int32_t *st,
+                                        int gi, const int32_t (&d)[8], uint32_t pos0, uint32_t X0, uint32_t Y0,
+                                        uint32_t Z0, bool vecbase) {
+  float o[8];
+  const uint32_t pos = pos0 + (uint32_t)gi * 8;
+  if (NDIM == 3) {
+    const int y = gi & 7, z = gi >> 3;
+#pragma unroll
+    for (int x = 0; x < 8; ++x) {
+      s.Y1[x] = y ? s.Y1[x] : 0;
+      if (K == 2) s.Y2[x] = y ? s.Y2[x] : 0;
+    }
+    int32_t *row = st + (y * 8) * T;
+    int32_t r1 = 0, r2 = 0;
+#pragma unroll
+    for (int x = 0; x < 8; ++x) {
+      int32_t q;
+      if (K == 1) {
+        r1 += d[x];
+        s.Y1[x] += r1;
+        q = row[x * T] + s.Y1[x];
+        row[x * T] = q;
+      } else {
+        r1 += d[x];
+        r2 += r1;
+        s.Y1[x] += r2;
+        s.Y2[x] += s.Y1[x];
+        const int32_t p1 = row[x * T] + s.Y2[x];
+        row[x * T] = p1;
+        q = row[(64 + x) * T] + p1;
+        row[(64 + x) * T] = q;
+      }
+      o[x] = value<EXC>(p, sd, pos + x, q);
+    }
+    if (Z0 + z < g.nz && Y0 + y < g.ny)
+      store8(p.out, ((uint64_t)(Z0 + z) * g.ny + (Y0 + y)) * g.nx + X0, X0 + 8 <= g.nx, vecbase, X0, g.nx, o);
+  } else if (NDIM == 2) {
+    const int y = gi >> 2, x8 = gi & 3;
+    s.r1 = x8 ? s.r1 : 0;
+    if (K == 2) s.r2 = x8 ? s.r2 : 0;
+    int32_t *col = st + (x8 * 8) * T;
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      int32_t q;
+      if (K == 1) {
+        s.r1 += d[u];
+        q = col[u * T] + s.r1;
+        col[u * T] = q;
+      } else {
+        s.r1 += d[u];
+        s.r2 += s.r1;
+        const int32_t y1 = col[u * T] + s.r2;
+        col[u * T] = y1;
+        q = col[(32 + u) * T] + y1;
+        col[(32 + u) * T] = q;
+      }
+      o[u] = value<EXC>(p, sd, pos + u, q);
+    }
+    if (Y0 + y < g.ny)
+      store8(p.out, (uint64_t)(Y0 + y) * g.nx + X0 + 8 * x8, X0 + 8 * x8 + 8 <= g.nx, vecbase, X0 + 8 * x8, g.nx,
+             o);
+  } else {
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      s.r1 += d[u];
+      if (K == 2) s.r2 += s.r1;
+      o[u] = value<EXC>(p, sd, pos + u, K == 1 ? s.r1 : s.r2);
+    }
+    const uint32_t x0 = X0 + 8 * (uint32_t)gi;
+    store8(p.out, x0, x0 + 8 <= g.nx, vecbase, x0, g.nx, o);
+  }
+}
+
+// One chunk (= one block).  The codes are decoded eight at a time, one
+// group ahead of the reconstruction: the decode of group gi+1 (a serial
+// chain through the bit reader) and the reconstruction of group gi
+// (independent arithmetic and stores) sit in the same straight-line code,
+// so they overlap.  Outliers are looked up per group, off that path.
+template <int NDIM, int K, bool EXC, int T>
 __device__ __forceinline__ void decode_chunk(const DecParams &p, const Geom &g, const uint16_t *slut,
-                                             int32_t *st, uint32_t *ring, uint64_t j, uint64_t start, bool vecbase) {
-  constexpr int T = kDecThreads;
+                                             int32_t *st, uint32_t *ring, uint64_t j, uint64_t start,
+                                             uint32_t cbits, bool vecbase) {
+  constexpr int NG = (NDIM == 3 ? 512 : 1024) / 8;
   bool bad = false;
-  BitReader br;
-  const uint32_t cbits = __ldg(p.chunk_bits + j);
+  BitReader<T> br;
   br.init(p.words, p.n_words, start, cbits, ring);
   const uint32_t start_off = br.off;
   const uint32_t pos0 = (uint32_t)(j * g.bsize);
@@ -296,174 +407,70 @@ __device__ __forceinline__ void decode_chunk(const DecParams &p, const Geom &g, 
   const uint32_t byi = (uint32_t)(jr % g.nby), bzi = (uint32_t)(jr / g.nby);
   const uint32_t X0 = bxi * g.bx, Y0 = byi * g.by, Z0 = bzi * g.bz;
   for (int i = 0; i < DecState<NDIM, K>::kWords; ++i) st[i * T] = 0;
+  Prefix s;
+  s.r1 = 0;
+  s.r2 = 0;
+#pragma unroll
+  for (int x = 0; x < 8; ++x) { s.Y1[x] = 0; s.Y2[x] = 0; }
 
-  if (NDIM == 3) {
-    // st[(y*8+x)*T]: plane sums of order 1; st[(64+y*8+x)*T]: order 2
-    const bool xfull = X0 + 8 <= g.nx;
+  int32_t cur[8];
+  if (br.group8(slut, p.R, cur)) fix_outliers(p, sd, pos0, pos0, cur, bad);
+  cur[0] += anchor;  // the block origin's residual is its anchor
 #pragma unroll 1
-    for (int z = 0; z < 8; ++z) {
-      int32_t Y1[8], Y2[8];
+  for (int gi = 0; gi < NG - 1; ++gi) {
+    int32_t nxt[8];
+    const bool zero = br.group8(slut, p.R, nxt);
+    consume<NDIM, K, EXC, T>(p, g, sd, s, st, gi, cur, pos0, X0, Y0, Z0, vecbase);
+    if (zero) fix_outliers(p, sd, pos0, pos0 + (uint32_t)(gi + 1) * 8, nxt, bad);
 #pragma unroll
-      for (int i = 0; i < 8; ++i) { Y1[i] = 0; Y2[i] = 0; }
-      const bool zin = Z0 + z < g.nz;
-#pragma unroll 1
-      for (int y = 0; y < 8; ++y) {
-        int32_t r1 = 0, r2 = 0;
-        float o[8];
-        int32_t *row = st + (y * 8) * T;
-#pragma unroll
-        for (int x = 0; x < 8; ++x) {
-          const uint32_t pos = pos0 + (uint32_t)(z * 64 + y * 8 + x);
-          int32_t d = next_delta(br, slut, p, sd, pos0, pos, bad);
-          if (x == 0) d += (y == 0 && z == 0) ? anchor : 0;
-          int32_t q;
-          if (K == 1) {
-            r1 += d; Y1[x] += r1;
-            q = row[x * T] + Y1[x];
-            row[x * T] = q;
-          } else {
-            r1 += d; r2 += r1; Y1[x] += r2; Y2[x] += Y1[x];
-            const int32_t p1 = row[x * T] + Y2[x];
-            row[x * T] = p1;
-            q = row[(64 + x) * T] + p1;
-            row[(64 + x) * T] = q;
-          }
-          o[x] = value<EXC>(p, sd, pos, q);
-        }
-        if (zin && Y0 + y < g.ny) {
-          const uint64_t f = ((uint64_t)(Z0 + z) * g.ny + (Y0 + y)) * g.nx + X0;
-          if (xfull) {
-            store4(p.out, f, vecbase, o);
-            store4(p.out, f + 4, vecbase, o + 4);
-          } else {
-#pragma unroll
-            for (int x = 0; x < 8; ++x)
-              if (X0 + x < g.nx) p.out[f + x] = o[x];
-          }
-        }
-      }
-    }
-  } else if (NDIM == 2) {
-    // st[x*T]: column sums of order 1; st[(32+x)*T]: order 2
-    const bool xfull = X0 + 32 <= g.nx;
-#pragma unroll 1
-    for (int y = 0; y < 32; ++y) {
-      int32_t r1 = 0, r2 = 0;
-      const bool yin = Y0 + y < g.ny;
-      const uint64_t f = ((uint64_t)(Y0 + y)) * g.nx + X0;
-#pragma unroll 1
-      for (int x8 = 0; x8 < 4; ++x8) {
-        float o[8];
-        int32_t *col = st + (x8 * 8) * T;
-#pragma unroll
-        for (int u = 0; u < 8; ++u) {
-          const uint32_t pos = pos0 + (uint32_t)(y * 32 + x8 * 8 + u);
-          int32_t d = next_delta(br, slut, p, sd, pos0, pos, bad);
-          if (u == 0) d += (x8 == 0 && y == 0) ? anchor : 0;
-          int32_t q;
-          if (K == 1) {
-            r1 += d;
-            q = col[u * T] + r1;
-            col[u * T] = q;
-          } else {
-            r1 += d; r2 += r1;
-            const int32_t y1 = col[u * T] + r2;
-            col[u * T] = y1;
-            q = col[(32 + u) * T] + y1;
-            col[(32 + u) * T] = q;
-          }
-          o[u] = value<EXC>(p, sd, pos, q);
-        }
-        if (yin) {
-          const uint64_t fx = f + 8 * x8;
-          if (xfull) {
-            store4(p.out, fx, vecbase, o);
-            store4(p.out, fx + 4, vecbase, o + 4);
-          } else {
-#pragma unroll
-            for (int u = 0; u < 8; ++u)
-              if (X0 + 8 * x8 + u < g.nx) p.out[fx + u] = o[u];
-          }
-        }
-      }
-    }
-  } else {
-    // the anchor enters the first running sum once, as the origin residual
-    int32_t r1 = anchor, r2 = 0;
-    const uint64_t f0 = (uint64_t)X0;
-    const bool full = X0 + 1024 <= g.nx;
-#pragma unroll 1
-    for (int x8 = 0; x8 < 128; ++x8) {
-      float o[8];
-#pragma unroll
-      for (int u = 0; u < 8; ++u) {
-        const uint32_t pos = pos0 + (uint32_t)(8 * x8 + u);
-        int32_t d = next_delta(br, slut, p, sd, pos0, pos, bad);
-        int32_t q;
-        if (K == 1) { r1 += d; q = r1; }
-        else { r1 += d; r2 += r1; q = r2; }
-        o[u] = value<EXC>(p, sd, pos, q);
-      }
-      if (full) {
-        store4(p.out, f0 + 8 * x8, vecbase, o);
-        store4(p.out, f0 + 8 * x8 + 4, vecbase, o + 4);
-      } else {
-#pragma unroll
-        for (int u = 0; u < 8; ++u)
-          if (X0 + 8 * x8 + u < g.nx) p.out[f0 + 8 * x8 + u] = o[u];
-      }
-    }
+    for (int u = 0; u < 8; ++u) cur[u] = nxt[u];
   }
+  consume<NDIM, K, EXC, T>(p, g, sd, s, st, NG - 1, cur, pos0, X0, Y0, Z0, vecbase);
   asm volatile("cp.async.wait_all;\n" ::: "memory");  // the ring is reused by the next chunk
-  if (br.consumed(start_off) != cbits || bad || !(br.vall & kLutValid))
-    dec_err(p.err, FZ_ECORRUPT);
+  if (br.consumed(start_off) != cbits || bad) dec_err(p.err, FZ_ECORRUPT);
 }
 
-// Decode groups grp, grp + step, ... below g_end of one field whose table
-// is in slut; all threads of the CTA call it together.
+// Work units of one field whose table is in slut, claimed by this warp from
+// the field's counter until none is left.
 template <int NDIM, int K>
-__device__ __forceinline__ void decode_groups(const DecParams &p, const Geom &g, const uint16_t *slut,
-                                              int32_t *sstate, uint32_t *sring, unsigned long long *swarp,
-                                              uint64_t grp, uint64_t g_end, uint64_t step) {
-  const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+__device__ __forceinline__ void decode_units(const DecParams &p, const Geom &g, const uint16_t *slut,
+                                             int32_t *sstate, uint32_t *sring) {
+  constexpr int T = DecCta<NDIM, K>::T;
+  const int t = threadIdx.x;
   const bool vecbase = ((g.nx & 3u) == 0) && (((uintptr_t)p.out & 15u) == 0);
-  for (; grp < g_end; grp += step) {
-    const uint64_t j = grp * kDecThreads + t;
-    const bool valid = j < p.n_chunks;
-    const uint32_t cb = valid ? __ldg(p.chunk_bits + j) : 0u;
-    unsigned long long incl = cb;
-#pragma unroll
-    for (int off = 1; off < 32; off <<= 1) {
-      const unsigned long long v = __shfl_up_sync(0xffffffffu, incl, off);
-      if (lane >= off) incl += v;
-    }
-    __syncthreads();  // the table is in place and swarp is free again
-    if (lane == 31) swarp[warp] = incl;
-    __syncthreads();
-    unsigned long long start = p.goff[grp] + incl - cb;
-    for (int w = 0; w < warp; ++w) start += swarp[w];
-    if (valid) {
-      if (p.n_exc) decode_chunk<NDIM, K, true>(p, g, slut, sstate + t, sring + t, j, start, vecbase);
-      else decode_chunk<NDIM, K, false>(p, g, slut, sstate + t, sring + t, j, start, vecbase);
+  for (;;) {
+    const uint32_t u = claim_unit(p.err + 1);
+    if (u >= p.n_units) break;
+    uint32_t cb;
+    const uint64_t start = unit_start(p.chunk_bits, p.goff, p.n_chunks, u, cb);
+    const uint64_t j = (uint64_t)u * kDecUnit + (t & 31);
+    if (j < p.n_chunks) {
+      if (p.n_exc) decode_chunk<NDIM, K, true, T>(p, g, slut, sstate + t, sring + t, j, start, cb, vecbase);
+      else decode_chunk<NDIM, K, false, T>(p, g, slut, sstate + t, sring + t, j, start, cb, vecbase);
     }
   }
 }
 
+template <int T>
 __device__ __forceinline__ void load_lut(uint16_t *slut, const uint16_t *lut) {
   const uint4 *src = reinterpret_cast<const uint4 *>(lut);
   uint4 *dst = reinterpret_cast<uint4 *>(slut);
-  for (int i = threadIdx.x; i < kLutSize / 8; i += kDecThreads) dst[i] = __ldg(src + i);
+  for (int i = threadIdx.x; i < kLutSize / 8; i += T) dst[i] = __ldg(src + i);
 }
 
+// One CTA per SM; every warp takes work units (32 chunks, one per lane)
+// from a counter, so uneven chunks and small fields still spread over all
+// SMs.
 template <int NDIM, int K>
-__global__ void __launch_bounds__(kDecThreads) k_decode(DecParams p, Geom g) {
+__global__ void __launch_bounds__(DecCta<NDIM, K>::T, 1) k_decode(DecParams p, Geom g) {
+  constexpr int T = DecCta<NDIM, K>::T;
   extern __shared__ __align__(16) unsigned char d_smem[];
   uint16_t *slut = reinterpret_cast<uint16_t *>(d_smem);
   int32_t *sstate = reinterpret_cast<int32_t *>(d_smem + sizeof(uint16_t) * kLutSize);
-  uint32_t *sring = reinterpret_cast<uint32_t *>(sstate + DecState<NDIM, K>::kWords * kDecThreads);
-  __shared__ unsigned long long swarp[kDecThreads / 32];
-  load_lut(slut, p.lut);
-  decode_groups<NDIM, K>(p, g, slut, sstate, sring, swarp, blockIdx.x, p.n_groups, gridDim.x);
+  uint32_t *sring = reinterpret_cast<uint32_t *>(sstate + DecState<NDIM, K>::kWords * T);
+  load_lut<T>(slut, p.lut);
+  __syncthreads();
+  decode_units<NDIM, K>(p, g, slut, sstate, sring);
 }
 
 // ---------------------------------------------------------------- batched decode
@@ -474,75 +481,88 @@ struct DecJob {
   const uint8_t *lens;
   uint32_t nsym, pad;
   uint64_t total_bits;
-  uint64_t group_base;  // first decode group in the job's class queue
+  uint64_t unit_base;   // first work unit in the job's class queue
 };
 
-// Group bit sums of every field: blockIdx.y = field.
+// Work-unit bit sums of every field: blockIdx.y = field.
 __global__ void k_dec_gsum_batch(const DecJob *__restrict__ jobs) {
   const DecJob &J = jobs[blockIdx.y];
-  const uint64_t gidx = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const uint64_t u = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
-  if (gidx >= J.p.n_groups) return;
-  const uint64_t c0 = gidx * kDecThreads + 8 * lane;
-  unsigned long long s = 0;
-  for (uint64_t c = c0; c < J.p.n_chunks && c < c0 + 8; ++c) s += J.p.chunk_bits[c];
-  for (int off = 16; off > 0; off >>= 1) s += __shfl_down_sync(0xffffffffu, s, off);
-  if (lane == 0) const_cast<uint64_t *>(J.p.goff)[gidx] = s;
+  if (u >= J.p.n_units) return;
+  const uint64_t j = u * kDecUnit + lane;
+  uint32_t v = j < J.p.n_chunks ? __ldg(J.p.chunk_bits + j) : 0u;
+  v = __reduce_add_sync(0xffffffffu, v);
+  if (lane == 0) const_cast<uint64_t *>(J.p.goff)[u] = v;
 }
 
-// Decode tables and group offsets: one CTA per field.
+// Decode tables and unit offsets: one CTA per field.
 __global__ void __launch_bounds__(kPrepThreads) k_dec_prep_batch(const DecJob *__restrict__ jobs) {
   const DecJob &J = jobs[blockIdx.x];
-  k_dec_prep_body(J.lens, J.nsym, const_cast<uint64_t *>(J.p.goff), J.p.n_groups, J.total_bits,
+  k_dec_prep_body(J.lens, J.nsym, const_cast<uint64_t *>(J.p.goff), J.p.n_units, J.total_bits,
                   const_cast<uint16_t *>(J.p.lut), J.p.err);
 }
 
-// The decode groups of every field of one class (dimensionality, Lorenzo
+// The work units of every field of one class (dimensionality, Lorenzo
 // order) form one queue cut into equal contiguous ranges, one per CTA; the
-// decode table is reloaded when the CTA moves to another field.
+// CTA's warps share the units of each field in its range, and the decode
+// table is reloaded when the CTA moves to another field.
 template <int NDIM, int K>
-__global__ void __launch_bounds__(kDecThreads) k_decode_batch(const DecJob *__restrict__ jobs,
-                                                               const uint32_t *__restrict__ members,
-                                                               uint32_t n_members, uint64_t total_groups) {
+__global__ void __launch_bounds__(DecCta<NDIM, K>::T, 1) k_decode_batch(const DecJob *__restrict__ jobs,
+                                                                         const uint32_t *__restrict__ members,
+                                                                         uint32_t n_members, uint64_t total_units) {
+  constexpr int T = DecCta<NDIM, K>::T;
+  constexpr int kWarps = T / 32;
   extern __shared__ __align__(16) unsigned char d_smem[];
   uint16_t *slut = reinterpret_cast<uint16_t *>(d_smem);
   int32_t *sstate = reinterpret_cast<int32_t *>(d_smem + sizeof(uint16_t) * kLutSize);
-  uint32_t *sring = reinterpret_cast<uint32_t *>(sstate + DecState<NDIM, K>::kWords * kDecThreads);
-  __shared__ unsigned long long swarp[kDecThreads / 32];
+  uint32_t *sring = reinterpret_cast<uint32_t *>(sstate + DecState<NDIM, K>::kWords * T);
   __shared__ DecParams sp;
   __shared__ Geom sg;
-  const uint64_t lo = total_groups * blockIdx.x / gridDim.x, hi = total_groups * (blockIdx.x + 1) / gridDim.x;
+  const int t = threadIdx.x, warp = t >> 5;
+  const uint64_t lo = total_units * blockIdx.x / gridDim.x, hi = total_units * (blockIdx.x + 1) / gridDim.x;
   uint32_t a = 0, b = n_members;
   while (a < b) {
     const uint32_t m = (a + b) >> 1;
     const DecJob &J = jobs[members[m]];
-    if (J.group_base + J.p.n_groups <= lo) a = m + 1; else b = m;
+    if (J.unit_base + J.p.n_units <= lo) a = m + 1; else b = m;
   }
-  for (uint64_t t = lo; t < hi && a < n_members; ++a) {
+  for (uint64_t r = lo; r < hi && a < n_members; ++a) {
     const DecJob &J = jobs[members[a]];
-    const uint64_t jb = J.group_base, je = jb + J.p.n_groups;
-    const uint64_t t0 = t > jb ? t : jb, t1 = hi < je ? hi : je;
+    const uint64_t jb = J.unit_base, je = jb + J.p.n_units;
+    const uint64_t t0 = r > jb ? r : jb, t1 = hi < je ? hi : je;
     __syncthreads();  // the previous field is done with the table and the staged parameters
-    if (threadIdx.x == 0) { sp = J.p; sg = J.g; }
-    load_lut(slut, J.p.lut);
+    if (t == 0) { sp = J.p; sg = J.g; }
+    load_lut<T>(slut, J.p.lut);
     __syncthreads();
-    if (t0 < t1) decode_groups<NDIM, K>(sp, sg, slut, sstate, sring, swarp, t0 - jb, t1 - jb, 1);
-    t = t1;
+    const bool vecbase = ((sg.nx & 3u) == 0) && (((uintptr_t)sp.out & 15u) == 0);
+    for (uint64_t u = t0 - jb + warp; u < t1 - jb; u += kWarps) {
+      uint32_t cb;
+      const uint64_t start = unit_start(sp.chunk_bits, sp.goff, sp.n_chunks, u, cb);
+      const uint64_t j = u * kDecUnit + (t & 31);
+      if (j < sp.n_chunks) {
+        if (sp.n_exc) decode_chunk<NDIM, K, true, T>(sp, sg, slut, sstate + t, sring + t, j, start, cb, vecbase);
+        else decode_chunk<NDIM, K, false, T>(sp, sg, slut, sstate + t, sring + t, j, start, cb, vecbase);
+      }
+    }
+    r = t1;
   }
 }
 
 template <int NDIM, int K>
 cudaError_t launch_dec_t(const DecParams &p, const Geom &g, int sm_count, cudaStream_t s) {
+  constexpr int T = DecCta<NDIM, K>::T;
   const int smem = (int)dec_smem_bytes<NDIM, K>();
   cudaError_t e = cudaFuncSetAttribute(k_decode<NDIM, K>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;
   int per_sm = 0;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_decode<NDIM, K>, kDecThreads, smem);
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_decode<NDIM, K>, T, smem);
   if (e != cudaSuccess) return e;
   if (per_sm < 1) per_sm = 1;
+  // at most one CTA per unit: the units of a small field spread over SMs
   uint64_t grid = (uint64_t)sm_count * per_sm;
-  if (grid > p.n_groups) grid = p.n_groups;
-  k_decode<NDIM, K><<<(unsigned)grid, kDecThreads, smem, s>>>(p, g);
+  if (grid > p.n_units) grid = p.n_units;
+  k_decode<NDIM, K><<<(unsigned)grid, T, smem, s>>>(p, g);
   return cudaGetLastError();
 }
 
@@ -550,13 +570,10 @@ cudaError_t launch_dec_t(const DecParams &p, const Geom &g, int sm_count, cudaSt
 
 cudaError_t launch_decode_prep(const uint8_t *d_in, const fz_header &h, const DecodeWs &ws, cudaStream_t s) {
   const uint64_t n_chunks = h.n_chunks;
-  const uint64_t n_groups = (n_chunks + kDecThreads - 1) / kDecThreads;
+  const uint64_t n_units = dec_units_of(n_chunks);
   const uint32_t *cbits = reinterpret_cast<const uint32_t *>(d_in + h.off_chunk_bits);
-  {
-    const uint64_t threads = n_groups * 32;
-    k_dec_gsum<<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(cbits, n_chunks, n_groups, ws.gsum);
-  }
-  k_dec_prep<<<1, kPrepThreads, 0, s>>>(d_in + h.off_lens, 2 * h.radius, ws.gsum, n_groups, h.total_bits, ws.lut,
+  k_dec_gsum<<<(unsigned)((n_units * 32 + 255) / 256), 256, 0, s>>>(cbits, n_chunks, n_units, ws.gsum);
+  k_dec_prep<<<1, kPrepThreads, 0, s>>>(d_in + h.off_lens, 2 * h.radius, ws.gsum, n_units, h.total_bits, ws.lut,
                                         ws.err);
   return cudaGetLastError();
 }
@@ -577,7 +594,7 @@ cudaError_t launch_decode_main(const uint8_t *d_in, const fz_header &h, float *d
   p.n_out = h.n_out;
   p.n_exc = h.n_exc;
   p.n_chunks = h.n_chunks;
-  p.n_groups = (h.n_chunks + kDecThreads - 1) / kDecThreads;
+  p.n_units = dec_units_of(h.n_chunks);
   p.goff = ws.gsum;
   p.lut = ws.lut;
   p.err = ws.err;
@@ -627,29 +644,30 @@ __global__ void k_plain_batch(const PlainJob *__restrict__ jobs, uint32_t n) {
 
 template <int NDIM, int K>
 cudaError_t launch_dec_batch_t(const DecJob *jobs, const uint32_t *members, uint32_t n_members,
-                               uint64_t total_groups, int per_sm, cudaStream_t s, int sms) {
+                               uint64_t total_units, int per_sm, cudaStream_t s, int sms) {
+  constexpr int T = DecCta<NDIM, K>::T;
   const int smem = (int)dec_smem_bytes<NDIM, K>();
   cudaError_t e = cudaFuncSetAttribute(k_decode_batch<NDIM, K>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;
   int occ = 0;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_decode_batch<NDIM, K>, kDecThreads, smem);
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_decode_batch<NDIM, K>, T, smem);
   if (e != cudaSuccess) return e;
   if (occ < 1) occ = 1;
   if (per_sm < 1 || per_sm > occ) per_sm = occ;
   uint64_t grid = (uint64_t)sms * per_sm;
-  if (grid > total_groups) grid = total_groups;
+  if (grid > total_units) grid = total_units;
   if (grid < 1) grid = 1;
-  k_decode_batch<NDIM, K><<<(unsigned)grid, kDecThreads, smem, s>>>(jobs, members, n_members, total_groups);
+  k_decode_batch<NDIM, K><<<(unsigned)grid, T, smem, s>>>(jobs, members, n_members, total_units);
   return cudaGetLastError();
 }
 }  // namespace
 
 size_t dec_job_bytes() { return sizeof(DecJob); }
 size_t plain_job_bytes() { return sizeof(PlainJob); }
-uint64_t dec_groups(const fz_header &h) { return (h.n_chunks + kDecThreads - 1) / kDecThreads; }
+uint64_t dec_units(const fz_header &h) { return dec_units_of(h.n_chunks); }
 
 void fill_dec_job(void *dst, const uint8_t *d_in, const fz_header &h, float *d_out, uint16_t *lut, uint64_t *gsum,
-                  uint32_t *err, uint64_t group_base) {
+                  uint32_t *err, uint64_t unit_base) {
   DecJob J;
   memset(&J, 0, sizeof(J));
   make_geom(h.ndim, h.dims, J.g);
@@ -665,7 +683,7 @@ void fill_dec_job(void *dst, const uint8_t *d_in, const fz_header &h, float *d_o
   p.n_out = h.n_out;
   p.n_exc = h.n_exc;
   p.n_chunks = h.n_chunks;
-  p.n_groups = dec_groups(h);
+  p.n_units = dec_units(h);
   p.goff = gsum;
   p.lut = lut;
   p.err = err;
@@ -675,7 +693,7 @@ void fill_dec_job(void *dst, const uint8_t *d_in, const fz_header &h, float *d_o
   J.lens = d_in + h.off_lens;
   J.nsym = 2 * h.radius;
   J.total_bits = h.total_bits;
-  J.group_base = group_base;
+  J.unit_base = unit_base;
   memcpy(dst, &J, sizeof(J));
 }
 
@@ -689,28 +707,28 @@ void fill_plain_job(void *dst, const uint8_t *d_in, uint64_t n, bool is_const, f
   memcpy(dst, &J, sizeof(J));
 }
 
-cudaError_t launch_decode_batch_prep(const void *jobs, uint32_t n, uint64_t max_groups, cudaStream_t s) {
+cudaError_t launch_decode_batch_prep(const void *jobs, uint32_t n, uint64_t max_units, cudaStream_t s) {
   const DecJob *J = reinterpret_cast<const DecJob *>(jobs);
-  const uint64_t gx = (max_groups * 32 + 255) / 256;
+  const uint64_t gx = (max_units * 32 + 255) / 256;
   k_dec_gsum_batch<<<dim3((unsigned)gx, n), 256, 0, s>>>(J);
   k_dec_prep_batch<<<n, kPrepThreads, 0, s>>>(J);
   return cudaGetLastError();
 }
 
 cudaError_t launch_decode_batch_main(int ndim, int k, const void *jobs, const uint32_t *members, uint32_t n_members,
-                                     uint64_t total_groups, int per_sm, cudaStream_t s, int sms) {
+                                     uint64_t total_units, int per_sm, cudaStream_t s, int sms) {
   const DecJob *J = reinterpret_cast<const DecJob *>(jobs);
   const bool k2 = k == 2;
   switch (ndim) {
     case 1:
-      return k2 ? launch_dec_batch_t<1, 2>(J, members, n_members, total_groups, per_sm, s, sms)
-                : launch_dec_batch_t<1, 1>(J, members, n_members, total_groups, per_sm, s, sms);
+      return k2 ? launch_dec_batch_t<1, 2>(J, members, n_members, total_units, per_sm, s, sms)
+                : launch_dec_batch_t<1, 1>(J, members, n_members, total_units, per_sm, s, sms);
     case 2:
-      return k2 ? launch_dec_batch_t<2, 2>(J, members, n_members, total_groups, per_sm, s, sms)
-                : launch_dec_batch_t<2, 1>(J, members, n_members, total_groups, per_sm, s, sms);
+      return k2 ? launch_dec_batch_t<2, 2>(J, members, n_members, total_units, per_sm, s, sms)
+                : launch_dec_batch_t<2, 1>(J, members, n_members, total_units, per_sm, s, sms);
     default:
-      return k2 ? launch_dec_batch_t<3, 2>(J, members, n_members, total_groups, per_sm, s, sms)
-                : launch_dec_batch_t<3, 1>(J, members, n_members, total_groups, per_sm, s, sms);
+      return k2 ? launch_dec_batch_t<3, 2>(J, members, n_members, total_units, per_sm, s, sms)
+                : launch_dec_batch_t<3, 1>(J, members, n_members, total_units, per_sm, s, sms);
   }
 }
 

@@ -7,8 +7,10 @@
 namespace fz {
 
 constexpr int kLutSize = 1 << kLutBits;
-// decode-table entry: bit 15 valid, bits 10..13 length-1, bits 0..9 symbol
-constexpr uint16_t kLutValid = 0x8000u;
+// decode-table entry: bits 10..13 codeword length (1..14), bits 0..9 symbol;
+// 0 marks a window that starts no codeword (only in a corrupt stream: the
+// reader then stops advancing and the chunk's bit count check fails)
+constexpr uint32_t kLutLenShift = 10;
 
 __device__ __forceinline__ void prefetch_l2(const void *p) {
   asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
@@ -20,26 +22,27 @@ __device__ __forceinline__ void cp_async4(uint32_t *dst_smem, const uint32_t *sr
   asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(d), "l"(src), "r"(n) : "memory");
   asm volatile("cp.async.commit_group;\n" ::: "memory");
 }
-__device__ __forceinline__ void cp_async_wait3() { asm volatile("cp.async.wait_group 3;\n" ::: "memory"); }
 
-constexpr int kRing = 4;  // stream words in flight per thread
+constexpr int kRing = 4;  // stream words in flight per thread (a power of two)
 
-// MSB-first bit reader over one chunk, all 32-bit: a window of two stream
-// words (a, b) and a bit offset into a; the next 32 bits are one funnel shift
-// away.  When the offset passes 32 the window slides by a word.  The words
-// ahead of the window wait in a per-thread ring in shared memory, filled by
-// asynchronous copies issued four slides early, so a slide never waits on
-// memory and no register is ever read while its load is in flight.  Words
-// past the end of the bitstream read as zero.
+// MSB-first bit reader over one chunk, all 32-bit: a window of three stream
+// words (a, b, c) and a bit offset (< 32) into a.  Codewords are decoded in
+// pairs: both fit in the window (2 x 14 bits from an offset below 32), and
+// afterwards the window slides by at most one word.  The slide is
+// predicated, not branched, so a warp whose lanes slide at different times
+// never diverges: the next word comes from a per-thread ring in shared
+// memory that asynchronous copies fill kRing slides ahead, so a slide never
+// waits on memory and no register is read while its load is in flight.
+// Words past the end of the bitstream read as zero.
+template <int T>  // threads of the CTA: the stride of the per-thread ring columns
 struct BitReader {
   const uint32_t *W;   // the chunk's first word
   uint32_t nw;         // words from W to the end of the bitstream
   uint32_t wi;         // next word to fetch into the ring, relative to W
-  uint32_t *ring;      // this thread's ring: ring[k * kDecThreads]
+  uint32_t ring_s;     // shared-memory address of this thread's ring column
   uint32_t rd;         // next ring slot to read
-  uint32_t a, b;
+  uint32_t a, b, c;
   uint32_t off;        // bits of a already consumed (0..31)
-  uint32_t vall;       // AND of all table entries used (valid bit check)
   __device__ __forceinline__ uint32_t ld(uint32_t i) const { return i < nw ? __ldg(W + i) : 0u; }
   __device__ __forceinline__ void init(const uint32_t *words, uint64_t n_words, uint64_t bitpos, uint32_t bits,
                                        uint32_t *ring_col) {
@@ -47,39 +50,92 @@ struct BitReader {
     W = words + sw;
     nw = (uint32_t)(n_words > sw ? (n_words - sw < 0xffffffffull ? n_words - sw : 0xffffffffull) : 0);
     off = (uint32_t)(bitpos & 31u);
-    ring = ring_col;
+    ring_s = (uint32_t)__cvta_generic_to_shared(ring_col);
     a = ld(0);
     b = ld(1);
+    c = ld(2);
 #pragma unroll
-    for (int k = 0; k < kRing; ++k) cp_async4(ring + k * kDecThreads, W + (2 + k < nw ? 2 + k : 0), 2 + k < nw);
-    wi = 2 + kRing;
+    for (int k = 0; k < kRing; ++k) cp_async4(ring_col + k * T, W + (3 + k < nw ? 3 + k : 0), 3 + k < nw);
+    wi = 3 + kRing;
     rd = 0;
-    vall = 0xffffffffu;
     // the whole chunk (a few 128-byte lines) is pulled into L2 up front
     const uint32_t cw = (off + bits + 31) / 32 + 2;
     for (uint32_t i = 32; i < cw && i < nw; i += 32) prefetch_l2(W + i);
   }
-  __device__ __forceinline__ uint32_t next(const uint16_t *slut) {
-    const uint32_t win = __funnelshift_l(b, a, off);
-    const uint32_t e = slut[win >> (32 - kLutBits)];
-    vall &= e;
-    off += ((e >> 10) & 15u) + 1u;
-    if (off >= 32) {
-      off -= 32;
-      cp_async_wait3();
-      a = b;
-      b = ring[rd * kDecThreads];
-      cp_async4(ring + rd * kDecThreads, W + (wi < nw ? wi : 0), wi < nw);
-      rd = (rd + 1) & (kRing - 1);
-      ++wi;
+  // Two symbols.
+  __device__ __forceinline__ void next2(const uint16_t *slut, uint32_t &s0, uint32_t &s1) {
+    const uint32_t e0 = slut[__funnelshift_l(b, a, off) >> (32 - kLutBits)];
+    const uint32_t o1 = off + ((e0 >> kLutLenShift) & 15u);  // < 46
+    const uint32_t w1 = o1 < 32 ? __funnelshift_l(b, a, o1) : __funnelshift_l(c, b, o1);
+    const uint32_t e1 = slut[w1 >> (32 - kLutBits)];
+    const uint32_t o2 = o1 + ((e1 >> kLutLenShift) & 15u);   // < 60
+    s0 = e0 & 1023u;
+    s1 = e1 & 1023u;
+    const uint32_t adv = o2 >> 5;  // 0 or 1
+    off = o2 & 31u;
+    a = adv ? b : a;
+    b = adv ? c : b;
+    // predicated slide: wait for the oldest copy, read its word into c,
+    // refill the slot with the word kRing slides ahead
+    const uint32_t slot = ring_s + rd * (uint32_t)(T * 4);
+    const bool more = wi < nw;
+    const uint32_t *src = W + (more ? wi : 0u);
+    asm volatile(
+        "{\n"
+        " .reg .pred p;\n"
+        " setp.ne.u32 p, %1, 0;\n"
+        " @p cp.async.wait_group %5;\n"
+        " @p ld.shared.u32 %0, [%2];\n"
+        " @p cp.async.ca.shared.global [%2], [%3], 4, %4;\n"
+        " @p cp.async.commit_group;\n"
+        "}\n"
+        : "+r"(c)
+        : "r"(adv), "r"(slot), "l"(src), "r"(more ? 4 : 0), "n"(kRing - 1));
+    rd = (rd + adv) & (kRing - 1);
+    wi += adv;
+  }
+  // Eight symbols as residuals sym - R; returns whether any symbol was 0
+  // (an outlier, whose residual is then -R until it is looked up).
+  __device__ __forceinline__ bool group8(const uint16_t *slut, int32_t R, int32_t (&d)[8]) {
+    bool zero = false;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      uint32_t s0, s1;
+      next2(slut, s0, s1);
+      zero = zero || s0 == 0 || s1 == 0;
+      d[2 * k] = (int32_t)s0 - R;
+      d[2 * k + 1] = (int32_t)s1 - R;
     }
-    return e & 1023u;
+    return zero;
   }
   // bits consumed since init, given the starting offset
   __device__ __forceinline__ uint32_t consumed(uint32_t start_off) const {
-    return (wi - 2 - kRing) * 32 + off - start_off;
+    return (wi - 3 - kRing) * 32 + off - start_off;
   }
 };
+
+// Start bit of each lane's chunk in work unit u (lane = chunk within the
+// unit); also returns the chunk's bit count.  All lanes call it.
+__device__ __forceinline__ uint64_t unit_start(const uint32_t *chunk_bits, const uint64_t *uoff, uint64_t n_chunks,
+                                               uint64_t u, uint32_t &cb) {
+  const int lane = threadIdx.x & 31;
+  const uint64_t j = u * kDecUnit + lane;
+  cb = j < n_chunks ? __ldg(chunk_bits + j) : 0u;
+  uint32_t incl = cb;  // a unit holds at most 32 x 1024 x 14 bits
+#pragma unroll
+  for (int off = 1; off < 32; off <<= 1) {
+    const uint32_t v = __shfl_up_sync(0xffffffffu, incl, off);
+    if (lane >= off) incl += v;
+  }
+  return uoff[u] + (incl - cb);
+}
+
+// Next work unit for this warp from a counter shared by all CTAs.
+__device__ __forceinline__ uint32_t claim_unit(uint32_t *counter) {
+  uint32_t u = 0;
+  if ((threadIdx.x & 31) == 0) u = atomicAdd(counter, 1u);
+  return __shfl_sync(0xffffffffu, u, 0);
+}
 
 __device__ __forceinline__ uint64_t lower_bound_u32(const uint32_t *a, uint64_t n, uint32_t key) {
   uint64_t lo = 0, hi = n;

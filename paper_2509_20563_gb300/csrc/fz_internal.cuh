@@ -16,7 +16,7 @@ constexpr int kLutBits = 14;       // decode table width: every codeword resolve
 constexpr int kTileElems = 4096;   // elements per quantization tile
 constexpr int kQuantThreads = 256; // 8 warps per quantization tile
 constexpr int kEncWarps = 8;       // chunks per encode tile (one warp per chunk)
-constexpr int kDecThreads = 256;   // chunks per decode CTA (one thread per chunk)
+constexpr int kDecUnit = 32;       // chunks per decode work unit (one warp, one chunk per lane)
 constexpr int kTileGroup = 1024;   // quantization tiles per outlier-offset group
 
 enum Mode : uint32_t { kModeNormal = 0, kModeConst = 1, kModeRaw = 2 };
@@ -313,10 +313,12 @@ cudaError_t launch_codebook_only(const uint64_t *hist, uint32_t nsym, uint8_t *l
                                  Ctl *ctl, cudaStream_t s);
 
 struct DecodeWs {
-  uint16_t *lut;           // 1 << kLutBits entries: valid bit, length-1, symbol
-  uint64_t *gsum;          // per decode group: sum of chunk bits, then exclusive offset
-  uint32_t *err;           // device error word
+  uint16_t *lut;           // 1 << kLutBits entries: codeword length, symbol
+  uint64_t *gsum;          // per work unit of kDecUnit chunks: sum of chunk bits, then exclusive offset
+  uint32_t *err;           // device error word; err[1] is the work-unit counter (both zeroed per call)
 };
+
+inline __host__ __device__ uint64_t dec_units_of(uint64_t n_chunks) { return (n_chunks + kDecUnit - 1) / kDecUnit; }
 cudaError_t launch_decode_prep(const uint8_t *d_in, const fz_header &h, const DecodeWs &ws, cudaStream_t s);
 cudaError_t launch_decode_main(const uint8_t *d_in, const fz_header &h, float *d_out, const DecodeWs &ws,
                                cudaStream_t s, int sm_count);
@@ -348,13 +350,13 @@ cudaError_t launch_assemble_batch(const BatchJob *jobs, uint32_t n, uint8_t *d_o
 // batched decompress (the job tables are opaque to the API layer)
 size_t dec_job_bytes();
 size_t plain_job_bytes();
-uint64_t dec_groups(const fz_header &h);
+uint64_t dec_units(const fz_header &h);
 void fill_dec_job(void *dst, const uint8_t *d_in, const fz_header &h, float *d_out, uint16_t *lut, uint64_t *gsum,
-                  uint32_t *err, uint64_t group_base);
+                  uint32_t *err, uint64_t unit_base);
 void fill_plain_job(void *dst, const uint8_t *d_in, uint64_t n, bool is_const, float *d_out);
-cudaError_t launch_decode_batch_prep(const void *jobs, uint32_t n, uint64_t max_groups, cudaStream_t s);
+cudaError_t launch_decode_batch_prep(const void *jobs, uint32_t n, uint64_t max_units, cudaStream_t s);
 cudaError_t launch_decode_batch_main(int ndim, int k, const void *jobs, const uint32_t *members, uint32_t n_members,
-                                     uint64_t total_groups, int per_sm, cudaStream_t s, int sms);
+                                     uint64_t total_units, int per_sm, cudaStream_t s, int sms);
 cudaError_t launch_plain_batch(const void *jobs, uint32_t n, uint64_t max_n, cudaStream_t s, int sms);
 cudaError_t launch_batch_results(const BatchJob *jobs, uint32_t n, const BatchCtl *bctl, Result *res,
                                  uint64_t *offsets, cudaStream_t s);

@@ -533,44 +533,39 @@ struct SelDecParams {
   const uint32_t *words;
   uint64_t n_words;
   const uint32_t *chunk_bits;
-  const uint64_t *goff;
-  uint64_t n_chunks, n_groups;
+  const uint64_t *goff;     // per work unit: first bit
+  uint64_t n_chunks, n_units;
   const uint16_t *lut;
   uint16_t *codes;
-  uint32_t *err;
+  uint32_t *err;            // err[0] error word, err[1] work-unit counter
 };
 
 __device__ __forceinline__ void sel_err(uint32_t *err, uint32_t code) { atomicCAS(err, 0u, code); }
 
-// Phase 1: one thread per chunk (= block), codes written row by row.
-__global__ void __launch_bounds__(kDecThreads) k_dec_codes(SelDecParams p) {
+constexpr int kSelDecThreads = 768;
+
+// Phase 1: one thread per chunk (= block), codes written row by row; warps
+// take work units of 32 chunks from a counter.
+__global__ void __launch_bounds__(kSelDecThreads, 1) k_dec_codes(SelDecParams p) {
+  constexpr int T = kSelDecThreads;
   extern __shared__ __align__(16) unsigned char dc_smem[];
   uint16_t *slut = reinterpret_cast<uint16_t *>(dc_smem);
   uint32_t *sring = reinterpret_cast<uint32_t *>(dc_smem + sizeof(uint16_t) * kLutSize);
-  __shared__ unsigned long long swarp[kDecThreads / 32];
-  const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+  const int t = threadIdx.x;
   {
     const uint4 *src = reinterpret_cast<const uint4 *>(p.lut);
     uint4 *dst = reinterpret_cast<uint4 *>(slut);
-    for (int i = t; i < kLutSize / 8; i += kDecThreads) dst[i] = __ldg(src + i);
+    for (int i = t; i < kLutSize / 8; i += T) dst[i] = __ldg(src + i);
   }
-  for (uint64_t grp = blockIdx.x; grp < p.n_groups; grp += gridDim.x) {
-    const uint64_t j = grp * kDecThreads + t;
-    const bool valid = j < p.n_chunks;
-    const uint32_t cb = valid ? __ldg(p.chunk_bits + j) : 0u;
-    unsigned long long incl = cb;
-#pragma unroll
-    for (int off = 1; off < 32; off <<= 1) {
-      const unsigned long long v = __shfl_up_sync(0xffffffffu, incl, off);
-      if (lane >= off) incl += v;
-    }
-    __syncthreads();
-    if (lane == 31) swarp[warp] = incl;
-    __syncthreads();
-    unsigned long long start = p.goff[grp] + incl - cb;
-    for (int w = 0; w < warp; ++w) start += swarp[w];
-    if (!valid) continue;
-    BitReader br;
+  __syncthreads();
+  for (;;) {
+    const uint32_t u = claim_unit(p.err + 1);
+    if (u >= p.n_units) break;
+    uint32_t cb;
+    const uint64_t start = unit_start(p.chunk_bits, p.goff, p.n_chunks, u, cb);
+    const uint64_t j = (uint64_t)u * kDecUnit + (t & 31);
+    if (j >= p.n_chunks) continue;
+    BitReader<T> br;
     br.init(p.words, p.n_words, start, cb, sring + t);
     const uint32_t start_off = br.off;
     uint4 *dst = reinterpret_cast<uint4 *>(p.codes + j * 512);
@@ -578,11 +573,11 @@ __global__ void __launch_bounds__(kDecThreads) k_dec_codes(SelDecParams p) {
     for (int r = 0; r < 64; ++r) {
       uint32_t c[8];
 #pragma unroll
-      for (int u = 0; u < 8; ++u) c[u] = br.next(slut);
+      for (int u2 = 0; u2 < 4; ++u2) br.next2(slut, c[2 * u2], c[2 * u2 + 1]);
       dst[r] = make_uint4(c[0] | (c[1] << 16), c[2] | (c[3] << 16), c[4] | (c[5] << 16), c[6] | (c[7] << 16));
     }
     asm volatile("cp.async.wait_all;\n" ::: "memory");
-    if (br.consumed(start_off) != cb || !(br.vall & kLutValid)) sel_err(p.err, FZ_ECORRUPT);
+    if (br.consumed(start_off) != cb) sel_err(p.err, FZ_ECORRUPT);
   }
 }
 
@@ -801,19 +796,16 @@ cudaError_t launch_sel_decode(const uint8_t *d_in, const fz_header &h, float *d_
   p.chunk_bits = reinterpret_cast<const uint32_t *>(d_in + h.off_chunk_bits);
   p.goff = ws.gsum;
   p.n_chunks = h.n_chunks;
-  p.n_groups = (h.n_chunks + kDecThreads - 1) / kDecThreads;
+  p.n_units = dec_units_of(h.n_chunks);
   p.lut = ws.lut;
   p.codes = codes;
   p.err = ws.err;
-  const int smem = (int)(sizeof(uint16_t) * kLutSize + sizeof(uint32_t) * kRing * kDecThreads);
+  const int smem = (int)(sizeof(uint16_t) * kLutSize + sizeof(uint32_t) * kRing * kSelDecThreads);
   cudaError_t e = cudaFuncSetAttribute(k_dec_codes, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;
-  int per_sm = 0;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_dec_codes, kDecThreads, smem);
-  if (e != cudaSuccess) return e;
-  uint64_t grid = (uint64_t)sm_count * (per_sm > 0 ? per_sm : 1);
-  if (grid > p.n_groups) grid = p.n_groups;
-  k_dec_codes<<<(unsigned)grid, kDecThreads, smem, s>>>(p);
+  uint64_t grid = (uint64_t)sm_count;
+  if (grid > p.n_units) grid = p.n_units;
+  k_dec_codes<<<(unsigned)grid, kSelDecThreads, smem, s>>>(p);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   ReconParams rp;
   rp.codes = codes;
