@@ -282,6 +282,27 @@ fz_status fz_compress_batch(fz_ctx *ctx, uint32_t n, const float *const *d_in, c
 fz_status fz_decompress_batch(fz_ctx *ctx, uint32_t n, const void *d_in, const uint64_t *h_offsets,
                               float *const *d_out, const uint64_t *out_cap_values, void *stream);
 
+/* ---- decompression that allocates nothing ----
+ * The paper has no counterpart; this is a library convenience.  For callers
+ * that must not allocate: code running while another component owns the
+ * device's memory budget, or latency-critical paths where the implicit
+ * synchronization of cudaMalloc/cudaFree is not acceptable.  Same result as
+ * fz_decompress, bit for bit, but without a context: the scratch (error
+ * word, work-unit counter, decode table, per-unit bit offsets) is one fixed
+ * array in the library's device image, shared by every call on a device,
+ * and the call makes no cudaMalloc, cudaFree, cudaMallocHost or other
+ * allocating call.  Limits: Lorenzo streams of at most FZ_NOALLOC_MAX_CHUNKS
+ * chunks (FZ_EBUFFER beyond; 3D blocks of 8^3 = 33.5M values, 1D/2D blocks
+ * of 1024 = 67M values), plus RAW and CONST streams of any size;
+ * per-block-selection streams give FZ_EUNSUPPORTED.  Runs on the calling
+ * thread's current device.  Calls whose device work overlaps (different
+ * streams or host threads) race on the shared array and must be ordered by
+ * the caller.  The first call on a device looks up the array's address.
+ * Synchronizes `stream`. */
+#define FZ_NOALLOC_MAX_CHUNKS 65536
+fz_status fz_decompress_noalloc(const void *d_in, uint64_t in_bytes, const void *h_header, float *d_out,
+                                uint64_t out_cap_values, void *stream);
+
 /* Batched-call options: autotune (default 1) times candidate launch shapes
  * on the first call with a new batch shape; graphs (default 1) captures and
  * replays the batch sequence as a CUDA graph (0 runs it eagerly every call).

@@ -76,12 +76,13 @@ def _declare(L):
                                     C.c_uint64, _vp, _vp]
     L.fz_decompress_batch.argtypes = [_vp, C.c_uint32, _vp, _vp, _vp, _vp, _vp]
     L.fz_ctx_set_batch_options.argtypes = [_vp, C.c_int, C.c_int]
+    L.fz_decompress_noalloc.argtypes = [_vp, C.c_uint64, _vp, _vp, C.c_uint64, _vp]
     L.fz_ctx_set_profiling.argtypes = [_vp, C.c_int]
     L.fz_ctx_get_profile.argtypes = [_vp, _vp]
     for name in ("fz_ctx_create", "fz_ctx_destroy", "fz_compress", "fz_decompress", "fz_stream_info",
                  "fz_lorenzo_quantize", "fz_huffman_codebook", "fz_block_report", "fz_mlp_grad", "fz_mlp_adam",
                  "fz_ctx_set_profiling", "fz_ctx_get_profile", "fz_compress_batch", "fz_decompress_batch",
-                 "fz_ctx_set_batch_options"):
+                 "fz_ctx_set_batch_options", "fz_decompress_noalloc"):
         getattr(L, name).restype = C.c_int
 
 
@@ -292,6 +293,26 @@ def profile(device: int = 0, ctx: Context | None = None) -> Profile:
 def set_batch_options(autotune: bool = True, graphs: bool = True, device: int = 0, ctx: Context | None = None):
     c = ctx if ctx is not None else _ctx(device)
     _check(lib().fz_ctx_set_batch_options(c.handle, int(autotune), int(graphs)), "fz_ctx_set_batch_options")
+
+
+def decompress_noalloc(buf: torch.Tensor, out: torch.Tensor | None = None, header: bytes | None = None,
+                       stream=None) -> torch.Tensor:
+    """Like :func:`decompress`, through the entry point that allocates
+    nothing on the device (fixed scratch; see ``fz_decompress_noalloc``).
+    ``out`` is allocated here (by torch) when not given; pass it to keep the
+    call itself free of allocations."""
+    if not (buf.is_cuda and buf.dtype == torch.uint8):
+        raise ValueError("decompress_noalloc expects a uint8 CUDA tensor")
+    header = header if header is not None else getattr(buf, "fz_header", None)
+    if out is None:
+        h = header if header is not None else bytes(buf[:HEADER_BYTES].cpu().numpy())
+        out = torch.empty(stream_info(h)[0], dtype=torch.float32, device=buf.device)
+    hb = C.create_string_buffer(bytes(header[:HEADER_BYTES]), HEADER_BYTES) if header is not None else None
+    with torch.cuda.device(buf.device):
+        st = lib().fz_decompress_noalloc(C.c_void_p(buf.data_ptr()), buf.numel(), hb, C.c_void_p(out.data_ptr()),
+                                         out.numel(), _stream(stream))
+    _check(st, "fz_decompress_noalloc")
+    return out
 
 
 def lorenzo_quantize(x: torch.Tensor, eb: float, mode: str = "rel", predictor="lorenzo1", radius: int = 512,
