@@ -111,6 +111,18 @@ def test_special_values():
     assert got.size == 256 + 4 * w.size
 
 
+@pytest.mark.parametrize("shape", [(40, 37, 70), (100003,), (61, 450)])
+def test_prequant_near_the_integer_limit(shape):
+    """Values whose scaled magnitude |x / 2eb| lies in [2^22, 2^23) next to
+    ordinary ones: the quantizer's two rounding forms must agree with the
+    oracle's rint everywhere."""
+    s = synth.smooth_nd(shape, seed=12).numpy()
+    x = (s * 1000.0).astype(np.float32)
+    x.ravel()[::3] += np.float32(3.0e6)  # scaled by 1 / (2 * 0.25): about 6e6
+    _roundtrip_check(x, 0.25, "abs")
+    _roundtrip_check(x, 0.4, "abs")
+
+
 def test_deterministic():
     x = torch.from_numpy(synth.grf3d(64, device="cpu").numpy()).cuda()
     a = fz.compress(x, 1e-4).cpu().numpy()
