@@ -288,8 +288,8 @@ fz_status fz_decompress_batch(fz_ctx *ctx, uint32_t n, const void *d_in, const u
  * device's memory budget, or latency-critical paths where the implicit
  * synchronization of cudaMalloc/cudaFree is not acceptable.  Same result as
  * fz_decompress, bit for bit, but without a context: the scratch (error
- * word, work-unit counter, decode table, per-unit bit offsets) is one fixed
- * array in the library's device image, shared by every call on a device,
+ * word, work-unit counter, per-unit bit offsets) is one fixed array in the
+ * library's device image, shared by every call on a device,
  * and the call makes no cudaMalloc, cudaFree, cudaMallocHost or other
  * allocating call.  Limits: Lorenzo streams of at most FZ_NOALLOC_MAX_CHUNKS
  * chunks (FZ_EBUFFER beyond; 3D blocks of 8^3 = 33.5M values, 1D/2D blocks

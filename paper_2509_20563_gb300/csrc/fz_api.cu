@@ -399,7 +399,7 @@ fz_status fz_decompress(fz_ctx *ctx, const void *d_in, uint64_t in_bytes, const 
   size_t off = 0;
   auto take = [&](size_t bytes) { size_t o = off; off += up(bytes); return o; };
   const bool selpath = h.predictor > FZ_PRED_LORENZO2;
-  const size_t o_err = take(16), o_lut = take(2u << kLutBits), o_gsum = take(8 * n_units),
+  const size_t o_err = take(16), o_gsum = take(8 * n_units), o_lut = take(2u << kLutBits),
                o_codes = selpath ? take(2 * g.npad) : 0;
   if ((st = ensure_ws(ctx, off))) return st;
   char *base = reinterpret_cast<char *>(ctx->ws);
@@ -408,16 +408,18 @@ fz_status fz_decompress(fz_ctx *ctx, const void *d_in, uint64_t in_bytes, const 
   ws.lut = reinterpret_cast<uint16_t *>(base + o_lut);
   ws.gsum = reinterpret_cast<uint64_t *>(base + o_gsum);
   StageClock clk(ctx, s, true);
-  e = cudaMemsetAsync(ws.err, 0, 16, s);
-  if (e == cudaSuccess) { e = launch_decode_prep(in, h, ws, s); clk.mark("dec_prep", 2); }
-  if (e == cudaSuccess) {
-    if (selpath) {
+  if (selpath) {
+    e = cudaMemsetAsync(ws.err, 0, 16, s);
+    if (e == cudaSuccess) { e = launch_decode_prep(in, h, ws, s); clk.mark("dec_prep", 2); }
+    if (e == cudaSuccess) {
       e = launch_sel_decode(in, h, d_out, ws, reinterpret_cast<uint16_t *>(base + o_codes), s, ctx->sm_count);
       clk.mark("decode", 2);
-    } else {
-      e = launch_decode_main(in, h, d_out, ws, s, ctx->sm_count);
-      clk.mark("decode", 1);
     }
+  } else {
+    // unit offsets, then the decoder (which builds its decode table itself)
+    e = cudaMemsetAsync(ws.err, 0, 16, s);
+    if (e == cudaSuccess) { e = launch_decode_offsets(in, h, ws, s); clk.mark("dec_offsets", 2); }
+    if (e == cudaSuccess) { e = launch_decode_main(in, h, d_out, ws, s, ctx->sm_count); clk.mark("decode", 1); }
   }
   if (e == cudaSuccess) e = cudaMemcpyAsync(ctx->h_pinned, ws.err, 4, cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);

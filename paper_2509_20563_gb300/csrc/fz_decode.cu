@@ -45,13 +45,14 @@ __global__ void k_dec_gsum(const uint32_t *__restrict__ chunk_bits, uint64_t n_c
   if (lane == 0) usum[u] = v;
 }
 
+__device__ __forceinline__ void dec_scan_body(uint64_t *gsum, uint64_t n_units, uint64_t total_bits, uint32_t *err);
+
 __device__ __forceinline__ void k_dec_prep_body(const uint8_t *__restrict__ lens_in, uint32_t nsym, uint64_t *gsum,
                                                 uint64_t n_units, uint64_t total_bits, uint16_t *lut, uint32_t *err) {
   __shared__ uint32_t first[kLmax + 1], cnt[kLmax + 1], basel[kLmax + 1];
   __shared__ uint32_t wcnt[32][kLmax + 1];
   __shared__ uint32_t wk[32];
   __shared__ uint16_t sorted[kMaxSym];
-  __shared__ unsigned long long wsum[32];
   const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
   int L = t < (int)nsym ? lens_in[t] : 0;
   const bool badlen = L > kLmax;
@@ -114,7 +115,14 @@ __device__ __forceinline__ void k_dec_prep_body(const uint8_t *__restrict__ lens
     }
     lut[e] = v;
   }
-  // exclusive scan of the work units' bit sums (in place)
+  dec_scan_body(gsum, n_units, total_bits, err);
+}
+
+// Exclusive scan, in place, of the work units' bit sums by one CTA of
+// kPrepThreads threads; the grand total must equal the header's bit count.
+__device__ __forceinline__ void dec_scan_body(uint64_t *gsum, uint64_t n_units, uint64_t total_bits, uint32_t *err) {
+  __shared__ unsigned long long wsum[32];
+  const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
   const uint64_t per = (n_units + kPrepThreads - 1) / kPrepThreads;
   const uint64_t g0 = (uint64_t)t * per;
   unsigned long long loc = 0;
@@ -144,10 +152,105 @@ __device__ __forceinline__ void k_dec_prep_body(const uint8_t *__restrict__ lens
   }
 }
 
+__global__ void __launch_bounds__(kPrepThreads) k_dec_scan(uint64_t *gsum, uint64_t n_units, uint64_t total_bits,
+                                                            uint32_t *err) {
+  dec_scan_body(gsum, n_units, total_bits, err);
+}
+
 __global__ void __launch_bounds__(kPrepThreads) k_dec_prep(const uint8_t *__restrict__ lens_in, uint32_t nsym,
                                                             uint64_t *gsum, uint64_t n_units,
                                                             uint64_t total_bits, uint16_t *lut, uint32_t *err) {
   k_dec_prep_body(lens_in, nsym, gsum, n_units, total_bits, lut, err);
+}
+
+// Shared memory of the in-kernel decode-table build.
+struct LutBuild {
+  uint32_t wcnt[32][kLmax + 1];  // per group of 32 symbols and length: count, then exclusive prefix
+  uint32_t gk[32];               // per group: Kraft sum in units of 2^-14, or ~0 for a length above 14
+  uint32_t cnt[kLmax + 1], first[kLmax + 1], basel[kLmax + 1], limit[kLmax + 1];
+  uint32_t ok;
+  uint16_t sorted[kMaxSym];
+};
+
+// The canonical decode table of the length table lens[0..nsym) built by the
+// T threads of a CTA into slut: codes of length l occupy the contiguous
+// range [first[l], first[l] + cnt[l]) << (14 - l) of the 14-bit window, the
+// ranges follow each other in length order, and entry e holds the symbol of
+// rank (e >> (14 - l)) - first[l] among the symbols of its length l.
+// Windows past the last range (an incomplete code) stay 0.  Returns false
+// (in every thread) for a length above 14 or a Kraft sum outside (0, 1].
+template <int T>
+__device__ bool build_lut(const uint8_t *__restrict__ lens, uint32_t nsym, uint16_t *slut, LutBuild &b) {
+  constexpr int W = T / 32;
+  const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+  for (int grp = warp; grp < 32; grp += W) {
+    const int sym = grp * 32 + lane;
+    int L = sym < (int)nsym ? lens[sym] : 0;
+    const bool badlen = L > kLmax;
+    if (badlen) L = 0;
+    const uint32_t k = __reduce_add_sync(0xffffffffu, L ? (1u << (kLmax - L)) : 0u);
+    const bool wbad = __any_sync(0xffffffffu, badlen);
+#pragma unroll 1
+    for (int l = 1; l <= kLmax; ++l) {
+      const uint32_t bl = __ballot_sync(0xffffffffu, L == l);
+      if (lane == l) b.wcnt[grp][l] = __popc(bl);
+    }
+    if (lane == 0) b.gk[grp] = wbad ? 0xffffffffu : k;
+  }
+  __syncthreads();
+  if (t >= 1 && t <= kLmax) {  // per-length counts and group prefixes
+    uint32_t acc = 0;
+    for (int grp = 0; grp < 32; ++grp) { const uint32_t v = b.wcnt[grp][t]; b.wcnt[grp][t] = acc; acc += v; }
+    b.cnt[t] = acc;
+  }
+  if (t == 32) {
+    unsigned long long kraft = 0;
+    bool bad = false;
+    for (int grp = 0; grp < 32; ++grp) {
+      if (b.gk[grp] == 0xffffffffu) bad = true;
+      else kraft += b.gk[grp];
+    }
+    b.ok = (!bad && kraft > 0 && kraft <= (1ull << kLmax)) ? 1u : 0u;
+  }
+  __syncthreads();
+  if (!b.ok) return false;
+  if (t == 0) {
+    uint32_t c = 0, base = 0;
+    b.cnt[0] = 0;
+    for (int l = 1; l <= kLmax; ++l) {
+      c = (c + b.cnt[l - 1]) << 1;
+      b.first[l] = c;
+      b.basel[l] = base;
+      base += b.cnt[l];
+      b.limit[l] = (c + b.cnt[l]) << (kLmax - l);
+    }
+  }
+  __syncthreads();
+  for (int grp = warp; grp < 32; grp += W) {
+    const int sym = grp * 32 + lane;
+    const int L = sym < (int)nsym ? lens[sym] : 0;
+    uint32_t rank = 0;
+#pragma unroll 1
+    for (int l = 1; l <= kLmax; ++l) {
+      const uint32_t bl = __ballot_sync(0xffffffffu, L == l);
+      if (L == l) rank = __popc(bl & ((1u << lane) - 1));
+    }
+    if (L) b.sorted[b.basel[L] + b.wcnt[grp][L] + rank] = (uint16_t)sym;
+  }
+  __syncthreads();
+  uint32_t lim[kLmax + 1];
+#pragma unroll
+  for (int l = 1; l <= kLmax; ++l) lim[l] = b.limit[l];
+  for (int e = t; e < kLutSize; e += T) {
+    int l = 1;
+#pragma unroll
+    for (int k = 1; k < kLmax; ++k) l += (uint32_t)e >= lim[k] ? 1 : 0;
+    uint16_t v = 0;
+    if ((uint32_t)e < lim[kLmax])
+      v = (uint16_t)((l << kLutLenShift) | b.sorted[b.basel[l] + ((uint32_t)e >> (kLmax - l)) - b.first[l]]);
+    slut[e] = v;
+  }
+  return true;
 }
 
 struct DecParams {
@@ -161,7 +264,10 @@ struct DecParams {
   const uint32_t *exc_val;
   uint64_t n_out, n_exc, n_chunks, n_units;
   const uint64_t *goff;   // per work unit: first bit
-  const uint16_t *lut;
+  const uint16_t *lut;    // decode table (batched decode)
+  const uint8_t *lens;    // code-length table (single-field decode builds its table from it)
+  uint32_t nsym;
+  uint64_t total_bits;
   uint32_t *err;          // err[0] error word, err[1] work-unit counter
   float *out;
   float ebx2;
@@ -438,12 +544,13 @@ __device__ __forceinline__ void decode_units(const DecParams &p, const Geom &g, 
   constexpr int T = DecCta<NDIM, K>::T;
   const int t = threadIdx.x;
   const bool vecbase = ((g.nx & 3u) == 0) && (((uintptr_t)p.out & 15u) == 0);
+  const int lane = t & 31;
   for (;;) {
     const uint32_t u = claim_unit(p.err + 1);
     if (u >= p.n_units) break;
     uint32_t cb;
     const uint64_t start = unit_start(p.chunk_bits, p.goff, p.n_chunks, u, cb);
-    const uint64_t j = (uint64_t)u * kDecUnit + (t & 31);
+    const uint64_t j = (uint64_t)u * kDecUnit + lane;
     if (j < p.n_chunks) {
       if (p.n_exc) decode_chunk<NDIM, K, true, T>(p, g, slut, sstate + t, sring + t, j, start, cb, vecbase);
       else decode_chunk<NDIM, K, false, T>(p, g, slut, sstate + t, sring + t, j, start, cb, vecbase);
@@ -468,7 +575,12 @@ __global__ void __launch_bounds__(DecCta<NDIM, K>::T, 1) k_decode(DecParams p, G
   uint16_t *slut = reinterpret_cast<uint16_t *>(d_smem);
   int32_t *sstate = reinterpret_cast<int32_t *>(d_smem + sizeof(uint16_t) * kLutSize);
   uint32_t *sring = reinterpret_cast<uint32_t *>(sstate + DecState<NDIM, K>::kWords * T);
-  load_lut<T>(slut, p.lut);
+  __shared__ LutBuild lb;
+  // every CTA builds the decode table from the 1 KB length table itself
+  if (!build_lut<T>(p.lens, p.nsym, slut, lb)) {
+    if (threadIdx.x == 0) dec_err(p.err, FZ_ECORRUPT);
+    return;
+  }
   __syncthreads();
   decode_units<NDIM, K>(p, g, slut, sstate, sring);
 }
@@ -578,6 +690,15 @@ cudaError_t launch_decode_prep(const uint8_t *d_in, const fz_header &h, const De
   return cudaGetLastError();
 }
 
+cudaError_t launch_decode_offsets(const uint8_t *d_in, const fz_header &h, const DecodeWs &ws, cudaStream_t s) {
+  const uint64_t n_chunks = h.n_chunks;
+  const uint64_t n_units = dec_units_of(n_chunks);
+  const uint32_t *cbits = reinterpret_cast<const uint32_t *>(d_in + h.off_chunk_bits);
+  k_dec_gsum<<<(unsigned)((n_units * 32 + 255) / 256), 256, 0, s>>>(cbits, n_chunks, n_units, ws.gsum);
+  k_dec_scan<<<1, kPrepThreads, 0, s>>>(ws.gsum, n_units, h.total_bits, ws.err);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_decode_main(const uint8_t *d_in, const fz_header &h, float *d_out, const DecodeWs &ws,
                                cudaStream_t s, int sm_count) {
   Geom g;
@@ -596,6 +717,9 @@ cudaError_t launch_decode_main(const uint8_t *d_in, const fz_header &h, float *d
   p.n_chunks = h.n_chunks;
   p.n_units = dec_units_of(h.n_chunks);
   p.goff = ws.gsum;
+  p.lens = d_in + h.off_lens;
+  p.nsym = 2 * h.radius;
+  p.total_bits = h.total_bits;
   p.lut = ws.lut;
   p.err = ws.err;
   p.out = d_out;

@@ -137,7 +137,7 @@ __device__ __forceinline__ void encode_tile(const CompressWs &ws, uint8_t *d_out
         if (r) lw[w0 + 1] |= head << (32 - r);
       }
     }
-    const unsigned long long base = lookback_resolve_warp(ws.estatus, tile, tbits, ctl);
+    const unsigned long long base = lookback_resolve_warp(ws.estatus, tile, tbits, &ctl->res.err);
     if (lane == 0) {
       sm.base = base;
       if (tile == n_tiles - 1 && base + tbits != ctl->total_bits) set_err(ctl, FZ_ECORRUPT);

@@ -179,7 +179,7 @@ __device__ uint64_t lookback_resolve(uint64_t *status, uint64_t tile, uint64_t a
 // loads per 32 tiles.  All lanes of the warp must call it; returns the
 // exclusive prefix in every lane.
 __device__ __forceinline__ uint64_t lookback_resolve_warp(uint64_t *status, uint64_t tile, uint64_t agg,
-                                                          Ctl *ctl) {
+                                                          uint32_t *err) {
   const int lane = threadIdx.x & 31;
   if (tile == 0) return 0;
   uint64_t excl = 0;
@@ -206,7 +206,7 @@ __device__ __forceinline__ uint64_t lookback_resolve_warp(uint64_t *status, uint
     if (inc_mask) break;
     hi -= 32;
   }
-  if (timed_out && lane == 0) set_err(ctl, FZ_ETIMEOUT);
+  if (timed_out && lane == 0) atomicCAS(err, 0u, (uint32_t)FZ_ETIMEOUT);
   if (lane == 0) st_status(&status[tile], kLbFlagInc | ((excl + agg) & kLbMask));
   return excl;
 }
@@ -320,6 +320,8 @@ struct DecodeWs {
 
 inline __host__ __device__ uint64_t dec_units_of(uint64_t n_chunks) { return (n_chunks + kDecUnit - 1) / kDecUnit; }
 cudaError_t launch_decode_prep(const uint8_t *d_in, const fz_header &h, const DecodeWs &ws, cudaStream_t s);
+// work-unit bit offsets only (the Lorenzo decoder builds its decode table itself)
+cudaError_t launch_decode_offsets(const uint8_t *d_in, const fz_header &h, const DecodeWs &ws, cudaStream_t s);
 cudaError_t launch_decode_main(const uint8_t *d_in, const fz_header &h, float *d_out, const DecodeWs &ws,
                                cudaStream_t s, int sm_count);
 cudaError_t launch_fill(float *out, uint64_t n, uint32_t bits, cudaStream_t s, int sm_count);

@@ -1,7 +1,7 @@
 // fz_noalloc.cu -- decompression that allocates nothing.
 //
-// fz_decompress keeps its scratch (decode table, per-unit bit offsets, error
-// word) in a context workspace that it grows with cudaMalloc, and reads the
+// fz_decompress keeps its scratch (error word, per-unit bit offsets) in a
+// context workspace that it grows with cudaMalloc, and reads the
 // error word back through pinned host memory.  Some callers cannot allow
 // either: code that runs while another component owns the device's memory
 // budget (a framework's caching allocator holding the whole pool), code in
@@ -12,10 +12,10 @@
 // the call makes no allocation of any kind -- no cudaMalloc, cudaFree,
 // cudaMallocHost or allocating library routine, and no context.
 //
-// The array holds the error word and work-unit counter (cleared at the
-// start of every call), the 16384-entry decode table and one bit offset per
-// work unit of 32 chunks, so it bounds the stream: at most
-// FZ_NOALLOC_MAX_CHUNKS chunks (Huffman blocks).  Larger streams are
+// The array holds the error word and work-unit counter (cleared at the start
+// of every call) and one bit offset per work unit of 32 chunks (the decoder
+// builds its decode table in shared memory), so it bounds the stream: at
+// most FZ_NOALLOC_MAX_CHUNKS chunks (Huffman blocks).  Larger streams are
 // rejected with FZ_EBUFFER before any device work.  Every call on a device
 // shares the one array: calls whose device work overlaps (on different
 // streams, or from different host threads) race on it and must be ordered by
@@ -30,10 +30,9 @@
 namespace fz {
 namespace {
 
-constexpr size_t kNaErrBytes = 256;                                  // error word + unit counter, padded
-constexpr size_t kNaLutBytes = sizeof(uint16_t) << kLutBits;         // decode table
+constexpr size_t kNaErrBytes = 256;                                      // error word + unit counter, padded
 constexpr size_t kNaUnitBytes = 8 * (FZ_NOALLOC_MAX_CHUNKS / kDecUnit);  // per-unit bit offsets
-constexpr size_t kNaScratchBytes = kNaErrBytes + kNaLutBytes + kNaUnitBytes;
+constexpr size_t kNaScratchBytes = kNaErrBytes + kNaUnitBytes;
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNaScratchBytes];
 
@@ -111,10 +110,10 @@ fz_status fz_decompress_noalloc(const void *d_in, uint64_t in_bytes, const void 
   char *b = reinterpret_cast<char *>(base);
   DecodeWs ws;
   ws.err = reinterpret_cast<uint32_t *>(b);
-  ws.lut = reinterpret_cast<uint16_t *>(b + kNaErrBytes);
-  ws.gsum = reinterpret_cast<uint64_t *>(b + kNaErrBytes + kNaLutBytes);
+  ws.lut = nullptr;
+  ws.gsum = reinterpret_cast<uint64_t *>(b + kNaErrBytes);
   e = cudaMemsetAsync(ws.err, 0, 16, s);  // error word and work-unit counter start at zero
-  if (e == cudaSuccess) e = launch_decode_prep(in, h, ws, s);
+  if (e == cudaSuccess) e = launch_decode_offsets(in, h, ws, s);
   if (e == cudaSuccess) e = launch_decode_main(in, h, d_out, ws, s, sms);
   uint32_t err = 0;
   if (e == cudaSuccess) e = cudaMemcpyAsync(&err, ws.err, 4, cudaMemcpyDeviceToHost, s);
