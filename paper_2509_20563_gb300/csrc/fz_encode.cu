@@ -101,11 +101,14 @@ __device__ __forceinline__ void encode_tile(const CompressWs &ws, uint8_t *d_out
     uint32_t wi = rb >> 5;
     int cnt = (int)(rb & 31u);
     unsigned long long buf = 0;
+    // codewords two at a time (at most 28 bits), so at most one word fills per step
 #pragma unroll
-    for (int k = 0; k < PER; ++k) {
-      const uint32_t L = cw[k] >> 24, c = cw[k] & 0xffffffu;
-      buf |= (unsigned long long)c << (64 - cnt - (int)L);
-      cnt += (int)L;
+    for (int k = 0; k < PER; k += 2) {
+      const uint32_t L1 = cw[k + 1] >> 24;
+      const uint32_t v = ((cw[k] & 0xffffffu) << L1) | (cw[k + 1] & 0xffffffu);
+      const int n = (int)((cw[k] >> 24) + L1);
+      buf |= (unsigned long long)v << (64 - cnt - n);
+      cnt += n;
       if (cnt >= 32) {
         atomicOr(&lw[wi], (uint32_t)(buf >> 32));
         ++wi;

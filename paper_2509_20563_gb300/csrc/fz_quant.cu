@@ -19,6 +19,10 @@
 // HBM traffic: 4 bytes read and 2 bytes written per value.
 #include "fz_internal.cuh"
 
+#ifndef FZ_QUANT_MINB
+#define FZ_QUANT_MINB 3
+#endif
+
 namespace fz {
 
 namespace {
@@ -433,7 +437,7 @@ __device__ __forceinline__ void quant_tiles(const float *__restrict__ x, const G
 }
 
 template <int NDIM, int K>
-__global__ void __launch_bounds__(kQuantThreads, 3) k_quant(const float *__restrict__ x, Geom g, uint32_t R,
+__global__ void __launch_bounds__(kQuantThreads, FZ_QUANT_MINB) k_quant(const float *__restrict__ x, Geom g, uint32_t R,
                                                              CompressWs ws) {
   extern __shared__ __align__(16) unsigned char q_smem[];
   QuantSmem<NDIM> &sm = *reinterpret_cast<QuantSmem<NDIM> *>(q_smem);
