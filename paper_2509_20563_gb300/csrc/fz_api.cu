@@ -102,6 +102,7 @@ size_t layout_compress_split(const Geom &g, char *zbase, char *rbase, CompressWs
   ws.exc_idx = reinterpret_cast<uint32_t *>(rtake(4 * cap));
   ws.exc_val = reinterpret_cast<uint32_t *>(rtake(4 * cap));
   ws.ids = reinterpret_cast<uint8_t *>(rtake(g.n_blocks));
+  ws.tdst = reinterpret_cast<uint2 *>(rtake(8 * g.n_qtiles));
   if (rest_bytes) *rest_bytes = ro;
   return zo;
 }
@@ -345,7 +346,7 @@ fz_status fz_compress(fz_ctx *ctx, const float *d_in, uint32_t ndim, const uint6
   cudaError_t e = launch_codebook(g, r.R, r.pred, eb_mode, eb, ws, s);
   clk.mark("codebook", 1);
   if (e == cudaSuccess) { e = launch_encode(g, ws, out, s, ctx->sm_count); clk.mark("encode", 1); }
-  if (e == cudaSuccess) { e = launch_assemble(d_in, g, r.R, ws, out, s, ctx->sm_count); clk.mark("assemble", 1); }
+  if (e == cudaSuccess) { e = launch_assemble(d_in, g, r.R, ws, out, s, ctx->sm_count); clk.mark("assemble", 2); }
   if (e == cudaSuccess) e = cudaMemcpyAsync(ctx->h_pinned, &ws.ctl->res, sizeof(Result), cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) return from_cuda(e);
@@ -399,14 +400,17 @@ fz_status fz_decompress(fz_ctx *ctx, const void *d_in, uint64_t in_bytes, const 
   size_t off = 0;
   auto take = [&](size_t bytes) { size_t o = off; off += up(bytes); return o; };
   const bool selpath = h.predictor > FZ_PRED_LORENZO2;
+  // a per-block first-outlier table pays off when most blocks hold outliers
+  const bool ofirst = !selpath && h.n_out > h.n_chunks / 8;
   const size_t o_err = take(16), o_gsum = take(8 * n_units), o_lut = take(2u << kLutBits),
-               o_codes = selpath ? take(2 * g.npad) : 0;
+               o_codes = selpath ? take(2 * g.npad) : 0, o_ofirst = ofirst ? take(4 * h.n_chunks) : 0;
   if ((st = ensure_ws(ctx, off))) return st;
   char *base = reinterpret_cast<char *>(ctx->ws);
   DecodeWs ws;
   ws.err = reinterpret_cast<uint32_t *>(base + o_err);
   ws.lut = reinterpret_cast<uint16_t *>(base + o_lut);
   ws.gsum = reinterpret_cast<uint64_t *>(base + o_gsum);
+  ws.ofirst = ofirst ? reinterpret_cast<uint32_t *>(base + o_ofirst) : nullptr;
   StageClock clk(ctx, s, true);
   if (selpath) {
     e = cudaMemsetAsync(ws.err, 0, 16, s);
@@ -419,6 +423,7 @@ fz_status fz_decompress(fz_ctx *ctx, const void *d_in, uint64_t in_bytes, const 
     // unit offsets, then the decoder (which builds its decode table itself)
     e = cudaMemsetAsync(ws.err, 0, 16, s);
     if (e == cudaSuccess) { e = launch_decode_offsets(in, h, ws, s); clk.mark("dec_offsets", 2); }
+    if (e == cudaSuccess && ofirst) { e = launch_outlier_starts(in, h, ws, s, ctx->sm_count); clk.mark("outliers", 1); }
     if (e == cudaSuccess) { e = launch_decode_main(in, h, d_out, ws, s, ctx->sm_count); clk.mark("decode", 1); }
   }
   if (e == cudaSuccess) e = cudaMemcpyAsync(ctx->h_pinned, ws.err, 4, cudaMemcpyDeviceToHost, s);

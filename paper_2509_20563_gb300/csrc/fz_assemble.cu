@@ -1,7 +1,8 @@
 // fz_assemble.cu -- stream assembly: the header, the code-length table and
 // the anchors are copied into their 16-byte aligned sections, the outliers
 // and exceptions are gathered from the quantizer's per-tile scratch slots
-// into code-stream order, and the alignment gaps are zeroed (the chunk bit
+// into code-stream order (slot offsets per tile in k_assemble, the copies in
+// k_gather, a warp per tile), and the alignment gaps are zeroed (the chunk bit
 // lengths and the bitstream were written in place by the encoder).  For a
 // RAW stream the input floats are copied; for a CONST stream the single
 // value is written.
@@ -114,11 +115,9 @@ __device__ __forceinline__ void assemble_body(const float *__restrict__ x, const
     zero_gap(d_out, h.off_bits + 4 * ((h.total_bits + 31) / 32), h.total_bytes);
   }
   if ((n_out | n_exc) == 0) return;
-  // ---- ordered gather: one CTA per group of kTileGroup tiles
-  uint32_t *oidx = reinterpret_cast<uint32_t *>(d_out + h.off_out_idx);
-  int32_t *oval = reinterpret_cast<int32_t *>(d_out + h.off_out_val);
-  uint32_t *eidx = reinterpret_cast<uint32_t *>(d_out + h.off_exc_idx);
-  uint32_t *eval = reinterpret_cast<uint32_t *>(d_out + h.off_exc_val);
+  // ---- every tile's first outlier and exception slot in the stream (tile
+  // order = code-stream order): one CTA per group of kTileGroup tiles; the
+  // copies follow in gather_body
   const uint64_t n_tg = (g.n_qtiles + kTileGroup - 1) / kTileGroup;
   for (uint64_t grp = bid; grp < n_tg; grp += nblk) {
     // totals of the earlier groups
@@ -135,31 +134,56 @@ __device__ __forceinline__ void assemble_body(const float *__restrict__ x, const
     const unsigned long long ob = s_ob, eb = s_eb;
     // this thread's tiles
     const uint64_t t0 = grp * kTileGroup + (uint64_t)threadIdx.x * kTilesPerThread;
-    uint4 ti[kTilesPerThread];
+    uint2 cnt[kTilesPerThread];
     uint2 mine = make_uint2(0, 0);
 #pragma unroll
     for (int k = 0; k < kTilesPerThread; ++k) {
-      ti[k] = (t0 + k < g.n_qtiles) ? ws.tinfo[t0 + k] : make_uint4(0, 0, 0, 0);
-      mine.x += ti[k].x;
-      mine.y += ti[k].y;
+      const uint4 ti = (t0 + k < g.n_qtiles) ? ws.tinfo[t0 + k] : make_uint4(0, 0, 0, 0);
+      cnt[k] = make_uint2(ti.x, ti.y);
+      mine.x += ti.x;
+      mine.y += ti.y;
     }
     uint2 excl;
     block_exscan2(mine, excl, sw);
     unsigned long long o = ob + excl.x, e = eb + excl.y;
 #pragma unroll
     for (int k = 0; k < kTilesPerThread; ++k) {
-      for (uint32_t i = 0; i < ti[k].x; ++i) {
-        const uint64_t src = (uint64_t)ti[k].z + i;
-        if (src < ws.cap_list && o + i < n_out) { oidx[o + i] = ws.out_idx[src]; oval[o + i] = ws.out_val[src]; }
-      }
-      for (uint32_t i = 0; i < ti[k].y; ++i) {
-        const uint64_t src = (uint64_t)ti[k].w + i;
-        if (src < ws.cap_list && e + i < n_exc) { eidx[e + i] = ws.exc_idx[src]; eval[e + i] = ws.exc_val[src]; }
-      }
-      o += ti[k].x;
-      e += ti[k].y;
+      if (t0 + k < g.n_qtiles) ws.tdst[t0 + k] = make_uint2((uint32_t)o, (uint32_t)e);
+      o += cnt[k].x;
+      e += cnt[k].y;
     }
     __syncthreads();
+  }
+}
+
+// The ordered gather of the outliers and exceptions: each tile's entries
+// are contiguous in the scratch lists and go to the stream slots computed
+// by assemble_body; warp w of nw takes tiles w, w + nw, ... and its lanes
+// copy a tile's entries side by side.
+__device__ __forceinline__ void gather_body(const Geom &g, const CompressWs &ws, uint8_t *d_out, uint64_t w,
+                                            uint64_t nw) {
+  const Ctl *ctl = ws.ctl;
+  if (ctl->mode != kModeNormal) return;
+  const fz_header &h = ctl->res.hdr;
+  const uint64_t n_out = h.n_out, n_exc = h.n_exc;
+  if ((n_out | n_exc) == 0) return;
+  uint32_t *oidx = reinterpret_cast<uint32_t *>(d_out + h.off_out_idx);
+  int32_t *oval = reinterpret_cast<int32_t *>(d_out + h.off_out_val);
+  uint32_t *eidx = reinterpret_cast<uint32_t *>(d_out + h.off_exc_idx);
+  uint32_t *eval = reinterpret_cast<uint32_t *>(d_out + h.off_exc_val);
+  const int lane = threadIdx.x & 31;
+  for (uint64_t tile = w; tile < g.n_qtiles; tile += nw) {
+    const uint4 ti = ws.tinfo[tile];
+    if ((ti.x | ti.y) == 0) continue;
+    const uint2 dst = ws.tdst[tile];
+    for (uint32_t i = lane; i < ti.x; i += 32) {
+      const uint64_t src = (uint64_t)ti.z + i, o = (uint64_t)dst.x + i;
+      if (src < ws.cap_list && o < n_out) { oidx[o] = ws.out_idx[src]; oval[o] = ws.out_val[src]; }
+    }
+    for (uint32_t i = lane; i < ti.y; i += 32) {
+      const uint64_t src = (uint64_t)ti.w + i, e = (uint64_t)dst.y + i;
+      if (src < ws.cap_list && e < n_exc) { eidx[e] = ws.exc_idx[src]; eval[e] = ws.exc_val[src]; }
+    }
   }
 }
 
@@ -167,6 +191,11 @@ __global__ void __launch_bounds__(kAsmThreads) k_assemble(const float *__restric
                                                            CompressWs ws, uint8_t *d_out) {
   __shared__ AsmSmem sm;
   assemble_body(x, g, R, ws, d_out, blockIdx.x, gridDim.x, sm);
+}
+
+__global__ void __launch_bounds__(kAsmThreads) k_gather(Geom g, CompressWs ws, uint8_t *d_out) {
+  const uint64_t w = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  gather_body(g, ws, d_out, w, (uint64_t)gridDim.x * (blockDim.x >> 5));
 }
 
 // Batched variant: the whole grid assembles the fields one after another.
@@ -180,6 +209,17 @@ __global__ void __launch_bounds__(kAsmThreads) k_assemble_batch(const BatchJob *
   }
 }
 
+__global__ void __launch_bounds__(kAsmThreads) k_gather_batch(const BatchJob *__restrict__ jobs, uint32_t n,
+                                                               uint8_t *d_out) {
+  const uint64_t w = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const uint64_t nw = (uint64_t)gridDim.x * (blockDim.x >> 5);
+  for (uint32_t j = 0; j < n; ++j) {
+    const BatchJob &J = jobs[j];
+    if (J.out_off == kNoOutput) continue;
+    gather_body(J.g, J.ws, d_out + J.out_off, w, nw);
+  }
+}
+
 }  // namespace
 
 cudaError_t launch_assemble_batch(const BatchJob *jobs, uint32_t n, uint8_t *d_out, uint64_t max_n, cudaStream_t s,
@@ -189,6 +229,7 @@ cudaError_t launch_assemble_batch(const BatchJob *jobs, uint32_t n, uint8_t *d_o
   if (want < grid) grid = want;
   if (grid < 2) grid = 2;
   k_assemble_batch<<<(unsigned)grid, kAsmThreads, 0, s>>>(jobs, n, d_out);
+  k_gather_batch<<<(unsigned)(sm_count * 8), kAsmThreads, 0, s>>>(jobs, n, d_out);
   return cudaGetLastError();
 }
 
@@ -202,6 +243,9 @@ cudaError_t launch_assemble(const float *x, const Geom &g, uint32_t R, const Com
   if (grid < n_tg) grid = n_tg < (uint64_t)sm_count * 8 ? n_tg : (uint64_t)sm_count * 8;
   if (grid < 2) grid = 2;
   k_assemble<<<(unsigned)grid, kAsmThreads, 0, s>>>(x, g, R, ws, d_out);
+  uint64_t ggrid = (g.n_qtiles + kAsmThreads / 32 - 1) / (kAsmThreads / 32);
+  if (ggrid > (uint64_t)sm_count * 8) ggrid = (uint64_t)sm_count * 8;
+  k_gather<<<(unsigned)ggrid, kAsmThreads, 0, s>>>(g, ws, d_out);
   return cudaGetLastError();
 }
 

@@ -322,7 +322,7 @@ fz_status fz_compress_batch(fz_ctx *ctx, uint32_t n, const float *const *d_in, c
     return rseg;
   };
   uint8_t *out = reinterpret_cast<uint8_t *>(d_out);
-  int nlaunch = 5;  // range, codebook, offsets, assemble, results
+  int nlaunch = 6;  // range, codebook, offsets, assemble (two kernels), results
   for (int c = 0; c < kQClasses; ++c) nlaunch += P.qmem[c].empty() ? 0 : 1;
   for (int c = 0; c < 2; ++c) nlaunch += P.emem[c].empty() ? 0 : 1;
   auto enqueue = [&](const BatchTune &t, uint64_t total_segs, cudaStream_t q) -> cudaError_t {

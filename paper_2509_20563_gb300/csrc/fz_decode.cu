@@ -266,6 +266,7 @@ struct DecParams {
   const uint64_t *goff;   // per work unit: first bit
   const uint16_t *lut;    // decode table (batched decode)
   const uint8_t *lens;    // code-length table (single-field decode builds its table from it)
+  const uint32_t *ofirst; // per block with outliers: index of its first outlier (or null: search)
   uint32_t nsym;
   uint64_t total_bits;
   uint32_t *err;          // err[0] error word, err[1] work-unit counter
@@ -279,30 +280,17 @@ struct DecParams {
 // they take and return their state by value so that nothing in the loop has
 // its address taken (which would move it to local memory).
 struct Side {
-  uint64_t oc, ec;
+  uint64_t oc, ec;   // next outlier / exception of the block in the lists (oc ~0: not located yet)
+  uint32_t next_o;   // position of outlier oc (prefetched; ~0 past the end)
+  int32_t next_v;    // its residual
   uint32_t next_e;
 };
 
-struct OutlierHit {
-  int32_t value;
-  uint32_t ok;
-  uint64_t oc;
-};
-
-__device__ __noinline__ OutlierHit fetch_outlier(const uint32_t *out_idx, const int32_t *out_val, uint64_t n_out,
-                                                 uint64_t oc, uint32_t pos0, uint32_t pos) {
-  OutlierHit r;
-  if (oc == ~0ull) oc = lower_bound_u32(out_idx, n_out, pos0);
-  if (oc < n_out && __ldg(out_idx + oc) == pos) {
-    r.value = __ldg(out_val + oc);
-    r.ok = 1;
-    r.oc = oc + 1;
-  } else {
-    r.value = 0;
-    r.ok = 0;
-    r.oc = oc;
-  }
-  return r;
+// Position and residual of outlier oc, loaded ahead of their use.
+__device__ __forceinline__ void load_outlier(const DecParams &p, Side &sd) {
+  const bool in = sd.oc < p.n_out;
+  sd.next_o = in ? __ldg(p.out_idx + sd.oc) : 0xffffffffu;
+  sd.next_v = in ? __ldg(p.out_val + sd.oc) : 0;
 }
 
 struct ExceptionHit {
@@ -321,6 +309,8 @@ __device__ __noinline__ ExceptionHit fetch_exception(const uint32_t *exc_idx, co
 
 __device__ __forceinline__ void init_side(const DecParams &p, Side &sd, uint32_t pos0) {
   sd.oc = ~0ull;
+  sd.next_o = 0xffffffffu;
+  sd.next_v = 0;
   sd.ec = 0;
   sd.next_e = 0xffffffffu;
   if (p.n_exc) {
@@ -394,15 +384,22 @@ constexpr size_t dec_smem_bytes() {
 // The stored residuals of the outliers among eight codes (code 0 decodes
 // to -R, which no in-range code gives).  Rare: out of the decode loop's
 // straight-line code.
-__device__ __forceinline__ void fix_outliers(const DecParams &p, Side &sd, uint32_t pos0, uint32_t pos,
+__device__ __forceinline__ void fix_outliers(const DecParams &p, Side &sd, uint64_t j, uint32_t pos0, uint32_t pos,
                                              int32_t (&d)[8], bool &bad) {
+  if (sd.oc == ~0ull) {  // the block's first outlier: from the per-block table, else by search
+    sd.oc = p.ofirst ? __ldg(p.ofirst + j) : lower_bound_u32(p.out_idx, p.n_out, pos0);
+    load_outlier(p, sd);
+  }
 #pragma unroll
   for (int u = 0; u < 8; ++u) {
     if (d[u] == -p.R) {
-      const OutlierHit h = fetch_outlier(p.out_idx, p.out_val, p.n_out, sd.oc, pos0, pos + u);
-      sd.oc = h.oc;
-      bad |= !h.ok;
-      d[u] = h.value;
+      const bool hit = sd.next_o == pos + u;
+      bad |= !hit;
+      d[u] = hit ? sd.next_v : 0;
+      if (hit) {
+        ++sd.oc;
+        load_outlier(p, sd);  // consumed at the next outlier, so its latency hides behind the decode
+      }
     }
   }
 }
@@ -520,14 +517,14 @@ __device__ __forceinline__ void decode_chunk(const DecParams &p, const Geom &g, 
   for (int x = 0; x < 8; ++x) { s.Y1[x] = 0; s.Y2[x] = 0; }
 
   int32_t cur[8];
-  if (br.group8(slut, p.R, cur)) fix_outliers(p, sd, pos0, pos0, cur, bad);
+  if (br.group8(slut, p.R, cur)) fix_outliers(p, sd, j, pos0, pos0, cur, bad);
   cur[0] += anchor;  // the block origin's residual is its anchor
 #pragma unroll 1
   for (int gi = 0; gi < NG - 1; ++gi) {
     int32_t nxt[8];
     const bool zero = br.group8(slut, p.R, nxt);
     consume<NDIM, K, EXC, T>(p, g, sd, s, st, gi, cur, pos0, X0, Y0, Z0, vecbase);
-    if (zero) fix_outliers(p, sd, pos0, pos0 + (uint32_t)(gi + 1) * 8, nxt, bad);
+    if (zero) fix_outliers(p, sd, j, pos0, pos0 + (uint32_t)(gi + 1) * 8, nxt, bad);
 #pragma unroll
     for (int u = 0; u < 8; ++u) cur[u] = nxt[u];
   }
@@ -690,6 +687,31 @@ cudaError_t launch_decode_prep(const uint8_t *d_in, const fz_header &h, const De
   return cudaGetLastError();
 }
 
+namespace {
+// First outlier of every block that has outliers (the list ascends by
+// position; blocks without outliers are left untouched and never read).
+__global__ void k_outlier_starts(const uint32_t *__restrict__ out_idx, uint64_t n_out, uint32_t bsize,
+                                 uint64_t n_chunks, uint32_t *ofirst) {
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_out;
+       i += (uint64_t)gridDim.x * blockDim.x) {
+    const uint32_t c = __ldg(out_idx + i) / bsize;
+    if (c < n_chunks && (i == 0 || __ldg(out_idx + i - 1) / bsize != c)) ofirst[c] = (uint32_t)i;
+  }
+}
+}  // namespace
+
+cudaError_t launch_outlier_starts(const uint8_t *d_in, const fz_header &h, const DecodeWs &ws, cudaStream_t s,
+                                  int sm_count) {
+  Geom g;
+  make_geom(h.ndim, h.dims, g);
+  uint64_t grid = (h.n_out + 255) / 256;
+  if (grid > (uint64_t)sm_count * 8) grid = (uint64_t)sm_count * 8;
+  if (grid < 1) grid = 1;
+  k_outlier_starts<<<(unsigned)grid, 256, 0, s>>>(reinterpret_cast<const uint32_t *>(d_in + h.off_out_idx), h.n_out,
+                                                  g.bsize, h.n_chunks, ws.ofirst);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_decode_offsets(const uint8_t *d_in, const fz_header &h, const DecodeWs &ws, cudaStream_t s) {
   const uint64_t n_chunks = h.n_chunks;
   const uint64_t n_units = dec_units_of(n_chunks);
@@ -718,6 +740,7 @@ cudaError_t launch_decode_main(const uint8_t *d_in, const fz_header &h, float *d
   p.n_units = dec_units_of(h.n_chunks);
   p.goff = ws.gsum;
   p.lens = d_in + h.off_lens;
+  p.ofirst = ws.ofirst;
   p.nsym = 2 * h.radius;
   p.total_bits = h.total_bits;
   p.lut = ws.lut;
@@ -816,6 +839,8 @@ void fill_dec_job(void *dst, const uint8_t *d_in, const fz_header &h, float *d_o
   p.R = (int32_t)h.radius;
   J.lens = d_in + h.off_lens;
   J.nsym = 2 * h.radius;
+  p.lens = d_in + h.off_lens;
+  p.ofirst = nullptr;
   J.total_bits = h.total_bits;
   J.unit_base = unit_base;
   memcpy(dst, &J, sizeof(J));

@@ -252,6 +252,7 @@ struct CompressWs {
   Ctl *ctl;
   uint4 *tinfo;            // per quantization tile: n_out, n_exc, first outlier slot, first exception slot
   uint2 *tgroup;           // per group of kTileGroup tiles: outlier and exception counts
+  uint2 *tdst;             // per quantization tile: its first outlier and exception slot in the stream
   uint64_t *estatus;       // look-back status per encode tile
   size_t zero_bytes;       // bytes from ctl to the end of estatus (memset per call)
   uint16_t *codes;         // npad block-major codes
@@ -316,10 +317,13 @@ struct DecodeWs {
   uint16_t *lut;           // 1 << kLutBits entries: codeword length, symbol
   uint64_t *gsum;          // per work unit of kDecUnit chunks: sum of chunk bits, then exclusive offset
   uint32_t *err;           // device error word; err[1] is the work-unit counter (both zeroed per call)
+  uint32_t *ofirst = nullptr;  // per block: index of its first outlier (filled when outliers are many)
 };
 
 inline __host__ __device__ uint64_t dec_units_of(uint64_t n_chunks) { return (n_chunks + kDecUnit - 1) / kDecUnit; }
 cudaError_t launch_decode_prep(const uint8_t *d_in, const fz_header &h, const DecodeWs &ws, cudaStream_t s);
+cudaError_t launch_outlier_starts(const uint8_t *d_in, const fz_header &h, const DecodeWs &ws, cudaStream_t s,
+                                  int sm_count);
 // work-unit bit offsets only (the Lorenzo decoder builds its decode table itself)
 cudaError_t launch_decode_offsets(const uint8_t *d_in, const fz_header &h, const DecodeWs &ws, cudaStream_t s);
 cudaError_t launch_decode_main(const uint8_t *d_in, const fz_header &h, float *d_out, const DecodeWs &ws,
