@@ -44,6 +44,20 @@ WORKLOAD = "3D FP32 512^3 Gaussian random field (k^-5/3), REL 1e-4, Lorenzo-1, r
 METRIC = "compress/decompress GB/s vs HBM peak at REL 1e-4; CR learned vs plain"
 
 
+def max_over_ranks(ms: float, world: int, device) -> float:
+    """The slowest rank's time (replicas: every rank times its own work)."""
+    if world <= 1:
+        return ms
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
+def aggregate_gbs(steps: int, world: int, bytes_per_step_per_rank: int, max_ms: float) -> float:
+    """Whole-job throughput: the bytes all ranks processed over the slowest rank's time."""
+    return steps * world * bytes_per_step_per_rank / (max_ms * 1e-3) / 1e9
+
+
 def _peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -221,10 +235,7 @@ def run_fz(args, rank, world, local_rank):
     tc = [a.elapsed_time(b) for a, b, _ in ev]
     td = [b.elapsed_time(c) for _, b, c in ev]
     tot_ms = sum(tc) + sum(td)
-    if world > 1:
-        t = torch.tensor([tot_ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        tot_ms = float(t.item())
+    tot_ms = max_over_ranks(tot_ms, world, dev)
     peak, peak_kind = _peaks()
     mc, md = statistics.mean(tc), statistics.mean(td)
     comp_gbs = 4 * N / (mc * 1e-3) / 1e9
@@ -243,7 +254,7 @@ def run_fz(args, rank, world, local_rank):
     kern = {k: statistics.mean(v) for k, v in {**stages_c, **stages_d}.items() if k in alg}
     dom = max(kern, key=kern.get)
     ach = alg[dom] / (kern[dom] * 1e-3) / 1e9
-    value = args.steps * world * 4 * N / (tot_ms * 1e-3) / 1e9
+    value = aggregate_gbs(args.steps, world, 4 * N, tot_ms)
     res = {"metric": METRIC, "value": round(value, 2), "unit": "GB/s", "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": round(tot_ms / args.steps, 4), "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
@@ -298,11 +309,8 @@ def run_fz(args, rank, world, local_rank):
         e1.record(stream)
         torch.cuda.synchronize(dev)
         ems = e0.elapsed_time(e1)
-        if world > 1:
-            t = torch.tensor([ems], device=dev)
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            ems = float(t.item())
-        res["e2e"] = {"value": round(args.e2e_steps * world * 4 * N / (ems * 1e-3) / 1e9, 2), "unit": "GB/s",
+        ems = max_over_ranks(ems, world, dev)
+        res["e2e"] = {"value": round(aggregate_gbs(args.e2e_steps, world, 4 * N, ems), 2), "unit": "GB/s",
                       "h2d_bytes_per_step": 4 * N + nb, "d2h_bytes_per_step": nb + 4 * N,
                       "steps": args.e2e_steps}
     if rank == 0 and world == 1 and not args.no_batch:
