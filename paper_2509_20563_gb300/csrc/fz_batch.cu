@@ -142,13 +142,18 @@ cudaGraphExec_t capture(fz_ctx *ctx, F &&enqueue) {
 }
 
 // Coordinate descent over the candidate values of each tuned parameter;
-// `run(t)` times one eager run with launch shape t (negative on error).
+// `run(t)` times one eager run with launch shape t (negative on error).  A
+// candidate's time is the best of two runs, and it must beat the incumbent
+// by 3% to replace it, so that timing noise does not pick a worse shape.
 template <class R>
 fz_status autotune(BatchTune &best, const std::vector<std::pair<int BatchTune::*, std::vector<int>>> &space,
                    R &&run) {
-  float best_ms = run(best);  // warm-up run (first-touch of the workspace)
-  if (best_ms < 0) return FZ_ECUDA;
-  best_ms = run(best);
+  auto best_of_two = [&](const BatchTune &t) {
+    const float a = run(t), b = run(t);
+    return (a < 0 || b < 0) ? -1.f : (a < b ? a : b);
+  };
+  if (run(best) < 0) return FZ_ECUDA;  // warm-up run (first touch of the workspace)
+  float best_ms = best_of_two(best);
   if (best_ms < 0) return FZ_ECUDA;
   for (const auto &dim : space) {
     const int keep = best.*(dim.first);
@@ -157,9 +162,9 @@ fz_status autotune(BatchTune &best, const std::vector<std::pair<int BatchTune::*
       if (v == keep) continue;
       BatchTune t = best;
       t.*(dim.first) = v;
-      const float ms = run(t);
+      const float ms = best_of_two(t);
       if (ms < 0) return FZ_ECUDA;
-      if (ms < best_ms) { best_ms = ms; arg = v; }
+      if (ms < 0.97f * best_ms) { best_ms = ms; arg = v; }
     }
     best.*(dim.first) = arg;
   }
