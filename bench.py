@@ -333,6 +333,7 @@ def bench_batch(fz, dev, stream, args):
     n_vals = sum(x.numel() for x in xs)
     ctx = fz.Context(dev.index or 0)
     buf, offs = fz.compress_batch(xs, args.eb, ctx=ctx)      # autotune + capture
+    tune_c = list(fz.profile(ctx=ctx).batch_tune)
     for _ in range(2):
         buf, offs = fz.compress_batch(xs, args.eb, out=buf, ctx=ctx)
     ys = fz.decompress_batch(buf, offs, ctx=ctx)
@@ -373,7 +374,10 @@ def bench_batch(fz, dev, stream, args):
             "batch_compress_roofline_frac": round(forced_c / (t_bc * 1e-3) / 1e9 / peak, 4),
             "batch_decompress_roofline_frac": round(forced_d / (t_bd * 1e-3) / 1e9 / peak, 4),
             "speedup_compress": round(t_sc / t_bc, 3), "speedup_decompress": round(t_sd / t_bd, 3),
-            "graphs": int(prof.batch_graphs), "plans": int(prof.batch_plans)}
+            "graphs": int(prof.batch_graphs), "plans": int(prof.batch_plans),
+            "autotuned_compress": {"range_segment_log2": tune_c[0], "quant_ctas_per_sm": tune_c[1],
+                                   "encode_ctas_per_sm": tune_c[2]},
+            "autotuned_decode_ctas_per_sm": int(prof.batch_tune[3])}
 
 
 def bench_learned(fz, dev, args):

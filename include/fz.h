@@ -230,6 +230,8 @@ typedef struct {
   float decompress_ms[FZ_MAX_STAGES];
   uint64_t launches;
   uint32_t batch_plans, batch_graphs;
+  int32_t batch_tune[4];                  /* launch shape of the newest batch plan: range segment log2,
+                                             quantizer / encoder / decoder CTAs per SM (0 = occupancy limit) */
 } fz_profile;
 
 /* Turn stage timing on (enable != 0) or off.  Host-only bookkeeping; the

@@ -280,7 +280,8 @@ class Profile(C.Structure):
     _fields_ = [("n_compress", C.c_uint32), ("n_decompress", C.c_uint32),
                 ("compress_names", (C.c_char * 16) * 12), ("compress_ms", C.c_float * 12),
                 ("decompress_names", (C.c_char * 16) * 12), ("decompress_ms", C.c_float * 12),
-                ("launches", C.c_uint64), ("batch_plans", C.c_uint32), ("batch_graphs", C.c_uint32)]
+                ("launches", C.c_uint64), ("batch_plans", C.c_uint32), ("batch_graphs", C.c_uint32),
+                ("batch_tune", C.c_int32 * 4)]
 
 
 def profile(device: int = 0, ctx: Context | None = None) -> Profile:

@@ -258,6 +258,13 @@ fz_status fz_ctx_get_profile(fz_ctx *ctx, fz_profile *out) {
   out->batch_plans = (uint32_t)ctx->plans.size();
   out->batch_graphs = 0;
   for (const BatchPlan *p : ctx->plans) out->batch_graphs += p->exec ? 1u : 0u;
+  if (!ctx->plans.empty()) {
+    const BatchTune &t = ctx->plans.back()->tune;
+    out->batch_tune[0] = t.range_seg_log2;
+    out->batch_tune[1] = t.quant_per_sm;
+    out->batch_tune[2] = t.encode_per_sm;
+    out->batch_tune[3] = t.decode_per_sm;
+  }
   if (!ctx->profiling) return FZ_OK;
   if (cudaSetDevice(ctx->device) != cudaSuccess) return FZ_ECUDA;
   for (int kind = 0; kind < 2; ++kind) {
@@ -289,8 +296,10 @@ fz_status fz_ctx_destroy(fz_ctx *ctx) {
   }
   destroy_batch_plans(ctx);
   if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
-  if (ctx->bws) cudaFree(ctx->bws);
-  if (ctx->h_batch) cudaFreeHost(ctx->h_batch);
+  for (int k = 0; k < 2; ++k) {
+    if (ctx->bws[k]) cudaFree(ctx->bws[k]);
+    if (ctx->h_batch[k]) cudaFreeHost(ctx->h_batch[k]);
+  }
   if (ctx->ws) cudaFree(ctx->ws);
   if (ctx->h_pinned) cudaFreeHost(ctx->h_pinned);
   cudaSetDevice(prev);

@@ -34,12 +34,17 @@
 
 namespace fz {
 
-void destroy_batch_plans(fz_ctx *ctx) {
+void destroy_batch_plans(fz_ctx *ctx, int kind) {
+  std::vector<BatchPlan *> keep;
   for (BatchPlan *p : ctx->plans) {
+    if (kind >= 0 && (int)p->decompress != kind) {
+      keep.push_back(p);
+      continue;
+    }
     if (p->exec) cudaGraphExecDestroy(p->exec);
     delete p;
   }
-  ctx->plans.clear();
+  ctx->plans.swap(keep);
 }
 
 namespace {
@@ -49,32 +54,39 @@ constexpr int kQClasses = 6;  // (ndim 1..3) x (Lorenzo order 1..2)
 
 inline int qclass(uint32_t ndim, uint32_t k) { return (int)(ndim - 1) * 2 + (int)(k - 1); }
 
-// Device and pinned host memory of batched calls.  Growing either one
-// invalidates every cached graph (they hold the old addresses).
-fz_status ensure_batch_mem(fz_ctx *ctx, size_t dev_bytes, size_t host_bytes) {
-  if (ctx->bws_bytes < dev_bytes) {
-    destroy_batch_plans(ctx);
-    if (ctx->bws) cudaFree(ctx->bws);
-    ctx->bws = nullptr;
-    ctx->bws_bytes = 0;
-    if (cudaMalloc(&ctx->bws, dev_bytes) != cudaSuccess) {
+// Device and pinned host memory of batched calls of one kind (0 compress,
+// 1 decompress), grown with 25% headroom.  Growing either invalidates that
+// kind's cached graphs (they hold the old addresses).
+fz_status ensure_batch_mem(fz_ctx *ctx, int kind, size_t dev_bytes, size_t host_bytes) {
+  if (ctx->bws_bytes[kind] < dev_bytes) {
+    destroy_batch_plans(ctx, kind);
+    if (ctx->bws[kind]) cudaFree(ctx->bws[kind]);
+    ctx->bws[kind] = nullptr;
+    ctx->bws_bytes[kind] = 0;
+    size_t want = dev_bytes + dev_bytes / 4;
+    if (cudaMalloc(&ctx->bws[kind], want) != cudaSuccess) {
       cudaGetLastError();
-      ctx->bws = nullptr;
-      return FZ_ENOMEM;
+      want = dev_bytes;
+      if (cudaMalloc(&ctx->bws[kind], want) != cudaSuccess) {
+        cudaGetLastError();
+        ctx->bws[kind] = nullptr;
+        return FZ_ENOMEM;
+      }
     }
-    ctx->bws_bytes = dev_bytes;
+    ctx->bws_bytes[kind] = want;
   }
-  if (ctx->h_batch_bytes < host_bytes) {
-    destroy_batch_plans(ctx);
-    if (ctx->h_batch) cudaFreeHost(ctx->h_batch);
-    ctx->h_batch = nullptr;
-    ctx->h_batch_bytes = 0;
-    if (cudaMallocHost(&ctx->h_batch, host_bytes) != cudaSuccess) {
+  if (ctx->h_batch_bytes[kind] < host_bytes) {
+    destroy_batch_plans(ctx, kind);
+    if (ctx->h_batch[kind]) cudaFreeHost(ctx->h_batch[kind]);
+    ctx->h_batch[kind] = nullptr;
+    ctx->h_batch_bytes[kind] = 0;
+    const size_t want = host_bytes + host_bytes / 4;
+    if (cudaMallocHost(&ctx->h_batch[kind], want) != cudaSuccess) {
       cudaGetLastError();
-      ctx->h_batch = nullptr;
+      ctx->h_batch[kind] = nullptr;
       return FZ_ENOMEM;
     }
-    ctx->h_batch_bytes = host_bytes;
+    ctx->h_batch_bytes[kind] = want;
   }
   if (!ctx->cap_stream && cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
     cudaGetLastError();
@@ -275,12 +287,12 @@ fz_status fz_compress_batch(fz_ctx *ctx, uint32_t n, const float *const *d_in, c
   const size_t o_rest = P.o_res + up(P.res_bytes);
   P.dev_bytes = o_rest + rtot;
   const size_t host_bytes = up(P.table_bytes) + up(P.res_bytes);
-  fz_status st = ensure_batch_mem(ctx, P.dev_bytes, host_bytes);
+  fz_status st = ensure_batch_mem(ctx, 0, P.dev_bytes, host_bytes);
   if (st) return st;
 
   // ---- the device table (host image in pinned memory)
-  char *dbase = reinterpret_cast<char *>(ctx->bws);
-  char *hbase = reinterpret_cast<char *>(ctx->h_batch);
+  char *dbase = reinterpret_cast<char *>(ctx->bws[0]);
+  char *hbase = reinterpret_cast<char *>(ctx->h_batch[0]);
   BatchJob *hjobs = reinterpret_cast<BatchJob *>(hbase);
   uint32_t *hmem = reinterpret_cast<uint32_t *>(hbase + P.jobs_bytes);
   char *hres = hbase + up(P.table_bytes);
@@ -410,9 +422,9 @@ fz_status fz_decompress_batch(fz_ctx *ctx, uint32_t n, const void *d_in, const u
   const size_t hdr_bytes = (size_t)FZ_HEADER_BYTES * n;
   const size_t djb = dec_job_bytes(), pjb = plain_job_bytes();
   const size_t tbl_max = djb * n + pjb * n + sizeof(uint32_t) * n;
-  fz_status st = ensure_batch_mem(ctx, up(16) + up(tbl_max), up(hdr_bytes) + up(tbl_max) + up(16));
+  fz_status st = ensure_batch_mem(ctx, 1, up(16) + up(tbl_max), up(hdr_bytes) + up(tbl_max) + up(16));
   if (st) return st;
-  char *hbase = reinterpret_cast<char *>(ctx->h_batch);
+  char *hbase = reinterpret_cast<char *>(ctx->h_batch[1]);
   cudaError_t e = cudaSuccess;
   for (uint32_t j = 0; j < n && e == cudaSuccess; ++j)
     e = cudaMemcpyAsync(hbase + (size_t)FZ_HEADER_BYTES * j, in + h_offsets[j], FZ_HEADER_BYTES,
@@ -462,9 +474,9 @@ fz_status fz_decompress_batch(fz_ctx *ctx, uint32_t n, const void *d_in, const u
     o_gsum[i] = dev;
     dev += up(8 * dec_units(hs[dec[i]]));
   }
-  if ((st = ensure_batch_mem(ctx, dev, up(hdr_bytes) + up(tbl) + up(16)))) return st;
-  char *dbase = reinterpret_cast<char *>(ctx->bws);
-  hbase = reinterpret_cast<char *>(ctx->h_batch);
+  if ((st = ensure_batch_mem(ctx, 1, dev, up(hdr_bytes) + up(tbl) + up(16)))) return st;
+  char *dbase = reinterpret_cast<char *>(ctx->bws[1]);
+  hbase = reinterpret_cast<char *>(ctx->h_batch[1]);
   char *htbl = hbase + up(hdr_bytes);
   uint32_t *herr = reinterpret_cast<uint32_t *>(htbl + up(tbl));
   uint32_t *derr = reinterpret_cast<uint32_t *>(dbase);

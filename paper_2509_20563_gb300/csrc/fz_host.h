@@ -33,10 +33,12 @@ struct fz_ctx {
   uint64_t launches = 0;
   // batched calls: workspace, pinned job tables / results, capture stream and
   // the cached plans (autotuned launch shapes and instantiated graphs)
-  void *bws = nullptr;
-  size_t bws_bytes = 0;
-  void *h_batch = nullptr;
-  size_t h_batch_bytes = 0;
+  // [0] batched compress, [1] batched decompress: separate, so that neither
+  // kind's growth invalidates the other kind's graphs
+  void *bws[2] = {nullptr, nullptr};
+  size_t bws_bytes[2] = {0, 0};
+  void *h_batch[2] = {nullptr, nullptr};
+  size_t h_batch_bytes[2] = {0, 0};
   cudaStream_t cap_stream = nullptr;
   std::vector<fz::BatchPlan *> plans;
   bool batch_tuning = true;
@@ -75,6 +77,6 @@ inline bool overlaps(const void *a, uint64_t na, const void *b, uint64_t nb) {
 // Defined in fz_api.cu.
 size_t layout_compress_split(const Geom &g, char *zbase, char *rbase, CompressWs &ws, size_t *rest_bytes);
 fz_status check_header(const fz_header &h, uint64_t in_bytes, Geom &g);
-void destroy_batch_plans(fz_ctx *ctx);
+void destroy_batch_plans(fz_ctx *ctx, int kind = -1);  // kind 0 compress, 1 decompress, -1 both
 
 }  // namespace fz
