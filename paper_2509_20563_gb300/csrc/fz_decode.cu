@@ -540,7 +540,9 @@ __device__ __forceinline__ void decode_units(const DecParams &p, const Geom &g, 
                                              int32_t *sstate, uint32_t *sring) {
   constexpr int T = DecCta<NDIM, K>::T;
   const int t = threadIdx.x;
-  const bool vecbase = ((g.nx & 3u) == 0) && (((uintptr_t)p.out & 15u) == 0);
+  // 16-byte stores of 4 consecutive x: aligned whenever rows start on a
+  // 4-value boundary (1D: always; 2D/3D: nx a multiple of 4)
+  const bool vecbase = (NDIM == 1 || (g.nx & 3u) == 0) && (((uintptr_t)p.out & 15u) == 0);
   const int lane = t & 31;
   for (;;) {
     const uint32_t u = claim_unit(p.err + 1);
@@ -644,7 +646,7 @@ __global__ void __launch_bounds__(DecCta<NDIM, K>::T, 1) k_decode_batch(const De
     if (t == 0) { sp = J.p; sg = J.g; }
     load_lut<T>(slut, J.p.lut);
     __syncthreads();
-    const bool vecbase = ((sg.nx & 3u) == 0) && (((uintptr_t)sp.out & 15u) == 0);
+    const bool vecbase = (NDIM == 1 || (sg.nx & 3u) == 0) && (((uintptr_t)sp.out & 15u) == 0);
     for (uint64_t u = t0 - jb + warp; u < t1 - jb; u += kWarps) {
       uint32_t cb;
       const uint64_t start = unit_start(sp.chunk_bits, sp.goff, sp.n_chunks, u, cb);

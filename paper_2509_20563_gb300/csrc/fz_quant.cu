@@ -110,7 +110,7 @@ __device__ __forceinline__ void load_tile(const float *__restrict__ x, const Geo
     const uint32_t X = t.x0 + col, Y = t.y0 + (row % S::BY), Z = t.z0 + row / S::BY;
     const bool inrow = Y < g.ny && Z < g.nz;
     const uint64_t fi = ((uint64_t)Z * g.ny + Y) * g.nx + X;
-    if (inrow && vec_ok && X < g.nx) {
+    if (inrow && vec_ok && X + 4 <= g.nx) {
       v[j] = __ldcs(reinterpret_cast<const float4 *>(x + fi));
     } else {
       float a[4];
@@ -331,7 +331,9 @@ __device__ __forceinline__ void quant_tiles(const float *__restrict__ x, const G
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const uint32_t nsym = 2 * R;
   for (int s = tid; s < kMaxSym; s += kQuantThreads) sm.shist[s] = 0;
-  const bool vec_ok = ((g.nx & 3u) == 0) && (((uintptr_t)x & 15u) == 0);
+  // 16-byte loads of 4 consecutive x: aligned whenever rows start on a
+  // 4-value boundary (1D: always; 2D/3D: nx a multiple of 4)
+  const bool vec_ok = (NDIM == 1 || (g.nx & 3u) == 0) && (((uintptr_t)x & 15u) == 0);
 
   float4 v[4];
   if (tile < t_end) load_tile<NDIM>(x, g, tile_xy<NDIM>(g, tile), tid, vec_ok, v);
