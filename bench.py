@@ -41,6 +41,12 @@ sys.path.insert(0, ROOT)
 import synth  # noqa: E402
 
 WORKLOAD = "3D FP32 512^3 Gaussian random field (k^-5/3), REL 1e-4, Lorenzo-1, radius 512"
+
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per launch of each
+# large kernel on exactly this workload (512^3, REL 1e-4), from one ncu
+# capture of the current kernels (profiles/dram_grf512_rel1e-4.md); reported
+# as roofline.traffic for the dominant kernel, null for any other workload.
+NCU_DRAM_BYTES_512 = {"range": 539690752, "quant": 747504384, "encode": 358804224, "decode": 705417216}
 METRIC = "compress/decompress GB/s vs HBM peak at REL 1e-4; CR learned vs plain"
 
 
@@ -271,7 +277,9 @@ def run_fz(args, rank, world, local_rank):
            "stages_ms": {**{f"c.{k}": round(statistics.mean(v), 4) for k, v in stages_c.items()},
                          **{f"d.{k}": round(statistics.mean(v), 4) for k, v in stages_d.items()}},
            "roofline": {"kernel": dom, "bound": "hbm", "achieved": round(ach, 1), "peak": peak, "unit": "GB/s",
-                        "frac": round(ach / peak, 4), "traffic": args.traffic,
+                        "frac": round(ach / peak, 4),
+                        "traffic": args.traffic if args.traffic is not None else
+                        (NCU_DRAM_BYTES_512.get(dom) if (args.size == 512 and args.eb == 1e-4) else None),
                         "algorithmic_bytes": alg[dom], "peak_kind": peak_kind},
            "gpu_launches": int(launches), "clocks": clk}
     # end to end through the C ABI with host buffers: H2D input, compress, D2H stream,
