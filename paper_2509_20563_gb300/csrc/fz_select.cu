@@ -24,6 +24,10 @@
 
 #include "fz_decode_common.cuh"
 
+#ifndef FZ_SEL_MINB
+#define FZ_SEL_MINB 3
+#endif
+
 namespace fz {
 
 namespace {
@@ -123,6 +127,73 @@ __device__ __forceinline__ uint32_t trial_bits(int32_t d, uint32_t R) {
   return 1u + 2u * (31u - (uint32_t)__clz((int)(a + 1)));
 }
 
+// ---------------------------------------------------------------- full blocks
+// A block wholly inside the domain whose far corners o + 8 {0,1}^3 are all in
+// the domain (every block except those on the field's upper faces).  Lane l
+// holds the 16 points p = 32 i + l: px = l & 7, py = (l >> 3) + 4 (i & 1),
+// pz = i >> 1.  The Lorenzo residuals come from registers by successive
+// differences with zero padding -- (1 - S_x)(1 - S_y)(1 - S_z), applied once
+// for order 1 and twice for order 2 -- instead of 8 or 27 shared-memory
+// reads per point.
+
+__device__ __forceinline__ bool full_block(const BlockView &b) {
+  return b.xlim == 8 && b.ylim == 8 && b.zlim == 8 && (b.cin & 0xffu) == 0xffu;
+}
+
+__device__ __forceinline__ void fb_load(const BlockView &b, int32_t (&a)[16]) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int i = 0; i < 16; ++i) a[i] = b.at(lane & 7, (lane >> 3) + 4 * (i & 1), i >> 1);
+}
+
+// One application of (1 - S_x)(1 - S_y)(1 - S_z), zero padding, in place.
+__device__ __forceinline__ void fb_lorenzo(int32_t (&a)[16]) {
+  const int lane = threadIdx.x & 31;
+  const bool xin = (lane & 7) != 0, yin = lane >= 8;
+#pragma unroll
+  for (int i = 0; i < 16; ++i) {
+    const int32_t l = __shfl_up_sync(0xffffffffu, a[i], 1);
+    a[i] -= xin ? l : 0;
+  }
+  // the row below: lane - 8, or for row 4 (odd i, lanes 0-7) row 3 of the same
+  // plane (lane + 24, i - 1); descending i reads every row before its own step
+#pragma unroll
+  for (int i = 15; i >= 0; --i) {
+    const int32_t up = __shfl_up_sync(0xffffffffu, a[i], 8);
+    const int32_t wrap = (i & 1) ? __shfl_down_sync(0xffffffffu, a[i - 1], 24) : 0;
+    a[i] -= yin ? up : wrap;
+  }
+#pragma unroll
+  for (int i = 15; i >= 2; --i) a[i] -= a[i - 2];  // the plane below, before its own z step
+}
+
+// Interpolation residual at a non-origin point of a full block: every
+// in-block point is available, and a neighbour at coordinate 8 on the pass
+// axis is the corner anchor when the other two coordinates are 0.
+__device__ __forceinline__ int32_t fb_interp(const BlockView &b, bool cubic, int px, int py, int pz) {
+  int s, a;
+  level_axis(px, py, pz, s, a);
+  const int c = a == 0 ? px : (a == 1 ? py : pz);
+  const bool on_axis = (a == 0 ? (py | pz) : (a == 1 ? (px | pz) : (px | py))) == 0;
+  auto at_c = [&](int cc) -> int32_t {  // 0 <= cc <= 8 along the pass axis
+    if (cc >= 8) return b.cq[1 << a];
+    return b.at(a == 0 ? cc : px, a == 1 ? cc : py, a == 2 ? cc : pz);
+  };
+  const int32_t q = b.at(px, py, pz);
+  const int32_t vm1 = at_c(c - s);          // c - s >= 0 at every level
+  const bool ap1 = c + s < 8 || on_axis;     // c + s <= 8 at every level
+  const int32_t vp1 = ap1 ? at_c(c + s) : 0;
+  if (cubic) {
+    const bool am3 = c - 3 * s >= 0;
+    const bool ap3 = c + 3 * s < 8 || (c + 3 * s == 8 && on_axis);
+    if (am3 && ap1 && ap3) {
+      const int32_t vm3 = at_c(c - 3 * s), vp3 = at_c(c + 3 * s);
+      return q - ((-vm3 + 9 * vm1 + 9 * vp1 - vp3 + 8) >> 4);
+    }
+  }
+  return q - (ap1 ? (vm1 + vp1 + 1) >> 1 : vm1);
+}
+
 __device__ __forceinline__ unsigned long long warp_sum64(unsigned long long v) {
 #pragma unroll
   for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
@@ -159,6 +230,29 @@ __device__ __forceinline__ unsigned long long uabs64(long long v) {
 // Trial costs of the four predictors (every lane gets all four).
 __device__ void block_costs(const BlockView &b, uint32_t R, uint32_t cost[kNPred]) {
   const int lane = threadIdx.x & 31;
+  if (full_block(b)) {
+    int32_t a[16];
+    fb_load(b, a);
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+      fb_lorenzo(a);  // order 1, then order 2
+      uint32_t c = 0;
+#pragma unroll
+      for (int i = 0; i < 16; ++i) c += (i == 0 && lane == 0) ? 0u : trial_bits(a[i], R);
+      cost[k] = (uint32_t)warp_sum64(c);
+    }
+#pragma unroll
+    for (int k = 2; k < kNPred; ++k) {
+      uint32_t c = 0;
+      for (int i = 0; i < 16; ++i) {
+        const int p = 32 * i + lane;
+        if (p == 0) continue;
+        c += trial_bits(fb_interp(b, k == 3, p & 7, (p >> 3) & 7, p >> 6), R);
+      }
+      cost[k] = (uint32_t)warp_sum64(c);
+    }
+    return;
+  }
 #pragma unroll
   for (int k = 0; k < kNPred; ++k) {
     uint32_t c = 0;
@@ -343,7 +437,7 @@ struct SelSmem {
 };
 
 template <int MODE>
-__global__ void __launch_bounds__(kSelThreads) k_selquant(const float *__restrict__ x, Geom g, uint32_t R,
+__global__ void __launch_bounds__(kSelThreads, (MODE == kSelNet || MODE == kSelReport) ? 2 : FZ_SEL_MINB) k_selquant(const float *__restrict__ x, Geom g, uint32_t R,
                                                            uint32_t fixed_pid, CompressWs ws, SelOut so) {
   extern __shared__ __align__(16) unsigned char sel_smem[];
   SelSmem &sm = *reinterpret_cast<SelSmem *>(sel_smem);
@@ -430,13 +524,26 @@ __global__ void __launch_bounds__(kSelThreads) k_selquant(const float *__restric
       if (MODE != kSelReport) {
         if (lane == 0) { ws.ids[blk] = (uint8_t)pid; sm.pid[wb] = pid; }
         uint16_t *cdst = ws.codes + blk * 512;
+        // full blocks: Lorenzo residuals from registers, interpolation without availability tests
+        const bool full = full_block(b);
+        const bool fl = pid <= 1 && full;
+        int32_t ra[16];
+        if (fl) {
+          fb_load(b, ra);
+          fb_lorenzo(ra);
+          if (pid == 1) fb_lorenzo(ra);
+        }
+#pragma unroll
         for (int i = 0; i < 16; ++i) {
           const int p = 32 * i + lane;
           const int px = p & 7, py = (p >> 3) & 7, pz = p >> 6;
           const bool in = b.in(px, py, pz);
           uint32_t code = R;
+          if (!fl) ra[i] = 0;
           if (in) {
-            const int32_t d = residual(b, pid, px, py, pz);
+            const int32_t d = fl ? ra[i]
+                                 : (full && p != 0 ? fb_interp(b, pid == 3, px, py, pz) : residual(b, pid, px, py, pz));
+            ra[i] = d;
             if (p == 0) ws.anchors[blk] = d;
             else {
               const uint32_t c = (uint32_t)(d + (int32_t)R);
@@ -448,6 +555,14 @@ __global__ void __launch_bounds__(kSelThreads) k_selquant(const float *__restric
           }
           cdst[p] = (uint16_t)code;
           atomicAdd(&sm.shist[code], 1u);
+        }
+        // the block's residuals replace its q in the shared tile (only this warp
+        // reads them), for the outlier compaction below
+        __syncwarp();
+#pragma unroll
+        for (int i = 0; i < 16; ++i) {
+          const int p = 32 * i + lane;
+          sm.sq[(((p >> 3) & 7) + 8 * (p >> 6)) * kTXP + 8 * wb + (p & 7)] = ra[i];
         }
       }
     }
@@ -476,7 +591,6 @@ __global__ void __launch_bounds__(kSelThreads) k_selquant(const float *__restric
       uint32_t oo = sm.oslot, eo = sm.eslot;
       for (int w = 0; w < warp; ++w) { oo += sm.wout[w]; eo += sm.wexc[w]; }
       if (bvalid && (nout | nexc)) {
-        const int pid = sm.pid[wb];
         for (int i = 0; i < 16; ++i) {
           const int p = 32 * i + lane;
           const int px = p & 7, py = (p >> 3) & 7, pz = p >> 6;
@@ -485,7 +599,7 @@ __global__ void __launch_bounds__(kSelThreads) k_selquant(const float *__restric
           int32_t d = 0;
           bool outl = false;
           if (in && p != 0) {
-            d = residual(b, pid, px, py, pz);
+            d = b.at(px, py, pz);  // the residual, stored by the code pass
             const uint32_t c = (uint32_t)(d + (int32_t)R);
             outl = (c - 1u) >= 2u * R - 1u;
           }
