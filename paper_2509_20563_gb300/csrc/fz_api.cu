@@ -411,7 +411,7 @@ fz_status fz_decompress(fz_ctx *ctx, const void *d_in, uint64_t in_bytes, const 
   const bool selpath = h.predictor > FZ_PRED_LORENZO2;
   // a per-block first-outlier table pays off when most blocks hold outliers
   const bool ofirst = !selpath && h.n_out > h.n_chunks / 8;
-  const size_t o_err = take(16), o_gsum = take(8 * n_units), o_lut = take(2u << kLutBits),
+  const size_t o_err = take(dec_offset_zero_bytes(h)), o_gsum = take(8 * n_units), o_lut = take(2u << kLutBits),
                o_codes = selpath ? take(2 * g.npad) : 0, o_ofirst = ofirst ? take(4 * h.n_chunks) : 0;
   if ((st = ensure_ws(ctx, off))) return st;
   char *base = reinterpret_cast<char *>(ctx->ws);
@@ -430,8 +430,8 @@ fz_status fz_decompress(fz_ctx *ctx, const void *d_in, uint64_t in_bytes, const 
     }
   } else {
     // unit offsets, then the decoder (which builds its decode table itself)
-    e = cudaMemsetAsync(ws.err, 0, 16, s);
-    if (e == cudaSuccess) { e = launch_decode_offsets(in, h, ws, s); clk.mark("dec_offsets", 2); }
+    e = cudaMemsetAsync(ws.err, 0, dec_offset_zero_bytes(h), s);
+    if (e == cudaSuccess) { e = launch_decode_offsets(in, h, ws, s); clk.mark("dec_offsets", 1); }
     if (e == cudaSuccess && ofirst) { e = launch_outlier_starts(in, h, ws, s, ctx->sm_count); clk.mark("outliers", 1); }
     if (e == cudaSuccess) { e = launch_decode_main(in, h, d_out, ws, s, ctx->sm_count); clk.mark("decode", 1); }
   }

@@ -714,12 +714,73 @@ cudaError_t launch_outlier_starts(const uint8_t *d_in, const fz_header &h, const
   return cudaGetLastError();
 }
 
+namespace {
+constexpr int kOffThreads = 256;  // work units per CTA of k_dec_offsets (one per thread)
+
+// First bit of every work unit in one pass: thread = unit, the unit's bit
+// total from its 32 chunk lengths (128 contiguous bytes), a CTA scan, and a
+// bounded decoupled look-back over the CTAs (all resident: a few dozen
+// CTAs) for the CTA's base.  The status words follow the error word and
+// the work-unit counter; everything starts at zero.
+__global__ void __launch_bounds__(kOffThreads) k_dec_offsets(const uint32_t *__restrict__ chunk_bits,
+                                                             uint64_t n_chunks, uint64_t n_units,
+                                                             uint64_t total_bits, uint64_t *uoff, uint32_t *err) {
+  __shared__ unsigned long long wsum[kOffThreads / 32];
+  __shared__ unsigned long long s_base;
+  const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+  uint64_t *status = reinterpret_cast<uint64_t *>(err + 4);
+  const uint64_t u = (uint64_t)blockIdx.x * kOffThreads + t;
+  unsigned long long v = 0;
+  if (u < n_units) {
+    const uint64_t c0 = u * kDecUnit;
+    if (c0 + kDecUnit <= n_chunks && ((uintptr_t)(chunk_bits + c0) & 15u) == 0) {
+      const uint4 *p = reinterpret_cast<const uint4 *>(chunk_bits + c0);
+#pragma unroll
+      for (int k = 0; k < kDecUnit / 4; ++k) {
+        const uint4 w = __ldg(p + k);
+        v += (unsigned long long)w.x + w.y + w.z + w.w;
+      }
+    } else {
+      for (uint64_t c = c0; c < n_chunks && c < c0 + kDecUnit; ++c) v += __ldg(chunk_bits + c);
+    }
+  }
+  unsigned long long incl = v;
+#pragma unroll
+  for (int off = 1; off < 32; off <<= 1) {
+    const unsigned long long x = __shfl_up_sync(0xffffffffu, incl, off);
+    if (lane >= off) incl += x;
+  }
+  if (lane == 31) wsum[warp] = incl;
+  __syncthreads();
+  unsigned long long wpre = 0, tot = 0;
+#pragma unroll
+  for (int w = 0; w < kOffThreads / 32; ++w) {
+    wpre += w < warp ? wsum[w] : 0ull;
+    tot += wsum[w];
+  }
+  if (warp == 0) {
+    if (lane == 0) lookback_publish(status, blockIdx.x, tot);
+    const unsigned long long base = lookback_resolve_warp(status, blockIdx.x, tot, err);
+    if (lane == 0) {
+      s_base = base;
+      if (blockIdx.x == gridDim.x - 1 && base + tot != total_bits) dec_err(err, FZ_ECORRUPT);
+    }
+  }
+  __syncthreads();
+  if (u < n_units) uoff[u] = s_base + wpre + incl - v;
+}
+}  // namespace
+
+uint64_t dec_offset_zero_bytes(const fz_header &h) {
+  return 16 + 8 * ((dec_units_of(h.n_chunks) + kOffThreads - 1) / kOffThreads);
+}
+
 cudaError_t launch_decode_offsets(const uint8_t *d_in, const fz_header &h, const DecodeWs &ws, cudaStream_t s) {
   const uint64_t n_chunks = h.n_chunks;
   const uint64_t n_units = dec_units_of(n_chunks);
   const uint32_t *cbits = reinterpret_cast<const uint32_t *>(d_in + h.off_chunk_bits);
-  k_dec_gsum<<<(unsigned)((n_units * 32 + 255) / 256), 256, 0, s>>>(cbits, n_chunks, n_units, ws.gsum);
-  k_dec_scan<<<1, kPrepThreads, 0, s>>>(ws.gsum, n_units, h.total_bits, ws.err);
+  const uint64_t grid = (n_units + kOffThreads - 1) / kOffThreads;
+  k_dec_offsets<<<(unsigned)grid, kOffThreads, 0, s>>>(cbits, n_chunks, n_units, h.total_bits, ws.gsum, ws.err);
   return cudaGetLastError();
 }
 

@@ -324,6 +324,9 @@ inline __host__ __device__ uint64_t dec_units_of(uint64_t n_chunks) { return (n_
 cudaError_t launch_decode_prep(const uint8_t *d_in, const fz_header &h, const DecodeWs &ws, cudaStream_t s);
 cudaError_t launch_outlier_starts(const uint8_t *d_in, const fz_header &h, const DecodeWs &ws, cudaStream_t s,
                                   int sm_count);
+// bytes from the error word that launch_decode_offsets needs zeroed (error
+// word, work-unit counter, its look-back status words)
+uint64_t dec_offset_zero_bytes(const fz_header &h);
 // work-unit bit offsets only (the Lorenzo decoder builds its decode table itself)
 cudaError_t launch_decode_offsets(const uint8_t *d_in, const fz_header &h, const DecodeWs &ws, cudaStream_t s);
 cudaError_t launch_decode_main(const uint8_t *d_in, const fz_header &h, float *d_out, const DecodeWs &ws,

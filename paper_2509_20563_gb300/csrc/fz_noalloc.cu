@@ -30,7 +30,7 @@
 namespace fz {
 namespace {
 
-constexpr size_t kNaErrBytes = 256;                                      // error word + unit counter, padded
+constexpr size_t kNaErrBytes = 256;  // error word, unit counter, look-back words of the offset pass (<= 30 CTAs)
 constexpr size_t kNaUnitBytes = 8 * (FZ_NOALLOC_MAX_CHUNKS / kDecUnit);  // per-unit bit offsets
 constexpr size_t kNaScratchBytes = kNaErrBytes + kNaUnitBytes;
 
@@ -112,7 +112,8 @@ fz_status fz_decompress_noalloc(const void *d_in, uint64_t in_bytes, const void 
   ws.err = reinterpret_cast<uint32_t *>(b);
   ws.lut = nullptr;
   ws.gsum = reinterpret_cast<uint64_t *>(b + kNaErrBytes);
-  e = cudaMemsetAsync(ws.err, 0, 16, s);  // error word and work-unit counter start at zero
+  // error word, work-unit counter and the offset pass's look-back words start at zero
+  e = cudaMemsetAsync(ws.err, 0, dec_offset_zero_bytes(h), s);
   if (e == cudaSuccess) e = launch_decode_offsets(in, h, ws, s);
   if (e == cudaSuccess) e = launch_decode_main(in, h, d_out, ws, s, sms);
   uint32_t err = 0;

@@ -445,6 +445,7 @@ __global__ void __launch_bounds__(kSelThreads, (MODE == kSelNet || MODE == kSelR
   if (ctl->mode != kModeNormal) return;
   const float inv2eb = ctl->inv2eb, ebx2 = ctl->ebx2, eb_chk = ctl->eb_chk;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const bool vec_ok = ((g.nx & 3u) == 0) && (((uintptr_t)x & 15u) == 0);
   for (int s = tid; s < kMaxSym; s += kSelThreads) sm.shist[s] = 0;
   if (MODE == kSelNet)
     for (int i = tid; i < kNWeights; i += kSelThreads) sm.w[i] = bf16_to_f32(so.weights[i]);
@@ -463,12 +464,20 @@ __global__ void __launch_bounds__(kSelThreads, (MODE == kSelNet || MODE == kSelR
       const uint32_t X = x0 + col, Y = y0 + (row & 7), Z = z0 + (row >> 3);
       const bool inrow = Y < g.ny && Z < g.nz;
       const uint64_t fi = ((uint64_t)Z * g.ny + Y) * g.nx + X;
+      float xv[4];
+      if (inrow && vec_ok && X + 4 <= g.nx) {
+        const float4 f4 = __ldcs(reinterpret_cast<const float4 *>(x + fi));
+        xv[0] = f4.x; xv[1] = f4.y; xv[2] = f4.z; xv[3] = f4.w;
+      } else {
+#pragma unroll
+        for (int u = 0; u < 4; ++u) xv[u] = (inrow && X + u < g.nx) ? x[fi + u] : 0.0f;
+      }
       uint32_t ex = 0;
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
         const bool in = inrow && X + u < g.nx;
         bool ee = false;
-        const int32_t q = in ? prequant(x[fi + u], inv2eb, ebx2, eb_chk, ee) : 0;
+        const int32_t q = in ? prequant(xv[u], inv2eb, ebx2, eb_chk, ee) : 0;
         sm.sq[row * kTXP + col + u] = q;
         ex |= (uint32_t)(in && ee) << (8 * u);
       }
