@@ -5,15 +5,18 @@
 // codes) from a ticket counter, one warp per chunk.  Each lane owns a
 // contiguous run of codes: it sums their codeword lengths, the warp scans
 // the lane totals (the chunk's bit length, stored in the stream) and the CTA
-// scans the chunk totals.  The tile publishes its bit total for the bounded
-// decoupled look-back right away, then packs its codewords MSB-first into a
-// shared-memory image of the tile aligned to bit 0, appends the first 32
-// bits of the next tile (encoded from that tile's first codes), and only
-// then resolves its global bit offset -- by which time its predecessors have
-// usually published theirs.  The image is written out with a funnel shift by
-// the offset's low 5 bits; the CTA stores exactly the words whose first bit
-// lies in its tile, so every word is written once, by plain coalesced
-// stores, and the output needs no zeroing.
+// sums the chunk totals.  The tile publishes its bit total for a bounded
+// decoupled look-back right away, then packs its codewords (two at a time)
+// MSB-first into a shared-memory image of the tile aligned to bit 0 and
+// appends the first 32 bits of the next tile (encoded from that tile's first
+// codes).  A single field's CTAs keep two tiles in flight (k_encode_pipe):
+// the tile packed in one step resolves its global bit offset and is stored
+// in the next, so its predecessors have had a whole step to publish.  The
+// image is written out with a funnel shift by the offset's low 5 bits; the
+// CTA stores exactly the words whose first bit lies in its tile, so every
+// word is written once, by plain coalesced stores, and the output needs no
+// zeroing.  Batches (k_encode_batch) run one tile per step through
+// encode_tile, which lets a CTA switch fields between tiles.
 // HBM traffic: 2 bytes read per code plus the bitstream.
 #include "fz_internal.cuh"
 
@@ -161,23 +164,6 @@ __device__ __forceinline__ void encode_tile(const CompressWs &ws, uint8_t *d_out
   }
 }
 
-template <int CH>
-__global__ void __launch_bounds__(kEncThreads) k_encode(Geom g, CompressWs ws, uint8_t *d_out) {
-  __shared__ EncSmem<CH> sm;
-  Ctl *ctl = ws.ctl;
-  if (ctl->mode != kModeNormal) return;
-  const int tid = threadIdx.x;
-  const uint64_t n_tiles = (g.n_blocks + kEncWarps - 1) / kEncWarps;
-  for (int s = tid; s < kMaxSym; s += kEncThreads) sm.senc[s] = ctl->enc[s];
-  for (;;) {
-    if (tid == 0) sm.tile = atomicAdd(&ctl->encode_ticket, 1u);
-    __syncthreads();
-    const uint64_t tile = sm.tile;
-    if (tile >= n_tiles) break;
-    encode_tile<CH>(ws, d_out, g.n_blocks, tile, sm);
-  }
-}
-
 // Batched variant: the encode tiles of every field of one chunk-size class
 // form one ticket queue, in field order, so a field's tiles are claimed in
 // order and its look-back always ends.  The codeword table is reloaded when
@@ -224,16 +210,174 @@ __global__ void __launch_bounds__(kEncThreads) k_encode_batch(const BatchJob *__
   }
 }
 
+// Single field, two tiles in flight per CTA: in each step the CTA counts,
+// publishes and packs its newest tile, then resolves the look-back and
+// stores the tile packed one step earlier, whose predecessors have had a
+// whole step to publish their prefixes.  Two images alternate.
+template <int CH>
+struct PipeSmem {
+  static constexpr int kMaxWords = EncSmem<CH>::kMaxWords;
+  uint32_t senc[kMaxSym];
+  __align__(16) uint32_t lw[2][kMaxWords];
+  uint32_t wtot[kEncWarps], woff[kEncWarps];
+  uint32_t tile, tbits;
+  unsigned long long base;
+};
+
+template <int CH>
+__global__ void __launch_bounds__(kEncThreads) k_encode_pipe(Geom g, CompressWs ws, uint8_t *d_out) {
+  constexpr int PER = CH / 32;
+  __shared__ PipeSmem<CH> sm;
+  Ctl *ctl = ws.ctl;
+  if (ctl->mode != kModeNormal) return;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const fz_header &h = ctl->res.hdr;
+  uint32_t *chunk_bits = reinterpret_cast<uint32_t *>(d_out + h.off_chunk_bits);
+  uint32_t *words = reinterpret_cast<uint32_t *>(d_out + h.off_bits);
+  const uint64_t n_chunks = g.n_blocks;
+  const uint64_t n_tiles = (n_chunks + kEncWarps - 1) / kEncWarps;
+  const uint64_t wlimit = (ctl->total_bits + 31) / 32;
+  for (int i = tid; i < kMaxSym; i += kEncThreads) sm.senc[i] = ctl->enc[i];
+  for (int i = tid; i < 2 * PipeSmem<CH>::kMaxWords; i += kEncThreads) (&sm.lw[0][0])[i] = 0;
+  if (tid == 0) sm.tile = atomicAdd(&ctl->encode_ticket, 1u);
+  __syncthreads();
+  uint64_t prev = ~0ull;
+  uint32_t prev_bits = 0;
+  int cb = 0;
+  for (;;) {
+    const uint64_t tile = sm.tile;  // written before the last barrier
+    const bool have = tile < n_tiles;
+    uint32_t tbits = 0;
+    if (have) {
+      uint32_t *lw = sm.lw[cb];
+      // ---- count and publish
+      const uint64_t chunk = tile * kEncWarps + warp;
+      const bool valid = chunk < n_chunks;
+      uint32_t cw[PER];
+      uint32_t lbits = 0;
+      if (valid) {
+        const uint4 *src = reinterpret_cast<const uint4 *>(ws.codes + chunk * CH + lane * PER);
+#pragma unroll
+        for (int v = 0; v < PER / 8; ++v) {
+          const uint4 u = __ldcs(src + v);
+          const uint32_t w4[4] = {u.x, u.y, u.z, u.w};
+#pragma unroll
+          for (int k = 0; k < 4; ++k) {
+            cw[8 * v + 2 * k] = sm.senc[w4[k] & 0xffffu];
+            cw[8 * v + 2 * k + 1] = sm.senc[w4[k] >> 16];
+          }
+        }
+#pragma unroll
+        for (int k = 0; k < PER; ++k) lbits += cw[k] >> 24;
+      } else {
+#pragma unroll
+        for (int k = 0; k < PER; ++k) cw[k] = 0;
+      }
+      uint32_t incl = lbits;
+#pragma unroll
+      for (int off = 1; off < 32; off <<= 1) {
+        const uint32_t v = __shfl_up_sync(0xffffffffu, incl, off);
+        if (lane >= off) incl += v;
+      }
+      if (lane == 31) {
+        sm.wtot[warp] = incl;
+        if (valid) chunk_bits[chunk] = incl;
+      }
+      __syncthreads();
+      uint32_t woff = 0;
+#pragma unroll
+      for (int w = 0; w < kEncWarps; ++w) {
+        const uint32_t t = sm.wtot[w];
+        woff += w < warp ? t : 0u;
+        tbits += t;
+      }
+      if (tid == 0) lookback_publish(ws.estatus, tile, tbits);
+      // ---- pack MSB-first at the tile-local bit offset, codewords in pairs
+      if (valid) {
+        const uint32_t rb = woff + incl - lbits;
+        uint32_t wi = rb >> 5;
+        int cnt = (int)(rb & 31u);
+        unsigned long long acc = 0;
+#pragma unroll
+        for (int k = 0; k < PER; k += 2) {
+          const uint32_t L1 = cw[k + 1] >> 24;
+          const uint32_t v = ((cw[k] & 0xffffffu) << L1) | (cw[k + 1] & 0xffffffu);
+          const int n = (int)((cw[k] >> 24) + L1);
+          acc |= (unsigned long long)v << (64 - cnt - n);
+          cnt += n;
+          if (cnt >= 32) {
+            atomicOr(&lw[wi], (uint32_t)(acc >> 32));
+            ++wi;
+            acc <<= 32;
+            cnt -= 32;
+          }
+        }
+        if (cnt > 0) atomicOr(&lw[wi], (uint32_t)(acc >> 32));
+      }
+      // ---- first 32 bits of the next tile, right after this tile's bits
+      if (warp == kEncWarps - 1 && tile + 1 < n_tiles) {
+        const uint32_t e = sm.senc[ws.codes[(tile + 1) * kEncWarps * (uint64_t)CH + lane]];
+        const uint32_t L = e >> 24, c = e & 0xffffffu;
+        uint32_t p = L;
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+          const uint32_t v = __shfl_up_sync(0xffffffffu, p, off);
+          if (lane >= off) p += v;
+        }
+        p -= L;
+        const uint32_t contrib = p < 32 ? (uint32_t)(((unsigned long long)c << (64 - p - L)) >> 32) : 0u;
+        const uint32_t head = __reduce_or_sync(0xffffffffu, contrib);
+        if (lane == 0) {
+          const uint32_t r = tbits & 31u, w0 = tbits >> 5;
+          atomicOr(&lw[w0], head >> r);
+          if (r) atomicOr(&lw[w0 + 1], head << (32 - r));
+        }
+      }
+    }
+    // ---- the previous tile: its base by look-back, then its words
+    if (prev != ~0ull && warp == 0) {
+      const unsigned long long base = lookback_resolve_warp(ws.estatus, prev, prev_bits, &ctl->res.err);
+      if (lane == 0) {
+        sm.base = base;
+        if (prev == n_tiles - 1 && base + prev_bits != ctl->total_bits) set_err(ctl, FZ_ECORRUPT);
+      }
+    }
+    if (tid == 0 && have) sm.tile = atomicAdd(&ctl->encode_ticket, 1u);
+    __syncthreads();  // packing, head, base and the next ticket are visible
+    if (prev != ~0ull) {
+      const uint32_t *plw = sm.lw[cb ^ 1];
+      const unsigned long long base = sm.base;
+      const uint32_t r = (uint32_t)(base & 31u);
+      const uint64_t gw0 = base >> 5;
+      const uint32_t jmax = (uint32_t)(((base + prev_bits - 1) >> 5) - gw0);
+      if (tid == 0 && gw0 + jmax >= wlimit) set_err(ctl, FZ_ECORRUPT);
+      for (uint32_t j = (r ? 1u : 0u) + tid; j <= jmax; j += kEncThreads) {
+        const uint32_t v = r ? ((plw[j - 1] << (32 - r)) | (plw[j] >> r)) : plw[j];
+        if (gw0 + j < wlimit) words[gw0 + j] = v;
+      }
+      __syncthreads();  // every word of the previous image has been read
+      uint32_t *z = sm.lw[cb ^ 1];
+      const uint32_t nz = (prev_bits + 32 + 31) / 32 + 1;
+      for (uint32_t w = tid; w < nz; w += kEncThreads) z[w] = 0;
+    }
+    if (!have) break;
+    prev = tile;
+    prev_bits = tbits;
+    cb ^= 1;
+    __syncthreads();  // the cleared image is ready for the next tile
+  }
+}
+
 template <int CH>
 cudaError_t launch_t(const Geom &g, const CompressWs &ws, uint8_t *d_out, cudaStream_t s, int sms) {
   int per_sm = 0;
-  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_encode<CH>, kEncThreads, 0);
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_encode_pipe<CH>, kEncThreads, 0);
   if (e != cudaSuccess) return e;
   if (per_sm < 1) per_sm = 1;
   const uint64_t n_tiles = (g.n_blocks + kEncWarps - 1) / kEncWarps;
   uint64_t grid = (uint64_t)sms * per_sm;
   if (grid > n_tiles) grid = n_tiles;
-  k_encode<CH><<<(unsigned)grid, kEncThreads, 0, s>>>(g, ws, d_out);
+  k_encode_pipe<CH><<<(unsigned)grid, kEncThreads, 0, s>>>(g, ws, d_out);
   return cudaGetLastError();
 }
 
