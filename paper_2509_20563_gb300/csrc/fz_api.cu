@@ -103,6 +103,8 @@ size_t layout_compress_split(const Geom &g, char *zbase, char *rbase, CompressWs
   ws.exc_val = reinterpret_cast<uint32_t *>(rtake(4 * cap));
   ws.ids = reinterpret_cast<uint8_t *>(rtake(g.n_blocks));
   ws.tdst = reinterpret_cast<uint2 *>(rtake(8 * g.n_qtiles));
+  ws.winfo = reinterpret_cast<WarpSlots *>(rtake(sizeof(WarpSlots) * 8 * g.n_qtiles));
+  ws.otiles = reinterpret_cast<uint32_t *>(rtake(4 * g.n_qtiles));
   if (rest_bytes) *rest_bytes = ro;
   return zo;
 }

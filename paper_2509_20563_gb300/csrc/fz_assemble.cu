@@ -148,7 +148,11 @@ __device__ __forceinline__ void assemble_body(const float *__restrict__ x, const
     unsigned long long o = ob + excl.x, e = eb + excl.y;
 #pragma unroll
     for (int k = 0; k < kTilesPerThread; ++k) {
-      if (t0 + k < g.n_qtiles) ws.tdst[t0 + k] = make_uint2((uint32_t)o, (uint32_t)e);
+      if (t0 + k < g.n_qtiles) {
+        ws.tdst[t0 + k] = make_uint2((uint32_t)o, (uint32_t)e);
+        if (cnt[k].x | cnt[k].y)  // list the tile for the gather
+          ws.otiles[atomicAdd(&const_cast<Ctl *>(ctl)->n_otiles, 1u)] = (uint32_t)(t0 + k);
+      }
       o += cnt[k].x;
       e += cnt[k].y;
     }
@@ -172,17 +176,66 @@ __device__ __forceinline__ void gather_body(const Geom &g, const CompressWs &ws,
   uint32_t *eidx = reinterpret_cast<uint32_t *>(d_out + h.off_exc_idx);
   uint32_t *eval = reinterpret_cast<uint32_t *>(d_out + h.off_exc_val);
   const int lane = threadIdx.x & 31;
-  for (uint64_t tile = w; tile < g.n_qtiles; tile += nw) {
-    const uint4 ti = ws.tinfo[tile];
-    if ((ti.x | ti.y) == 0) continue;
-    const uint2 dst = ws.tdst[tile];
-    for (uint32_t i = lane; i < ti.x; i += 32) {
-      const uint64_t src = (uint64_t)ti.z + i, o = (uint64_t)dst.x + i;
-      if (src < ws.cap_list && o < n_out) { oidx[o] = ws.out_idx[src]; oval[o] = ws.out_val[src]; }
+  // the 3D Lorenzo quantizer files 8 slices per warp (one per block, by
+  // block then warp); the other quantizers one slice per warp
+  const bool by_block = g.ndim == 3 && h.predictor <= FZ_PRED_LORENZO2;
+  auto copy = [&](uint64_t so, uint64_t se, uint32_t no, uint32_t ne, uint64_t o, uint64_t e) {
+    for (uint32_t i = lane; i < no; i += 32) {
+      const uint64_t src = so + i;
+      if (src < ws.cap_list && o + i < n_out) { oidx[o + i] = ws.out_idx[src]; oval[o + i] = ws.out_val[src]; }
     }
-    for (uint32_t i = lane; i < ti.y; i += 32) {
-      const uint64_t src = (uint64_t)ti.w + i, e = (uint64_t)dst.y + i;
-      if (src < ws.cap_list && e < n_exc) { eidx[e] = ws.exc_idx[src]; eval[e] = ws.exc_val[src]; }
+    for (uint32_t i = lane; i < ne; i += 32) {
+      const uint64_t src = se + i;
+      if (src < ws.cap_list && e + i < n_exc) { eidx[e + i] = ws.exc_idx[src]; eval[e + i] = ws.exc_val[src]; }
+    }
+  };
+  if (by_block) {
+    // a warp per (tile, block): the block's 8 slices (one per warp of the
+    // quantizer) follow the earlier blocks' slices of the tile
+    auto bytesum = [](unsigned long long v) -> uint32_t {
+      return (uint32_t)__dp4a((uint32_t)v, 0x01010101u, 0u) + (uint32_t)__dp4a((uint32_t)(v >> 32), 0x01010101u, 0u);
+    };
+    const uint64_t n_list = ctl->n_otiles;
+    for (uint64_t item = w; item < n_list * 8; item += nw) {
+      const uint64_t tile = ws.otiles[item >> 3];
+      const int b = (int)(item & 7);
+      const uint2 dst = ws.tdst[tile];
+      const unsigned long long below = b ? (1ull << (8 * b)) - 1 : 0ull;
+      uint32_t no = 0, ne = 0, so = 0, se = 0, po = 0, pe = 0;
+      if (lane < 8) {
+        const WarpSlots wsl = ws.winfo[tile * 8 + lane];
+        no = (uint32_t)(wsl.ocnt >> (8 * b)) & 255u;
+        ne = (uint32_t)(wsl.ecnt >> (8 * b)) & 255u;
+        po = bytesum(wsl.ocnt & below);
+        pe = bytesum(wsl.ecnt & below);
+        so = wsl.oslot + po;
+        se = wsl.eslot + pe;
+      }
+      const uint32_t bo = __reduce_add_sync(0xffffffffu, po), be = __reduce_add_sync(0xffffffffu, pe);
+      uint64_t o = (uint64_t)dst.x + bo, e = (uint64_t)dst.y + be;
+      for (int k = 0; k < 8; ++k) {
+        const uint32_t nk = __shfl_sync(0xffffffffu, no, k), ek = __shfl_sync(0xffffffffu, ne, k);
+        const uint32_t sk = __shfl_sync(0xffffffffu, so, k), tk = __shfl_sync(0xffffffffu, se, k);
+        if (nk | ek) copy(sk, tk, nk, ek, o, e);
+        o += nk;
+        e += ek;
+      }
+    }
+    return;
+  }
+  const uint64_t n_list = ctl->n_otiles;
+  for (uint64_t item = w; item < n_list; item += nw) {
+    const uint64_t tile = ws.otiles[item];
+    const uint2 dst = ws.tdst[tile];
+    uint64_t o = dst.x, e = dst.y;
+    const WarpSlots *wsl = ws.winfo + tile * 8;
+    {
+      for (int k = 0; k < 8; ++k) {
+        const uint32_t no = (uint32_t)(wsl[k].ocnt & 0xffffu), ne = (uint32_t)(wsl[k].ecnt & 0xffffu);
+        if (no | ne) copy(wsl[k].oslot, wsl[k].eslot, no, ne, o, e);
+        o += no;
+        e += ne;
+      }
     }
   }
 }
@@ -243,7 +296,7 @@ cudaError_t launch_assemble(const float *x, const Geom &g, uint32_t R, const Com
   if (grid < n_tg) grid = n_tg < (uint64_t)sm_count * 8 ? n_tg : (uint64_t)sm_count * 8;
   if (grid < 2) grid = 2;
   k_assemble<<<(unsigned)grid, kAsmThreads, 0, s>>>(x, g, R, ws, d_out);
-  uint64_t ggrid = (g.n_qtiles + kAsmThreads / 32 - 1) / (kAsmThreads / 32);
+  uint64_t ggrid = (8 * g.n_qtiles + kAsmThreads / 32 - 1) / (kAsmThreads / 32);
   if (ggrid > (uint64_t)sm_count * 8) ggrid = (uint64_t)sm_count * 8;
   k_gather<<<(unsigned)ggrid, kAsmThreads, 0, s>>>(g, ws, d_out);
   return cudaGetLastError();

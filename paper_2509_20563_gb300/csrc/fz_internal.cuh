@@ -72,7 +72,7 @@ struct Ctl {
   // REL range: max of inverted ordered keys for the minimum, max of ordered
   // keys for the maximum, and the same on raw bit patterns.
   unsigned int lo_nkey, hi_key, bits_nmin, bits_max, any_finite, range_done;
-  unsigned int encode_ticket, pad_t;
+  unsigned int encode_ticket, n_otiles;  // encoder tickets; quantization tiles holding outliers/exceptions
   unsigned long long n_out, n_exc;   // totals; also the append cursors of the scratch lists
   // constants (written by the range tail or the ABS constants kernel)
   double eb_abs;
@@ -246,6 +246,17 @@ __device__ __forceinline__ uint16_t f32_to_bf16_rne(float f) {
 }
 __device__ __forceinline__ float bf16_to_f32(uint16_t h) { return __uint_as_float((uint32_t)h << 16); }
 
+// Outliers and exceptions one warp of a quantization tile appended to the
+// scratch lists: the first slots and the counts per slice.  The 3D Lorenzo
+// quantizer's warp holds one z-plane of the tile's 8 blocks: 8 slices (one
+// per block, a count per byte).  Otherwise the warp's positions form one
+// slice (count in the low 16 bits).  Slices go to the stream in code order:
+// 3D Lorenzo by block then warp, otherwise by warp.
+struct WarpSlots {
+  uint32_t oslot, eslot;
+  unsigned long long ocnt, ecnt;
+};
+
 // ---------------------------------------------------------------- workspace layout
 // Device scratch owned by the context for one compress call.
 struct CompressWs {
@@ -253,6 +264,8 @@ struct CompressWs {
   uint4 *tinfo;            // per quantization tile: n_out, n_exc, first outlier slot, first exception slot
   uint2 *tgroup;           // per group of kTileGroup tiles: outlier and exception counts
   uint2 *tdst;             // per quantization tile: its first outlier and exception slot in the stream
+  struct WarpSlots *winfo; // per quantization tile and warp: where its outliers/exceptions went (8 per tile)
+  uint32_t *otiles;        // the tiles that hold outliers or exceptions (Ctl::n_otiles of them), any order
   uint64_t *estatus;       // look-back status per encode tile
   size_t zero_bytes;       // bytes from ctl to the end of estatus (memset per call)
   uint16_t *codes;         // npad block-major codes

@@ -128,8 +128,6 @@ struct QuantSmem {
   int32_t sq[2][TileShape<NDIM>::ROWS * TXP];  // double-buffered q (1D/2D) or x/y-differenced q (3D)
   uint8_t sexc[2][kTileElems];                 // exception flags, tile row-major
   uint32_t shist[kMaxSym];
-  uint32_t wout[8], wexc[8];
-  uint32_t oslot, eslot;  // this tile's first entries in the scratch lists
 };
 
 // Residual at (row, col) of the shared tile for the ordered-compaction pass
@@ -362,76 +360,92 @@ __device__ __forceinline__ void quant_tiles(const float *__restrict__ x, const G
       else tile_codes12<NDIM, K, false>(g, t, qc, ws, sq, sexc, sm.shist, nout, nexc);
     }
 
-    // ---- outliers / exceptions of this tile (rare): ordered compaction
+    // ---- outliers / exceptions (rare): each warp compacts its own positions
+    // in code order, without waiting for the other warps -- 3D: its z-plane of
+    // each of the tile's blocks, 1D/2D: its half block.  The shared tiles are
+    // double-buffered, so the values read here stay put until the next-but-one
+    // tile, which starts after the next tile's barrier.
     nout = __reduce_add_sync(0xffffffffu, nout);
     nexc = __reduce_add_sync(0xffffffffu, nexc);
-    if (lane == 0) { sm.wout[warp] = nout; sm.wexc[warp] = nexc; }
-    if (__syncthreads_or((nout | nexc) != 0)) {
-      if (tid == 0) {
-        uint32_t to = 0, te = 0;
-        for (int w = 0; w < 8; ++w) { to += sm.wout[w]; te += sm.wexc[w]; }
-        const unsigned long long os = to ? atomicAdd(&ctl->n_out, (unsigned long long)to) : 0ull;
-        const unsigned long long es = te ? atomicAdd(&ctl->n_exc, (unsigned long long)te) : 0ull;
-        ws.tinfo[tile] = make_uint4(to, te, (uint32_t)os, (uint32_t)es);
+    WarpSlots wsl;
+    wsl.oslot = 0;
+    wsl.eslot = 0;
+    wsl.ocnt = 0;
+    wsl.ecnt = 0;
+    if ((nout | nexc) != 0) {
+      if (lane == 0) {
+        wsl.oslot = nout ? (uint32_t)atomicAdd(&ctl->n_out, (unsigned long long)nout) : 0u;
+        wsl.eslot = nexc ? (uint32_t)atomicAdd(&ctl->n_exc, (unsigned long long)nexc) : 0u;
+        if (nout) atomicAdd(&ws.tinfo[tile].x, nout);
+        if (nexc) atomicAdd(&ws.tinfo[tile].y, nexc);
         const uint64_t grp = tile / kTileGroup;
-        if (to) atomicAdd(&ws.tgroup[grp].x, to);
-        if (te) atomicAdd(&ws.tgroup[grp].y, te);
-        sm.oslot = (uint32_t)os;
-        sm.eslot = (uint32_t)es;
+        if (nout) atomicAdd(&ws.tgroup[grp].x, nout);
+        if (nexc) atomicAdd(&ws.tgroup[grp].y, nexc);
       }
-      __syncthreads();
-      // Each warp walks one block in code order (3D: warp = block; 1D/2D:
-      // warp = half block) and appends its entries after the earlier warps'.
-      const int wb = warp / S::WPB, seg = warp % S::WPB;
-      const uint32_t bxi = t.tx * S::NB + wb;
-      const bool bvalid = bxi < g.nbx;
-      const uint64_t blk = (uint64_t)bxi + (uint64_t)g.nbx * (t.by + (uint64_t)g.nby * t.bz);
-      uint32_t co = 0, ce = 0;
-      if (bvalid) {
-        for (int i = 0; i < kIter; ++i) {
-          const int p = seg * kPerWarp + 32 * i + lane;
-          const int px = p % S::BX, py = (p / S::BX) % S::BY, pz = p / (S::BX * S::BY);
-          const int row = py + S::BY * pz, col = wb * S::BX + px;
-          const bool in = (t.x0 + col < g.nx) && (t.y0 + py < g.ny) && (t.z0 + pz < g.nz);
-          const int32_t d = smem_residual<NDIM, K>(sq, row, col, px, py, pz);
-          bool outl;
-          make_code(d, qc.R, in, p == 0, outl);
-          co += __popc(__ballot_sync(0xffffffffu, outl));
-          ce += __popc(__ballot_sync(0xffffffffu, in && sexc[row * S::TX + col]));
+      wsl.oslot = __shfl_sync(0xffffffffu, wsl.oslot, 0);
+      wsl.eslot = __shfl_sync(0xffffffffu, wsl.eslot, 0);
+      uint32_t oo = wsl.oslot, eo = wsl.eslot;
+      // append the outliers and exceptions of `n` positions (code order = lane order per step)
+      auto emit = [&](bool outl, int32_t d, bool e, uint32_t pos, uint64_t fi, uint32_t &co, uint32_t &ce) {
+        uint32_t m = __ballot_sync(0xffffffffu, outl);
+        if (outl) {
+          const uint64_t o = (uint64_t)oo + __popc(m & ((1u << lane) - 1));
+          if (o < ws.cap_list) { ws.out_idx[o] = pos; ws.out_val[o] = d; }
         }
-      }
-      __syncthreads();
-      if (lane == 0) { sm.wout[warp] = co; sm.wexc[warp] = ce; }
-      __syncthreads();
-      uint32_t oo = sm.oslot, eo = sm.eslot;
-      for (int w = 0; w < warp; ++w) { oo += sm.wout[w]; eo += sm.wexc[w]; }
-      if (bvalid && (co | ce)) {
-        for (int i = 0; i < kIter; ++i) {
-          const int p = seg * kPerWarp + 32 * i + lane;
-          const int px = p % S::BX, py = (p / S::BX) % S::BY, pz = p / (S::BX * S::BY);
-          const int row = py + S::BY * pz, col = wb * S::BX + px;
-          const bool in = (t.x0 + col < g.nx) && (t.y0 + py < g.ny) && (t.z0 + pz < g.nz);
-          const uint32_t pos = (uint32_t)(blk * g.bsize + p);
-          const int32_t d = smem_residual<NDIM, K>(sq, row, col, px, py, pz);
-          bool outl;
-          make_code(d, qc.R, in, p == 0, outl);
-          uint32_t m = __ballot_sync(0xffffffffu, outl);
-          if (outl) {
-            const uint64_t o = (uint64_t)oo + __popc(m & ((1u << lane) - 1));
-            if (o < ws.cap_list) { ws.out_idx[o] = pos; ws.out_val[o] = d; }
-          }
-          oo += __popc(m);
-          const bool e = in && sexc[row * S::TX + col];
-          m = __ballot_sync(0xffffffffu, e);
-          if (e) {
-            const uint64_t o = (uint64_t)eo + __popc(m & ((1u << lane) - 1));
+        oo += __popc(m);
+        co += __popc(m);
+        m = __ballot_sync(0xffffffffu, e);
+        if (e) {
+          const uint64_t o = (uint64_t)eo + __popc(m & ((1u << lane) - 1));
+          if (o < ws.cap_list) { ws.exc_idx[o] = pos; ws.exc_val[o] = __float_as_uint(x[fi]); }
+        }
+        eo += __popc(m);
+        ce += __popc(m);
+      };
+      if (NDIM == 3) {
+        const int pz = warp;
+        for (int b = 0; b < S::NB; ++b) {
+          const uint32_t bxi = t.tx * S::NB + b;
+          if (bxi >= g.nbx) break;
+          const uint64_t blk = (uint64_t)bxi + (uint64_t)g.nbx * (t.by + (uint64_t)g.nby * t.bz);
+          uint32_t co = 0, ce = 0;
+#pragma unroll
+          for (int half = 0; half < 2; ++half) {
+            const int idx = 32 * half + lane, px = idx & 7, py = idx >> 3;
+            const int row = py + 8 * pz, col = 8 * b + px;
+            const bool in = (t.x0 + col < g.nx) && (t.y0 + py < g.ny) && (t.z0 + pz < g.nz);
+            const int32_t d = smem_residual<3, K>(sq, row, col, px, py, pz);
+            bool outl;
+            make_code(d, qc.R, in, idx == 0 && pz == 0, outl);
             const uint64_t fi = ((uint64_t)(t.z0 + pz) * g.ny + (t.y0 + py)) * g.nx + (t.x0 + col);
-            if (o < ws.cap_list) { ws.exc_idx[o] = pos; ws.exc_val[o] = __float_as_uint(x[fi]); }
+            emit(outl, d, in && sexc[row * S::TX + col], (uint32_t)(blk * 512 + 64 * pz + idx), fi, co, ce);
           }
-          eo += __popc(m);
+          wsl.ocnt |= (unsigned long long)co << (8 * b);
+          wsl.ecnt |= (unsigned long long)ce << (8 * b);
         }
+      } else {
+        const int wb = warp / S::WPB, seg = warp % S::WPB;
+        const uint32_t bxi = t.tx * S::NB + wb;
+        const uint64_t blk = (uint64_t)bxi + (uint64_t)g.nbx * (t.by + (uint64_t)g.nby * t.bz);
+        uint32_t co = 0, ce = 0;
+        if (bxi < g.nbx) {
+          for (int i = 0; i < kIter; ++i) {
+            const int p = seg * kPerWarp + 32 * i + lane;
+            const int px = p % S::BX, py = (p / S::BX) % S::BY;
+            const int row = py, col = wb * S::BX + px;
+            const bool in = (t.x0 + col < g.nx) && (t.y0 + py < g.ny);
+            const int32_t d = smem_residual<NDIM, K>(sq, row, col, px, py, 0);
+            bool outl;
+            make_code(d, qc.R, in, p == 0, outl);
+            const uint64_t fi = (uint64_t)(t.y0 + py) * g.nx + (t.x0 + col);
+            emit(outl, d, in && sexc[row * S::TX + col], (uint32_t)(blk * g.bsize + p), fi, co, ce);
+          }
+        }
+        wsl.ocnt = co;
+        wsl.ecnt = ce;
       }
     }
+    if (lane == 0) ws.winfo[tile * 8 + warp] = wsl;
   }
   __syncthreads();
   for (int s = tid; s < (int)nsym; s += kQuantThreads)

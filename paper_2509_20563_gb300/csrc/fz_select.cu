@@ -599,6 +599,14 @@ __global__ void __launch_bounds__(kSelThreads, (MODE == kSelNet || MODE == kSelR
       __syncthreads();
       uint32_t oo = sm.oslot, eo = sm.eslot;
       for (int w = 0; w < warp; ++w) { oo += sm.wout[w]; eo += sm.wexc[w]; }
+      if (lane == 0) {  // one slice per warp (= block), in warp order
+        WarpSlots wsl;
+        wsl.oslot = oo;
+        wsl.eslot = eo;
+        wsl.ocnt = sm.wout[warp];
+        wsl.ecnt = sm.wexc[warp];
+        ws.winfo[tile * 8 + warp] = wsl;
+      }
       if (bvalid && (nout | nexc)) {
         for (int i = 0; i < 16; ++i) {
           const int p = 32 * i + lane;
