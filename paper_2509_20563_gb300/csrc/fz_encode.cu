@@ -11,7 +11,9 @@
 // appends the first 32 bits of the next tile (encoded from that tile's first
 // codes).  A single field's CTAs keep two tiles in flight (k_encode_pipe):
 // the tile packed in one step resolves its global bit offset and is stored
-// in the next, so its predecessors have had a whole step to publish.  The
+// in the next, so its predecessors have had a whole step to publish; the
+// codes of a CTA's next tile are loaded into registers during the step
+// before (its ticket is taken a step ahead).  The
 // image is written out with a funnel shift by the offset's low 5 bits; the
 // CTA stores exactly the words whose first bit lies in its tile, so every
 // word is written once, by plain coalesced stores, and the output needs no
@@ -25,6 +27,10 @@ namespace fz {
 namespace {
 
 constexpr int kEncThreads = kEncWarps * 32;
+
+#ifndef FZ_ENC_MINB
+#define FZ_ENC_MINB 6
+#endif
 
 template <int CH>
 struct EncSmem {
@@ -219,13 +225,22 @@ struct PipeSmem {
   static constexpr int kMaxWords = EncSmem<CH>::kMaxWords;
   uint32_t senc[kMaxSym];
   __align__(16) uint32_t lw[2][kMaxWords];
-  uint32_t wtot[kEncWarps], woff[kEncWarps];
-  uint32_t tile, tbits;
+  uint32_t wtot[kEncWarps];
+  uint32_t tk[2];  // tickets: the current tile and the next one
   unsigned long long base;
 };
 
+// The codes of one lane of one chunk (PER consecutive codes, 16-byte loads).
+template <int PER>
+__device__ __forceinline__ void load_lane_codes(const uint16_t *codes, uint64_t chunk, int CH, int lane,
+                                                uint4 (&raw)[PER / 8]) {
+  const uint4 *src = reinterpret_cast<const uint4 *>(codes + chunk * CH + lane * PER);
+#pragma unroll
+  for (int v = 0; v < PER / 8; ++v) raw[v] = __ldcs(src + v);
+}
+
 template <int CH>
-__global__ void __launch_bounds__(kEncThreads) k_encode_pipe(Geom g, CompressWs ws, uint8_t *d_out) {
+__global__ void __launch_bounds__(kEncThreads, FZ_ENC_MINB) k_encode_pipe(Geom g, CompressWs ws, uint8_t *d_out) {
   constexpr int PER = CH / 32;
   __shared__ PipeSmem<CH> sm;
   Ctl *ctl = ws.ctl;
@@ -239,51 +254,61 @@ __global__ void __launch_bounds__(kEncThreads) k_encode_pipe(Geom g, CompressWs 
   const uint64_t wlimit = (ctl->total_bits + 31) / 32;
   for (int i = tid; i < kMaxSym; i += kEncThreads) sm.senc[i] = ctl->enc[i];
   for (int i = tid; i < 2 * PipeSmem<CH>::kMaxWords; i += kEncThreads) (&sm.lw[0][0])[i] = 0;
-  if (tid == 0) sm.tile = atomicAdd(&ctl->encode_ticket, 1u);
+  if (tid == 0) sm.tk[0] = atomicAdd(&ctl->encode_ticket, 1u);
   __syncthreads();
+  uint64_t tile = sm.tk[0];
+  // the codes of the tile in hand are loaded one step ahead of their use
+  uint4 raw[PER / 8];
+  if (tile < n_tiles && tile * kEncWarps + warp < n_chunks) load_lane_codes<PER>(ws.codes, tile * kEncWarps + warp, CH, lane, raw);
   uint64_t prev = ~0ull;
   uint32_t prev_bits = 0;
   int cb = 0;
   for (;;) {
-    const uint64_t tile = sm.tile;  // written before the last barrier
     const bool have = tile < n_tiles;
     uint32_t tbits = 0;
-    if (have) {
-      uint32_t *lw = sm.lw[cb];
-      // ---- count and publish
-      const uint64_t chunk = tile * kEncWarps + warp;
-      const bool valid = chunk < n_chunks;
-      uint32_t cw[PER];
-      uint32_t lbits = 0;
-      if (valid) {
-        const uint4 *src = reinterpret_cast<const uint4 *>(ws.codes + chunk * CH + lane * PER);
+    uint32_t *lw = sm.lw[cb];
+    const uint64_t chunk = tile * kEncWarps + warp;
+    const bool valid = have && chunk < n_chunks;
+    if (tid == 0 && have) sm.tk[cb ^ 1] = atomicAdd(&ctl->encode_ticket, 1u);
+    // the next tile's first 32 codes (its head), read ahead of their use
+    uint32_t hcode = 0;
+    if (have && warp == kEncWarps - 1 && tile + 1 < n_tiles)
+      hcode = ws.codes[(tile + 1) * kEncWarps * (uint64_t)CH + lane];
+    // ---- count and publish
+    uint32_t cw[PER];
+    uint32_t lbits = 0;
+    if (valid) {
 #pragma unroll
-        for (int v = 0; v < PER / 8; ++v) {
-          const uint4 u = __ldcs(src + v);
-          const uint32_t w4[4] = {u.x, u.y, u.z, u.w};
+      for (int v = 0; v < PER / 8; ++v) {
+        const uint32_t w4[4] = {raw[v].x, raw[v].y, raw[v].z, raw[v].w};
 #pragma unroll
-          for (int k = 0; k < 4; ++k) {
-            cw[8 * v + 2 * k] = sm.senc[w4[k] & 0xffffu];
-            cw[8 * v + 2 * k + 1] = sm.senc[w4[k] >> 16];
-          }
+        for (int k = 0; k < 4; ++k) {
+          cw[8 * v + 2 * k] = sm.senc[w4[k] & 0xffffu];
+          cw[8 * v + 2 * k + 1] = sm.senc[w4[k] >> 16];
         }
-#pragma unroll
-        for (int k = 0; k < PER; ++k) lbits += cw[k] >> 24;
-      } else {
-#pragma unroll
-        for (int k = 0; k < PER; ++k) cw[k] = 0;
       }
-      uint32_t incl = lbits;
 #pragma unroll
-      for (int off = 1; off < 32; off <<= 1) {
-        const uint32_t v = __shfl_up_sync(0xffffffffu, incl, off);
-        if (lane >= off) incl += v;
-      }
-      if (lane == 31) {
-        sm.wtot[warp] = incl;
-        if (valid) chunk_bits[chunk] = incl;
-      }
-      __syncthreads();
+      for (int k = 0; k < PER; ++k) lbits += cw[k] >> 24;
+    } else {
+#pragma unroll
+      for (int k = 0; k < PER; ++k) cw[k] = 0;
+    }
+    uint32_t incl = lbits;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+      const uint32_t v = __shfl_up_sync(0xffffffffu, incl, off);
+      if (lane >= off) incl += v;
+    }
+    if (lane == 31) {
+      sm.wtot[warp] = incl;
+      if (valid) chunk_bits[chunk] = incl;
+    }
+    __syncthreads();
+    // ---- the next tile's codes go out now and land during this step
+    const uint64_t next = have ? (uint64_t)sm.tk[cb ^ 1] : n_tiles;
+    if (next < n_tiles && next * kEncWarps + warp < n_chunks)
+      load_lane_codes<PER>(ws.codes, next * kEncWarps + warp, CH, lane, raw);
+    if (have) {
       uint32_t woff = 0;
 #pragma unroll
       for (int w = 0; w < kEncWarps; ++w) {
@@ -316,7 +341,7 @@ __global__ void __launch_bounds__(kEncThreads) k_encode_pipe(Geom g, CompressWs 
       }
       // ---- first 32 bits of the next tile, right after this tile's bits
       if (warp == kEncWarps - 1 && tile + 1 < n_tiles) {
-        const uint32_t e = sm.senc[ws.codes[(tile + 1) * kEncWarps * (uint64_t)CH + lane]];
+        const uint32_t e = sm.senc[hcode];
         const uint32_t L = e >> 24, c = e & 0xffffffu;
         uint32_t p = L;
 #pragma unroll
@@ -342,8 +367,7 @@ __global__ void __launch_bounds__(kEncThreads) k_encode_pipe(Geom g, CompressWs 
         if (prev == n_tiles - 1 && base + prev_bits != ctl->total_bits) set_err(ctl, FZ_ECORRUPT);
       }
     }
-    if (tid == 0 && have) sm.tile = atomicAdd(&ctl->encode_ticket, 1u);
-    __syncthreads();  // packing, head, base and the next ticket are visible
+    __syncthreads();  // packing, head and base are visible
     if (prev != ~0ull) {
       const uint32_t *plw = sm.lw[cb ^ 1];
       const unsigned long long base = sm.base;
@@ -363,6 +387,7 @@ __global__ void __launch_bounds__(kEncThreads) k_encode_pipe(Geom g, CompressWs 
     if (!have) break;
     prev = tile;
     prev_bits = tbits;
+    tile = next;
     cb ^= 1;
     __syncthreads();  // the cleared image is ready for the next tile
   }

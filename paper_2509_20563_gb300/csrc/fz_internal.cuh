@@ -232,6 +232,23 @@ __device__ __forceinline__ int32_t prequant(float x, float inv2eb, float ebx2, f
   return q;
 }
 
+// prequant() without the float<->int conversion instructions, for
+// |x * inv2eb| < 2^22: t + 1.5*2^23 then lies in [2^23, 2^24), where the
+// floats are exactly the integers, so the rounded sum is rint(t) (ties to
+// even, like cvt.rni) and its mantissa holds rint(t) + 2^22.  Sets slow
+// (and returns garbage) outside that range, NaN included; the caller then
+// takes prequant().  Same q and exception flag as prequant() otherwise.
+__device__ __forceinline__ int32_t prequant_fast(float x, float inv2eb, float ebx2, float eb_chk, bool &exc,
+                                                 bool &slow) {
+  constexpr float kMagic = 12582912.0f;  // 1.5 * 2^23, bit pattern 0x4B400000
+  const float t = __fmul_rn(x, inv2eb);
+  slow = !(fabsf(t) < 4194304.0f);
+  const float s = __fadd_rn(t, kMagic);
+  const float r = __fmul_rn(__fsub_rn(s, kMagic), ebx2);
+  exc = fabsf(__fsub_rn(x, r)) > eb_chk;
+  return __float_as_int(s) - 0x4B400000;
+}
+
 // Selector network shape: 32 block features -> 64 hidden (ReLU) -> 4
 // predictor logits.  Parameter order in every weight array: W1[64][32],
 // b1[64], W2[4][64], b2[4].

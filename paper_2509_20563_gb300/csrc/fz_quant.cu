@@ -165,21 +165,45 @@ __device__ __forceinline__ void tile_front(const Geom &g, const TileXY &t, const
   using S = TileShape<NDIM>;
   constexpr int TXP = S::TX + 8;
   const int tid = threadIdx.x, lane = tid & 31;
+  // prequantization by the float adder; values of magnitude 2^22 steps and
+  // above (and NaN/Inf) send the thread's 16 values through prequant()
+  bool slow_any = false;
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    const float a[4] = {v[j].x, v[j].y, v[j].z, v[j].w};
+    exf[j] = 0;
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      bool ee, sl;
+      q[j][u] = prequant_fast(a[u], qc.inv2eb, qc.ebx2, qc.eb_chk, ee, sl);
+      slow_any |= sl;
+      exf[j] |= (uint32_t)ee << (8 * u);
+    }
+  }
+  if (slow_any) {
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const float a[4] = {v[j].x, v[j].y, v[j].z, v[j].w};
+      exf[j] = 0;
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        bool ee;
+        q[j][u] = prequant(a[u], qc.inv2eb, qc.ebx2, qc.eb_chk, ee);
+        exf[j] |= (uint32_t)ee << (8 * u);
+      }
+    }
+  }
 #pragma unroll
   for (int j = 0; j < 4; ++j) {
     int row, col;
     elem_rc<NDIM>(tid, j, row, col);
     const uint32_t X = t.x0 + col, Y = t.y0 + (row % S::BY), Z = t.z0 + row / S::BY;
     const bool inrow = INTERIOR || (Y < g.ny && Z < g.nz);
-    const float a[4] = {v[j].x, v[j].y, v[j].z, v[j].w};
-    exf[j] = 0;
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
       const bool in = INTERIOR || (inrow && X + u < g.nx);
-      bool ee;
-      const int32_t qq = prequant(a[u], qc.inv2eb, qc.ebx2, qc.eb_chk, ee);
-      q[j][u] = in ? qq : 0;
-      exf[j] |= (uint32_t)(in && ee) << (8 * u);
+      q[j][u] = in ? q[j][u] : 0;
+      exf[j] &= in ? 0xffffffffu : ~(0xffu << (8 * u));
     }
     *reinterpret_cast<uint32_t *>(&sexc[row * S::TX + col]) = exf[j];
   }
