@@ -319,16 +319,24 @@ __device__ __forceinline__ void init_side(const DecParams &p, Side &sd, uint32_t
   }
 }
 
+// Dequantized values of eight reconstructed integers q, exceptions replaced
+// by their stored bits.
 template <bool EXC>
-__device__ __forceinline__ float value(const DecParams &p, Side &sd, uint32_t pos, int32_t q) {
-  float v = __fmul_rn(__int2float_rn(q), p.ebx2);
-  if (EXC && pos == sd.next_e) {
-    const ExceptionHit h = fetch_exception(p.exc_idx, p.exc_val, p.n_exc, sd.ec);
-    sd.ec = h.ec;
-    sd.next_e = h.next_e;
-    v = __uint_as_float(h.bits);
+__device__ __forceinline__ void values8(const DecParams &p, Side &sd, uint32_t pos, const int32_t (&q)[8],
+                                        float (&o)[8]) {
+#pragma unroll
+  for (int x = 0; x < 8; ++x) o[x] = __fmul_rn(__int2float_rn(q[x]), p.ebx2);
+  if (EXC) {
+#pragma unroll
+    for (int x = 0; x < 8; ++x) {
+      if (pos + x == sd.next_e) {
+        const ExceptionHit h = fetch_exception(p.exc_idx, p.exc_val, p.n_exc, sd.ec);
+        sd.ec = h.ec;
+        sd.next_e = h.next_e;
+        o[x] = __uint_as_float(h.bits);
+      }
+    }
   }
-  return v;
 }
 
 __device__ __forceinline__ void store4(float *out, uint64_t f, bool vec, const float *o) {
@@ -427,15 +435,14 @@ __device__ __forceinline__ void consume(const DecParams &p, const Geom &g, Side 
       if (K == 2) s.Y2[x] = y ? s.Y2[x] : 0;
     }
     int32_t *row = st + (y * 8) * T;
-    int32_t r1 = 0, r2 = 0;
+    int32_t r1 = 0, r2 = 0, q[8];
 #pragma unroll
     for (int x = 0; x < 8; ++x) {
-      int32_t q;
       if (K == 1) {
         r1 += d[x];
         s.Y1[x] += r1;
-        q = row[x * T] + s.Y1[x];
-        row[x * T] = q;
+        q[x] = row[x * T] + s.Y1[x];
+        row[x * T] = q[x];
       } else {
         r1 += d[x];
         r2 += r1;
@@ -443,11 +450,11 @@ __device__ __forceinline__ void consume(const DecParams &p, const Geom &g, Side 
         s.Y2[x] += s.Y1[x];
         const int32_t p1 = row[x * T] + s.Y2[x];
         row[x * T] = p1;
-        q = row[(64 + x) * T] + p1;
-        row[(64 + x) * T] = q;
+        q[x] = row[(64 + x) * T] + p1;
+        row[(64 + x) * T] = q[x];
       }
-      o[x] = value<EXC>(p, sd, pos + x, q);
     }
+    values8<EXC>(p, sd, pos, q, o);
     if (Z0 + z < g.nz && Y0 + y < g.ny)
       store8(p.out, ((uint64_t)(Z0 + z) * g.ny + (Y0 + y)) * g.nx + X0, X0 + 8 <= g.nx, vecbase, X0, g.nx, o);
   } else if (NDIM == 2) {
@@ -455,33 +462,35 @@ __device__ __forceinline__ void consume(const DecParams &p, const Geom &g, Side 
     s.r1 = x8 ? s.r1 : 0;
     if (K == 2) s.r2 = x8 ? s.r2 : 0;
     int32_t *col = st + (x8 * 8) * T;
+    int32_t q[8];
 #pragma unroll
     for (int u = 0; u < 8; ++u) {
-      int32_t q;
       if (K == 1) {
         s.r1 += d[u];
-        q = col[u * T] + s.r1;
-        col[u * T] = q;
+        q[u] = col[u * T] + s.r1;
+        col[u * T] = q[u];
       } else {
         s.r1 += d[u];
         s.r2 += s.r1;
         const int32_t y1 = col[u * T] + s.r2;
         col[u * T] = y1;
-        q = col[(32 + u) * T] + y1;
-        col[(32 + u) * T] = q;
+        q[u] = col[(32 + u) * T] + y1;
+        col[(32 + u) * T] = q[u];
       }
-      o[u] = value<EXC>(p, sd, pos + u, q);
     }
+    values8<EXC>(p, sd, pos, q, o);
     if (Y0 + y < g.ny)
       store8(p.out, (uint64_t)(Y0 + y) * g.nx + X0 + 8 * x8, X0 + 8 * x8 + 8 <= g.nx, vecbase, X0 + 8 * x8, g.nx,
              o);
   } else {
+    int32_t q[8];
 #pragma unroll
     for (int u = 0; u < 8; ++u) {
       s.r1 += d[u];
       if (K == 2) s.r2 += s.r1;
-      o[u] = value<EXC>(p, sd, pos + u, K == 1 ? s.r1 : s.r2);
+      q[u] = K == 1 ? s.r1 : s.r2;
     }
+    values8<EXC>(p, sd, pos, q, o);
     const uint32_t x0 = X0 + 8 * (uint32_t)gi;
     store8(p.out, x0, x0 + 8 <= g.nx, vecbase, x0, g.nx, o);
   }
