@@ -20,7 +20,7 @@
 #include "fz_internal.cuh"
 
 #ifndef FZ_QUANT_MINB
-#define FZ_QUANT_MINB 3
+#define FZ_QUANT_MINB 4
 #endif
 
 namespace fz {
