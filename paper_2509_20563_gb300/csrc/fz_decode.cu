@@ -514,9 +514,9 @@ __device__ __forceinline__ void decode_chunk(const DecParams &p, const Geom &g, 
   Side sd;
   init_side(p, sd, pos0);
   const int32_t anchor = __ldg(p.anchors + j);
-  const uint32_t bxi = (uint32_t)(j % g.nbx);
-  const uint64_t jr = j / g.nbx;
-  const uint32_t byi = (uint32_t)(jr % g.nby), bzi = (uint32_t)(jr / g.nby);
+  const uint32_t j32 = (uint32_t)j;  // blocks number at most nx*ny*nz < 2^32
+  const uint32_t bxi = j32 % g.nbx, jr = j32 / g.nbx;
+  const uint32_t byi = jr % g.nby, bzi = jr / g.nby;
   const uint32_t X0 = bxi * g.bx, Y0 = byi * g.by, Z0 = bzi * g.bz;
   for (int i = 0; i < DecState<NDIM, K>::kWords; ++i) st[i * T] = 0;
   Prefix s;

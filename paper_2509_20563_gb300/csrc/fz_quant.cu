@@ -71,11 +71,36 @@ template <int NDIM>
 __device__ __forceinline__ TileXY tile_xy(const Geom &g, uint64_t tile) {
   using S = TileShape<NDIM>;
   TileXY t;
-  const uint32_t t32 = (uint32_t)tile;  // tiles number fewer than 2^32 / 4096
+  const uint32_t t32 = (uint32_t)tile;  // tiles number at most nx*ny*nz < 2^32
   t.tx = t32 % g.tiles_x;
   const uint32_t rest = t32 / g.tiles_x;
   t.by = rest % g.nby;
   t.bz = rest / g.nby;
+  t.x0 = t.tx * S::NB * S::BX;
+  t.y0 = t.by * S::BY;
+  t.z0 = t.bz * S::BZ;
+  return t;
+}
+
+// A tile step split like a tile index (x, y, z tile counts), so that the
+// coordinates of tile + step follow from those of tile by adds and carries.
+struct TileStep {
+  uint32_t sx, sy, sz;
+};
+__device__ __forceinline__ TileStep tile_step(const Geom &g, uint64_t step) {
+  const uint32_t s32 = (uint32_t)step, r = s32 / g.tiles_x;
+  return TileStep{s32 % g.tiles_x, r % g.nby, r / g.nby};
+}
+template <int NDIM>
+__device__ __forceinline__ TileXY tile_advance(const Geom &g, TileXY t, const TileStep &s) {
+  using S = TileShape<NDIM>;
+  t.tx += s.sx;
+  const uint32_t cx = t.tx >= g.tiles_x ? 1u : 0u;
+  t.tx -= cx ? g.tiles_x : 0u;
+  t.by += s.sy + cx;
+  const uint32_t cy = t.by >= g.nby ? 1u : 0u;
+  t.by -= cy ? g.nby : 0u;
+  t.bz += s.sz + cy;
   t.x0 = t.tx * S::NB * S::BX;
   t.y0 = t.by * S::BY;
   t.z0 = t.bz * S::BZ;
@@ -358,9 +383,11 @@ __device__ __forceinline__ void quant_tiles(const float *__restrict__ x, const G
   const bool vec_ok = (NDIM == 1 || (g.nx & 3u) == 0) && (((uintptr_t)x & 15u) == 0);
 
   float4 v[4];
-  if (tile < t_end) load_tile<NDIM>(x, g, tile_xy<NDIM>(g, tile), tid, vec_ok, v);
+  const TileStep tstep = tile_step(g, t_step);
+  TileXY tn = tile_xy<NDIM>(g, tile);  // coordinates of the tile whose loads are in flight
+  if (tile < t_end) load_tile<NDIM>(x, g, tn, tid, vec_ok, v);
   for (int buf = 0; tile < t_end; tile += t_step, buf ^= 1) {
-    const TileXY t = tile_xy<NDIM>(g, tile);
+    const TileXY t = tn;
     // a tile that lies wholly inside the domain skips every bounds test
     const bool interior = vec_ok && t.x0 + S::TX <= g.nx && t.y0 + S::BY <= g.ny && t.z0 + S::BZ <= g.nz;
     int32_t *sq = sm.sq[buf];
@@ -374,7 +401,8 @@ __device__ __forceinline__ void quant_tiles(const float *__restrict__ x, const G
     // ---- next tile's loads go out now and land while this tile is coded
     {
       const uint64_t nt = tile + t_step;
-      if (nt < t_end) load_tile<NDIM>(x, g, tile_xy<NDIM>(g, nt), tid, vec_ok, v);
+      tn = tile_advance<NDIM>(g, t, tstep);
+      if (nt < t_end) load_tile<NDIM>(x, g, tn, tid, vec_ok, v);
     }
     if (NDIM == 3) {
       if (interior) tile_codes3<K, true>(g, t, qc, ws, sq, sm.shist, q, exf, nout, nexc);
