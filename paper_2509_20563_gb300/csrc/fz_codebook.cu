@@ -350,12 +350,10 @@ __global__ void __launch_bounds__(kCbThreads) k_codebook_only(const uint64_t *hi
 
 cudaError_t launch_codebook(const Geom &g, uint32_t R, uint32_t pred, uint32_t eb_mode, double eb,
                             const CompressWs &ws, cudaStream_t st) {
-  static bool attr_set = false;  // the attribute is per function; setting it twice is harmless
-  if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(k_codebook, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(CbSmem));
-    if (e != cudaSuccess) return e;
-    attr_set = true;
-  }
+  static LaunchCache cache;
+  int per_sm = 0;
+  const cudaError_t e = cached_per_sm(k_codebook, kCbThreads, (int)sizeof(CbSmem), cache, per_sm);
+  if (e != cudaSuccess) return e;
   k_codebook<<<1, kCbThreads, sizeof(CbSmem), st>>>(g, R, pred, eb_mode, eb, ws);
   return cudaGetLastError();
 }

@@ -673,12 +673,10 @@ template <int NDIM, int K>
 cudaError_t launch_dec_t(const DecParams &p, const Geom &g, int sm_count, cudaStream_t s) {
   constexpr int T = DecCta<NDIM, K>::T;
   const int smem = (int)dec_smem_bytes<NDIM, K>();
-  cudaError_t e = cudaFuncSetAttribute(k_decode<NDIM, K>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-  if (e != cudaSuccess) return e;
+  static LaunchCache cache;
   int per_sm = 0;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_decode<NDIM, K>, T, smem);
+  const cudaError_t e = cached_per_sm(k_decode<NDIM, K>, T, smem, cache, per_sm);
   if (e != cudaSuccess) return e;
-  if (per_sm < 1) per_sm = 1;
   // at most one CTA per unit: the units of a small field spread over SMs
   uint64_t grid = (uint64_t)sm_count * per_sm;
   if (grid > p.n_units) grid = p.n_units;

@@ -395,10 +395,10 @@ __global__ void __launch_bounds__(kEncThreads, FZ_ENC_MINB) k_encode_pipe(Geom g
 
 template <int CH>
 cudaError_t launch_t(const Geom &g, const CompressWs &ws, uint8_t *d_out, cudaStream_t s, int sms) {
+  static LaunchCache cache;
   int per_sm = 0;
-  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_encode_pipe<CH>, kEncThreads, 0);
+  const cudaError_t e = cached_per_sm(k_encode_pipe<CH>, kEncThreads, 0, cache, per_sm);
   if (e != cudaSuccess) return e;
-  if (per_sm < 1) per_sm = 1;
   const uint64_t n_tiles = (g.n_blocks + kEncWarps - 1) / kEncWarps;
   uint64_t grid = (uint64_t)sms * per_sm;
   if (grid > n_tiles) grid = n_tiles;

@@ -6,6 +6,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <atomic>
+
 #include "../../include/fz.h"
 
 namespace fz {
@@ -55,6 +57,40 @@ inline __host__ __device__ void make_geom(uint32_t ndim, const uint64_t dims[3],
   g.npad = g.n_blocks * g.bsize;
   g.tiles_x = (g.nbx + g.tile_nb - 1) / g.tile_nb;
   g.n_qtiles = (uint64_t)g.tiles_x * g.nby * g.nbz;
+}
+
+// Launch shape of one kernel, computed on its first launch on each device:
+// the kernel's dynamic shared memory limit raised to the launch's size and
+// its resident CTAs per SM, so that later launches make no attribute or
+// occupancy query.
+constexpr int kMaxLaunchDevices = 64;
+struct LaunchCache {
+  std::atomic<int> per_sm[kMaxLaunchDevices];
+};
+template <typename Kernel>
+cudaError_t cached_per_sm(Kernel kernel, int threads, int smem, LaunchCache &c, int &per_sm) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  const bool cacheable = dev >= 0 && dev < kMaxLaunchDevices;
+  if (cacheable) {
+    const int v = c.per_sm[dev].load(std::memory_order_relaxed);
+    if (v > 0) {
+      per_sm = v;
+      return cudaSuccess;
+    }
+  }
+  if (smem > 0) {
+    e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+  }
+  int v = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, kernel, threads, smem);
+  if (e != cudaSuccess) return e;
+  if (v < 1) v = 1;
+  if (cacheable) c.per_sm[dev].store(v, std::memory_order_relaxed);
+  per_sm = v;
+  return cudaSuccess;
 }
 
 // Per-call control block.  Zeroed by one memset at the start of each

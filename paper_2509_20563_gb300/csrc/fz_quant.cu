@@ -550,12 +550,10 @@ __global__ void __launch_bounds__(kQuantThreads, 3) k_quant_batch(const BatchJob
 template <int NDIM, int K>
 cudaError_t launch_t(const float *x, const Geom &g, uint32_t R, const CompressWs &ws, cudaStream_t s, int sms) {
   const int smem = (int)sizeof(QuantSmem<NDIM>);
-  cudaError_t e = cudaFuncSetAttribute(k_quant<NDIM, K>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-  if (e != cudaSuccess) return e;
+  static LaunchCache cache;
   int per_sm = 0;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_quant<NDIM, K>, kQuantThreads, smem);
+  const cudaError_t e = cached_per_sm(k_quant<NDIM, K>, kQuantThreads, smem, cache, per_sm);
   if (e != cudaSuccess) return e;
-  if (per_sm < 1) per_sm = 1;
   uint64_t grid = (uint64_t)sms * per_sm;
   if (grid > g.n_qtiles) grid = g.n_qtiles;
   k_quant<NDIM, K><<<(unsigned)grid, kQuantThreads, smem, s>>>(x, g, R, ws);

@@ -647,12 +647,10 @@ template <int MODE>
 cudaError_t launch_sel_t(const float *x, const Geom &g, uint32_t R, uint32_t pid, const CompressWs &ws,
                          const SelOut &so, cudaStream_t s, int sms) {
   const int smem = (int)sizeof(SelSmem);
-  cudaError_t e = cudaFuncSetAttribute(k_selquant<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-  if (e != cudaSuccess) return e;
+  static LaunchCache cache;
   int per_sm = 0;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_selquant<MODE>, kSelThreads, smem);
+  const cudaError_t e = cached_per_sm(k_selquant<MODE>, kSelThreads, smem, cache, per_sm);
   if (e != cudaSuccess) return e;
-  if (per_sm < 1) per_sm = 1;
   uint64_t grid = (uint64_t)sms * per_sm;
   if (grid > g.n_qtiles) grid = g.n_qtiles;
   k_selquant<MODE><<<(unsigned)grid, kSelThreads, smem, s>>>(x, g, R, pid, ws, so);
