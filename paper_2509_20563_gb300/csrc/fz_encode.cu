@@ -29,7 +29,10 @@ namespace {
 constexpr int kEncThreads = kEncWarps * 32;
 
 #ifndef FZ_ENC_MINB
-#define FZ_ENC_MINB 6
+#define FZ_ENC_MINB 6  // CTAs per SM, 512-code chunks (3D)
+#endif
+#ifndef FZ_ENC_MINB1024
+#define FZ_ENC_MINB1024 3  // CTAs per SM, 1024-code chunks (1D, 2D)
 #endif
 
 template <int CH>
@@ -240,7 +243,7 @@ __device__ __forceinline__ void load_lane_codes(const uint16_t *codes, uint64_t 
 }
 
 template <int CH>
-__global__ void __launch_bounds__(kEncThreads, FZ_ENC_MINB) k_encode_pipe(Geom g, CompressWs ws, uint8_t *d_out) {
+__global__ void __launch_bounds__(kEncThreads, CH == 512 ? FZ_ENC_MINB : FZ_ENC_MINB1024) k_encode_pipe(Geom g, CompressWs ws, uint8_t *d_out) {
   constexpr int PER = CH / 32;
   __shared__ PipeSmem<CH> sm;
   Ctl *ctl = ws.ctl;
