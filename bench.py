@@ -47,7 +47,7 @@ WORKLOAD = "3D FP32 512^3 Gaussian random field (k^-5/3), REL 1e-4, Lorenzo-1, r
 # large kernel on exactly this workload (512^3, REL 1e-4), from one ncu
 # capture of the current kernels (profiles/dram_grf512_rel1e-4.md); reported
 # as roofline.traffic for the dominant kernel, null for any other workload.
-NCU_DRAM_BYTES_512 = {"range": 539690752, "quant": 747504384, "encode": 358804224, "decode": 705417216}
+NCU_DRAM_BYTES_512 = {"range": 539739648, "quant": 754302976, "encode": 356544512, "decode": 705456896}
 METRIC = "compress/decompress GB/s vs HBM peak at REL 1e-4; CR learned vs plain"
 
 
