@@ -94,17 +94,71 @@ struct BitReader {
     rd = (rd + adv) & (kRing - 1);
     wi += adv;
   }
+  // Four symbols.  They all lie in the window: from an offset below 32,
+  // four codewords of at most 14 bits end by bit 87 < 96, and the fourth
+  // starts by bit 73, so its 14-bit lookup window needs no fourth word.  The
+  // window then slides by 0, 1 or 2 words (predicated, as in next2).
+  __device__ __forceinline__ void next4(const uint16_t *slut, uint32_t (&s)[4]) {
+    uint32_t o = off;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      uint32_t w;
+      if (k == 0) w = __funnelshift_l(b, a, o);                                   // o < 32
+      else if (k < 3) w = o < 32 ? __funnelshift_l(b, a, o) : __funnelshift_l(c, b, o);  // o < 60
+      else w = o < 32 ? __funnelshift_l(b, a, o) : (o < 64 ? __funnelshift_l(c, b, o) : c << (o & 31u));
+      const uint32_t e = slut[w >> (32 - kLutBits)];
+      s[k] = e & 1023u;
+      o += (e >> kLutLenShift) & 15u;
+    }
+    const uint32_t adv = o >> 5;  // 0, 1 or 2
+    off = o & 31u;
+    // the oldest one or two ring slots become the window's new words and are
+    // refilled with the words kRing slides ahead; waiting for all but the
+    // newest kRing - 2 copies covers both slots
+    const uint32_t slot0 = ring_s + rd * (uint32_t)(T * 4);
+    const uint32_t slot1 = ring_s + ((rd + 1) & (kRing - 1)) * (uint32_t)(T * 4);
+    const bool more0 = wi < nw, more1 = wi + 1 < nw;
+    const uint32_t *src0 = W + (more0 ? wi : 0u);
+    const uint32_t *src1 = W + (more1 ? wi + 1 : 0u);
+    uint32_t r0 = 0, r1 = 0;
+    asm volatile(
+        "{\n"
+        " .reg .pred p1, p2;\n"
+        " setp.ne.u32 p1, %2, 0;\n"
+        " setp.gt.u32 p2, %2, 1;\n"
+        " @p1 cp.async.wait_group %9;\n"
+        " @p1 ld.shared.u32 %0, [%3];\n"
+        " @p2 ld.shared.u32 %1, [%4];\n"
+        " @p1 cp.async.ca.shared.global [%3], [%5], 4, %7;\n"
+        " @p1 cp.async.commit_group;\n"
+        " @p2 cp.async.ca.shared.global [%4], [%6], 4, %8;\n"
+        " @p2 cp.async.commit_group;\n"
+        "}\n"
+        : "+r"(r0), "+r"(r1)
+        : "r"(adv), "r"(slot0), "r"(slot1), "l"(src0), "l"(src1), "r"(more0 ? 4 : 0), "r"(more1 ? 4 : 0),
+          "n"(kRing - 2));
+    const uint32_t na = adv == 0 ? a : (adv == 1 ? b : c);
+    const uint32_t nb = adv == 0 ? b : (adv == 1 ? c : r0);
+    const uint32_t nc = adv == 0 ? c : (adv == 1 ? r0 : r1);
+    a = na;
+    b = nb;
+    c = nc;
+    rd = (rd + adv) & (kRing - 1);
+    wi += adv;
+  }
   // Eight symbols as residuals sym - R; returns whether any symbol was 0
   // (an outlier, whose residual is then -R until it is looked up).
   __device__ __forceinline__ bool group8(const uint16_t *slut, int32_t R, int32_t (&d)[8]) {
     bool zero = false;
 #pragma unroll
-    for (int k = 0; k < 4; ++k) {
-      uint32_t s0, s1;
-      next2(slut, s0, s1);
-      zero = zero || s0 == 0 || s1 == 0;
-      d[2 * k] = (int32_t)s0 - R;
-      d[2 * k + 1] = (int32_t)s1 - R;
+    for (int k = 0; k < 2; ++k) {
+      uint32_t s[4];
+      next4(slut, s);
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        zero = zero || s[u] == 0;
+        d[4 * k + u] = (int32_t)s[u] - R;
+      }
     }
     return zero;
   }
