@@ -151,7 +151,7 @@ template <int NDIM>
 struct QuantSmem {
   static constexpr int TXP = TileShape<NDIM>::TX + 8;
   int32_t sq[2][TileShape<NDIM>::ROWS * TXP];  // double-buffered q (1D/2D) or x/y-differenced q (3D)
-  uint8_t sexc[2][kTileElems];                 // exception flags, tile row-major
+  uint8_t sexc[2][NDIM == 3 ? 16 : kTileElems];  // exception flags, tile row-major (1D/2D)
   uint32_t shist[kMaxSym];
 };
 
@@ -182,17 +182,23 @@ __device__ __forceinline__ int32_t smem_residual(const int32_t *sq, int row, int
 }
 
 // Phase A of a tile: prequantize this thread's 16 values, difference them
-// along x and y in registers (3D), and store them to the shared tile.
+// along x and y in registers (3D), and store them to the shared tile.  The
+// thread's exceptions: 1D/2D flag them in the shared tile (their codes are
+// produced by other threads), 3D only counts them (the same thread codes
+// them; the rare compaction pass finds them again from the input).
 template <int NDIM, int K, bool INTERIOR>
 __device__ __forceinline__ void tile_front(const Geom &g, const TileXY &t, const float4 (&v)[4],
                                            const QuantConst &qc, int32_t *sq, uint8_t *sexc, int32_t (&q)[4][4],
-                                           uint32_t (&exf)[4]) {
+                                           uint32_t &nexc) {
   using S = TileShape<NDIM>;
   constexpr int TXP = S::TX + 8;
+  constexpr bool kCountOnly = NDIM == 3 && INTERIOR;
   const int tid = threadIdx.x, lane = tid & 31;
   // prequantization by the float adder; values of magnitude 2^22 steps and
   // above (and NaN/Inf) send the thread's 16 values through prequant()
   bool slow_any = false;
+  uint32_t exf[4];
+  nexc = 0;
 #pragma unroll
   for (int j = 0; j < 4; ++j) {
     const float a[4] = {v[j].x, v[j].y, v[j].z, v[j].w};
@@ -202,10 +208,12 @@ __device__ __forceinline__ void tile_front(const Geom &g, const TileXY &t, const
       bool ee, sl;
       q[j][u] = prequant_fast(a[u], qc.inv2eb, qc.ebx2, qc.eb_chk, ee, sl);
       slow_any |= sl;
-      exf[j] |= (uint32_t)ee << (8 * u);
+      if (kCountOnly) nexc += ee ? 1u : 0u;
+      else exf[j] |= (uint32_t)ee << (8 * u);
     }
   }
   if (slow_any) {
+    nexc = 0;
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
       const float a[4] = {v[j].x, v[j].y, v[j].z, v[j].w};
@@ -214,7 +222,8 @@ __device__ __forceinline__ void tile_front(const Geom &g, const TileXY &t, const
       for (int u = 0; u < 4; ++u) {
         bool ee;
         q[j][u] = prequant(a[u], qc.inv2eb, qc.ebx2, qc.eb_chk, ee);
-        exf[j] |= (uint32_t)ee << (8 * u);
+        if (kCountOnly) nexc += ee ? 1u : 0u;
+        else exf[j] |= (uint32_t)ee << (8 * u);
       }
     }
   }
@@ -230,7 +239,11 @@ __device__ __forceinline__ void tile_front(const Geom &g, const TileXY &t, const
       q[j][u] = in ? q[j][u] : 0;
       exf[j] &= in ? 0xffffffffu : ~(0xffu << (8 * u));
     }
-    *reinterpret_cast<uint32_t *>(&sexc[row * S::TX + col]) = exf[j];
+    if (NDIM == 3) {
+      if (!kCountOnly) nexc += __popc(exf[j]);
+    } else {
+      *reinterpret_cast<uint32_t *>(&sexc[row * S::TX + col]) = exf[j];
+    }
   }
   if (NDIM == 3) {
     // (1 - S_x)^K within the thread's 4 columns; the left neighbour column
@@ -274,8 +287,7 @@ __device__ __forceinline__ void tile_front(const Geom &g, const TileXY &t, const
 template <int K, bool INTERIOR>
 __device__ __forceinline__ void tile_codes3(const Geom &g, const TileXY &t, const QuantConst &qc,
                                             const CompressWs &ws, const int32_t *sq, uint32_t *shist,
-                                            const int32_t (&q)[4][4], const uint32_t (&exf)[4], uint32_t &nout,
-                                            uint32_t &nexc) {
+                                            const int32_t (&q)[4][4], uint32_t &nout, uint32_t &nexc) {
   using S = TileShape<3>;
   constexpr int TXP = S::TX + 8;
   const int tid = threadIdx.x, lane = tid & 31, pz = tid >> 5;
@@ -307,7 +319,6 @@ __device__ __forceinline__ void tile_codes3(const Geom &g, const TileXY &t, cons
       if (origin && bvalid) ws.anchors[blk] = d[u];
       nout += outl;
     }
-    nexc += __popc(exf[j]);
     if (bvalid) {
       const uint64_t p0 = blk * 512 + pz * 64 + py * 8 + px0;
       *reinterpret_cast<uint2 *>(ws.codes + p0) =
@@ -394,9 +405,8 @@ __device__ __forceinline__ void quant_tiles(const float *__restrict__ x, const G
     uint8_t *sexc = sm.sexc[buf];
     uint32_t nout = 0, nexc = 0;
     int32_t q[4][4];
-    uint32_t exf[4];
-    if (interior) tile_front<NDIM, K, true>(g, t, v, qc, sq, sexc, q, exf);
-    else tile_front<NDIM, K, false>(g, t, v, qc, sq, sexc, q, exf);
+    if (interior) tile_front<NDIM, K, true>(g, t, v, qc, sq, sexc, q, nexc);
+    else tile_front<NDIM, K, false>(g, t, v, qc, sq, sexc, q, nexc);
     __syncthreads();
     // ---- next tile's loads go out now and land while this tile is coded
     {
@@ -405,9 +415,10 @@ __device__ __forceinline__ void quant_tiles(const float *__restrict__ x, const G
       if (nt < t_end) load_tile<NDIM>(x, g, tn, tid, vec_ok, v);
     }
     if (NDIM == 3) {
-      if (interior) tile_codes3<K, true>(g, t, qc, ws, sq, sm.shist, q, exf, nout, nexc);
-      else tile_codes3<K, false>(g, t, qc, ws, sq, sm.shist, q, exf, nout, nexc);
+      if (interior) tile_codes3<K, true>(g, t, qc, ws, sq, sm.shist, q, nout, nexc);
+      else tile_codes3<K, false>(g, t, qc, ws, sq, sm.shist, q, nout, nexc);
     } else {
+      nexc = 0;  // counted by the coding threads from the shared flags
       if (interior) tile_codes12<NDIM, K, true>(g, t, qc, ws, sq, sexc, sm.shist, nout, nexc);
       else tile_codes12<NDIM, K, false>(g, t, qc, ws, sq, sexc, sm.shist, nout, nexc);
     }
@@ -470,7 +481,10 @@ __device__ __forceinline__ void quant_tiles(const float *__restrict__ x, const G
             bool outl;
             make_code(d, qc.R, in, idx == 0 && pz == 0, outl);
             const uint64_t fi = ((uint64_t)(t.z0 + pz) * g.ny + (t.y0 + py)) * g.nx + (t.x0 + col);
-            emit(outl, d, in && sexc[row * S::TX + col], (uint32_t)(blk * 512 + 64 * pz + idx), fi, co, ce);
+            // this warp's exceptions, found again from the input (nexc > 0 only)
+            bool ex = false;
+            if (nexc != 0 && in) prequant(x[fi], qc.inv2eb, qc.ebx2, qc.eb_chk, ex);
+            emit(outl, d, ex, (uint32_t)(blk * 512 + 64 * pz + idx), fi, co, ce);
           }
           wsl.ocnt |= (unsigned long long)co << (8 * b);
           wsl.ecnt |= (unsigned long long)ce << (8 * b);
