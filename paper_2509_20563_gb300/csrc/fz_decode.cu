@@ -378,9 +378,15 @@ struct DecState {
 #ifndef FZ_DEC_T3
 #define FZ_DEC_T3 448
 #endif
+#ifndef FZ_DEC_T2
+#define FZ_DEC_T2 512  // 2D order 1: 640 and 768 measured slower on a 1800 x 3600 field
+#endif
+#ifndef FZ_DEC_T1
+#define FZ_DEC_T1 1024  // 1D: 768 and 896 measured slower on a 281M-value field
+#endif
 template <int NDIM, int K>
 struct DecCta {
-  static constexpr int T = NDIM == 3 ? (K == 1 ? FZ_DEC_T3 : 288) : (NDIM == 2 ? (K == 1 ? 640 : 448) : 768);
+  static constexpr int T = NDIM == 3 ? (K == 1 ? FZ_DEC_T3 : 288) : (NDIM == 2 ? (K == 1 ? FZ_DEC_T2 : 448) : FZ_DEC_T1);
 };
 
 template <int NDIM, int K>
