@@ -189,15 +189,18 @@ def run_fz(args, rank, world, local_rank):
     nbytes = C.c_uint64()
     hdr = C.create_string_buffer(256)
 
+    # the call arguments are built once, as a caller in a loop would
+    fz_compress, fz_decompress = L.fz_compress, L.fz_decompress
+    xp, bufp, yp = C.c_void_p(x.data_ptr()), C.c_void_p(buf.data_ptr()), C.c_void_p(y.data_ptr())
+    c_args = (ctx.handle, xp, 3, dims, 1, args.eb, C.byref(pipe), bufp, bound, C.byref(nbytes), hdr, sp)
+
     def compress():
-        st = L.fz_compress(ctx.handle, C.c_void_p(x.data_ptr()), 3, dims, 1, args.eb, C.byref(pipe),
-                           C.c_void_p(buf.data_ptr()), bound, C.byref(nbytes), hdr, sp)
+        st = fz_compress(*c_args)
         if st:
             raise fz.FzError(st, "fz_compress")
 
     def decompress():
-        st = L.fz_decompress(ctx.handle, C.c_void_p(buf.data_ptr()), nbytes.value, hdr, C.c_void_p(y.data_ptr()),
-                             N, sp)
+        st = fz_decompress(ctx.handle, bufp, nbytes.value, hdr, yp, N, sp)
         if st:
             raise fz.FzError(st, "fz_decompress")
 

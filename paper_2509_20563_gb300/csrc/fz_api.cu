@@ -105,6 +105,7 @@ size_t layout_compress_split(const Geom &g, char *zbase, char *rbase, CompressWs
   ws.tdst = reinterpret_cast<uint2 *>(rtake(8 * g.n_qtiles));
   ws.winfo = reinterpret_cast<WarpSlots *>(rtake(sizeof(WarpSlots) * 8 * g.n_qtiles));
   ws.otiles = reinterpret_cast<uint32_t *>(rtake(4 * g.n_qtiles));
+  ws.h_res = nullptr;  // set by the single-field compress only
   if (rest_bytes) *rest_bytes = ro;
   return zo;
 }
@@ -357,8 +358,8 @@ fz_status fz_compress(fz_ctx *ctx, const float *d_in, uint32_t ndim, const uint6
   cudaError_t e = launch_codebook(g, r.R, r.pred, eb_mode, eb, ws, s);
   clk.mark("codebook", 1);
   if (e == cudaSuccess) { e = launch_encode(g, ws, out, s, ctx->sm_count); clk.mark("encode", 1); }
+  ws.h_res = reinterpret_cast<Result *>(ctx->h_pinned);  // pinned, mapped: written by the last kernel
   if (e == cudaSuccess) { e = launch_assemble(d_in, g, r.R, ws, out, s, ctx->sm_count); clk.mark("assemble", 2); }
-  if (e == cudaSuccess) e = cudaMemcpyAsync(ctx->h_pinned, &ws.ctl->res, sizeof(Result), cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) return from_cuda(e);
   const Result *res = reinterpret_cast<const Result *>(ctx->h_pinned);
@@ -435,13 +436,15 @@ fz_status fz_decompress(fz_ctx *ctx, const void *d_in, uint64_t in_bytes, const 
     e = cudaMemsetAsync(ws.err, 0, dec_offset_zero_bytes(h), s);
     if (e == cudaSuccess) { e = launch_decode_offsets(in, h, ws, s); clk.mark("dec_offsets", 1); }
     if (e == cudaSuccess && ofirst) { e = launch_outlier_starts(in, h, ws, s, ctx->sm_count); clk.mark("outliers", 1); }
+    // the decoder's last CTA writes the error word into the pinned buffer
+    ws.h_err = reinterpret_cast<uint32_t *>(ctx->h_pinned);
+    *reinterpret_cast<volatile uint32_t *>(ws.h_err) = 0;
     if (e == cudaSuccess) { e = launch_decode_main(in, h, d_out, ws, s, ctx->sm_count); clk.mark("decode", 1); }
   }
-  if (e == cudaSuccess) e = cudaMemcpyAsync(ctx->h_pinned, ws.err, 4, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess && selpath) e = cudaMemcpyAsync(ctx->h_pinned, ws.err, 4, cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) return from_cuda(e);
-  uint32_t err;
-  memcpy(&err, ctx->h_pinned, 4);
+  const uint32_t err = *reinterpret_cast<volatile const uint32_t *>(ctx->h_pinned);
   return (fz_status)err;
 }
 

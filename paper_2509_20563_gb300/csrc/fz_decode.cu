@@ -269,7 +269,8 @@ struct DecParams {
   const uint32_t *ofirst; // per block with outliers: index of its first outlier (or null: search)
   uint32_t nsym;
   uint64_t total_bits;
-  uint32_t *err;          // err[0] error word, err[1] work-unit counter
+  uint32_t *err;          // err[0] error word, err[1] work-unit counter, err[2] CTAs done
+  uint32_t *h_err;        // host-mapped copy of err[0], written by the last CTA (or null)
   float *out;
   float ebx2;
   int32_t R;
@@ -591,12 +592,22 @@ __global__ void __launch_bounds__(DecCta<NDIM, K>::T, 1) k_decode(DecParams p, G
   uint32_t *sring = reinterpret_cast<uint32_t *>(sstate + DecState<NDIM, K>::kWords * T);
   __shared__ LutBuild lb;
   // every CTA builds the decode table from the 1 KB length table itself
-  if (!build_lut<T>(p.lens, p.nsym, slut, lb)) {
-    if (threadIdx.x == 0) dec_err(p.err, FZ_ECORRUPT);
-    return;
+  if (build_lut<T>(p.lens, p.nsym, slut, lb)) {
+    __syncthreads();
+    decode_units<NDIM, K>(p, g, slut, sstate, sring);
+  } else if (threadIdx.x == 0) {
+    dec_err(p.err, FZ_ECORRUPT);
   }
+  // the last CTA to finish hands the error word to the host directly
   __syncthreads();
-  decode_units<NDIM, K>(p, g, slut, sstate, sring);
+  if (p.h_err && threadIdx.x == 0) {
+    __threadfence();
+    if (atomicAdd(p.err + 2, 1u) == gridDim.x - 1) {
+      __threadfence();
+      *reinterpret_cast<volatile uint32_t *>(p.h_err) = atomicAdd(p.err, 0u);
+      __threadfence_system();
+    }
+  }
 }
 
 // ---------------------------------------------------------------- batched decode
@@ -821,6 +832,7 @@ cudaError_t launch_decode_main(const uint8_t *d_in, const fz_header &h, float *d
   p.total_bits = h.total_bits;
   p.lut = ws.lut;
   p.err = ws.err;
+  p.h_err = ws.h_err;
   p.out = d_out;
   memcpy(&p.ebx2, &h.ebx2_bits, 4);
   p.R = (int32_t)h.radius;

@@ -329,6 +329,7 @@ struct CompressWs {
   uint32_t *exc_val;
   uint64_t cap_list;       // floor(N/8)
   uint8_t *ids;            // per block: predictor id (per-block selection only)
+  Result *h_res;           // host-mapped copy of ctl->res written by the last compress kernel (or null)
 };
 
 // ---------------------------------------------------------------- batched calls
@@ -384,6 +385,7 @@ struct DecodeWs {
   uint64_t *gsum;          // per work unit of kDecUnit chunks: sum of chunk bits, then exclusive offset
   uint32_t *err;           // device error word; err[1] is the work-unit counter (both zeroed per call)
   uint32_t *ofirst = nullptr;  // per block: index of its first outlier (filled when outliers are many)
+  uint32_t *h_err = nullptr;   // host-mapped word that receives the final error word (or null)
 };
 
 inline __host__ __device__ uint64_t dec_units_of(uint64_t n_chunks) { return (n_chunks + kDecUnit - 1) / kDecUnit; }
