@@ -16,11 +16,16 @@
 // and the decode loop has no data-dependent branch.
 //
 // Kernels:
-//   k_dec_gsum  -- per group of 256 chunks, the sum of their bit lengths
-//   k_dec_prep  -- one CTA: canonical codes from the length table, the
-//                  16384-entry decode table, and the exclusive scan of the
-//                  group sums
-//   k_decode    -- persistent; one thread per chunk of the current group
+//   k_dec_offsets    -- first bit of every work unit (32 chunks): a CTA scan
+//                       of the chunk bit lengths and a decoupled look-back
+//                       across CTAs; checks the total against the header
+//   k_outlier_starts -- per block, its first outlier (streams with many)
+//   k_decode         -- persistent, one CTA per SM: each CTA builds the
+//                       decode table from the length table, each warp
+//                       claims work units and each lane decodes one chunk
+//   k_dec_gsum, k_dec_prep (per-block predictor streams and batches): unit
+//                       sums, one-CTA scan and decode table
+//   k_*_batch        -- the same for every field of a batch
 #include <string.h>
 
 #include "fz_decode_common.cuh"
@@ -150,11 +155,6 @@ __device__ __forceinline__ void dec_scan_body(uint64_t *gsum, uint64_t n_units, 
     gsum[i] = run;
     run += v;
   }
-}
-
-__global__ void __launch_bounds__(kPrepThreads) k_dec_scan(uint64_t *gsum, uint64_t n_units, uint64_t total_bits,
-                                                            uint32_t *err) {
-  dec_scan_body(gsum, n_units, total_bits, err);
 }
 
 __global__ void __launch_bounds__(kPrepThreads) k_dec_prep(const uint8_t *__restrict__ lens_in, uint32_t nsym,

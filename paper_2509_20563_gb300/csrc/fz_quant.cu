@@ -2,7 +2,8 @@
 //
 // One persistent kernel walks the tiles of 4096 values (runs of consecutive
 // blocks along x) in a static schedule; the loads of the next tile are in
-// flight while the current one is processed.  Per tile:
+// flight while the current one is processed, and the tile after that is
+// being pulled into L2.  Per tile:
 //   * FP32 prequantization q = rint(x * inv2eb) with the per-value bound
 //     check (exceptions), straight from registers;
 //   * the block-local Lorenzo residual, written as successive differences
@@ -13,9 +14,9 @@
 //     through shared memory.  1D and 2D tiles difference in shared memory;
 //   * radius-R codes in block-major order, anchors at block origins, the
 //     code histogram in shared memory;
-//   * outliers and exceptions, compacted in code-stream order inside the
-//     tile and appended to a scratch list at a slot taken with one atomic per
-//     tile; the assembler later lays the tiles out in order.
+//   * outliers and exceptions, compacted by each warp in code-stream order
+//     into a scratch list at slots taken with one atomic per warp and tile;
+//     the assembler later lays the tiles out in order.
 // HBM traffic: 4 bytes read and 2 bytes written per value.
 #include "fz_internal.cuh"
 
@@ -193,21 +194,21 @@ __device__ __forceinline__ int32_t smem_residual(const int32_t *sq, int row, int
   using S = TileShape<NDIM>;
   constexpr int TXP = S::TX + 8;
   int32_t s = 0;
-  if (NDIM == 3) {
+  if constexpr (NDIM == 3) {
 #pragma unroll
     for (int oz = 0; oz <= K; ++oz)
       if (pz >= oz) s += lz_coef<K>(oz) * sq[(row - 8 * oz) * TXP + col];
-    return s;
+  } else {
+#pragma unroll
+    for (int oy = 0; oy <= (NDIM >= 2 ? K : 0); ++oy)
+#pragma unroll
+      for (int ox = 0; ox <= K; ++ox) {
+        int c = lz_coef<K>(ox);
+        if (NDIM >= 2) c *= lz_coef<K>(oy);
+        const bool ok = px >= ox && py >= oy;
+        s += ok ? c * sq[(row - oy) * TXP + col - ox] : 0;
+      }
   }
-#pragma unroll
-  for (int oy = 0; oy <= (NDIM >= 2 ? K : 0); ++oy)
-#pragma unroll
-    for (int ox = 0; ox <= K; ++ox) {
-      int c = lz_coef<K>(ox);
-      if (NDIM >= 2) c *= lz_coef<K>(oy);
-      const bool ok = px >= ox && py >= oy;
-      s += ok ? c * sq[(row - oy) * TXP + col - ox] : 0;
-    }
   return s;
 }
 
