@@ -1,11 +1,13 @@
 // fz_assemble.cu -- stream assembly: the header, the code-length table and
 // the anchors are copied into their 16-byte aligned sections, the outliers
-// and exceptions are gathered from the quantizer's per-tile scratch slots
-// into code-stream order (slot offsets per tile in k_assemble, the copies in
-// k_gather, a warp per tile), and the alignment gaps are zeroed (the chunk bit
-// lengths and the bitstream were written in place by the encoder).  For a
-// RAW stream the input floats are copied; for a CONST stream the single
-// value is written.
+// and exceptions are gathered from the quantizer's per-warp scratch slots
+// into code-stream order (slot offsets per tile and the list of tiles that
+// hold any in k_assemble; the copies in k_gather, a warp per (tile, block)
+// of those tiles in 3D, else per tile), and the alignment gaps are zeroed
+// (the chunk bit lengths and the bitstream were written in place by the
+// encoder).  For a RAW stream the input floats are copied; for a CONST
+// stream the single value is written.  k_gather, the last kernel of a
+// single-field compress, also copies the call's result to the host.
 #include "fz_internal.cuh"
 
 namespace fz {
