@@ -212,6 +212,49 @@ def test_corrupt_streams_are_rejected_without_fault():
     torch.cuda.synchronize()
 
 
+def test_chunk_length_corruption_is_reported():
+    """One chunk bit length off by one: the work-unit offsets no longer add up
+    to the header's bit total, and the error word reaches the caller (the
+    decoder's last CTA writes it to the host)."""
+    x = synth.grf3d(64, seed=4, device="cuda")
+    buf = fz.compress(x, 1e-4)
+    host = buf.cpu().numpy()
+    hdr = host[:256].tobytes()
+    off_cb = int(np.frombuffer(hdr[160:168], np.uint64)[0])
+    t = host.copy()
+    cb = t[off_cb:off_cb + 4].view(np.uint32)
+    cb[0] += 1
+    with pytest.raises(fz.FzError) as e:
+        fz.decompress(torch.from_numpy(t).cuda(), header=hdr)
+    assert e.value.code == 5
+    # the same context decodes a good stream right after
+    y = fz.decompress(buf)
+    assert float((y.double() - x.double()).abs().max()) <= 1e-4 * (float(x.max()) - float(x.min()))
+
+
+def test_calls_alternating_between_two_streams():
+    """Compress and decompress on two CUDA streams in turn, with host copies
+    queued behind them: every stream and reconstruction equals the
+    default-stream result bit for bit."""
+    x = synth.grf3d(96, seed=6, device="cuda")
+    ref = fz.compress(x, 1e-4)
+    yref = fz.decompress(ref)
+    streams = [torch.cuda.Stream(), torch.cuda.Stream()]
+    outs = []
+    for i in range(6):
+        s = streams[i % 2]
+        s.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(s):
+            xs = x.clone()
+            b = fz.compress(xs, 1e-4, stream=s)
+            y = fz.decompress(b, stream=s)
+            outs.append((b.cpu(), y.cpu()))
+    torch.cuda.synchronize()
+    for b, y in outs:
+        assert torch.equal(b, ref.cpu())
+        assert torch.equal(y.view(torch.int32), yref.cpu().view(torch.int32))
+
+
 def test_bad_arguments():
     x = torch.zeros(100, device="cuda")
     with pytest.raises(fz.FzError) as e:
