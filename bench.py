@@ -51,6 +51,33 @@ NCU_DRAM_BYTES_512 = {"range": 539739136, "quant": 755608320, "encode": 35643494
 METRIC = "compress/decompress GB/s vs HBM peak at REL 1e-4; CR learned vs plain"
 
 
+def _bind_near_gpu(dev_index: int):
+    """Moves this thread to the CPUs of the NUMA node the GPU is attached to
+    (from the PCI device's sysfs entry), so that pinned host memory allocated
+    next is local to the GPU's host link.  Returns (node or None, previous
+    CPU set or None); does nothing where the node or its CPUs are unknown."""
+    try:
+        pr = torch.cuda.get_device_properties(dev_index)
+        addr = f"{pr.pci_domain_id:04x}:{pr.pci_bus_id:02x}:{pr.pci_device_id:02x}.0"
+        with open(f"/sys/bus/pci/devices/{addr}/numa_node") as f:
+            node = int(f.read().strip())
+        if node < 0:
+            return None, None
+        cpus = set()
+        with open(f"/sys/devices/system/node/node{node}/cpulist") as f:
+            for part in f.read().strip().split(","):
+                lo, _, hi = part.partition("-")
+                cpus.update(range(int(lo), int(hi or lo) + 1))
+        prev = os.sched_getaffinity(0)
+        use = cpus & prev
+        if not use:
+            return None, None
+        os.sched_setaffinity(0, use)
+        return node, prev
+    except (OSError, ValueError, AttributeError):
+        return None, None
+
+
 def max_over_ranks(ms: float, world: int, device) -> float:
     """The slowest rank's time (replicas: every rank times its own work)."""
     if world <= 1:
@@ -292,6 +319,9 @@ def run_fz(args, rank, world, local_rank):
     # reconstruction copy to the host overlaps the next step's input copy (the
     # library calls themselves run one after another: each waits for its stream).
     if args.e2e_steps > 0:
+        # pinned host buffers on the GPU's own NUMA node (the thread runs there
+        # while they are allocated and copied): a far node halves the link
+        numa, saved_cpus = _bind_near_gpu(local_rank)
         hx = torch.empty(x.shape, dtype=torch.float32, pin_memory=True)
         hx.copy_(x)
         slots = []
@@ -342,7 +372,9 @@ def run_fz(args, rank, world, local_rank):
         assert ok
         res["e2e"] = {"value": round(aggregate_gbs(args.e2e_steps, world, 4 * N, ems), 2), "unit": "GB/s",
                       "h2d_bytes_per_step": 4 * N + nb, "d2h_bytes_per_step": nb + 4 * N,
-                      "steps": args.e2e_steps, "streams": 2}
+                      "steps": args.e2e_steps, "streams": 2, "host_numa_node": numa}
+        if saved_cpus is not None:
+            os.sched_setaffinity(0, saved_cpus)
     if rank == 0 and world == 1 and not args.no_batch:
         res["batch"] = bench_batch(fz, dev, stream, args)
     if rank == 0 and world == 1 and not args.no_learned:
