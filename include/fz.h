@@ -13,7 +13,9 @@
  * Conventions for every entry point:
  *   - Pointers named d_* are device pointers on the context's device; h_* are
  *     host pointers.  The caller owns all buffers it passes.  The context owns
- *     its workspace (device scratch), which grows on demand.
+ *     its workspace (device scratch), which grows on demand, and a small
+ *     pinned host block into which the last kernel of a compress or
+ *     decompress writes the call's result or error word.
  *   - Fields are float32, C order with x fastest: dims[0] = nx (fastest),
  *     dims[1] = ny, dims[2] = nz.  Unused trailing dims must be 1 or are
  *     ignored beyond ndim.  1 <= ndim <= 3, every dim >= 1, N = prod(dims) <
