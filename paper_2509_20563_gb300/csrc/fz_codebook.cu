@@ -50,23 +50,32 @@ __device__ __forceinline__ uint32_t rank_of(const unsigned long long *a, uint32_
 // of equal weight.  Each level's merge is parallel: every leaf and every
 // package finds its merged position by binary search in the other list.
 // Returns false if no symbol is used.
-__device__ bool build_codebook(CbSmem &s, uint32_t nsym, uint32_t *code_out) {
+__device__ bool build_codebook(CbSmem &s, uint32_t nsym, uint32_t *code_out, uint32_t &my_code) {
   const int t = threadIdx.x, lane = t & 31;
-  // ---- 1. sort keys (count << 10 | symbol); unused symbols sort last
-  s.key[t] = (t < (int)nsym && s.cnt[t]) ? ((s.cnt[t] << 10) | (unsigned long long)t) : ~0ull;
+  // ---- 1. sort keys (count << 10 | symbol); unused symbols sort last.
+  // Bitonic network, one key per thread: partners closer than 32 are in the
+  // same warp (shuffles); farther ones meet in shared memory, alternating
+  // between two arrays so that each step needs one barrier.
+  unsigned long long v = (t < (int)nsym && s.cnt[t]) ? ((s.cnt[t] << 10) | (unsigned long long)t) : ~0ull;
   s.len[t] = 0;
-  __syncthreads();
+  int buf = 0;
   for (int k = 2; k <= kMaxSym; k <<= 1) {
     for (int j = k >> 1; j > 0; j >>= 1) {
-      const int ixj = t ^ j;
-      if (ixj > t) {
-        const bool asc = (t & k) == 0;
-        const unsigned long long a = s.key[t], b = s.key[ixj];
-        if ((a > b) == asc) { s.key[t] = b; s.key[ixj] = a; }
+      unsigned long long o;
+      if (j >= 32) {
+        s.S[buf][t] = v;
+        __syncthreads();
+        o = s.S[buf][t ^ j];
+        buf ^= 1;
+      } else {
+        o = __shfl_xor_sync(0xffffffffu, v, j);
       }
-      __syncthreads();
+      const bool keep_min = ((t & j) == 0) == ((t & k) == 0);
+      v = keep_min ? (v < o ? v : o) : (v < o ? o : v);
     }
   }
+  s.key[t] = v;
+  __syncthreads();
   const uint32_t m = (uint32_t)__syncthreads_count(s.key[t] != ~0ull);
   if (m == 0) return false;
   if ((uint32_t)t < m) {
@@ -160,7 +169,8 @@ __device__ bool build_codebook(CbSmem &s, uint32_t nsym, uint32_t *code_out) {
     }
   }
   __syncthreads();
-  if (t < (int)nsym) code_out[t] = L ? (s.next_code[L] + s.wcnt[warp][L] + rank) : 0u;
+  my_code = L ? (s.next_code[L] + s.wcnt[warp][L] + rank) : 0u;
+  if (code_out && t < (int)nsym) code_out[t] = my_code;
   return true;
 }
 
@@ -196,7 +206,8 @@ __device__ __forceinline__ void codebook_body(const Geom &g, uint32_t R, uint32_
   if (mode == kModeNormal) {
     s.cnt[t] = t < (int)nsym ? ctl->hist[t] : 0ull;
     __syncthreads();
-    bool ok = build_codebook(s, nsym, ctl->enc);
+    uint32_t code = 0;
+    bool ok = build_codebook(s, nsym, nullptr, code);
     __syncthreads();
     if (!ok) {
       if (t == 0) set_err(ctl, FZ_ECORRUPT);
@@ -206,8 +217,8 @@ __device__ __forceinline__ void codebook_body(const Geom &g, uint32_t R, uint32_
     if (t < (int)nsym) {
       uint32_t L = s.len[t];
       ctl->lens[t] = (uint8_t)L;
-      ctl->enc[t] = (L << 24) | ctl->enc[t];
-      b = ctl->hist[t] * (unsigned long long)L;
+      ctl->enc[t] = (L << 24) | code;
+      b = s.cnt[t] * (unsigned long long)L;
     }
     for (int off = 16; off > 0; off >>= 1) b += __shfl_down_sync(0xffffffffu, b, off);
     if ((t & 31) == 0) s.key[t >> 5] = b;  // the sort keys are no longer needed
@@ -337,7 +348,8 @@ __global__ void __launch_bounds__(kCbThreads) k_codebook_only(const uint64_t *hi
   const int t = threadIdx.x;
   s.cnt[t] = t < (int)nsym ? hist[t] : 0ull;
   __syncthreads();
-  bool ok = build_codebook(s, nsym, codes);
+  uint32_t code = 0;
+  bool ok = build_codebook(s, nsym, codes, code);
   __syncthreads();
   if (!ok) {
     if (t == 0) set_err(ctl, FZ_EINVAL);
