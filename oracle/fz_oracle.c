@@ -73,9 +73,9 @@ static float round_down_f32(double d) {
   return f;
 }
 
-/* REL range: minimum and maximum over the finite values of x.  Returns the
- * number of finite values.  Also reports whether every value of x has the same
- * bit pattern (needed for the constant-field stream). */
+/* REL range: minimum and maximum over the finite values of x.  Returns 1 if
+ * x holds a finite value, else 0.  Also reports whether every value of x has
+ * the same bit pattern (needed for the constant-field stream). */
 int orc_range(const float *x, uint64_t n, float *lo, float *hi, int *all_same_bits) {
   uint64_t nf = 0;
   float mn = 0.0f, mx = 0.0f;

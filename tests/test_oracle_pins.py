@@ -33,6 +33,39 @@ def f32(v):
     return np.float32(v)
 
 
+# ---------------------------------------------------------------- value range (§3.2, §4.2)
+@pytest.mark.parametrize("seed", range(8))
+def test_value_range_over_finite_values(seed):
+    """The REL range is the minimum and maximum over the finite values: numpy's
+    nanmin/nanmax after masking the infinities; the same-bits flag is an exact
+    comparison of the bit patterns."""
+    rng = np.random.default_rng(seed)
+    x = (rng.standard_normal(4097) * 10 ** rng.uniform(-3, 3)).astype(np.float32)
+    k = int(rng.integers(0, 40))
+    idx = rng.choice(x.size, size=k, replace=False)
+    x[idx] = rng.choice(np.array([np.nan, np.inf, -np.inf, 0.0, -0.0], np.float32), size=k)
+    anyf, lo, hi, same = oracle.value_range(x)
+    fin = x[np.isfinite(x)]
+    assert anyf == (fin.size > 0)
+    assert lo == fin.min() and hi == fin.max()
+    assert not same
+
+
+def test_value_range_special_cases():
+    # no finite value at all
+    anyf, _, _, same = oracle.value_range(np.array([np.nan, np.inf, -np.inf], np.float32))
+    assert not anyf and not same
+    # a constant field: every bit pattern equal
+    anyf, lo, hi, same = oracle.value_range(np.full(1000, 2.5, np.float32))
+    assert anyf and lo == hi == 2.5 and same
+    # +0 and -0 compare equal but differ in bits: a zero range, not bit-constant
+    anyf, lo, hi, same = oracle.value_range(np.array([0.0, -0.0], np.float32))
+    assert anyf and lo == hi == 0.0 and not same
+    # all NaN with one payload: bit-constant without a finite value
+    anyf, _, _, same = oracle.value_range(np.full(7, np.nan, np.float32))
+    assert not anyf and same
+
+
 # ---------------------------------------------------------------- constants
 @pytest.mark.parametrize("eb_abs", [1e-3, 0.0256, 3.7e-7, 1.0, 12345.678, 2.0 ** -20, 1e30])
 def test_constants_directed_rounding(eb_abs):
