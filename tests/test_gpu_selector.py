@@ -65,6 +65,31 @@ def test_selector_streams_bit_exact(pred, shape):
     assert (np.abs(x[f].astype(np.float64) - y[f]) <= eba).all()
 
 
+def test_selector_subnormal_chain_matches_oracle():
+    """Weights whose logits differ between a fused and an unfused (or
+    reversed) multiply-add chain (worked by hand in
+    tests/golden/mlp_subnormal_chain.txt): the GPU must pick predictor 1 in
+    every block, as the oracle does."""
+    import os
+    w = np.zeros(oracle.NW, np.uint16)
+    with open(os.path.join(os.path.dirname(__file__), "golden", "mlp_subnormal_chain.txt")) as f:
+        for line in f:
+            p = line.split()
+            if p and p[0] == "weight":
+                w[int(p[1])] = int(p[2], 16)
+    x = synth.stitched3d(64, seed=9, region=32, device="cpu")[:40, :37, :70].numpy().copy()
+    ref = oracle.compress(x, 1e-4, predictor="mlp", weights=w)
+    buf = fz.compress(torch.from_numpy(x).cuda(), 1e-4, predictor="mlp",
+                      selector_weights=torch.from_numpy(w.view(np.int16)).cuda())
+    got = buf.cpu().numpy()
+    assert got.size == ref.size and np.array_equal(got, ref)
+    off_ids = int(np.frombuffer(got[144:152].tobytes(), np.uint64)[0])
+    nb = 5 * 5 * 9
+    ids = np.unpackbits(got[off_ids:off_ids + (nb + 3) // 4][:, None], axis=1, bitorder="little")
+    ids = (ids.reshape(-1, 4, 2) * np.array([1, 2])).sum(-1).ravel()[:nb]
+    assert (ids == 1).all()
+
+
 def test_mlp_gradient_matches_oracle():
     rng = np.random.default_rng(2)
     wb = _rand_weights(3)

@@ -230,6 +230,46 @@ def test_canonical_codes_rfc1951_example():
     assert [format(int(c), f"0{int(l)}b") for c, l in zip(codes, lens)] == [r[2] for r in rows]
 
 
+def _golden_cases(name):
+    """Cases of a golden file: a line 'case <id> [nsym=<n>]' opens a case,
+    data rows follow."""
+    cases, cur = [], None
+    with open(os.path.join(GOLD, name)) as f:
+        for line in f:
+            line = line.strip()
+            if not line or line.startswith("#"):
+                continue
+            if line.startswith("case "):
+                parts = line.split()
+                opts = dict(p.split("=") for p in parts[2:])
+                cur = {"id": parts[1], "nsym": int(opts.get("nsym", 0)), "rows": []}
+                cases.append(cur)
+            else:
+                cur["rows"].append(line.split())
+    return cases
+
+
+@pytest.mark.parametrize("case", _golden_cases("huffman_ties.txt"), ids=lambda c: c["id"])
+def test_huffman_ties_hand_derived(case):
+    """Ties between a leaf and a package of equal weight, and between equal
+    counts of different symbols, decide which optimal code is chosen: the
+    lengths and codewords worked by hand in tests/golden/huffman_ties.txt
+    from the stated rule (leaf first on equal weight; leaves by (count,
+    symbol))."""
+    rows = case["rows"]
+    nsym = case["nsym"] or (max(int(r[0]) for r in rows) + 1)
+    counts = np.zeros(nsym, np.uint64)
+    for r in rows:
+        counts[int(r[0])] = int(r[1])
+    ln = oracle.huffman_lengths(counts)
+    codes = oracle.canonical_codes(ln)
+    for r in rows:
+        s = int(r[0])
+        assert int(ln[s]) == int(r[2]), (case["id"], s, int(ln[s]))
+        assert format(int(codes[s]), f"0{int(ln[s])}b") == r[3], (case["id"], s)
+    assert int(ln.sum()) == sum(int(r[2]) for r in rows)  # unused symbols get no code
+
+
 @pytest.mark.parametrize("seed", range(12))
 def test_huffman_optimal_kraft_prefix_free(seed):
     rng = np.random.default_rng(seed)

@@ -213,3 +213,131 @@ def test_selector_streams_roundtrip_and_ids():
     w = _rand_weights(np.random.default_rng(0))
     y = oracle.decompress(oracle.compress(x, eb, predictor="mlp", weights=w))
     assert (np.abs(x.astype(np.float64) - y) <= eb_abs).all()
+
+
+# ---------------------------------------------------------------- hand-worked goldens
+GOLD = __import__("os").path.join(__import__("os").path.dirname(__file__), "golden")
+
+
+def _interp_cases():
+    rows = []
+    with open(GOLD + "/interp_rounding.txt") as f:
+        for line in f:
+            line = line.strip()
+            if line and not line.startswith("#"):
+                rows.append(line.split())
+    return rows
+
+
+@pytest.mark.parametrize("row", _interp_cases(), ids=lambda r: r[0])
+def test_interp_rounding_hand_worked(row):
+    """Odd neighbour sums (linear form) and cubic numerators at or next to a
+    multiple of 16 plus 8, where the rounding constant and the floor of the
+    arithmetic shift decide the prediction: residuals worked by hand in
+    tests/golden/interp_rounding.txt."""
+    name, pred, px, py, pz, want = row[:6]
+    q = np.zeros(512, np.int64)
+    cq = np.zeros(8, np.int32)
+    for a in row[6:]:
+        kind, rest = a.split(":")
+        key, val = rest.split("=")
+        if kind == "q":
+            x, y, z = (int(v) for v in key.split(","))
+            q[(z * 8 + y) * 8 + x] = int(val)
+        else:
+            cq[int(key)] = int(val)
+    d = oracle.interp_block(pred == "cubic", False, q, np.ones(512, np.uint8), cq, np.ones(8, np.uint8))
+    i = (int(pz) * 8 + int(py)) * 8 + int(px)
+    assert int(d[i]) == int(want), (name, int(d[i]))
+    # and the inverse restores q exactly
+    r = oracle.interp_block(pred == "cubic", True, d, np.ones(512, np.uint8), cq, np.ones(8, np.uint8))
+    assert np.array_equal(r, q)
+
+
+def _round_binary(r, mant_bits):
+    """Exact rational r rounded to the binary format with `mant_bits` stored
+    mantissa bits and the binary32 exponent range (subnormals kept), to
+    nearest, ties to even; returns a Fraction."""
+    from fractions import Fraction
+    if r == 0:
+        return Fraction(0)
+    neg = r < 0
+    a = -r if neg else r
+    e = a.numerator.bit_length() - a.denominator.bit_length()
+    if Fraction(2) ** e > a:
+        e -= 1
+    quantum = Fraction(2) ** (max(e, -126) - mant_bits)
+    m = a / quantum
+    qi, rem = divmod(m.numerator, m.denominator)
+    if 2 * rem > m.denominator or (2 * rem == m.denominator and qi % 2 == 1):
+        qi += 1
+    v = qi * quantum
+    return -v if neg else v
+
+
+def _exact_logits(w16, f16):
+    """The selector's inference as a chain of binary32 fused multiply-adds,
+    each one the exact product plus accumulator rounded once (IEEE-754
+    fusedMultiplyAdd), with the hidden layer rounded to bfloat16."""
+    from fractions import Fraction
+    val = lambda h: Fraction(float(np.array([int(h) << 16], np.uint32).view(np.float32)[0]))
+    W = [val(v) for v in w16]
+    F = [val(v) for v in f16]
+    nf, nh = oracle.NFEAT, oracle.NHID
+    h = []
+    for j in range(nh):
+        acc = W[nf * nh + j]
+        for k in range(nf):
+            acc = _round_binary(acc + W[j * nf + k] * F[k], 23)
+        acc = acc if acc > 0 else Fraction(0)
+        h.append(_round_binary(acc, 7))
+    out = []
+    for i in range(oracle.NPRED):
+        acc = W[nf * nh + nh + oracle.NPRED * nh + i]
+        for j in range(nh):
+            acc = _round_binary(acc + W[nf * nh + nh + i * nh + j] * h[j], 23)
+        out.append(np.float32(float(acc)))
+    return np.array(out, np.float32)
+
+
+def test_mlp_subnormal_chain_hand_worked():
+    """The hand-worked case of tests/golden/mlp_subnormal_chain.txt: a
+    product below the subnormal grid makes a fused chain, an unfused one and
+    a reversed one give different logits and different argmax."""
+    w = np.zeros(oracle.NW, np.uint16)
+    want, want_best = {}, None
+    with open(GOLD + "/mlp_subnormal_chain.txt") as f:
+        for line in f:
+            p = line.split()
+            if not p or p[0].startswith("#"):
+                continue
+            if p[0] == "weight":
+                w[int(p[1])] = int(p[2], 16)
+            elif p[0] == "logit":
+                want[int(p[1])] = int(p[2], 16)
+            elif p[0] == "argmax":
+                want_best = int(p[1])
+    rng = np.random.default_rng(1)
+    for _ in range(3):  # the logits do not depend on the features (W1 = 0)
+        f = rng.integers(0, 0x4280, oracle.NFEAT).astype(np.uint16)
+        best, lg = oracle.mlp_infer(w, f)
+        assert [int(v) for v in lg.view(np.uint32)] == [want[i] for i in range(4)]
+        assert best == want_best
+    assert np.array_equal(_exact_logits(w, f).view(np.uint32), lg.view(np.uint32))
+
+
+def test_mlp_inference_is_an_exact_fma_chain():
+    """Random bfloat16 weights and features: the oracle's logits equal, bit
+    for bit, the chain of exactly rounded binary32 fused multiply-adds in
+    index order (which fixes the order of the sums and the rounding of the
+    hidden layer)."""
+    rng = np.random.default_rng(7)
+    for trial in range(6):
+        w32 = (rng.standard_normal(oracle.NW) * 0.3).astype(np.float32)
+        w = torch.from_numpy(w32).to(torch.bfloat16).view(torch.int16).numpy().view(np.uint16)
+        f32 = rng.uniform(0, 24, oracle.NFEAT).astype(np.float32)
+        f = torch.from_numpy(f32).to(torch.bfloat16).view(torch.int16).numpy().view(np.uint16)
+        best, lg = oracle.mlp_infer(w, f)
+        ex = _exact_logits(w, f)
+        assert np.array_equal(ex.view(np.uint32), lg.view(np.uint32)), (trial, ex, lg)
+        assert best == int(np.argmax(ex))
