@@ -64,13 +64,20 @@ typedef enum {
   FZ_SEL_EXHAUSTIVE = 17/* per-block predictor picked by exhaustive trial */
 } fz_predictor;
 
-/* Pipeline description.  Zero-initialise and set struct_size = sizeof(fz_pipeline).
- * A NULL pipeline pointer means: first-order Lorenzo, radius 512. */
+/* Pipeline description: the modules of one pipeline (§3.2-§3.3: predictor,
+ * quantization radius, block shape of the predictor, Huffman chunk size).
+ * Zero-initialise and set struct_size = sizeof(fz_pipeline).  A NULL
+ * pipeline pointer means: first-order Lorenzo, radius 512, default block,
+ * default chunk. */
 typedef struct {
   uint32_t struct_size;
   uint32_t predictor;          /* fz_predictor */
   uint32_t radius;             /* code radius R, 2..512; 0 selects 512 */
-  uint32_t reserved;
+  uint32_t block[3];           /* predictor block extents x, y, z; all 0 = the default for ndim (1D 1024,
+                                  2D 32x32, 3D 8x8x8), which is also the only shape this build accepts
+                                  (others: FZ_EUNSUPPORTED); axes beyond ndim must be 0 or 1 */
+  uint32_t chunk;              /* symbols per Huffman chunk; 0 = the block size */
+  uint32_t reserved;           /* must be 0 */
   const void *selector_weights;/* device pointer to a selector weight blob (FZ_SEL_MLP only) */
 } fz_pipeline;
 
@@ -153,6 +160,18 @@ fz_status fz_decompress(fz_ctx *ctx, const void *d_in, uint64_t in_bytes, const 
  * header. */
 fz_status fz_stream_info(const void *h_header, uint64_t header_bytes, uint32_t *ndim, uint64_t dims[3],
                          double *eb_abs, uint32_t *flags);
+
+/* Validate a host copy of a stream header (at least 256 bytes) against a
+ * stream of stream_bytes bytes without touching the device: magic, version,
+ * dims, flags, radius, predictor, block shape and chunk size, and that
+ * every section lies 16-byte aligned, in order and entirely inside the
+ * stream (no offset or length may reach past stream_bytes, whatever its
+ * value).  fz_decompress, fz_decompress_noalloc and fz_decompress_batch run
+ * the same check before any launch.  The paper defines no stream format;
+ * this is the library's own.  Returns FZ_OK, FZ_ECORRUPT,
+ * FZ_EUNSUPPORTED (flags of a later format) or FZ_EINVAL (null pointer or
+ * stream_bytes < 256). */
+fz_status fz_stream_check(const void *h_header, uint64_t stream_bytes);
 
 /* Stage entry point (prediction + quantization module, §3.1-§3.2): runs the
  * REL range and constants, prequantization, Lorenzo prediction and code
@@ -244,6 +263,25 @@ fz_status fz_ctx_set_profiling(fz_ctx *ctx, int enable);
  * recorded events). */
 fz_status fz_ctx_get_profile(fz_ctx *ctx, fz_profile *out);
 
+/* Bound of every device-side wait of the context's calls (the decoupled
+ * look-back of the encoder and of the decoder's offset pass), in SM clock
+ * cycles; 0 restores the default of 4e9 (about two seconds).  A wait that
+ * runs out records FZ_ETIMEOUT, which the call returns, and the kernel
+ * finishes normally, so the context stays usable.  The look-backs resolve
+ * tiles in the order of a ticket counter, so their waits end by
+ * construction; the bound guards against a corrupted device state.  The
+ * paper describes no device-side waits; this is a library setting.
+ * FZ_EINVAL for a negative value. */
+fz_status fz_ctx_set_spin_limit(fz_ctx *ctx, long long cycles);
+
+/* Self-test of the bounded wait: one warp runs the library's look-back on a
+ * predecessor status word that nothing ever writes, under the context's
+ * spin limit.  Returns FZ_ETIMEOUT when the wait gave up as designed and
+ * the device is still usable; FZ_OK would mean the wait ended without its
+ * predecessor (a defect).  Synchronizes `stream`.  No counterpart in the
+ * paper. */
+fz_status fz_selftest_bounded_wait(fz_ctx *ctx, void *stream);
+
 /* Human-readable name of a status code (static string). */
 const char *fz_status_str(fz_status s);
 
@@ -301,8 +339,9 @@ fz_status fz_decompress_batch(fz_ctx *ctx, uint32_t n, const void *d_in, const u
  * per-block-selection streams give FZ_EUNSUPPORTED.  Runs on the calling
  * thread's current device.  Calls whose device work overlaps (different
  * streams or host threads) race on the shared array and must be ordered by
- * the caller.  The first call on a device looks up the array's address.
- * Synchronizes `stream`. */
+ * the caller.  Every call looks up the array's address on the current
+ * device (cudaGetSymbolAddress, which allocates nothing), so calls remain
+ * valid after the device's context is recreated.  Synchronizes `stream`. */
 #define FZ_NOALLOC_MAX_CHUNKS 65536
 fz_status fz_decompress_noalloc(const void *d_in, uint64_t in_bytes, const void *h_header, float *d_out,
                                 uint64_t out_cap_values, void *stream);

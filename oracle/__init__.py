@@ -104,6 +104,10 @@ def _declare(L):
     L.orc_mlp_loss_grad.restype = C.c_double
     L.orc_mlp_loss_double.argtypes = [C.POINTER(C.c_double), u16p, u8p, C.c_uint64]
     L.orc_mlp_loss_double.restype = C.c_double
+    dp = C.POINTER(C.c_double)
+    L.orc_adam_step.argtypes = [dp, dp, dp, dp, C.c_uint64, C.c_uint32, C.c_double, C.c_double, C.c_double,
+                                C.c_double]
+    L.orc_adam_step.restype = None
     L.orc_field_blocks.argtypes = [f32p, u64p, C.c_uint32, C.c_double, C.c_uint32, u8p, u64p, u16p]
 
 
@@ -329,6 +333,15 @@ def mlp_loss_double(W, feat, labels):
     f = np.ascontiguousarray(feat, dtype=np.uint16)
     lb = np.ascontiguousarray(labels, dtype=np.uint8)
     return lib().orc_mlp_loss_double(W.ctypes.data_as(C.POINTER(C.c_double)), _p(f, u16p), _p(lb, u8p), lb.size)
+
+
+def adam_step(w, g, m, v, t: int, lr: float, beta1: float = 0.9, beta2: float = 0.999, eps: float = 1e-8):
+    """One Adam step in float64; returns the updated (w, m, v) as new arrays."""
+    w, g, m, v = (np.array(a, dtype=np.float64, copy=True).ravel() for a in (w, g, m, v))
+    dp = C.POINTER(C.c_double)
+    lib().orc_adam_step(w.ctypes.data_as(dp), g.ctypes.data_as(dp), m.ctypes.data_as(dp), v.ctypes.data_as(dp),
+                        w.size, int(t), float(lr), float(beta1), float(beta2), float(eps))
+    return w, m, v
 
 
 def field_blocks(x: np.ndarray, eb: float, mode: str = "rel", radius: int = 512):

@@ -734,6 +734,25 @@ double orc_mlp_loss_grad(const uint16_t *w, const uint16_t *feat, const uint8_t 
   return loss / (double)nb;
 }
 
+/* One step of Adam (Kingma and Ba, "Adam: A method for stochastic
+ * optimization", ICLR 2015, Algorithm 1), step number t >= 1, in double, on
+ * n parameters:
+ *   m <- b1 m + (1 - b1) g
+ *   v <- b2 v + (1 - b2) g^2
+ *   mhat = m / (1 - b1^t),  vhat = v / (1 - b2^t)
+ *   w <- w - lr mhat / (sqrt(vhat) + eps)
+ * (the selector's optimizer on its float32 master weights). */
+void orc_adam_step(double *w, const double *g, double *m, double *v, uint64_t n, uint32_t t, double lr, double b1,
+                   double b2, double eps) {
+  const double c1 = 1.0 - pow(b1, (double)t), c2 = 1.0 - pow(b2, (double)t);
+  for (uint64_t i = 0; i < n; i++) {
+    m[i] = b1 * m[i] + (1.0 - b1) * g[i];
+    v[i] = b2 * v[i] + (1.0 - b2) * g[i] * g[i];
+    const double mhat = m[i] / c1, vhat = v[i] / c2;
+    w[i] = w[i] - lr * mhat / (sqrt(vhat) + eps);
+  }
+}
+
 /* The same loss with the weights given as doubles (for finite differences). */
 double orc_mlp_loss_double(const double *W, const uint16_t *feat, const uint8_t *label, uint64_t nb) {
   double loss = 0.0;

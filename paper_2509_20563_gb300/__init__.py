@@ -20,6 +20,7 @@ import torch
 
 __all__ = ["lib", "Context", "compress", "decompress", "lorenzo_quantize", "huffman_codebook", "stream_info",
            "block_report", "mlp_grad", "mlp_adam", "compress_batch", "decompress_batch", "FzError", "HEADER_BYTES",
+           "stream_check", "set_spin_limit", "selftest_bounded_wait",
            "SELECTOR_WEIGHTS"]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -44,7 +45,8 @@ class FzError(RuntimeError):
 
 class Pipeline(C.Structure):
     _fields_ = [("struct_size", C.c_uint32), ("predictor", C.c_uint32), ("radius", C.c_uint32),
-                ("reserved", C.c_uint32), ("selector_weights", C.c_void_p)]
+                ("block", C.c_uint32 * 3), ("chunk", C.c_uint32), ("reserved", C.c_uint32),
+                ("selector_weights", C.c_void_p)]
 
 
 _u64p = C.POINTER(C.c_uint64)
@@ -78,6 +80,9 @@ def _declare(L):
     L.fz_ctx_set_batch_options.argtypes = [_vp, C.c_int, C.c_int]
     L.fz_decompress_noalloc.argtypes = [_vp, C.c_uint64, _vp, _vp, C.c_uint64, _vp]
     L.fz_ctx_set_profiling.argtypes = [_vp, C.c_int]
+    L.fz_stream_check.argtypes = [_vp, C.c_uint64]
+    L.fz_ctx_set_spin_limit.argtypes = [_vp, C.c_longlong]
+    L.fz_selftest_bounded_wait.argtypes = [_vp, _vp]
     L.fz_ctx_get_profile.argtypes = [_vp, _vp]
     for name in ("fz_ctx_create", "fz_ctx_destroy", "fz_compress", "fz_decompress", "fz_stream_info",
                  "fz_lorenzo_quantize", "fz_huffman_codebook", "fz_block_report", "fz_mlp_grad", "fz_mlp_adam",
@@ -145,11 +150,14 @@ def _dims(shape):
     return d
 
 
-def _pipeline(predictor="lorenzo1", radius=512, selector_weights=None) -> Pipeline:
+def _pipeline(predictor="lorenzo1", radius=512, selector_weights=None, chunk=0, block=None) -> Pipeline:
     p = Pipeline()
     p.struct_size = C.sizeof(Pipeline)
     p.predictor = PREDICTORS[predictor] if isinstance(predictor, str) else int(predictor)
     p.radius = int(radius)
+    p.chunk = int(chunk)
+    for a, b in enumerate(block or ()):
+        p.block[a] = int(b)
     p.selector_weights = selector_weights.data_ptr() if selector_weights is not None else None
     return p
 
@@ -164,8 +172,11 @@ def compress_bound(shape) -> int:
 
 
 def compress(x: torch.Tensor, eb: float, mode: str = "rel", predictor="lorenzo1", radius: int = 512,
-             out: torch.Tensor | None = None, stream=None, selector_weights=None) -> torch.Tensor:
+             out: torch.Tensor | None = None, stream=None, selector_weights=None, chunk: int = 0,
+             block=None) -> torch.Tensor:
     """Compress a contiguous float32 CUDA tensor (1-3 dims, last axis fastest).
+    ``chunk`` is the Huffman chunk in symbols (0: the library's default) and
+    ``block`` the predictor block (x, y, z extents; None: the default).
     Returns a uint8 CUDA tensor holding exactly the stream; its host header
     copy is attached as ``.fz_header`` (bytes)."""
     if not (x.is_cuda and x.dtype == torch.float32 and x.is_contiguous()):
@@ -177,7 +188,7 @@ def compress(x: torch.Tensor, eb: float, mode: str = "rel", predictor="lorenzo1"
         out = torch.empty(bound, dtype=torch.uint8, device=x.device)
     nbytes = C.c_uint64()
     hdr = C.create_string_buffer(HEADER_BYTES)
-    pipe = _pipeline(predictor, radius, selector_weights)
+    pipe = _pipeline(predictor, radius, selector_weights, chunk, block)
     st = lib().fz_compress(_ctx(x.device.index or 0).handle, C.c_void_p(x.data_ptr()), x.dim(), _dims(x.shape),
                            1 if mode == "rel" else 0, float(eb), C.byref(pipe), C.c_void_p(out.data_ptr()),
                            out.numel(), C.byref(nbytes), hdr, _stream(stream))
@@ -194,6 +205,25 @@ def stream_info(header: bytes):
            "fz_stream_info")
     shape = tuple(int(dims[a]) for a in range(ndim.value))[::-1]
     return shape, eb_abs.value, flags.value
+
+
+def stream_check(header: bytes, stream_bytes: int) -> int:
+    """Host-only validation of a stream header against a stream length
+    (fz_stream_check); returns the status code (0 = valid)."""
+    buf = C.create_string_buffer(bytes(header[:HEADER_BYTES]), HEADER_BYTES)
+    return int(lib().fz_stream_check(buf, int(stream_bytes)))
+
+
+def set_spin_limit(cycles: int, device: int = 0) -> None:
+    """Bound of the device-side look-back waits of the default context
+    (clock cycles; 0 restores the library default)."""
+    _check(lib().fz_ctx_set_spin_limit(_ctx(device).handle, int(cycles)), "fz_ctx_set_spin_limit")
+
+
+def selftest_bounded_wait(device: int = 0, stream=None) -> int:
+    """Run the bounded-wait self-test (fz_selftest_bounded_wait); returns
+    its status code, FZ_ETIMEOUT (6) when the wait gave up as designed."""
+    return int(lib().fz_selftest_bounded_wait(_ctx(device).handle, _stream(stream)))
 
 
 def decompress(buf: torch.Tensor, out: torch.Tensor | None = None, header: bytes | None = None,

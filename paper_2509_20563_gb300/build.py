@@ -38,7 +38,9 @@ def build(force: bool = False, verbose: bool = False, extra_flags=None) -> str:
     """Compile csrc/*.cu for sm_103a and link libfz.so; returns its path."""
     os.makedirs(OUT, exist_ok=True)
     srcs = sorted(glob.glob(os.path.join(CSRC, "*.cu")))
-    hdrs = sorted(glob.glob(os.path.join(CSRC, "*.cuh"))) + [os.path.join(ROOT, "include", "fz.h")]
+    # every header any translation unit may include: a change to one rebuilds all
+    hdrs = (sorted(glob.glob(os.path.join(CSRC, "*.cuh"))) + sorted(glob.glob(os.path.join(CSRC, "*.h"))) +
+            sorted(glob.glob(os.path.join(ROOT, "include", "*.h"))))
     flags = NVFLAGS + list(extra_flags or [])
     cc = nvcc()
     jobs = []

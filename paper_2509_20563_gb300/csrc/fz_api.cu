@@ -1,6 +1,7 @@
 // fz_api.cu -- the C ABI of libfz.so: argument validation, workspace sizing,
 // launch order of the stage kernels and the final status read-back.  No
 // stage of the compression path runs on the host.
+#include <stddef.h>
 #include <string.h>
 
 #include <new>
@@ -122,18 +123,37 @@ size_t layout_compress(const Geom &g, char *base, CompressWs &ws) {
 
 struct Req {
   uint32_t pred, R;
+  uint32_t chunk;  // 0: the block size
   const uint16_t *weights;
 };
 
 fz_status parse_pipe(const fz_pipeline *pipe, uint32_t ndim, Req &r) {
   r.pred = FZ_PRED_LORENZO1;
   r.R = 512;
+  r.chunk = 0;
   r.weights = nullptr;
   if (pipe) {
     if (pipe->struct_size < sizeof(uint32_t) * 3) return FZ_EINVAL;
     r.pred = pipe->predictor;
     if (pipe->radius) r.R = pipe->radius;
-    if (pipe->struct_size >= sizeof(fz_pipeline)) r.weights = reinterpret_cast<const uint16_t *>(pipe->selector_weights);
+    if (pipe->struct_size >= offsetof(fz_pipeline, reserved)) {
+      const uint64_t d1[3] = {1, 1, 1};
+      Geom g;
+      make_geom(ndim, d1, g);
+      const uint32_t want[3] = {g.bx, g.by, g.bz};
+      const bool dflt = !pipe->block[0] && !pipe->block[1] && !pipe->block[2];
+      for (uint32_t a = 0; a < 3 && !dflt; ++a) {
+        const uint32_t b = pipe->block[a];
+        if (a >= ndim ? b > 1 : b == 0) return FZ_EINVAL;
+        if (a < ndim && b != want[a]) return FZ_EUNSUPPORTED;
+      }
+      r.chunk = pipe->chunk;
+      if (r.chunk && r.chunk != g.bsize) return FZ_EUNSUPPORTED;
+    }
+    if (pipe->struct_size >= sizeof(fz_pipeline)) {
+      if (pipe->reserved) return FZ_EINVAL;
+      r.weights = reinterpret_cast<const uint16_t *>(pipe->selector_weights);
+    }
   }
   if (r.R < 2 || r.R > 512) return FZ_EINVAL;
   switch (r.pred) {
@@ -184,8 +204,12 @@ fz_status check_header(const fz_header &h, uint64_t in_bytes, Geom &g) {
   if (!(h.predictor <= FZ_PRED_INTERP_CUBIC || sel)) return FZ_ECORRUPT;
   if (sel != (h.flags == FZ_FLAG_IDS)) return FZ_ECORRUPT;
   if (h.predictor > FZ_PRED_LORENZO2 && h.ndim != 3) return FZ_ECORRUPT;
+  // every bound below is written so that no sum can wrap around 2^64: an
+  // offset is first checked against the stream length, a length against
+  // what is left of the stream after its offset
+  auto fits = [&](uint64_t off, uint64_t len) { return off <= in_bytes && len <= in_bytes - off; };
   if (sel && (h.off_ids < FZ_HEADER_BYTES + 2ull * h.radius || (h.off_ids & 15u) ||
-              h.off_ids + (h.n_blocks + 3) / 4 > h.off_anchors))
+              !fits(h.off_ids, (h.n_blocks + 3) / 4) || h.off_ids + (h.n_blocks + 3) / 4 > h.off_anchors))
     return FZ_ECORRUPT;
   if (h.block[0] != g.bx || h.block[1] != g.by || h.block[2] != g.bz || h.chunk != g.bsize) return FZ_ECORRUPT;
   if (h.n_blocks != g.n_blocks || h.n_chunks != g.n_blocks) return FZ_ECORRUPT;
@@ -199,6 +223,7 @@ fz_status check_header(const fz_header &h, uint64_t in_bytes, Geom &g) {
   if (h.off_lens != FZ_HEADER_BYTES) return FZ_ECORRUPT;
   for (int i = 0; i < 8; ++i) {
     if (secs[i][0] & 15u) return FZ_ECORRUPT;
+    if (!fits(secs[i][0], secs[i][1])) return FZ_ECORRUPT;
     if (secs[i][0] + secs[i][1] > secs[i + 1][0]) return FZ_ECORRUPT;
   }
   return FZ_OK;
@@ -330,6 +355,14 @@ fz_status fz_stream_info(const void *h_header, uint64_t header_bytes, uint32_t *
   return FZ_OK;
 }
 
+fz_status fz_stream_check(const void *h_header, uint64_t stream_bytes) {
+  if (!h_header || stream_bytes < FZ_HEADER_BYTES) return FZ_EINVAL;
+  fz_header h;
+  memcpy(&h, h_header, sizeof(h));
+  Geom g;
+  return check_header(h, stream_bytes, g);
+}
+
 fz_status fz_compress(fz_ctx *ctx, const float *d_in, uint32_t ndim, const uint64_t dims[3], uint32_t eb_mode,
                       double eb, const fz_pipeline *pipe, void *d_out, uint64_t out_cap, uint64_t *out_bytes,
                       void *h_header, void *stream) {
@@ -352,6 +385,7 @@ fz_status fz_compress(fz_ctx *ctx, const float *d_in, uint32_t ndim, const uint6
   size_t need = layout_compress(g, nullptr, ws);
   if ((st = ensure_ws(ctx, need)) || (st = ensure_pinned(ctx))) return st;
   layout_compress(g, reinterpret_cast<char *>(ctx->ws), ws);
+  ws.spin = ctx->spin_cycles;
   StageClock clk(ctx, s, false);
   if ((st = run_front(ctx, d_in, g, eb_mode, eb, r, ws, s, clk))) return st;
   uint8_t *out = reinterpret_cast<uint8_t *>(d_out);
@@ -423,6 +457,7 @@ fz_status fz_decompress(fz_ctx *ctx, const void *d_in, uint64_t in_bytes, const 
   ws.lut = reinterpret_cast<uint16_t *>(base + o_lut);
   ws.gsum = reinterpret_cast<uint64_t *>(base + o_gsum);
   ws.ofirst = ofirst ? reinterpret_cast<uint32_t *>(base + o_ofirst) : nullptr;
+  ws.spin = ctx->spin_cycles;
   StageClock clk(ctx, s, true);
   if (selpath) {
     e = cudaMemsetAsync(ws.err, 0, 16, s);
@@ -435,6 +470,9 @@ fz_status fz_decompress(fz_ctx *ctx, const void *d_in, uint64_t in_bytes, const 
     // unit offsets, then the decoder (which builds its decode table itself)
     e = cudaMemsetAsync(ws.err, 0, dec_offset_zero_bytes(h), s);
     if (e == cudaSuccess) { e = launch_decode_offsets(in, h, ws, s); clk.mark("dec_offsets", 1); }
+    // blocks without outliers keep ~0 in the table: a corrupt chunk that
+    // decodes an outlier code there is then always reported
+    if (e == cudaSuccess && ofirst) e = cudaMemsetAsync(ws.ofirst, 0xff, 4 * h.n_chunks, s);
     if (e == cudaSuccess && ofirst) { e = launch_outlier_starts(in, h, ws, s, ctx->sm_count); clk.mark("outliers", 1); }
     // the decoder's last CTA writes the error word into the pinned buffer
     ws.h_err = reinterpret_cast<uint32_t *>(ctx->h_pinned);
@@ -558,6 +596,29 @@ fz_status fz_mlp_grad(fz_ctx *ctx, const float *d_weights, const uint16_t *d_fea
     if (e == cudaSuccess) memcpy(h_loss, ctx->h_pinned, 4);
   }
   return from_cuda(e);
+}
+
+fz_status fz_ctx_set_spin_limit(fz_ctx *ctx, long long cycles) {
+  if (!ctx || cycles < 0) return FZ_EINVAL;
+  ctx->spin_cycles = cycles;
+  return FZ_OK;
+}
+
+fz_status fz_selftest_bounded_wait(fz_ctx *ctx, void *stream) {
+  if (!ctx) return FZ_EINVAL;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  if (cudaSetDevice(ctx->device) != cudaSuccess) return FZ_ECUDA;
+  fz_status st;
+  if ((st = ensure_ws(ctx, 256)) || (st = ensure_pinned(ctx))) return st;
+  uint32_t *scratch = reinterpret_cast<uint32_t *>(ctx->ws);
+  cudaError_t e = cudaMemsetAsync(scratch, 0, 32, s);
+  if (e == cudaSuccess) { e = launch_lookback_selftest(scratch, ctx->spin_cycles, s); ctx->launches += 1; }
+  if (e == cudaSuccess) e = cudaMemcpyAsync(ctx->h_pinned, scratch, 4, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return from_cuda(e);
+  uint32_t err = 0;
+  memcpy(&err, ctx->h_pinned, 4);
+  return (fz_status)err;
 }
 
 fz_status fz_mlp_adam(fz_ctx *ctx, float *d_weights, const float *d_grad, float *d_m, float *d_v, uint32_t step,

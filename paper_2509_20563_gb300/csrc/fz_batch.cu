@@ -319,6 +319,7 @@ fz_status fz_compress_batch(fz_ctx *ctx, uint32_t n, const float *const *d_in, c
       J.x = d_in[j];
       J.g = geo[j];
       layout_compress_split(geo[j], dbase + zo, dbase + ro, J.ws, nullptr);
+      J.ws.spin = ctx->spin_cycles;
       zo += zsz[j];
       ro += rsz[j];
       J.eb = eb[j];

@@ -715,7 +715,9 @@ cudaError_t launch_decode_prep(const uint8_t *d_in, const fz_header &h, const De
 
 namespace {
 // First outlier of every block that has outliers (the list ascends by
-// position; blocks without outliers are left untouched and never read).
+// position).  Blocks without outliers keep the ~0 the caller filled in; a
+// decoder that meets an outlier code there finds no outlier at that index
+// and reports a corrupt stream.
 __global__ void k_outlier_starts(const uint32_t *__restrict__ out_idx, uint64_t n_out, uint32_t bsize,
                                  uint64_t n_chunks, uint32_t *ofirst) {
   for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_out;
@@ -743,17 +745,25 @@ constexpr int kOffThreads = 256;  // work units per CTA of k_dec_offsets (one pe
 
 // First bit of every work unit in one pass: thread = unit, the unit's bit
 // total from its 32 chunk lengths (128 contiguous bytes), a CTA scan, and a
-// bounded decoupled look-back over the CTAs (all resident: a few dozen
-// CTAs) for the CTA's base.  The status words follow the error word and
-// the work-unit counter; everything starts at zero.
+// bounded decoupled look-back over the CTAs for the CTA's base.  A CTA's
+// range of units is the ticket it draws from a counter (err[3]) when it
+// starts, not its blockIdx: every predecessor in ticket order has started
+// and will publish, whatever order the hardware dispatches the CTAs in.  The
+// status words follow the error word, the work-unit counter, the CTA
+// counter and the ticket; everything starts at zero.
 __global__ void __launch_bounds__(kOffThreads) k_dec_offsets(const uint32_t *__restrict__ chunk_bits,
                                                              uint64_t n_chunks, uint64_t n_units,
-                                                             uint64_t total_bits, uint64_t *uoff, uint32_t *err) {
+                                                             uint64_t total_bits, uint64_t *uoff, uint32_t *err,
+                                                             long long spin) {
   __shared__ unsigned long long wsum[kOffThreads / 32];
   __shared__ unsigned long long s_base;
+  __shared__ uint32_t s_tile;
   const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
   uint64_t *status = reinterpret_cast<uint64_t *>(err + 4);
-  const uint64_t u = (uint64_t)blockIdx.x * kOffThreads + t;
+  if (t == 0) s_tile = atomicAdd(err + 3, 1u);
+  __syncthreads();
+  const uint32_t tile = s_tile;
+  const uint64_t u = (uint64_t)tile * kOffThreads + t;
   unsigned long long v = 0;
   if (u < n_units) {
     const uint64_t c0 = u * kDecUnit;
@@ -783,17 +793,30 @@ __global__ void __launch_bounds__(kOffThreads) k_dec_offsets(const uint32_t *__r
     tot += wsum[w];
   }
   if (warp == 0) {
-    if (lane == 0) lookback_publish(status, blockIdx.x, tot);
-    const unsigned long long base = lookback_resolve_warp(status, blockIdx.x, tot, err);
+    if (lane == 0) lookback_publish(status, tile, tot);
+    const unsigned long long base = lookback_resolve_warp(status, tile, tot, err, spin);
     if (lane == 0) {
       s_base = base;
-      if (blockIdx.x == gridDim.x - 1 && base + tot != total_bits) dec_err(err, FZ_ECORRUPT);
+      if (tile == gridDim.x - 1 && base + tot != total_bits) dec_err(err, FZ_ECORRUPT);
     }
   }
   __syncthreads();
   if (u < n_units) uoff[u] = s_base + wpre + incl - v;
 }
 }  // namespace
+
+namespace {
+// A look-back whose one predecessor never publishes: the bounded wait must
+// give up after `spin` cycles and record FZ_ETIMEOUT in err[0].
+__global__ void k_lookback_selftest(uint64_t *status, uint32_t *err, long long spin) {
+  lookback_resolve_warp(status, 1, 1, err, spin);
+}
+}  // namespace
+
+cudaError_t launch_lookback_selftest(uint32_t *scratch, long long spin, cudaStream_t s) {
+  k_lookback_selftest<<<1, 32, 0, s>>>(reinterpret_cast<uint64_t *>(scratch + 4), scratch, spin);
+  return cudaGetLastError();
+}
 
 uint64_t dec_offset_zero_bytes(const fz_header &h) {
   return 16 + 8 * ((dec_units_of(h.n_chunks) + kOffThreads - 1) / kOffThreads);
@@ -804,7 +827,8 @@ cudaError_t launch_decode_offsets(const uint8_t *d_in, const fz_header &h, const
   const uint64_t n_units = dec_units_of(n_chunks);
   const uint32_t *cbits = reinterpret_cast<const uint32_t *>(d_in + h.off_chunk_bits);
   const uint64_t grid = (n_units + kOffThreads - 1) / kOffThreads;
-  k_dec_offsets<<<(unsigned)grid, kOffThreads, 0, s>>>(cbits, n_chunks, n_units, h.total_bits, ws.gsum, ws.err);
+  k_dec_offsets<<<(unsigned)grid, kOffThreads, 0, s>>>(cbits, n_chunks, n_units, h.total_bits, ws.gsum, ws.err,
+                                                       ws.spin);
   return cudaGetLastError();
 }
 

@@ -152,7 +152,7 @@ __device__ __forceinline__ void encode_tile(const CompressWs &ws, uint8_t *d_out
         if (r) lw[w0 + 1] |= head << (32 - r);
       }
     }
-    const unsigned long long base = lookback_resolve_warp(ws.estatus, tile, tbits, &ctl->res.err);
+    const unsigned long long base = lookback_resolve_warp(ws.estatus, tile, tbits, &ctl->res.err, ws.spin);
     if (lane == 0) {
       sm.base = base;
       if (tile == n_tiles - 1 && base + tbits != ctl->total_bits) set_err(ctl, FZ_ECORRUPT);
@@ -364,7 +364,7 @@ __global__ void __launch_bounds__(kEncThreads, CH == 512 ? FZ_ENC_MINB : FZ_ENC_
     }
     // ---- the previous tile: its base by look-back, then its words
     if (prev != ~0ull && warp == 0) {
-      const unsigned long long base = lookback_resolve_warp(ws.estatus, prev, prev_bits, &ctl->res.err);
+      const unsigned long long base = lookback_resolve_warp(ws.estatus, prev, prev_bits, &ctl->res.err, ws.spin);
       if (lane == 0) {
         sm.base = base;
         if (prev == n_tiles - 1 && base + prev_bits != ctl->total_bits) set_err(ctl, FZ_ECORRUPT);

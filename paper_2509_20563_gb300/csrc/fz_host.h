@@ -43,6 +43,7 @@ struct fz_ctx {
   std::vector<fz::BatchPlan *> plans;
   bool batch_tuning = true;
   bool batch_graphs = true;
+  long long spin_cycles = 0;  // bound of every look-back wait, in clock cycles (0: the library default)
 };
 
 namespace fz {

@@ -154,7 +154,8 @@ __device__ __forceinline__ void device_constants(double eb_abs, float &ebx2, flo
 // Status word per tile: bits 63..62 = 1 (aggregate) or 2 (inclusive prefix),
 // low 62 bits = value.  Tiles are numbered in the order they are claimed from
 // a ticket counter, so every predecessor is resident or finished and the wait
-// always ends; the clock bound only guards against a corrupted state.
+// always ends; the clock bound (kSpinCycles unless the context sets another)
+// only guards against a corrupted state, and turns it into FZ_ETIMEOUT.
 constexpr uint64_t kLbFlagAgg = 1ull << 62;
 constexpr uint64_t kLbFlagInc = 2ull << 62;
 constexpr uint64_t kLbMask = (1ull << 62) - 1;
@@ -215,8 +216,9 @@ __device__ uint64_t lookback_resolve(uint64_t *status, uint64_t tile, uint64_t a
 // loads per 32 tiles.  All lanes of the warp must call it; returns the
 // exclusive prefix in every lane.
 __device__ __forceinline__ uint64_t lookback_resolve_warp(uint64_t *status, uint64_t tile, uint64_t agg,
-                                                          uint32_t *err) {
+                                                          uint32_t *err, long long spin = 0) {
   const int lane = threadIdx.x & 31;
+  if (spin <= 0) spin = kSpinCycles;
   if (tile == 0) return 0;
   uint64_t excl = 0;
   int64_t hi = (int64_t)tile - 1;  // highest predecessor not yet summed
@@ -231,7 +233,7 @@ __device__ __forceinline__ uint64_t lookback_resolve_warp(uint64_t *status, uint
     const int stop = inc_mask ? __ffs(inc_mask) - 1 : 31;
     const uint32_t missing = __ballot_sync(0xffffffffu, flag == 0 && lane <= stop);
     if (missing) {
-      if (clock64() - t0 > kSpinCycles) { timed_out = true; break; }
+      if (clock64() - t0 > spin) { timed_out = true; break; }
       __nanosleep(32);
       continue;
     }
@@ -330,6 +332,7 @@ struct CompressWs {
   uint64_t cap_list;       // floor(N/8)
   uint8_t *ids;            // per block: predictor id (per-block selection only)
   Result *h_res;           // host-mapped copy of ctl->res written by the last compress kernel (or null)
+  long long spin = 0;      // look-back wait bound in clock cycles (0: kSpinCycles)
 };
 
 // ---------------------------------------------------------------- batched calls
@@ -386,6 +389,7 @@ struct DecodeWs {
   uint32_t *err;           // device error word; err[1] is the work-unit counter (both zeroed per call)
   uint32_t *ofirst = nullptr;  // per block: index of its first outlier (filled when outliers are many)
   uint32_t *h_err = nullptr;   // host-mapped word that receives the final error word (or null)
+  long long spin = 0;          // look-back wait bound in clock cycles (0: kSpinCycles)
 };
 
 inline __host__ __device__ uint64_t dec_units_of(uint64_t n_chunks) { return (n_chunks + kDecUnit - 1) / kDecUnit; }
@@ -400,6 +404,9 @@ cudaError_t launch_decode_offsets(const uint8_t *d_in, const fz_header &h, const
 cudaError_t launch_decode_main(const uint8_t *d_in, const fz_header &h, float *d_out, const DecodeWs &ws,
                                cudaStream_t s, int sm_count);
 cudaError_t launch_fill(float *out, uint64_t n, uint32_t bits, cudaStream_t s, int sm_count);
+// one warp waits on a look-back predecessor that never publishes (scratch:
+// err word at [0], status words from [4], 32 bytes zeroed by the caller)
+cudaError_t launch_lookback_selftest(uint32_t *scratch, long long spin, cudaStream_t s);
 cudaError_t launch_selquant(const float *x, const Geom &g, uint32_t R, uint32_t pred, const CompressWs &ws,
                             const uint16_t *weights, cudaStream_t s, int sm_count);
 cudaError_t launch_select_report(const float *x, const Geom &g, uint32_t R, const CompressWs &ws, uint8_t *labels,

@@ -19,11 +19,10 @@
 // rejected with FZ_EBUFFER before any device work.  Every call on a device
 // shares the one array: calls whose device work overlaps (on different
 // streams, or from different host threads) race on it and must be ordered by
-// the caller.  The first call on each device looks the array's address up
-// (cudaGetSymbolAddress, with that device current); later calls reuse it.
+// the caller.  Every call looks the array's address up with
+// cudaGetSymbolAddress on the current device, so the calls stay valid after
+// the device's context is recreated.
 #include <string.h>
-
-#include <mutex>
 
 #include "fz_host.h"
 
@@ -36,24 +35,18 @@ constexpr size_t kNaScratchBytes = kNaErrBytes + kNaUnitBytes;
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNaScratchBytes];
 
-constexpr int kMaxDevices = 64;
-std::mutex g_mu;
-void *g_ptr[kMaxDevices] = {};
-
-// Device address of the scratch array on the current device.
-fz_status scratch_ptr(int dev, void **out) {
-  if (dev < 0 || dev >= kMaxDevices) return FZ_EUNSUPPORTED;
-  std::lock_guard<std::mutex> lock(g_mu);
-  if (!g_ptr[dev]) {
-    void *p = nullptr;
-    const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-    if (e != cudaSuccess || !p) {
-      cudaGetLastError();
-      return FZ_ECUDA;
-    }
-    g_ptr[dev] = p;
+// Device address of the scratch array in the current device's context.
+// Looked up on every call (a cheap query that allocates nothing): a cached
+// address would go stale if the context were torn down and recreated, for
+// example after cudaDeviceReset, which loads the module at a new address.
+fz_status scratch_ptr(void **out) {
+  void *p = nullptr;
+  const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+  if (e != cudaSuccess || !p) {
+    cudaGetLastError();
+    return FZ_ECUDA;
   }
-  *out = g_ptr[dev];
+  *out = p;
   return FZ_OK;
 }
 
@@ -106,7 +99,7 @@ fz_status fz_decompress_noalloc(const void *d_in, uint64_t in_bytes, const void 
   if (h.predictor > FZ_PRED_LORENZO2) return FZ_EUNSUPPORTED;
   if (h.n_chunks > FZ_NOALLOC_MAX_CHUNKS) return FZ_EBUFFER;
   void *base = nullptr;
-  if ((st = scratch_ptr(dev, &base))) return st;
+  if ((st = scratch_ptr(&base))) return st;
   char *b = reinterpret_cast<char *>(base);
   DecodeWs ws;
   ws.err = reinterpret_cast<uint32_t *>(b);

@@ -153,7 +153,10 @@ cudaError_t launch_mlp_grad(const float *w, const uint16_t *feat, const uint8_t 
 
 cudaError_t launch_adam(float *w, const float *grad, float *m, float *v, uint16_t *w_bf16, uint32_t step, float lr,
                         float beta1, float beta2, float eps, cudaStream_t s) {
-  const float c1 = 1.0f - powf(beta1, (float)step), c2 = 1.0f - powf(beta2, (float)step);
+  // bias corrections 1 - beta^t in double: in float the subtraction cancels
+  // most of the digits of beta^t for small t
+  const float c1 = (float)(1.0 - pow((double)beta1, (double)step));
+  const float c2 = (float)(1.0 - pow((double)beta2, (double)step));
   k_adam<<<(kNWeights + 255) / 256, 256, 0, s>>>(w, grad, m, v, w_bf16, lr, beta1, beta2, eps, c1, c2);
   return cudaGetLastError();
 }

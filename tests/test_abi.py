@@ -86,3 +86,72 @@ def test_batch_bound_and_argument_checks(fzlib):
     assert fzlib.fz_compress_batch(None, 3, None, ndim, dims, 1, None, None, None, 0, offs, None) == 1
     assert fzlib.fz_decompress_batch(None, 0, None, offs, None, None, None) == 1
     assert fzlib.fz_ctx_set_batch_options(None, 1, 1) == 1
+
+
+def _hdr_u64(buf, off, val):
+    b = bytearray(buf)
+    b[off:off + 8] = int(val).to_bytes(8, "little")
+    return bytes(b)
+
+
+def test_stream_check_rejects_wrapping_offsets(fzlib):
+    """fz_stream_check (the validation every decompress runs before any
+    launch) on a valid oracle stream, then with each section offset pushed
+    to a 16-aligned value near 2^64 (where offset + length wraps around and
+    an unsigned chain of sums would pass), and with the stream truncated."""
+    import paper_2509_20563_gb300 as fz
+    import synth
+    x = synth.smooth_nd((20, 30, 40), 1).numpy()
+    buf = oracle.compress(x, 1e-3).tobytes()
+    hdr, n = buf[:256], len(buf)
+    assert fz.stream_check(hdr, n) == 0
+    assert fz.stream_check(hdr, n - 1) == 5          # total_bytes beyond the stream
+    # off_lens 136, off_ids 144, off_anchors 152, off_chunk_bits 160, off_out_idx 168,
+    # off_out_val 176, off_exc_idx 184, off_exc_val 192, off_bits 200
+    for off in (136, 152, 160, 168, 176, 184, 192, 200):
+        for v in ((1 << 64) - 16, (1 << 64) - 4096, 1 << 63, n + 16):
+            assert fz.stream_check(_hdr_u64(hdr, off, v), n) == 5, (off, v)
+    # counts that make a section longer than the stream
+    for off, v in ((112, (1 << 32) - 1), (120, (1 << 32) - 1), (128, 1 << 62)):
+        assert fz.stream_check(_hdr_u64(hdr, off, v), n) == 5, (off, v)
+    assert fz.stream_check(hdr, 255) == 1
+    assert fzlib.fz_stream_check(None, 4096) == 1
+
+
+def test_struct_layout_matches_header(tmp_path):
+    """The ctypes mirror of fz_pipeline and the documented fz_header offsets
+    agree with what a C compiler makes of include/fz.h."""
+    import subprocess
+    import paper_2509_20563_gb300 as fz
+    src = tmp_path / "layout.c"
+    fields_h = ["magic", "version", "flags", "ndim", "eb_mode", "dims", "eb", "eb_abs", "ebx2_bits",
+                "inv2eb_bits", "ebchk_bits", "radius", "block", "predictor", "chunk", "n_blocks", "n_chunks",
+                "n_out", "n_exc", "total_bits", "off_lens", "off_ids", "off_anchors", "off_chunk_bits",
+                "off_out_idx", "off_out_val", "off_exc_idx", "off_exc_val", "off_bits", "total_bytes"]
+    fields_p = ["struct_size", "predictor", "radius", "block", "chunk", "reserved", "selector_weights"]
+    lines = ['#include <stdio.h>', '#include <stddef.h>', f'#include "{ROOT}/include/fz.h"', "int main(void){"]
+    lines += [f'printf("h {f} %zu\\n", offsetof(fz_header, {f}));' for f in fields_h]
+    lines += [f'printf("p {f} %zu\\n", offsetof(fz_pipeline, {f}));' for f in fields_p]
+    lines += ['printf("hs %zu\\nps %zu\\n", sizeof(fz_header), sizeof(fz_pipeline)); return 0;}']
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-std=c11", "-o", str(exe), str(src)], check=True)
+    out = dict((" ".join(l.split()[:-1]), int(l.split()[-1]))
+               for l in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.splitlines())
+    assert out["hs"] == 256
+    assert out["ps"] == C.sizeof(fz.Pipeline)
+    for f in fields_p:
+        assert out[f"p {f}"] == getattr(fz.Pipeline, f).offset, f
+    # the oracle writes the header by byte offset: the same offsets
+    want = {"magic": 0, "version": 4, "flags": 6, "ndim": 8, "eb_mode": 12, "dims": 16, "eb": 40, "eb_abs": 48,
+            "ebx2_bits": 56, "inv2eb_bits": 60, "ebchk_bits": 64, "radius": 68, "block": 72, "predictor": 84,
+            "chunk": 88, "n_blocks": 96, "n_chunks": 104, "n_out": 112, "n_exc": 120, "total_bits": 128,
+            "off_lens": 136, "off_ids": 144, "off_anchors": 152, "off_chunk_bits": 160, "off_out_idx": 168,
+            "off_out_val": 176, "off_exc_idx": 184, "off_exc_val": 192, "off_bits": 200, "total_bytes": 208}
+    for f, o in want.items():
+        assert out[f"h {f}"] == o, f
+
+
+def test_pipeline_and_spin_limit_argument_checks(fzlib):
+    assert fzlib.fz_ctx_set_spin_limit(None, 100) == 1
+    assert fzlib.fz_selftest_bounded_wait(None, None) == 1

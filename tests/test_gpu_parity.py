@@ -6,6 +6,8 @@ oracle's byte for byte and the reconstructions must be bit-identical.  Sizes
 span several quantization/encode/decode tiles and ragged tails; the last
 tests run the full workload sizes of the benchmark.
 """
+import ctypes as C
+
 import numpy as np
 import pytest
 import torch
@@ -175,7 +177,7 @@ def test_codebook_edge_cases():
         fib.append(fib[-1] + fib[-2])
     c = np.zeros(1024, np.int64)
     c[100:145] = fib
-    _codebook_case(c)  # forces the 24-bit length limit
+    _codebook_case(c)  # forces the 14-bit length limit
     c = np.ones(1024, np.int64)
     _codebook_case(c)  # all equal weights: ties everywhere
 
@@ -191,6 +193,18 @@ def test_corrupt_streams_are_rejected_without_fault():
     with pytest.raises(fz.FzError) as e:
         fz.decompress(buf, header=bytes(bad))
     assert e.value.code == 5
+    # section offsets near 2^64 (offset + length wraps around): rejected on
+    # the host before any launch, by every decompress entry point
+    for off in (152, 160, 168, 200):
+        w = bytearray(hdr)
+        w[off:off + 8] = ((1 << 64) - 16).to_bytes(8, "little")
+        with pytest.raises(fz.FzError) as e:
+            fz.decompress(buf, header=bytes(w))
+        assert e.value.code == 5
+        out = torch.empty(x.size, dtype=torch.float32, device="cuda")
+        hb = C.create_string_buffer(bytes(w), 256)
+        assert fz.lib().fz_decompress_noalloc(C.c_void_p(buf.data_ptr()), buf.numel(), hb,
+                                              C.c_void_p(out.data_ptr()), out.numel(), None) == 5
     # over-subscribed code-length table
     t = host.copy()
     t[256:256 + 1024] = 1
@@ -269,18 +283,25 @@ def test_bad_arguments():
 
 
 # ---------------------------------------------------------------- full workload sizes
-def _full_check(x, eb):
-    """GPU stream == oracle stream on the full field; bound on every value."""
+def _full_check(x, eb, predictor="lorenzo1", weights=None):
+    """Full workload size: GPU stream == oracle stream byte for byte, the
+    GPU reconstruction == the oracle's reconstruction bit for bit (the
+    decoder's multi-unit path: every warp claims several work units here),
+    and the bound on every value."""
     xd = x.cuda() if not x.is_cuda else x
-    buf = fz.compress(xd, eb)
+    wd = torch.from_numpy(weights.view(np.int16)).cuda() if weights is not None else None
+    buf = fz.compress(xd, eb, predictor=predictor, selector_weights=wd)
     y = fz.decompress(buf)
     f = xd[torch.isfinite(xd)]
     eba = eb * (float(f.max()) - float(f.min()))
     assert float((y.double() - xd.double()).abs().max()) <= eba
     xh = xd.cpu().numpy()
-    ref = oracle.compress(xh, eb)
+    ref = oracle.compress(xh, eb, predictor=predictor, weights=weights)
     got = buf.cpu().numpy()
     assert got.size == ref.size and np.array_equal(got, ref)
+    del buf
+    yref = oracle.decompress(ref)
+    assert np.array_equal(y.cpu().numpy().view(np.uint32), yref.view(np.uint32))
     return got.size
 
 
@@ -291,9 +312,37 @@ def test_full_512cubed_grf_rel1e4():
 
 
 def test_full_hacc_1d_rel():
+    """All three bounds of the particle workload, plus REL 1e-6 (the paper's
+    Table 3 blanks that entry for this dataset; every bound must succeed
+    here)."""
     x = synth.hacc1d(synth.HACC_N, seed=3, device="cuda")
-    for eb in (1e-2, 1e-4):
+    for eb in (1e-2, 1e-3, 1e-4, 1e-6):
         _full_check(x, eb)
+
+
+def test_bounded_wait_times_out_and_context_survives():
+    """The look-back's bounded wait, on a predecessor that never publishes,
+    gives up after the context's spin limit with FZ_ETIMEOUT; the same
+    context then compresses and decompresses normally."""
+    fz.set_spin_limit(100000)  # about 50 microseconds
+    try:
+        assert fz.selftest_bounded_wait() == 6
+        assert fz.selftest_bounded_wait() == 6
+    finally:
+        fz.set_spin_limit(0)
+    _roundtrip_check(synth.blobs3d((48, 40, 56), seed=3).numpy(), 1e-3)
+
+
+def test_pipeline_block_and_chunk_arguments():
+    """The pipeline's block shape and chunk size: the defaults, written out,
+    give the default stream; other values are rejected before any launch."""
+    x = torch.from_numpy(synth.blobs3d((24, 24, 24), seed=4).numpy()).cuda()
+    ref = fz.compress(x, 1e-3).cpu()
+    assert torch.equal(fz.compress(x, 1e-3, block=(8, 8, 8), chunk=512).cpu(), ref)
+    for kw, code in (({"block": (4, 4, 4)}, 7), ({"block": (8, 8, 0)}, 1), ({"chunk": 300}, 7)):
+        with pytest.raises(fz.FzError) as e:
+            fz.compress(x, 1e-3, **kw)
+        assert e.value.code == code, kw
 
 
 def test_full_cesm_2d_rel():

@@ -115,6 +115,41 @@ def test_mlp_gradient_matches_oracle():
     assert np.array_equal(g2.view(np.uint32), g3.view(np.uint32))
 
 
+def test_adam_step_matches_oracle():
+    """fz_mlp_adam (float32 on the GPU) against the oracle's float64 Adam
+    step (Kingma and Ba 2015, Algorithm 1) over five steps with random
+    gradients.  Tolerance: each float32 operation errs by at most 2^-24
+    relative; the moments take three operations per step and stay below the
+    largest |g| (and g^2), and the step mhat / (sqrt(vhat) + eps) has about
+    ten operations, so |dm| <= 1e-6 max|g|, |dv| <= 1e-6 max g^2 and
+    |dw| <= 2^-22 |w| + 1e-5 lr per step.  The bfloat16 copy is the
+    round-to-nearest-even of the float32 master, bit for bit."""
+    rng = np.random.default_rng(21)
+    n = oracle.NW
+    w0 = (rng.standard_normal(n) * 0.3).astype(np.float32)
+    wd = torch.from_numpy(w0).cuda()
+    md = torch.zeros(n, device="cuda")
+    vd = torch.zeros(n, device="cuda")
+    wb = torch.empty(n, dtype=torch.int16, device="cuda")
+    w, m, v = w0.astype(np.float64), np.zeros(n), np.zeros(n)
+    lr, b1, b2, eps = 3e-3, 0.9, 0.999, 1e-8
+    gmax = 0.0
+    for t in range(1, 6):
+        g = (rng.standard_normal(n) * np.exp(rng.uniform(-6, 1, n))).astype(np.float32)
+        gmax = max(gmax, float(np.abs(g).max()))
+        fz.mlp_adam(wd, torch.from_numpy(g).cuda(), md, vd, t, lr, b1, b2, eps, w_bf16=wb)
+        # the oracle gets exactly the float32 hyper-parameters the kernel sees
+        w, m, v = oracle.adam_step(w, g.astype(np.float64), m, v, t, float(np.float32(lr)),
+                                   float(np.float32(b1)), float(np.float32(b2)), float(np.float32(eps)))
+        torch.cuda.synchronize()
+        wg, mg, vg = wd.cpu().double().numpy(), md.cpu().double().numpy(), vd.cpu().double().numpy()
+        assert np.abs(mg - m).max() <= 1e-6 * gmax, t
+        assert np.abs(vg - v).max() <= 1e-6 * gmax * gmax, t
+        assert (np.abs(wg - w) <= 2.0 ** -22 * np.abs(w) + 1e-5 * lr * t).all(), t
+        want = torch.from_numpy(wd.cpu().numpy()).to(torch.bfloat16).view(torch.int16)
+        assert torch.equal(wb.cpu(), want)
+
+
 def _cr(x, pred, w=None):
     buf = fz.compress(x, 1e-4, predictor=pred, selector_weights=w)
     y = fz.decompress(buf)
@@ -139,3 +174,16 @@ def test_trained_selector_beats_plain_and_tracks_exhaustive():
     print(f"CR plain {cr_plain:.4f} exhaustive {cr_exh:.4f} mlp {cr_mlp:.4f}")
     assert cr_mlp > cr_plain
     assert cr_mlp >= 0.98 * cr_exh
+    # the full 512^3 streams of both selections, with the trained weights,
+    # byte for byte against the oracle, and their reconstructions bit for bit
+    xh = x.cpu().numpy()
+    wh = wb.cpu().numpy().view(np.uint16)
+    for pred, w in (("exhaustive", None), ("mlp", wh)):
+        wd = torch.from_numpy(w.view(np.int16)).cuda() if w is not None else None
+        buf = fz.compress(x, 1e-4, predictor=pred, selector_weights=wd)
+        y = fz.decompress(buf).cpu().numpy()
+        got = buf.cpu().numpy()
+        del buf
+        ref = oracle.compress(xh, 1e-4, predictor=pred, weights=w)
+        assert got.size == ref.size and np.array_equal(got, ref), pred
+        assert np.array_equal(_bits(y), _bits(oracle.decompress(ref))), pred

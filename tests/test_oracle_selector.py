@@ -341,3 +341,42 @@ def test_mlp_inference_is_an_exact_fma_chain():
         ex = _exact_logits(w, f)
         assert np.array_equal(ex.view(np.uint32), lg.view(np.uint32)), (trial, ex, lg)
         assert best == int(np.argmax(ex))
+
+
+# ---------------------------------------------------------------- optimizer (Adam, Kingma and Ba 2015, Alg. 1)
+def test_adam_hand_worked_steps():
+    """Three steps on one parameter, worked in exact decimal arithmetic in
+    tests/golden/adam_steps.txt."""
+    w, m, v = np.ones(1), np.zeros(1), np.zeros(1)
+    with open(GOLD + "/adam_steps.txt") as f:
+        rows = [l.split() for l in f if l.strip() and not l.startswith("#")]
+    for t, g, em, ev, ew in rows:
+        w, m, v = oracle.adam_step(w, [float(g)], m, v, int(t), 0.1, 0.9, 0.999, 1e-8)
+        assert m[0] == pytest.approx(float(em), rel=1e-14)
+        assert v[0] == pytest.approx(float(ev), rel=1e-13)
+        assert w[0] == pytest.approx(float(ew), rel=1e-14)
+
+
+def test_adam_closed_forms():
+    """With a constant gradient g the bias-corrected moments are exactly g and
+    g^2 at every step, so every step moves w by lr g / (|g| + eps); a zero
+    gradient never moves w; the step is invariant to scaling g (up to eps)."""
+    rng = np.random.default_rng(4)
+    n = 257
+    g = rng.standard_normal(n) * np.exp(rng.uniform(-8, 3, n))
+    w0 = rng.standard_normal(n)
+    lr, eps = 1e-2, 1e-8
+    w, m, v = w0.copy(), np.zeros(n), np.zeros(n)
+    for t in range(1, 41):
+        wp = w
+        w, m, v = oracle.adam_step(w, g, m, v, t, lr, 0.9, 0.999, eps)
+        assert np.allclose(m / (1 - 0.9 ** t), g, rtol=1e-12, atol=0)
+        assert np.allclose(v / (1 - 0.999 ** t), g * g, rtol=1e-11, atol=0)
+        assert np.allclose(wp - w, lr * g / (np.abs(g) + eps), rtol=1e-9, atol=1e-15)
+    wz, mz, vz = oracle.adam_step(w0, np.zeros(n), np.zeros(n), np.zeros(n), 1, lr)
+    assert np.array_equal(wz, w0) and not mz.any() and not vz.any()
+    # scale invariance: g and 1000 g give the same step when |g| >> eps
+    big = np.abs(g) > 1e-3
+    w1, _, _ = oracle.adam_step(w0, g, np.zeros(n), np.zeros(n), 1, lr, eps=0.0)
+    w2, _, _ = oracle.adam_step(w0, 1000 * g, np.zeros(n), np.zeros(n), 1, lr, eps=0.0)
+    assert np.allclose(w1[big], w2[big], rtol=1e-14, atol=1e-15)
