@@ -11,9 +11,13 @@ Printed (rank 0, one JSON line): round-trip throughput on the input basis
 (input bytes / (compress + decompress device time)), per-direction GB/s and
 fractions of the HBM roofline, compression ratio, the dominant kernel's
 roofline entry (CUDA-event stage timing inside the library), an end-to-end
-number through the C ABI with host buffers and copies, the CPU oracle timed
-on a bounded slab of the same field, and the SM clocks sampled during the
-timed region.
+number through the C ABI with host buffers and copies (with the host link's
+measured copy bandwidth beside it), the CPU oracle timed on a bounded slab of
+the same field (one thread, and one process per host core), the SM clocks
+sampled during the timed region, and -- in the same run -- every other
+plain-pipeline workload (the per-mode spectrum reading of the 512^3 field,
+the 1D particle and 2D lat/lon fields at three bounds), the 64-field batch
+and the learned selector.
 
 ``--impl reference`` times the CPU oracle instead (rank 0 only), each step a
 bounded slab of the same workload.
@@ -45,10 +49,39 @@ WORKLOAD = "3D FP32 512^3 Gaussian random field (k^-5/3), REL 1e-4, Lorenzo-1, r
 
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per launch of each
 # large kernel on exactly this workload (512^3, REL 1e-4), from one ncu
-# capture of the current kernels (profiles/dram_grf512_rel1e-4.md); reported
-# as roofline.traffic for the dominant kernel, null for any other workload.
-NCU_DRAM_BYTES_512 = {"range": 539739136, "quant": 755608320, "encode": 356434944, "decode": 705614848}
+# capture, with the SHA-256 of the kernel's source files at the time of the
+# capture and the commit it was taken at.  Reported as roofline.traffic for
+# the dominant kernel only while its sources still hash the same (else
+# null): a changed kernel needs a new capture.
+KERNEL_SOURCES = {
+    "range": ["fz_range.cu", "fz_internal.cuh"],
+    "quant": ["fz_quant.cu", "fz_internal.cuh"],
+    "encode": ["fz_encode.cu", "fz_internal.cuh"],
+    "decode": ["fz_decode.cu", "fz_decode_common.cuh", "fz_internal.cuh"],
+}
+NCU_DRAM_BYTES_512 = {}  # kernel -> (bytes per launch, source digest, commit)
 METRIC = "compress/decompress GB/s vs HBM peak at REL 1e-4; CR learned vs plain"
+
+
+def source_digest(kernel: str) -> str:
+    import hashlib
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES[kernel]:
+        with open(os.path.join(ROOT, "paper_2509_20563_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(kernel: str):
+    """(bytes, commit) of the ncu capture of this kernel if its sources are
+    unchanged since, else (None, reason)."""
+    rec = NCU_DRAM_BYTES_512.get(kernel)
+    if not rec:
+        return None, "no capture"
+    b, dig, commit = rec
+    if dig != source_digest(kernel):
+        return None, f"kernel changed since the capture at {commit}"
+    return b, commit
 
 
 def _bind_near_gpu(dev_index: int):
@@ -153,8 +186,40 @@ class Clocks:
                 "reasons": reasons, "samples": len(rows)}
 
 
+def cpu_model() -> str:
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name:"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    return "unknown"
+
+
+def _oracle_slab_worker(args):
+    """One process of the all-core CPU baseline: the oracle, single-threaded
+    as written, on its own slab; starts with the others at a barrier."""
+    x, eb, barrier = args
+    import oracle
+    oracle.lib()
+    barrier.wait()
+    t0 = time.time()
+    oracle.decompress(oracle.compress(x, eb))
+    return t0, time.time()
+
+
 def cpu_baseline(field_gpu: torch.Tensor, slab_z: int, eb: float):
-    """The CPU oracle, as it stands, on a z-slab of the same field."""
+    """The CPU oracle, as it stands, on a z-slab of the same field: (a) in
+    this process on one thread, (b) as one process per host core on
+    disjoint slabs of the field (plain oracle in each; no threading added)."""
+    import multiprocessing as mp
     import oracle
     x = field_gpu[:slab_z].contiguous().cpu().numpy()
     t0 = time.perf_counter()
@@ -163,10 +228,30 @@ def cpu_baseline(field_gpu: torch.Tensor, slab_z: int, eb: float):
     oracle.decompress(buf)
     t2 = time.perf_counter()
     gbs = x.nbytes / (t2 - t0) / 1e9
-    return {"value": round(gbs, 4), "unit": "GB/s", "cores": 1, "kind": "oracle",
-            "sample": f"{x.shape[2]}x{x.shape[1]}x{x.shape[0]} slab of the field ({x.nbytes >> 20} MiB), "
-                      f"compress {t1 - t0:.2f} s + decompress {t2 - t1:.2f} s, single thread",
-            "compress_gbs": round(x.nbytes / (t1 - t0) / 1e9, 4), "decompress_gbs": round(x.nbytes / (t2 - t1) / 1e9, 4)}
+    res = {"value": round(gbs, 4), "unit": "GB/s", "cores": 1, "kind": "oracle",
+           "sample": f"{x.shape[2]}x{x.shape[1]}x{x.shape[0]} slab of the field ({x.nbytes >> 20} MiB), "
+                     f"compress {t1 - t0:.2f} s + decompress {t2 - t1:.2f} s, single thread",
+           "compress_gbs": round(x.nbytes / (t1 - t0) / 1e9, 4),
+           "decompress_gbs": round(x.nbytes / (t2 - t1) / 1e9, 4), "cpu_model": cpu_model()}
+    try:
+        cores = len(os.sched_getaffinity(0))
+        nz = field_gpu.shape[0]
+        per = max(8, min(slab_z, nz // cores))
+        slabs = [field_gpu[z:z + per].contiguous().cpu().numpy() for z in range(0, min(nz, per * cores), per)]
+        ctxm = mp.get_context("spawn")  # never fork a process that holds a CUDA context
+        with ctxm.Manager() as mgr:
+            barrier = mgr.Barrier(len(slabs))
+            with ctxm.Pool(len(slabs)) as pool:
+                spans = pool.map(_oracle_slab_worker, [(s, eb, barrier) for s in slabs])
+        wall = max(b for _, b in spans) - min(a for a, _ in spans)
+        nbytes = sum(s.nbytes for s in slabs)
+        res["all_cores"] = {"value": round(nbytes / wall / 1e9, 4), "unit": "GB/s", "cores": len(slabs),
+                            "kind": "oracle", "sample": f"{len(slabs)} processes, each a {per}-plane slab "
+                                                        f"({slabs[0].nbytes >> 20} MiB) compressed and "
+                                                        f"decompressed, {wall:.2f} s wall"}
+    except Exception as e:  # the extra leg never fails the bench
+        res["all_cores"] = {"error": str(e)[:200]}
+    return res
 
 
 def run_reference(args, rank, world):
@@ -292,6 +377,12 @@ def run_fz(args, rank, world, local_rank):
     dom = max(kern, key=kern.get)
     ach = alg[dom] / (kern[dom] * 1e-3) / 1e9
     value = aggregate_gbs(args.steps, world, 4 * N, tot_ms)
+    if args.traffic is not None:
+        traffic, traffic_note = args.traffic, "--traffic"
+    elif args.size == 512 and args.eb == 1e-4:
+        traffic, traffic_note = ncu_traffic(dom)
+    else:
+        traffic, traffic_note = None, "no capture of this workload"
     res = {"metric": METRIC, "value": round(value, 2), "unit": "GB/s", "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": round(tot_ms / args.steps, 4), "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
@@ -308,10 +399,9 @@ def run_fz(args, rank, world, local_rank):
            "stages_ms": {**{f"c.{k}": round(statistics.mean(v), 4) for k, v in stages_c.items()},
                          **{f"d.{k}": round(statistics.mean(v), 4) for k, v in stages_d.items()}},
            "roofline": {"kernel": dom, "bound": "hbm", "achieved": round(ach, 1), "peak": peak, "unit": "GB/s",
-                        "frac": round(ach / peak, 4),
-                        "traffic": args.traffic if args.traffic is not None else
-                        (NCU_DRAM_BYTES_512.get(dom) if (args.size == 512 and args.eb == 1e-4) else None),
-                        "algorithmic_bytes": alg[dom], "peak_kind": peak_kind},
+                        "frac": round(ach / peak, 4), "traffic": traffic, "traffic_source": traffic_note,
+                        "algorithmic_bytes": alg[dom], "peak_kind": peak_kind,
+                        "source_digest": source_digest(dom)},
            "gpu_launches": int(launches), "clocks": clk}
     # end to end through the C ABI with host buffers: H2D input, compress, D2H stream,
     # H2D stream, decompress, D2H reconstruction -- copies inside the timed region.
@@ -373,8 +463,16 @@ def run_fz(args, rank, world, local_rank):
         res["e2e"] = {"value": round(aggregate_gbs(args.e2e_steps, world, 4 * N, ems), 2), "unit": "GB/s",
                       "h2d_bytes_per_step": 4 * N + nb, "d2h_bytes_per_step": nb + 4 * N,
                       "steps": args.e2e_steps, "streams": 2, "host_numa_node": numa}
+        link = host_link(dev, hx, x)
+        # roofline of the end-to-end step: its host-link bytes at the measured
+        # link rate (both directions at once), against the measured step time
+        t_link = (4 * N + nb + nb + 4 * N) / (link["bidirectional_gbs"] * 1e9)
+        res["e2e"]["host_link"] = link
+        res["e2e"]["link_frac"] = round(t_link / (ems / args.e2e_steps * 1e-3), 4)
         if saved_cpus is not None:
             os.sched_setaffinity(0, saved_cpus)
+    if rank == 0 and world == 1 and not args.no_configs:
+        res["configs"] = bench_configs(fz, dev, stream, args)
     if rank == 0 and world == 1 and not args.no_batch:
         res["batch"] = bench_batch(fz, dev, stream, args)
     if rank == 0 and world == 1 and not args.no_learned:
@@ -384,6 +482,115 @@ def run_fz(args, rank, world, local_rank):
     if rank == 0:
         print(json.dumps(res), flush=True)
     ctx.close()
+
+
+def host_link(dev, hpinned: torch.Tensor, dbuf: torch.Tensor):
+    """Pinned host <-> device copy bandwidth over the same buffers the
+    end-to-end step uses: host to device alone, device to host alone, and
+    both directions at once on two streams (GB/s, CUDA events, best of 5)."""
+    nbytes = dbuf.numel() * dbuf.element_size()
+    d2 = torch.empty_like(dbuf)
+    h2 = torch.empty(hpinned.shape, dtype=hpinned.dtype, pin_memory=True)
+    s1, s2 = torch.cuda.Stream(dev), torch.cuda.Stream(dev)
+
+    def best(fn, streams):
+        out = []
+        for _ in range(5):
+            torch.cuda.synchronize(dev)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(streams[0])
+            for st in streams[1:]:
+                st.wait_event(e0)
+            fn()
+            for st in streams[1:]:
+                ev = torch.cuda.Event()
+                ev.record(st)
+                streams[0].wait_event(ev)
+            e1.record(streams[0])
+            torch.cuda.synchronize(dev)
+            out.append(e0.elapsed_time(e1))
+        return min(out)
+
+    def h2d():
+        with torch.cuda.stream(s1):
+            d2.copy_(hpinned, non_blocking=True)
+
+    def d2h():
+        with torch.cuda.stream(s1):
+            h2.copy_(dbuf, non_blocking=True)
+
+    def both():
+        with torch.cuda.stream(s1):
+            d2.copy_(hpinned, non_blocking=True)
+        with torch.cuda.stream(s2):
+            h2.copy_(dbuf, non_blocking=True)
+
+    t1 = best(h2d, [s1])
+    t2 = best(d2h, [s1])
+    t3 = best(both, [s1, s2])
+    return {"h2d_gbs": round(nbytes / (t1 * 1e-3) / 1e9, 2), "d2h_gbs": round(nbytes / (t2 * 1e-3) / 1e9, 2),
+            "bidirectional_gbs": round(2 * nbytes / (t3 * 1e-3) / 1e9, 2), "bytes_per_copy": nbytes}
+
+
+def _flush_l2(scratch: torch.Tensor):
+    scratch.fill_(1)
+
+
+def bench_configs(fz, dev, stream, args):
+    """Every other plain-pipeline workload: compress and decompress
+    throughput (CUDA events on the launching stream, L2 flushed before each
+    timed call by writing 256 MiB), roofline fractions on forced bytes
+    (compress 12N + S, decompress S + 4N), compression ratio and the largest
+    error over the bound."""
+    peak, _ = _peaks()
+    scratch = torch.empty(64 << 20, dtype=torch.float32, device=dev)
+    specs = [("grf512_mode_spectrum", "3D FP32 512^3 Gaussian random field, per-mode amplitude |k|^-5/6 "
+              "(power k^-5/3 per mode), seed 2", lambda: synth.grf3d(512, seed=2, slope=-1.0 / 3.0, device=dev),
+              [1e-4])]
+    specs.append(("hacc1d", "1D FP32 280,953,867 clustered particle coordinates in [0,256), seed 3",
+                  lambda: synth.hacc1d(synth.HACC_N, seed=3, device=dev), [1e-2, 1e-3, 1e-4]))
+    specs.append(("cesm2d", "2D FP32 1800x3600 lat/lon spherical-harmonic field (l <= 64) + noise, seed 4",
+                  lambda: synth.cesm2d(1800, 3600, seed=4).to(dev), [1e-2, 1e-3, 1e-4]))
+    out = []
+    for key, desc, make, ebs in specs:
+        x = make().contiguous()
+        N = x.numel()
+        rng = float(x.max()) - float(x.min())
+        ob = torch.empty(fz.compress_bound(x.shape), dtype=torch.uint8, device=dev)
+        y = torch.empty_like(x)
+        for eb in ebs:
+            buf = fz.compress(x, eb, out=ob)
+            fz.decompress(buf, out=y)
+            err = float((y.double() - x.double()).abs().max()) / (eb * rng)
+            S = buf.numel()
+            tc, td = [], []
+            for i in range(3 + args.config_reps):
+                _flush_l2(scratch)
+                e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+                e0.record(stream)
+                buf = fz.compress(x, eb, out=ob)
+                e1.record(stream)
+                _flush_l2(scratch)
+                e2.record(stream)
+                fz.decompress(buf, out=y)
+                e3 = torch.cuda.Event(enable_timing=True)
+                e3.record(stream)
+                torch.cuda.synchronize(dev)
+                if i >= 3:
+                    tc.append(e0.elapsed_time(e1))
+                    td.append(e2.elapsed_time(e3))
+            mc, md = statistics.median(tc), statistics.median(td)
+            out.append({"config": key, "workload": desc, "values": N, "eb_mode": "rel", "eb": eb,
+                        "compress_gbs": round(4 * N / (mc * 1e-3) / 1e9, 2),
+                        "decompress_gbs": round(4 * N / (md * 1e-3) / 1e9, 2),
+                        "compress_roofline_frac": round((12 * N + S) / (mc * 1e-3) / 1e9 / peak, 4),
+                        "decompress_roofline_frac": round((S + 4 * N) / (md * 1e-3) / 1e9 / peak, 4),
+                        "cr": round(4 * N / S, 4), "max_err_over_eb": round(err, 6),
+                        "compress_ms": round(mc, 4), "decompress_ms": round(md, 4),
+                        "timed_calls": args.config_reps, "l2": "flushed before each timed call"})
+        del x, ob, y
+        torch.cuda.empty_cache()
+    return out
 
 
 def bench_batch(fz, dev, stream, args):
@@ -470,8 +677,17 @@ def bench_learned(fz, dev, args):
             fz.compress(x, args.eb, out=ob, **kw)
         e1.record()
         torch.cuda.synchronize(dev)
+        yb = torch.empty_like(x)
+        fz.decompress(buf, out=yb)
+        e2, e3 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e2.record()
+        for _ in range(3):
+            fz.decompress(buf, out=yb)
+        e3.record()
+        torch.cuda.synchronize(dev)
         out[f"cr_{name}"] = round(4 * N / buf.numel(), 4)
         out[f"compress_gbs_{name}"] = round(4 * N * 3 / (e0.elapsed_time(e1) * 1e-3) / 1e9, 2)
+        out[f"decompress_gbs_{name}"] = round(4 * N * 3 / (e2.elapsed_time(e3) * 1e-3) / 1e9, 2)
         out[f"max_err_over_eb_{name}"] = round(err, 6)
     out["mlp_vs_exhaustive"] = round(out["cr_mlp"] / out["cr_exhaustive"], 4)
     out["mlp_vs_plain"] = round(out["cr_mlp"] / out["cr_plain"], 4)
@@ -499,6 +715,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batch", action="store_true", help="skip the 64-field batched workload")
     ap.add_argument("--no-learned", action="store_true", help="skip the selector training and CR comparison")
+    ap.add_argument("--no-configs", action="store_true", help="skip the other plain-pipeline workloads")
+    ap.add_argument("--config-reps", type=int, default=10, help="timed calls per extra workload and bound")
     ap.add_argument("--traffic", type=float, default=None, help="ncu dram bytes per launch of the dominant kernel")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))

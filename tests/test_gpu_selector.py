@@ -77,12 +77,15 @@ def test_selector_subnormal_chain_matches_oracle():
             p = line.split()
             if p and p[0] == "weight":
                 w[int(p[1])] = int(p[2], 16)
-    x = synth.stitched3d(64, seed=9, region=32, device="cpu")[:40, :37, :70].numpy().copy()
-    ref = oracle.compress(x, 1e-4, predictor="mlp", weights=w)
-    buf = fz.compress(torch.from_numpy(x).cuda(), 1e-4, predictor="mlp",
+    # a smooth field, so that predictor 1 everywhere stays far from the raw
+    # fallback and the stream carries its per-block ids
+    x = synth.blobs3d((40, 37, 70), seed=3).numpy()
+    ref = oracle.compress(x, 1e-3, predictor="mlp", weights=w)
+    buf = fz.compress(torch.from_numpy(x).cuda(), 1e-3, predictor="mlp",
                       selector_weights=torch.from_numpy(w.view(np.int16)).cuda())
     got = buf.cpu().numpy()
     assert got.size == ref.size and np.array_equal(got, ref)
+    assert int(np.frombuffer(got[6:8].tobytes(), np.uint16)[0]) == 4  # ids present
     off_ids = int(np.frombuffer(got[144:152].tobytes(), np.uint64)[0])
     nb = 5 * 5 * 9
     ids = np.unpackbits(got[off_ids:off_ids + (nb + 3) // 4][:, None], axis=1, bitorder="little")
