@@ -857,9 +857,32 @@ static int write_raw(const float *x, uint64_t n, uint32_t ndim, uint32_t ebmode,
  * eb_mode 0 = ABS, 1 = REL (value range over finite values).  Output is the
  * complete stream; with a per-block choice it carries the 2-bit predictor id
  * of every block. */
+/* Huffman chunk sizes of the format (symbols per chunk; chunk j covers
+ * code-stream symbols [jC, min((j+1)C, Npad))): the block size, a power-of-
+ * two multiple of it up to 4096, or, for 3D, 64 (one 8x8 plane of a block).
+ * The chunking only decides where chunk_bits cuts the bitstream: the
+ * bitstream itself does not depend on C. */
+static int chunk_valid(uint32_t ndim, uint64_t bsize, uint64_t C) {
+  if (C == bsize) return 1;
+  if (ndim == 3 && C == 64) return 1;
+  return C > bsize && C <= 4096 && (C % bsize) == 0 && (C & (C - 1)) == 0;
+}
+
+int orc_compress_chunk(const float *x, uint32_t ndim, const uint64_t dims[3], uint32_t eb_mode, double eb,
+                       uint32_t pred, uint32_t R, const uint16_t *w, uint32_t chunk, uint8_t *out, uint64_t cap,
+                       uint64_t *out_bytes);
+
 int orc_compress_pred(const float *x, uint32_t ndim, const uint64_t dims[3], uint32_t eb_mode, double eb,
                       uint32_t pred, uint32_t R, const uint16_t *w, uint8_t *out, uint64_t cap,
                       uint64_t *out_bytes) {
+  return orc_compress_chunk(x, ndim, dims, eb_mode, eb, pred, R, w, 0, out, cap, out_bytes);
+}
+
+/* The whole compression path with Huffman chunks of `chunk` symbols (0: the
+ * block size). */
+int orc_compress_chunk(const float *x, uint32_t ndim, const uint64_t dims[3], uint32_t eb_mode, double eb,
+                       uint32_t pred, uint32_t R, const uint16_t *w, uint32_t chunk, uint8_t *out, uint64_t cap,
+                       uint64_t *out_bytes) {
   uint64_t n;
   int st = check_args(ndim, dims, &n);
   if (st) return st;
@@ -868,6 +891,11 @@ int orc_compress_pred(const float *x, uint32_t ndim, const uint64_t dims[3], uin
   if (pred >= 2 && ndim != 3) return ORC_EUNSUPPORTED;
   if (pred == 16 && !w) return ORC_EINVAL;
   if (R < 2 || R > 512) return ORC_EINVAL;
+  {
+    uint32_t b[3];
+    orc_block_shape(ndim, b);
+    if (chunk && !chunk_valid(ndim, (uint64_t)b[0] * b[1] * b[2], chunk)) return ORC_EUNSUPPORTED;
+  }
   const int sel = pred >= 16;
   uint64_t dd[3] = {1, 1, 1};
   for (uint32_t a = 0; a < ndim; a++) dd[a] = dims[a];
@@ -980,7 +1008,8 @@ int orc_compress_pred(const float *x, uint32_t ndim, const uint64_t dims[3], uin
   for (uint32_t s = 0; s < nsym; s++) total_bits += hist[s] * len[s];
 
   /* layout */
-  uint64_t n_chunks = g.n_blocks, C = g.bsize;
+  uint64_t C = chunk ? chunk : g.bsize;
+  uint64_t n_chunks = (g.n_blocks * g.bsize + C - 1) / C;
   uint64_t off_lens = HDR;
   uint64_t off_ids = align16(off_lens + nsym);
   uint64_t ids_bytes = sel ? (g.n_blocks + 3) / 4 : 0;
@@ -1045,9 +1074,10 @@ int orc_compress_pred(const float *x, uint32_t ndim, const uint64_t dims[3], uin
   uint32_t *words = (uint32_t *)calloc(n_words + 1, 4);
   if (!words) { st = ORC_ENOMEM; goto done; }
   uint64_t p = 0;
+  const uint64_t npad = g.n_blocks * g.bsize;
   for (uint64_t j = 0; j < n_chunks; j++) {
     uint64_t cb = 0;
-    for (uint64_t i = j * C; i < (j + 1) * C; i++) {
+    for (uint64_t i = j * C; i < (j + 1) * C && i < npad; i++) {
       put_bits(words, p, code[codes[i]], len[codes[i]]);
       p += len[codes[i]];
       cb += len[codes[i]];
@@ -1136,7 +1166,8 @@ int orc_decompress(const uint8_t *in, uint64_t in_bytes, float *out, uint64_t ou
   uint64_t nb = get_u64(in + H_NBLOCKS), nch = get_u64(in + H_NCHUNKS);
   uint64_t n_out = get_u64(in + H_NOUT), n_exc = get_u64(in + H_NEXC), tbits = get_u64(in + H_TBITS);
   uint64_t C = get_u32(in + H_CHUNK);
-  if (nb != g.n_blocks || nch != g.n_blocks || C != g.bsize) return ORC_ECORRUPT;
+  const uint64_t npad = g.n_blocks * g.bsize;
+  if (nb != g.n_blocks || !chunk_valid(ndim, g.bsize, C) || nch != (npad + C - 1) / C) return ORC_ECORRUPT;
   if (n_out > n || n_exc > n) return ORC_ECORRUPT;
   uint64_t o_len = get_u64(in + H_OFF_LENS), o_anch = get_u64(in + H_OFF_ANCH), o_cb = get_u64(in + H_OFF_CBITS);
   uint64_t o_oi = get_u64(in + H_OFF_OIDX), o_ov = get_u64(in + H_OFF_OVAL), o_ei = get_u64(in + H_OFF_EIDX);
@@ -1167,21 +1198,33 @@ int orc_decompress(const uint8_t *in, uint64_t in_bytes, float *out, uint64_t ou
   }
   if (ns == 0) return ORC_ECORRUPT;
   uint32_t *words = (uint32_t *)malloc((n_words + 1) * 4);
+  uint16_t *codes = (uint16_t *)malloc(npad * 2);
   int64_t *v = (int64_t *)malloc(g.bsize * 8);
   int32_t *qb = (int32_t *)malloc(g.bsize * 4);
   uint8_t *inb = (uint8_t *)malloc(g.bsize);
   uint64_t *fidx = (uint64_t *)malloc(g.bsize * 8);
-  if (!words || !v || !qb || !inb || !fidx) { st = ORC_ENOMEM; goto ddone; }
+  if (!words || !codes || !v || !qb || !inb || !fidx) { st = ORC_ENOMEM; goto ddone; }
   for (uint64_t w = 0; w < n_words; w++) words[w] = get_u32(in + o_bits + 4 * w);
+  /* step 11a: the code stream, chunk by chunk; each chunk must use exactly
+   * its stored bit count */
   uint64_t p = 0, oc = 0, ec = 0;
-  for (uint64_t blk = 0; blk < nb; blk++) {
-    uint64_t cb = get_u32(in + o_cb + 4 * blk), p_end = p + cb;
+  for (uint64_t j = 0; j < nch; j++) {
+    uint64_t cb = get_u32(in + o_cb + 4 * j), p_end = p + cb;
     if (p_end > tbits) { st = ORC_ECORRUPT; goto ddone; }
-    gather_block(&g, blk, NULL, qb, inb, fidx);
-    for (uint64_t i = 0; i < g.bsize; i++) {
+    for (uint64_t i = j * C; i < (j + 1) * C && i < npad; i++) {
       uint32_t sym;
       if (decode_one(words, p_end, &p, first, count, base, sorted, &sym)) { st = ORC_ECORRUPT; goto ddone; }
+      codes[i] = (uint16_t)sym;
+    }
+    if (p != p_end) { st = ORC_ECORRUPT; goto ddone; }
+  }
+  /* step 11b: per block, residuals (outliers from their list), anchors,
+   * inverse prediction, dequantization and exceptions */
+  for (uint64_t blk = 0; blk < nb; blk++) {
+    gather_block(&g, blk, NULL, qb, inb, fidx);
+    for (uint64_t i = 0; i < g.bsize; i++) {
       uint64_t pos = blk * g.bsize + i;
+      const uint32_t sym = codes[pos];
       if (sym == 0) {
         if (oc >= n_out || get_u32(in + o_oi + 4 * oc) != pos) { st = ORC_ECORRUPT; goto ddone; }
         v[i] = (int32_t)get_u32(in + o_ov + 4 * oc);
@@ -1190,7 +1233,6 @@ int orc_decompress(const uint8_t *in, uint64_t in_bytes, float *out, uint64_t ou
         v[i] = (int64_t)sym - (int64_t)R;
       }
     }
-    if (p != p_end) { st = ORC_ECORRUPT; goto ddone; }
     v[0] += (int32_t)get_u32(in + o_anch + 4 * blk);
     int pid = sel ? (in[o_ids + (blk >> 2)] >> (2 * (blk & 3))) & 3 : (int)pred;
     if (pid < 2) {
@@ -1220,7 +1262,7 @@ int orc_decompress(const uint8_t *in, uint64_t in_bytes, float *out, uint64_t ou
   }
   if (oc != n_out || ec != n_exc || p != tbits) st = ORC_ECORRUPT;
 ddone:
-  free(words); free(v); free(qb); free(inb); free(fidx);
+  free(words); free(codes); free(v); free(qb); free(inb); free(fidx);
   return st;
 }
 

@@ -148,7 +148,8 @@ fz_status parse_pipe(const fz_pipeline *pipe, uint32_t ndim, Req &r) {
         if (a < ndim && b != want[a]) return FZ_EUNSUPPORTED;
       }
       r.chunk = pipe->chunk;
-      if (r.chunk && r.chunk != g.bsize) return FZ_EUNSUPPORTED;
+      if (r.chunk && !chunk_supported(ndim, g.bsize, r.chunk)) return FZ_EUNSUPPORTED;
+      if (r.chunk && r.chunk != g.bsize && pipe->predictor > FZ_PRED_LORENZO2) return FZ_EUNSUPPORTED;
     }
     if (pipe->struct_size >= sizeof(fz_pipeline)) {
       if (pipe->reserved) return FZ_EINVAL;
@@ -211,8 +212,11 @@ fz_status check_header(const fz_header &h, uint64_t in_bytes, Geom &g) {
   if (sel && (h.off_ids < FZ_HEADER_BYTES + 2ull * h.radius || (h.off_ids & 15u) ||
               !fits(h.off_ids, (h.n_blocks + 3) / 4) || h.off_ids + (h.n_blocks + 3) / 4 > h.off_anchors))
     return FZ_ECORRUPT;
-  if (h.block[0] != g.bx || h.block[1] != g.by || h.block[2] != g.bz || h.chunk != g.bsize) return FZ_ECORRUPT;
-  if (h.n_blocks != g.n_blocks || h.n_chunks != g.n_blocks) return FZ_ECORRUPT;
+  if (h.block[0] != g.bx || h.block[1] != g.by || h.block[2] != g.bz) return FZ_ECORRUPT;
+  if (!chunk_supported(h.ndim, g.bsize, h.chunk)) return FZ_ECORRUPT;
+  if (h.chunk != g.bsize && h.predictor > FZ_PRED_LORENZO2) return FZ_EUNSUPPORTED;
+  set_chunk(g, h.chunk);
+  if (h.n_blocks != g.n_blocks || h.n_chunks != g.n_chunks) return FZ_ECORRUPT;
   if (h.n_out > n || h.n_exc > n || h.total_bits > (uint64_t)kLmax * g.npad) return FZ_ECORRUPT;
   const uint64_t secs[9][2] = {{h.off_lens, sel ? h.off_ids - h.off_lens : 2ull * h.radius},
                                {h.off_anchors, 4 * h.n_blocks},
@@ -381,6 +385,7 @@ fz_status fz_compress(fz_ctx *ctx, const float *d_in, uint32_t ndim, const uint6
   uint64_t d3[3] = {dims[0], ndim >= 2 ? dims[1] : 1, ndim >= 3 ? dims[2] : 1};
   Geom g;
   make_geom(ndim, d3, g);
+  if (r.chunk) set_chunk(g, r.chunk);
   CompressWs ws;
   size_t need = layout_compress(g, nullptr, ws);
   if ((st = ensure_ws(ctx, need)) || (st = ensure_pinned(ctx))) return st;
@@ -447,9 +452,10 @@ fz_status fz_decompress(fz_ctx *ctx, const void *d_in, uint64_t in_bytes, const 
   auto take = [&](size_t bytes) { size_t o = off; off += up(bytes); return o; };
   const bool selpath = h.predictor > FZ_PRED_LORENZO2;
   // a per-block first-outlier table pays off when most blocks hold outliers
-  const bool ofirst = !selpath && h.n_out > h.n_chunks / 8;
+  // plane-parallel streams (64-symbol chunks) locate outliers per plane
+  const bool ofirst = !selpath && h.n_out > h.n_blocks / 8 && !(h.ndim == 3 && h.chunk == 64);
   const size_t o_err = take(dec_offset_zero_bytes(h)), o_gsum = take(8 * n_units), o_lut = take(2u << kLutBits),
-               o_codes = selpath ? take(2 * g.npad) : 0, o_ofirst = ofirst ? take(4 * h.n_chunks) : 0;
+               o_codes = selpath ? take(2 * g.npad) : 0, o_ofirst = ofirst ? take(4 * h.n_blocks) : 0;
   if ((st = ensure_ws(ctx, off))) return st;
   char *base = reinterpret_cast<char *>(ctx->ws);
   DecodeWs ws;
@@ -472,7 +478,7 @@ fz_status fz_decompress(fz_ctx *ctx, const void *d_in, uint64_t in_bytes, const 
     if (e == cudaSuccess) { e = launch_decode_offsets(in, h, ws, s); clk.mark("dec_offsets", 1); }
     // blocks without outliers keep ~0 in the table: a corrupt chunk that
     // decodes an outlier code there is then always reported
-    if (e == cudaSuccess && ofirst) e = cudaMemsetAsync(ws.ofirst, 0xff, 4 * h.n_chunks, s);
+    if (e == cudaSuccess && ofirst) e = cudaMemsetAsync(ws.ofirst, 0xff, 4 * h.n_blocks, s);
     if (e == cudaSuccess && ofirst) { e = launch_outlier_starts(in, h, ws, s, ctx->sm_count); clk.mark("outliers", 1); }
     // the decoder's last CTA writes the error word into the pinned buffer
     ws.h_err = reinterpret_cast<uint32_t *>(ctx->h_pinned);

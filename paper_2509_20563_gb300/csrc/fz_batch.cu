@@ -451,6 +451,7 @@ fz_status fz_decompress_batch(fz_ctx *ctx, uint32_t n, const void *d_in, const u
       if (geo[j].n > max_plain) max_plain = geo[j].n;
     } else {
       if (h.predictor > FZ_PRED_LORENZO2) return FZ_EUNSUPPORTED;
+      if (h.chunk != geo[j].bsize) return FZ_EUNSUPPORTED;  // batched decode: one chunk per block
       const int c = qclass(h.ndim, h.predictor == FZ_PRED_LORENZO2 ? 2 : 1);
       mem[c].push_back((uint32_t)dec.size());
       units[c] += dec_units(h);

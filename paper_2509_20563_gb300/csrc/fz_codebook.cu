@@ -234,7 +234,7 @@ __device__ __forceinline__ void codebook_body(const Geom &g, uint32_t R, uint32_
   fz_header &h = ctl->res.hdr;
   const uint64_t N = g.n;
   if (mode == kModeNormal) {
-    const uint64_t nb = g.n_blocks, nch = g.n_blocks;
+    const uint64_t nb = g.n_blocks, nch = g.n_chunks;
     const uint64_t n_out = ctl->n_out, n_exc = ctl->n_exc, tb = s.total_bits;
     const bool sel = pred == FZ_SEL_MLP || pred == FZ_SEL_EXHAUSTIVE;
     const uint64_t off_lens = FZ_HEADER_BYTES;
@@ -258,7 +258,7 @@ __device__ __forceinline__ void codebook_body(const Geom &g, uint32_t R, uint32_
       h.radius = R;
       h.block[0] = g.bx; h.block[1] = g.by; h.block[2] = g.bz;
       h.predictor = pred;
-      h.chunk = g.bsize;
+      h.chunk = g.chunk;
       h.n_blocks = nb; h.n_chunks = nch; h.n_out = n_out; h.n_exc = n_exc; h.total_bits = tb;
       h.off_lens = off_lens; h.off_ids = sel ? off_ids : 0; h.off_anchors = off_anch; h.off_chunk_bits = off_cb;
       h.off_out_idx = off_oidx; h.off_out_val = off_oval; h.off_exc_idx = off_eidx; h.off_exc_val = off_eval;

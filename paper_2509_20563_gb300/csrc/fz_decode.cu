@@ -503,48 +503,54 @@ __device__ __forceinline__ void consume(const DecParams &p, const Geom &g, Side 
   }
 }
 
-// One chunk (= one block).  The codes are decoded eight at a time, one
+// One chunk: nblk consecutive blocks from jb on (the chunk is one block, or
+// a power-of-two number of blocks), read by one bit reader.  The codes are
+// decoded eight at a time, one
 // group ahead of the reconstruction: the decode of group gi+1 (a serial
 // chain through the bit reader) and the reconstruction of group gi
 // (independent arithmetic and stores) sit in the same straight-line code,
 // so they overlap.  Outliers are looked up per group, off that path.
 template <int NDIM, int K, bool EXC, int T>
 __device__ __forceinline__ void decode_chunk(const DecParams &p, const Geom &g, const uint16_t *slut,
-                                             int32_t *st, uint32_t *ring, uint64_t j, uint64_t start,
-                                             uint32_t cbits, bool vecbase) {
+                                             int32_t *st, uint32_t *ring, uint64_t jb, uint32_t nblk,
+                                             uint64_t start, uint32_t cbits, bool vecbase) {
   constexpr int NG = (NDIM == 3 ? 512 : 1024) / 8;
   bool bad = false;
   BitReader<T> br;
   br.init(p.words, p.n_words, start, cbits, ring);
   const uint32_t start_off = br.off;
-  const uint32_t pos0 = (uint32_t)(j * g.bsize);
-  Side sd;
-  init_side(p, sd, pos0);
-  const int32_t anchor = __ldg(p.anchors + j);
-  const uint32_t j32 = (uint32_t)j;  // blocks number at most nx*ny*nz < 2^32
-  const uint32_t bxi = j32 % g.nbx, jr = j32 / g.nbx;
-  const uint32_t byi = jr % g.nby, bzi = jr / g.nby;
-  const uint32_t X0 = bxi * g.bx, Y0 = byi * g.by, Z0 = bzi * g.bz;
-  for (int i = 0; i < DecState<NDIM, K>::kWords; ++i) st[i * T] = 0;
-  Prefix s;
-  s.r1 = 0;
-  s.r2 = 0;
-#pragma unroll
-  for (int x = 0; x < 8; ++x) { s.Y1[x] = 0; s.Y2[x] = 0; }
-
-  int32_t cur[8];
-  if (br.group8(slut, p.R, cur)) fix_outliers(p, sd, j, pos0, pos0, cur, bad);
-  cur[0] += anchor;  // the block origin's residual is its anchor
 #pragma unroll 1
-  for (int gi = 0; gi < NG - 1; ++gi) {
-    int32_t nxt[8];
-    const bool zero = br.group8(slut, p.R, nxt);
-    consume<NDIM, K, EXC, T>(p, g, sd, s, st, gi, cur, pos0, X0, Y0, Z0, vecbase);
-    if (zero) fix_outliers(p, sd, j, pos0, pos0 + (uint32_t)(gi + 1) * 8, nxt, bad);
+  for (uint32_t bi = 0; bi < nblk; ++bi) {
+    const uint64_t j = jb + bi;
+    const uint32_t pos0 = (uint32_t)(j * g.bsize);
+    Side sd;
+    init_side(p, sd, pos0);
+    const int32_t anchor = __ldg(p.anchors + j);
+    const uint32_t j32 = (uint32_t)j;  // blocks number at most nx*ny*nz < 2^32
+    const uint32_t bxi = j32 % g.nbx, jr = j32 / g.nbx;
+    const uint32_t byi = jr % g.nby, bzi = jr / g.nby;
+    const uint32_t X0 = bxi * g.bx, Y0 = byi * g.by, Z0 = bzi * g.bz;
+    for (int i = 0; i < DecState<NDIM, K>::kWords; ++i) st[i * T] = 0;
+    Prefix s;
+    s.r1 = 0;
+    s.r2 = 0;
 #pragma unroll
-    for (int u = 0; u < 8; ++u) cur[u] = nxt[u];
+    for (int x = 0; x < 8; ++x) { s.Y1[x] = 0; s.Y2[x] = 0; }
+
+    int32_t cur[8];
+    if (br.group8(slut, p.R, cur)) fix_outliers(p, sd, j, pos0, pos0, cur, bad);
+    cur[0] += anchor;  // the block origin's residual is its anchor
+#pragma unroll 1
+    for (int gi = 0; gi < NG - 1; ++gi) {
+      int32_t nxt[8];
+      const bool zero = br.group8(slut, p.R, nxt);
+      consume<NDIM, K, EXC, T>(p, g, sd, s, st, gi, cur, pos0, X0, Y0, Z0, vecbase);
+      if (zero) fix_outliers(p, sd, j, pos0, pos0 + (uint32_t)(gi + 1) * 8, nxt, bad);
+#pragma unroll
+      for (int u = 0; u < 8; ++u) cur[u] = nxt[u];
+    }
+    consume<NDIM, K, EXC, T>(p, g, sd, s, st, NG - 1, cur, pos0, X0, Y0, Z0, vecbase);
   }
-  consume<NDIM, K, EXC, T>(p, g, sd, s, st, NG - 1, cur, pos0, X0, Y0, Z0, vecbase);
   asm volatile("cp.async.wait_all;\n" ::: "memory");  // the ring is reused by the next chunk
   if (br.consumed(start_off) != cbits || bad) dec_err(p.err, FZ_ECORRUPT);
 }
@@ -567,10 +573,204 @@ __device__ __forceinline__ void decode_units(const DecParams &p, const Geom &g, 
     const uint64_t start = unit_start(p.chunk_bits, p.goff, p.n_chunks, u, cb);
     const uint64_t j = (uint64_t)u * kDecUnit + lane;
     if (j < p.n_chunks) {
-      if (p.n_exc) decode_chunk<NDIM, K, true, T>(p, g, slut, sstate + t, sring + t, j, start, cb, vecbase);
-      else decode_chunk<NDIM, K, false, T>(p, g, slut, sstate + t, sring + t, j, start, cb, vecbase);
+      // a chunk of k >= 1 whole blocks (the last one may hold fewer)
+      const uint32_t k = g.chunk / g.bsize;
+      const uint64_t jb = j * k;
+      const uint32_t nblk = (uint32_t)(g.n_blocks - jb < k ? g.n_blocks - jb : k);
+      if (p.n_exc) decode_chunk<NDIM, K, true, T>(p, g, slut, sstate + t, sring + t, jb, nblk, start, cb, vecbase);
+      else decode_chunk<NDIM, K, false, T>(p, g, slut, sstate + t, sring + t, jb, nblk, start, cb, vecbase);
     }
   }
+}
+
+// ---------------------------------------------------------------- 64-symbol chunks (3D)
+// A stream whose Huffman chunk is one 8x8 plane of a block (64 symbols) is
+// decoded plane-parallel: a work unit of 32 chunks is 4 blocks x 8 planes,
+// lane l of the warp decodes plane l & 7 of block 4u + (l >> 3).  Per row
+// y, each lane forms the x and y prefix sums of its plane's row (the first
+// two of the three inverse-Lorenzo sums); an 8x8 transpose through a small
+// per-warp shared tile then gives lane (group, x) the eight planes' values
+// at column x, whose prefix sum along z completes the inverse in
+// registers.  So no lane keeps a plane of prefix state (the one-block-per-
+// lane decoder needs 256 bytes of it per thread), and the eight stores of a
+// row (one per z) each cover 4 blocks x 8 floats of one field row.
+// Exceptions are written by k_exc_scatter afterwards.
+#ifndef FZ_DEC_TP
+#define FZ_DEC_TP 768
+#endif
+constexpr int kPlaneT = FZ_DEC_TP;
+constexpr int kPlaneTile = 4 * 72;  // per warp: 4 blocks x (8 planes x 8 values + 8 words of padding)
+
+template <int K, int T>
+__device__ __forceinline__ void decode_plane_unit(const DecParams &p, const Geom &g, const uint16_t *slut,
+                                                  uint32_t *ring, int32_t *tile, uint64_t u) {
+  const int lane = threadIdx.x & 31, zpl = lane & 7, grp = lane >> 3;
+  uint32_t cb;
+  const uint64_t start = unit_start(p.chunk_bits, p.goff, p.n_chunks, u, cb);
+  const uint64_t j = u * kDecUnit + (uint64_t)lane;
+  const bool valid = j < p.n_chunks;  // n_chunks is 8 n_blocks: a block's 8 lanes agree
+  const uint64_t blk = valid ? j >> 3 : 0;
+  bool bad = false;
+  BitReader<T> br;
+  br.init(p.words, p.n_words, valid ? start : 0, valid ? cb : 0, ring);
+  const uint32_t start_off = br.off;
+  const uint32_t pos0 = (uint32_t)(blk * 512u) + (uint32_t)zpl * 64u;  // this lane's plane
+  Side sd;
+  sd.oc = ~0ull;
+  sd.next_o = 0xffffffffu;
+  sd.next_v = 0;
+  const uint32_t b32 = (uint32_t)blk;
+  const uint32_t bxi = b32 % g.nbx, br_ = b32 / g.nbx;
+  const uint32_t byi = br_ % g.nby, bzi = br_ / g.nby;
+  const uint32_t X0 = bxi * 8u, Y0 = byi * 8u, Z0 = bzi * 8u;
+  // after the transpose this lane writes column x = zpl of the block
+  const bool xin = valid && X0 + (uint32_t)zpl < g.nx;
+  const uint32_t nz_in = g.nz - Z0 < 8u ? g.nz - Z0 : 8u;
+  const uint64_t plane = (uint64_t)g.ny * g.nx;
+  int32_t Y1[8], Y2[8];
+#pragma unroll
+  for (int x = 0; x < 8; ++x) { Y1[x] = 0; Y2[x] = 0; }
+  int32_t *trow = tile + grp * 72;
+  int32_t cur[8];
+  if (br.group8(slut, p.R, cur)) fix_outliers(p, sd, blk, pos0, pos0, cur, bad);
+  if (zpl == 0 && valid) cur[0] += __ldg(p.anchors + blk);  // the block origin's residual is its anchor
+#pragma unroll 1
+  for (int y = 0; y < 8; ++y) {
+    int32_t nxt[8];
+    bool zn = false;
+    if (y < 7) zn = br.group8(slut, p.R, nxt);
+    // x and y prefix sums of this plane's row y
+    int32_t v[8], r1 = 0, r2 = 0;
+#pragma unroll
+    for (int x = 0; x < 8; ++x) {
+      r1 += cur[x];
+      if (K == 1) {
+        Y1[x] += r1;
+        v[x] = Y1[x];
+      } else {
+        r2 += r1;
+        Y1[x] += r2;
+        Y2[x] += Y1[x];
+        v[x] = Y2[x];
+      }
+    }
+    // transpose within the block's 8 lanes: lane (grp, x) gets w[z]
+    __syncwarp();
+    reinterpret_cast<int4 *>(trow + zpl * 8)[0] = make_int4(v[0], v[1], v[2], v[3]);
+    reinterpret_cast<int4 *>(trow + zpl * 8)[1] = make_int4(v[4], v[5], v[6], v[7]);
+    __syncwarp();
+    int32_t w[8];
+#pragma unroll
+    for (int z = 0; z < 8; ++z) w[z] = trow[z * 8 + zpl];
+    // z prefix sum(s), dequantization and the row's eight stores
+#pragma unroll
+    for (int z = 1; z < 8; ++z) w[z] += w[z - 1];
+    if (K == 2) {
+#pragma unroll
+      for (int z = 1; z < 8; ++z) w[z] += w[z - 1];
+    }
+    if (xin && Y0 + (uint32_t)y < g.ny) {
+      uint64_t f = ((uint64_t)Z0 * g.ny + Y0 + (uint32_t)y) * g.nx + X0 + (uint32_t)zpl;
+#pragma unroll
+      for (int z = 0; z < 8; ++z) {
+        if ((uint32_t)z < nz_in) p.out[f] = __fmul_rn(__int2float_rn(w[z]), p.ebx2);
+        f += plane;
+      }
+    }
+    if (y < 7) {
+      if (zn) fix_outliers(p, sd, blk, pos0, pos0 + (uint32_t)(y + 1) * 8u, nxt, bad);
+#pragma unroll
+      for (int x = 0; x < 8; ++x) cur[x] = nxt[x];
+    }
+  }
+  asm volatile("cp.async.wait_all;\n" ::: "memory");  // the ring is reused by the next unit
+  if (valid && (br.consumed(start_off) != cb || bad)) dec_err(p.err, FZ_ECORRUPT);
+}
+
+// One CTA per SM, as k_decode: every CTA builds the decode table, every warp
+// claims work units from the counter.
+template <int K>
+__global__ void __launch_bounds__(kPlaneT, 1) k_decode_planes(DecParams p, Geom g) {
+  constexpr int T = kPlaneT;
+  extern __shared__ __align__(16) unsigned char d_smem[];
+  uint16_t *slut = reinterpret_cast<uint16_t *>(d_smem);
+  uint32_t *sring = reinterpret_cast<uint32_t *>(d_smem + sizeof(uint16_t) * kLutSize);
+  int32_t *stile = reinterpret_cast<int32_t *>(sring + kRing * T);
+  __shared__ LutBuild lb;
+  const int t = threadIdx.x;
+  if (build_lut<T>(p.lens, p.nsym, slut, lb)) {
+    __syncthreads();
+    int32_t *tile = stile + (t >> 5) * kPlaneTile;
+    for (;;) {
+      const uint32_t u = claim_unit(p.err + 1);
+      if (u >= p.n_units) break;
+      decode_plane_unit<K, T>(p, g, slut, sring + t, tile, u);
+    }
+  } else if (t == 0) {
+    dec_err(p.err, FZ_ECORRUPT);
+  }
+  __syncthreads();
+  if (p.h_err && t == 0) {
+    __threadfence();
+    if (atomicAdd(p.err + 2, 1u) == gridDim.x - 1) {
+      __threadfence();
+      *reinterpret_cast<volatile uint32_t *>(p.h_err) = atomicAdd(p.err, 0u);
+      __threadfence_system();
+    }
+  }
+}
+
+constexpr size_t plane_smem_bytes() {
+  return sizeof(uint16_t) * kLutSize + sizeof(uint32_t) * kRing * kPlaneT +
+         sizeof(int32_t) * kPlaneTile * (kPlaneT / 32);
+}
+
+// Exceptions of a stream decoded plane-parallel: each stored value
+// overwrites its position (code-stream index in 8x8x8 blocks -> field
+// index).  The list must ascend strictly and name in-domain points.  The
+// last CTA hands the error word to the host when asked.
+__global__ void k_exc_scatter(const uint32_t *__restrict__ exc_idx, const uint32_t *__restrict__ exc_val,
+                              uint64_t n_exc, Geom g, float *out, uint32_t *err, uint32_t *h_err) {
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_exc;
+       i += (uint64_t)gridDim.x * blockDim.x) {
+    const uint32_t pos = __ldg(exc_idx + i);
+    const uint32_t b = pos >> 9, w = pos & 511u;
+    const uint32_t x = (b % g.nbx) * 8u + (w & 7u), r = b / g.nbx;
+    const uint32_t y = (r % g.nby) * 8u + ((w >> 3) & 7u), z = (r / g.nby) * 8u + (w >> 6);
+    const bool ok = (uint64_t)b < g.n_blocks && x < g.nx && y < g.ny && z < g.nz &&
+                    (i == 0 || __ldg(exc_idx + i - 1) < pos);
+    if (ok) out[((uint64_t)z * g.ny + y) * g.nx + x] = __uint_as_float(__ldg(exc_val + i));
+    else dec_err(err, FZ_ECORRUPT);
+  }
+  __syncthreads();
+  if (h_err && threadIdx.x == 0) {
+    __threadfence();
+    if (atomicAdd(err + 2, 1u) == gridDim.x - 1) {
+      __threadfence();
+      *reinterpret_cast<volatile uint32_t *>(h_err) = atomicAdd(err, 0u);
+      __threadfence_system();
+    }
+  }
+}
+
+template <int K>
+cudaError_t launch_planes_t(const DecParams &p, const Geom &g, int sm_count, cudaStream_t s) {
+  const int smem = (int)plane_smem_bytes();
+  static LaunchCache cache;
+  int per_sm = 0;
+  const cudaError_t e = cached_per_sm(k_decode_planes<K>, kPlaneT, smem, cache, per_sm);
+  if (e != cudaSuccess) return e;
+  uint64_t grid = (uint64_t)sm_count * per_sm;
+  if (grid > p.n_units) grid = p.n_units;
+  DecParams q = p;
+  if (p.n_exc) q.h_err = nullptr;  // the exception pass reports instead
+  k_decode_planes<K><<<(unsigned)grid, kPlaneT, smem, s>>>(q, g);
+  cudaError_t e2 = cudaGetLastError();
+  if (e2 != cudaSuccess || !p.n_exc) return e2;
+  uint64_t eg = (p.n_exc + 255) / 256;
+  if (eg > (uint64_t)sm_count * 4) eg = (uint64_t)sm_count * 4;
+  k_exc_scatter<<<(unsigned)eg, 256, 0, s>>>(p.exc_idx, p.exc_val, p.n_exc, g, p.out, p.err, p.h_err);
+  return cudaGetLastError();
 }
 
 template <int T>
@@ -678,8 +878,8 @@ __global__ void __launch_bounds__(DecCta<NDIM, K>::T, 1) k_decode_batch(const De
       const uint64_t start = unit_start(sp.chunk_bits, sp.goff, sp.n_chunks, u, cb);
       const uint64_t j = u * kDecUnit + (t & 31);
       if (j < sp.n_chunks) {
-        if (sp.n_exc) decode_chunk<NDIM, K, true, T>(sp, sg, slut, sstate + t, sring + t, j, start, cb, vecbase);
-        else decode_chunk<NDIM, K, false, T>(sp, sg, slut, sstate + t, sring + t, j, start, cb, vecbase);
+        if (sp.n_exc) decode_chunk<NDIM, K, true, T>(sp, sg, slut, sstate + t, sring + t, j, 1, start, cb, vecbase);
+        else decode_chunk<NDIM, K, false, T>(sp, sg, slut, sstate + t, sring + t, j, 1, start, cb, vecbase);
       }
     }
     r = t1;
@@ -719,11 +919,11 @@ namespace {
 // decoder that meets an outlier code there finds no outlier at that index
 // and reports a corrupt stream.
 __global__ void k_outlier_starts(const uint32_t *__restrict__ out_idx, uint64_t n_out, uint32_t bsize,
-                                 uint64_t n_chunks, uint32_t *ofirst) {
+                                 uint64_t n_blocks, uint32_t *ofirst) {
   for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_out;
        i += (uint64_t)gridDim.x * blockDim.x) {
     const uint32_t c = __ldg(out_idx + i) / bsize;
-    if (c < n_chunks && (i == 0 || __ldg(out_idx + i - 1) / bsize != c)) ofirst[c] = (uint32_t)i;
+    if (c < n_blocks && (i == 0 || __ldg(out_idx + i - 1) / bsize != c)) ofirst[c] = (uint32_t)i;
   }
 }
 }  // namespace
@@ -736,7 +936,7 @@ cudaError_t launch_outlier_starts(const uint8_t *d_in, const fz_header &h, const
   if (grid > (uint64_t)sm_count * 8) grid = (uint64_t)sm_count * 8;
   if (grid < 1) grid = 1;
   k_outlier_starts<<<(unsigned)grid, 256, 0, s>>>(reinterpret_cast<const uint32_t *>(d_in + h.off_out_idx), h.n_out,
-                                                  g.bsize, h.n_chunks, ws.ofirst);
+                                                  g.bsize, h.n_blocks, ws.ofirst);
   return cudaGetLastError();
 }
 
@@ -836,6 +1036,7 @@ cudaError_t launch_decode_main(const uint8_t *d_in, const fz_header &h, float *d
                                cudaStream_t s, int sm_count) {
   Geom g;
   make_geom(h.ndim, h.dims, g);
+  set_chunk(g, h.chunk);
   DecParams p;
   p.words = reinterpret_cast<const uint32_t *>(d_in + h.off_bits);
   p.n_words = (h.total_bits + 31) / 32;
@@ -861,6 +1062,10 @@ cudaError_t launch_decode_main(const uint8_t *d_in, const fz_header &h, float *d
   memcpy(&p.ebx2, &h.ebx2_bits, 4);
   p.R = (int32_t)h.radius;
   const bool k2 = h.predictor == FZ_PRED_LORENZO2;
+  if (g.ndim == 3 && g.chunk == 64) {
+    p.ofirst = nullptr;  // outliers are located per plane by search
+    return k2 ? launch_planes_t<2>(p, g, sm_count, s) : launch_planes_t<1>(p, g, sm_count, s);
+  }
   switch (g.ndim) {
     case 1: return k2 ? launch_dec_t<1, 2>(p, g, sm_count, s) : launch_dec_t<1, 1>(p, g, sm_count, s);
     case 2: return k2 ? launch_dec_t<2, 2>(p, g, sm_count, s) : launch_dec_t<2, 1>(p, g, sm_count, s);

@@ -45,10 +45,34 @@ struct EncSmem {
   unsigned long long base;
 };
 
+// Stored chunk lengths below one block: with 64-symbol chunks in 512-symbol
+// blocks (16 codes per lane) the lanes 4s..4s+3 hold sub-chunk s, and the
+// last of them stores the difference of the inclusive scan.  Every lane of
+// the warp calls it.
+template <int PER>
+__device__ __forceinline__ void store_sub_chunks(uint32_t *chunk_bits, uint64_t block, uint32_t incl, int lane,
+                                                 uint32_t chunk, bool valid) {
+  if (PER != 16 || chunk != 64) return;
+  const uint32_t prev = __shfl_up_sync(0xffffffffu, incl, 4);
+  if (valid && (lane & 3) == 3) chunk_bits[block * 8 + (lane >> 2)] = lane >= 4 ? incl - prev : incl;
+}
+
+// Stored chunk lengths above one block (chunk = k blocks, k = 2, 4, 8 divides
+// the tile's 8 blocks): the first 8 / k threads each add up the bit totals
+// of k consecutive blocks of the tile.
+__device__ __forceinline__ void store_multi_chunks(uint32_t *chunk_bits, const uint32_t *wtot, uint64_t tile,
+                                                   uint32_t k, uint64_t n_chunks, int tid) {
+  if (k <= 1 || tid >= (int)(kEncWarps / k)) return;
+  uint32_t sum = 0;
+  for (uint32_t w = (uint32_t)tid * k; w < (uint32_t)(tid + 1) * k; ++w) sum += wtot[w];
+  const uint64_t c = tile * (kEncWarps / k) + (uint64_t)tid;
+  if (c < n_chunks) chunk_bits[c] = sum;
+}
+
 // One encode tile (kEncWarps chunks) of one field whose codeword table is
 // in sm.senc; all threads of the CTA call it together.
 template <int CH>
-__device__ __forceinline__ void encode_tile(const CompressWs &ws, uint8_t *d_out, uint64_t n_chunks, uint64_t tile,
+__device__ __forceinline__ void encode_tile(const CompressWs &ws, uint8_t *d_out, uint64_t n_blk, uint64_t tile,
                                             EncSmem<CH> &sm) {
   constexpr int PER = CH / 32;  // codes per lane (16 or 32)
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -56,17 +80,17 @@ __device__ __forceinline__ void encode_tile(const CompressWs &ws, uint8_t *d_out
   const fz_header &h = ctl->res.hdr;
   uint32_t *chunk_bits = reinterpret_cast<uint32_t *>(d_out + h.off_chunk_bits);
   uint32_t *words = reinterpret_cast<uint32_t *>(d_out + h.off_bits);
-  const uint64_t n_tiles = (n_chunks + kEncWarps - 1) / kEncWarps;
+  const uint64_t n_tiles = (n_blk + kEncWarps - 1) / kEncWarps;
   const uint64_t wlimit = (ctl->total_bits + 31) / 32;
   uint32_t *senc = sm.senc, *lw = sm.lw;
 
   // ---- lane codes and bit counts
-  const uint64_t chunk = tile * kEncWarps + warp;
-  const bool valid = chunk < n_chunks;
+  const uint64_t blk = tile * kEncWarps + warp;
+  const bool valid = blk < n_blk;
   uint32_t cw[PER];
   uint32_t lbits = 0;
   if (valid) {
-    const uint4 *src = reinterpret_cast<const uint4 *>(ws.codes + chunk * CH + lane * PER);
+    const uint4 *src = reinterpret_cast<const uint4 *>(ws.codes + blk * CH + lane * PER);
 #pragma unroll
     for (int v = 0; v < PER / 8; ++v) {
       const uint4 u = __ldcs(src + v);
@@ -92,9 +116,11 @@ __device__ __forceinline__ void encode_tile(const CompressWs &ws, uint8_t *d_out
   const uint32_t lane_off = incl - lbits;
   if (lane == 31) {
     sm.wtot[warp] = incl;
-    if (valid) chunk_bits[chunk] = incl;
+    if (valid && h.chunk == CH) chunk_bits[blk] = incl;
   }
+  store_sub_chunks<PER>(chunk_bits, blk, incl, lane, h.chunk, valid);
   __syncthreads();
+  store_multi_chunks(chunk_bits, sm.wtot, tile, h.chunk / CH, h.n_chunks, tid);
   if (tid == 0) {
     uint32_t acc = 0;
     for (int w = 0; w < kEncWarps; ++w) { sm.woff[w] = acc; acc += sm.wtot[w]; }
@@ -252,8 +278,8 @@ __global__ void __launch_bounds__(kEncThreads, CH == 512 ? FZ_ENC_MINB : FZ_ENC_
   const fz_header &h = ctl->res.hdr;
   uint32_t *chunk_bits = reinterpret_cast<uint32_t *>(d_out + h.off_chunk_bits);
   uint32_t *words = reinterpret_cast<uint32_t *>(d_out + h.off_bits);
-  const uint64_t n_chunks = g.n_blocks;
-  const uint64_t n_tiles = (n_chunks + kEncWarps - 1) / kEncWarps;
+  const uint64_t n_blk = g.n_blocks;
+  const uint64_t n_tiles = (n_blk + kEncWarps - 1) / kEncWarps;
   const uint64_t wlimit = (ctl->total_bits + 31) / 32;
   for (int i = tid; i < kMaxSym; i += kEncThreads) sm.senc[i] = ctl->enc[i];
   for (int i = tid; i < 2 * PipeSmem<CH>::kMaxWords; i += kEncThreads) (&sm.lw[0][0])[i] = 0;
@@ -262,7 +288,7 @@ __global__ void __launch_bounds__(kEncThreads, CH == 512 ? FZ_ENC_MINB : FZ_ENC_
   uint64_t tile = sm.tk[0];
   // the codes of the tile in hand are loaded one step ahead of their use
   uint4 raw[PER / 8];
-  if (tile < n_tiles && tile * kEncWarps + warp < n_chunks) load_lane_codes<PER>(ws.codes, tile * kEncWarps + warp, CH, lane, raw);
+  if (tile < n_tiles && tile * kEncWarps + warp < n_blk) load_lane_codes<PER>(ws.codes, tile * kEncWarps + warp, CH, lane, raw);
   uint64_t prev = ~0ull;
   uint32_t prev_bits = 0;
   int cb = 0;
@@ -270,8 +296,8 @@ __global__ void __launch_bounds__(kEncThreads, CH == 512 ? FZ_ENC_MINB : FZ_ENC_
     const bool have = tile < n_tiles;
     uint32_t tbits = 0;
     uint32_t *lw = sm.lw[cb];
-    const uint64_t chunk = tile * kEncWarps + warp;
-    const bool valid = have && chunk < n_chunks;
+    const uint64_t blk = tile * kEncWarps + warp;
+    const bool valid = have && blk < n_blk;
     if (tid == 0 && have) sm.tk[cb ^ 1] = atomicAdd(&ctl->encode_ticket, 1u);
     // the next tile's first 32 codes (its head), read ahead of their use
     uint32_t hcode = 0;
@@ -304,12 +330,14 @@ __global__ void __launch_bounds__(kEncThreads, CH == 512 ? FZ_ENC_MINB : FZ_ENC_
     }
     if (lane == 31) {
       sm.wtot[warp] = incl;
-      if (valid) chunk_bits[chunk] = incl;
+      if (valid && g.chunk == CH) chunk_bits[blk] = incl;
     }
+    store_sub_chunks<PER>(chunk_bits, blk, incl, lane, g.chunk, valid);
     __syncthreads();
+    if (have) store_multi_chunks(chunk_bits, sm.wtot, tile, g.chunk / CH, g.n_chunks, tid);
     // ---- the next tile's codes go out now and land during this step
     const uint64_t next = have ? (uint64_t)sm.tk[cb ^ 1] : n_tiles;
-    if (next < n_tiles && next * kEncWarps + warp < n_chunks)
+    if (next < n_tiles && next * kEncWarps + warp < n_blk)
       load_lane_codes<PER>(ws.codes, next * kEncWarps + warp, CH, lane, raw);
     if (have) {
       uint32_t woff = 0;

@@ -38,6 +38,9 @@ struct Geom {
   uint32_t tile_nb;        // blocks per tile along x
   uint32_t tiles_x;        // tiles per block-row
   uint64_t n_qtiles;
+  // Huffman chunks: chunk j covers code-stream symbols [j chunk, (j+1) chunk)
+  uint32_t chunk;          // symbols per chunk (default: bsize)
+  uint64_t n_chunks;       // ceil(npad / chunk)
 };
 
 inline __host__ __device__ void make_geom(uint32_t ndim, const uint64_t dims[3], Geom &g) {
@@ -57,6 +60,22 @@ inline __host__ __device__ void make_geom(uint32_t ndim, const uint64_t dims[3],
   g.npad = g.n_blocks * g.bsize;
   g.tiles_x = (g.nbx + g.tile_nb - 1) / g.tile_nb;
   g.n_qtiles = (uint64_t)g.tiles_x * g.nby * g.nbz;
+  g.chunk = g.bsize;
+  g.n_chunks = g.n_blocks;
+}
+
+// Huffman chunk sizes of the format: the block size, a power-of-two
+// multiple of it up to 4096, or, for 3D blocks, 64 (one 8x8 plane).  Only
+// first- and second-order Lorenzo streams use a chunk other than the block.
+inline __host__ __device__ bool chunk_supported(uint32_t ndim, uint32_t bsize, uint32_t C) {
+  if (C == bsize) return true;
+  if (ndim == 3 && C == 64) return true;
+  return C > bsize && C <= 4096 && C % bsize == 0 && (C & (C - 1)) == 0;
+}
+
+inline __host__ __device__ void set_chunk(Geom &g, uint32_t C) {
+  g.chunk = C;
+  g.n_chunks = (g.npad + C - 1) / C;
 }
 
 // Launch shape of one kernel, computed on its first launch on each device:

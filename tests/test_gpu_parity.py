@@ -339,7 +339,8 @@ def test_pipeline_block_and_chunk_arguments():
     x = torch.from_numpy(synth.blobs3d((24, 24, 24), seed=4).numpy()).cuda()
     ref = fz.compress(x, 1e-3).cpu()
     assert torch.equal(fz.compress(x, 1e-3, block=(8, 8, 8), chunk=512).cpu(), ref)
-    for kw, code in (({"block": (4, 4, 4)}, 7), ({"block": (8, 8, 0)}, 1), ({"chunk": 300}, 7)):
+    for kw, code in (({"block": (4, 4, 4)}, 7), ({"block": (8, 8, 0)}, 1), ({"chunk": 300}, 7),
+                     ({"chunk": 256}, 7), ({"chunk": 8192}, 7)):
         with pytest.raises(fz.FzError) as e:
             fz.compress(x, 1e-3, **kw)
         assert e.value.code == code, kw
@@ -349,3 +350,65 @@ def test_full_cesm_2d_rel():
     x = synth.cesm2d(1800, 3600, seed=4)
     for eb in (1e-2, 1e-3, 1e-4):
         _full_check(x, eb)
+
+
+# ---------------------------------------------------------------- Huffman chunk sizes
+@pytest.mark.parametrize("shape,chunks", [((40, 37, 70), (64, 1024, 2048, 4096)), ((17, 9, 33), (64, 4096)),
+                                          ((16, 64, 130), (64, 2048)), ((61, 450), (2048, 4096)),
+                                          ((100003,), (2048, 4096)), ((5000,), (4096,))])
+@pytest.mark.parametrize("predictor", ["lorenzo1", "lorenzo2"])
+def test_chunk_sizes_bit_exact(shape, chunks, predictor):
+    """Every chunk size of the format: the GPU stream equals the oracle's
+    byte for byte, and the GPU decoder (the plane-parallel one for 64-symbol
+    chunks, the block decoder for multiples of the block) reconstructs the
+    oracle's floats bit for bit; exceptions (NaN, infinity) included."""
+    x = synth.smooth_nd(shape, seed=sum(shape) + 1).numpy().copy()
+    flat = x.reshape(-1)
+    flat[7] = np.nan
+    flat[flat.size // 2] = np.inf
+    k = 2 if predictor == "lorenzo2" else 1
+    xd = torch.from_numpy(x).cuda()
+    for C in chunks:
+        ref = oracle.compress(x, 1e-3, lorenzo_k=k, chunk=C)
+        buf = fz.compress(xd, 1e-3, predictor=predictor, chunk=C)
+        got = buf.cpu().numpy()
+        assert got.size == ref.size and np.array_equal(got, ref), C
+        yref = oracle.decompress(ref)
+        y = fz.decompress(buf).cpu().numpy()
+        assert np.array_equal(_bits(y), _bits(yref)), C
+        y2 = fz.decompress(torch.from_numpy(ref).cuda()).cpu().numpy()
+        assert np.array_equal(_bits(y2), _bits(yref)), C
+
+
+def test_chunk64_outliers_and_corruption():
+    """64-symbol chunks with many outliers (radius 2) and with the lengths of
+    two neighbouring chunks exchanged one bit (total unchanged): the first
+    decodes bit-exactly, the second is reported as corrupt."""
+    x = synth.blobs3d((40, 48, 56), seed=11).numpy()
+    ref = oracle.compress(x, 1e-4, radius=2, chunk=64)
+    buf = fz.compress(torch.from_numpy(x).cuda(), 1e-4, radius=2, chunk=64)
+    assert np.array_equal(buf.cpu().numpy(), ref)
+    assert np.array_equal(_bits(fz.decompress(buf).cpu().numpy()), _bits(oracle.decompress(ref)))
+    h = ref[:256].tobytes()
+    off_cb = int.from_bytes(h[160:168], "little")
+    t = ref.copy()
+    cb = t[off_cb:off_cb + 64].view(np.uint32)
+    cb[5] += 1
+    cb[6] -= 1
+    with pytest.raises(fz.FzError) as e:
+        fz.decompress(torch.from_numpy(t).cuda())
+    assert e.value.code == 5
+
+
+def test_full_512cubed_grf_chunk64():
+    """The headline field with one-plane chunks, at full size, against the
+    oracle: stream byte for byte, reconstruction bit for bit."""
+    x = synth.grf3d(512, seed=2, device="cuda")
+    xd = x.contiguous()
+    buf = fz.compress(xd, 1e-4, chunk=64)
+    y = fz.decompress(buf)
+    xh = xd.cpu().numpy()
+    ref = oracle.compress(xh, 1e-4, chunk=64)
+    got = buf.cpu().numpy()
+    assert got.size == ref.size and np.array_equal(got, ref)
+    assert np.array_equal(y.cpu().numpy().view(np.uint32), oracle.decompress(ref).view(np.uint32))

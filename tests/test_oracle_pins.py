@@ -541,3 +541,65 @@ def test_corrupt_streams_rejected():
             assert y.shape == x.shape
         except oracle.OracleError:
             pass
+
+
+# ---------------------------------------------------------------- Huffman chunk size (§3.2 chunked encoder)
+def _sections(buf):
+    h = buf[:256].tobytes()
+    u64 = lambda o: int.from_bytes(h[o:o + 8], "little")
+    u32 = lambda o: int.from_bytes(h[o:o + 4], "little")
+    return {"chunk": u32(88), "n_blocks": u64(96), "n_chunks": u64(104), "total_bits": u64(128),
+            "off_cb": u64(160), "off_bits": u64(200), "total": u64(208)}
+
+
+@pytest.mark.parametrize("shape,chunks", [((40, 37, 70), (64, 1024, 2048, 4096)), ((9, 8, 17), (64, 4096)),
+                                          ((61, 450), (2048, 4096)), ((100003,), (2048, 4096))])
+def test_chunk_size_only_regroups_chunk_bits(shape, chunks):
+    """Chunk j covers code-stream symbols [jC, min((j+1)C, Npad)): the
+    bitstream is the same for every C, chunk j's stored length is the sum of
+    the code lengths of its symbols (brute force from the stage codes and
+    the codebook), the lengths add up to the total, and the reconstruction
+    does not change."""
+    x = synth.smooth_nd(shape, seed=len(shape) + 7).numpy()
+    eb = 1e-3
+    base = oracle.compress(x, eb)
+    sb = _sections(base)
+    ndim = len(shape)
+    ebx2, inv2eb, ebchk = oracle.constants(eb * (float(x.max()) - float(x.min())))
+    codes, _, hist, _, _ = oracle.quantize_stage(x, ndim, shape[::-1], inv2eb, ebx2, ebchk)
+    lens = oracle.huffman_lengths(hist).astype(np.int64)
+    bits_per = lens[codes.astype(np.int64)]
+    y0 = oracle.decompress(base)
+    for C in chunks:
+        buf = oracle.compress(x, eb, chunk=C)
+        s = _sections(buf)
+        assert s["chunk"] == C and s["n_chunks"] == -(-codes.size // C)
+        nw = (s["total_bits"] + 31) // 32
+        assert s["total_bits"] == sb["total_bits"]
+        assert np.array_equal(buf[s["off_bits"]:s["off_bits"] + 4 * nw], base[sb["off_bits"]:sb["off_bits"] + 4 * nw])
+        cb = buf[s["off_cb"]:s["off_cb"] + 4 * s["n_chunks"]].view(np.uint32).astype(np.int64)
+        want = np.add.reduceat(bits_per, np.arange(0, codes.size, C))
+        assert np.array_equal(cb, want)
+        assert int(cb.sum()) == s["total_bits"]
+        assert np.array_equal(oracle.decompress(buf).view(np.uint32), y0.view(np.uint32))
+
+
+def test_chunk_size_rejects_bad_values_and_bad_lengths():
+    x = synth.smooth_nd((20, 24, 28), seed=3).numpy()
+    for C in (32, 100, 256, 768, 8192):
+        with pytest.raises(oracle.OracleError) as e:
+            oracle.compress(x, 1e-3, chunk=C)
+        assert e.value.code == oracle.EUNSUPPORTED
+    with pytest.raises(oracle.OracleError):
+        oracle.compress(synth.smooth_nd((5000,), 1).numpy(), 1e-3, chunk=64)  # 64 is for 3D blocks only
+    buf = oracle.compress(x, 1e-3, chunk=64)
+    s = _sections(buf)
+    cb = buf[s["off_cb"]:s["off_cb"] + 4 * s["n_chunks"]].view(np.uint32)
+    # moving one bit from a chunk to its neighbour keeps the total but breaks both chunks
+    t = buf.copy()
+    tc = t[s["off_cb"]:s["off_cb"] + 4 * s["n_chunks"]].view(np.uint32)
+    tc[3] += 1
+    tc[4] -= 1
+    with pytest.raises(oracle.OracleError) as e:
+        oracle.decompress(t)
+    assert e.value.code == oracle.ECORRUPT

@@ -80,3 +80,19 @@ def test_noalloc_limit_and_unsupported():
     with pytest.raises(fz.FzError) as e:
         fz.decompress_noalloc(buf3)
     assert e.value.code == 7
+
+
+def test_noalloc_plane_chunks_twice():
+    """A stream with one-plane (64-symbol) Huffman chunks, decoded by the
+    plane-parallel decoder with exceptions written afterwards: the no-alloc
+    entry point gives fz_decompress's floats on two calls in a row."""
+    x = synth.smooth_nd((40, 37, 70), 5).clone()
+    x[3, 4, 5] = float("nan")
+    xg = x.contiguous().cuda()
+    buf = fz.compress(xg, 1e-3, chunk=64)
+    ref = fz.decompress(buf)
+    out = torch.empty_like(ref)
+    for _ in range(2):
+        out.fill_(-1.0)
+        fz.decompress_noalloc(buf, out=out)
+        assert np.array_equal(_bits(out), _bits(ref))
