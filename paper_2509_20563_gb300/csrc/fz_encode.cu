@@ -268,7 +268,10 @@ __device__ __forceinline__ void load_lane_codes(const uint16_t *codes, uint64_t 
   for (int v = 0; v < PER / 8; ++v) raw[v] = __ldcs(src + v);
 }
 
-template <int CH>
+// CM: how chunk lengths are stored -- 0 one chunk per block, 1 64-symbol
+// chunks (3D), 2 chunks of several blocks; a template parameter so that the
+// default case carries none of the others' code.
+template <int CH, int CM>
 __global__ void __launch_bounds__(kEncThreads, CH == 512 ? FZ_ENC_MINB : FZ_ENC_MINB1024) k_encode_pipe(Geom g, CompressWs ws, uint8_t *d_out) {
   constexpr int PER = CH / 32;
   __shared__ PipeSmem<CH> sm;
@@ -330,11 +333,11 @@ __global__ void __launch_bounds__(kEncThreads, CH == 512 ? FZ_ENC_MINB : FZ_ENC_
     }
     if (lane == 31) {
       sm.wtot[warp] = incl;
-      if (valid && g.chunk == CH) chunk_bits[blk] = incl;
+      if (CM == 0 && valid) chunk_bits[blk] = incl;
     }
-    store_sub_chunks<PER>(chunk_bits, blk, incl, lane, g.chunk, valid);
+    if (CM == 1) store_sub_chunks<PER>(chunk_bits, blk, incl, lane, 64u, valid);
     __syncthreads();
-    if (have) store_multi_chunks(chunk_bits, sm.wtot, tile, g.chunk / CH, g.n_chunks, tid);
+    if (CM == 2 && have) store_multi_chunks(chunk_bits, sm.wtot, tile, g.chunk / CH, g.n_chunks, tid);
     // ---- the next tile's codes go out now and land during this step
     const uint64_t next = have ? (uint64_t)sm.tk[cb ^ 1] : n_tiles;
     if (next < n_tiles && next * kEncWarps + warp < n_blk)
@@ -424,16 +427,16 @@ __global__ void __launch_bounds__(kEncThreads, CH == 512 ? FZ_ENC_MINB : FZ_ENC_
   }
 }
 
-template <int CH>
+template <int CH, int CM>
 cudaError_t launch_t(const Geom &g, const CompressWs &ws, uint8_t *d_out, cudaStream_t s, int sms) {
   static LaunchCache cache;
   int per_sm = 0;
-  const cudaError_t e = cached_per_sm(k_encode_pipe<CH>, kEncThreads, 0, cache, per_sm);
+  const cudaError_t e = cached_per_sm(k_encode_pipe<CH, CM>, kEncThreads, 0, cache, per_sm);
   if (e != cudaSuccess) return e;
   const uint64_t n_tiles = (g.n_blocks + kEncWarps - 1) / kEncWarps;
   uint64_t grid = (uint64_t)sms * per_sm;
   if (grid > n_tiles) grid = n_tiles;
-  k_encode_pipe<CH><<<(unsigned)grid, kEncThreads, 0, s>>>(g, ws, d_out);
+  k_encode_pipe<CH, CM><<<(unsigned)grid, kEncThreads, 0, s>>>(g, ws, d_out);
   return cudaGetLastError();
 }
 
@@ -462,8 +465,14 @@ cudaError_t launch_encode_batch(int chunk, const BatchJob *jobs, const uint32_t 
 }
 
 cudaError_t launch_encode(const Geom &g, const CompressWs &ws, uint8_t *d_out, cudaStream_t s, int sm_count) {
-  if (g.bsize == 512) return launch_t<512>(g, ws, d_out, s, sm_count);
-  return launch_t<1024>(g, ws, d_out, s, sm_count);
+  const int cm = g.chunk == g.bsize ? 0 : (g.chunk < g.bsize ? 1 : 2);
+  if (g.bsize == 512) {
+    if (cm == 0) return launch_t<512, 0>(g, ws, d_out, s, sm_count);
+    if (cm == 1) return launch_t<512, 1>(g, ws, d_out, s, sm_count);
+    return launch_t<512, 2>(g, ws, d_out, s, sm_count);
+  }
+  if (cm == 0) return launch_t<1024, 0>(g, ws, d_out, s, sm_count);
+  return launch_t<1024, 2>(g, ws, d_out, s, sm_count);
 }
 
 }  // namespace fz
