@@ -473,6 +473,8 @@ def run_fz(args, rank, world, local_rank):
             os.sched_setaffinity(0, saved_cpus)
     if rank == 0 and world == 1 and not args.no_configs:
         res["configs"] = bench_configs(fz, dev, stream, args)
+    if rank == 0 and world == 1 and not args.no_rd:
+        res["rate_distortion"] = bench_rate_distortion(fz, dev, x, res.get("e2e", {}).get("host_link"))
     if rank == 0 and world == 1 and not args.no_batch:
         res["batch"] = bench_batch(fz, dev, stream, args)
     if rank == 0 and world == 1 and not args.no_learned:
@@ -591,6 +593,23 @@ def bench_configs(fz, dev, stream, args):
         del x, ob, y
         torch.cuda.empty_cache()
     return out
+
+
+def bench_rate_distortion(fz, dev, x512, link):
+    """§4.2's evaluation on the stand-in workloads: bit rate against PSNR at
+    REL 1e-2 .. 1e-6, and Eq. 1's overall speedup over the host link measured
+    in this run (host to device) and over 25 and 100 GB/s links."""
+    import paper_2509_20563_gb300.report as report
+    bws = [25.0, 100.0]
+    if link and link.get("h2d_gbs"):
+        bws.insert(0, float(link["h2d_gbs"]))
+    fields = {"grf512": x512, "hacc1d": synth.hacc1d(synth.HACC_N, seed=3, device=dev),
+              "cesm2d": synth.cesm2d(1800, 3600, seed=4).to(dev).contiguous()}
+    rows = report.rate_distortion(fields, [1e-2, 1e-3, 1e-4, 1e-5, 1e-6], bws, reps=3)
+    del fields
+    torch.cuda.empty_cache()
+    return {"bandwidths_gbs": bws, "rows": rows,
+            "note": "Eq. 1 speedup = 1 / (((BW CR)^-1 + T_compress^-1) BW); PSNR from fz_error_stats"}
 
 
 def bench_batch(fz, dev, stream, args):
@@ -716,6 +735,7 @@ def main():
     ap.add_argument("--no-batch", action="store_true", help="skip the 64-field batched workload")
     ap.add_argument("--no-learned", action="store_true", help="skip the selector training and CR comparison")
     ap.add_argument("--no-configs", action="store_true", help="skip the other plain-pipeline workloads")
+    ap.add_argument("--no-rd", action="store_true", help="skip the rate-distortion / Eq. 1 report")
     ap.add_argument("--config-reps", type=int, default=10, help="timed calls per extra workload and bound")
     ap.add_argument("--traffic", type=float, default=None, help="ncu dram bytes per launch of the dominant kernel")
     args = ap.parse_args()

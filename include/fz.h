@@ -282,6 +282,23 @@ fz_status fz_ctx_set_spin_limit(fz_ctx *ctx, long long cycles);
  * paper. */
 fz_status fz_selftest_bounded_wait(fz_ctx *ctx, void *stream);
 
+/* ---- reconstruction quality (rate-distortion evaluation, §4.2) ----
+ * Statistics of a reconstruction d_y against its original d_x (n float32
+ * values each, device): over the finite originals the largest |y - x| and the
+ * sum of squared errors (double accumulation, deterministic order), the
+ * value range, their count, and the number of non-finite originals whose
+ * reconstruction does not carry the same bits; psnr_db = 20 log10(range) -
+ * 10 log10(sse / n_finite) (infinite for an exact reconstruction).  The
+ * paper's rate-distortion figure plots this PSNR against the bit rate
+ * (stream bits per value).  Uses the context workspace; synchronizes
+ * `stream`.  FZ_EINVAL for n = 0 or unaligned pointers. */
+typedef struct {
+  double max_abs_err, sse, x_min, x_max, psnr_db;
+  uint64_t n_finite, n_nonfinite_mismatch;
+} fz_error_report;
+fz_status fz_error_stats(fz_ctx *ctx, const float *d_x, const float *d_y, uint64_t n, fz_error_report *out,
+                         void *stream);
+
 /* Human-readable name of a status code (static string). */
 const char *fz_status_str(fz_status s);
 

@@ -20,7 +20,7 @@ import torch
 
 __all__ = ["lib", "Context", "compress", "decompress", "lorenzo_quantize", "huffman_codebook", "stream_info",
            "block_report", "mlp_grad", "mlp_adam", "compress_batch", "decompress_batch", "FzError", "HEADER_BYTES",
-           "stream_check", "set_spin_limit", "selftest_bounded_wait",
+           "stream_check", "set_spin_limit", "selftest_bounded_wait", "error_stats",
            "SELECTOR_WEIGHTS"]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -47,6 +47,12 @@ class Pipeline(C.Structure):
     _fields_ = [("struct_size", C.c_uint32), ("predictor", C.c_uint32), ("radius", C.c_uint32),
                 ("block", C.c_uint32 * 3), ("chunk", C.c_uint32), ("reserved", C.c_uint32),
                 ("selector_weights", C.c_void_p)]
+
+
+class ErrorReport(C.Structure):
+    """fz_error_report: reconstruction statistics of fz_error_stats."""
+    _fields_ = [("max_abs_err", C.c_double), ("sse", C.c_double), ("x_min", C.c_double), ("x_max", C.c_double),
+                ("psnr_db", C.c_double), ("n_finite", C.c_uint64), ("n_nonfinite_mismatch", C.c_uint64)]
 
 
 _u64p = C.POINTER(C.c_uint64)
@@ -81,6 +87,7 @@ def _declare(L):
     L.fz_decompress_noalloc.argtypes = [_vp, C.c_uint64, _vp, _vp, C.c_uint64, _vp]
     L.fz_ctx_set_profiling.argtypes = [_vp, C.c_int]
     L.fz_stream_check.argtypes = [_vp, C.c_uint64]
+    L.fz_error_stats.argtypes = [_vp, _vp, _vp, C.c_uint64, C.POINTER(ErrorReport), _vp]
     L.fz_ctx_set_spin_limit.argtypes = [_vp, C.c_longlong]
     L.fz_selftest_bounded_wait.argtypes = [_vp, _vp]
     L.fz_ctx_get_profile.argtypes = [_vp, _vp]
@@ -205,6 +212,20 @@ def stream_info(header: bytes):
            "fz_stream_info")
     shape = tuple(int(dims[a]) for a in range(ndim.value))[::-1]
     return shape, eb_abs.value, flags.value
+
+
+def error_stats(x: torch.Tensor, y: torch.Tensor, stream=None, ctx: "Context | None" = None) -> dict:
+    """Reconstruction statistics of y against x (fz_error_stats): max abs
+    error, sum of squared errors, value range, PSNR (dB), finite count and
+    non-finite mismatches."""
+    if not (x.is_cuda and y.is_cuda and x.dtype == torch.float32 and y.dtype == torch.float32
+            and x.is_contiguous() and y.is_contiguous() and x.numel() == y.numel()):
+        raise ValueError("error_stats expects two contiguous float32 CUDA tensors of the same size")
+    r = ErrorReport()
+    c = ctx if ctx is not None else _ctx(x.device.index or 0)
+    _check(lib().fz_error_stats(c.handle, C.c_void_p(x.data_ptr()), C.c_void_p(y.data_ptr()), x.numel(),
+                                C.byref(r), _stream(stream)), "fz_error_stats")
+    return {f: getattr(r, f) for f, _ in ErrorReport._fields_}
 
 
 def stream_check(header: bytes, stream_bytes: int) -> int:
