@@ -473,6 +473,8 @@ def run_fz(args, rank, world, local_rank):
             os.sched_setaffinity(0, saved_cpus)
     if rank == 0 and world == 1 and not args.no_configs:
         res["configs"] = bench_configs(fz, dev, stream, args)
+    if rank == 0 and world == 1 and not args.no_hist:
+        res["histogram"] = bench_histogram(fz, dev, stream, x)
     if rank == 0 and world == 1 and not args.no_rd:
         res["rate_distortion"] = bench_rate_distortion(fz, dev, x, res.get("e2e", {}).get("host_link"))
     if rank == 0 and world == 1 and not args.no_batch:
@@ -612,6 +614,39 @@ def bench_rate_distortion(fz, dev, x512, link):
             "note": "Eq. 1 speedup = 1 / (((BW CR)^-1 + T_compress^-1) BW); PSNR from fz_error_stats"}
 
 
+def bench_histogram(fz, dev, stream, x512):
+    """The histogram stage (§3.2) on its own, both methods: Lorenzo-1 codes of
+    the 512^3 field and interpolation (cubic) codes of the smooth stitched
+    512^3 field (whose codes repeat a few values), 2N code bytes read per
+    call, CUDA events on the launching stream, median of 20 calls."""
+    peak, _ = _peaks()
+    out = []
+    xs = synth.stitched3d(512, seed=200, region=64, device=dev)
+    for name, x, pred in (("grf512_lorenzo1", x512, "lorenzo1"), ("stitched512_interp_cubic", xs, "interp_cubic")):
+        codes, _, hist, _, _, _ = fz.lorenzo_quantize(x, 1e-4, predictor=pred)
+        top = torch.topk(hist.double(), 16).values.sum().item() / hist.sum().item()
+        row = {"codes": name, "n": int(codes.numel()), "top16_share": round(top, 4)}
+        for method in ("private", "topk"):
+            h = fz.histogram(codes, 1024, method)
+            assert torch.equal(h, hist)
+            ts = []
+            for _ in range(20):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                fz.histogram(codes, 1024, method)
+                e1.record(stream)
+                torch.cuda.synchronize(dev)
+                ts.append(e0.elapsed_time(e1))
+            ms = statistics.median(ts)
+            gbs = 2 * codes.numel() / (ms * 1e-3) / 1e9
+            row[method] = {"ms": round(ms, 4), "gbs": round(gbs, 1), "roofline_frac": round(gbs / peak, 4)}
+        out.append(row)
+        del codes
+    del xs
+    torch.cuda.empty_cache()
+    return out
+
+
 def bench_batch(fz, dev, stream, args):
     """64 fields of uneven size (32 cubes of side 32-256, 32 lat/lon fields of
     side 512-4096) at REL 1e-4: one batched call (graph replay after the
@@ -642,9 +677,12 @@ def bench_batch(fz, dev, stream, args):
 
     t_bc = timed(lambda: fz.compress_batch(xs, args.eb, out=buf, ctx=ctx))
     t_bd = timed(lambda: fz.decompress_batch(buf, offs, outs=ys, ctx=ctx))
+    # the per-field calls use the chunk the batch chose for each field
+    hb = buf[: offs[-1]].cpu().numpy()
+    chunks = [int(np.frombuffer(hb[offs[j] + 88: offs[j] + 92].tobytes(), np.uint32)[0]) for j in range(len(xs))]
     outs = [torch.empty(fz.compress_bound(x.shape), dtype=torch.uint8, device=dev) for x in xs]
-    singles = [fz.compress(x, args.eb, out=o) for x, o in zip(xs, outs)]
-    t_sc = timed(lambda: [fz.compress(x, args.eb, out=o) for x, o in zip(xs, outs)])
+    singles = [fz.compress(x, args.eb, out=o, chunk=c) for x, o, c in zip(xs, outs, chunks)]
+    t_sc = timed(lambda: [fz.compress(x, args.eb, out=o, chunk=c) for x, o, c in zip(xs, outs, chunks)])
     recon = [torch.empty_like(x) for x in xs]
     t_sd = timed(lambda: [fz.decompress(b, out=r) for b, r in zip(singles, recon)])
     peak, _ = _peaks()
@@ -665,7 +703,8 @@ def bench_batch(fz, dev, stream, args):
             "graphs": int(prof.batch_graphs), "plans": int(prof.batch_plans),
             "autotuned_compress": {"range_segment_log2": tune_c[0], "quant_ctas_per_sm": tune_c[1],
                                    "encode_ctas_per_sm": tune_c[2]},
-            "autotuned_decode_ctas_per_sm": int(prof.batch_tune[3])}
+            "autotuned_decode_ctas_per_sm": int(prof.batch_tune[3]),
+            "autotuned_chunk": {"3d": int(prof.batch_chunk[0]), "1d_2d": int(prof.batch_chunk[1])}}
 
 
 def bench_learned(fz, dev, args):
@@ -736,6 +775,7 @@ def main():
     ap.add_argument("--no-learned", action="store_true", help="skip the selector training and CR comparison")
     ap.add_argument("--no-configs", action="store_true", help="skip the other plain-pipeline workloads")
     ap.add_argument("--no-rd", action="store_true", help="skip the rate-distortion / Eq. 1 report")
+    ap.add_argument("--no-hist", action="store_true", help="skip the histogram-stage comparison")
     ap.add_argument("--config-reps", type=int, default=10, help="timed calls per extra workload and bound")
     ap.add_argument("--traffic", type=float, default=None, help="ncu dram bytes per launch of the dominant kernel")
     args = ap.parse_args()

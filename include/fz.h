@@ -253,6 +253,8 @@ typedef struct {
   uint32_t batch_plans, batch_graphs;
   int32_t batch_tune[4];                  /* launch shape of the newest batch plan: range segment log2,
                                              quantizer / encoder / decoder CTAs per SM (0 = occupancy limit) */
+  uint32_t batch_chunk[2];                /* Huffman chunk of the newest batch compress plan: 3D fields,
+                                             1D and 2D fields (0 = no field of that kind) */
 } fz_profile;
 
 /* Turn stage timing on (enable != 0) or off.  Host-only bookkeeping; the
@@ -281,6 +283,22 @@ fz_status fz_ctx_set_spin_limit(fz_ctx *ctx, long long cycles);
  * predecessor (a defect).  Synchronizes `stream`.  No counterpart in the
  * paper. */
 fz_status fz_selftest_bounded_wait(fz_ctx *ctx, void *stream);
+
+/* ---- histogram module (§3.2) as a stage of its own ----
+ * Counts of the n codes d_codes (u16, 16-byte aligned, every code < nsym,
+ * nsym <= 1024) into d_hist (u64[nsym], device), by one of two methods that
+ * give the same exact counts: FZ_HIST_PRIVATE (warp-private shared-memory
+ * histograms) or FZ_HIST_TOPK, the top-k variant §3.2 describes as the better
+ * one when the codes repeat a few values: the 16 most frequent codes of a
+ * strided sample are counted in per-thread packed registers and only the
+ * others take shared-memory atomics.  (The compression path counts its codes
+ * inside the quantizer; this entry point serves a code array on its own, such
+ * as the output of fz_lorenzo_quantize.)  Uses the context workspace;
+ * synchronizes `stream`.  FZ_EINVAL for bad arguments or a code >= nsym. */
+#define FZ_HIST_PRIVATE 0u
+#define FZ_HIST_TOPK 1u
+fz_status fz_histogram(fz_ctx *ctx, const uint16_t *d_codes, uint64_t n, uint32_t nsym, uint32_t method,
+                       uint64_t *d_hist, void *stream);
 
 /* ---- reconstruction quality (rate-distortion evaluation, §4.2) ----
  * Statistics of a reconstruction d_y against its original d_x (n float32
@@ -321,7 +339,16 @@ uint64_t fz_compress_batch_bound(uint32_t n, const uint32_t *ndim, const uint64_
 
 /* Compress n fields (1 <= n <= 65535).  d_in: host array of n device
  * pointers (float32, 4-byte aligned); ndim: n values; dims: 3n values; eb:
- * n error bounds (all in mode eb_mode).  The streams are packed into d_out
+ * n error bounds (all in mode eb_mode).  pipe->chunk: 0 lets the autotuner
+ * pick the Huffman chunk of each kind of field (3D; 1D and 2D) among the
+ * block size and its double and quadruple -- the round trip (compress then
+ * decompress) of the batch is timed for each, starting from the largest
+ * chunk (the shortest stream), and a smaller chunk is kept only when it is
+ * at least 3% faster; the tuning pass decompresses into temporary device
+ * memory the size of the batch's input, freed before the call returns.
+ * Without tuning (fz_ctx_set_batch_options) chunk 0 means the block size.
+ * A nonzero chunk applies to every field and must be a supported chunk of
+ * at least the block size (64-symbol chunks are not batched).  The streams are packed into d_out
  * (device, 16-byte aligned, out_cap bytes), stream j starting at
  * h_offsets[j] (a multiple of 16) and its length in its header
  * (total_bytes); h_offsets[n] is the packed size (host array of n+1

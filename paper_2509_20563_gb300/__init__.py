@@ -20,7 +20,7 @@ import torch
 
 __all__ = ["lib", "Context", "compress", "decompress", "lorenzo_quantize", "huffman_codebook", "stream_info",
            "block_report", "mlp_grad", "mlp_adam", "compress_batch", "decompress_batch", "FzError", "HEADER_BYTES",
-           "stream_check", "set_spin_limit", "selftest_bounded_wait", "error_stats",
+           "stream_check", "set_spin_limit", "selftest_bounded_wait", "error_stats", "histogram",
            "SELECTOR_WEIGHTS"]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -88,6 +88,7 @@ def _declare(L):
     L.fz_ctx_set_profiling.argtypes = [_vp, C.c_int]
     L.fz_stream_check.argtypes = [_vp, C.c_uint64]
     L.fz_error_stats.argtypes = [_vp, _vp, _vp, C.c_uint64, C.POINTER(ErrorReport), _vp]
+    L.fz_histogram.argtypes = [_vp, _vp, C.c_uint64, C.c_uint32, C.c_uint32, _vp, _vp]
     L.fz_ctx_set_spin_limit.argtypes = [_vp, C.c_longlong]
     L.fz_selftest_bounded_wait.argtypes = [_vp, _vp]
     L.fz_ctx_get_profile.argtypes = [_vp, _vp]
@@ -228,6 +229,22 @@ def error_stats(x: torch.Tensor, y: torch.Tensor, stream=None, ctx: "Context | N
     return {f: getattr(r, f) for f, _ in ErrorReport._fields_}
 
 
+HIST_METHODS = {"private": 0, "topk": 1}
+
+
+def histogram(codes: torch.Tensor, nsym: int, method: str = "private", stream=None,
+              ctx: "Context | None" = None) -> torch.Tensor:
+    """Counts of a contiguous uint16 code array on the GPU (fz_histogram);
+    returns an int64 CUDA tensor of nsym counts."""
+    if not (codes.is_cuda and codes.dtype in (torch.int16, torch.uint16) and codes.is_contiguous()):
+        raise ValueError("histogram expects a contiguous 16-bit CUDA tensor")
+    out = torch.empty(int(nsym), dtype=torch.int64, device=codes.device)
+    c = ctx if ctx is not None else _ctx(codes.device.index or 0)
+    _check(lib().fz_histogram(c.handle, C.c_void_p(codes.data_ptr()), codes.numel(), int(nsym),
+                              HIST_METHODS[method], C.c_void_p(out.data_ptr()), _stream(stream)), "fz_histogram")
+    return out
+
+
 def stream_check(header: bytes, stream_bytes: int) -> int:
     """Host-only validation of a stream header against a stream length
     (fz_stream_check); returns the status code (0 = valid)."""
@@ -281,12 +298,13 @@ def _batch_shapes(xs):
 
 
 def compress_batch(xs, eb, mode: str = "rel", predictor="lorenzo1", radius: int = 512, out=None, stream=None,
-                   ctx: Context | None = None):
+                   ctx: Context | None = None, chunk: int = 0):
     """Compress a list of contiguous float32 CUDA tensors (1-3 dims each) in
-    one batched call.  ``eb`` is one bound or one per field.  Returns the
+    one batched call.  ``eb`` is one bound or one per field; ``chunk`` 0
+    lets the autotuner pick the Huffman chunk per kind of field.  Returns the
     packed uint8 buffer and the stream offsets (n+1 ints); stream j is
     ``buf[off[j]:off[j] + its total_bytes]``, byte-identical to ``compress``
-    of field j."""
+    of field j with the chunk its header records."""
     xs = list(xs)
     n = len(xs)
     if n == 0:
@@ -302,7 +320,7 @@ def compress_batch(xs, eb, mode: str = "rel", predictor="lorenzo1", radius: int 
     ptrs = (C.c_void_p * n)(*[x.data_ptr() for x in xs])
     ebarr = (C.c_double * n)(*ebs)
     offs = (C.c_uint64 * (n + 1))()
-    pipe = _pipeline(predictor, radius)
+    pipe = _pipeline(predictor, radius, chunk=chunk)
     c = ctx if ctx is not None else _ctx(xs[0].device.index or 0)
     st = lib().fz_compress_batch(c.handle, n, ptrs, ndim, dims, 1 if mode == "rel" else 0, ebarr, C.byref(pipe),
                                  C.c_void_p(out.data_ptr()), out.numel(), offs, _stream(stream))
@@ -332,7 +350,7 @@ class Profile(C.Structure):
                 ("compress_names", (C.c_char * 16) * 12), ("compress_ms", C.c_float * 12),
                 ("decompress_names", (C.c_char * 16) * 12), ("decompress_ms", C.c_float * 12),
                 ("launches", C.c_uint64), ("batch_plans", C.c_uint32), ("batch_graphs", C.c_uint32),
-                ("batch_tune", C.c_int32 * 4)]
+                ("batch_tune", C.c_int32 * 4), ("batch_chunk", C.c_uint32 * 2)]
 
 
 def profile(device: int = 0, ctx: Context | None = None) -> Profile:

@@ -297,6 +297,11 @@ fz_status fz_ctx_get_profile(fz_ctx *ctx, fz_profile *out) {
     out->batch_tune[2] = t.encode_per_sm;
     out->batch_tune[3] = t.decode_per_sm;
   }
+  for (auto it = ctx->plans.rbegin(); it != ctx->plans.rend(); ++it) {
+    if ((*it)->decompress) continue;
+    for (int c = 0; c < 2; ++c) out->batch_chunk[c] = (*it)->chunk[c];
+    break;
+  }
   if (!ctx->profiling) return FZ_OK;
   if (cudaSetDevice(ctx->device) != cudaSuccess) return FZ_ECUDA;
   for (int kind = 0; kind < 2; ++kind) {

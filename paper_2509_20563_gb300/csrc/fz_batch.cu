@@ -26,6 +26,7 @@
 //
 // FZModules composes its pipelines from modules launched one field at a time
 // (§3.3); batching many fields into one graph is this library's addition.
+#include <stddef.h>
 #include <string.h>
 
 #include <new>
@@ -183,6 +184,71 @@ fz_status autotune(BatchTune &best, const std::vector<std::pair<int BatchTune::*
   return FZ_OK;
 }
 
+// Chunk tuning of a batched compress: for each encode class (3D; 1D and 2D)
+// that has fields, the chunk multipliers 4, 2, 1 (largest first: the
+// shortest stream) are tried in turn; each trial compresses the batch with
+// `compress(t)` (timed, results in `offs`) and decompresses it into
+// temporary device memory with fz_decompress_batch (timed, untuned, eager).
+// A smaller chunk replaces the incumbent only if its round trip is at least
+// 3% faster.  Every trial's round trip must succeed.
+template <class C>
+fz_status tune_chunks(fz_ctx *ctx, BatchTune &best, uint32_t n, const std::vector<uint32_t> *emem,
+                      void *d_out, const float *const *d_in, const std::vector<Geom> &geo, cudaStream_t s,
+                      C &&compress, const uint64_t *offs) {
+  if (emem[0].empty() && emem[1].empty()) return FZ_OK;
+  uint64_t total = 0;
+  std::vector<uint64_t> at(n);
+  for (uint32_t j = 0; j < n; ++j) { at[j] = total; total += up(4 * geo[j].n); }
+  void *scratch = nullptr;
+  if (cudaMalloc(&scratch, total) != cudaSuccess) {
+    cudaGetLastError();
+    return FZ_OK;  // no room to tune: keep the incumbent
+  }
+  std::vector<float *> outs(n);
+  for (uint32_t j = 0; j < n; ++j) outs[j] = reinterpret_cast<float *>(reinterpret_cast<char *>(scratch) + at[j]);
+  const bool tuning = ctx->batch_tuning, graphs = ctx->batch_graphs;
+  ctx->batch_tuning = false;
+  ctx->batch_graphs = false;
+  std::vector<uint64_t> h(n + 1);
+  fz_status st = FZ_OK;
+  auto round_trip = [&](const BatchTune &t) -> float {
+    const float c = compress(t);
+    if (c < 0) return -1.f;
+    if (offs[n + 1]) return -1.f;
+    for (uint32_t j = 0; j <= n; ++j) h[j] = offs[j];
+    fz_status ds = FZ_OK;
+    const float d = time_run(s, [&](cudaStream_t q) {
+      ds = fz_decompress_batch(ctx, n, d_out, h.data(), outs.data(), nullptr, q);
+      return ds == FZ_OK ? cudaSuccess : cudaErrorUnknown;
+    });
+    return (d < 0 || ds != FZ_OK) ? -1.f : c + d;
+  };
+  for (int c = 0; c < 2 && st == FZ_OK; ++c) {
+    if (emem[c].empty()) continue;
+    BatchTune t = best;
+    t.chunk_log2[c] = 2;
+    round_trip(t);  // warm-up of this class's chunk
+    float inc = round_trip(t);
+    if (inc < 0) { st = FZ_ECUDA; break; }
+    int arg = 2;
+    for (int v = 1; v >= 0; --v) {
+      BatchTune u = best;
+      u.chunk_log2[c] = v;
+      const float a = round_trip(u), b = round_trip(u);
+      if (a < 0 || b < 0) { st = FZ_ECUDA; break; }
+      const float ms = a < b ? a : b;
+      if (ms < 0.97f * inc) { inc = ms; arg = v; }
+    }
+    best.chunk_log2[c] = arg;
+  }
+  ctx->batch_tuning = tuning;
+  ctx->batch_graphs = graphs;
+  destroy_batch_plans(ctx, 1);  // the untuned decompress plans of the trials
+  cudaFree(scratch);
+  (void)d_in;
+  return st;
+}
+
 // ----------------------------------------------------------------- compress
 struct CPlan {
   uint32_t n = 0;
@@ -225,11 +291,12 @@ fz_status fz_compress_batch(fz_ctx *ctx, uint32_t n, const float *const *d_in, c
                             void *d_out, uint64_t out_cap, uint64_t *h_offsets, void *stream) {
   if (!ctx || !d_in || !ndim || !dims || !eb || !d_out || !h_offsets || n == 0 || n > kMaxBatch) return FZ_EINVAL;
   if (eb_mode > FZ_EB_REL || ((uintptr_t)d_out & 15u)) return FZ_EINVAL;
-  uint32_t pred = FZ_PRED_LORENZO1, R = 512;
+  uint32_t pred = FZ_PRED_LORENZO1, R = 512, chunk = 0;
   if (pipe) {
     if (pipe->struct_size < sizeof(uint32_t) * 3) return FZ_EINVAL;
     pred = pipe->predictor;
     if (pipe->radius) R = pipe->radius;
+    if (pipe->struct_size >= offsetof(fz_pipeline, reserved)) chunk = pipe->chunk;
   }
   if (R < 2 || R > 512) return FZ_EINVAL;
   if (pred > FZ_PRED_LORENZO2) return pred <= FZ_SEL_EXHAUSTIVE ? FZ_EUNSUPPORTED : FZ_EINVAL;
@@ -250,6 +317,7 @@ fz_status fz_compress_batch(fz_ctx *ctx, uint32_t n, const float *const *d_in, c
   key.push_back(eb_mode);
   key.push_back(R);
   key.push_back(pred);
+  key.push_back(chunk);
   key.push_back((uint64_t)(uintptr_t)d_out);
   key.push_back(out_cap);
   for (uint32_t j = 0; j < n; ++j) {
@@ -260,6 +328,7 @@ fz_status fz_compress_batch(fz_ctx *ctx, uint32_t n, const float *const *d_in, c
     if (overlaps(d_in[j], 4 * nv, d_out, out_cap)) return FZ_EINVAL;
     const uint64_t d3[3] = {dj[0], ndim[j] >= 2 ? dj[1] : 1, ndim[j] >= 3 ? dj[2] : 1};
     make_geom(ndim[j], d3, geo[j]);
+    if (chunk && (chunk < geo[j].bsize || !chunk_supported(ndim[j], geo[j].bsize, chunk))) return FZ_EUNSUPPORTED;
     CompressWs tmp;
     zsz[j] = layout_compress_split(geo[j], nullptr, nullptr, tmp, &rsz[j]);
     ztot += zsz[j];
@@ -318,6 +387,8 @@ fz_status fz_compress_batch(fz_ctx *ctx, uint32_t n, const float *const *d_in, c
       memset(&J, 0, sizeof(J));
       J.x = d_in[j];
       J.g = geo[j];
+      // the Huffman chunk of the field's encode class (explicit or tuned)
+      set_chunk(J.g, chunk ? chunk : geo[j].bsize << t.chunk_log2[geo[j].bsize == 512 ? 0 : 1]);
       layout_compress_split(geo[j], dbase + zo, dbase + ro, J.ws, nullptr);
       J.ws.spin = ctx->spin_cycles;
       zo += zsz[j];
@@ -371,7 +442,7 @@ fz_status fz_compress_batch(fz_ctx *ctx, uint32_t n, const float *const *d_in, c
   BatchPlan *plan = find_plan(ctx, key);
   cudaError_t e = cudaSuccess;
   if (!plan) {
-    BatchTune t{18, 0, 0, 0};  // 0 = the occupancy limit
+    BatchTune t{18, 0, 0, 0, {0, 0}};  // 0 = the occupancy limit
     if (ctx->batch_tuning) {
       auto run = [&](const BatchTune &c) {
         const uint64_t segs = fill(c);
@@ -383,10 +454,17 @@ fz_status fz_compress_batch(fz_ctx *ctx, uint32_t n, const float *const *d_in, c
           {&BatchTune::encode_per_sm, {2, 4, 0}},
       };
       if ((st = autotune(t, space, run))) return st;
+      if (!chunk && (st = tune_chunks(ctx, t, n, P.emem, d_out, d_in, geo, s, [&](const BatchTune &c) {
+            const uint64_t segs = fill(c);
+            return time_run(s, [&](cudaStream_t q) { return enqueue(c, segs, q); });
+          }, reinterpret_cast<const uint64_t *>(hres + sizeof(Result) * (size_t)n))))
+        return st;
     }
     plan = add_plan(ctx, key, false);
     if (!plan) return FZ_ENOMEM;
     plan->tune = t;
+    for (int c = 0; c < 2; ++c)
+      plan->chunk[c] = P.emem[c].empty() ? 0u : (chunk ? chunk : (c == 0 ? 512u : 1024u) << t.chunk_log2[c]);
     if (ctx->batch_graphs) {
       const uint64_t segs = fill(t);
       plan->exec = capture(ctx, [&](cudaStream_t q) { return enqueue(t, segs, q); });
@@ -451,7 +529,7 @@ fz_status fz_decompress_batch(fz_ctx *ctx, uint32_t n, const void *d_in, const u
       if (geo[j].n > max_plain) max_plain = geo[j].n;
     } else {
       if (h.predictor > FZ_PRED_LORENZO2) return FZ_EUNSUPPORTED;
-      if (h.chunk != geo[j].bsize) return FZ_EUNSUPPORTED;  // batched decode: one chunk per block
+      if (h.chunk < geo[j].bsize) return FZ_EUNSUPPORTED;  // batched decode: chunks of whole blocks
       const int c = qclass(h.ndim, h.predictor == FZ_PRED_LORENZO2 ? 2 : 1);
       mem[c].push_back((uint32_t)dec.size());
       units[c] += dec_units(h);
@@ -460,6 +538,7 @@ fz_status fz_decompress_batch(fz_ctx *ctx, uint32_t n, const void *d_in, const u
     }
     key.push_back(h.flags);
     key.push_back(h.predictor);
+    key.push_back(h.chunk);
     key.push_back(h.ndim);
     for (int a = 0; a < 3; ++a) key.push_back(h.dims[a]);
   }
@@ -525,7 +604,7 @@ fz_status fz_decompress_batch(fz_ctx *ctx, uint32_t n, const void *d_in, const u
   };
   BatchPlan *plan = find_plan(ctx, key);
   if (!plan) {
-    BatchTune t{18, 0, 0, 0};
+    BatchTune t{18, 0, 0, 0, {0, 0}};
     if (ctx->batch_tuning && nd) {
       auto run = [&](const BatchTune &c) { return time_run(s, [&](cudaStream_t q) { return enqueue(c, q); }); };
       std::vector<std::pair<int BatchTune::*, std::vector<int>>> space = {{&BatchTune::decode_per_sm, {1, 0}}};

@@ -878,8 +878,11 @@ __global__ void __launch_bounds__(DecCta<NDIM, K>::T, 1) k_decode_batch(const De
       const uint64_t start = unit_start(sp.chunk_bits, sp.goff, sp.n_chunks, u, cb);
       const uint64_t j = u * kDecUnit + (t & 31);
       if (j < sp.n_chunks) {
-        if (sp.n_exc) decode_chunk<NDIM, K, true, T>(sp, sg, slut, sstate + t, sring + t, j, 1, start, cb, vecbase);
-        else decode_chunk<NDIM, K, false, T>(sp, sg, slut, sstate + t, sring + t, j, 1, start, cb, vecbase);
+        const uint32_t k = sg.chunk / sg.bsize;  // blocks per chunk
+        const uint64_t jb = j * k;
+        const uint32_t nblk = (uint32_t)(sg.n_blocks - jb < k ? sg.n_blocks - jb : k);
+        if (sp.n_exc) decode_chunk<NDIM, K, true, T>(sp, sg, slut, sstate + t, sring + t, jb, nblk, start, cb, vecbase);
+        else decode_chunk<NDIM, K, false, T>(sp, sg, slut, sstate + t, sring + t, jb, nblk, start, cb, vecbase);
       }
     }
     r = t1;
@@ -1135,6 +1138,7 @@ void fill_dec_job(void *dst, const uint8_t *d_in, const fz_header &h, float *d_o
   DecJob J;
   memset(&J, 0, sizeof(J));
   make_geom(h.ndim, h.dims, J.g);
+  set_chunk(J.g, h.chunk);
   DecParams &p = J.p;
   p.words = reinterpret_cast<const uint32_t *>(d_in + h.off_bits);
   p.n_words = (h.total_bits + 31) / 32;

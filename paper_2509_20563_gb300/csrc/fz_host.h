@@ -13,6 +13,7 @@ struct BatchPlan {
   bool decompress = false;
   std::vector<uint64_t> key;
   BatchTune tune{};
+  uint32_t chunk[2] = {0, 0};  // compress plans: the chunk of each encode class (0 = class absent)
   cudaGraphExec_t exec = nullptr;
 };
 }  // namespace fz

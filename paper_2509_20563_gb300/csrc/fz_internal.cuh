@@ -385,6 +385,7 @@ struct BatchTune {
   int quant_per_sm;     // quantizer CTAs per SM
   int encode_per_sm;    // encoder CTAs per SM
   int decode_per_sm;    // decoder CTAs per SM
+  int chunk_log2[2];    // Huffman chunk = block size << chunk_log2, per encode class (3D; 1D and 2D)
 };
 
 }  // namespace fz

@@ -42,20 +42,28 @@ def _fields(seed=5):
     return [f.contiguous() for f in fs], ebs
 
 
-def _check_batch(xs, ebs, mode="rel", predictor="lorenzo1", with_oracle=True):
+def _chunk_of(stream_bytes):
+    """The Huffman chunk a stream's header records (0 for raw and constant streams)."""
+    return int(np.frombuffer(np.ascontiguousarray(stream_bytes[88:92]).tobytes(), np.uint32)[0])
+
+
+def _check_batch(xs, ebs, mode="rel", predictor="lorenzo1", with_oracle=True, chunk=0, ctx=None):
     xg = [x.cuda() for x in xs]
-    buf, offs = fz.compress_batch(xg, ebs, mode=mode, predictor=predictor)
+    buf, offs = fz.compress_batch(xg, ebs, mode=mode, predictor=predictor, chunk=chunk, ctx=ctx)
     assert len(offs) == len(xs) + 1
     hb = buf[: offs[-1]].cpu().numpy()
     singles = []
     for j, (x, eb) in enumerate(zip(xs, ebs)):
-        one = fz.compress(xg[j], eb, mode=mode, predictor=predictor)
+        C = _chunk_of(hb[offs[j]: offs[j] + 256])  # the batch's chunk for this field (tuned or given)
+        if chunk:
+            assert C in (0, chunk), (j, C)
+        one = fz.compress(xg[j], eb, mode=mode, predictor=predictor, chunk=C)
         s = one.cpu().numpy()
         assert offs[j] % 16 == 0
         assert offs[j + 1] - offs[j] == (s.size + 15) // 16 * 16, j
         assert np.array_equal(hb[offs[j]: offs[j] + s.size], s), j
         if with_oracle:
-            ref = oracle.compress(x.numpy(), eb, mode=mode, lorenzo_k=2 if predictor == "lorenzo2" else 1)
+            ref = oracle.compress(x.numpy(), eb, mode=mode, lorenzo_k=2 if predictor == "lorenzo2" else 1, chunk=C)
             assert np.array_equal(s, ref), j
         singles.append(one)
     ys = fz.decompress_batch(buf, offs)
@@ -99,15 +107,18 @@ def test_batch_modes(mode, predictor):
 
 
 def test_batch_options_do_not_change_bytes():
+    """Launch shapes (tuned or not, graph or eager) never change the bytes
+    when the chunk is fixed; the chunk itself is the one tuned parameter that
+    does (and every stream records it)."""
     xs, ebs = _fields(seed=9)
     xg = [x.cuda() for x in xs]
-    ref, ro = fz.compress_batch(xg, ebs)
+    ref, ro = fz.compress_batch(xg, ebs, chunk=1024)
     ref = ref[: ro[-1]].cpu().numpy()
     try:
         for tune, graphs in [(False, False), (False, True), (True, False)]:
             fz.set_batch_options(autotune=tune, graphs=graphs)
             for _ in range(2):
-                buf, offs = fz.compress_batch(xg, ebs)
+                buf, offs = fz.compress_batch(xg, ebs, chunk=1024)
                 assert offs == ro
                 assert np.array_equal(buf[: offs[-1]].cpu().numpy(), ref)
     finally:
@@ -136,8 +147,33 @@ def test_batch_full_size_workload():
     buf, offs = fz.compress_batch(xs, 1e-4)
     ys = fz.decompress_batch(buf, offs)
     for j, x in enumerate(xs):
-        one = fz.compress(x, 1e-4)
+        C = _chunk_of(buf[offs[j]: offs[j] + 256].cpu().numpy())
+        one = fz.compress(x, 1e-4, chunk=C)
         assert torch.equal(buf[offs[j]: offs[j] + one.numel()], one), j
         eba = 1e-4 * (float(x.max()) - float(x.min()))
         assert float((ys[j].double() - x.double()).abs().max()) <= eba, j
         del one
+
+
+@pytest.mark.parametrize("chunk", [2048, 4096])
+def test_batch_explicit_chunk(chunk):
+    """A chunk given for the whole batch: every Huffman stream records it and
+    equals the single call and the oracle with that chunk; the batched
+    decoder reads the multi-block chunks bit-exactly."""
+    xs, ebs = _fields(seed=8)
+    _check_batch(xs, ebs, chunk=chunk)
+
+
+def test_batch_autotuner_picks_a_chunk():
+    """The autotuner's chunk choice (per kind of field) is one of the block
+    size, its double or its quadruple, is reported by the profile, and is the
+    chunk every stream of that kind records."""
+    ctx = fz.Context(0)
+    try:
+        xs, ebs = _fields(seed=9)
+        _check_batch(xs, ebs, with_oracle=False, ctx=ctx)
+        prof = fz.profile(ctx=ctx)
+        c3, c12 = int(prof.batch_chunk[0]), int(prof.batch_chunk[1])
+        assert c3 in (512, 1024, 2048) and c12 in (1024, 2048, 4096)
+    finally:
+        ctx.close()
