@@ -90,6 +90,8 @@ def _declare(L):
                                     u16p, u8p, C.c_uint64, u64p]
     L.orc_compress_chunk.argtypes = [f32p, C.c_uint32, u64p, C.c_uint32, C.c_double, C.c_uint32, C.c_uint32,
                                      u16p, C.c_uint32, u8p, C.c_uint64, u64p]
+    L.orc_compress_full.argtypes = [f32p, C.c_uint32, u64p, C.c_uint32, C.c_double, C.c_uint32, C.c_uint32,
+                                    u16p, C.c_uint32, C.c_uint32, u8p, C.c_uint64, u64p]
     L.orc_interp_block.argtypes = [C.c_int, C.c_int, u8p, i32p, u8p, i64p]
     L.orc_interp_block.restype = None
     L.orc_block_costs.argtypes = [i32p, u8p, i32p, u8p, C.c_uint32, u64p]
@@ -242,11 +244,13 @@ PRED_IDS = {"lorenzo1": 0, "lorenzo2": 1, "interp_linear": 2, "interp_cubic": 3,
 
 
 def compress(x: np.ndarray, eb: float, mode: str = "rel", lorenzo_k: int = 1, radius: int = 512,
-             predictor=None, weights: np.ndarray | None = None, chunk: int = 0) -> np.ndarray:
+             predictor=None, weights: np.ndarray | None = None, chunk: int = 0,
+             encoder: str = "huffman") -> np.ndarray:
     """Compress a C-order float32 array (last axis fastest = the format's x).
     ``predictor`` (name or id) overrides ``lorenzo_k``; ``weights`` are the
     selector network's bfloat16 bits for predictor "mlp"; ``chunk`` is the
-    Huffman chunk in symbols (0: the block size)."""
+    Huffman chunk in symbols (0: the block size); ``encoder`` "huffman" or
+    "shuffle" (bit-shuffle + zero-word encoding)."""
     x = np.ascontiguousarray(x, dtype=np.float32)
     shape = x.shape
     ndim = len(shape)
@@ -259,8 +263,9 @@ def compress(x: np.ndarray, eb: float, mode: str = "rel", lorenzo_k: int = 1, ra
     if weights is not None:
         weights = np.ascontiguousarray(weights, dtype=np.uint16)
         wp = _p(weights, u16p)
-    st = lib().orc_compress_chunk(_p(x, f32p), ndim, _p(d, u64p), 1 if mode == "rel" else 0, float(eb), pred,
-                                  radius, wp, int(chunk), _p(out, u8p), cap, C.byref(nb))
+    st = lib().orc_compress_full(_p(x, f32p), ndim, _p(d, u64p), 1 if mode == "rel" else 0, float(eb), pred,
+                                 radius, wp, int(chunk), {"huffman": 0, "shuffle": 1}[encoder], _p(out, u8p), cap,
+                                 C.byref(nb))
     _chk(st, "compress")
     return out[: nb.value].copy()
 

@@ -395,6 +395,7 @@ static uint32_t get_bit(const uint32_t *w, uint64_t p) { return (w[p >> 5] >> (3
 #define F_RAW 1u
 #define F_CONST 2u
 #define F_IDS 4u
+#define F_SHUF 8u /* bit-shuffle + zero-word encoding instead of Huffman */
 
 static void put_min_header(uint8_t *h, uint16_t flags, uint32_t ndim, uint32_t ebmode,
                            const uint64_t dims[3], double eb, uint64_t total) {
@@ -857,6 +858,83 @@ static int write_raw(const float *x, uint64_t n, uint32_t ndim, uint32_t ebmode,
  * eb_mode 0 = ABS, 1 = REL (value range over finite values).  Output is the
  * complete stream; with a per-block choice it carries the 2-bit predictor id
  * of every block. */
+/* ------------------------------------------------------------------------ */
+/* Bit-shuffle + zero-word encoder (FZMod-Speed, §3.2-§3.3: the encoder of  */
+/* FZ-GPU, in place of the Huffman coder)                                   */
+/* ------------------------------------------------------------------------ */
+/* The codes (0..2R-1, code 0 = outlier) become residuals d = code - R and
+ * then zig-zag values v = 2d (d >= 0) or -2d - 1 (d < 0), so that small
+ * residuals have few nonzero bits (v < 2R).  Each run of 64 codes is read as
+ * 32 rows of 32 bits, row r = v[2r] | v[2r+1] << 16, and the 32x32 bit
+ * matrix is transposed: column word b has bit r = bit b of row r.  A 32-bit
+ * map per run flags the nonzero column words; only those are stored, in
+ * column order.  A tile of 1024 codes (16 runs) is one chunk: its stored
+ * length is 32 bits per word it stores. */
+#define SHUF_RUN 64u
+#define SHUF_TILE 1024u
+
+static uint32_t zigzag(int32_t d) { return d >= 0 ? (uint32_t)d << 1 : ((uint32_t)(-(d + 1)) << 1) | 1u; }
+static int32_t unzigzag(uint32_t v) { return (v & 1u) ? -(int32_t)(v >> 1) - 1 : (int32_t)(v >> 1); }
+
+/* Encodes npad codes: maps[npad/64], words (capacity cap_words), per-tile
+ * lengths in bits; returns the number of words, or ~0 if cap_words is too
+ * small. */
+static uint64_t shuf_encode(const uint16_t *codes, uint64_t npad, uint32_t R, uint32_t *maps, uint32_t *words,
+                            uint64_t cap_words, uint32_t *tile_bits) {
+  uint64_t nw = 0;
+  const uint64_t n_runs = npad / SHUF_RUN, n_tiles = (npad + SHUF_TILE - 1) / SHUF_TILE;
+  for (uint64_t t = 0; t < n_tiles; t++) tile_bits[t] = 0;
+  for (uint64_t k = 0; k < n_runs; k++) {
+    uint32_t row[32];
+    for (int r = 0; r < 32; r++) {
+      uint32_t v0 = zigzag((int32_t)codes[k * SHUF_RUN + 2 * r] - (int32_t)R);
+      uint32_t v1 = zigzag((int32_t)codes[k * SHUF_RUN + 2 * r + 1] - (int32_t)R);
+      row[r] = v0 | (v1 << 16);
+    }
+    uint32_t map = 0;
+    for (int b = 0; b < 32; b++) {
+      uint32_t w = 0;
+      for (int r = 0; r < 32; r++) w |= ((row[r] >> b) & 1u) << r;
+      if (w) {
+        map |= 1u << b;
+        if (nw >= cap_words) return ~0ull;
+        words[nw++] = w;
+        tile_bits[k * SHUF_RUN / SHUF_TILE] += 32;
+      }
+    }
+    maps[k] = map;
+  }
+  return nw;
+}
+
+/* Inverse of shuf_encode for one tile: reads the tile's runs from maps and
+ * words[*pw ..], checks that the tile uses exactly tile_bits bits and that
+ * every value is below 2R; writes the codes. */
+static int shuf_decode_tile(const uint8_t *maps_b, const uint8_t *words_b, uint64_t n_words, uint64_t *pw,
+                            uint64_t t, uint64_t npad, uint32_t R, uint32_t tile_bits, uint16_t *codes) {
+  if (tile_bits % 32) return ORC_ECORRUPT;
+  const uint64_t w_end = *pw + tile_bits / 32;
+  if (w_end > n_words) return ORC_ECORRUPT;
+  for (uint64_t k = t * (SHUF_TILE / SHUF_RUN); k < (t + 1) * (SHUF_TILE / SHUF_RUN) && k * SHUF_RUN < npad; k++) {
+    uint32_t map = get_u32(maps_b + 4 * k), row[32];
+    memset(row, 0, sizeof(row));
+    for (int b = 0; b < 32; b++) {
+      if (!((map >> b) & 1u)) continue;
+      if (*pw >= w_end) return ORC_ECORRUPT;
+      uint32_t w = get_u32(words_b + 4 * *pw);
+      (*pw)++;
+      for (int r = 0; r < 32; r++) row[r] |= ((w >> r) & 1u) << b;
+    }
+    for (int r = 0; r < 32; r++) {
+      uint32_t v0 = row[r] & 0xffffu, v1 = row[r] >> 16;
+      if (v0 >= 2 * R || v1 >= 2 * R) return ORC_ECORRUPT;
+      codes[k * SHUF_RUN + 2 * r] = (uint16_t)(unzigzag(v0) + (int32_t)R);
+      codes[k * SHUF_RUN + 2 * r + 1] = (uint16_t)(unzigzag(v1) + (int32_t)R);
+    }
+  }
+  return *pw == w_end ? ORC_OK : ORC_ECORRUPT;
+}
+
 /* Huffman chunk sizes of the format (symbols per chunk; chunk j covers
  * code-stream symbols [jC, min((j+1)C, Npad))): the block size, a power-of-
  * two multiple of it up to 4096, or, for 3D, 64 (one 8x8 plane of a block).
@@ -868,9 +946,15 @@ static int chunk_valid(uint32_t ndim, uint64_t bsize, uint64_t C) {
   return C > bsize && C <= 4096 && (C % bsize) == 0 && (C & (C - 1)) == 0;
 }
 
+int orc_compress_full(const float *x, uint32_t ndim, const uint64_t dims[3], uint32_t eb_mode, double eb,
+                      uint32_t pred, uint32_t R, const uint16_t *w, uint32_t chunk, uint32_t encoder, uint8_t *out,
+                      uint64_t cap, uint64_t *out_bytes);
+
 int orc_compress_chunk(const float *x, uint32_t ndim, const uint64_t dims[3], uint32_t eb_mode, double eb,
                        uint32_t pred, uint32_t R, const uint16_t *w, uint32_t chunk, uint8_t *out, uint64_t cap,
-                       uint64_t *out_bytes);
+                       uint64_t *out_bytes) {
+  return orc_compress_full(x, ndim, dims, eb_mode, eb, pred, R, w, chunk, 0, out, cap, out_bytes);
+}
 
 int orc_compress_pred(const float *x, uint32_t ndim, const uint64_t dims[3], uint32_t eb_mode, double eb,
                       uint32_t pred, uint32_t R, const uint16_t *w, uint8_t *out, uint64_t cap,
@@ -878,11 +962,12 @@ int orc_compress_pred(const float *x, uint32_t ndim, const uint64_t dims[3], uin
   return orc_compress_chunk(x, ndim, dims, eb_mode, eb, pred, R, w, 0, out, cap, out_bytes);
 }
 
-/* The whole compression path with Huffman chunks of `chunk` symbols (0: the
- * block size). */
-int orc_compress_chunk(const float *x, uint32_t ndim, const uint64_t dims[3], uint32_t eb_mode, double eb,
-                       uint32_t pred, uint32_t R, const uint16_t *w, uint32_t chunk, uint8_t *out, uint64_t cap,
-                       uint64_t *out_bytes) {
+/* The whole compression path.  encoder 0: Huffman with chunks of `chunk`
+ * symbols (0: the block size); encoder 1: the bit-shuffle + zero-word
+ * encoder (Lorenzo predictors only, chunk 0 or 1024). */
+int orc_compress_full(const float *x, uint32_t ndim, const uint64_t dims[3], uint32_t eb_mode, double eb,
+                      uint32_t pred, uint32_t R, const uint16_t *w, uint32_t chunk, uint32_t encoder, uint8_t *out,
+                      uint64_t cap, uint64_t *out_bytes) {
   uint64_t n;
   int st = check_args(ndim, dims, &n);
   if (st) return st;
@@ -891,7 +976,11 @@ int orc_compress_chunk(const float *x, uint32_t ndim, const uint64_t dims[3], ui
   if (pred >= 2 && ndim != 3) return ORC_EUNSUPPORTED;
   if (pred == 16 && !w) return ORC_EINVAL;
   if (R < 2 || R > 512) return ORC_EINVAL;
-  {
+  if (encoder > 1) return ORC_EINVAL;
+  if (encoder == 1) {
+    if (pred > 1 || (chunk && chunk != SHUF_TILE)) return ORC_EUNSUPPORTED;
+    chunk = SHUF_TILE;
+  } else {
     uint32_t b[3];
     orc_block_shape(ndim, b);
     if (chunk && !chunk_valid(ndim, (uint64_t)b[0] * b[1] * b[2], chunk)) return ORC_EUNSUPPORTED;
@@ -1000,18 +1089,31 @@ int orc_compress_chunk(const float *x, uint32_t ndim, const uint64_t dims[3], ui
   uint32_t nsym = 2 * R;
   uint8_t len[ORC_MAXSYM];
   uint32_t code[ORC_MAXSYM];
-  st = orc_huffman_lengths(hist, nsym, len);
-  if (st) goto done;
-  st = orc_canonical_codes(len, nsym, code);
-  if (st) goto done;
   uint64_t total_bits = 0;
-  for (uint32_t s = 0; s < nsym; s++) total_bits += hist[s] * len[s];
+  const uint64_t npad = g.n_blocks * g.bsize;
+  uint32_t *smaps = NULL, *swords = NULL, *stile = NULL;
+  if (encoder == 0) {
+    st = orc_huffman_lengths(hist, nsym, len);
+    if (st) goto done;
+    st = orc_canonical_codes(len, nsym, code);
+    if (st) goto done;
+    for (uint32_t s = 0; s < nsym; s++) total_bits += hist[s] * len[s];
+  } else {
+    /* step 10 (shuffle): the whole encoding first; its size decides the layout */
+    const uint64_t cap_words = (npad / SHUF_RUN) * 32;
+    smaps = (uint32_t *)malloc((npad / SHUF_RUN) * 4 + 4);
+    swords = (uint32_t *)malloc(cap_words * 4 + 4);
+    stile = (uint32_t *)malloc(((npad + SHUF_TILE - 1) / SHUF_TILE) * 4 + 4);
+    if (!smaps || !swords || !stile) { st = ORC_ENOMEM; free(smaps); free(swords); free(stile); goto done; }
+    total_bits = 32 * shuf_encode(codes, npad, R, smaps, swords, cap_words, stile);
+  }
 
   /* layout */
   uint64_t C = chunk ? chunk : g.bsize;
-  uint64_t n_chunks = (g.n_blocks * g.bsize + C - 1) / C;
+  uint64_t n_chunks = (npad + C - 1) / C;
   uint64_t off_lens = HDR;
-  uint64_t off_ids = align16(off_lens + nsym);
+  /* Huffman: the code lengths; shuffle: the 32-bit word maps, one per 64 codes */
+  uint64_t off_ids = align16(off_lens + (encoder ? 4 * (npad / SHUF_RUN) : nsym));
   uint64_t ids_bytes = sel ? (g.n_blocks + 3) / 4 : 0;
   uint64_t off_anch = align16(off_ids + ids_bytes);
   uint64_t off_cb = align16(off_anch + 4 * g.n_blocks);
@@ -1024,14 +1126,15 @@ int orc_compress_chunk(const float *x, uint32_t ndim, const uint64_t dims[3], ui
   uint64_t total = align16(off_bits + 4 * n_words);
   if (total > HDR + 4 * n) {
     st = write_raw(x, n, ndim, eb_mode, dd, eb, out, cap, out_bytes);
+    free(smaps); free(swords); free(stile);
     goto done;
   }
-  if (cap < total) { st = ORC_EBUFFER; goto done; }
+  if (cap < total) { st = ORC_EBUFFER; free(smaps); free(swords); free(stile); goto done; }
   memset(out, 0, total);
   uint8_t *h = out;
   put_u32(h + H_MAGIC, MAGIC);
   put_u16(h + H_VERSION, 1);
-  put_u16(h + H_FLAGS, sel ? F_IDS : 0);
+  put_u16(h + H_FLAGS, sel ? F_IDS : (encoder ? F_SHUF : 0));
   put_u32(h + H_NDIM, ndim);
   put_u32(h + H_EBMODE, eb_mode);
   for (int a = 0; a < 3; a++) put_u64(h + H_DIMS + 8 * a, dd[a]);
@@ -1059,7 +1162,8 @@ int orc_compress_chunk(const float *x, uint32_t ndim, const uint64_t dims[3], ui
   put_u64(h + H_OFF_EVAL, off_eval);
   put_u64(h + H_OFF_BITS, off_bits);
   put_u64(h + H_TOTAL, total);
-  memcpy(out + off_lens, len, nsym);
+  if (encoder == 0) memcpy(out + off_lens, len, nsym);
+  else for (uint64_t k = 0; k < npad / SHUF_RUN; k++) put_u32(out + off_lens + 4 * k, smaps[k]);
   if (sel) memcpy(out + off_ids, ids, ids_bytes);
   for (uint64_t b = 0; b < g.n_blocks; b++) put_u32(out + off_anch + 4 * b, (uint32_t)anchors[b]);
   for (uint64_t i = 0; i < n_out; i++) {
@@ -1070,11 +1174,18 @@ int orc_compress_chunk(const float *x, uint32_t ndim, const uint64_t dims[3], ui
     put_u32(out + off_eidx + 4 * i, eidx[i]);
     put_u32(out + off_eval + 4 * i, eval[i]);
   }
+  if (encoder == 1) {
+    for (uint64_t j = 0; j < n_chunks; j++) put_u32(out + off_cb + 4 * j, stile[j]);
+    for (uint64_t k = 0; k < n_words; k++) put_u32(out + off_bits + 4 * k, swords[k]);
+    free(smaps); free(swords); free(stile);
+    *out_bytes = total;
+    st = ORC_OK;
+    goto done;
+  }
   /* step 10: chunked encode; chunk j = code-stream symbols [jC, (j+1)C) */
   uint32_t *words = (uint32_t *)calloc(n_words + 1, 4);
   if (!words) { st = ORC_ENOMEM; goto done; }
   uint64_t p = 0;
-  const uint64_t npad = g.n_blocks * g.bsize;
   for (uint64_t j = 0; j < n_chunks; j++) {
     uint64_t cb = 0;
     for (uint64_t i = j * C; i < (j + 1) * C && i < npad; i++) {
@@ -1150,7 +1261,8 @@ int orc_decompress(const uint8_t *in, uint64_t in_bytes, float *out, uint64_t ou
     for (uint64_t i = 0; i < n; i++) out[i] = v;
     return ORC_OK;
   }
-  if (flags != 0 && flags != F_IDS) return ORC_EUNSUPPORTED;
+  if (flags != 0 && flags != F_IDS && flags != F_SHUF) return ORC_EUNSUPPORTED;
+  const int shuf = flags == F_SHUF;
   grid_t g;
   make_grid(ndim, dims, &g);
   uint32_t R = get_u32(in + H_RADIUS), nsym = 2 * R;
@@ -1159,6 +1271,7 @@ int orc_decompress(const uint8_t *in, uint64_t in_bytes, float *out, uint64_t ou
   if (R < 2 || R > 512) return ORC_ECORRUPT;
   if (sel != (pred == 16 || pred == 17) || !(pred <= 3 || pred == 16 || pred == 17)) return ORC_ECORRUPT;
   if (pred >= 2 && ndim != 3) return ORC_ECORRUPT;
+  if (shuf && pred > 1) return ORC_ECORRUPT;
   uint64_t o_ids = get_u64(in + H_OFF_IDS);
   for (int a = 0; a < 3; a++)
     if (get_u32(in + H_BLOCK + 4 * a) != g.b[a]) return ORC_ECORRUPT;
@@ -1167,36 +1280,40 @@ int orc_decompress(const uint8_t *in, uint64_t in_bytes, float *out, uint64_t ou
   uint64_t n_out = get_u64(in + H_NOUT), n_exc = get_u64(in + H_NEXC), tbits = get_u64(in + H_TBITS);
   uint64_t C = get_u32(in + H_CHUNK);
   const uint64_t npad = g.n_blocks * g.bsize;
-  if (nb != g.n_blocks || !chunk_valid(ndim, g.bsize, C) || nch != (npad + C - 1) / C) return ORC_ECORRUPT;
+  if (nb != g.n_blocks || !(shuf ? C == SHUF_TILE : chunk_valid(ndim, g.bsize, C)) || nch != (npad + C - 1) / C)
+    return ORC_ECORRUPT;
+  const uint64_t lens_bytes = shuf ? 4 * (npad / SHUF_RUN) : nsym;
   if (n_out > n || n_exc > n) return ORC_ECORRUPT;
   uint64_t o_len = get_u64(in + H_OFF_LENS), o_anch = get_u64(in + H_OFF_ANCH), o_cb = get_u64(in + H_OFF_CBITS);
   uint64_t o_oi = get_u64(in + H_OFF_OIDX), o_ov = get_u64(in + H_OFF_OVAL), o_ei = get_u64(in + H_OFF_EIDX);
   uint64_t o_ev = get_u64(in + H_OFF_EVAL), o_bits = get_u64(in + H_OFF_BITS);
   uint64_t n_words = (tbits + 31) / 32;
   if (sel && o_ids + (nb + 3) / 4 > total) return ORC_ECORRUPT;
-  if (o_len + nsym > total || o_anch + 4 * nb > total || o_cb + 4 * nch > total || o_oi + 4 * n_out > total ||
+  if (o_len + lens_bytes > total || o_anch + 4 * nb > total || o_cb + 4 * nch > total || o_oi + 4 * n_out > total ||
       o_ov + 4 * n_out > total || o_ei + 4 * n_exc > total || o_ev + 4 * n_exc > total ||
       o_bits + 4 * n_words > total)
     return ORC_ECORRUPT;
   uint8_t len[ORC_MAXSYM];
   uint32_t code[ORC_MAXSYM];
-  memcpy(len, in + o_len, nsym);
-  if (orc_canonical_codes(len, nsym, code)) return ORC_ECORRUPT;
   /* canonical decode tables: per length the first code, count and the start
    * of its symbols in the (length, symbol)-sorted list */
   uint32_t first[ORC_LMAX + 1] = {0}, count[ORC_LMAX + 1] = {0}, base[ORC_LMAX + 1] = {0};
   uint16_t sorted[ORC_MAXSYM];
-  uint32_t ns = 0;
-  for (int l = 1; l <= ORC_LMAX; l++) {
-    base[l] = ns;
-    for (uint32_t s = 0; s < nsym; s++)
-      if (len[s] == l) {
-        if (count[l] == 0) first[l] = code[s];
-        count[l]++;
-        sorted[ns++] = (uint16_t)s;
-      }
+  if (!shuf) {
+    memcpy(len, in + o_len, nsym);
+    if (orc_canonical_codes(len, nsym, code)) return ORC_ECORRUPT;
+    uint32_t ns = 0;
+    for (int l = 1; l <= ORC_LMAX; l++) {
+      base[l] = ns;
+      for (uint32_t s = 0; s < nsym; s++)
+        if (len[s] == l) {
+          if (count[l] == 0) first[l] = code[s];
+          count[l]++;
+          sorted[ns++] = (uint16_t)s;
+        }
+    }
+    if (ns == 0) return ORC_ECORRUPT;
   }
-  if (ns == 0) return ORC_ECORRUPT;
   uint32_t *words = (uint32_t *)malloc((n_words + 1) * 4);
   uint16_t *codes = (uint16_t *)malloc(npad * 2);
   int64_t *v = (int64_t *)malloc(g.bsize * 8);
@@ -1208,7 +1325,16 @@ int orc_decompress(const uint8_t *in, uint64_t in_bytes, float *out, uint64_t ou
   /* step 11a: the code stream, chunk by chunk; each chunk must use exactly
    * its stored bit count */
   uint64_t p = 0, oc = 0, ec = 0;
-  for (uint64_t j = 0; j < nch; j++) {
+  if (shuf) {
+    uint64_t pw = 0;
+    for (uint64_t j = 0; j < nch; j++) {
+      st = shuf_decode_tile(in + o_len, in + o_bits, n_words, &pw, j, npad, R, get_u32(in + o_cb + 4 * j), codes);
+      if (st) goto ddone;
+    }
+    if (pw != n_words || tbits != 32 * n_words) { st = ORC_ECORRUPT; goto ddone; }
+    p = tbits;
+  }
+  for (uint64_t j = 0; j < nch && !shuf; j++) {
     uint64_t cb = get_u32(in + o_cb + 4 * j), p_end = p + cb;
     if (p_end > tbits) { st = ORC_ECORRUPT; goto ddone; }
     for (uint64_t i = j * C; i < (j + 1) * C && i < npad; i++) {

@@ -603,3 +603,91 @@ def test_chunk_size_rejects_bad_values_and_bad_lengths():
     with pytest.raises(oracle.OracleError) as e:
         oracle.decompress(t)
     assert e.value.code == oracle.ECORRUPT
+
+
+# ---------------------------------------------------------------- bit-shuffle + zero-word encoder (FZMod-Speed, §3.3)
+def _numpy_shuffle(codes, R):
+    """The encoder's definition through numpy's bit unpacking: zig-zag the
+    residuals, view 64 codes as 32 little-endian rows of 32 bits, transpose
+    each 32x32 bit matrix (np.unpackbits / np.packbits), keep the nonzero
+    column words in column order."""
+    d = codes.astype(np.int64) - R
+    v = np.where(d >= 0, 2 * d, -2 * d - 1).astype(np.uint32)
+    rows = (v[0::2] | (v[1::2] << 16)).astype("<u4").reshape(-1, 32)           # runs x 32 rows
+    bits = np.unpackbits(rows.view(np.uint8).reshape(-1, 32, 4), axis=2, bitorder="little")  # runs x 32 x 32
+    cols = np.ascontiguousarray(bits.transpose(0, 2, 1))                         # runs x col b x row r
+    words = np.packbits(cols, axis=2, bitorder="little").reshape(-1, 32, 4).view("<u4")[..., 0]  # runs x 32
+    nz = words != 0
+    maps = (nz.astype(np.uint64) << np.arange(32, dtype=np.uint64)).sum(1).astype(np.uint32)
+    return maps, words[nz].astype(np.uint32), nz
+
+
+@pytest.mark.parametrize("shape", [(40, 37, 70), (9, 8, 17), (61, 450), (100003,)])
+@pytest.mark.parametrize("eb", [1e-2, 1e-4])
+def test_shuffle_encoder_matches_numpy_transpose(shape, eb):
+    x = synth.smooth_nd(shape, seed=len(shape) + 11).numpy()
+    buf = oracle.compress(x, eb, encoder="shuffle")
+    h = buf[:256].tobytes()
+    u64 = lambda o: int.from_bytes(h[o:o + 8], "little")
+    if int.from_bytes(h[6:8], "little") != 8:
+        pytest.skip("raw fallback")
+    ndim = len(shape)
+    ebx2, inv2eb, ebchk = oracle.constants(eb * (float(x.max()) - float(x.min())))
+    codes, _, _, _, _ = oracle.quantize_stage(x, ndim, shape[::-1], inv2eb, ebx2, ebchk)
+    maps, words, nz = _numpy_shuffle(codes, 512)
+    off_maps, off_cb, off_bits, tbits = u64(136), u64(160), u64(200), u64(128)
+    assert int.from_bytes(h[88:92], "little") == 1024
+    assert np.array_equal(buf[off_maps:off_maps + 4 * maps.size].view(np.uint32), maps)
+    assert tbits == 32 * words.size
+    assert np.array_equal(buf[off_bits:off_bits + 4 * words.size].view(np.uint32), words)
+    # chunk j (1024 codes = 16 runs) stores 32 bits per word it keeps
+    per_run = nz.sum(1)
+    n_tiles = -(-codes.size // 1024)
+    want = np.add.reduceat(per_run, np.arange(0, per_run.size, 16)) * 32
+    assert np.array_equal(buf[off_cb:off_cb + 4 * n_tiles].view(np.uint32), want)
+    # zig-zag values stay below 2R: no column word above bit 9 of either half
+    assert not (maps & 0xFC00FC00).any()
+    y = oracle.decompress(buf)
+    eba = eb * (float(x.max()) - float(x.min()))
+    assert (np.abs(y.astype(np.float64) - x) <= eba).all()
+    # the same codes as the Huffman stream: identical reconstruction
+    assert np.array_equal(y.view(np.uint32), oracle.decompress(oracle.compress(x, eb)).view(np.uint32))
+
+
+def test_shuffle_special_cases_and_corruption():
+    """A field whose residuals are all zero stores no word; bad arguments and
+    damaged maps or tile lengths are rejected."""
+    x = np.tile(np.arange(64, dtype=np.float32), (8, 8, 1))  # affine in x: Lorenzo-1 residual 1 -> few bits
+    buf = oracle.compress(np.zeros((16, 16, 16), np.float32) + 2.0, 1e-3, mode="abs", encoder="shuffle")
+    h = buf[:256].tobytes()
+    assert int.from_bytes(h[128:136], "little") == 0  # no word at all
+    assert (np.abs(oracle.decompress(buf).astype(np.float64) - 2.0) <= 1e-3).all()
+    with pytest.raises(oracle.OracleError) as e:
+        oracle.compress(x, 1e-3, encoder="shuffle", predictor="interp_linear")
+    assert e.value.code == oracle.EUNSUPPORTED
+    with pytest.raises(oracle.OracleError) as e:
+        oracle.compress(x, 1e-3, encoder="shuffle", chunk=2048)
+    assert e.value.code == oracle.EUNSUPPORTED
+    buf = oracle.compress(synth.smooth_nd((24, 20, 40), 2).numpy(), 1e-3, encoder="shuffle")
+    h = buf[:256].tobytes()
+    off_maps, off_cb = int.from_bytes(h[136:144], "little"), int.from_bytes(h[160:168], "little")
+    t = buf.copy()
+    t[off_maps] ^= 1  # a column word appears or disappears: the tile length no longer matches
+    with pytest.raises(oracle.OracleError):
+        oracle.decompress(t)
+    t = buf.copy()
+    t[off_cb:off_cb + 8].view(np.uint32)[:] += np.array([32, -32], np.int64).astype(np.uint32)
+    with pytest.raises(oracle.OracleError):
+        oracle.decompress(t)
+
+
+def test_zigzag_closed_forms():
+    """Zig-zag order of the residuals (0, -1, 1, -2, 2, ...) through the
+    encoder: a run of identical codes c gives one value repeated, whose
+    column words are all-ones exactly at the set bits of zigzag(c - R)."""
+    R = 512
+    for d, v in ((0, 0), (-1, 1), (1, 2), (-2, 3), (2, 4), (-512, 1023), (511, 1022)):
+        maps, words, _ = _numpy_shuffle(np.full(64, R + d, np.uint16), R)
+        want = [b for b in range(10) if (v >> b) & 1] + [16 + b for b in range(10) if (v >> b) & 1]
+        assert [b for b in range(32) if (int(maps[0]) >> b) & 1] == want, d
+        assert (words == 0xFFFFFFFF).all()
