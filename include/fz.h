@@ -77,7 +77,8 @@ typedef struct {
                                   2D 32x32, 3D 8x8x8), which is also the only shape this build accepts
                                   (others: FZ_EUNSUPPORTED); axes beyond ndim must be 0 or 1 */
   uint32_t chunk;              /* symbols per Huffman chunk; 0 = the block size */
-  uint32_t reserved;           /* must be 0 */
+  uint32_t encoder;            /* FZ_ENC_HUFFMAN (0) or FZ_ENC_SHUFFLE (1, the bit-shuffle + zero-word encoder of
+                                  FZMod-Speed, §3.3; Lorenzo predictors only, chunk 0 or 1024) */
   const void *selector_weights;/* device pointer to a selector weight blob (FZ_SEL_MLP only) */
 } fz_pipeline;
 
@@ -117,6 +118,11 @@ typedef struct {
 #define FZ_FLAG_RAW 1u
 #define FZ_FLAG_CONST 2u
 #define FZ_FLAG_IDS 4u
+#define FZ_FLAG_SHUF 8u  /* bit-shuffle stream: the lens section holds one u32 map of nonzero column words per 64
+                            codes, the chunk (1024 codes) lengths count 32 bits per stored word, the bitstream
+                            section holds the words (see fz_pipeline.encoder) */
+#define FZ_ENC_HUFFMAN 0u
+#define FZ_ENC_SHUFFLE 1u
 
 typedef struct fz_ctx fz_ctx;
 

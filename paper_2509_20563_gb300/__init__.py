@@ -45,7 +45,7 @@ class FzError(RuntimeError):
 
 class Pipeline(C.Structure):
     _fields_ = [("struct_size", C.c_uint32), ("predictor", C.c_uint32), ("radius", C.c_uint32),
-                ("block", C.c_uint32 * 3), ("chunk", C.c_uint32), ("reserved", C.c_uint32),
+                ("block", C.c_uint32 * 3), ("chunk", C.c_uint32), ("encoder", C.c_uint32),
                 ("selector_weights", C.c_void_p)]
 
 
@@ -158,12 +158,17 @@ def _dims(shape):
     return d
 
 
-def _pipeline(predictor="lorenzo1", radius=512, selector_weights=None, chunk=0, block=None) -> Pipeline:
+ENCODERS = {"huffman": 0, "shuffle": 1}
+
+
+def _pipeline(predictor="lorenzo1", radius=512, selector_weights=None, chunk=0, block=None,
+              encoder="huffman") -> Pipeline:
     p = Pipeline()
     p.struct_size = C.sizeof(Pipeline)
     p.predictor = PREDICTORS[predictor] if isinstance(predictor, str) else int(predictor)
     p.radius = int(radius)
     p.chunk = int(chunk)
+    p.encoder = ENCODERS[encoder] if isinstance(encoder, str) else int(encoder)
     for a, b in enumerate(block or ()):
         p.block[a] = int(b)
     p.selector_weights = selector_weights.data_ptr() if selector_weights is not None else None
@@ -181,10 +186,11 @@ def compress_bound(shape) -> int:
 
 def compress(x: torch.Tensor, eb: float, mode: str = "rel", predictor="lorenzo1", radius: int = 512,
              out: torch.Tensor | None = None, stream=None, selector_weights=None, chunk: int = 0,
-             block=None) -> torch.Tensor:
+             block=None, encoder: str = "huffman") -> torch.Tensor:
     """Compress a contiguous float32 CUDA tensor (1-3 dims, last axis fastest).
-    ``chunk`` is the Huffman chunk in symbols (0: the library's default) and
-    ``block`` the predictor block (x, y, z extents; None: the default).
+    ``chunk`` is the Huffman chunk in symbols (0: the library's default),
+    ``block`` the predictor block (x, y, z extents; None: the default) and
+    ``encoder`` "huffman" or "shuffle" (FZMod-Speed's bit-shuffle encoder).
     Returns a uint8 CUDA tensor holding exactly the stream; its host header
     copy is attached as ``.fz_header`` (bytes)."""
     if not (x.is_cuda and x.dtype == torch.float32 and x.is_contiguous()):
@@ -196,7 +202,7 @@ def compress(x: torch.Tensor, eb: float, mode: str = "rel", predictor="lorenzo1"
         out = torch.empty(bound, dtype=torch.uint8, device=x.device)
     nbytes = C.c_uint64()
     hdr = C.create_string_buffer(HEADER_BYTES)
-    pipe = _pipeline(predictor, radius, selector_weights, chunk, block)
+    pipe = _pipeline(predictor, radius, selector_weights, chunk, block, encoder)
     st = lib().fz_compress(_ctx(x.device.index or 0).handle, C.c_void_p(x.data_ptr()), x.dim(), _dims(x.shape),
                            1 if mode == "rel" else 0, float(eb), C.byref(pipe), C.c_void_p(out.data_ptr()),
                            out.numel(), C.byref(nbytes), hdr, _stream(stream))

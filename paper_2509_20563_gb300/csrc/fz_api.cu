@@ -88,7 +88,11 @@ size_t layout_compress_split(const Geom &g, char *zbase, char *rbase, CompressWs
     ro += up(bytes);
     return p;
   };
-  const uint64_t n_etiles = (g.n_blocks + kEncWarps - 1) / kEncWarps;
+  // look-back words: one per Huffman encode tile (8 blocks) or per
+  // bit-shuffle unit (4096 codes), whichever are more
+  uint64_t n_etiles = (g.n_blocks + kEncWarps - 1) / kEncWarps;
+  const uint64_t n_sunits = (g.npad + 4095) / 4096;
+  if (n_sunits > n_etiles) n_etiles = n_sunits;
   ws.ctl = reinterpret_cast<Ctl *>(ztake(sizeof(Ctl)));
   ws.tinfo = reinterpret_cast<uint4 *>(ztake(16 * g.n_qtiles));
   ws.tgroup = reinterpret_cast<uint2 *>(ztake(8 * ((g.n_qtiles + kTileGroup - 1) / kTileGroup)));
@@ -123,7 +127,8 @@ size_t layout_compress(const Geom &g, char *base, CompressWs &ws) {
 
 struct Req {
   uint32_t pred, R;
-  uint32_t chunk;  // 0: the block size
+  uint32_t chunk;    // 0: the block size
+  uint32_t encoder;  // FZ_ENC_*
   const uint16_t *weights;
 };
 
@@ -131,12 +136,13 @@ fz_status parse_pipe(const fz_pipeline *pipe, uint32_t ndim, Req &r) {
   r.pred = FZ_PRED_LORENZO1;
   r.R = 512;
   r.chunk = 0;
+  r.encoder = FZ_ENC_HUFFMAN;
   r.weights = nullptr;
   if (pipe) {
     if (pipe->struct_size < sizeof(uint32_t) * 3) return FZ_EINVAL;
     r.pred = pipe->predictor;
     if (pipe->radius) r.R = pipe->radius;
-    if (pipe->struct_size >= offsetof(fz_pipeline, reserved)) {
+    if (pipe->struct_size >= offsetof(fz_pipeline, encoder)) {
       const uint64_t d1[3] = {1, 1, 1};
       Geom g;
       make_geom(ndim, d1, g);
@@ -148,12 +154,22 @@ fz_status parse_pipe(const fz_pipeline *pipe, uint32_t ndim, Req &r) {
         if (a < ndim && b != want[a]) return FZ_EUNSUPPORTED;
       }
       r.chunk = pipe->chunk;
-      if (r.chunk && !chunk_supported(ndim, g.bsize, r.chunk)) return FZ_EUNSUPPORTED;
-      if (r.chunk && r.chunk != g.bsize && pipe->predictor > FZ_PRED_LORENZO2) return FZ_EUNSUPPORTED;
     }
     if (pipe->struct_size >= sizeof(fz_pipeline)) {
-      if (pipe->reserved) return FZ_EINVAL;
+      r.encoder = pipe->encoder;
       r.weights = reinterpret_cast<const uint16_t *>(pipe->selector_weights);
+    }
+    if (r.encoder > FZ_ENC_SHUFFLE) return FZ_EINVAL;
+    if (r.encoder == FZ_ENC_SHUFFLE) {
+      // the shuffle format fixes its chunk at 1024 codes
+      if (pipe->predictor > FZ_PRED_LORENZO2 || (r.chunk && r.chunk != 1024)) return FZ_EUNSUPPORTED;
+      r.chunk = 0;
+    } else if (r.chunk) {
+      const uint64_t d1[3] = {1, 1, 1};
+      Geom g;
+      make_geom(ndim, d1, g);
+      if (!chunk_supported(ndim, g.bsize, r.chunk)) return FZ_EUNSUPPORTED;
+      if (r.chunk != g.bsize && pipe->predictor > FZ_PRED_LORENZO2) return FZ_EUNSUPPORTED;
     }
   }
   if (r.R < 2 || r.R > 512) return FZ_EINVAL;
@@ -199,7 +215,8 @@ fz_status check_header(const fz_header &h, uint64_t in_bytes, Geom &g) {
   make_geom(h.ndim, h.dims, g);
   if (h.flags == FZ_FLAG_RAW) return h.total_bytes == FZ_HEADER_BYTES + 4 * n ? FZ_OK : FZ_ECORRUPT;
   if (h.flags == FZ_FLAG_CONST) return h.total_bytes == FZ_HEADER_BYTES + 16 ? FZ_OK : FZ_ECORRUPT;
-  if (h.flags != 0 && h.flags != FZ_FLAG_IDS) return FZ_EUNSUPPORTED;
+  if (h.flags != 0 && h.flags != FZ_FLAG_IDS && h.flags != FZ_FLAG_SHUF) return FZ_EUNSUPPORTED;
+  const bool shuf = h.flags == FZ_FLAG_SHUF;
   if (h.radius < 2 || h.radius > 512) return FZ_ECORRUPT;
   const bool sel = h.predictor == FZ_SEL_MLP || h.predictor == FZ_SEL_EXHAUSTIVE;
   if (!(h.predictor <= FZ_PRED_INTERP_CUBIC || sel)) return FZ_ECORRUPT;
@@ -213,12 +230,14 @@ fz_status check_header(const fz_header &h, uint64_t in_bytes, Geom &g) {
               !fits(h.off_ids, (h.n_blocks + 3) / 4) || h.off_ids + (h.n_blocks + 3) / 4 > h.off_anchors))
     return FZ_ECORRUPT;
   if (h.block[0] != g.bx || h.block[1] != g.by || h.block[2] != g.bz) return FZ_ECORRUPT;
-  if (!chunk_supported(h.ndim, g.bsize, h.chunk)) return FZ_ECORRUPT;
+  if (shuf ? (h.chunk != 1024 || h.predictor > FZ_PRED_LORENZO2) : !chunk_supported(h.ndim, g.bsize, h.chunk))
+    return FZ_ECORRUPT;
   if (h.chunk != g.bsize && h.predictor > FZ_PRED_LORENZO2) return FZ_EUNSUPPORTED;
+  if (shuf && (h.total_bits & 31u)) return FZ_ECORRUPT;
   set_chunk(g, h.chunk);
   if (h.n_blocks != g.n_blocks || h.n_chunks != g.n_chunks) return FZ_ECORRUPT;
   if (h.n_out > n || h.n_exc > n || h.total_bits > (uint64_t)kLmax * g.npad) return FZ_ECORRUPT;
-  const uint64_t secs[9][2] = {{h.off_lens, sel ? h.off_ids - h.off_lens : 2ull * h.radius},
+  const uint64_t secs[9][2] = {{h.off_lens, sel ? h.off_ids - h.off_lens : (shuf ? 4 * (g.npad / 64) : 2ull * h.radius)},
                                {h.off_anchors, 4 * h.n_blocks},
                                {h.off_chunk_bits, 4 * h.n_chunks},   {h.off_out_idx, 4 * h.n_out},
                                {h.off_out_val, 4 * h.n_out},         {h.off_exc_idx, 4 * h.n_exc},
@@ -399,9 +418,16 @@ fz_status fz_compress(fz_ctx *ctx, const float *d_in, uint32_t ndim, const uint6
   StageClock clk(ctx, s, false);
   if ((st = run_front(ctx, d_in, g, eb_mode, eb, r, ws, s, clk))) return st;
   uint8_t *out = reinterpret_cast<uint8_t *>(d_out);
-  cudaError_t e = launch_codebook(g, r.R, r.pred, eb_mode, eb, ws, s);
-  clk.mark("codebook", 1);
-  if (e == cudaSuccess) { e = launch_encode(g, ws, out, s, ctx->sm_count); clk.mark("encode", 1); }
+  cudaError_t e;
+  if (r.encoder == FZ_ENC_SHUFFLE) {
+    e = launch_shuf_layout(g, r.R, r.pred, eb_mode, eb, ws, s);
+    clk.mark("layout", 1);
+    if (e == cudaSuccess) { e = launch_shuf_encode(g, ws, out, s, ctx->sm_count); clk.mark("encode", 1); }
+  } else {
+    e = launch_codebook(g, r.R, r.pred, eb_mode, eb, ws, s);
+    clk.mark("codebook", 1);
+    if (e == cudaSuccess) { e = launch_encode(g, ws, out, s, ctx->sm_count); clk.mark("encode", 1); }
+  }
   ws.h_res = reinterpret_cast<Result *>(ctx->h_pinned);  // pinned, mapped: written by the last kernel
   if (e == cudaSuccess) { e = launch_assemble(d_in, g, r.R, ws, out, s, ctx->sm_count); clk.mark("assemble", 2); }
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
@@ -457,8 +483,10 @@ fz_status fz_decompress(fz_ctx *ctx, const void *d_in, uint64_t in_bytes, const 
   auto take = [&](size_t bytes) { size_t o = off; off += up(bytes); return o; };
   const bool selpath = h.predictor > FZ_PRED_LORENZO2;
   // a per-block first-outlier table pays off when most blocks hold outliers
-  // plane-parallel streams (64-symbol chunks) locate outliers per plane
-  const bool ofirst = !selpath && h.n_out > h.n_blocks / 8 && !(h.ndim == 3 && h.chunk == 64);
+  // plane-parallel streams (64-symbol chunks) and bit-shuffle streams locate
+  // outliers per plane or chunk
+  const bool ofirst = !selpath && h.n_out > h.n_blocks / 8 && !(h.ndim == 3 && h.chunk == 64) &&
+                      h.flags != FZ_FLAG_SHUF;
   const size_t o_err = take(dec_offset_zero_bytes(h)), o_gsum = take(8 * n_units), o_lut = take(2u << kLutBits),
                o_codes = selpath ? take(2 * g.npad) : 0, o_ofirst = ofirst ? take(4 * h.n_blocks) : 0;
   if ((st = ensure_ws(ctx, off))) return st;

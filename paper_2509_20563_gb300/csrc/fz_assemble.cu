@@ -91,9 +91,10 @@ __device__ __forceinline__ void assemble_body(const float *__restrict__ x, const
   }
   const uint32_t nsym = 2 * R;
   const uint64_t nb = h.n_blocks, n_out = h.n_out, n_exc = h.n_exc;
-  copy_bytes(d_out + h.off_lens, ctl->lens, nsym, tid, nth);
-  copy_bytes(d_out + h.off_anchors, reinterpret_cast<const uint8_t *>(ws.anchors), 4 * nb, tid, nth);
   uint64_t lens_end = h.off_lens + nsym;
+  if (h.flags & FZ_FLAG_SHUF) lens_end = h.off_lens + 4 * (g.npad / 64);  // the encoder wrote the word maps
+  else copy_bytes(d_out + h.off_lens, ctl->lens, nsym, tid, nth);
+  copy_bytes(d_out + h.off_anchors, reinterpret_cast<const uint8_t *>(ws.anchors), 4 * nb, tid, nth);
   if (h.flags & FZ_FLAG_IDS) {
     // 2-bit predictor ids, four blocks per byte, first block in the low bits
     const uint64_t nbytes = (nb + 3) / 4;

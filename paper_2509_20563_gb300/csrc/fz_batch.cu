@@ -211,10 +211,11 @@ fz_status tune_chunks(fz_ctx *ctx, BatchTune &best, uint32_t n, const std::vecto
   ctx->batch_graphs = false;
   std::vector<uint64_t> h(n + 1);
   fz_status st = FZ_OK;
+  bool give_up = false;  // the batch itself fails (output too small, ...): the real call reports it
   auto round_trip = [&](const BatchTune &t) -> float {
     const float c = compress(t);
     if (c < 0) return -1.f;
-    if (offs[n + 1]) return -1.f;
+    if (offs[n + 1]) { give_up = true; return -1.f; }
     for (uint32_t j = 0; j <= n; ++j) h[j] = offs[j];
     fz_status ds = FZ_OK;
     const float d = time_run(s, [&](cudaStream_t q) {
@@ -229,18 +230,22 @@ fz_status tune_chunks(fz_ctx *ctx, BatchTune &best, uint32_t n, const std::vecto
     t.chunk_log2[c] = 2;
     round_trip(t);  // warm-up of this class's chunk
     float inc = round_trip(t);
+    if (give_up) break;
     if (inc < 0) { st = FZ_ECUDA; break; }
     int arg = 2;
     for (int v = 1; v >= 0; --v) {
       BatchTune u = best;
       u.chunk_log2[c] = v;
       const float a = round_trip(u), b = round_trip(u);
+      if (give_up) { arg = 0; break; }
       if (a < 0 || b < 0) { st = FZ_ECUDA; break; }
       const float ms = a < b ? a : b;
       if (ms < 0.97f * inc) { inc = ms; arg = v; }
     }
+    if (give_up) break;
     best.chunk_log2[c] = arg;
   }
+  if (give_up) best.chunk_log2[0] = best.chunk_log2[1] = 0;
   ctx->batch_tuning = tuning;
   ctx->batch_graphs = graphs;
   destroy_batch_plans(ctx, 1);  // the untuned decompress plans of the trials
@@ -296,7 +301,7 @@ fz_status fz_compress_batch(fz_ctx *ctx, uint32_t n, const float *const *d_in, c
     if (pipe->struct_size < sizeof(uint32_t) * 3) return FZ_EINVAL;
     pred = pipe->predictor;
     if (pipe->radius) R = pipe->radius;
-    if (pipe->struct_size >= offsetof(fz_pipeline, reserved)) chunk = pipe->chunk;
+    if (pipe->struct_size >= offsetof(fz_pipeline, encoder)) chunk = pipe->chunk;
   }
   if (R < 2 || R > 512) return FZ_EINVAL;
   if (pred > FZ_PRED_LORENZO2) return pred <= FZ_SEL_EXHAUSTIVE ? FZ_EUNSUPPORTED : FZ_EINVAL;

@@ -174,20 +174,6 @@ __device__ bool build_codebook(CbSmem &s, uint32_t nsym, uint32_t *code_out, uin
   return true;
 }
 
-__device__ void write_min_header(fz_header &h, uint16_t flags, const Geom &g, uint32_t eb_mode, double eb,
-                                 uint64_t total) {
-  uint8_t *p = reinterpret_cast<uint8_t *>(&h);
-  for (int i = 0; i < (int)sizeof(fz_header); ++i) p[i] = 0;
-  h.magic = FZ_MAGIC;
-  h.version = 1;
-  h.flags = flags;
-  h.ndim = g.ndim;
-  h.eb_mode = eb_mode;
-  h.dims[0] = g.nx; h.dims[1] = g.ny; h.dims[2] = g.nz;
-  h.eb = eb;
-  h.total_bytes = total;
-}
-
 // The codebook, the layout decision and the header of one field; all
 // threads of the CTA call it together.
 __device__ __forceinline__ void codebook_body(const Geom &g, uint32_t R, uint32_t pred, uint32_t eb_mode, double eb,

@@ -1065,6 +1065,7 @@ cudaError_t launch_decode_main(const uint8_t *d_in, const fz_header &h, float *d
   memcpy(&p.ebx2, &h.ebx2_bits, 4);
   p.R = (int32_t)h.radius;
   const bool k2 = h.predictor == FZ_PRED_LORENZO2;
+  if (h.flags == FZ_FLAG_SHUF) return launch_shuf_decode(d_in, h, d_out, ws, s, sm_count);
   if (g.ndim == 3 && g.chunk == 64) {
     p.ofirst = nullptr;  // outliers are located per plane by search
     return k2 ? launch_planes_t<2>(p, g, sm_count, s) : launch_planes_t<1>(p, g, sm_count, s);

@@ -142,6 +142,22 @@ struct Ctl {
   Result res;
 };
 
+// The header of a RAW or CONST stream (and the start of every header): only
+// magic, version, flags, ndim, eb_mode, dims, eb and total_bytes are set.
+__device__ __forceinline__ void write_min_header(fz_header &h, uint16_t flags, const Geom &g, uint32_t eb_mode,
+                                                 double eb, uint64_t total) {
+  uint8_t *p = reinterpret_cast<uint8_t *>(&h);
+  for (int i = 0; i < (int)sizeof(fz_header); ++i) p[i] = 0;
+  h.magic = FZ_MAGIC;
+  h.version = 1;
+  h.flags = flags;
+  h.ndim = g.ndim;
+  h.eb_mode = eb_mode;
+  h.dims[0] = g.nx; h.dims[1] = g.ny; h.dims[2] = g.nz;
+  h.eb = eb;
+  h.total_bytes = total;
+}
+
 // ---------------------------------------------------------------- errors
 __device__ __forceinline__ void set_err(Ctl *ctl, uint32_t code) { atomicCAS(&ctl->res.err, 0u, code); }
 
@@ -402,6 +418,10 @@ cudaError_t launch_assemble(const float *x, const Geom &g, uint32_t R, const Com
                             cudaStream_t s, int sm_count);
 cudaError_t launch_codebook_only(const uint64_t *hist, uint32_t nsym, uint8_t *lens, uint32_t *codes,
                                  Ctl *ctl, cudaStream_t s);
+// bit-shuffle + zero-word encoder (FZMod-Speed)
+cudaError_t launch_shuf_layout(const Geom &g, uint32_t R, uint32_t pred, uint32_t eb_mode, double eb,
+                               const CompressWs &ws, cudaStream_t s);
+cudaError_t launch_shuf_encode(const Geom &g, const CompressWs &ws, uint8_t *d_out, cudaStream_t s, int sm_count);
 
 struct DecodeWs {
   uint16_t *lut;           // 1 << kLutBits entries: codeword length, symbol
@@ -424,6 +444,8 @@ cudaError_t launch_decode_offsets(const uint8_t *d_in, const fz_header &h, const
 cudaError_t launch_decode_main(const uint8_t *d_in, const fz_header &h, float *d_out, const DecodeWs &ws,
                                cudaStream_t s, int sm_count);
 cudaError_t launch_fill(float *out, uint64_t n, uint32_t bits, cudaStream_t s, int sm_count);
+cudaError_t launch_shuf_decode(const uint8_t *d_in, const fz_header &h, float *d_out, const DecodeWs &ws,
+                               cudaStream_t s, int sm_count);
 // one warp waits on a look-back predecessor that never publishes (scratch:
 // err word at [0], status words from [4], 32 bytes zeroed by the caller)
 cudaError_t launch_lookback_selftest(uint32_t *scratch, long long spin, cudaStream_t s);

@@ -128,7 +128,7 @@ def test_struct_layout_matches_header(tmp_path):
                 "inv2eb_bits", "ebchk_bits", "radius", "block", "predictor", "chunk", "n_blocks", "n_chunks",
                 "n_out", "n_exc", "total_bits", "off_lens", "off_ids", "off_anchors", "off_chunk_bits",
                 "off_out_idx", "off_out_val", "off_exc_idx", "off_exc_val", "off_bits", "total_bytes"]
-    fields_p = ["struct_size", "predictor", "radius", "block", "chunk", "reserved", "selector_weights"]
+    fields_p = ["struct_size", "predictor", "radius", "block", "chunk", "encoder", "selector_weights"]
     lines = ['#include <stdio.h>', '#include <stddef.h>', f'#include "{ROOT}/include/fz.h"', "int main(void){"]
     lines += [f'printf("h {f} %zu\\n", offsetof(fz_header, {f}));' for f in fields_h]
     lines += [f'printf("p {f} %zu\\n", offsetof(fz_pipeline, {f}));' for f in fields_p]

@@ -44,9 +44,12 @@ def test_error_stats_match_float64(n):
     assert st["sse"] == pytest.approx(float((d * d).sum()), rel=1e-12)
     assert st["x_min"] == float(x[f].min()) and st["x_max"] == float(x[f].max())
     mse = float((d * d).sum()) / f.sum()
-    if mse > 0:
-        want = 20 * math.log10(float(x[f].max()) - float(x[f].min())) - 10 * math.log10(mse)
+    rng_x = float(x[f].max()) - float(x[f].min())
+    if mse > 0 and rng_x > 0:
+        want = 20 * math.log10(rng_x) - 10 * math.log10(mse)
         assert st["psnr_db"] == pytest.approx(want, rel=1e-10)
+    else:
+        assert math.isinf(st["psnr_db"])
     # deterministic: the same call gives the same bits
     st2 = fz.error_stats(torch.from_numpy(x).cuda(), torch.from_numpy(y).cuda())
     assert st2 == st
@@ -70,6 +73,9 @@ def test_rate_distortion_sweep_against_oracle_and_bound():
         assert row["bit_rate"] == pytest.approx(8.0 * ref.size / xh.size, abs=1e-4)
         yr = oracle.decompress(ref).astype(np.float64)
         mse = float(((yr - xh.astype(np.float64)) ** 2).mean())
+        if mse == 0:  # a raw stream at the tightest bound: exact
+            assert math.isinf(row["psnr_db"])
+            continue
         psnr = 20 * math.log10(rng) - 10 * math.log10(mse)
         assert row["psnr_db"] == pytest.approx(psnr, abs=2e-3)
         assert row["psnr_db"] >= -20 * math.log10(eb)
