@@ -473,6 +473,8 @@ def run_fz(args, rank, world, local_rank):
             os.sched_setaffinity(0, saved_cpus)
     if rank == 0 and world == 1 and not args.no_configs:
         res["configs"] = bench_configs(fz, dev, stream, args)
+    if rank == 0 and world == 1 and not args.no_speed:
+        res["speed_pipeline"] = bench_speed(fz, dev, stream, x, args)
     if rank == 0 and world == 1 and not args.no_hist:
         res["histogram"] = bench_histogram(fz, dev, stream, x)
     if rank == 0 and world == 1 and not args.no_rd:
@@ -612,6 +614,60 @@ def bench_rate_distortion(fz, dev, x512, link):
     torch.cuda.empty_cache()
     return {"bandwidths_gbs": bws, "rows": rows,
             "note": "Eq. 1 speedup = 1 / (((BW CR)^-1 + T_compress^-1) BW); PSNR from fz_error_stats"}
+
+
+def bench_speed(fz, dev, stream, x512, args):
+    """FZMod-Speed (§3.3): the same quantization codes through the bit-shuffle
+    + zero-word encoder instead of Huffman, on the three stand-in workloads;
+    compress and decompress GB/s (L2 flushed before each timed call, median
+    of the timed calls), roofline fractions on the same forced bytes as the
+    Huffman path (compress 12N + S, decompress S + 4N) and the CR beside the
+    Huffman stream's."""
+    peak, _ = _peaks()
+    scratch = torch.empty(64 << 20, dtype=torch.float32, device=dev)
+    specs = [("grf512", lambda: x512, 1e-4),
+             ("hacc1d", lambda: synth.hacc1d(synth.HACC_N, seed=3, device=dev), 1e-3),
+             ("cesm2d", lambda: synth.cesm2d(1800, 3600, seed=4).to(dev).contiguous(), 1e-4)]
+    out = []
+    for key, make, eb in specs:
+        x = make()
+        N = x.numel()
+        ob = torch.empty(fz.compress_bound(x.shape), dtype=torch.uint8, device=dev)
+        y = torch.empty_like(x)
+        S_h = fz.compress(x, eb, out=ob).numel()
+        buf = fz.compress(x, eb, out=ob, encoder="shuffle")
+        fz.decompress(buf, out=y)
+        err = float((y.double() - x.double()).abs().max()) / (eb * (float(x.max()) - float(x.min())))
+        tc, td = [], []
+        for i in range(3 + args.config_reps):
+            _flush_l2(scratch)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            buf = fz.compress(x, eb, out=ob, encoder="shuffle")
+            e1.record(stream)
+            _flush_l2(scratch)
+            e2, e3 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e2.record(stream)
+            fz.decompress(buf, out=y)
+            e3.record(stream)
+            torch.cuda.synchronize(dev)
+            if i >= 3:
+                tc.append(e0.elapsed_time(e1))
+                td.append(e2.elapsed_time(e3))
+        S = buf.numel()
+        mc, md = statistics.median(tc), statistics.median(td)
+        out.append({"workload": key, "eb": eb, "values": N, "cr_shuffle": round(4 * N / S, 4),
+                    "cr_huffman": round(4 * N / S_h, 4), "max_err_over_eb": round(err, 6),
+                    "compress_gbs": round(4 * N / (mc * 1e-3) / 1e9, 2),
+                    "decompress_gbs": round(4 * N / (md * 1e-3) / 1e9, 2),
+                    "compress_roofline_frac": round((12 * N + S) / (mc * 1e-3) / 1e9 / peak, 4),
+                    "decompress_roofline_frac": round((S + 4 * N) / (md * 1e-3) / 1e9 / peak, 4)})
+        if key != "grf512":
+            del x
+        del ob, y
+    del scratch
+    torch.cuda.empty_cache()
+    return out
 
 
 def bench_histogram(fz, dev, stream, x512):
@@ -776,6 +832,7 @@ def main():
     ap.add_argument("--no-configs", action="store_true", help="skip the other plain-pipeline workloads")
     ap.add_argument("--no-rd", action="store_true", help="skip the rate-distortion / Eq. 1 report")
     ap.add_argument("--no-hist", action="store_true", help="skip the histogram-stage comparison")
+    ap.add_argument("--no-speed", action="store_true", help="skip the bit-shuffle (FZMod-Speed) pipeline")
     ap.add_argument("--config-reps", type=int, default=10, help="timed calls per extra workload and bound")
     ap.add_argument("--traffic", type=float, default=None, help="ncu dram bytes per launch of the dominant kernel")
     args = ap.parse_args()

@@ -296,7 +296,7 @@ fz_status fz_selftest_bounded_wait(fz_ctx *ctx, void *stream);
  * give the same exact counts: FZ_HIST_PRIVATE (warp-private shared-memory
  * histograms) or FZ_HIST_TOPK, the top-k variant §3.2 describes as the better
  * one when the codes repeat a few values: the 16 most frequent codes of a
- * strided sample are counted in per-thread packed registers and only the
+ * sample (64 windows of 1024 codes spread over the array) are counted in per-thread packed registers and only the
  * others take shared-memory atomics.  (The compression path counts its codes
  * inside the quantizer; this entry point serves a code array on its own, such
  * as the output of fz_lorenzo_quantize.)  Uses the context workspace;

@@ -69,9 +69,12 @@ struct AsmSmem {
 
 // Assembly of one field's stream by CTAs bid = 0..nblk-1 (all threads of
 // each CTA call it together).
+// pad16: also zero the bytes from the stream's end to the next 16-byte
+// boundary (batched calls pack the streams at 16-byte offsets; a RAW stream of
+// N floats ends unaligned when N is not a multiple of 4).
 __device__ __forceinline__ void assemble_body(const float *__restrict__ x, const Geom &g, uint32_t R,
                                               const CompressWs &ws, uint8_t *d_out, uint32_t bid, uint32_t nblk,
-                                              AsmSmem &sm) {
+                                              AsmSmem &sm, bool pad16 = false) {
   uint2 *sw = sm.sw;
   unsigned long long &s_ob = sm.ob, &s_eb = sm.eb;
   const Ctl *ctl = ws.ctl;
@@ -81,6 +84,10 @@ __device__ __forceinline__ void assemble_body(const float *__restrict__ x, const
   const uint64_t nth = (uint64_t)nblk * blockDim.x;
   const uint8_t *hb = reinterpret_cast<const uint8_t *>(&h);
   if (tid < FZ_HEADER_BYTES) d_out[tid] = hb[tid];
+  if (pad16 && tid < 16) {
+    const uint64_t t = h.total_bytes;
+    if (t + tid < align16(t)) d_out[t + tid] = 0;
+  }
   if (mode == kModeRaw) {
     copy_bytes(d_out + FZ_HEADER_BYTES, reinterpret_cast<const uint8_t *>(x), 4 * g.n, tid, nth);
     return;
@@ -269,7 +276,7 @@ __global__ void __launch_bounds__(kAsmThreads) k_assemble_batch(const BatchJob *
   for (uint32_t j = 0; j < n; ++j) {
     const BatchJob &J = jobs[j];
     if (J.out_off == kNoOutput) continue;
-    assemble_body(J.x, J.g, J.R, J.ws, d_out + J.out_off, blockIdx.x, gridDim.x, sm);
+    assemble_body(J.x, J.g, J.R, J.ws, d_out + J.out_off, blockIdx.x, gridDim.x, sm, true);
   }
 }
 

@@ -249,11 +249,17 @@ __global__ void __launch_bounds__(kEncThreads) k_encode_batch(const BatchJob *__
 // publishes and packs its newest tile, then resolves the look-back and
 // stores the tile packed one step earlier, whose predecessors have had a
 // whole step to publish their prefixes.  Two images alternate.
-template <int CH>
+// D tile images in a ring: the tile packed in one step is stored D - 1
+// steps later, so its look-back predecessors have had D - 1 steps to
+// publish (D = 2 by default; FZ_ENC_DEPTH selects another depth).
+#ifndef FZ_ENC_DEPTH
+#define FZ_ENC_DEPTH 2
+#endif
+template <int CH, int D>
 struct PipeSmem {
   static constexpr int kMaxWords = EncSmem<CH>::kMaxWords;
   uint32_t senc[kMaxSym];
-  __align__(16) uint32_t lw[2][kMaxWords];
+  __align__(16) uint32_t lw[D][kMaxWords];
   uint32_t wtot[kEncWarps];
   uint32_t tk[2];  // tickets: the current tile and the next one
   unsigned long long base;
@@ -274,7 +280,8 @@ __device__ __forceinline__ void load_lane_codes(const uint16_t *codes, uint64_t 
 template <int CH, int CM>
 __global__ void __launch_bounds__(kEncThreads, CH == 512 ? FZ_ENC_MINB : FZ_ENC_MINB1024) k_encode_pipe(Geom g, CompressWs ws, uint8_t *d_out) {
   constexpr int PER = CH / 32;
-  __shared__ PipeSmem<CH> sm;
+  constexpr int D = FZ_ENC_DEPTH;
+  __shared__ PipeSmem<CH, D> sm;
   Ctl *ctl = ws.ctl;
   if (ctl->mode != kModeNormal) return;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -285,23 +292,27 @@ __global__ void __launch_bounds__(kEncThreads, CH == 512 ? FZ_ENC_MINB : FZ_ENC_
   const uint64_t n_tiles = (n_blk + kEncWarps - 1) / kEncWarps;
   const uint64_t wlimit = (ctl->total_bits + 31) / 32;
   for (int i = tid; i < kMaxSym; i += kEncThreads) sm.senc[i] = ctl->enc[i];
-  for (int i = tid; i < 2 * PipeSmem<CH>::kMaxWords; i += kEncThreads) (&sm.lw[0][0])[i] = 0;
+  for (int i = tid; i < D * PipeSmem<CH, D>::kMaxWords; i += kEncThreads) (&sm.lw[0][0])[i] = 0;
   if (tid == 0) sm.tk[0] = atomicAdd(&ctl->encode_ticket, 1u);
   __syncthreads();
   uint64_t tile = sm.tk[0];
   // the codes of the tile in hand are loaded one step ahead of their use
   uint4 raw[PER / 8];
   if (tile < n_tiles && tile * kEncWarps + warp < n_blk) load_lane_codes<PER>(ws.codes, tile * kEncWarps + warp, CH, lane, raw);
-  uint64_t prev = ~0ull;
-  uint32_t prev_bits = 0;
-  int cb = 0;
+  // tiles packed but not yet stored, oldest first, and their bit totals
+  uint64_t pend[D - 1];
+  uint32_t pend_bits[D - 1];
+#pragma unroll
+  for (int i = 0; i < D - 1; ++i) { pend[i] = ~0ull; pend_bits[i] = 0; }
+  int cb = 0;  // image of the current tile; the oldest pending tile's is (cb + 1) % D
+  int tb = 0;  // ticket slot of the current tile
   for (;;) {
     const bool have = tile < n_tiles;
     uint32_t tbits = 0;
     uint32_t *lw = sm.lw[cb];
     const uint64_t blk = tile * kEncWarps + warp;
     const bool valid = have && blk < n_blk;
-    if (tid == 0 && have) sm.tk[cb ^ 1] = atomicAdd(&ctl->encode_ticket, 1u);
+    if (tid == 0 && have) sm.tk[tb ^ 1] = atomicAdd(&ctl->encode_ticket, 1u);
     // the next tile's first 32 codes (its head), read ahead of their use
     uint32_t hcode = 0;
     if (have && warp == kEncWarps - 1 && tile + 1 < n_tiles)
@@ -339,7 +350,7 @@ __global__ void __launch_bounds__(kEncThreads, CH == 512 ? FZ_ENC_MINB : FZ_ENC_
     __syncthreads();
     if (CM == 2 && have) store_multi_chunks(chunk_bits, sm.wtot, tile, g.chunk / CH, g.n_chunks, tid);
     // ---- the next tile's codes go out now and land during this step
-    const uint64_t next = have ? (uint64_t)sm.tk[cb ^ 1] : n_tiles;
+    const uint64_t next = have ? (uint64_t)sm.tk[tb ^ 1] : n_tiles;
     if (next < n_tiles && next * kEncWarps + warp < n_blk)
       load_lane_codes<PER>(ws.codes, next * kEncWarps + warp, CH, lane, raw);
     if (have) {
@@ -393,7 +404,10 @@ __global__ void __launch_bounds__(kEncThreads, CH == 512 ? FZ_ENC_MINB : FZ_ENC_
         }
       }
     }
-    // ---- the previous tile: its base by look-back, then its words
+    // ---- the oldest pending tile: its base by look-back, then its words
+    const uint64_t prev = pend[0];
+    const uint32_t prev_bits = pend_bits[0];
+    const int pcb = (cb + 1) % D;
     if (prev != ~0ull && warp == 0) {
       const unsigned long long base = lookback_resolve_warp(ws.estatus, prev, prev_bits, &ctl->res.err, ws.spin);
       if (lane == 0) {
@@ -403,7 +417,7 @@ __global__ void __launch_bounds__(kEncThreads, CH == 512 ? FZ_ENC_MINB : FZ_ENC_
     }
     __syncthreads();  // packing, head and base are visible
     if (prev != ~0ull) {
-      const uint32_t *plw = sm.lw[cb ^ 1];
+      const uint32_t *plw = sm.lw[pcb];
       const unsigned long long base = sm.base;
       const uint32_t r = (uint32_t)(base & 31u);
       const uint64_t gw0 = base >> 5;
@@ -414,15 +428,24 @@ __global__ void __launch_bounds__(kEncThreads, CH == 512 ? FZ_ENC_MINB : FZ_ENC_
         if (gw0 + j < wlimit) words[gw0 + j] = v;
       }
       __syncthreads();  // every word of the previous image has been read
-      uint32_t *z = sm.lw[cb ^ 1];
+      uint32_t *z = sm.lw[pcb];
       const uint32_t nz = (prev_bits + 32 + 31) / 32 + 1;
       for (uint32_t w = tid; w < nz; w += kEncThreads) z[w] = 0;
     }
-    if (!have) break;
-    prev = tile;
-    prev_bits = tbits;
-    tile = next;
-    cb ^= 1;
+    // shift the pending queue; after the last tile, drain what is left
+#pragma unroll
+    for (int i = 0; i < D - 2; ++i) { pend[i] = pend[i + 1]; pend_bits[i] = pend_bits[i + 1]; }
+    pend[D - 2] = have ? tile : ~0ull;
+    pend_bits[D - 2] = have ? tbits : 0u;
+    bool left = false;
+#pragma unroll
+    for (int i = 0; i < D - 1; ++i) left = left || pend[i] != ~0ull;
+    if (!have && !left) break;
+    if (have) {
+      tile = next;
+      tb ^= 1;
+    }
+    cb = (cb + 1) % D;
     __syncthreads();  // the cleared image is ready for the next tile
   }
 }

@@ -7,7 +7,8 @@
 //     added up per CTA and flushed to the global counts.
 //   FZ_HIST_TOPK -- the top-k variant (§3.2: better when the codes repeat a
 //     few values, as after a good predictor).  A one-CTA pass counts a
-//     strided sample and keeps its k = 16 most frequent codes; in the main
+//     sample (64 windows of 1024 codes spread over the array) and keeps its
+//     k = 16 most frequent codes; in the main
 //     pass each thread counts those 16 codes in two 64-bit registers of
 //     eight 8-bit counters (an add of 1 << 8 slot), folded into shared
 //     memory every 255 codes, and only the other codes take a shared
@@ -25,7 +26,7 @@ namespace {
 constexpr int kHiThreads = 256;
 constexpr int kHiWarps = kHiThreads / 32;
 constexpr int kTopK = 16;
-constexpr uint32_t kSampleStride = 61;  // codes between two sampled codes
+constexpr uint32_t kSampleWindows = 64, kSampleWindow = 1024;  // 64K codes in 64 evenly spread windows
 
 // Warp-private shared histograms; n a multiple of 8 codes is read as uint4.
 __global__ void __launch_bounds__(kHiThreads) k_hist_private(const uint16_t *__restrict__ codes, uint64_t n,
@@ -63,15 +64,20 @@ __global__ void __launch_bounds__(kHiThreads) k_hist_private(const uint16_t *__r
   if (bad) atomicAdd(hist + nsym, 1ull);  // codes outside the alphabet: counted apart
 }
 
-// One CTA: counts a strided sample and writes the 16 most frequent codes
-// (ties to the lower code) into slot[] as a code -> slot table (0xff: none).
+// One CTA: counts a sample of at most 64K codes (64 windows of 1024
+// consecutive codes spread evenly over the array, read coalesced) and
+// writes the 16 most frequent codes (ties to the lower code) into slot[] as
+// a code -> slot table (0xff: none).
 __global__ void __launch_bounds__(kHiThreads) k_hist_sample(const uint16_t *__restrict__ codes, uint64_t n,
                                                             uint32_t nsym, uint8_t *slot) {
   extern __shared__ uint32_t hs[];  // nsym
   for (uint32_t i = threadIdx.x; i < nsym; i += kHiThreads) hs[i] = 0;
   __syncthreads();
-  for (uint64_t i = (uint64_t)threadIdx.x * kSampleStride; i < n; i += (uint64_t)kHiThreads * kSampleStride) {
-    const uint32_t a = codes[i];
+  const uint64_t span = n > kSampleWindow ? (n - kSampleWindow) / (kSampleWindows - 1) : 0;
+  for (uint32_t i = threadIdx.x; i < kSampleWindows * kSampleWindow; i += kHiThreads) {
+    const uint64_t pos = (uint64_t)(i / kSampleWindow) * span + (i % kSampleWindow);
+    if (pos >= n) continue;
+    const uint32_t a = codes[pos];
     if (a < nsym) atomicAdd(hs + a, 1u);
   }
   __syncthreads();

@@ -233,21 +233,28 @@ __device__ __forceinline__ void decode_shuf_chunk(const ShDec &p, const Geom &g,
   int32_t d[16][2];
   uint64_t w = w0;
   uint32_t zeros = 0;
+  // every word of the chunk is requested before the first transpose, so
+  // the loads' latencies overlap (their addresses depend on the maps only)
+  uint32_t cols[16];
+#pragma unroll
+  for (int kk = 0; kk < 16; ++kk) {
+    cols[kk] = 0;
+    if (kk < nr) {
+      const uint32_t map = __shfl_sync(0xffffffffu, mymap, kk);
+      const uint64_t wi = w + __popc(map & ((1u << lane) - 1u));
+      if ((map >> lane) & 1u) {
+        if (wi < p.n_words) cols[kk] = __ldg(p.words + wi);
+        else bad = true;
+      }
+      w += __popc(map);
+    }
+  }
 #pragma unroll
   for (int kk = 0; kk < 16; ++kk) {
     d[kk][0] = 0;
     d[kk][1] = 0;
     if (kk < nr) {
-      const uint32_t map = __shfl_sync(0xffffffffu, mymap, kk);
-      const bool has = (map >> lane) & 1u;
-      const uint64_t wi = w + __popc(map & ((1u << lane) - 1u));
-      uint32_t col = 0;
-      if (has) {
-        if (wi < p.n_words) col = __ldg(p.words + wi);
-        else bad = true;
-      }
-      w += __popc(map);
-      const uint32_t row = transpose32(col);
+      const uint32_t row = transpose32(cols[kk]);
       const uint32_t v0 = row & 0xffffu, v1 = row >> 16;
       bad |= v0 >= 2u * (uint32_t)p.R || v1 >= 2u * (uint32_t)p.R;
       d[kk][0] = unzigzag(v0);
@@ -357,7 +364,22 @@ __device__ __forceinline__ void decode_shuf_chunk(const ShDec &p, const Geom &g,
     eb0 = __shfl_sync(0xffffffffu, eb0, 0);
     ee0 = __shfl_sync(0xffffffffu, ee0, 0);
   }
-  // dequantize and store
+  // dequantize and store; block coordinates once per chunk
+  uint32_t bx0 = 0, by0 = 0, bz0 = 0, bx1 = 0, by1 = 0, bz1 = 0;
+  {
+    const uint32_t b0 = NDIM == 3 ? (uint32_t)(2 * j) : (uint32_t)j;
+    bx0 = b0 % g.nbx;
+    const uint32_t r_0 = b0 / g.nbx;
+    by0 = r_0 % g.nby;
+    bz0 = r_0 / g.nby;
+    if (NDIM == 3) {
+      const uint32_t b1 = b0 + 1;
+      bx1 = b1 % g.nbx;
+      const uint32_t r_1 = b1 / g.nbx;
+      by1 = r_1 % g.nby;
+      bz1 = r_1 / g.nby;
+    }
+  }
 #pragma unroll
   for (int kk = 0; kk < 16; ++kk) {
     if (kk >= nr) continue;
@@ -372,17 +394,14 @@ __device__ __forceinline__ void decode_shuf_chunk(const ShDec &p, const Geom &g,
     uint64_t f;
     uint32_t x, y, z;
     if (NDIM == 3) {
-      const uint64_t blk = 2 * j + (uint64_t)(kk >> 3);
-      const uint32_t b32 = (uint32_t)blk;
-      const uint32_t bxi = b32 % g.nbx, br_ = b32 / g.nbx;
-      x = (bxi * 8u) + 2u * (uint32_t)(lane & 3);
-      y = (br_ % g.nby) * 8u + (uint32_t)(lane >> 2);
-      z = (br_ / g.nby) * 8u + (uint32_t)(kk & 7);
+      const bool second = kk >= 8;
+      x = (second ? bx1 : bx0) * 8u + 2u * (uint32_t)(lane & 3);
+      y = (second ? by1 : by0) * 8u + (uint32_t)(lane >> 2);
+      z = (second ? bz1 : bz0) * 8u + (uint32_t)(kk & 7);
       f = ((uint64_t)z * g.ny + y) * g.nx + x;
     } else if (NDIM == 2) {
-      const uint32_t b32 = (uint32_t)j;
-      x = (b32 % g.nbx) * 32u + 2u * (uint32_t)(lane & 15);
-      y = (b32 / g.nbx) * 32u + 2u * (uint32_t)kk + (uint32_t)(lane >> 4);
+      x = bx0 * 32u + 2u * (uint32_t)(lane & 15);
+      y = by0 * 32u + 2u * (uint32_t)kk + (uint32_t)(lane >> 4);
       z = 0;
       f = (uint64_t)y * g.nx + x;
     } else {

@@ -125,6 +125,22 @@ def test_batch_options_do_not_change_bytes():
         fz.set_batch_options(True, True)
 
 
+def test_batch_padding_is_written():
+    """Streams are packed at 16-byte offsets; the bytes between a stream's end
+    and the next offset (a RAW stream of N floats, N not a multiple of 4, ends
+    unaligned) are zero, whatever the output buffer held before."""
+    xs, ebs = _fields(seed=5)
+    xg = [x.cuda() for x in xs]
+    outs = []
+    for fill in (0x00, 0xA5):
+        nd = fz._batch_shapes(xg)
+        bound = int(fz.lib().fz_compress_batch_bound(len(xg), nd[0], nd[1]))
+        o = torch.full((bound,), fill, dtype=torch.uint8, device="cuda")
+        buf, offs = fz.compress_batch(xg, ebs, chunk=1024, out=o)
+        outs.append(buf[: offs[-1]].cpu().numpy().copy())
+    assert np.array_equal(outs[0], outs[1])
+
+
 def test_batch_output_too_small():
     xs, ebs = _fields(seed=10)
     xg = [x.cuda() for x in xs]
