@@ -94,6 +94,7 @@ def _declare(L):
                                     u16p, C.c_uint32, C.c_uint32, u8p, C.c_uint64, u64p]
     L.orc_interp_block.argtypes = [C.c_int, C.c_int, u8p, i32p, u8p, i64p]
     L.orc_interp_block.restype = None
+    L.orc_ginterp_field.argtypes = [C.c_int, u64p, i64p]
     L.orc_block_costs.argtypes = [i32p, u8p, i32p, u8p, C.c_uint32, u64p]
     L.orc_log2fix.argtypes = [C.c_uint64]
     L.orc_log2fix.restype = C.c_float
@@ -240,7 +241,8 @@ def compress_bound(shape) -> int:
     return int(lib().orc_compress_bound(len(shape), _p(d, u64p)))
 
 
-PRED_IDS = {"lorenzo1": 0, "lorenzo2": 1, "interp_linear": 2, "interp_cubic": 3, "mlp": 16, "exhaustive": 17}
+PRED_IDS = {"lorenzo1": 0, "lorenzo2": 1, "interp_linear": 2, "interp_cubic": 3, "ginterp": 4, "mlp": 16,
+            "exhaustive": 17}
 
 
 def compress(x: np.ndarray, eb: float, mode: str = "rel", lorenzo_k: int = 1, radius: int = 512,
@@ -281,6 +283,19 @@ def interp_block(cubic: bool, inverse: bool, values, inb=None, corner_q=None, co
     cq = np.zeros(8, np.int32) if corner_q is None else np.ascontiguousarray(corner_q, dtype=np.int32)
     ci = np.zeros(8, np.uint8) if corner_in is None else np.ascontiguousarray(corner_in, dtype=np.uint8)
     lib().orc_interp_block(int(cubic), int(inverse), _p(inb, u8p), _p(cq, i32p), _p(ci, u8p), _p(v, i64p))
+    return v
+
+
+def ginterp_field(values, inverse: bool = False) -> np.ndarray:
+    """Full-field multilevel interpolation of a 3D integer array (C order,
+    shape (nz, ny, nx)): residuals of q (forward) or q from the residuals
+    (inverse); the anchors (all coordinates multiples of 8) pass through."""
+    v = np.ascontiguousarray(values, dtype=np.int64)
+    if v.ndim != 3:
+        raise ValueError("3D array expected")
+    v = v.copy()
+    d = _dims3(v.shape[::-1])
+    _chk(lib().orc_ginterp_field(int(inverse), _p(d, u64p), _p(v, i64p)), "ginterp_field")
     return v
 
 

@@ -497,6 +497,66 @@ void orc_interp_block(int cubic, int inverse, const uint8_t *inb, const int32_t 
   free(w);
 }
 
+/* ------------------------------------------------------------------------ */
+/* Full-field multilevel interpolation (FZMod-Quality, §3.3: the G-Interp    */
+/* spline predictor of cuSZ-i in place of Lorenzo, §3.1-§3.2)                */
+/* ------------------------------------------------------------------------ */
+
+/* Open loop on the integer field q of a 3D field (field order, x fastest),
+ * with the anchor grid of the 8x8x8 blocks: the points whose three
+ * coordinates are all multiples of 8 keep q.  Every other point is predicted
+ * exactly once.  Levels s = 4, 2, 1; within a level the passes along x, then
+ * y, then z; the pass (s, a) covers the points whose a coordinate is s mod 2s,
+ * whose earlier coordinates are 0 mod s and whose later coordinates are 0 mod
+ * 2s.  Its neighbours p +- s and p +- 3s along a were predicted in an earlier
+ * pass or are anchors; a neighbour is available when it lies in the domain,
+ * anywhere in the field (not only in p's block).  Prediction: the cubic form
+ * (-q[-3] + 9 q[-1] + 9 q[+1] - q[+3] + 8) >> 4 when all four are available,
+ * else (q[-1] + q[+1] + 1) >> 1 when both near ones are, else q[-1] (p - s is
+ * always in the domain).  Forward (inverse = 0): v holds q on entry and the
+ * residuals q - prediction on exit (anchors keep q).  Inverse: v holds the
+ * residuals on entry (anchors: q) and q on exit. */
+int orc_ginterp_field(int inverse, const uint64_t d[3], int64_t *v) {
+  const uint64_t n = d[0] * d[1] * d[2];
+  int64_t *w = (int64_t *)malloc((n ? n : 1) * sizeof(int64_t));
+  if (!w) return ORC_ENOMEM;
+  /* w: q.  Forward: all of q.  Inverse: the anchors now, the other points
+   * as their pass reconstructs them. */
+  for (uint64_t i = 0; i < n; i++) w[i] = v[i];
+  for (uint64_t s = 4; s >= 1; s >>= 1)
+    for (int a = 0; a < 3; a++) {
+      uint64_t start[3], step[3];
+      for (int b = 0; b < 3; b++) {
+        start[b] = b == a ? s : 0;
+        step[b] = b == a ? 2 * s : (b < a ? s : 2 * s);
+      }
+      const uint64_t stride = a == 0 ? 1 : (a == 1 ? d[0] : d[0] * d[1]);
+      for (uint64_t z = start[2]; z < d[2]; z += step[2])
+        for (uint64_t y = start[1]; y < d[1]; y += step[1])
+          for (uint64_t x = start[0]; x < d[0]; x += step[0]) {
+            const uint64_t c = a == 0 ? x : (a == 1 ? y : z);
+            const uint64_t i = (z * d[1] + y) * d[0] + x;
+            const int am3 = c >= 3 * s, ap1 = c + s < d[a], ap3 = c + 3 * s < d[a];
+            const int64_t qm1 = w[i - s * stride];
+            int64_t pred;
+            if (am3 && ap3) {
+              const int64_t qm3 = w[i - 3 * s * stride], qp1 = w[i + s * stride], qp3 = w[i + 3 * s * stride];
+              pred = (-qm3 + 9 * qm1 + 9 * qp1 - qp3 + 8) >> 4;
+            } else if (ap1) {
+              pred = (qm1 + w[i + s * stride] + 1) >> 1;
+            } else {
+              pred = qm1;
+            }
+            if (inverse) w[i] = v[i] + pred;
+            else v[i] = w[i] - pred;
+          }
+    }
+  if (inverse)
+    for (uint64_t i = 0; i < n; i++) v[i] = w[i];
+  free(w);
+  return ORC_OK;
+}
+
 /* Residuals of predictor pid (0 Lorenzo-1, 1 Lorenzo-2, 2 interpolation
  * linear, 3 interpolation cubic) for one block; qb in block order. */
 static void block_residual(int pid, uint32_t ndim, const uint32_t b[3], const int32_t *qb, const uint8_t *inb,
@@ -972,7 +1032,7 @@ int orc_compress_full(const float *x, uint32_t ndim, const uint64_t dims[3], uin
   int st = check_args(ndim, dims, &n);
   if (st) return st;
   if (!(eb > 0.0) || !isfinite(eb) || eb_mode > 1) return ORC_EINVAL;
-  if (!(pred <= 3 || pred == 16 || pred == 17)) return ORC_EINVAL;
+  if (!(pred <= 4 || pred == 16 || pred == 17)) return ORC_EINVAL;
   if (pred >= 2 && ndim != 3) return ORC_EUNSUPPORTED;
   if (pred == 16 && !w) return ORC_EINVAL;
   if (R < 2 || R > 512) return ORC_EINVAL;
@@ -1038,9 +1098,17 @@ int orc_compress_full(const float *x, uint32_t ndim, const uint64_t dims[3], uin
   memset(hist, 0, sizeof(hist));
   uint64_t n_out = 0, n_exc = 0;
   int overflow = 0;
-  if (!codes || !anchors || !oidx || !oval || !eidx || !eval || !qb || !inb || !fidx || !delta || !ids) {
+  /* full-field interpolation: the residuals of the whole field first */
+  int64_t *gres = pred == 4 ? (int64_t *)malloc(n * sizeof(int64_t)) : NULL;
+  if (!codes || !anchors || !oidx || !oval || !eidx || !eval || !qb || !inb || !fidx || !delta || !ids ||
+      (pred == 4 && !gres)) {
     st = ORC_ENOMEM;
     goto done;
+  }
+  if (pred == 4) {
+    for (uint64_t i = 0; i < n; i++) gres[i] = q[i];
+    st = orc_ginterp_field(0, dd, gres);
+    if (st) goto done;
   }
   for (uint64_t blk = 0; blk < g.n_blocks; blk++) {
     gather_block(&g, blk, q, qb, inb, fidx);
@@ -1059,7 +1127,10 @@ int orc_compress_full(const float *x, uint32_t ndim, const uint64_t dims[3], uin
       pid = orc_mlp_infer(w, feat, lg);
     }
     if (sel) ids[blk >> 2] |= (uint8_t)(pid << (2 * (blk & 3)));
-    block_residual(pid, ndim, g.b, qb, inb, cq, cin, delta);
+    if (pid == 4)
+      for (uint64_t i = 0; i < g.bsize; i++) delta[i] = inb[i] ? gres[fidx[i]] : 0;
+    else
+      block_residual(pid, ndim, g.b, qb, inb, cq, cin, delta);
     for (uint64_t i = 0; i < g.bsize; i++) {
       uint64_t pos = blk * g.bsize + i;
       uint16_t c;
@@ -1201,7 +1272,7 @@ int orc_compress_full(const float *x, uint32_t ndim, const uint64_t dims[3], uin
   st = ORC_OK;
 done:
   free(q); free(exc); free(codes); free(anchors); free(oidx); free(oval); free(eidx); free(eval);
-  free(qb); free(inb); free(fidx); free(delta); free(ids);
+  free(qb); free(inb); free(fidx); free(delta); free(ids); free(gres);
   return st;
 }
 
@@ -1269,7 +1340,7 @@ int orc_decompress(const uint8_t *in, uint64_t in_bytes, float *out, uint64_t ou
   uint32_t pred = get_u32(in + H_PRED);
   const int sel = flags == F_IDS;
   if (R < 2 || R > 512) return ORC_ECORRUPT;
-  if (sel != (pred == 16 || pred == 17) || !(pred <= 3 || pred == 16 || pred == 17)) return ORC_ECORRUPT;
+  if (sel != (pred == 16 || pred == 17) || !(pred <= 4 || pred == 16 || pred == 17)) return ORC_ECORRUPT;
   if (pred >= 2 && ndim != 3) return ORC_ECORRUPT;
   if (shuf && pred > 1) return ORC_ECORRUPT;
   uint64_t o_ids = get_u64(in + H_OFF_IDS);
@@ -1320,7 +1391,9 @@ int orc_decompress(const uint8_t *in, uint64_t in_bytes, float *out, uint64_t ou
   int32_t *qb = (int32_t *)malloc(g.bsize * 4);
   uint8_t *inb = (uint8_t *)malloc(g.bsize);
   uint64_t *fidx = (uint64_t *)malloc(g.bsize * 8);
-  if (!words || !codes || !v || !qb || !inb || !fidx) { st = ORC_ENOMEM; goto ddone; }
+  /* full-field interpolation: the residual field, inverted as a whole */
+  int64_t *gres = pred == 4 ? (int64_t *)malloc(n * sizeof(int64_t)) : NULL;
+  if (!words || !codes || !v || !qb || !inb || !fidx || (pred == 4 && !gres)) { st = ORC_ENOMEM; goto ddone; }
   for (uint64_t w = 0; w < n_words; w++) words[w] = get_u32(in + o_bits + 4 * w);
   /* step 11a: the code stream, chunk by chunk; each chunk must use exactly
    * its stored bit count */
@@ -1361,6 +1434,11 @@ int orc_decompress(const uint8_t *in, uint64_t in_bytes, float *out, uint64_t ou
     }
     v[0] += (int32_t)get_u32(in + o_anch + 4 * blk);
     int pid = sel ? (in[o_ids + (blk >> 2)] >> (2 * (blk & 3))) & 3 : (int)pred;
+    if (pid == 4) {
+      for (uint64_t i = 0; i < g.bsize; i++)
+        if (inb[i]) gres[fidx[i]] = v[i];
+      continue;
+    }
     if (pid < 2) {
       orc_lorenzo_block_inverse(pid + 1, ndim, g.b, v);
     } else {
@@ -1386,9 +1464,28 @@ int orc_decompress(const uint8_t *in, uint64_t in_bytes, float *out, uint64_t ou
       out[fidx[i]] = r;
     }
   }
+  if (pred == 4) {
+    /* step 11c: inverse interpolation of the whole field, then
+     * dequantization and exceptions in code-stream order */
+    st = orc_ginterp_field(1, g.d, gres);
+    if (st) goto ddone;
+    for (uint64_t blk = 0; blk < nb; blk++) {
+      gather_block(&g, blk, NULL, qb, inb, fidx);
+      for (uint64_t i = 0; i < g.bsize; i++) {
+        if (!inb[i]) continue;
+        uint64_t pos = blk * g.bsize + i;
+        float r = (float)(int32_t)gres[fidx[i]] * ebx2;
+        if (ec < n_exc && get_u32(in + o_ei + 4 * ec) == pos) {
+          r = u2f(get_u32(in + o_ev + 4 * ec));
+          ec++;
+        }
+        out[fidx[i]] = r;
+      }
+    }
+  }
   if (oc != n_out || ec != n_exc || p != tbits) st = ORC_ECORRUPT;
 ddone:
-  free(words); free(codes); free(v); free(qb); free(inb); free(fidx);
+  free(words); free(codes); free(v); free(qb); free(inb); free(fidx); free(gres);
   return st;
 }
 
