@@ -475,6 +475,8 @@ def run_fz(args, rank, world, local_rank):
         res["configs"] = bench_configs(fz, dev, stream, args)
     if rank == 0 and world == 1 and not args.no_speed:
         res["speed_pipeline"] = bench_speed(fz, dev, stream, x, args)
+    if rank == 0 and world == 1 and not args.no_quality:
+        res["quality_pipeline"] = bench_quality(fz, dev, stream, x, args)
     if rank == 0 and world == 1 and not args.no_hist:
         res["histogram"] = bench_histogram(fz, dev, stream, x)
     if rank == 0 and world == 1 and not args.no_rd:
@@ -670,6 +672,57 @@ def bench_speed(fz, dev, stream, x512, args):
     return out
 
 
+def bench_quality(fz, dev, stream, x512, args):
+    """FZMod-Quality (§3.3): the full-field multilevel interpolation predictor
+    with the Huffman encoder, on the 512^3 Gaussian random field and on the
+    smooth stitched 512^3 field, REL 1e-4 and 1e-3; compress and decompress
+    GB/s (L2 flushed before each timed call, median of the timed calls),
+    roofline fractions on the forced bytes of the Lorenzo path (compress
+    12N + S, decompress S + 4N) and the CR beside the Lorenzo stream's."""
+    peak, _ = _peaks()
+    scratch = torch.empty(64 << 20, dtype=torch.float32, device=dev)
+    stitched = synth.stitched3d(512, device=dev)
+    specs = [("grf512", x512, 1e-4), ("grf512", x512, 1e-3), ("stitched512", stitched, 1e-4),
+             ("stitched512", stitched, 1e-3)]
+    out = []
+    for key, x, eb in specs:
+        N = x.numel()
+        ob = torch.empty(fz.compress_bound(x.shape), dtype=torch.uint8, device=dev)
+        y = torch.empty_like(x)
+        S_l = fz.compress(x, eb, out=ob).numel()
+        buf = fz.compress(x, eb, out=ob, predictor="ginterp")
+        fz.decompress(buf, out=y)
+        err = float((y.double() - x.double()).abs().max()) / (eb * (float(x.max()) - float(x.min())))
+        tc, td = [], []
+        for i in range(3 + args.config_reps):
+            _flush_l2(scratch)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            buf = fz.compress(x, eb, out=ob, predictor="ginterp")
+            e1.record(stream)
+            _flush_l2(scratch)
+            e2, e3 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e2.record(stream)
+            fz.decompress(buf, out=y)
+            e3.record(stream)
+            torch.cuda.synchronize(dev)
+            if i >= 3:
+                tc.append(e0.elapsed_time(e1))
+                td.append(e2.elapsed_time(e3))
+        S = buf.numel()
+        mc, md = statistics.median(tc), statistics.median(td)
+        out.append({"workload": key, "eb": eb, "values": N, "cr_ginterp": round(4 * N / S, 4),
+                    "cr_lorenzo1": round(4 * N / S_l, 4), "max_err_over_eb": round(err, 6),
+                    "compress_gbs": round(4 * N / (mc * 1e-3) / 1e9, 2),
+                    "decompress_gbs": round(4 * N / (md * 1e-3) / 1e9, 2),
+                    "compress_roofline_frac": round((12 * N + S) / (mc * 1e-3) / 1e9 / peak, 4),
+                    "decompress_roofline_frac": round((S + 4 * N) / (md * 1e-3) / 1e9 / peak, 4)})
+        del ob, y
+    del scratch, stitched
+    torch.cuda.empty_cache()
+    return out
+
+
 def bench_histogram(fz, dev, stream, x512):
     """The histogram stage (§3.2) on its own, both methods: Lorenzo-1 codes of
     the 512^3 field and interpolation (cubic) codes of the smooth stitched
@@ -833,6 +886,8 @@ def main():
     ap.add_argument("--no-rd", action="store_true", help="skip the rate-distortion / Eq. 1 report")
     ap.add_argument("--no-hist", action="store_true", help="skip the histogram-stage comparison")
     ap.add_argument("--no-speed", action="store_true", help="skip the bit-shuffle (FZMod-Speed) pipeline")
+    ap.add_argument("--no-quality", action="store_true",
+                    help="skip the full-field interpolation (FZMod-Quality) pipeline")
     ap.add_argument("--config-reps", type=int, default=10, help="timed calls per extra workload and bound")
     ap.add_argument("--traffic", type=float, default=None, help="ncu dram bytes per launch of the dominant kernel")
     args = ap.parse_args()

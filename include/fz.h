@@ -58,8 +58,13 @@ typedef enum {
 typedef enum {
   FZ_PRED_LORENZO1 = 0, /* first-order Lorenzo, 1D/2D/3D (cuSZ, §3.1) */
   FZ_PRED_LORENZO2 = 1, /* second-order Lorenzo, 1D/2D/3D */
-  FZ_PRED_INTERP_LIN = 2,
+  FZ_PRED_INTERP_LIN = 2,   /* block-local interpolation (3D), the selector's candidates */
   FZ_PRED_INTERP_CUBIC = 3,
+  FZ_PRED_GINTERP = 4,      /* full-field multilevel interpolation, FZMod-Quality's G-Interp predictor (§3.3,
+                               from cuSZ-i via §3.1-§3.2), 3D only: anchors at the points whose coordinates
+                               are all multiples of 8; levels 4, 2, 1, passes along x, y, z; cubic from
+                               p +- s, p +- 3s where all four lie in the domain, else linear, else p - s;
+                               Huffman encoder with the default chunk only */
   FZ_SEL_MLP = 16,      /* per-block predictor picked by the learned selector */
   FZ_SEL_EXHAUSTIVE = 17/* per-block predictor picked by exhaustive trial */
 } fz_predictor;

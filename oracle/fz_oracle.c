@@ -1079,9 +1079,12 @@ int orc_compress_full(const float *x, uint32_t ndim, const uint64_t dims[3], uin
   if (!q || !exc) { free(q); free(exc); return ORC_ENOMEM; }
   orc_prequant(x, n, inv2eb, ebx2, eb_chk, q, exc);
 
-  /* steps 4-7: blocks, residuals, codes, outliers, exceptions, histogram */
+  /* steps 4-7: blocks, residuals, codes, outliers, exceptions, histogram;
+   * code-stream positions are 32-bit in the format (outlier and exception
+   * indices) */
   grid_t g;
   make_grid(ndim, dd, &g);
+  if (g.npad > 0xffffffffull) { free(q); free(exc); return ORC_EUNSUPPORTED; }
   uint16_t *codes = (uint16_t *)malloc(g.npad * sizeof(uint16_t));
   int32_t *anchors = (int32_t *)malloc(g.n_blocks * sizeof(int32_t));
   uint64_t cap_list = n / 8;

@@ -31,7 +31,8 @@ SELECTOR_FEATURES = 32
 
 STATUS = {0: "FZ_OK", 1: "FZ_EINVAL", 2: "FZ_ENOMEM", 3: "FZ_ECUDA", 4: "FZ_EBUFFER", 5: "FZ_ECORRUPT",
           6: "FZ_ETIMEOUT", 7: "FZ_EUNSUPPORTED"}
-PREDICTORS = {"lorenzo1": 0, "lorenzo2": 1, "interp_linear": 2, "interp_cubic": 3, "mlp": 16, "exhaustive": 17}
+PREDICTORS = {"lorenzo1": 0, "lorenzo2": 1, "interp_linear": 2, "interp_cubic": 3, "ginterp": 4, "mlp": 16,
+              "exhaustive": 17}
 
 _lock = threading.Lock()
 _lib = None

@@ -178,6 +178,7 @@ fz_status parse_pipe(const fz_pipeline *pipe, uint32_t ndim, Req &r) {
     case FZ_PRED_LORENZO2: return FZ_OK;
     case FZ_PRED_INTERP_LIN:
     case FZ_PRED_INTERP_CUBIC:
+    case FZ_PRED_GINTERP:
     case FZ_SEL_EXHAUSTIVE: return ndim == 3 ? FZ_OK : FZ_EUNSUPPORTED;
     case FZ_SEL_MLP:
       if (ndim != 3) return FZ_EUNSUPPORTED;
@@ -213,13 +214,14 @@ fz_status check_header(const fz_header &h, uint64_t in_bytes, Geom &g) {
     if (h.dims[a] != 1) return FZ_ECORRUPT;
   if (h.total_bytes > in_bytes || h.total_bytes < FZ_HEADER_BYTES) return FZ_ECORRUPT;
   make_geom(h.ndim, h.dims, g);
+  if (h.flags != FZ_FLAG_RAW && h.flags != FZ_FLAG_CONST && !positions_fit(g)) return FZ_ECORRUPT;
   if (h.flags == FZ_FLAG_RAW) return h.total_bytes == FZ_HEADER_BYTES + 4 * n ? FZ_OK : FZ_ECORRUPT;
   if (h.flags == FZ_FLAG_CONST) return h.total_bytes == FZ_HEADER_BYTES + 16 ? FZ_OK : FZ_ECORRUPT;
   if (h.flags != 0 && h.flags != FZ_FLAG_IDS && h.flags != FZ_FLAG_SHUF) return FZ_EUNSUPPORTED;
   const bool shuf = h.flags == FZ_FLAG_SHUF;
   if (h.radius < 2 || h.radius > 512) return FZ_ECORRUPT;
   const bool sel = h.predictor == FZ_SEL_MLP || h.predictor == FZ_SEL_EXHAUSTIVE;
-  if (!(h.predictor <= FZ_PRED_INTERP_CUBIC || sel)) return FZ_ECORRUPT;
+  if (!(h.predictor <= FZ_PRED_GINTERP || sel)) return FZ_ECORRUPT;
   if (sel != (h.flags == FZ_FLAG_IDS)) return FZ_ECORRUPT;
   if (h.predictor > FZ_PRED_LORENZO2 && h.ndim != 3) return FZ_ECORRUPT;
   // every bound below is written so that no sum can wrap around 2^64: an
@@ -409,6 +411,7 @@ fz_status fz_compress(fz_ctx *ctx, const float *d_in, uint32_t ndim, const uint6
   uint64_t d3[3] = {dims[0], ndim >= 2 ? dims[1] : 1, ndim >= 3 ? dims[2] : 1};
   Geom g;
   make_geom(ndim, d3, g);
+  if (!positions_fit(g)) return FZ_EUNSUPPORTED;
   if (r.chunk) set_chunk(g, r.chunk);
   CompressWs ws;
   size_t need = layout_compress(g, nullptr, ws);
@@ -485,10 +488,16 @@ fz_status fz_decompress(fz_ctx *ctx, const void *d_in, uint64_t in_bytes, const 
   // a per-block first-outlier table pays off when most blocks hold outliers
   // plane-parallel streams (64-symbol chunks) and bit-shuffle streams locate
   // outliers per plane or chunk
-  const bool ofirst = !selpath && h.n_out > h.n_blocks / 8 && !(h.ndim == 3 && h.chunk == 64) &&
-                      h.flags != FZ_FLAG_SHUF;
+  // the full-field interpolation decoder always takes it (its code decoder
+  // matches every outlier code to the list through it)
+  const bool gipath = h.predictor == FZ_PRED_GINTERP;
+  const bool ofirst = gipath || (!selpath && h.n_out > h.n_blocks / 8 &&
+                                             !(h.ndim == 3 && h.chunk == 64) && h.flags != FZ_FLAG_SHUF);
   const size_t o_err = take(dec_offset_zero_bytes(h)), o_gsum = take(8 * n_units), o_lut = take(2u << kLutBits),
-               o_codes = selpath ? take(2 * g.npad) : 0, o_ofirst = ofirst ? take(4 * h.n_blocks) : 0;
+               o_codes = selpath ? take(2 * g.npad) : 0, o_ofirst = ofirst ? take(4 * h.n_blocks) : 0,
+               o_q4 = gipath ? take(4 * ginterp_level_values(h, 4)) : 0,
+               o_q2 = gipath ? take(4 * ginterp_level_values(h, 2)) : 0,
+               o_ovals = gipath ? take(4 * g.npad) : 0;
   if ((st = ensure_ws(ctx, off))) return st;
   char *base = reinterpret_cast<char *>(ctx->ws);
   DecodeWs ws;
@@ -501,7 +510,15 @@ fz_status fz_decompress(fz_ctx *ctx, const void *d_in, uint64_t in_bytes, const 
   if (selpath) {
     e = cudaMemsetAsync(ws.err, 0, 16, s);
     if (e == cudaSuccess) { e = launch_decode_prep(in, h, ws, s); clk.mark("dec_prep", 2); }
-    if (e == cudaSuccess) {
+    if (e == cudaSuccess && ofirst) e = cudaMemsetAsync(ws.ofirst, 0xff, 4 * h.n_blocks, s);
+    if (e == cudaSuccess && ofirst) { e = launch_outlier_starts(in, h, ws, s, ctx->sm_count); clk.mark("outliers", 1); }
+    if (e == cudaSuccess && gipath) {
+      e = launch_gi_decode(in, h, d_out, ws, reinterpret_cast<uint16_t *>(base + o_codes),
+                           reinterpret_cast<int32_t *>(base + o_ovals),
+                           reinterpret_cast<int32_t *>(base + o_q4), reinterpret_cast<int32_t *>(base + o_q2), s,
+                           ctx->sm_count);
+      clk.mark("decode", 5 + (h.n_exc ? 1 : 0));
+    } else if (e == cudaSuccess) {
       e = launch_sel_decode(in, h, d_out, ws, reinterpret_cast<uint16_t *>(base + o_codes), s, ctx->sm_count);
       clk.mark("decode", 2);
     }
@@ -542,6 +559,7 @@ fz_status fz_lorenzo_quantize(fz_ctx *ctx, const float *d_in, uint32_t ndim, con
   uint64_t d3[3] = {dims[0], ndim >= 2 ? dims[1] : 1, ndim >= 3 ? dims[2] : 1};
   Geom g;
   make_geom(ndim, d3, g);
+  if (!positions_fit(g)) return FZ_EUNSUPPORTED;
   CompressWs ws;
   size_t need = layout_compress(g, nullptr, ws);
   if ((st = ensure_ws(ctx, need)) || (st = ensure_pinned(ctx))) return st;

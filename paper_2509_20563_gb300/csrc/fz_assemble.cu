@@ -172,8 +172,55 @@ __device__ __forceinline__ void assemble_body(const float *__restrict__ x, const
 
 // The ordered gather of the outliers and exceptions: each tile's entries
 // are contiguous in the scratch lists and go to the stream slots computed
-// by assemble_body; warp w of nw takes tiles w, w + nw, ... and its lanes
-// copy a tile's entries side by side.
+// by assemble_body.  A warp takes one item (a tile, or in 3D Lorenzo one
+// block of a tile) whose entries sit in 8 slices of the scratch lists (one
+// per quantizer warp): lane k < 8 holds slice k's count n and start slot,
+// and the warp copies the item's entries as one range -- entry i lies in
+// the last slice whose prefix offset is <= i -- with four entries in flight
+// per lane.
+__device__ __forceinline__ void gather_range(uint32_t n, uint32_t slot, uint64_t dst, uint64_t limit, uint64_t cap,
+                                             const uint32_t *__restrict__ sidx, const uint32_t *__restrict__ sval,
+                                             uint32_t *didx, uint32_t *dval) {
+  const int lane = threadIdx.x & 31;
+  uint32_t incl = n;  // inclusive prefix of the 8 counts (lanes 8..31 hold 0)
+#pragma unroll
+  for (int off = 1; off < 8; off <<= 1) {
+    const uint32_t v = __shfl_up_sync(0xffffffffu, incl, off);
+    if ((lane & 7) >= off) incl += v;
+  }
+  const uint32_t total = __shfl_sync(0xffffffffu, incl, 7);
+  if (total == 0) return;
+  uint32_t ex[8], base[8];  // slice k: prefix offset, start slot - prefix offset (mod 2^32)
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    ex[k] = __shfl_sync(0xffffffffu, incl - n, k);
+    base[k] = __shfl_sync(0xffffffffu, slot, k) - ex[k];
+  }
+  for (uint32_t i0 = 0; i0 < total; i0 += 128) {
+    uint32_t vi[4], vv[4];
+    bool ok[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const uint32_t i = i0 + 32 * u + lane;
+      uint32_t b = base[0];
+#pragma unroll
+      for (int k = 1; k < 8; ++k) b = i >= ex[k] ? base[k] : b;
+      const uint64_t src = (uint32_t)(b + i);
+      ok[u] = i < total && src < cap && dst + i < limit;
+      vi[u] = ok[u] ? __ldg(sidx + src) : 0u;
+      vv[u] = ok[u] ? __ldg(sval + src) : 0u;
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const uint32_t i = i0 + 32 * u + lane;
+      if (ok[u]) {
+        didx[dst + i] = vi[u];
+        dval[dst + i] = vv[u];
+      }
+    }
+  }
+}
+
 __device__ __forceinline__ void gather_body(const Geom &g, const CompressWs &ws, uint8_t *d_out, uint64_t w,
                                             uint64_t nw) {
   const Ctl *ctl = ws.ctl;
@@ -182,36 +229,30 @@ __device__ __forceinline__ void gather_body(const Geom &g, const CompressWs &ws,
   const uint64_t n_out = h.n_out, n_exc = h.n_exc;
   if ((n_out | n_exc) == 0) return;
   uint32_t *oidx = reinterpret_cast<uint32_t *>(d_out + h.off_out_idx);
-  int32_t *oval = reinterpret_cast<int32_t *>(d_out + h.off_out_val);
+  uint32_t *oval = reinterpret_cast<uint32_t *>(d_out + h.off_out_val);
   uint32_t *eidx = reinterpret_cast<uint32_t *>(d_out + h.off_exc_idx);
   uint32_t *eval = reinterpret_cast<uint32_t *>(d_out + h.off_exc_val);
+  const uint32_t *s_oval = reinterpret_cast<const uint32_t *>(ws.out_val);
   const int lane = threadIdx.x & 31;
   // the 3D Lorenzo quantizer files 8 slices per warp (one per block, by
   // block then warp); the other quantizers one slice per warp
   const bool by_block = g.ndim == 3 && h.predictor <= FZ_PRED_LORENZO2;
-  auto copy = [&](uint64_t so, uint64_t se, uint32_t no, uint32_t ne, uint64_t o, uint64_t e) {
-    for (uint32_t i = lane; i < no; i += 32) {
-      const uint64_t src = so + i;
-      if (src < ws.cap_list && o + i < n_out) { oidx[o + i] = ws.out_idx[src]; oval[o + i] = ws.out_val[src]; }
-    }
-    for (uint32_t i = lane; i < ne; i += 32) {
-      const uint64_t src = se + i;
-      if (src < ws.cap_list && e + i < n_exc) { eidx[e + i] = ws.exc_idx[src]; eval[e + i] = ws.exc_val[src]; }
-    }
+  const uint64_t n_list = ctl->n_otiles;
+  const uint64_t n_items = by_block ? n_list * 8 : n_list;
+  auto bytesum = [](unsigned long long v) -> uint32_t {
+    return (uint32_t)__dp4a((uint32_t)v, 0x01010101u, 0u) + (uint32_t)__dp4a((uint32_t)(v >> 32), 0x01010101u, 0u);
   };
-  if (by_block) {
-    // a warp per (tile, block): the block's 8 slices (one per warp of the
-    // quantizer) follow the earlier blocks' slices of the tile
-    auto bytesum = [](unsigned long long v) -> uint32_t {
-      return (uint32_t)__dp4a((uint32_t)v, 0x01010101u, 0u) + (uint32_t)__dp4a((uint32_t)(v >> 32), 0x01010101u, 0u);
-    };
-    const uint64_t n_list = ctl->n_otiles;
-    for (uint64_t item = w; item < n_list * 8; item += nw) {
-      const uint64_t tile = ws.otiles[item >> 3];
+  for (uint64_t item = w; item < n_items; item += nw) {
+    const uint64_t tile = ws.otiles[by_block ? item >> 3 : item];
+    const uint2 dst = ws.tdst[tile];
+    uint32_t no = 0, ne = 0, so = 0, se = 0;
+    uint64_t o = dst.x, e = dst.y;
+    if (by_block) {
+      // a (tile, block) item: the block's slices follow the earlier blocks'
+      // entries of each quantizer warp's slice
       const int b = (int)(item & 7);
-      const uint2 dst = ws.tdst[tile];
       const unsigned long long below = b ? (1ull << (8 * b)) - 1 : 0ull;
-      uint32_t no = 0, ne = 0, so = 0, se = 0, po = 0, pe = 0;
+      uint32_t po = 0, pe = 0;
       if (lane < 8) {
         const WarpSlots wsl = ws.winfo[tile * 8 + lane];
         no = (uint32_t)(wsl.ocnt >> (8 * b)) & 255u;
@@ -221,32 +262,17 @@ __device__ __forceinline__ void gather_body(const Geom &g, const CompressWs &ws,
         so = wsl.oslot + po;
         se = wsl.eslot + pe;
       }
-      const uint32_t bo = __reduce_add_sync(0xffffffffu, po), be = __reduce_add_sync(0xffffffffu, pe);
-      uint64_t o = (uint64_t)dst.x + bo, e = (uint64_t)dst.y + be;
-      for (int k = 0; k < 8; ++k) {
-        const uint32_t nk = __shfl_sync(0xffffffffu, no, k), ek = __shfl_sync(0xffffffffu, ne, k);
-        const uint32_t sk = __shfl_sync(0xffffffffu, so, k), tk = __shfl_sync(0xffffffffu, se, k);
-        if (nk | ek) copy(sk, tk, nk, ek, o, e);
-        o += nk;
-        e += ek;
-      }
+      o += __reduce_add_sync(0xffffffffu, po);
+      e += __reduce_add_sync(0xffffffffu, pe);
+    } else if (lane < 8) {
+      const WarpSlots wsl = ws.winfo[tile * 8 + lane];
+      no = (uint32_t)(wsl.ocnt & 0xffffu);
+      ne = (uint32_t)(wsl.ecnt & 0xffffu);
+      so = wsl.oslot;
+      se = wsl.eslot;
     }
-    return;
-  }
-  const uint64_t n_list = ctl->n_otiles;
-  for (uint64_t item = w; item < n_list; item += nw) {
-    const uint64_t tile = ws.otiles[item];
-    const uint2 dst = ws.tdst[tile];
-    uint64_t o = dst.x, e = dst.y;
-    const WarpSlots *wsl = ws.winfo + tile * 8;
-    {
-      for (int k = 0; k < 8; ++k) {
-        const uint32_t no = (uint32_t)(wsl[k].ocnt & 0xffffu), ne = (uint32_t)(wsl[k].ecnt & 0xffffu);
-        if (no | ne) copy(wsl[k].oslot, wsl[k].eslot, no, ne, o, e);
-        o += no;
-        e += ne;
-      }
-    }
+    gather_range(no, so, o, n_out, ws.cap_list, ws.out_idx, s_oval, oidx, oval);
+    gather_range(ne, se, e, n_exc, ws.cap_list, ws.exc_idx, ws.exc_val, eidx, eval);
   }
 }
 

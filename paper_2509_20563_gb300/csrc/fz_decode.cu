@@ -931,6 +931,19 @@ __global__ void k_outlier_starts(const uint32_t *__restrict__ out_idx, uint64_t 
 }
 }  // namespace
 
+cudaError_t launch_exc_scatter(const uint8_t *d_in, const fz_header &h, float *d_out, uint32_t *err, uint32_t *h_err,
+                               cudaStream_t s, int sm_count) {
+  Geom g;
+  make_geom(h.ndim, h.dims, g);
+  uint64_t eg = (h.n_exc + 255) / 256;
+  if (eg > (uint64_t)sm_count * 4) eg = (uint64_t)sm_count * 4;
+  if (eg == 0) eg = 1;
+  k_exc_scatter<<<(unsigned)eg, 256, 0, s>>>(reinterpret_cast<const uint32_t *>(d_in + h.off_exc_idx),
+                                             reinterpret_cast<const uint32_t *>(d_in + h.off_exc_val), h.n_exc, g,
+                                             d_out, err, h_err);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_outlier_starts(const uint8_t *d_in, const fz_header &h, const DecodeWs &ws, cudaStream_t s,
                                   int sm_count) {
   Geom g;

@@ -43,6 +43,10 @@ struct Geom {
   uint64_t n_chunks;       // ceil(npad / chunk)
 };
 
+// Code-stream positions (block-major, padding included) are 32-bit in the
+// stream format (outlier and exception indices) and in the kernels.
+inline __host__ __device__ bool positions_fit(const Geom &g) { return g.npad <= 0xffffffffull; }
+
 inline __host__ __device__ void make_geom(uint32_t ndim, const uint64_t dims[3], Geom &g) {
   g.ndim = ndim;
   g.nx = (uint32_t)dims[0];
@@ -455,6 +459,18 @@ cudaError_t launch_select_report(const float *x, const Geom &g, uint32_t R, cons
                                  uint32_t *costs, uint16_t *feat, cudaStream_t s, int sm_count);
 cudaError_t launch_sel_decode(const uint8_t *d_in, const fz_header &h, float *d_out, const DecodeWs &ws,
                               uint16_t *codes, cudaStream_t s, int sm_count);
+// the code stream of a stream with one chunk per block into `codes` (npad symbols); with `ovals`
+// (npad entries) and ws.ofirst also every outlier's residual at its position, the list checked
+cudaError_t launch_dec_codes(const uint8_t *d_in, const fz_header &h, const DecodeWs &ws, uint16_t *codes,
+                             int32_t *ovals, cudaStream_t s, int sm_count);
+// the exceptions of a stream over the reconstructed field (list checked: ascending, in the domain)
+cudaError_t launch_exc_scatter(const uint8_t *d_in, const fz_header &h, float *d_out, uint32_t *err, uint32_t *h_err,
+                               cudaStream_t s, int sm_count);
+// full-field interpolation streams: values of the level-s grid (ceil(dims / s) points)
+uint64_t ginterp_level_values(const fz_header &h, uint32_t s);
+// codes, the level-4 grid into q4, the level-2 grid into q2, the field into d_out
+cudaError_t launch_gi_decode(const uint8_t *d_in, const fz_header &h, float *d_out, const DecodeWs &ws,
+                             uint16_t *codes, int32_t *ovals, int32_t *q4, int32_t *q2, cudaStream_t s, int sm_count);
 cudaError_t launch_mlp_grad(const float *w, const uint16_t *feat, const uint8_t *labels, uint32_t n,
                             float *partial, float *grad, float *loss, cudaStream_t s);
 cudaError_t launch_adam(float *w, const float *grad, float *m, float *v, uint16_t *w_bf16, uint32_t step, float lr,

@@ -35,7 +35,7 @@ namespace {
 constexpr int kTX = 64, kTXP = 72, kRows = 64;  // tile: 8 blocks along x, rows (y, z)
 constexpr int kSelThreads = 256;
 
-enum SelMode : int { kSelFixed = 0, kSelExhaustive = 1, kSelNet = 2, kSelReport = 3 };
+enum SelMode : int { kSelFixed = 0, kSelExhaustive = 1, kSelNet = 2, kSelReport = 3, kSelGinterp = 4 };
 
 // Per-warp view of one block inside the shared tile.
 struct BlockView {
@@ -44,6 +44,7 @@ struct BlockView {
   uint32_t cin;        // corner availability bits
   int wb;              // block within the tile
   uint32_t xlim, ylim, zlim;  // in-domain extent of the block (1..8 per axis)
+  const uint4 *itab;   // full-block interpolation stencils (InterpTab entries), quantizer only
   __device__ __forceinline__ bool in(int px, int py, int pz) const {
     return (uint32_t)px < xlim && (uint32_t)py < ylim && (uint32_t)pz < zlim;
   }
@@ -121,6 +122,43 @@ __device__ __forceinline__ int32_t residual(const BlockView &b, int pid, int px,
   }
 }
 
+// ---------------------------------------------------------------- full-field interpolation
+// Residual of the full-field multilevel interpolation (FZMod-Quality's
+// G-Interp, §3.3) at a non-origin point of a block: the level s and pass axis
+// come from the point's coordinates in its block (block origins are
+// multiples of 8, so these are its field coordinates mod 8), and the
+// neighbours p +- s, p +- 3s along the axis are available anywhere in the
+// domain.  Their q comes from the shared tile when they lie in it, else from
+// the input, prequantized here (the same q the tile would hold).
+struct GiTile {
+  const float *x;
+  const int32_t *sq;       // the tile's q, row (y + 8 z), column x (kTXP per row)
+  uint32_t x0, y0, z0;     // tile origin in the field
+  uint32_t nx, ny, nz;
+  float inv2eb, ebx2, eb_chk;
+  __device__ __forceinline__ int32_t q(uint32_t X, uint32_t Y, uint32_t Z) const {
+    const uint32_t tx = X - x0, ty = Y - y0, tz = Z - z0;  // below the tile wraps to large
+    if (tx < (uint32_t)kTX && ty < 8u && tz < 8u) return sq[(ty + 8 * tz) * kTXP + tx];
+    bool e;
+    return prequant(__ldg(x + ((uint64_t)Z * ny + Y) * nx + X), inv2eb, ebx2, eb_chk, e);
+  }
+};
+
+__device__ __forceinline__ int32_t gi_residual(const GiTile &t, int px, int py, int pz, uint32_t X, uint32_t Y,
+                                               uint32_t Z) {
+  int s, a;
+  level_axis(px, py, pz, s, a);
+  const uint32_t c = a == 0 ? X : (a == 1 ? Y : Z), m = a == 0 ? t.nx : (a == 1 ? t.ny : t.nz);
+  const int sx = a == 0 ? s : 0, sy = a == 1 ? s : 0, sz = a == 2 ? s : 0;
+  auto at = [&](int k) { return (int64_t)t.q(X + k * sx, Y + k * sy, Z + k * sz); };
+  const int64_t qm1 = at(-1);
+  int64_t pred;
+  if (c >= 3u * s && c + 3u * s < m) pred = (-at(-3) + 9 * qm1 + 9 * at(1) - at(3) + 8) >> 4;
+  else if (c + (uint32_t)s < m) pred = (qm1 + at(1) + 1) >> 1;
+  else pred = qm1;
+  return (int32_t)(at(0) - pred);
+}
+
 __device__ __forceinline__ uint32_t trial_bits(int32_t d, uint32_t R) {
   const uint32_t a = (uint32_t)(d < 0 ? -d : d);
   if (a >= R) return 96u;
@@ -167,31 +205,53 @@ __device__ __forceinline__ void fb_lorenzo(int32_t (&a)[16]) {
   for (int i = 15; i >= 2; --i) a[i] -= a[i - 2];  // the plane below, before its own z step
 }
 
-// Interpolation residual at a non-origin point of a full block: every
-// in-block point is available, and a neighbour at coordinate 8 on the pass
-// axis is the corner anchor when the other two coordinates are 0.
-__device__ __forceinline__ int32_t fb_interp(const BlockView &b, bool cubic, int px, int py, int pz) {
-  int s, a;
-  level_axis(px, py, pz, s, a);
-  const int c = a == 0 ? px : (a == 1 ? py : pz);
-  const bool on_axis = (a == 0 ? (py | pz) : (a == 1 ? (px | pz) : (px | py))) == 0;
-  auto at_c = [&](int cc) -> int32_t {  // 0 <= cc <= 8 along the pass axis
-    if (cc >= 8) return b.cq[1 << a];
-    return b.at(a == 0 ? cc : px, a == 1 ? cc : py, a == 2 ? cc : pz);
-  };
-  const int32_t q = b.at(px, py, pz);
-  const int32_t vm1 = at_c(c - s);          // c - s >= 0 at every level
-  const bool ap1 = c + s < 8 || on_axis;     // c + s <= 8 at every level
-  const int32_t vp1 = ap1 ? at_c(c + s) : 0;
-  if (cubic) {
-    const bool am3 = c - 3 * s >= 0;
-    const bool ap3 = c + 3 * s < 8 || (c + 3 * s == 8 && on_axis);
-    if (am3 && ap1 && ap3) {
-      const int32_t vm3 = at_c(c - 3 * s), vp3 = at_c(c + 3 * s);
-      return q - ((-vm3 + 9 * vm1 + 9 * vp1 - vp3 + 8) >> 4);
+// The interpolation stencil of every non-origin point p of a full block
+// (every in-block point is available, and a neighbour at coordinate 8 on the
+// pass axis is the corner anchor o + 8 e_a when the other two coordinates
+// are 0), one 16-byte entry per p, built once per CTA:
+//   x, y: the shared-tile offsets (relative to p, int16 pairs) of p - s, p + s
+//         and of p - 3s, p + 3s along the pass axis;
+//   z:    bits 0-1 the form with the cubic predictor (0: q[-s], 1: linear,
+//         2: cubic; the linear predictor takes at most 1), bit 8 / bit 9:
+//         p + s / p + 3s is the corner anchor, bits 16+: its index 1 << a.
+__device__ void build_interp_table(uint4 *tab) {
+  for (int p = threadIdx.x; p < 512; p += blockDim.x) {
+    const int px = p & 7, py = (p >> 3) & 7, pz = p >> 6;
+    uint4 e = make_uint4(0u, 0u, 0u, 0u);
+    if (p != 0) {
+      int s, a;
+      level_axis(px, py, pz, s, a);
+      const int c = a == 0 ? px : (a == 1 ? py : pz);
+      const bool on_axis = (a == 0 ? (py | pz) : (a == 1 ? (px | pz) : (px | py))) == 0;
+      const int d = a == 0 ? 1 : (a == 1 ? kTXP : 8 * kTXP);
+      const bool ap1 = c + s < 8 || on_axis;  // c + s <= 8 at every level
+      const bool am3 = c - 3 * s >= 0, ap3 = c + 3 * s < 8 || (c + 3 * s == 8 && on_axis);
+      const uint32_t form = (am3 && ap1 && ap3) ? 2u : (ap1 ? 1u : 0u);
+      auto pk = [](int lo, int hi) { return (uint32_t)(uint16_t)(int16_t)lo | ((uint32_t)(uint16_t)(int16_t)hi << 16); };
+      e.x = pk(-s * d, s * d);
+      e.y = pk(-3 * s * d, 3 * s * d);
+      e.z = form | (c + s == 8 ? 0x100u : 0u) | (c + 3 * s == 8 ? 0x200u : 0u) | ((uint32_t)(1 << a) << 16);
     }
+    tab[p] = e;
   }
-  return q - (ap1 ? (vm1 + vp1 + 1) >> 1 : vm1);
+}
+
+// Interpolation residual at a non-origin point of a full block, from its
+// stencil entry.
+__device__ __forceinline__ int32_t fb_interp(const BlockView &b, bool cubic, int px, int py, int pz) {
+  const uint4 e = b.itab[px + 8 * py + 64 * pz];
+  const int idx = (py + 8 * pz) * kTXP + 8 * b.wb + px;
+  const int32_t q = b.sq[idx];
+  const uint32_t form = e.z & 3u;
+  const int32_t vm1 = b.sq[idx + (int16_t)(e.x & 0xffffu)];  // c - s >= 0 at every level
+  if (form == 0) return q - vm1;
+  const int32_t vp1 = (e.z & 0x100u) ? b.cq[e.z >> 16] : b.sq[idx + (int16_t)(e.x >> 16)];
+  if (cubic && form == 2) {
+    const int32_t vm3 = b.sq[idx + (int16_t)(e.y & 0xffffu)];
+    const int32_t vp3 = (e.z & 0x200u) ? b.cq[e.z >> 16] : b.sq[idx + (int16_t)(e.y >> 16)];
+    return q - ((-vm3 + 9 * vm1 + 9 * vp1 - vp3 + 8) >> 4);
+  }
+  return q - ((vm1 + vp1 + 1) >> 1);
 }
 
 __device__ __forceinline__ unsigned long long warp_sum64(unsigned long long v) {
@@ -273,11 +333,144 @@ __device__ __forceinline__ float log2fix(unsigned long long s) {
   return __fadd_rn((float)e, (float)m * 0.0625f);
 }
 
+__device__ __forceinline__ uint32_t uabs32(int32_t v) { return (uint32_t)(v < 0 ? -v : v); }
+
+// Sum over the warp of 32 per-lane values at once: lane f ends with the sum
+// of everyone's v[f].  Five exchange steps; in each a lane keeps half of
+// its values, sends the other half to its partner and adds what it gets.
+__device__ __forceinline__ unsigned long long warp_transpose_sum(const uint32_t (&v)[32]) {
+  const int lane = threadIdx.x & 31;
+  unsigned long long w[16];
+  {
+    const bool up = (lane & 16) != 0;
+#pragma unroll
+    for (int k = 0; k < 16; ++k) {
+      const uint32_t send = up ? v[k] : v[k + 16], keep = up ? v[k + 16] : v[k];
+      w[k] = (unsigned long long)keep + __shfl_xor_sync(0xffffffffu, send, 16);
+    }
+  }
+#pragma unroll
+  for (int half = 8; half >= 1; half >>= 1) {
+    const bool up = (lane & half) != 0;
+#pragma unroll
+    for (int k = 0; k < half; ++k) {
+      const unsigned long long send = up ? w[k] : w[k + half], keep = up ? w[k + half] : w[k];
+      w[k] = keep + __shfl_xor_sync(0xffffffffu, send, half);
+    }
+  }
+  return w[0];
+}
+
+// The 32 statistics of a full block (every point in the domain, every
+// corner available), the same integers as the general path below: the block
+// is held in registers in the full-block layout (lane: x = lane & 7, rows
+// y0 = lane >> 3 and y0 + 4; register i: y = y0 + 4 (i & 1), z = i >> 1),
+// neighbours along x come by shuffles within the row's 8 lanes, along y by
+// shuffles from the lanes 8, 16, 24 apart (or, for the upper rows, from the
+// register of the lower row), along z from the registers two, four and six
+// back.  Per-lane sums stay in 32 bits (|q| < 2^23: 16 third differences stay
+// below 2^30); the warp sums are exact 64-bit sums.
+__device__ uint16_t fb_features(const BlockView &b, uint32_t R) {
+  const int lane = threadIdx.x & 31;
+  const int px = lane & 7, y0 = lane >> 3;
+  int32_t a[16];
+  fb_load(b, a);
+  uint32_t v[32];
+#pragma unroll
+  for (int f = 0; f < 32; ++f) v[f] = 0;
+  uint32_t mx[4] = {0, 0, 0, 0};
+  // predictor residuals on the all-odd points (two per lane)
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    const int o = lane + 32 * h;
+    const int ox = 2 * (o & 3) + 1, oy = 2 * ((o >> 2) & 3) + 1, oz = 2 * (o >> 4) + 1;
+    const uint32_t r[4] = {uabs32(res_lorenzo<1>(b, ox, oy, oz)), uabs32(res_lorenzo<2>(b, ox, oy, oz)),
+                           uabs32(fb_interp(b, false, ox, oy, oz)), uabs32(fb_interp(b, true, ox, oy, oz))};
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      v[2 * k] += r[k];
+      mx[k] = r[k] > mx[k] ? r[k] : mx[k];
+    }
+    v[25] += r[0] >= R ? 1u : 0u;
+  }
+  int32_t qmin = a[0], qmax = a[0], qsum = 0;  // 16 values below 2^23: the sum fits
+  int32_t qx1[16], qy1[16];
+#pragma unroll
+  for (int i = 0; i < 16; ++i) {
+    const int py = y0 + 4 * (i & 1), pz = i >> 1;
+    const int32_t q = a[i];
+    qsum += q;
+    qmin = q < qmin ? q : qmin;
+    qmax = q > qmax ? q : qmax;
+    // neighbours along x (lanes 1, 2, 3 back in the same row)
+    const int32_t x1 = __shfl_up_sync(0xffffffffu, q, 1), x2 = __shfl_up_sync(0xffffffffu, q, 2),
+                  x3 = __shfl_up_sync(0xffffffffu, q, 3);
+    // along y: rows y - 1, y - 2, y - 3
+    const int32_t u8 = __shfl_up_sync(0xffffffffu, q, 8), u16 = __shfl_up_sync(0xffffffffu, q, 16),
+                  u24 = __shfl_up_sync(0xffffffffu, q, 24);
+    int32_t y1 = u8, y2 = u16, y3 = u24;
+    if (i & 1) {  // upper row: rows below 4 are the lower row's register of the lanes 24, 16, 8 ahead
+      const int32_t d24 = __shfl_down_sync(0xffffffffu, a[i - 1], 24), d16 = __shfl_down_sync(0xffffffffu, a[i - 1], 16),
+                    d8 = __shfl_down_sync(0xffffffffu, a[i - 1], 8);
+      y1 = y0 >= 1 ? u8 : d24;
+      y2 = y0 >= 2 ? u16 : d16;
+      y3 = y0 >= 3 ? u24 : d8;
+    }
+    qx1[i] = x1;
+    qy1[i] = y1;
+    const int32_t z1 = i >= 2 ? a[i - 2] : 0, z2 = i >= 4 ? a[i - 4] : 0, z3 = i >= 6 ? a[i - 6] : 0;
+    const int32_t n1[3] = {x1, y1, z1}, n2[3] = {x2, y2, z2}, n3[3] = {x3, y3, z3};
+    const int c[3] = {px, py, pz};
+#pragma unroll
+    for (int ax = 0; ax < 3; ++ax) {
+      if (c[ax] >= 1) {
+        const int32_t d1 = q - n1[ax];
+        v[8 + ax] += uabs32(d1);
+        if (c[ax] >= 2) {
+          const int32_t d1p = n1[ax] - n2[ax];
+          v[11 + ax] += uabs32(d1 - d1p);
+          v[20 + ax] += ((d1 > 0 && d1p < 0) || (d1 < 0 && d1p > 0)) ? 1u : 0u;
+          if (c[ax] >= 3) v[14 + ax] += uabs32(d1 - 2 * d1p + (n2[ax] - n3[ax]));
+        }
+      }
+    }
+    // mixed differences: (x, y) with the x-neighbour's y-neighbour, (x, z)
+    // and (y, z) with the plane below's neighbours
+    const int32_t xy = __shfl_up_sync(0xffffffffu, y1, 1);
+    if (px >= 1 && py >= 1) v[17] += uabs32(q - x1 - y1 + xy);
+    if (px >= 1 && pz >= 1) v[18] += uabs32(q - x1 - z1 + qx1[i >= 2 ? i - 2 : 0]);
+    if (py >= 1 && pz >= 1) v[19] += uabs32(q - y1 - z1 + qy1[i >= 2 ? i - 2 : 0]);
+    if (px >= 2) v[31] += uabs32(q - x2);
+  }
+  // the block sum needs 64 bits: 32 lane sums below 2^27 each
+  long long tsum = (long long)qsum;
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) tsum += __shfl_xor_sync(0xffffffffu, tsum, off);
+  const long long mean = tsum >> 9;  // floor(sum / 512)
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[23] += (uint32_t)((long long)a[i] >= mean ? (long long)a[i] - mean : mean - (long long)a[i]);
+  unsigned long long st = warp_transpose_sum(v);
+  // maxima, spread and the constant statistics of a full block
+  const uint32_t m0 = __reduce_max_sync(0xffffffffu, mx[0]), m1 = __reduce_max_sync(0xffffffffu, mx[1]),
+                 m2 = __reduce_max_sync(0xffffffffu, mx[2]), m3 = __reduce_max_sync(0xffffffffu, mx[3]);
+  const int32_t gmax = __reduce_max_sync(0xffffffffu, qmax), gmin = __reduce_min_sync(0xffffffffu, qmin);
+  if (lane == 1) st = m0;
+  if (lane == 3) st = m1;
+  if (lane == 5) st = m2;
+  if (lane == 7) st = m3;
+  if (lane == 24) st = (unsigned long long)((long long)gmax - (long long)gmin);
+  if (lane >= 26 && lane <= 28) st = 1;  // the +x, +y, +z corners
+  if (lane == 29) st = 512;
+  if (lane == 30) st = uabs32(b.at(0, 0, 0));
+  return f32_to_bf16_rne(log2fix(st));
+}
+
 // The 32 block statistics (see the selector's definition: sums and maxima
 // of predictor residuals on the 64 all-odd points, difference sums, sign
 // changes, spread, corner availability, size, anchor) -> bfloat16 features.
 // Returns this lane's feature (lane f holds feature f).
 __device__ uint16_t block_feature(const BlockView &b, uint32_t R) {
+  if (full_block(b)) return fb_features(b, R);
   const int lane = threadIdx.x & 31;
   unsigned long long st[kNFeat];
 #pragma unroll
@@ -381,6 +574,16 @@ __device__ uint16_t block_feature(const BlockView &b, uint32_t R) {
   return f32_to_bf16_rne(log2fix(mine));
 }
 
+// The network's weights as the CTA keeps them in shared memory (binary32):
+// the stream order, except W1 and W2 transposed (W1t[k][j], W2t[j][i]) so
+// that the lanes of a warp, one per hidden unit or logit, read consecutive
+// words (the stored order puts them a row apart: one shared-memory bank).
+__device__ __forceinline__ int smem_weight_index(int i) {
+  if (i < kOffB1) return kOffW1 + (i % kNFeat) * kNHid + i / kNFeat;              // W1[j][k] -> W1t[k][j]
+  if (i >= kOffW2 && i < kOffB2) return kOffW2 + ((i - kOffW2) % kNHid) * kNPred + (i - kOffW2) / kNHid;
+  return i;
+}
+
 // Exact network inference: lane l computes hidden units l and l + 32,
 // lanes 0..3 the logits, each with fmaf in index order.  Returns the
 // argmax (ties to the lowest id) in every lane.
@@ -393,7 +596,7 @@ __device__ int mlp_choose(const float *w, uint16_t feat_lane) {
     const int j = lane + 32 * u;
     float acc = w[kOffB1 + j];
 #pragma unroll 8
-    for (int k = 0; k < kNFeat; ++k) acc = __fmaf_rn(w[kOffW1 + j * kNFeat + k], __shfl_sync(0xffffffffu, f, k), acc);
+    for (int k = 0; k < kNFeat; ++k) acc = __fmaf_rn(w[kOffW1 + k * kNHid + j], __shfl_sync(0xffffffffu, f, k), acc);
     acc = acc > 0.0f ? acc : 0.0f;
     h[u] = bf16_to_f32(f32_to_bf16_rne(acc));
   }
@@ -403,7 +606,7 @@ __device__ int mlp_choose(const float *w, uint16_t feat_lane) {
     float acc = w[kOffB2 + i];
     for (int j = 0; j < kNHid; ++j) {
       const float hj = __shfl_sync(0xffffffffu, h[j >> 5], j & 31);
-      acc = __fmaf_rn(w[kOffW2 + i * kNHid + j], hj, acc);
+      acc = __fmaf_rn(w[kOffW2 + j * kNPred + i], hj, acc);
     }
     lg = acc;
   }
@@ -434,6 +637,7 @@ struct SelSmem {
   uint32_t wout[8], wexc[8];
   uint32_t oslot, eslot;
   int pid[8];
+  uint4 itab[512];
 };
 
 template <int MODE>
@@ -447,8 +651,9 @@ __global__ void __launch_bounds__(kSelThreads, (MODE == kSelNet || MODE == kSelR
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const bool vec_ok = ((g.nx & 3u) == 0) && (((uintptr_t)x & 15u) == 0);
   for (int s = tid; s < kMaxSym; s += kSelThreads) sm.shist[s] = 0;
+  build_interp_table(sm.itab);
   if (MODE == kSelNet)
-    for (int i = tid; i < kNWeights; i += kSelThreads) sm.w[i] = bf16_to_f32(so.weights[i]);
+    for (int i = tid; i < kNWeights; i += kSelThreads) sm.w[smem_weight_index(i)] = bf16_to_f32(so.weights[i]);
   __syncthreads();
 
   for (uint64_t tile = blockIdx.x; tile < g.n_qtiles; tile += gridDim.x) {
@@ -510,6 +715,21 @@ __global__ void __launch_bounds__(kSelThreads, (MODE == kSelNet || MODE == kSelR
     b.xlim = g.nx - x0 - 8 * wb < 8 ? g.nx - x0 - 8 * wb : 8;
     b.ylim = g.ny - y0 < 8 ? g.ny - y0 : 8;
     b.zlim = g.nz - z0 < 8 ? g.nz - z0 : 8;
+    b.itab = sm.itab;
+    GiTile gt;
+    if (MODE == kSelGinterp) {
+      gt.x = x;
+      gt.sq = sm.sq;
+      gt.x0 = x0;
+      gt.y0 = y0;
+      gt.z0 = z0;
+      gt.nx = g.nx;
+      gt.ny = g.ny;
+      gt.nz = g.nz;
+      gt.inv2eb = inv2eb;
+      gt.ebx2 = ebx2;
+      gt.eb_chk = eb_chk;
+    }
     uint32_t nout = 0, nexc = 0;
     if (bvalid) {
       int pid = (int)fixed_pid;
@@ -550,8 +770,11 @@ __global__ void __launch_bounds__(kSelThreads, (MODE == kSelNet || MODE == kSelR
           uint32_t code = R;
           if (!fl) ra[i] = 0;
           if (in) {
-            const int32_t d = fl ? ra[i]
-                                 : (full && p != 0 ? fb_interp(b, pid == 3, px, py, pz) : residual(b, pid, px, py, pz));
+            int32_t d;
+            if (MODE == kSelGinterp)
+              d = p == 0 ? b.at(0, 0, 0) : gi_residual(gt, px, py, pz, gt.x0 + 8 * wb + px, y0 + py, z0 + pz);
+            else
+              d = fl ? ra[i] : (full && p != 0 ? fb_interp(b, pid == 3, px, py, pz) : residual(b, pid, px, py, pz));
             ra[i] = d;
             if (p == 0) ws.anchors[blk] = d;
             else {
@@ -563,15 +786,22 @@ __global__ void __launch_bounds__(kSelThreads, (MODE == kSelNet || MODE == kSelR
             nexc += sm.sexc[(py + 8 * pz) * kTX + 8 * wb + px] ? 1u : 0u;
           }
           cdst[p] = (uint16_t)code;
-          atomicAdd(&sm.shist[code], 1u);
+          // one shared atomic per distinct code of the warp (smooth blocks
+          // give most lanes the same code)
+          const uint32_t peers = __match_any_sync(0xffffffffu, code);
+          if (lane == __ffs(peers) - 1) atomicAdd(&sm.shist[code], (uint32_t)__popc(peers));
         }
         // the block's residuals replace its q in the shared tile (only this warp
-        // reads them), for the outlier compaction below
-        __syncwarp();
+        // reads them), for the outlier compaction below; the full-field
+        // interpolation reads the q of neighbouring blocks in the tile, so it
+        // keeps q and the compaction recomputes its residuals
+        if (MODE != kSelGinterp) {
+          __syncwarp();
 #pragma unroll
-        for (int i = 0; i < 16; ++i) {
-          const int p = 32 * i + lane;
-          sm.sq[(((p >> 3) & 7) + 8 * (p >> 6)) * kTXP + 8 * wb + (p & 7)] = ra[i];
+          for (int i = 0; i < 16; ++i) {
+            const int p = 32 * i + lane;
+            sm.sq[(((p >> 3) & 7) + 8 * (p >> 6)) * kTXP + 8 * wb + (p & 7)] = ra[i];
+          }
         }
       }
     }
@@ -616,7 +846,8 @@ __global__ void __launch_bounds__(kSelThreads, (MODE == kSelNet || MODE == kSelR
           int32_t d = 0;
           bool outl = false;
           if (in && p != 0) {
-            d = b.at(px, py, pz);  // the residual, stored by the code pass
+            if (MODE == kSelGinterp) d = gi_residual(gt, px, py, pz, gt.x0 + 8 * wb + px, y0 + py, z0 + pz);
+            else d = b.at(px, py, pz);  // the residual, stored by the code pass
             const uint32_t c = (uint32_t)(d + (int32_t)R);
             outl = (c - 1u) >= 2u * R - 1u;
           }
@@ -667,6 +898,12 @@ struct SelDecParams {
   const uint16_t *lut;
   uint16_t *codes;
   uint32_t *err;            // err[0] error word, err[1] work-unit counter
+  // optional (OV): the residual of every outlier written at its position
+  const uint32_t *ofirst;   // per block with outliers: index of its first outlier (others ~0)
+  const uint32_t *out_idx;
+  const int32_t *out_val;
+  uint64_t n_out;
+  int32_t *ovals;
 };
 
 __device__ __forceinline__ void sel_err(uint32_t *err, uint32_t code) { atomicCAS(err, 0u, code); }
@@ -675,6 +912,14 @@ constexpr int kSelDecThreads = 768;
 
 // Phase 1: one thread per chunk (= block), codes written row by row; warps
 // take work units of 32 chunks from a counter.
+// With OV, the r-th outlier code (0) of a block takes entry r of the
+// block's run of the outlier list (from the block's first entry on) and
+// its residual goes to ovals at the code's position; the outlier codes are
+// counted in err[3].  The list is checked elsewhere to ascend strictly and
+// to name only outlier codes; with as many entries as outlier codes, it is
+// then exactly the outlier codes in order, and every match made here is
+// right.
+template <bool OV>
 __global__ void __launch_bounds__(kSelDecThreads, 1) k_dec_codes(SelDecParams p) {
   constexpr int T = kSelDecThreads;
   extern __shared__ __align__(16) unsigned char dc_smem[];
@@ -698,15 +943,31 @@ __global__ void __launch_bounds__(kSelDecThreads, 1) k_dec_codes(SelDecParams p)
     br.init(p.words, p.n_words, start, cb, sring + t);
     const uint32_t start_off = br.off;
     uint4 *dst = reinterpret_cast<uint4 *>(p.codes + j * 512);
+    uint64_t oc = ~0ull;  // next outlier entry of this block (located at its first outlier)
+    uint32_t nzero = 0;
+    bool bad = false;
 #pragma unroll 1
     for (int r = 0; r < 64; ++r) {
       uint32_t c[8];
 #pragma unroll
       for (int u2 = 0; u2 < 4; ++u2) br.next2(slut, c[2 * u2], c[2 * u2 + 1]);
       dst[r] = make_uint4(c[0] | (c[1] << 16), c[2] | (c[3] << 16), c[4] | (c[5] << 16), c[6] | (c[7] << 16));
+      if (OV && (c[0] == 0 || c[1] == 0 || c[2] == 0 || c[3] == 0 || c[4] == 0 || c[5] == 0 || c[6] == 0 ||
+                 c[7] == 0)) {
+        if (oc == ~0ull) oc = __ldg(p.ofirst + j);  // ~0 for a block without outliers: out of the list
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+          if (c[k] != 0) continue;
+          if (oc < p.n_out) p.ovals[j * 512u + (uint64_t)(8 * r + k)] = __ldg(p.out_val + oc);
+          else bad = true;
+          ++oc;
+          ++nzero;
+        }
+      }
     }
     asm volatile("cp.async.wait_all;\n" ::: "memory");
-    if (br.consumed(start_off) != cb) sel_err(p.err, FZ_ECORRUPT);
+    if (OV && nzero) atomicAdd(p.err + 3, nzero);
+    if (br.consumed(start_off) != cb || bad) sel_err(p.err, FZ_ECORRUPT);
   }
 }
 
@@ -738,11 +999,54 @@ __device__ __forceinline__ uint64_t lb_u32(const uint32_t *a, uint64_t n, uint32
 constexpr int kReconWarps = 8;
 
 // Phase 2: one warp per block.  The block's q is rebuilt in shared memory.
+// First point of each interpolation pass (levels 4, 2, 1; axes x, y, z) in
+// the pass-ordered point list: a pass of level s along axis a holds
+// (8 / 2s) (8 / s)^a (8 / 2s)^(2 - a) points.
+__constant__ uint16_t kPassStart[10] = {0, 1, 3, 7, 15, 31, 63, 127, 255, 511};
+
+// The pass-ordered point list of an 8x8x8 block (each pass's points in
+// raster order: slot = the pass's start + the point's rank on the pass's
+// lattice) and every non-origin point's stencil in the block layout (the
+// entry format of build_interp_table, offsets with strides 1, 8, 64).
+__device__ void build_recon_tables(uint16_t *list, uint4 *tab) {
+  for (int p = threadIdx.x; p < 512; p += blockDim.x) {
+    const int c[3] = {p & 7, (p >> 3) & 7, p >> 6};
+    uint4 e = make_uint4(0u, 0u, 0u, 0u);
+    if (p != 0) {
+      int s, a;
+      level_axis(c[0], c[1], c[2], s, a);
+      const bool on_axis = (a == 0 ? (c[1] | c[2]) : (a == 1 ? (c[0] | c[2]) : (c[0] | c[1]))) == 0;
+      const int d = a == 0 ? 1 : (a == 1 ? 8 : 64);
+      const int ca = c[a];
+      const bool ap1 = ca + s < 8 || on_axis;
+      const bool am3 = ca - 3 * s >= 0, ap3 = ca + 3 * s < 8 || (ca + 3 * s == 8 && on_axis);
+      const uint32_t form = (am3 && ap1 && ap3) ? 2u : (ap1 ? 1u : 0u);
+      auto pk = [](int lo, int hi) { return (uint32_t)(uint16_t)(int16_t)lo | ((uint32_t)(uint16_t)(int16_t)hi << 16); };
+      e.x = pk(-s * d, s * d);
+      e.y = pk(-3 * s * d, 3 * s * d);
+      e.z = form | (ca + s == 8 ? 0x100u : 0u) | (ca + 3 * s == 8 ? 0x200u : 0u) | ((uint32_t)(1 << a) << 16);
+      // rank on the pass's lattice: per axis the coordinate's index and count
+      int rank = 0;
+      for (int b = 2; b >= 0; --b) {
+        const int step = b == a ? 2 * s : (b < a ? s : 2 * s), first = b == a ? s : 0;
+        rank = rank * (8 / step) + (c[b] - first) / step;
+      }
+      const int li = s == 4 ? 0 : (s == 2 ? 1 : 2);
+      list[kPassStart[3 * li + a] + rank] = (uint16_t)p;
+    }
+    tab[p] = e;
+  }
+}
+
 __global__ void __launch_bounds__(kReconWarps * 32) k_sel_recon(ReconParams rp, Geom g) {
   __shared__ int32_t sq[kReconWarps][512];
   __shared__ int32_t scq[kReconWarps][8];
   __shared__ uint32_t sov[kReconWarps][512];
   __shared__ uint32_t smask[kReconWarps][16];
+  __shared__ uint16_t rlist[512];
+  __shared__ uint4 rtab[512];
+  build_recon_tables(rlist, rtab);
+  __syncthreads();
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const uint64_t nwarps = (uint64_t)gridDim.x * kReconWarps;
   for (uint64_t blk = (uint64_t)blockIdx.x * kReconWarps + w; blk < g.n_blocks; blk += nwarps) {
@@ -791,6 +1095,7 @@ __global__ void __launch_bounds__(kReconWarps * 32) k_sel_recon(ReconParams rp, 
     __syncwarp();
     BlockView b;
     b.sq = nullptr;
+    b.itab = nullptr;
     b.cq = scq[w];
     b.cin = cin;
     b.wb = 0;
@@ -818,6 +1123,33 @@ __global__ void __launch_bounds__(kReconWarps * 32) k_sel_recon(ReconParams rp, 
           }
           __syncwarp();
         }
+      }
+    } else if (xl == 8 && yl == 8 && zl == 8 && cin == 0xffu) {
+      // interpolation of a full block: the passes' points from the list,
+      // each from its stencil entry (every in-block point is available)
+      const bool cubic = pid == 3;
+      for (int pass = 0; pass < 9; ++pass) {
+        for (int k = kPassStart[pass] + lane; k < kPassStart[pass + 1]; k += 32) {
+          const int p = rlist[k];
+          const uint4 e = rtab[p];
+          const uint32_t form = e.z & 3u;
+          const int32_t vm1 = sq[w][p + (int16_t)(e.x & 0xffffu)];
+          int32_t pred = vm1;
+          if (form != 0) {
+            const int32_t vp1 = (e.z & 0x100u) ? scq[w][e.z >> 16] : sq[w][p + (int16_t)(e.x >> 16)];
+            // 32-bit wrapping arithmetic: exact for every stream the
+            // compressor writes (|q| < 2^23), harmless for a damaged one
+            if (cubic && form == 2) {
+              const int32_t vm3 = sq[w][p + (int16_t)(e.y & 0xffffu)];
+              const int32_t vp3 = (e.z & 0x200u) ? scq[w][e.z >> 16] : sq[w][p + (int16_t)(e.y >> 16)];
+              pred = (int32_t)(9u * ((uint32_t)vm1 + (uint32_t)vp1) - (uint32_t)vm3 - (uint32_t)vp3 + 8u) >> 4;
+            } else {
+              pred = (int32_t)((uint32_t)vm1 + (uint32_t)vp1 + 1u) >> 1;
+            }
+          }
+          sq[w][p] = (int32_t)((uint32_t)sq[w][p] + (uint32_t)pred);
+        }
+        __syncwarp();
       }
     } else {
       // interpolation: passes in order, each pass's points are independent
@@ -902,6 +1234,7 @@ cudaError_t launch_selquant(const float *x, const Geom &g, uint32_t R, uint32_t 
   switch (pred) {
     case FZ_SEL_MLP: return launch_sel_t<kSelNet>(x, g, R, 0, ws, so, s, sm_count);
     case FZ_SEL_EXHAUSTIVE: return launch_sel_t<kSelExhaustive>(x, g, R, 0, ws, so, s, sm_count);
+    case FZ_PRED_GINTERP: return launch_sel_t<kSelGinterp>(x, g, R, pred, ws, so, s, sm_count);
     default: return launch_sel_t<kSelFixed>(x, g, R, pred, ws, so, s, sm_count);
   }
 }
@@ -915,11 +1248,14 @@ cudaError_t launch_select_report(const float *x, const Geom &g, uint32_t R, cons
   return launch_sel_t<kSelReport>(x, g, R, 0, ws, so, s, sm_count);
 }
 
-cudaError_t launch_sel_decode(const uint8_t *d_in, const fz_header &h, float *d_out, const DecodeWs &ws,
-                              uint16_t *codes, cudaStream_t s, int sm_count) {
-  Geom g;
-  make_geom(h.ndim, h.dims, g);
+cudaError_t launch_dec_codes(const uint8_t *d_in, const fz_header &h, const DecodeWs &ws, uint16_t *codes,
+                             int32_t *ovals, cudaStream_t s, int sm_count) {
   SelDecParams p;
+  p.ofirst = ws.ofirst;
+  p.out_idx = reinterpret_cast<const uint32_t *>(d_in + h.off_out_idx);
+  p.out_val = reinterpret_cast<const int32_t *>(d_in + h.off_out_val);
+  p.n_out = h.n_out;
+  p.ovals = ovals;
   p.words = reinterpret_cast<const uint32_t *>(d_in + h.off_bits);
   p.n_words = (h.total_bits + 31) / 32;
   p.chunk_bits = reinterpret_cast<const uint32_t *>(d_in + h.off_chunk_bits);
@@ -930,12 +1266,23 @@ cudaError_t launch_sel_decode(const uint8_t *d_in, const fz_header &h, float *d_
   p.codes = codes;
   p.err = ws.err;
   const int smem = (int)(sizeof(uint16_t) * kLutSize + sizeof(uint32_t) * kRing * kSelDecThreads);
-  cudaError_t e = cudaFuncSetAttribute(k_dec_codes, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  const bool ov = ovals != nullptr;
+  cudaError_t e = cudaFuncSetAttribute(ov ? k_dec_codes<true> : k_dec_codes<false>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;
   uint64_t grid = (uint64_t)sm_count;
   if (grid > p.n_units) grid = p.n_units;
-  k_dec_codes<<<(unsigned)grid, kSelDecThreads, smem, s>>>(p);
-  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  if (ov) k_dec_codes<true><<<(unsigned)grid, kSelDecThreads, smem, s>>>(p);
+  else k_dec_codes<false><<<(unsigned)grid, kSelDecThreads, smem, s>>>(p);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sel_decode(const uint8_t *d_in, const fz_header &h, float *d_out, const DecodeWs &ws,
+                              uint16_t *codes, cudaStream_t s, int sm_count) {
+  Geom g;
+  make_geom(h.ndim, h.dims, g);
+  cudaError_t e = launch_dec_codes(d_in, h, ws, codes, nullptr, s, sm_count);
+  if (e != cudaSuccess) return e;
   ReconParams rp;
   rp.codes = codes;
   rp.anchors = reinterpret_cast<const int32_t *>(d_in + h.off_anchors);

@@ -118,6 +118,45 @@ def test_stream_check_rejects_wrapping_offsets(fzlib):
     assert fzlib.fz_stream_check(None, 4096) == 1
 
 
+def test_stream_check_rejects_positions_beyond_32_bits(fzlib):
+    """A Huffman stream of a field whose padded code stream would need
+    positions of 2^32 or more (the format's outlier and exception indices are
+    32-bit) is rejected; the same extents are fine for a raw stream."""
+    import paper_2509_20563_gb300 as fz
+    import synth
+    x = synth.smooth_nd((20, 30, 40), 1).numpy()
+    hdr = oracle.compress(x, 1e-3).tobytes()[:256]
+
+    def consistent(dims):
+        # a header whose sections are laid out for `dims` (no outliers or
+        # exceptions, one bit per code); the check reads nothing past it
+        nb = 1
+        for d in dims:
+            nb *= -(-d // 8)
+        a16 = lambda v: (v + 15) // 16 * 16
+        tb = nb * 512
+        o_anch = a16(256 + 1024)
+        o_cb = a16(o_anch + 4 * nb)
+        o_oi = a16(o_cb + 4 * nb)
+        o_bits = o_oi
+        total = a16(o_bits + 4 * (-(-tb // 32)))
+        h = hdr
+        for off, v in ((16, dims[0]), (24, dims[1]), (32, dims[2]), (96, nb), (104, nb), (112, 0), (120, 0),
+                       (128, tb), (136, 256), (144, 0), (152, o_anch), (160, o_cb), (168, o_oi), (176, o_oi),
+                       (184, o_oi), (192, o_oi), (200, o_bits), (208, total)):
+            h = _hdr_u64(h, off, v)
+        return h, total
+    h, total = consistent((20, 30, 40))
+    assert fz.stream_check(h, total) == 0
+    # 1620 x 1620 x 1630 has fewer than 2^32 values, its 8x8x8 blocks
+    # (1624 x 1624 x 1632) more than 2^32 code positions
+    assert 1620 * 1620 * 1630 < (1 << 32) < 1624 * 1624 * 1632
+    h, total = consistent((1620, 1620, 1630))
+    assert fz.stream_check(h, total) == 5
+    h, total = consistent((1600, 1600, 1600))
+    assert fz.stream_check(h, total) == 0
+
+
 def test_struct_layout_matches_header(tmp_path):
     """The ctypes mirror of fz_pipeline and the documented fz_header offsets
     agree with what a C compiler makes of include/fz.h."""
