@@ -485,13 +485,14 @@ fz_status fz_decompress(fz_ctx *ctx, const void *d_in, uint64_t in_bytes, const 
   size_t off = 0;
   auto take = [&](size_t bytes) { size_t o = off; off += up(bytes); return o; };
   const bool selpath = h.predictor > FZ_PRED_LORENZO2;
-  // a per-block first-outlier table pays off when most blocks hold outliers
-  // plane-parallel streams (64-symbol chunks) and bit-shuffle streams locate
-  // outliers per plane or chunk
-  // the full-field interpolation decoder always takes it (its code decoder
-  // matches every outlier code to the list through it)
+  // The per-block first-outlier table: the full-field interpolation decoder
+  // always takes it (its code decoder matches every outlier code to the list
+  // through it), the per-block predictor decoder whenever there are
+  // outliers; for Lorenzo streams it pays off when most blocks hold outliers
+  // (plane-parallel streams with 64-symbol chunks and bit-shuffle streams
+  // locate outliers per plane or chunk instead).
   const bool gipath = h.predictor == FZ_PRED_GINTERP;
-  const bool ofirst = gipath || (!selpath && h.n_out > h.n_blocks / 8 &&
+  const bool ofirst = gipath || (selpath && h.n_out) || (!selpath && h.n_out > h.n_blocks / 8 &&
                                              !(h.ndim == 3 && h.chunk == 64) && h.flags != FZ_FLAG_SHUF);
   const size_t o_err = take(dec_offset_zero_bytes(h)), o_gsum = take(8 * n_units), o_lut = take(2u << kLutBits),
                o_codes = selpath ? take(2 * g.npad) : 0, o_ofirst = ofirst ? take(4 * h.n_blocks) : 0,

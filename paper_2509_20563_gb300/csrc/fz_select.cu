@@ -786,10 +786,7 @@ __global__ void __launch_bounds__(kSelThreads, (MODE == kSelNet || MODE == kSelR
             nexc += sm.sexc[(py + 8 * pz) * kTX + 8 * wb + px] ? 1u : 0u;
           }
           cdst[p] = (uint16_t)code;
-          // one shared atomic per distinct code of the warp (smooth blocks
-          // give most lanes the same code)
-          const uint32_t peers = __match_any_sync(0xffffffffu, code);
-          if (lane == __ffs(peers) - 1) atomicAdd(&sm.shist[code], (uint32_t)__popc(peers));
+          atomicAdd(&sm.shist[code], 1u);
         }
         // the block's residuals replace its q in the shared tile (only this warp
         // reads them), for the outlier compaction below; the full-field
@@ -981,6 +978,7 @@ struct ReconParams {
   const uint32_t *exc_idx;
   const uint32_t *exc_val;
   uint64_t n_out, n_exc;
+  const uint32_t *ofirst;     // per block with outliers: index of its first outlier (others ~0); n_out > 0
   float *out;
   float ebx2;
   int32_t R;
@@ -1070,9 +1068,10 @@ __global__ void __launch_bounds__(kReconWarps * 32) k_sel_recon(ReconParams rp, 
       cin = __ballot_sync(0xffffffffu, lane < 8 && cx < g.nbx && cy < g.nby && cz < g.nbz) & 0xffu;
     }
     // residuals, with outliers scattered in position order
+    // the block's first outlier from the per-block table (~0: none, so an
+    // outlier code there finds no entry and is reported)
     uint64_t obase = 0;
-    if (lane == 0 && rp.n_out) obase = lb_u32(rp.out_idx, rp.n_out, pos0);
-    obase = __shfl_sync(0xffffffffu, obase, 0);
+    if (rp.n_out) obase = __ldg(rp.ofirst + blk);
     bool bad = false;
     uint32_t orank = 0;
     for (int i = 0; i < 16; ++i) {
@@ -1294,6 +1293,7 @@ cudaError_t launch_sel_decode(const uint8_t *d_in, const fz_header &h, float *d_
   rp.exc_val = reinterpret_cast<const uint32_t *>(d_in + h.off_exc_val);
   rp.n_out = h.n_out;
   rp.n_exc = h.n_exc;
+  rp.ofirst = ws.ofirst;
   rp.out = d_out;
   memcpy(&rp.ebx2, &h.ebx2_bits, 4);
   rp.R = (int32_t)h.radius;
