@@ -22,7 +22,7 @@ struct CbSmem {
   unsigned long long lw[kMaxSym];          // sorted leaf weights
   unsigned long long S[2][2 * kMaxSym];    // items of the current / next level
   unsigned long long pk[kMaxSym];          // packages of the current level
-  uint32_t flags[kLmax + 1][2 * kMaxSym / 32];  // per level: is-leaf bit per item
+  uint8_t leaf[kLmax + 1][2 * kMaxSym];      // per level and merged item: 1 for a leaf, 0 for a package
   uint32_t a[kLmax + 1];                   // selected leaves per level
   uint16_t lsym[kMaxSym];                  // sorted leaf symbols
   uint8_t len[kMaxSym];
@@ -88,10 +88,13 @@ __device__ bool build_codebook(CbSmem &s, uint32_t nsym, uint32_t *code_out, uin
     __syncthreads();
   } else {
     // ---- 2. package-merge, level kLmax (leaves only) down to level 1
-    for (int i = t; i < (kLmax + 1) * (2 * kMaxSym / 32); i += kCbThreads) (&s.flags[0][0])[i] = 0;
+    // (the flags are plain byte stores: every merged position of a level is
+    // written once, by its leaf or its package)
+    for (int i = t; i < (kLmax + 1) * (2 * kMaxSym) / 4; i += kCbThreads)
+      reinterpret_cast<uint32_t *>(&s.leaf[0][0])[i] = 0u;
     if ((uint32_t)t < m) s.S[0][t] = s.lw[t];
     __syncthreads();
-    if ((uint32_t)t < m) atomicOr(&s.flags[kLmax][t >> 5], 1u << (t & 31));
+    if ((uint32_t)t < m) s.leaf[kLmax][t] = 1;
     uint32_t n_cur = m;
     int cb = 0;
     for (int l = kLmax - 1; l >= 1; --l) {
@@ -101,7 +104,7 @@ __device__ bool build_codebook(CbSmem &s, uint32_t nsym, uint32_t *code_out, uin
       if ((uint32_t)t < m) {
         const uint32_t pos = (uint32_t)t + rank_of(s.pk, np, s.lw[t], true);
         s.S[cb ^ 1][pos] = s.lw[t];
-        atomicOr(&s.flags[l][pos >> 5], 1u << (pos & 31));
+        s.leaf[l][pos] = 1;
       }
       if ((uint32_t)t < np) {
         const uint32_t pos = (uint32_t)t + rank_of(s.lw, m, s.pk[t], false);
@@ -111,20 +114,15 @@ __device__ bool build_codebook(CbSmem &s, uint32_t nsym, uint32_t *code_out, uin
       n_cur = m + np;
       cb ^= 1;
     }
-    // ---- 3. selection: 2m-2 items at level 1; a_l leaves per level
-    if (t < 32) {
+    // ---- 3. selection: 2m-2 items at level 1; a_l leaves per level, counted
+    // by the whole CTA (thread t: items 2t and 2t + 1 of the level)
+    {
       uint32_t sel = 2 * m - 2;
       for (int l = 1; l <= kLmax; ++l) {
-        uint32_t c = 0;
-        for (int w = lane; w < 2 * kMaxSym / 32; w += 32) {
-          const uint32_t lo = (uint32_t)w * 32;
-          if (lo >= sel) break;
-          uint32_t bits = s.flags[l][w];
-          if (sel - lo < 32) bits &= (1u << (sel - lo)) - 1u;
-          c += __popc(bits);
-        }
-        c = __reduce_add_sync(0xffffffffu, c);
-        if (lane == 0) s.a[l] = c;
+        const uint32_t i0 = 2u * (uint32_t)t;
+        const uint32_t c = (uint32_t)__syncthreads_count(i0 < sel && s.leaf[l][i0]) +
+                           (uint32_t)__syncthreads_count(i0 + 1 < sel && s.leaf[l][i0 + 1]);
+        if (t == 0) s.a[l] = c;
         sel = 2 * (sel - c);
       }
     }
