@@ -73,12 +73,26 @@ __global__ void __launch_bounds__(kHiThreads) k_hist_sample(const uint16_t *__re
   extern __shared__ uint32_t hs[];  // nsym
   for (uint32_t i = threadIdx.x; i < nsym; i += kHiThreads) hs[i] = 0;
   __syncthreads();
-  const uint64_t span = n > kSampleWindow ? (n - kSampleWindow) / (kSampleWindows - 1) : 0;
-  for (uint32_t i = threadIdx.x; i < kSampleWindows * kSampleWindow; i += kHiThreads) {
-    const uint64_t pos = (uint64_t)(i / kSampleWindow) * span + (i % kSampleWindow);
-    if (pos >= n) continue;
-    const uint32_t a = codes[pos];
-    if (a < nsym) atomicAdd(hs + a, 1u);
+  // window starts at multiples of 8 codes (16-byte aligned: the array is),
+  // each thread's 32 loads of 8 codes issued before any is counted
+  const uint64_t span = n > kSampleWindow ? ((n - kSampleWindow) / (kSampleWindows - 1)) & ~7ull : 0;
+  constexpr int kPer = kSampleWindows * kSampleWindow / 8 / kHiThreads;  // uint4 loads per thread
+  const uint4 *c4 = reinterpret_cast<const uint4 *>(codes);
+  uint4 v[kPer];
+#pragma unroll
+  for (int k = 0; k < kPer; ++k) {
+    const uint32_t i = threadIdx.x + k * kHiThreads;  // uint4 index within the sample
+    const uint64_t pos = (uint64_t)(i / (kSampleWindow / 8)) * span + 8ull * (i % (kSampleWindow / 8));
+    v[k] = pos + 8 <= n ? __ldg(c4 + pos / 8) : make_uint4(0xffffffffu, 0xffffffffu, 0xffffffffu, 0xffffffffu);
+  }
+#pragma unroll
+  for (int k = 0; k < kPer; ++k) {
+    const uint32_t ww[4] = {v[k].x, v[k].y, v[k].z, v[k].w};
+#pragma unroll
+    for (int h = 0; h < 8; ++h) {
+      const uint32_t a = (ww[h >> 1] >> (16 * (h & 1))) & 0xffffu;
+      if (a < nsym) atomicAdd(hs + a, 1u);
+    }
   }
   __syncthreads();
   if (threadIdx.x < 32) {  // one warp picks the top 16 by repeated arg-max
