@@ -59,7 +59,9 @@ KERNEL_SOURCES = {
     "encode": ["fz_encode.cu", "fz_internal.cuh"],
     "decode": ["fz_decode.cu", "fz_decode_common.cuh", "fz_internal.cuh"],
 }
-NCU_DRAM_BYTES_512 = {}  # kernel -> (bytes per launch, source digest, commit)
+# kernel -> (dram__bytes_read.sum + dram__bytes_write.sum of one launch at 512^3, digest of the kernel's
+# sources when captured, commit): one-pass ncu capture of the bench's own first decoder launch
+NCU_DRAM_BYTES_512 = {"decode": (232049408 + 477818112, "1b73267f98e957ae", "d43f7c2")}
 METRIC = "compress/decompress GB/s vs HBM peak at REL 1e-4; CR learned vs plain"
 
 

@@ -255,11 +255,19 @@ __global__ void __launch_bounds__(kEncThreads) k_encode_batch(const BatchJob *__
 #ifndef FZ_ENC_DEPTH
 #define FZ_ENC_DEPTH 2
 #endif
+// FZ_ENC_ZB: one image more than the depth, and the image stored in one step
+// is cleared in the next (the barrier at the end of a step orders the
+// clearing after its reads and before its next use), which saves the
+// barrier between storing an image and clearing it
+#ifndef FZ_ENC_ZB
+#define FZ_ENC_ZB 0
+#endif
 template <int CH, int D>
 struct PipeSmem {
   static constexpr int kMaxWords = EncSmem<CH>::kMaxWords;
+  static constexpr int kImages = D + (FZ_ENC_ZB ? 1 : 0);
   uint32_t senc[kMaxSym];
-  __align__(16) uint32_t lw[D][kMaxWords];
+  __align__(16) uint32_t lw[kImages][kMaxWords];
   uint32_t wtot[kEncWarps];
   uint32_t tk[2];  // tickets: the current tile and the next one
   unsigned long long base;
@@ -292,7 +300,9 @@ __global__ void __launch_bounds__(kEncThreads, CH == 512 ? FZ_ENC_MINB : FZ_ENC_
   const uint64_t n_tiles = (n_blk + kEncWarps - 1) / kEncWarps;
   const uint64_t wlimit = (ctl->total_bits + 31) / 32;
   for (int i = tid; i < kMaxSym; i += kEncThreads) sm.senc[i] = ctl->enc[i];
-  for (int i = tid; i < D * PipeSmem<CH, D>::kMaxWords; i += kEncThreads) (&sm.lw[0][0])[i] = 0;
+  constexpr int NI = PipeSmem<CH, D>::kImages;
+  for (int i = tid; i < NI * PipeSmem<CH, D>::kMaxWords; i += kEncThreads) (&sm.lw[0][0])[i] = 0;
+  uint32_t stored_bits = 0;  // bits of the tile stored in the previous step (FZ_ENC_ZB)
   if (tid == 0) sm.tk[0] = atomicAdd(&ctl->encode_ticket, 1u);
   __syncthreads();
   uint64_t tile = sm.tk[0];
@@ -304,12 +314,18 @@ __global__ void __launch_bounds__(kEncThreads, CH == 512 ? FZ_ENC_MINB : FZ_ENC_
   uint32_t pend_bits[D - 1];
 #pragma unroll
   for (int i = 0; i < D - 1; ++i) { pend[i] = ~0ull; pend_bits[i] = 0; }
-  int cb = 0;  // image of the current tile; the oldest pending tile's is (cb + 1) % D
+  int cb = 0;  // image of the current tile; the oldest pending tile's is (cb + NI - (D - 1)) % NI
   int tb = 0;  // ticket slot of the current tile
   for (;;) {
     const bool have = tile < n_tiles;
     uint32_t tbits = 0;
     uint32_t *lw = sm.lw[cb];
+    if (FZ_ENC_ZB) {
+      // the image stored in the previous step is the next step's packing image
+      uint32_t *z = sm.lw[(cb + 1) % NI];
+      const uint32_t nz = stored_bits ? (stored_bits + 32 + 31) / 32 + 1 : 0u;
+      for (uint32_t w = tid; w < nz; w += kEncThreads) z[w] = 0;
+    }
     const uint64_t blk = tile * kEncWarps + warp;
     const bool valid = have && blk < n_blk;
     if (tid == 0 && have) sm.tk[tb ^ 1] = atomicAdd(&ctl->encode_ticket, 1u);
@@ -407,7 +423,7 @@ __global__ void __launch_bounds__(kEncThreads, CH == 512 ? FZ_ENC_MINB : FZ_ENC_
     // ---- the oldest pending tile: its base by look-back, then its words
     const uint64_t prev = pend[0];
     const uint32_t prev_bits = pend_bits[0];
-    const int pcb = (cb + 1) % D;
+    const int pcb = (cb + NI - (D - 1)) % NI;
     if (prev != ~0ull && warp == 0) {
       const unsigned long long base = lookback_resolve_warp(ws.estatus, prev, prev_bits, &ctl->res.err, ws.spin);
       if (lane == 0) {
@@ -427,11 +443,14 @@ __global__ void __launch_bounds__(kEncThreads, CH == 512 ? FZ_ENC_MINB : FZ_ENC_
         const uint32_t v = r ? ((plw[j - 1] << (32 - r)) | (plw[j] >> r)) : plw[j];
         if (gw0 + j < wlimit) words[gw0 + j] = v;
       }
-      __syncthreads();  // every word of the previous image has been read
-      uint32_t *z = sm.lw[pcb];
-      const uint32_t nz = (prev_bits + 32 + 31) / 32 + 1;
-      for (uint32_t w = tid; w < nz; w += kEncThreads) z[w] = 0;
+      if (!FZ_ENC_ZB) {
+        __syncthreads();  // every word of the previous image has been read
+        uint32_t *z = sm.lw[pcb];
+        const uint32_t nz = (prev_bits + 32 + 31) / 32 + 1;
+        for (uint32_t w = tid; w < nz; w += kEncThreads) z[w] = 0;
+      }
     }
+    stored_bits = prev != ~0ull ? prev_bits : 0u;
     // shift the pending queue; after the last tile, drain what is left
 #pragma unroll
     for (int i = 0; i < D - 2; ++i) { pend[i] = pend[i + 1]; pend_bits[i] = pend_bits[i + 1]; }
@@ -445,7 +464,7 @@ __global__ void __launch_bounds__(kEncThreads, CH == 512 ? FZ_ENC_MINB : FZ_ENC_
       tile = next;
       tb ^= 1;
     }
-    cb = (cb + 1) % D;
+    cb = (cb + 1) % NI;
     __syncthreads();  // the cleared image is ready for the next tile
   }
 }
