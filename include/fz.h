@@ -300,9 +300,10 @@ fz_status fz_selftest_bounded_wait(fz_ctx *ctx, void *stream);
  * nsym <= 1024) into d_hist (u64[nsym], device), by one of two methods that
  * give the same exact counts: FZ_HIST_PRIVATE (warp-private shared-memory
  * histograms) or FZ_HIST_TOPK, the top-k variant §3.2 describes as the better
- * one when the codes repeat a few values: the 16 most frequent codes of a
- * sample (64 windows of 1024 codes spread over the array) are counted in per-thread packed registers and only the
- * others take shared-memory atomics.  (The compression path counts its codes
+ * one when the codes repeat a few values: the 4 most frequent codes of a
+ * sample (64 windows of 1024 codes spread over the array) are counted by
+ * packed 16-bit comparisons into per-thread registers and only the others
+ * take shared-memory atomics.  (The compression path counts its codes
  * inside the quantizer; this entry point serves a code array on its own, such
  * as the output of fz_lorenzo_quantize.)  Uses the context workspace;
  * synchronizes `stream`.  FZ_EINVAL for bad arguments or a code >= nsym. */

@@ -8,12 +8,13 @@
 //   FZ_HIST_TOPK -- the top-k variant (§3.2: better when the codes repeat a
 //     few values, as after a good predictor).  A one-CTA pass counts a
 //     sample (64 windows of 1024 codes spread over the array) and keeps its
-//     k = 16 most frequent codes; in the main
-//     pass each thread counts those 16 codes in two 64-bit registers of
-//     eight 8-bit counters (an add of 1 << 8 slot), folded into shared
-//     memory every 255 codes, and only the other codes take a shared
-//     atomic.  Which codes are chosen only moves work between the two
-//     paths: the counts are exact either way.
+//     k = 4 most frequent codes; in the main pass every 32-bit word (two
+//     codes) is compared with each of the 4 codes at once (a packed 16-bit
+//     equality), the matches are counted in four 32-bit registers per
+//     thread, and only the other codes take a shared atomic -- so codes that
+//     repeat do not serialize on one shared address.  Which codes are chosen
+//     only moves work between the two paths: the counts are exact either
+//     way.
 //
 // Both read the codes with 16-byte loads over a grid of a few CTAs per SM.
 #include <string.h>
@@ -25,7 +26,7 @@ namespace {
 
 constexpr int kHiThreads = 256;
 constexpr int kHiWarps = kHiThreads / 32;
-constexpr int kTopK = 16;
+constexpr int kTopK = 4;
 constexpr uint32_t kSampleWindows = 64, kSampleWindow = 1024;  // 64K codes in 64 evenly spread windows
 
 // Warp-private shared histograms; n a multiple of 8 codes is read as uint4.
@@ -65,11 +66,11 @@ __global__ void __launch_bounds__(kHiThreads) k_hist_private(const uint16_t *__r
 }
 
 // One CTA: counts a sample of at most 64K codes (64 windows of 1024
-// consecutive codes spread evenly over the array, read coalesced) and
-// writes the 16 most frequent codes (ties to the lower code) into slot[] as
-// a code -> slot table (0xff: none).
+// consecutive codes spread evenly over the array) and writes its kTopK most
+// frequent codes (ties to the lower code) to top[0..kTopK), 0xffff for a
+// slot that the sample leaves empty.
 __global__ void __launch_bounds__(kHiThreads) k_hist_sample(const uint16_t *__restrict__ codes, uint64_t n,
-                                                            uint32_t nsym, uint8_t *slot) {
+                                                            uint32_t nsym, uint16_t *top) {
   extern __shared__ uint32_t hs[];  // nsym
   for (uint32_t i = threadIdx.x; i < nsym; i += kHiThreads) hs[i] = 0;
   __syncthreads();
@@ -95,15 +96,15 @@ __global__ void __launch_bounds__(kHiThreads) k_hist_sample(const uint16_t *__re
     }
   }
   __syncthreads();
-  if (threadIdx.x < 32) {  // one warp picks the top 16 by repeated arg-max
+  if (threadIdx.x < 32) {  // one warp picks the top codes by repeated arg-max
     const int lane = threadIdx.x;
-    for (uint32_t s = lane; s < nsym; s += 32) slot[s] = 0xff;
+    if (lane < kTopK) top[lane] = 0xffffu;
     __syncwarp();
     for (int k = 0; k < kTopK; ++k) {
       uint32_t best = 0, arg = 0xffffffffu;
       for (uint32_t s = lane; s < nsym; s += 32) {
         const uint32_t c = hs[s];
-        if (slot[s] == 0xff && (c > best || (c == best && c > 0 && s < arg))) { best = c; arg = s; }
+        if (c > best || (c == best && c > 0 && s < arg)) { best = c; arg = s; }
       }
       for (int off = 16; off > 0; off >>= 1) {
         const uint32_t b2 = __shfl_down_sync(0xffffffffu, best, off), a2 = __shfl_down_sync(0xffffffffu, arg, off);
@@ -111,82 +112,73 @@ __global__ void __launch_bounds__(kHiThreads) k_hist_sample(const uint16_t *__re
       }
       arg = __shfl_sync(0xffffffffu, arg, 0);
       best = __shfl_sync(0xffffffffu, best, 0);
-      if (best == 0 || arg == 0xffffffffu) break;  // fewer than 16 codes seen
-      if (lane == 0) slot[arg] = (uint8_t)k;
+      if (best == 0 || arg == 0xffffffffu) break;  // fewer than kTopK codes seen
+      if (lane == 0) {
+        top[k] = (uint16_t)arg;
+        hs[arg] = 0;  // not picked again
+      }
       __syncwarp();
     }
   }
 }
 
-// Adds the 16 packed byte counters of every thread of the CTA into the
-// shared counts of their codes (warp reductions, one lane adds).
-__device__ __forceinline__ void fold_topk(unsigned long long &lo, unsigned long long &hi, const uint16_t *topsym,
-                                          uint32_t *hs) {
-  const int lane = threadIdx.x & 31;
+// The main pass: per 32-bit word (two codes), one packed 16-bit equality
+// with each chosen code pair (c | c << 16) gives 0xffff per matching half;
+// popcount / 16 over a thread's words is its count of that code.  Halves
+// that match none take one shared atomic.  Chosen slots left empty (0xffff)
+// are masked off.
+__global__ void __launch_bounds__(kHiThreads) k_hist_topk(const uint16_t *__restrict__ codes, uint64_t n,
+                                                          uint32_t nsym, const uint16_t *__restrict__ top_g,
+                                                          unsigned long long *hist) {
+  extern __shared__ uint32_t hs[];  // nsym counts
+  for (uint32_t i = threadIdx.x; i < nsym; i += kHiThreads) hs[i] = 0;
+  uint32_t pair[kTopK], en[kTopK], cnt[kTopK];
 #pragma unroll
   for (int k = 0; k < kTopK; ++k) {
-    const uint32_t c = (uint32_t)(((k < 8 ? lo : hi) >> (8 * (k & 7))) & 0xffu);
-    const uint32_t t = __reduce_add_sync(0xffffffffu, c);
-    if (lane == 0 && t) atomicAdd(hs + topsym[k], t);
-  }
-  lo = 0;
-  hi = 0;
-}
-
-__global__ void __launch_bounds__(kHiThreads) k_hist_topk(const uint16_t *__restrict__ codes, uint64_t n,
-                                                          uint32_t nsym, const uint8_t *__restrict__ slot_g,
-                                                          unsigned long long *hist) {
-  extern __shared__ uint32_t hs[];            // nsym counts
-  uint8_t *slot = reinterpret_cast<uint8_t *>(hs + nsym);  // nsym code -> slot
-  __shared__ uint16_t topsym[kTopK];
-  for (uint32_t i = threadIdx.x; i < nsym; i += kHiThreads) {
-    hs[i] = 0;
-    const uint8_t sl = slot_g[i];
-    slot[i] = sl;
-    if (sl < kTopK) topsym[sl] = (uint16_t)i;
-  }
-  if (threadIdx.x < kTopK) {
-    // slots the sample left empty point at code 0, whose counter stays 0
-    bool used = false;
-    for (uint32_t i = 0; i < nsym; ++i) used |= slot_g[i] == threadIdx.x;
-    if (!used) topsym[threadIdx.x] = 0;
+    const uint32_t c = __ldg(top_g + k);
+    en[k] = c < nsym ? 0xffffffffu : 0u;
+    pair[k] = c | (c << 16);
+    cnt[k] = 0;
   }
   __syncthreads();
-  unsigned long long lo = 0, hi = 0;
   bool bad = false;
   const uint64_t nv = n / 8;
   const uint4 *c4 = reinterpret_cast<const uint4 *>(codes);
-  // every thread runs the same number of iterations so that the warp-wide
-  // folds line up; iterations past the end count nothing
   const uint64_t stride = (uint64_t)gridDim.x * kHiThreads;
-  const uint64_t iters = (nv + stride - 1) / stride;
-  uint32_t since = 0;
-  for (uint64_t it = 0; it < iters; ++it) {
-    const uint64_t v = it * stride + (uint64_t)blockIdx.x * kHiThreads + threadIdx.x;
-    if (v < nv) {
-      const uint4 w = __ldcs(c4 + v);
-      const uint32_t ww[4] = {w.x, w.y, w.z, w.w};
+  for (uint64_t v = (uint64_t)blockIdx.x * kHiThreads + threadIdx.x; v < nv; v += stride) {
+    const uint4 w = __ldcs(c4 + v);
+    const uint32_t ww[4] = {w.x, w.y, w.z, w.w};
 #pragma unroll
-      for (int k = 0; k < 8; ++k) {
-        const uint32_t a = (ww[k >> 1] >> (16 * (k & 1))) & 0xffffu;
-        if (a >= nsym) { bad = true; continue; }
-        const uint32_t sl = slot[a];
-        if (sl < 8) lo += 1ull << (8 * sl);
-        else if (sl < kTopK) hi += 1ull << (8 * (sl - 8));
-        else atomicAdd(hs + a, 1u);
+    for (int q = 0; q < 4; ++q) {
+      uint32_t hit = 0;
+#pragma unroll
+      for (int k = 0; k < kTopK; ++k) {
+        const uint32_t m = __vcmpeq2(ww[q], pair[k]) & en[k];
+        cnt[k] += __popc(m);
+        hit |= m;
+      }
+      if (hit != 0xffffffffu) {  // a code that is none of the chosen ones
+        const uint32_t a = ww[q] & 0xffffu, b2 = ww[q] >> 16;
+        if (!(hit & 0xffffu)) {
+          if (a < nsym) atomicAdd(hs + a, 1u); else bad = true;
+        }
+        if (!(hit >> 16)) {
+          if (b2 < nsym) atomicAdd(hs + b2, 1u); else bad = true;
+        }
       }
     }
-    since += 8;
-    if (since > 255 - 8) {  // before any 8-bit counter can overflow
-      fold_topk(lo, hi, topsym, hs);
-      since = 0;
-    }
   }
-  fold_topk(lo, hi, topsym, hs);
   for (uint64_t i = nv * 8 + (uint64_t)blockIdx.x * kHiThreads + threadIdx.x; i < n; i += stride) {
     const uint32_t a = codes[i];
     if (a < nsym) atomicAdd(hs + a, 1u);
     else bad = true;
+  }
+  // the chosen codes' counts: a warp sum per code, one shared atomic per warp
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int k = 0; k < kTopK; ++k) {
+    const uint32_t t = __reduce_add_sync(0xffffffffu, cnt[k] >> 4);
+    if (lane == 0 && t) atomicAdd(hs + (pair[k] & 0xffffu), t);
   }
   __syncthreads();
   for (uint32_t s = threadIdx.x; s < nsym; s += kHiThreads)
@@ -207,8 +199,8 @@ extern "C" fz_status fz_histogram(fz_ctx *ctx, const uint16_t *d_codes, uint64_t
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   if (cudaSetDevice(ctx->device) != cudaSuccess) return FZ_ECUDA;
   // workspace: the counts (nsym + 1 words, the last one flags codes >= nsym)
-  // and the code -> slot table of the top-k method
-  const size_t need = up(8 * (nsym + 1)) + up(nsym);
+  // and the chosen codes of the top-k method
+  const size_t need = up(8 * (nsym + 1)) + up(2 * kTopK);
   if (ctx->ws_bytes < need) {
     if (ctx->ws) cudaFree(ctx->ws);
     ctx->ws = nullptr;
@@ -225,7 +217,7 @@ extern "C" fz_status fz_histogram(fz_ctx *ctx, const uint16_t *d_codes, uint64_t
     return FZ_ENOMEM;
   }
   unsigned long long *counts = reinterpret_cast<unsigned long long *>(ctx->ws);
-  uint8_t *slot = reinterpret_cast<uint8_t *>(ctx->ws) + up(8 * (nsym + 1));
+  uint16_t *top = reinterpret_cast<uint16_t *>(reinterpret_cast<uint8_t *>(ctx->ws) + up(8 * (nsym + 1)));
   uint64_t grid = (n / 8 + kHiThreads - 1) / kHiThreads;
   const uint64_t cap = (uint64_t)ctx->sm_count * 4;
   if (grid > cap) grid = cap;
@@ -241,11 +233,11 @@ extern "C" fz_status fz_histogram(fz_ctx *ctx, const uint16_t *d_codes, uint64_t
     ctx->launches += 1;
   } else {
     if (e == cudaSuccess) {
-      k_hist_sample<<<1, kHiThreads, sizeof(uint32_t) * nsym, s>>>(d_codes, n, nsym, slot);
+      k_hist_sample<<<1, kHiThreads, sizeof(uint32_t) * nsym, s>>>(d_codes, n, nsym, top);
       e = cudaGetLastError();
     }
     if (e == cudaSuccess) {
-      k_hist_topk<<<(unsigned)grid, kHiThreads, sizeof(uint32_t) * nsym + nsym, s>>>(d_codes, n, nsym, slot, counts);
+      k_hist_topk<<<(unsigned)grid, kHiThreads, sizeof(uint32_t) * nsym, s>>>(d_codes, n, nsym, top, counts);
       e = cudaGetLastError();
     }
     ctx->launches += 2;
