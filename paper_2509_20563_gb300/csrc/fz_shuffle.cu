@@ -380,43 +380,51 @@ __device__ __forceinline__ void decode_shuf_chunk(const ShDec &p, const Geom &g,
       bz1 = r_1 / g.nby;
     }
   }
+  // field coordinates of code (run kk, lane ln, half e) of the chunk; field
+  // indices fit 32 bits (fewer than 2^32 values)
+  auto coords = [&](int kk, int ln, uint32_t e, uint32_t &x, uint32_t &y, uint32_t &z) {
+    if (NDIM == 3) {
+      const bool second = kk >= 8;
+      x = (second ? bx1 : bx0) * 8u + 2u * (uint32_t)(ln & 3) + e;
+      y = (second ? by1 : by0) * 8u + (uint32_t)(ln >> 2);
+      z = (second ? bz1 : bz0) * 8u + (uint32_t)(kk & 7);
+    } else if (NDIM == 2) {
+      x = bx0 * 32u + 2u * (uint32_t)(ln & 15) + e;
+      y = by0 * 32u + 2u * (uint32_t)kk + (uint32_t)(ln >> 4);
+      z = 0;
+    } else {
+      x = (uint32_t)j * 1024u + 64u * (uint32_t)kk + 2u * (uint32_t)ln + e;
+      y = 0;
+      z = 0;
+    }
+  };
+  const bool vec = (((uintptr_t)p.out) & 7u) == 0;
 #pragma unroll
   for (int kk = 0; kk < 16; ++kk) {
     if (kk >= nr) continue;
-    float o0 = __fmul_rn(__int2float_rn(d[kk][0]), p.ebx2), o1 = __fmul_rn(__int2float_rn(d[kk][1]), p.ebx2);
-    for (uint64_t i = eb0; i < ee0; ++i) {
-      const uint32_t rel = __ldg(p.exc_idx + i) - pos0;
-      if ((int)(rel >> 6) == kk && (int)((rel >> 1) & 31u) == lane) {
-        if (rel & 1u) o1 = __uint_as_float(__ldg(p.exc_val + i));
-        else o0 = __uint_as_float(__ldg(p.exc_val + i));
-      }
-    }
-    uint64_t f;
+    const float o0 = __fmul_rn(__int2float_rn(d[kk][0]), p.ebx2), o1 = __fmul_rn(__int2float_rn(d[kk][1]), p.ebx2);
     uint32_t x, y, z;
-    if (NDIM == 3) {
-      const bool second = kk >= 8;
-      x = (second ? bx1 : bx0) * 8u + 2u * (uint32_t)(lane & 3);
-      y = (second ? by1 : by0) * 8u + (uint32_t)(lane >> 2);
-      z = (second ? bz1 : bz0) * 8u + (uint32_t)(kk & 7);
-      f = ((uint64_t)z * g.ny + y) * g.nx + x;
-    } else if (NDIM == 2) {
-      x = bx0 * 32u + 2u * (uint32_t)(lane & 15);
-      y = by0 * 32u + 2u * (uint32_t)kk + (uint32_t)(lane >> 4);
-      z = 0;
-      f = (uint64_t)y * g.nx + x;
-    } else {
-      x = (uint32_t)j * 1024u + 64u * (uint32_t)kk + 2u * (uint32_t)lane;
-      y = 0;
-      z = 0;
-      f = x;
-    }
+    coords(kk, lane, 0u, x, y, z);
+    const uint32_t f = (z * g.ny + y) * g.nx + x;
     if (y < g.ny && z < g.nz) {
-      if (x + 1 < g.nx && (f & 1) == 0 && (((uintptr_t)p.out) & 7u) == 0) {
+      if (x + 1 < g.nx && (f & 1) == 0 && vec) {
         *reinterpret_cast<float2 *>(p.out + f) = make_float2(o0, o1);
       } else {
         if (x < g.nx) p.out[f] = o0;
         if (x + 1 < g.nx) p.out[f + 1] = o1;
       }
+    }
+  }
+  // exceptions of the chunk (rare): their stored bits replace the values the
+  // warp has just written (the warp's stores are ordered before these)
+  if (eb0 < ee0) {
+    __syncwarp();
+    for (uint64_t i = eb0 + (uint64_t)lane; i < ee0; i += 32) {
+      const uint32_t rel = __ldg(p.exc_idx + i) - pos0;  // < nr * 64: the chunk's range
+      uint32_t x, y, z;
+      coords((int)(rel >> 6), (int)((rel >> 1) & 31u), rel & 1u, x, y, z);
+      if (x < g.nx && y < g.ny && z < g.nz) p.out[(z * g.ny + y) * g.nx + x] = __uint_as_float(__ldg(p.exc_val + i));
+      else bad = true;
     }
   }
 }
