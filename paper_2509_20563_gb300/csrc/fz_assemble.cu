@@ -279,10 +279,13 @@ __device__ __forceinline__ void gather_body(const Geom &g, const CompressWs &ws,
 __global__ void __launch_bounds__(kAsmThreads) k_assemble(const float *__restrict__ x, Geom g, uint32_t R,
                                                            CompressWs ws, uint8_t *d_out) {
   __shared__ AsmSmem sm;
+  dep_wait();
+  dep_trigger();
   assemble_body(x, g, R, ws, d_out, blockIdx.x, gridDim.x, sm);
 }
 
 __global__ void __launch_bounds__(kAsmThreads) k_gather(Geom g, CompressWs ws, uint8_t *d_out) {
+  dep_wait();
   // the call's result, final once the encoder has run, goes straight to the
   // host's pinned buffer (no device-to-host copy after the kernels)
   if (blockIdx.x == 0 && threadIdx.x < 32 && ws.h_res) {
@@ -339,11 +342,11 @@ cudaError_t launch_assemble(const float *x, const Geom &g, uint32_t R, const Com
   const uint64_t n_tg = (g.n_qtiles + kTileGroup - 1) / kTileGroup;
   if (grid < n_tg) grid = n_tg < (uint64_t)sm_count * 8 ? n_tg : (uint64_t)sm_count * 8;
   if (grid < 2) grid = 2;
-  k_assemble<<<(unsigned)grid, kAsmThreads, 0, s>>>(x, g, R, ws, d_out);
+  cudaError_t e = launch_dep(k_assemble, (unsigned)grid, (unsigned)kAsmThreads, 0, s, x, g, R, ws, d_out);
+  if (e != cudaSuccess) return e;
   uint64_t ggrid = (8 * g.n_qtiles + kAsmThreads / 32 - 1) / (kAsmThreads / 32);
   if (ggrid > (uint64_t)sm_count * 8) ggrid = (uint64_t)sm_count * 8;
-  k_gather<<<(unsigned)ggrid, kAsmThreads, 0, s>>>(g, ws, d_out);
-  return cudaGetLastError();
+  return launch_dep(k_gather, (unsigned)ggrid, (unsigned)kAsmThreads, 0, s, g, ws, d_out);
 }
 
 }  // namespace fz

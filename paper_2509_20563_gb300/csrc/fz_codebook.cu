@@ -263,6 +263,8 @@ __global__ void __launch_bounds__(kCbThreads) k_codebook(Geom g, uint32_t R, uin
                                                           double eb, CompressWs ws) {
   extern __shared__ __align__(16) unsigned char cb_smem[];
   __shared__ uint32_t s_mode;
+  dep_wait();
+  dep_trigger();
   codebook_body(g, R, pred, eb_mode, eb, ws, *reinterpret_cast<CbSmem *>(cb_smem), s_mode);
 }
 
@@ -348,10 +350,10 @@ cudaError_t launch_codebook(const Geom &g, uint32_t R, uint32_t pred, uint32_t e
                             const CompressWs &ws, cudaStream_t st) {
   static LaunchCache cache;
   int per_sm = 0;
+  // (sets the kernel's shared-memory limit once)
   const cudaError_t e = cached_per_sm(k_codebook, kCbThreads, (int)sizeof(CbSmem), cache, per_sm);
   if (e != cudaSuccess) return e;
-  k_codebook<<<1, kCbThreads, sizeof(CbSmem), st>>>(g, R, pred, eb_mode, eb, ws);
-  return cudaGetLastError();
+  return launch_dep(k_codebook, 1u, (unsigned)kCbThreads, sizeof(CbSmem), st, g, R, pred, eb_mode, eb, ws);
 }
 
 cudaError_t launch_codebook_batch(const BatchJob *jobs, uint32_t n, cudaStream_t st) {

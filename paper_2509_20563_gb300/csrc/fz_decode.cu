@@ -791,8 +791,11 @@ __global__ void __launch_bounds__(DecCta<NDIM, K>::T, 1) k_decode(DecParams p, G
   int32_t *sstate = reinterpret_cast<int32_t *>(d_smem + sizeof(uint16_t) * kLutSize);
   uint32_t *sring = reinterpret_cast<uint32_t *>(sstate + DecState<NDIM, K>::kWords * T);
   __shared__ LutBuild lb;
-  // every CTA builds the decode table from the 1 KB length table itself
-  if (build_lut<T>(p.lens, p.nsym, slut, lb)) {
+  // every CTA builds the decode table from the 1 KB length table itself (an
+  // input of the call: it overlaps the offset pass, launched before)
+  const bool ok = build_lut<T>(p.lens, p.nsym, slut, lb);
+  dep_wait();  // the unit offsets
+  if (ok) {
     __syncthreads();
     decode_units<NDIM, K>(p, g, slut, sstate, sring);
   } else if (threadIdx.x == 0) {
@@ -900,8 +903,7 @@ cudaError_t launch_dec_t(const DecParams &p, const Geom &g, int sm_count, cudaSt
   // at most one CTA per unit: the units of a small field spread over SMs
   uint64_t grid = (uint64_t)sm_count * per_sm;
   if (grid > p.n_units) grid = p.n_units;
-  k_decode<NDIM, K><<<(unsigned)grid, T, smem, s>>>(p, g);
-  return cudaGetLastError();
+  return launch_dep(k_decode<NDIM, K>, (unsigned)grid, (unsigned)T, (size_t)smem, s, p, g);
 }
 
 }  // namespace
@@ -971,6 +973,7 @@ __global__ void __launch_bounds__(kOffThreads) k_dec_offsets(const uint32_t *__r
                                                              uint64_t n_chunks, uint64_t n_units,
                                                              uint64_t total_bits, uint64_t *uoff, uint32_t *err,
                                                              long long spin) {
+  dep_trigger();  // the decoder builds its table meanwhile
   __shared__ unsigned long long wsum[kOffThreads / 32];
   __shared__ unsigned long long s_base;
   __shared__ uint32_t s_tile;

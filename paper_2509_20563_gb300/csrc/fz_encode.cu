@@ -300,6 +300,8 @@ __global__ void __launch_bounds__(kEncThreads, CH == 512 ? FZ_ENC_MINB : FZ_ENC_
   constexpr int PER = CH / 32;
   constexpr int D = FZ_ENC_DEPTH;
   __shared__ PipeSmem<CH, D> sm;
+  dep_wait();
+  dep_trigger();
   Ctl *ctl = ws.ctl;
   if (ctl->mode != kModeNormal) return;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -497,8 +499,7 @@ cudaError_t launch_t(const Geom &g, const CompressWs &ws, uint8_t *d_out, cudaSt
   const uint64_t n_tiles = (g.n_blocks + kEncWarps - 1) / kEncWarps;
   uint64_t grid = (uint64_t)sms * per_sm;
   if (grid > n_tiles) grid = n_tiles;
-  k_encode_pipe<CH, CM><<<(unsigned)grid, kEncThreads, 0, s>>>(g, ws, d_out);
-  return cudaGetLastError();
+  return launch_dep(k_encode_pipe<CH, CM>, (unsigned)grid, (unsigned)kEncThreads, 0, s, g, ws, d_out);
 }
 
 template <int CH>

@@ -43,6 +43,33 @@ struct Geom {
   uint64_t n_chunks;       // ceil(npad / chunk)
 };
 
+// ---- programmatic dependent launch between the stages of one call
+// A stage launched with launch_dep may start while the previous kernel of the
+// stream runs; before it reads anything an earlier stage wrote it calls
+// dep_wait(), which returns once the previous kernel has completed and its
+// writes are visible (an earlier kernel of the stream completed before that
+// one passed its own wait).  Work before dep_wait() touches only the call's
+// inputs.  dep_trigger(), called after the kernel's own wait, lets the next
+// stage start.  Both are no-ops in kernels launched the ordinary way.
+__device__ __forceinline__ void dep_wait() { asm volatile("griddepcontrol.wait;\n" ::: "memory"); }
+__device__ __forceinline__ void dep_trigger() { asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory"); }
+
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_dep(void (*kernel)(KArgs...), unsigned grid, unsigned block, size_t smem, cudaStream_t s,
+                              Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(block);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, args...);
+}
+
 // Code-stream positions (block-major, padding included) are 32-bit in the
 // stream format (outlier and exception indices) and in the kernels.
 inline __host__ __device__ bool positions_fit(const Geom &g) { return g.npad <= 0xffffffffull; }

@@ -399,8 +399,10 @@ __device__ __forceinline__ void tile_codes12(const Geom &g, const TileXY &t, con
 }
 
 // The tiles tile, tile + step, ... below t_end of one field, then the
-// field's histogram flush.  All threads of the CTA call it together.
-template <int NDIM, int K>
+// field's histogram flush.  All threads of the CTA call it together.  DEP:
+// launched behind the range pass (launch_dep): the first tile's loads of the
+// input go out before the wait for the pass's constants.
+template <int NDIM, int K, bool DEP = false>
 __device__ __forceinline__ void quant_tiles(const float *__restrict__ x, const Geom &g, uint32_t R,
                                             const CompressWs &ws, uint64_t tile, uint64_t t_end, uint64_t t_step,
                                             QuantSmem<NDIM> &sm) {
@@ -410,13 +412,6 @@ __device__ __forceinline__ void quant_tiles(const float *__restrict__ x, const G
   static_assert(S::TX * S::ROWS == kTileElems, "tile size");
   static_assert(S::NB * S::WPB == kQuantThreads / 32, "warps per tile");
 
-  Ctl *ctl = ws.ctl;
-  if (ctl->mode != kModeNormal) return;
-  QuantConst qc;
-  qc.inv2eb = ctl->inv2eb;
-  qc.ebx2 = ctl->ebx2;
-  qc.eb_chk = ctl->eb_chk;
-  qc.R = (int32_t)R;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const uint32_t nsym = 2 * R;
   for (int s = tid; s < kMaxSym; s += kQuantThreads) sm.shist[s] = 0;
@@ -428,6 +423,17 @@ __device__ __forceinline__ void quant_tiles(const float *__restrict__ x, const G
   const TileStep tstep = tile_step(g, t_step);
   TileXY tn = tile_xy<NDIM>(g, tile);  // coordinates of the tile whose loads are in flight
   if (tile < t_end) load_tile<NDIM>(x, g, tn, tid, vec_ok, v);
+  if (DEP) {
+    dep_wait();
+    dep_trigger();
+  }
+  Ctl *ctl = ws.ctl;
+  if (ctl->mode != kModeNormal) return;
+  QuantConst qc;
+  qc.inv2eb = ctl->inv2eb;
+  qc.ebx2 = ctl->ebx2;
+  qc.eb_chk = ctl->eb_chk;
+  qc.R = (int32_t)R;
   for (int buf = 0; tile < t_end; tile += t_step, buf ^= 1) {
     const TileXY t = tn;
     // a tile that lies wholly inside the domain skips every bounds test
@@ -558,7 +564,7 @@ __global__ void __launch_bounds__(kQuantThreads, FZ_QUANT_MINB) k_quant(const fl
                                                              CompressWs ws) {
   extern __shared__ __align__(16) unsigned char q_smem[];
   QuantSmem<NDIM> &sm = *reinterpret_cast<QuantSmem<NDIM> *>(q_smem);
-  quant_tiles<NDIM, K>(x, g, R, ws, blockIdx.x, g.n_qtiles, gridDim.x, sm);
+  quant_tiles<NDIM, K, true>(x, g, R, ws, blockIdx.x, g.n_qtiles, gridDim.x, sm);
 }
 
 // Batched variant: the quantization tiles of every field of one class
@@ -605,8 +611,7 @@ cudaError_t launch_t(const float *x, const Geom &g, uint32_t R, const CompressWs
   if (e != cudaSuccess) return e;
   uint64_t grid = (uint64_t)sms * per_sm;
   if (grid > g.n_qtiles) grid = g.n_qtiles;
-  k_quant<NDIM, K><<<(unsigned)grid, kQuantThreads, smem, s>>>(x, g, R, ws);
-  return cudaGetLastError();
+  return launch_dep(k_quant<NDIM, K>, (unsigned)grid, kQuantThreads, (size_t)smem, s, x, g, R, ws);
 }
 
 template <int NDIM, int K>

@@ -69,6 +69,7 @@ __device__ void range_tail(Ctl *ctl, uint32_t eb_mode, double eb) {
 
 __global__ void __launch_bounds__(kRangeThreads) k_range(const float *__restrict__ x, uint64_t n, Ctl *ctl,
                                                           uint32_t eb_mode, double eb) {
+  dep_trigger();  // the quantizer's first loads (of the input) may start
   Acc a;
   a.init();
   const uint64_t tid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;

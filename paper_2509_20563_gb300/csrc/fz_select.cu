@@ -1036,8 +1036,8 @@ __device__ void build_recon_tables(uint16_t *list, uint4 *tab) {
   }
 }
 
-__global__ void __launch_bounds__(kReconWarps * 32) k_sel_recon(ReconParams rp, Geom g) {
-  __shared__ int32_t sq[kReconWarps][512];
+__global__ void __launch_bounds__(kReconWarps * 32, 4) k_sel_recon(ReconParams rp, Geom g) {
+  __shared__ __align__(16) int32_t sq[kReconWarps][512];
   __shared__ int32_t scq[kReconWarps][8];
   __shared__ uint32_t sov[kReconWarps][512];
   __shared__ uint32_t smask[kReconWarps][16];
@@ -1073,24 +1073,47 @@ __global__ void __launch_bounds__(kReconWarps * 32) k_sel_recon(ReconParams rp, 
     uint64_t obase = 0;
     if (rp.n_out) obase = __ldg(rp.ofirst + blk);
     bool bad = false;
-    uint32_t orank = 0;
-    for (int i = 0; i < 16; ++i) {
-      const int p = 32 * i + lane;
-      const uint32_t code = __ldg(rp.codes + pos0 + p);
-      const bool isout = code == 0;
-      const uint32_t m = __ballot_sync(0xffffffffu, isout);
-      int32_t d = (int32_t)code - rp.R;
-      if (isout) {
-        const uint64_t k = obase + orank + __popc(m & ((1u << lane) - 1));
-        if (k < rp.n_out && __ldg(rp.out_idx + k) == pos0 + p) d = __ldg(rp.out_val + k);
-        else { bad = true; d = 0; }
+    {
+      // lane l: the block's codes 16 l .. 16 l + 15, two 16-byte loads (the
+      // code buffer holds whole blocks at 1 KB boundaries)
+      const uint4 *cp = reinterpret_cast<const uint4 *>(rp.codes + pos0) + 2 * lane;
+      const uint4 c0 = __ldg(cp), c1 = __ldg(cp + 1);
+      const uint32_t cw[8] = {c0.x, c0.y, c0.z, c0.w, c1.x, c1.y, c1.z, c1.w};
+      int32_t dv[16];
+      uint32_t nz = 0;
+#pragma unroll
+      for (int k = 0; k < 16; ++k) {
+        const uint32_t code = (cw[k >> 1] >> (16 * (k & 1))) & 0xffffu;
+        dv[k] = (int32_t)code - rp.R;
+        nz += code == 0 ? 1u : 0u;
       }
-      orank += __popc(m);
-      if (p == 0) d += __ldg(rp.anchors + blk);
-      sq[w][p] = d;
-      sov[w][p] = 0;
+      if (__any_sync(0xffffffffu, nz != 0)) {
+        // outliers in position order: the lanes' zero counts scanned
+        uint32_t incl = nz;
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+          const uint32_t v = __shfl_up_sync(0xffffffffu, incl, off);
+          if (lane >= off) incl += v;
+        }
+        uint64_t k = obase + (incl - nz);
+#pragma unroll
+        for (int kk = 0; kk < 16; ++kk) {
+          if (((cw[kk >> 1] >> (16 * (kk & 1))) & 0xffffu) == 0) {
+            const uint32_t pos = pos0 + 16u * (uint32_t)lane + (uint32_t)kk;
+            int32_t d = 0;
+            if (k < rp.n_out && __ldg(rp.out_idx + k) == pos) d = __ldg(rp.out_val + k);
+            else bad = true;
+            dv[kk] = d;
+            ++k;
+          }
+        }
+      }
+      if (lane == 0) dv[0] += __ldg(rp.anchors + blk);
+      int4 *dst = reinterpret_cast<int4 *>(&sq[w][16 * lane]);
+#pragma unroll
+      for (int u = 0; u < 4; ++u) dst[u] = make_int4(dv[4 * u], dv[4 * u + 1], dv[4 * u + 2], dv[4 * u + 3]);
     }
-    if (lane < 16) smask[w][lane] = 0;
+    if (lane < 16) smask[w][lane] = 0;  // no exception yet (the override values are read only where set)
     __syncwarp();
     BlockView b;
     b.sq = nullptr;
