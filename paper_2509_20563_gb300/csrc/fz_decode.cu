@@ -366,9 +366,12 @@ __device__ __forceinline__ void store8(float *out, uint64_t f, bool full, bool v
 // Per-thread prefix state that does not fit registers lives in shared
 // memory, one column per thread ([i][thread] layout, conflict-free):
 // 3D: the plane sums P (64 per order), 2D: the column sums Y (32 per order).
-template <int NDIM, int K>
+// Words of per-thread prefix state.  NS (narrow state, 3D order 1): the
+// previous plane's values relative to the block's anchor as 16-bit integers,
+// 32 words instead of 64 (see narrow_state_ok).
+template <int NDIM, int K, bool NS = false>
 struct DecState {
-  static constexpr int kWords = NDIM == 3 ? 64 * K : (NDIM == 2 ? 32 * K : 0);
+  static constexpr int kWords = NS ? 32 : (NDIM == 3 ? 64 * K : (NDIM == 2 ? 32 * K : 0));
 };
 
 // Threads per decode CTA (one CTA per SM).  The decode table is shared by
@@ -385,15 +388,24 @@ struct DecState {
 #ifndef FZ_DEC_T1
 #define FZ_DEC_T1 1024  // 1D: 768 and 896 measured slower on a 281M-value field
 #endif
-template <int NDIM, int K>
+#ifndef FZ_DEC_NARROW
+#define FZ_DEC_NARROW 1
+#endif
+#ifndef FZ_DEC_T3N
+// narrow state: 576 and 640 threads measured alike, 704 slower (L1 then too
+// small for the bitstream lines)
+#define FZ_DEC_T3N 576
+#endif
+template <int NDIM, int K, bool NS = false>
 struct DecCta {
-  static constexpr int T = NDIM == 3 ? (K == 1 ? FZ_DEC_T3 : 288) : (NDIM == 2 ? (K == 1 ? FZ_DEC_T2 : 448) : FZ_DEC_T1);
+  static constexpr int T = NS ? FZ_DEC_T3N
+                              : (NDIM == 3 ? (K == 1 ? FZ_DEC_T3 : 288) : (NDIM == 2 ? (K == 1 ? FZ_DEC_T2 : 448) : FZ_DEC_T1));
 };
 
-template <int NDIM, int K>
+template <int NDIM, int K, bool NS = false>
 constexpr size_t dec_smem_bytes() {
   return sizeof(uint16_t) * kLutSize +
-         sizeof(int32_t) * (size_t)(DecState<NDIM, K>::kWords + kRing) * DecCta<NDIM, K>::T;
+         sizeof(int32_t) * (size_t)(DecState<NDIM, K, NS>::kWords + kRing) * DecCta<NDIM, K, NS>::T;
 }
 
 // The stored residuals of the outliers among eight codes (code 0 decodes
@@ -419,6 +431,26 @@ __device__ __forceinline__ void fix_outliers(const DecParams &p, Side &sd, uint6
   }
 }
 
+// A thread's per-block prefix state in shared memory, in 16-byte slots:
+// words 4k..4k+3 of thread t at slot k * T + t, so the eight words of a row
+// move with two 16-byte accesses (four shared-memory instructions per row
+// instead of sixteen).
+template <int T>
+__device__ __forceinline__ void st_load8(const int32_t *st, int w0, int32_t (&v)[8]) {
+  const int4 *p = reinterpret_cast<const int4 *>(st) + (w0 >> 2) * T;
+  const int4 a = p[0], b = p[T];
+  v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
+  v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
+}
+template <int T>
+__device__ __forceinline__ void st_store8(int32_t *st, int w0, const int32_t (&v)[8]) {
+  int4 *p = reinterpret_cast<int4 *>(st) + (w0 >> 2) * T;
+  p[0] = make_int4(v[0], v[1], v[2], v[3]);
+  p[T] = make_int4(v[4], v[5], v[6], v[7]);
+}
+// the state pointer of thread t
+__device__ __forceinline__ int32_t *st_thread(int32_t *sstate, int t) { return sstate + 4 * t; }
+
 // Prefix-sum state of the inverse Lorenzo for one chunk.
 struct Prefix {
   int32_t r1, r2;          // running sums along x (orders 1, 2)
@@ -428,10 +460,10 @@ struct Prefix {
 // Inverse Lorenzo, dequantization and store of group gi (eight codes) of a
 // chunk: 3D group = one x-row (z = gi / 8, y = gi % 8); 2D group = a quarter
 // row (y = gi / 4); 1D group = eight consecutive values.
-template <int NDIM, int K, bool EXC, int T>
+template <int NDIM, int K, bool EXC, int T, bool NS = false>
 __device__ __forceinline__ void consume(const DecParams &p, const Geom &g, Side &sd, Prefix &s, int32_t *st,
                                         int gi, const int32_t (&d)[8], uint32_t pos0, uint32_t X0, uint32_t Y0,
-                                        uint32_t Z0, bool vecbase) {
+                                        uint32_t Z0, bool vecbase, int32_t anchor) {
   float o[8];
   const uint32_t pos = pos0 + (uint32_t)gi * 8;
   if (NDIM == 3) {
@@ -441,25 +473,43 @@ __device__ __forceinline__ void consume(const DecParams &p, const Geom &g, Side 
       s.Y1[x] = y ? s.Y1[x] : 0;
       if (K == 2) s.Y2[x] = y ? s.Y2[x] : 0;
     }
-    int32_t *row = st + (y * 8) * T;
-    int32_t r1 = 0, r2 = 0, q[8];
+    int32_t r1 = 0, r2 = 0, q[8], z1[8], z2[8];
+    int4 *nrow = reinterpret_cast<int4 *>(st) + y * T;  // NS: row y's eight 16-bit values
+    if (NS) {
+      const int4 w = *nrow;
+      const uint32_t wv[4] = {(uint32_t)w.x, (uint32_t)w.y, (uint32_t)w.z, (uint32_t)w.w};
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        z1[2 * i] = (int32_t)(wv[i] << 16) >> 16;
+        z1[2 * i + 1] = (int32_t)wv[i] >> 16;
+      }
+    } else {
+      st_load8<T>(st, y * 8, z1);
+    }
+    if (K == 2) st_load8<T>(st, 64 + y * 8, z2);
 #pragma unroll
     for (int x = 0; x < 8; ++x) {
       if (K == 1) {
         r1 += d[x];
         s.Y1[x] += r1;
-        q[x] = row[x * T] + s.Y1[x];
-        row[x * T] = q[x];
+        q[x] = z1[x] + s.Y1[x];
       } else {
         r1 += d[x];
         r2 += r1;
         s.Y1[x] += r2;
         s.Y2[x] += s.Y1[x];
-        const int32_t p1 = row[x * T] + s.Y2[x];
-        row[x * T] = p1;
-        q[x] = row[(64 + x) * T] + p1;
-        row[(64 + x) * T] = q[x];
+        z1[x] += s.Y2[x];
+        q[x] = z2[x] + z1[x];
       }
+    }
+    if (K == 2) st_store8<T>(st, y * 8, z1);
+    if (NS) {
+      *nrow = make_int4((int32_t)__byte_perm(q[0], q[1], 0x5410), (int32_t)__byte_perm(q[2], q[3], 0x5410),
+                        (int32_t)__byte_perm(q[4], q[5], 0x5410), (int32_t)__byte_perm(q[6], q[7], 0x5410));
+#pragma unroll
+      for (int x = 0; x < 8; ++x) q[x] += anchor;
+    } else {
+      st_store8<T>(st, K == 1 ? y * 8 : 64 + y * 8, q);
     }
     values8<EXC>(p, sd, pos, q, o);
     if (Z0 + z < g.nz && Y0 + y < g.ny)
@@ -468,23 +518,23 @@ __device__ __forceinline__ void consume(const DecParams &p, const Geom &g, Side 
     const int y = gi >> 2, x8 = gi & 3;
     s.r1 = x8 ? s.r1 : 0;
     if (K == 2) s.r2 = x8 ? s.r2 : 0;
-    int32_t *col = st + (x8 * 8) * T;
-    int32_t q[8];
+    int32_t q[8], c1[8], c2[8];
+    st_load8<T>(st, x8 * 8, c1);
+    if (K == 2) st_load8<T>(st, 32 + x8 * 8, c2);
 #pragma unroll
     for (int u = 0; u < 8; ++u) {
       if (K == 1) {
         s.r1 += d[u];
-        q[u] = col[u * T] + s.r1;
-        col[u * T] = q[u];
+        q[u] = c1[u] + s.r1;
       } else {
         s.r1 += d[u];
         s.r2 += s.r1;
-        const int32_t y1 = col[u * T] + s.r2;
-        col[u * T] = y1;
-        q[u] = col[(32 + u) * T] + y1;
-        col[(32 + u) * T] = q[u];
+        c1[u] += s.r2;
+        q[u] = c2[u] + c1[u];
       }
     }
+    if (K == 2) st_store8<T>(st, x8 * 8, c1);
+    st_store8<T>(st, K == 1 ? x8 * 8 : 32 + x8 * 8, q);
     values8<EXC>(p, sd, pos, q, o);
     if (Y0 + y < g.ny)
       store8(p.out, (uint64_t)(Y0 + y) * g.nx + X0 + 8 * x8, X0 + 8 * x8 + 8 <= g.nx, vecbase, X0 + 8 * x8, g.nx,
@@ -510,7 +560,7 @@ __device__ __forceinline__ void consume(const DecParams &p, const Geom &g, Side 
 // chain through the bit reader) and the reconstruction of group gi
 // (independent arithmetic and stores) sit in the same straight-line code,
 // so they overlap.  Outliers are looked up per group, off that path.
-template <int NDIM, int K, bool EXC, int T>
+template <int NDIM, int K, bool EXC, int T, bool NS = false>
 __device__ __forceinline__ void decode_chunk(const DecParams &p, const Geom &g, const uint16_t *slut,
                                              int32_t *st, uint32_t *ring, uint64_t jb, uint32_t nblk,
                                              uint64_t start, uint32_t cbits, bool vecbase) {
@@ -530,7 +580,8 @@ __device__ __forceinline__ void decode_chunk(const DecParams &p, const Geom &g, 
     const uint32_t bxi = j32 % g.nbx, jr = j32 / g.nbx;
     const uint32_t byi = jr % g.nby, bzi = jr / g.nby;
     const uint32_t X0 = bxi * g.bx, Y0 = byi * g.by, Z0 = bzi * g.bz;
-    for (int i = 0; i < DecState<NDIM, K>::kWords; ++i) st[i * T] = 0;
+    for (int i = 0; i < DecState<NDIM, K, NS>::kWords / 4; ++i)
+      reinterpret_cast<int4 *>(st)[i * T] = make_int4(0, 0, 0, 0);
     Prefix s;
     s.r1 = 0;
     s.r2 = 0;
@@ -539,17 +590,17 @@ __device__ __forceinline__ void decode_chunk(const DecParams &p, const Geom &g, 
 
     int32_t cur[8];
     if (br.group8(slut, p.R, cur)) fix_outliers(p, sd, j, pos0, pos0, cur, bad);
-    cur[0] += anchor;  // the block origin's residual is its anchor
+    if (!NS) cur[0] += anchor;  // the block origin's residual is its anchor (NS: added at the output)
 #pragma unroll 1
     for (int gi = 0; gi < NG - 1; ++gi) {
       int32_t nxt[8];
       const bool zero = br.group8(slut, p.R, nxt);
-      consume<NDIM, K, EXC, T>(p, g, sd, s, st, gi, cur, pos0, X0, Y0, Z0, vecbase);
+      consume<NDIM, K, EXC, T, NS>(p, g, sd, s, st, gi, cur, pos0, X0, Y0, Z0, vecbase, anchor);
       if (zero) fix_outliers(p, sd, j, pos0, pos0 + (uint32_t)(gi + 1) * 8, nxt, bad);
 #pragma unroll
       for (int u = 0; u < 8; ++u) cur[u] = nxt[u];
     }
-    consume<NDIM, K, EXC, T>(p, g, sd, s, st, NG - 1, cur, pos0, X0, Y0, Z0, vecbase);
+    consume<NDIM, K, EXC, T, NS>(p, g, sd, s, st, NG - 1, cur, pos0, X0, Y0, Z0, vecbase, anchor);
   }
   asm volatile("cp.async.wait_all;\n" ::: "memory");  // the ring is reused by the next chunk
   if (br.consumed(start_off) != cbits || bad) dec_err(p.err, FZ_ECORRUPT);
@@ -557,10 +608,10 @@ __device__ __forceinline__ void decode_chunk(const DecParams &p, const Geom &g, 
 
 // Work units of one field whose table is in slut, claimed by this warp from
 // the field's counter until none is left.
-template <int NDIM, int K>
+template <int NDIM, int K, bool NS>
 __device__ __forceinline__ void decode_units(const DecParams &p, const Geom &g, const uint16_t *slut,
                                              int32_t *sstate, uint32_t *sring) {
-  constexpr int T = DecCta<NDIM, K>::T;
+  constexpr int T = DecCta<NDIM, K, NS>::T;
   const int t = threadIdx.x;
   // 16-byte stores of 4 consecutive x: aligned whenever rows start on a
   // 4-value boundary (1D: always; 2D/3D: nx a multiple of 4)
@@ -577,8 +628,9 @@ __device__ __forceinline__ void decode_units(const DecParams &p, const Geom &g, 
       const uint32_t k = g.chunk / g.bsize;
       const uint64_t jb = j * k;
       const uint32_t nblk = (uint32_t)(g.n_blocks - jb < k ? g.n_blocks - jb : k);
-      if (p.n_exc) decode_chunk<NDIM, K, true, T>(p, g, slut, sstate + t, sring + t, jb, nblk, start, cb, vecbase);
-      else decode_chunk<NDIM, K, false, T>(p, g, slut, sstate + t, sring + t, jb, nblk, start, cb, vecbase);
+      int32_t *st = st_thread(sstate, t);
+      if (!NS && p.n_exc) decode_chunk<NDIM, K, true, T>(p, g, slut, st, sring + t, jb, nblk, start, cb, vecbase);
+      else decode_chunk<NDIM, K, false, T, NS>(p, g, slut, st, sring + t, jb, nblk, start, cb, vecbase);
     }
   }
 }
@@ -783,13 +835,13 @@ __device__ __forceinline__ void load_lut(uint16_t *slut, const uint16_t *lut) {
 // One CTA per SM; every warp takes work units (32 chunks, one per lane)
 // from a counter, so uneven chunks and small fields still spread over all
 // SMs.
-template <int NDIM, int K>
-__global__ void __launch_bounds__(DecCta<NDIM, K>::T, 1) k_decode(DecParams p, Geom g) {
-  constexpr int T = DecCta<NDIM, K>::T;
+template <int NDIM, int K, bool NS>
+__global__ void __launch_bounds__(DecCta<NDIM, K, NS>::T, 1) k_decode(DecParams p, Geom g) {
+  constexpr int T = DecCta<NDIM, K, NS>::T;
   extern __shared__ __align__(16) unsigned char d_smem[];
   uint16_t *slut = reinterpret_cast<uint16_t *>(d_smem);
   int32_t *sstate = reinterpret_cast<int32_t *>(d_smem + sizeof(uint16_t) * kLutSize);
-  uint32_t *sring = reinterpret_cast<uint32_t *>(sstate + DecState<NDIM, K>::kWords * T);
+  uint32_t *sring = reinterpret_cast<uint32_t *>(sstate + DecState<NDIM, K, NS>::kWords * T);
   __shared__ LutBuild lb;
   // every CTA builds the decode table from the 1 KB length table itself (an
   // input of the call: it overlaps the offset pass, launched before)
@@ -797,7 +849,7 @@ __global__ void __launch_bounds__(DecCta<NDIM, K>::T, 1) k_decode(DecParams p, G
   dep_wait();  // the unit offsets
   if (ok) {
     __syncthreads();
-    decode_units<NDIM, K>(p, g, slut, sstate, sring);
+    decode_units<NDIM, K, NS>(p, g, slut, sstate, sring);
   } else if (threadIdx.x == 0) {
     dec_err(p.err, FZ_ECORRUPT);
   }
@@ -884,26 +936,42 @@ __global__ void __launch_bounds__(DecCta<NDIM, K>::T, 1) k_decode_batch(const De
         const uint32_t k = sg.chunk / sg.bsize;  // blocks per chunk
         const uint64_t jb = j * k;
         const uint32_t nblk = (uint32_t)(sg.n_blocks - jb < k ? sg.n_blocks - jb : k);
-        if (sp.n_exc) decode_chunk<NDIM, K, true, T>(sp, sg, slut, sstate + t, sring + t, jb, nblk, start, cb, vecbase);
-        else decode_chunk<NDIM, K, false, T>(sp, sg, slut, sstate + t, sring + t, jb, nblk, start, cb, vecbase);
+        int32_t *st = st_thread(sstate, t);
+        if (sp.n_exc) decode_chunk<NDIM, K, true, T>(sp, sg, slut, st, sring + t, jb, nblk, start, cb, vecbase);
+        else decode_chunk<NDIM, K, false, T>(sp, sg, slut, st, sring + t, jb, nblk, start, cb, vecbase);
       }
     }
     r = t1;
   }
 }
 
-template <int NDIM, int K>
+template <int NDIM, int K, bool NS = false>
 cudaError_t launch_dec_t(const DecParams &p, const Geom &g, int sm_count, cudaStream_t s) {
-  constexpr int T = DecCta<NDIM, K>::T;
-  const int smem = (int)dec_smem_bytes<NDIM, K>();
+  constexpr int T = DecCta<NDIM, K, NS>::T;
+  const int smem = (int)dec_smem_bytes<NDIM, K, NS>();
   static LaunchCache cache;
   int per_sm = 0;
-  const cudaError_t e = cached_per_sm(k_decode<NDIM, K>, T, smem, cache, per_sm);
+  const cudaError_t e = cached_per_sm(k_decode<NDIM, K, NS>, T, smem, cache, per_sm);
   if (e != cudaSuccess) return e;
   // at most one CTA per unit: the units of a small field spread over SMs
   uint64_t grid = (uint64_t)sm_count * per_sm;
   if (grid > p.n_units) grid = p.n_units;
-  return launch_dep(k_decode<NDIM, K>, (unsigned)grid, (unsigned)T, (size_t)smem, s, p, g);
+  return launch_dep(k_decode<NDIM, K, NS>, (unsigned)grid, (unsigned)T, (size_t)smem, s, p, g);
+}
+
+// Whether the 16-bit relative plane state holds every value of the stream:
+// REL bound eb >= 2^-15 and no exceptions.  Then every quantized value q lies
+// within range * inv2eb + 2 <= 1 / (2 eb) + 2 <= 16386 of its block's
+// anchor: both are prequantized finite values in [lo, hi] (|x * inv2eb| <
+// 2^23, so each product and each rounding to an integer is off by at most
+// 1/2), and inv2eb = 1 / (2 eb (hi - lo)) up to float rounding.
+bool narrow_state_ok(const fz_header &h) {
+#if FZ_DEC_NARROW
+  return h.eb_mode == FZ_EB_REL && h.eb >= 1.0 / 32768.0 && h.n_exc == 0;
+#else
+  (void)h;
+  return false;
+#endif
 }
 
 }  // namespace
@@ -1089,7 +1157,9 @@ cudaError_t launch_decode_main(const uint8_t *d_in, const fz_header &h, float *d
   switch (g.ndim) {
     case 1: return k2 ? launch_dec_t<1, 2>(p, g, sm_count, s) : launch_dec_t<1, 1>(p, g, sm_count, s);
     case 2: return k2 ? launch_dec_t<2, 2>(p, g, sm_count, s) : launch_dec_t<2, 1>(p, g, sm_count, s);
-    default: return k2 ? launch_dec_t<3, 2>(p, g, sm_count, s) : launch_dec_t<3, 1>(p, g, sm_count, s);
+    default:
+      if (k2) return launch_dec_t<3, 2>(p, g, sm_count, s);
+      return narrow_state_ok(h) ? launch_dec_t<3, 1, true>(p, g, sm_count, s) : launch_dec_t<3, 1>(p, g, sm_count, s);
   }
 }
 

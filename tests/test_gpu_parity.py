@@ -125,6 +125,22 @@ def test_prequant_near_the_integer_limit(shape):
     _roundtrip_check(x, 0.4, "abs")
 
 
+@pytest.mark.parametrize("eb", [2.0 ** -15, 2.0 ** -16, 1e-4])
+@pytest.mark.parametrize("shape", [(40, 37, 70), (24, 24, 520)])
+def test_block_spread_at_the_narrow_state_limit(eb, shape):
+    """Blocks whose values sweep the whole value range along x, upwards in
+    half of them and downwards in the others, so that a block's quantized
+    values differ from its anchor by up to 1 / (2 eb): at REL 2^-15 the
+    decoder's 16-bit plane state (REL bounds of at least 2^-15, no
+    exceptions) is at its limit; at 2^-16 the spread needs the 32-bit state.
+    The long shape gives every decoding warp several work units."""
+    z, y, x = np.meshgrid(*(np.arange(n) for n in shape), indexing="ij")
+    ramp = (x % 8) / 7.0
+    up = ((x // 8 + y // 8 + z // 8) % 2) == 0
+    f = (np.where(up, ramp, 1.0 - ramp) * 1000.0 - 200.0).astype(np.float32)
+    _roundtrip_check(f, eb, "rel")
+
+
 def test_deterministic():
     x = torch.from_numpy(synth.grf3d(64, device="cpu").numpy()).cuda()
     a = fz.compress(x, 1e-4).cpu().numpy()
