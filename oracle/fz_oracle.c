@@ -997,12 +997,14 @@ static int shuf_decode_tile(const uint8_t *maps_b, const uint8_t *words_b, uint6
 
 /* Huffman chunk sizes of the format (symbols per chunk; chunk j covers
  * code-stream symbols [jC, min((j+1)C, Npad))): the block size, a power-of-
- * two multiple of it up to 4096, or, for 3D, 64 (one 8x8 plane of a block).
- * The chunking only decides where chunk_bits cuts the bitstream: the
- * bitstream itself does not depend on C. */
-static int chunk_valid(uint32_t ndim, uint64_t bsize, uint64_t C) {
+ * two multiple of it up to 4096, for 3D 64 (one 8x8 plane of a block), or,
+ * for 2D with the first-order Lorenzo predictor (pred 0), 128, 256 or 512
+ * (4, 8 or 16 rows of a 32x32 block).  The chunking only decides where
+ * chunk_bits cuts the bitstream: the bitstream itself does not depend on C. */
+static int chunk_valid(uint32_t ndim, uint64_t bsize, uint64_t C, uint32_t pred) {
   if (C == bsize) return 1;
   if (ndim == 3 && C == 64) return 1;
+  if (ndim == 2 && pred == 0 && (C == 128 || C == 256 || C == 512)) return 1;
   return C > bsize && C <= 4096 && (C % bsize) == 0 && (C & (C - 1)) == 0;
 }
 
@@ -1043,7 +1045,7 @@ int orc_compress_full(const float *x, uint32_t ndim, const uint64_t dims[3], uin
   } else {
     uint32_t b[3];
     orc_block_shape(ndim, b);
-    if (chunk && !chunk_valid(ndim, (uint64_t)b[0] * b[1] * b[2], chunk)) return ORC_EUNSUPPORTED;
+    if (chunk && !chunk_valid(ndim, (uint64_t)b[0] * b[1] * b[2], chunk, pred)) return ORC_EUNSUPPORTED;
   }
   const int sel = pred >= 16;
   uint64_t dd[3] = {1, 1, 1};
@@ -1354,7 +1356,8 @@ int orc_decompress(const uint8_t *in, uint64_t in_bytes, float *out, uint64_t ou
   uint64_t n_out = get_u64(in + H_NOUT), n_exc = get_u64(in + H_NEXC), tbits = get_u64(in + H_TBITS);
   uint64_t C = get_u32(in + H_CHUNK);
   const uint64_t npad = g.n_blocks * g.bsize;
-  if (nb != g.n_blocks || !(shuf ? C == SHUF_TILE : chunk_valid(ndim, g.bsize, C)) || nch != (npad + C - 1) / C)
+  if (nb != g.n_blocks || !(shuf ? C == SHUF_TILE : chunk_valid(ndim, g.bsize, C, pred)) ||
+      nch != (npad + C - 1) / C)
     return ORC_ECORRUPT;
   const uint64_t lens_bytes = shuf ? 4 * (npad / SHUF_RUN) : nsym;
   if (n_out > n || n_exc > n) return ORC_ECORRUPT;

@@ -553,7 +553,8 @@ def _sections(buf):
 
 
 @pytest.mark.parametrize("shape,chunks", [((40, 37, 70), (64, 1024, 2048, 4096)), ((9, 8, 17), (64, 4096)),
-                                          ((61, 450), (2048, 4096)), ((100003,), (2048, 4096))])
+                                          ((61, 450), (128, 256, 512, 2048, 4096)), ((100, 65), (128, 512)),
+                                          ((100003,), (2048, 4096))])
 def test_chunk_size_only_regroups_chunk_bits(shape, chunks):
     """Chunk j covers code-stream symbols [jC, min((j+1)C, Npad)): the
     bitstream is the same for every C, chunk j's stored length is the sum of
@@ -592,6 +593,12 @@ def test_chunk_size_rejects_bad_values_and_bad_lengths():
         assert e.value.code == oracle.EUNSUPPORTED
     with pytest.raises(oracle.OracleError):
         oracle.compress(synth.smooth_nd((5000,), 1).numpy(), 1e-3, chunk=64)  # 64 is for 3D blocks only
+    # chunks below the block: 2D first-order Lorenzo only
+    x2 = synth.smooth_nd((61, 450), seed=4).numpy()
+    for arr, C, k in ((synth.smooth_nd((5000,), 1).numpy(), 256, 1), (x2, 256, 2), (x2, 64, 1), (x2, 1000, 1)):
+        with pytest.raises(oracle.OracleError) as e:
+            oracle.compress(arr, 1e-3, lorenzo_k=k, chunk=C)
+        assert e.value.code == oracle.EUNSUPPORTED
     buf = oracle.compress(x, 1e-3, chunk=64)
     s = _sections(buf)
     cb = buf[s["off_cb"]:s["off_cb"] + 4 * s["n_chunks"]].view(np.uint32)
