@@ -561,7 +561,8 @@ def bench_configs(fz, dev, stream, args):
     throughput (CUDA events on the launching stream, L2 flushed before each
     timed call by writing 256 MiB), roofline fractions on forced bytes
     (compress 12N + S, decompress S + 4N), compression ratio and the largest
-    error over the bound."""
+    error over the bound.  An entry (eb, C) of a workload's bounds uses
+    Huffman chunks of C symbols instead of the block."""
     peak, _ = _peaks()
     scratch = torch.empty(64 << 20, dtype=torch.float32, device=dev)
     specs = [("grf512_mode_spectrum", "3D FP32 512^3 Gaussian random field, per-mode amplitude |k|^-5/6 "
@@ -570,7 +571,7 @@ def bench_configs(fz, dev, stream, args):
     specs.append(("hacc1d", "1D FP32 280,953,867 clustered particle coordinates in [0,256), seed 3",
                   lambda: synth.hacc1d(synth.HACC_N, seed=3, device=dev), [1e-2, 1e-3, 1e-4]))
     specs.append(("cesm2d", "2D FP32 1800x3600 lat/lon spherical-harmonic field (l <= 64) + noise, seed 4",
-                  lambda: synth.cesm2d(1800, 3600, seed=4).to(dev), [1e-2, 1e-3, 1e-4]))
+                  lambda: synth.cesm2d(1800, 3600, seed=4).to(dev), [1e-2, 1e-3, 1e-4, (1e-4, 256), (1e-4, 128)]))
     out = []
     for key, desc, make, ebs in specs:
         x = make().contiguous()
@@ -578,8 +579,9 @@ def bench_configs(fz, dev, stream, args):
         rng = float(x.max()) - float(x.min())
         ob = torch.empty(fz.compress_bound(x.shape), dtype=torch.uint8, device=dev)
         y = torch.empty_like(x)
-        for eb in ebs:
-            buf = fz.compress(x, eb, out=ob)
+        for spec in ebs:
+            eb, chunk = spec if isinstance(spec, tuple) else (spec, 0)
+            buf = fz.compress(x, eb, out=ob, chunk=chunk)
             fz.decompress(buf, out=y)
             err = float((y.double() - x.double()).abs().max()) / (eb * rng)
             S = buf.numel()
@@ -588,7 +590,7 @@ def bench_configs(fz, dev, stream, args):
                 _flush_l2(scratch)
                 e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
                 e0.record(stream)
-                buf = fz.compress(x, eb, out=ob)
+                buf = fz.compress(x, eb, out=ob, chunk=chunk)
                 e1.record(stream)
                 _flush_l2(scratch)
                 e2.record(stream)
@@ -601,6 +603,7 @@ def bench_configs(fz, dev, stream, args):
                     td.append(e2.elapsed_time(e3))
             mc, md = statistics.median(tc), statistics.median(td)
             out.append({"config": key, "workload": desc, "values": N, "eb_mode": "rel", "eb": eb,
+                        "chunk": chunk or "block",
                         "compress_gbs": round(4 * N / (mc * 1e-3) / 1e9, 2),
                         "decompress_gbs": round(4 * N / (md * 1e-3) / 1e9, 2),
                         "compress_roofline_frac": round((12 * N + S) / (mc * 1e-3) / 1e9 / peak, 4),

@@ -81,7 +81,12 @@ typedef struct {
   uint32_t block[3];           /* predictor block extents x, y, z; all 0 = the default for ndim (1D 1024,
                                   2D 32x32, 3D 8x8x8), which is also the only shape this build accepts
                                   (others: FZ_EUNSUPPORTED); axes beyond ndim must be 0 or 1 */
-  uint32_t chunk;              /* symbols per Huffman chunk; 0 = the block size */
+  uint32_t chunk;              /* symbols per Huffman chunk (§3.2 chunked encoder; chunk j holds code-stream
+                                  symbols [jC, (j+1)C)); 0 = the block size.  Also: a power-of-two multiple
+                                  of the block up to 4096; 3D: 64 (one 8x8 plane of a block); 2D first-order
+                                  Lorenzo: 128, 256 or 512 (4, 8 or 16 rows of a 32x32 block, decoded by
+                                  neighbouring lanes that pass each other the column state); Lorenzo
+                                  predictors only for chunks other than the block; else FZ_EUNSUPPORTED */
   uint32_t encoder;            /* FZ_ENC_HUFFMAN (0) or FZ_ENC_SHUFFLE (1, the bit-shuffle + zero-word encoder of
                                   FZMod-Speed, §3.3; Lorenzo predictors only, chunk 0 or 1024) */
   const void *selector_weights;/* device pointer to a selector weight blob (FZ_SEL_MLP only) */
@@ -110,7 +115,7 @@ typedef struct {
   uint32_t radius;
   uint32_t block[3];
   uint32_t predictor;          /* fz_predictor used for every block, or FZ_SEL_* when ids are stored */
-  uint32_t chunk;              /* symbols per Huffman chunk (= block size) */
+  uint32_t chunk;              /* symbols per Huffman chunk (see fz_pipeline.chunk) */
   uint32_t reserved0;
   uint64_t n_blocks, n_chunks, n_out, n_exc, total_bits;
   uint64_t off_lens, off_ids, off_anchors, off_chunk_bits, off_out_idx, off_out_val,

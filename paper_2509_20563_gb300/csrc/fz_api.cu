@@ -168,7 +168,7 @@ fz_status parse_pipe(const fz_pipeline *pipe, uint32_t ndim, Req &r) {
       const uint64_t d1[3] = {1, 1, 1};
       Geom g;
       make_geom(ndim, d1, g);
-      if (!chunk_supported(ndim, g.bsize, r.chunk)) return FZ_EUNSUPPORTED;
+      if (!chunk_supported(ndim, g.bsize, r.chunk, pipe->predictor)) return FZ_EUNSUPPORTED;
       if (r.chunk != g.bsize && pipe->predictor > FZ_PRED_LORENZO2) return FZ_EUNSUPPORTED;
     }
   }
@@ -232,7 +232,7 @@ fz_status check_header(const fz_header &h, uint64_t in_bytes, Geom &g) {
               !fits(h.off_ids, (h.n_blocks + 3) / 4) || h.off_ids + (h.n_blocks + 3) / 4 > h.off_anchors))
     return FZ_ECORRUPT;
   if (h.block[0] != g.bx || h.block[1] != g.by || h.block[2] != g.bz) return FZ_ECORRUPT;
-  if (shuf ? (h.chunk != 1024 || h.predictor > FZ_PRED_LORENZO2) : !chunk_supported(h.ndim, g.bsize, h.chunk))
+  if (shuf ? (h.chunk != 1024 || h.predictor > FZ_PRED_LORENZO2) : !chunk_supported(h.ndim, g.bsize, h.chunk, h.predictor))
     return FZ_ECORRUPT;
   if (h.chunk != g.bsize && h.predictor > FZ_PRED_LORENZO2) return FZ_EUNSUPPORTED;
   if (shuf && (h.total_bits & 31u)) return FZ_ECORRUPT;
@@ -489,11 +489,11 @@ fz_status fz_decompress(fz_ctx *ctx, const void *d_in, uint64_t in_bytes, const 
   // always takes it (its code decoder matches every outlier code to the list
   // through it), the per-block predictor decoder whenever there are
   // outliers; for Lorenzo streams it pays off when most blocks hold outliers
-  // (plane-parallel streams with 64-symbol chunks and bit-shuffle streams
-  // locate outliers per plane or chunk instead).
+  // (streams with chunks below the block and bit-shuffle streams locate
+  // outliers per plane or chunk instead).
   const bool gipath = h.predictor == FZ_PRED_GINTERP;
   const bool ofirst = gipath || (selpath && h.n_out) || (!selpath && h.n_out > h.n_blocks / 8 &&
-                                             !(h.ndim == 3 && h.chunk == 64) && h.flags != FZ_FLAG_SHUF);
+                                             h.chunk >= g.bsize && h.flags != FZ_FLAG_SHUF);
   const size_t o_err = take(dec_offset_zero_bytes(h)), o_gsum = take(8 * n_units), o_lut = take(2u << kLutBits),
                o_codes = selpath ? take(2 * g.npad) : 0, o_ofirst = ofirst ? take(4 * h.n_blocks) : 0,
                o_q4 = gipath ? take(4 * ginterp_level_values(h, 4)) : 0,

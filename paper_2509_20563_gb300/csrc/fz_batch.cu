@@ -334,7 +334,7 @@ fz_status fz_compress_batch(fz_ctx *ctx, uint32_t n, const float *const *d_in, c
     const uint64_t d3[3] = {dj[0], ndim[j] >= 2 ? dj[1] : 1, ndim[j] >= 3 ? dj[2] : 1};
     make_geom(ndim[j], d3, geo[j]);
     if (!positions_fit(geo[j])) return FZ_EUNSUPPORTED;
-    if (chunk && (chunk < geo[j].bsize || !chunk_supported(ndim[j], geo[j].bsize, chunk))) return FZ_EUNSUPPORTED;
+    if (chunk && (chunk < geo[j].bsize || !chunk_supported(ndim[j], geo[j].bsize, chunk, pred))) return FZ_EUNSUPPORTED;
     CompressWs tmp;
     zsz[j] = layout_compress_split(geo[j], nullptr, nullptr, tmp, &rsz[j]);
     ztot += zsz[j];

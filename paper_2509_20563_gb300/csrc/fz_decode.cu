@@ -635,6 +635,188 @@ __device__ __forceinline__ void decode_units(const DecParams &p, const Geom &g, 
   }
 }
 
+// ---------------------------------------------------------------- 2D chunks below the block
+// A 2D first-order Lorenzo stream whose chunks are 4, 8 or 16 rows of a
+// 32x32 block (C = 128, 256 or 512): lane l of work unit u decodes chunk
+// 32u + l, rows RPC s .. RPC s + RPC - 1 (RPC = C / 32) of its block, s the
+// chunk's index within the block.  The state a chunk starts from (the
+// values of the row above it, per column) depends on the chunks above it,
+// which neighbouring lanes of the same warp decode.  So every lane decodes
+// its chunk into a shared-memory buffer of residuals (16-bit) while it sums
+// its column totals; each lane then adds up the totals of the chunks above
+// its own (read from their lanes' state columns) into its starting state;
+// and reconstructs its rows from the buffer.  Every lane takes part in the
+// warp-wide steps, with or without a chunk.  The CTA holds 384 x 128 / C
+// threads, so the buffers take 96 KB at every C.
+constexpr int kSub2dWords = 32;  // column state per thread (first order)
+
+template <int C>
+struct Sub2d {
+  static constexpr int T = 384 * 128 / C;  // 384, 192 or 96 threads
+  static constexpr int kSlots = C / 8;     // 16-byte buffer slots (eight residuals) per thread
+  static constexpr size_t kSmem =
+      sizeof(uint16_t) * kLutSize + sizeof(int32_t) * (size_t)(kSub2dWords + kRing) * T + 16 * (size_t)kSlots * T;
+};
+
+template <int C, bool EXC>
+__device__ __forceinline__ void decode_sub2d_chunk(const DecParams &p, const Geom &g, const uint16_t *slut,
+                                                   int32_t *sstate, uint32_t *ring, int4 *buf, uint64_t j,
+                                                   uint64_t start, uint32_t cbits, bool live, bool vecbase) {
+  constexpr int T = Sub2d<C>::T;
+  constexpr uint32_t kCpb = 1024 / C;  // chunks per block
+  constexpr uint32_t kNg = C / 8;      // groups of eight codes per chunk
+  const int t = threadIdx.x;
+  const uint64_t jb = j / kCpb;
+  const uint32_t sub = (uint32_t)(j % kCpb);
+  const uint32_t pos0 = (uint32_t)(jb * 1024);  // the block's first position
+  const uint32_t cpos = pos0 + sub * C;         // the chunk's first position
+  int32_t *st = st_thread(sstate, t);
+  const uint32_t j32 = (uint32_t)jb;
+  const uint32_t X0 = (j32 % g.nbx) * g.bx, Y0 = (j32 / g.nbx) * g.by;
+  const int32_t anchor = live ? __ldg(p.anchors + jb) : 0;
+  bool bad = false;
+  // ---- pass 1: decode into the buffer, sum the column totals (row prefix
+  // sums added per column)
+  for (int i = 0; i < kSub2dWords / 4; ++i) reinterpret_cast<int4 *>(st)[i * T] = make_int4(0, 0, 0, 0);
+  if (live) {
+    BitReader<T> br;
+    br.init(p.words, p.n_words, start, cbits, ring);
+    const uint32_t start_off = br.off;
+    Side sd;
+    init_side(p, sd, cpos);
+    int32_t r1 = 0;
+#pragma unroll 1
+    for (uint32_t gi = 0; gi < kNg; ++gi) {
+      int32_t d[8];
+      const bool zero = br.group8(slut, p.R, d);
+      buf[gi * T] = make_int4((int32_t)__byte_perm(d[0], d[1], 0x5410), (int32_t)__byte_perm(d[2], d[3], 0x5410),
+                              (int32_t)__byte_perm(d[4], d[5], 0x5410), (int32_t)__byte_perm(d[6], d[7], 0x5410));
+      if (zero) fix_outliers(p, sd, j, cpos, cpos + gi * 8, d, bad);
+      if (gi == 0 && sub == 0) d[0] += anchor;  // the block origin's residual is its anchor
+      const uint32_t x8 = gi & 3u;
+      r1 = x8 ? r1 : 0;
+      int32_t c[8];
+      st_load8<T>(st, (int)x8 * 8, c);
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        r1 += d[u];
+        c[u] += r1;
+      }
+      st_store8<T>(st, (int)x8 * 8, c);
+    }
+    asm volatile("cp.async.wait_all;\n" ::: "memory");
+    if (br.consumed(start_off) != cbits) bad = true;
+  }
+  __syncwarp();
+  // ---- starting state: the totals of the chunks above this one in the block
+  // (lanes t - sub .. t - 1 of this warp), gathered before any lane writes
+  int32_t a[kSub2dWords];
+#pragma unroll
+  for (int x = 0; x < kSub2dWords; ++x) a[x] = 0;
+  for (uint32_t k = 1; k <= sub; ++k) {
+    const int32_t *o = st_thread(sstate, t - (int)k);
+#pragma unroll
+    for (int w0 = 0; w0 < kSub2dWords; w0 += 8) {
+      int32_t c[8];
+      st_load8<T>(o, w0, c);
+#pragma unroll
+      for (int u = 0; u < 8; ++u) a[w0 + u] += c[u];
+    }
+  }
+  __syncwarp();
+#pragma unroll
+  for (int w0 = 0; w0 < kSub2dWords; w0 += 8) {
+    int32_t c[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) c[u] = a[w0 + u];
+    st_store8<T>(st, w0, c);
+  }
+  // ---- pass 2: reconstruct the chunk's rows from the buffered residuals
+  if (live) {
+    Side sd;
+    init_side(p, sd, cpos);
+    Prefix pf;
+    pf.r1 = 0;
+    pf.r2 = 0;
+#pragma unroll 1
+    for (uint32_t gi = 0; gi < kNg; ++gi) {
+      const int4 w = buf[gi * T];
+      const uint32_t wv[4] = {(uint32_t)w.x, (uint32_t)w.y, (uint32_t)w.z, (uint32_t)w.w};
+      int32_t d[8];
+      bool zero = false;
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        d[2 * i] = (int32_t)(wv[i] << 16) >> 16;
+        d[2 * i + 1] = (int32_t)wv[i] >> 16;
+        zero = zero || d[2 * i] == -p.R || d[2 * i + 1] == -p.R;
+      }
+      if (zero) fix_outliers(p, sd, j, cpos, cpos + gi * 8, d, bad);
+      if (gi == 0 && sub == 0) d[0] += anchor;
+      consume<2, 1, EXC, T>(p, g, sd, pf, st, (int)(sub * kNg + gi), d, pos0, X0, Y0, 0, vecbase, anchor);
+    }
+  }
+  if (bad) dec_err(p.err, FZ_ECORRUPT);
+}
+
+template <int C>
+__global__ void __launch_bounds__(Sub2d<C>::T) k_decode_sub2d(DecParams p, Geom g) {
+  constexpr int T = Sub2d<C>::T;
+  extern __shared__ __align__(16) unsigned char d_smem[];
+  uint16_t *slut = reinterpret_cast<uint16_t *>(d_smem);
+  int32_t *sstate = reinterpret_cast<int32_t *>(d_smem + sizeof(uint16_t) * kLutSize);
+  uint32_t *sring = reinterpret_cast<uint32_t *>(sstate + kSub2dWords * T);
+  int4 *sbuf = reinterpret_cast<int4 *>(sring + kRing * T);
+  __shared__ LutBuild lb;
+  const bool ok = build_lut<T>(p.lens, p.nsym, slut, lb);
+  dep_wait();  // the unit offsets
+  if (ok) {
+    __syncthreads();
+    const int t = threadIdx.x, lane = t & 31;
+    const bool vecbase = (g.nx & 3u) == 0 && (((uintptr_t)p.out & 15u) == 0);
+    for (;;) {
+      const uint32_t u = claim_unit(p.err + 1);
+      if (u >= p.n_units) break;
+      uint32_t cb;
+      const uint64_t start = unit_start(p.chunk_bits, p.goff, p.n_chunks, u, cb);
+      const uint64_t j = (uint64_t)u * kDecUnit + lane;
+      const bool live = j < p.n_chunks;
+      if (p.n_exc) decode_sub2d_chunk<C, true>(p, g, slut, sstate, sring + t, sbuf + t, j, start, cb, live, vecbase);
+      else decode_sub2d_chunk<C, false>(p, g, slut, sstate, sring + t, sbuf + t, j, start, cb, live, vecbase);
+    }
+  } else if (threadIdx.x == 0) {
+    dec_err(p.err, FZ_ECORRUPT);
+  }
+  __syncthreads();
+  if (p.h_err && threadIdx.x == 0) {
+    __threadfence();
+    if (atomicAdd(p.err + 2, 1u) == gridDim.x - 1) {
+      __threadfence();
+      *reinterpret_cast<volatile uint32_t *>(p.h_err) = atomicAdd(p.err, 0u);
+      __threadfence_system();
+    }
+  }
+}
+
+template <int C>
+cudaError_t launch_sub2d_t(const DecParams &p, const Geom &g, int sm_count, cudaStream_t s) {
+  constexpr int T = Sub2d<C>::T;
+  const int smem = (int)Sub2d<C>::kSmem;
+  static LaunchCache cache;
+  int per_sm = 0;
+  const cudaError_t e = cached_per_sm(k_decode_sub2d<C>, T, smem, cache, per_sm);
+  if (e != cudaSuccess) return e;
+  uint64_t grid = (uint64_t)sm_count * per_sm;
+  const uint64_t need = (p.n_units + T / 32 - 1) / (T / 32);  // CTAs whose warps all have a unit
+  if (grid > need) grid = need;
+  return launch_dep(k_decode_sub2d<C>, (unsigned)grid, (unsigned)T, (size_t)smem, s, p, g);
+}
+
+cudaError_t launch_sub2d(const DecParams &p, const Geom &g, int sm_count, cudaStream_t s) {
+  if (g.chunk == 128) return launch_sub2d_t<128>(p, g, sm_count, s);
+  if (g.chunk == 256) return launch_sub2d_t<256>(p, g, sm_count, s);
+  return launch_sub2d_t<512>(p, g, sm_count, s);
+}
+
 // ---------------------------------------------------------------- 64-symbol chunks (3D)
 // A stream whose Huffman chunk is one 8x8 plane of a block (64 symbols) is
 // decoded plane-parallel: a work unit of 32 chunks is 4 blocks x 8 planes,
@@ -1150,6 +1332,10 @@ cudaError_t launch_decode_main(const uint8_t *d_in, const fz_header &h, float *d
   p.R = (int32_t)h.radius;
   const bool k2 = h.predictor == FZ_PRED_LORENZO2;
   if (h.flags == FZ_FLAG_SHUF) return launch_shuf_decode(d_in, h, d_out, ws, s, sm_count);
+  if (g.ndim == 2 && g.chunk < g.bsize) {
+    p.ofirst = nullptr;  // outliers are located per chunk by search
+    return launch_sub2d(p, g, sm_count, s);
+  }
   if (g.ndim == 3 && g.chunk == 64) {
     p.ofirst = nullptr;  // outliers are located per plane by search
     return k2 ? launch_planes_t<2>(p, g, sm_count, s) : launch_planes_t<1>(p, g, sm_count, s);

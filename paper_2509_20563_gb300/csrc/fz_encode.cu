@@ -45,16 +45,19 @@ struct EncSmem {
   unsigned long long base;
 };
 
-// Stored chunk lengths below one block: with 64-symbol chunks in 512-symbol
-// blocks (16 codes per lane) the lanes 4s..4s+3 hold sub-chunk s, and the
+// Stored chunk lengths below one block: with chunks of C symbols and PER
+// codes per lane (3D: C = 64, PER = 16; 2D: C = 128, 256, 512, PER = 32) the
+// lanes LPC s .. LPC s + LPC - 1 (LPC = C / PER) hold sub-chunk s, and the
 // last of them stores the difference of the inclusive scan.  Every lane of
-// the warp calls it.
+// the warp calls it; chunks of a block or more store nothing here.
 template <int PER>
 __device__ __forceinline__ void store_sub_chunks(uint32_t *chunk_bits, uint64_t block, uint32_t incl, int lane,
                                                  uint32_t chunk, bool valid) {
-  if (PER != 16 || chunk != 64) return;
-  const uint32_t prev = __shfl_up_sync(0xffffffffu, incl, 4);
-  if (valid && (lane & 3) == 3) chunk_bits[block * 8 + (lane >> 2)] = lane >= 4 ? incl - prev : incl;
+  if (chunk >= 32u * PER || chunk < 2u * PER) return;
+  const uint32_t lpc = chunk / PER;  // a power of two: 2 to 16 lanes
+  const uint32_t prev = __shfl_up_sync(0xffffffffu, incl, lpc);
+  if (valid && ((uint32_t)lane & (lpc - 1)) == lpc - 1)
+    chunk_bits[block * (32 / lpc) + (uint32_t)lane / lpc] = (uint32_t)lane >= lpc ? incl - prev : incl;
 }
 
 // Stored chunk lengths above one block (chunk = k blocks, k = 2, 4, 8 divides
@@ -376,7 +379,7 @@ __global__ void __launch_bounds__(kEncThreads, CH == 512 ? FZ_ENC_MINB : FZ_ENC_
       wt[warp] = incl;
       if (CM == 0 && valid) chunk_bits[blk] = incl;
     }
-    if (CM == 1) store_sub_chunks<PER>(chunk_bits, blk, incl, lane, 64u, valid);
+    if (CM == 1) store_sub_chunks<PER>(chunk_bits, blk, incl, lane, g.chunk, valid);
     __syncthreads();
     if (FZ_ENC_ZB && FZ_ENC_NOEND) {
       // every thread has finished the previous step (its store included)
@@ -534,6 +537,7 @@ cudaError_t launch_encode(const Geom &g, const CompressWs &ws, uint8_t *d_out, c
     return launch_t<512, 2>(g, ws, d_out, s, sm_count);
   }
   if (cm == 0) return launch_t<1024, 0>(g, ws, d_out, s, sm_count);
+  if (cm == 1) return launch_t<1024, 1>(g, ws, d_out, s, sm_count);
   return launch_t<1024, 2>(g, ws, d_out, s, sm_count);
 }
 

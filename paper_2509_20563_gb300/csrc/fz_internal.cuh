@@ -96,11 +96,14 @@ inline __host__ __device__ void make_geom(uint32_t ndim, const uint64_t dims[3],
 }
 
 // Huffman chunk sizes of the format: the block size, a power-of-two
-// multiple of it up to 4096, or, for 3D blocks, 64 (one 8x8 plane).  Only
-// first- and second-order Lorenzo streams use a chunk other than the block.
-inline __host__ __device__ bool chunk_supported(uint32_t ndim, uint32_t bsize, uint32_t C) {
+// multiple of it up to 4096, for 3D blocks 64 (one 8x8 plane), or, for 2D
+// first-order Lorenzo streams, 128, 256 or 512 (4, 8 or 16 rows of a 32x32
+// block).  Only first- and second-order Lorenzo streams use a chunk other
+// than the block.
+inline __host__ __device__ bool chunk_supported(uint32_t ndim, uint32_t bsize, uint32_t C, uint32_t pred) {
   if (C == bsize) return true;
   if (ndim == 3 && C == 64) return true;
+  if (ndim == 2 && pred == FZ_PRED_LORENZO1 && (C == 128 || C == 256 || C == 512)) return true;
   return C > bsize && C <= 4096 && C % bsize == 0 && (C & (C - 1)) == 0;
 }
 

@@ -299,20 +299,20 @@ def test_bad_arguments():
 
 
 # ---------------------------------------------------------------- full workload sizes
-def _full_check(x, eb, predictor="lorenzo1", weights=None):
+def _full_check(x, eb, predictor="lorenzo1", weights=None, chunk=0):
     """Full workload size: GPU stream == oracle stream byte for byte, the
     GPU reconstruction == the oracle's reconstruction bit for bit (the
     decoder's multi-unit path: every warp claims several work units here),
     and the bound on every value."""
     xd = x.cuda() if not x.is_cuda else x
     wd = torch.from_numpy(weights.view(np.int16)).cuda() if weights is not None else None
-    buf = fz.compress(xd, eb, predictor=predictor, selector_weights=wd)
+    buf = fz.compress(xd, eb, predictor=predictor, selector_weights=wd, chunk=chunk)
     y = fz.decompress(buf)
     f = xd[torch.isfinite(xd)]
     eba = eb * (float(f.max()) - float(f.min()))
     assert float((y.double() - xd.double()).abs().max()) <= eba
     xh = xd.cpu().numpy()
-    ref = oracle.compress(xh, eb, predictor=predictor, weights=weights)
+    ref = oracle.compress(xh, eb, predictor=predictor, weights=weights, chunk=chunk)
     got = buf.cpu().numpy()
     assert got.size == ref.size and np.array_equal(got, ref)
     del buf
@@ -394,6 +394,55 @@ def test_chunk_sizes_bit_exact(shape, chunks, predictor):
         assert np.array_equal(_bits(y), _bits(yref)), C
         y2 = fz.decompress(torch.from_numpy(ref).cuda()).cpu().numpy()
         assert np.array_equal(_bits(y2), _bits(yref)), C
+
+
+@pytest.mark.parametrize("shape", [(61, 450), (100, 65), (33, 300), (256, 1100)])
+def test_chunks_below_the_block_2d(shape):
+    """2D first-order Lorenzo streams with chunks of 4, 8 or 16 block rows:
+    byte-identical streams, and reconstructions bit-identical to the
+    oracle's by the two-pass sub-chunk decoder (its lanes hand each other
+    the column state of the rows above their chunk), with exceptions (NaN,
+    infinities) and, at radius 4, outliers in most chunks; second-order
+    Lorenzo streams reject these chunks before any launch."""
+    x = synth.smooth_nd(shape, seed=sum(shape) + 3).numpy().copy()
+    flat = x.reshape(-1)
+    flat[7] = np.nan
+    flat[flat.size // 2] = np.inf
+    flat[flat.size // 3] = -np.inf
+    xd = torch.from_numpy(x).cuda()
+    for C in (128, 256, 512):
+        for radius in (512, 4):
+            ref = oracle.compress(x, 1e-3, radius=radius, chunk=C)
+            buf = fz.compress(xd, 1e-3, radius=radius, chunk=C)
+            got = buf.cpu().numpy()
+            assert got.size == ref.size and np.array_equal(got, ref), (C, radius)
+            yref = oracle.decompress(ref)
+            y = fz.decompress(buf).cpu().numpy()
+            assert np.array_equal(_bits(y), _bits(yref)), (C, radius)
+    with pytest.raises(fz.FzError) as e:
+        fz.compress(xd, 1e-3, predictor="lorenzo2", chunk=256)
+    assert e.value.code == 7
+
+
+def test_chunks_below_the_block_2d_corruption():
+    """One bit moved between the stored lengths of two neighbouring
+    sub-block chunks (total unchanged) is reported as a corrupt stream."""
+    x = synth.smooth_nd((61, 450), seed=9).numpy()
+    ref = oracle.compress(x, 1e-3, chunk=256)
+    h = ref[:256].tobytes()
+    off_cb = int.from_bytes(h[160:168], "little")
+    t = ref.copy()
+    cb = t[off_cb:off_cb + 64].view(np.uint32)
+    cb[5] += 1
+    cb[6] -= 1
+    with pytest.raises(fz.FzError) as e:
+        fz.decompress(torch.from_numpy(t).cuda())
+    assert e.value.code == 5
+
+
+@pytest.mark.parametrize("chunk", [128, 256])
+def test_full_cesm_2d_chunks_below_the_block(chunk):
+    _full_check(synth.cesm2d(1800, 3600, seed=4), 1e-4, chunk=chunk)
 
 
 def test_chunk64_outliers_and_corruption():
