@@ -303,28 +303,32 @@ __global__ void __launch_bounds__(kEncThreads, CH == 512 ? FZ_ENC_MINB : FZ_ENC_
   constexpr int PER = CH / 32;
   constexpr int D = FZ_ENC_DEPTH;
   __shared__ PipeSmem<CH, D> sm;
-  dep_wait();
-  dep_trigger();
   Ctl *ctl = ws.ctl;
-  if (ctl->mode != kModeNormal) return;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const fz_header &h = ctl->res.hdr;
-  uint32_t *chunk_bits = reinterpret_cast<uint32_t *>(d_out + h.off_chunk_bits);
-  uint32_t *words = reinterpret_cast<uint32_t *>(d_out + h.off_bits);
   const uint64_t n_blk = g.n_blocks;
   const uint64_t n_tiles = (n_blk + kEncWarps - 1) / kEncWarps;
-  const uint64_t wlimit = (ctl->total_bits + 31) / 32;
-  for (int i = tid; i < kMaxSym; i += kEncThreads) sm.senc[i] = ctl->enc[i];
   constexpr int NI = PipeSmem<CH, D>::kImages;
+  // Before the wait for the codebook: the first ticket, the images cleared
+  // and the first tile's codes loaded (the quantizer, which wrote them, has
+  // finished once the codebook runs; the ticket counter was zeroed before it)
   for (int i = tid; i < NI * PipeSmem<CH, D>::kMaxWords; i += kEncThreads) (&sm.lw[0][0])[i] = 0;
-  uint32_t stored_bits = 0;  // bits of the tile stored in the previous step (FZ_ENC_ZB)
-  int par = 0;               // step parity (FZ_ENC_NOEND)
   if (tid == 0) sm.tk[0] = atomicAdd(&ctl->encode_ticket, 1u);
   __syncthreads();
   uint64_t tile = sm.tk[0];
   // the codes of the tile in hand are loaded one step ahead of their use
   uint4 raw[PER / 8];
   if (tile < n_tiles && tile * kEncWarps + warp < n_blk) load_lane_codes<PER>(ws.codes, tile * kEncWarps + warp, CH, lane, raw);
+  dep_wait();  // the codebook: table, header, mode, total bits
+  dep_trigger();
+  if (ctl->mode != kModeNormal) return;
+  const fz_header &h = ctl->res.hdr;
+  uint32_t *chunk_bits = reinterpret_cast<uint32_t *>(d_out + h.off_chunk_bits);
+  uint32_t *words = reinterpret_cast<uint32_t *>(d_out + h.off_bits);
+  const uint64_t wlimit = (ctl->total_bits + 31) / 32;
+  for (int i = tid; i < kMaxSym; i += kEncThreads) sm.senc[i] = ctl->enc[i];
+  uint32_t stored_bits = 0;  // bits of the tile stored in the previous step (FZ_ENC_ZB)
+  int par = 0;               // step parity (FZ_ENC_NOEND)
+  __syncthreads();  // the codeword table is in place
   // tiles packed but not yet stored, oldest first, and their bit totals
   uint64_t pend[D - 1];
   uint32_t pend_bits[D - 1];
