@@ -35,6 +35,7 @@ import statistics
 import subprocess
 import sys
 import tempfile
+import threading
 import time
 
 import numpy as np
@@ -64,6 +65,7 @@ KERNEL_SOURCES = {
 NCU_DRAM_BYTES_512 = {"decode": (251098112 + 478425856, "cfd3b8398ccfb98f", "8aa30d1")}
 METRIC = "compress/decompress GB/s vs HBM peak at REL 1e-4; CR learned vs plain"
 PROFILE_EVERY = 8  # timed steps per step that records the library's stage events
+E2E_WORKERS = 4  # host threads (each with its own context and stream) of the end-to-end leg
 
 
 def source_digest(kernel: str) -> str:
@@ -417,9 +419,10 @@ def run_fz(args, rank, world, local_rank):
            "gpu_launches": int(launches), "clocks": clk}
     # end to end through the C ABI with host buffers: H2D input, compress, D2H stream,
     # H2D stream, decompress, D2H reconstruction -- copies inside the timed region.
-    # Steps alternate between two streams with their own buffers, so one step's
-    # reconstruction copy to the host overlaps the next step's input copy (the
-    # library calls themselves run one after another: each waits for its stream).
+    # Each library call waits for its own stream, so the steps run on
+    # E2E_WORKERS host threads, each with its own context (workspace), stream
+    # and buffers, the way a caller with several workers would: one worker's
+    # copies overlap the others' kernels and copies.
     if args.e2e_steps > 0:
         # pinned host buffers on the GPU's own NUMA node (the thread runs there
         # while they are allocated and copied): a far node halves the link
@@ -427,34 +430,43 @@ def run_fz(args, rank, world, local_rank):
         hx = torch.empty(x.shape, dtype=torch.float32, pin_memory=True)
         hx.copy_(x)
         slots = []
-        for _ in range(2):
+        for k in range(E2E_WORKERS):
             sl = {"s": torch.cuda.Stream(dev), "xd": torch.empty_like(x), "buf": torch.empty_like(buf),
                   "bd": torch.empty_like(buf), "y": torch.empty_like(x),
                   "hs": torch.empty(bound, dtype=torch.uint8, pin_memory=True),
-                  "hy": torch.empty(x.shape, dtype=torch.float32, pin_memory=True)}
+                  "hy": torch.empty(x.shape, dtype=torch.float32, pin_memory=True),
+                  "ctx": ctx if k == 0 else fz.Context(local_rank), "nbytes": C.c_uint64(),
+                  "hdr": C.create_string_buffer(256)}
             sl["sp"] = C.c_void_p(sl["s"].cuda_stream)
             slots.append(sl)
 
-        def e2e_step(i):
-            sl = slots[i % 2]
+        def e2e_step(sl):
             with torch.cuda.stream(sl["s"]):
                 sl["xd"].copy_(hx, non_blocking=True)
-            st = fz_compress(ctx.handle, C.c_void_p(sl["xd"].data_ptr()), 3, dims, 1, args.eb, C.byref(pipe),
-                             C.c_void_p(sl["buf"].data_ptr()), bound, C.byref(nbytes), hdr, sl["sp"])
+            st = fz_compress(sl["ctx"].handle, C.c_void_p(sl["xd"].data_ptr()), 3, dims, 1, args.eb, C.byref(pipe),
+                             C.c_void_p(sl["buf"].data_ptr()), bound, C.byref(sl["nbytes"]), sl["hdr"], sl["sp"])
             assert st == 0
-            nb = nbytes.value
+            nb = sl["nbytes"].value
             with torch.cuda.stream(sl["s"]):
                 sl["hs"][:nb].copy_(sl["buf"][:nb], non_blocking=True)
                 sl["bd"][:nb].copy_(sl["hs"][:nb], non_blocking=True)
-            st = fz_decompress(ctx.handle, C.c_void_p(sl["bd"].data_ptr()), nb, hdr, C.c_void_p(sl["y"].data_ptr()),
-                               N, sl["sp"])
+            st = fz_decompress(sl["ctx"].handle, C.c_void_p(sl["bd"].data_ptr()), nb, sl["hdr"],
+                               C.c_void_p(sl["y"].data_ptr()), N, sl["sp"])
             assert st == 0
             with torch.cuda.stream(sl["s"]):
                 sl["hy"].copy_(sl["y"], non_blocking=True)
             return nb
 
-        for i in range(2):
-            e2e_step(i)
+        def worker(sl, n_steps, errs):
+            try:
+                torch.cuda.set_device(dev)
+                for _ in range(n_steps):
+                    e2e_step(sl)
+            except BaseException as exc:  # reported by the main thread
+                errs.append(exc)
+
+        for sl in slots:  # warm-up, one worker after the other (first launches set up the library)
+            e2e_step(sl)
         torch.cuda.synchronize(dev)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         if world > 1:
@@ -462,25 +474,37 @@ def run_fz(args, rank, world, local_rank):
         e0.record(stream)
         for sl in slots:
             sl["s"].wait_stream(stream)
-        for i in range(args.e2e_steps):
-            nb = e2e_step(i)
+        errs = []
+        share = [args.e2e_steps // E2E_WORKERS + (1 if k < args.e2e_steps % E2E_WORKERS else 0)
+                 for k in range(E2E_WORKERS)]
+        threads = [threading.Thread(target=worker, args=(sl, n, errs)) for sl, n in zip(slots, share)]
+        for th in threads:
+            th.start()
+        for th in threads:
+            th.join()
+        if errs:
+            raise errs[0]
         for sl in slots:
             stream.wait_stream(sl["s"])
         e1.record(stream)
         torch.cuda.synchronize(dev)
         ems = e0.elapsed_time(e1)
         ems = max_over_ranks(ems, world, dev)
+        nb = slots[0]["nbytes"].value
         ok = all(torch.equal(sl["y"], y) for sl in slots)  # every step reconstructs the same field
         assert ok
         res["e2e"] = {"value": round(aggregate_gbs(args.e2e_steps, world, 4 * N, ems), 2), "unit": "GB/s",
                       "h2d_bytes_per_step": 4 * N + nb, "d2h_bytes_per_step": nb + 4 * N,
-                      "steps": args.e2e_steps, "streams": 2, "host_numa_node": numa}
+                      "steps": args.e2e_steps, "streams": E2E_WORKERS, "host_threads": E2E_WORKERS,
+                      "contexts": E2E_WORKERS, "host_numa_node": numa}
         link = host_link(dev, hx, x)
         # roofline of the end-to-end step: its host-link bytes at the measured
         # link rate (both directions at once), against the measured step time
         t_link = (4 * N + nb + nb + 4 * N) / (link["bidirectional_gbs"] * 1e9)
         res["e2e"]["host_link"] = link
         res["e2e"]["link_frac"] = round(t_link / (ems / args.e2e_steps * 1e-3), 4)
+        for sl in slots[1:]:
+            sl["ctx"].close()
         if saved_cpus is not None:
             os.sched_setaffinity(0, saved_cpus)
     if rank == 0 and world == 1 and not args.no_configs:
@@ -897,7 +921,7 @@ def main():
     ap.add_argument("--impl", default="fz", choices=["fz", "reference"])
     ap.add_argument("--size", type=int, default=512)
     ap.add_argument("--eb", type=float, default=1e-4)
-    ap.add_argument("--e2e-steps", type=int, default=5)
+    ap.add_argument("--e2e-steps", type=int, default=16, help="end-to-end steps, shared by the host threads")
     ap.add_argument("--cpu-slab", type=int, default=160, help="z-slab of the field the CPU oracle times")
     ap.add_argument("--ref-slab", type=int, default=16, help="z-slab per step for --impl reference")
     ap.add_argument("--no-cpu-baseline", action="store_true")
