@@ -96,3 +96,20 @@ def test_noalloc_plane_chunks_twice():
         out.fill_(-1.0)
         fz.decompress_noalloc(buf, out=out)
         assert np.array_equal(_bits(out), _bits(ref))
+
+
+@pytest.mark.parametrize("chunk", [128, 512])
+def test_noalloc_2d_chunks_below_the_block_twice(chunk):
+    """A 2D stream whose chunks are block rows, decoded by the sub-chunk
+    decoder (outliers at radius 8, an exception): the no-alloc entry point
+    gives fz_decompress's floats on two calls in a row."""
+    x = synth.smooth_nd((333, 517), 8).clone()
+    x[100, 200] = float("inf")
+    xg = x.contiguous().cuda()
+    buf = fz.compress(xg, 1e-4, radius=8, chunk=chunk)
+    ref = fz.decompress(buf)
+    out = torch.empty_like(ref)
+    for _ in range(2):
+        out.fill_(-1.0)
+        fz.decompress_noalloc(buf, out=out)
+        assert np.array_equal(_bits(out), _bits(ref))
