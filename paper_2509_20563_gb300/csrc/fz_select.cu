@@ -628,6 +628,7 @@ struct SelOut {
 };
 
 struct SelSmem {
+  float4 stage[4][kSelThreads];  // the next tile's input, thread t's four 4-vectors (asynchronous copies)
   int32_t sq[kRows * kTXP];
   uint8_t sexc[kTileElems];
   uint32_t shist[kMaxSym];
@@ -639,6 +640,35 @@ struct SelSmem {
   int pid[8];
   uint4 itab[512];
 };
+
+// 16-byte asynchronous copy global -> shared; an invalid copy zero-fills
+// and reads nothing.
+__device__ __forceinline__ void cp_async16(void *dst_smem, const void *src, bool valid) {
+  const uint32_t d = (uint32_t)__cvta_generic_to_shared(dst_smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(d), "l"(src), "r"(valid ? 16 : 0)
+               : "memory");
+}
+
+// Issue the copies of tile tl's input that thread tid will prequantize: its
+// four 4-vectors (row-major tile order, 4 values per thread per step), those
+// wholly inside the domain; the others are loaded when they are used.
+__device__ __forceinline__ void sel_issue_tile(const float *x, const Geom &g, uint64_t tl, bool vec_ok, int tid,
+                                               float4 (&stage)[4][kSelThreads]) {
+  if (!vec_ok || tl >= g.n_qtiles) return;
+  const uint32_t t32 = (uint32_t)tl;
+  const uint32_t tx = t32 % g.tiles_x, rest = t32 / g.tiles_x;
+  const uint32_t x0 = tx * kTX, y0 = (rest % g.nby) * 8, z0 = (rest / g.nby) * 8;
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    const int e = 4 * (tid + kSelThreads * j);
+    const int row = e / kTX, col = e % kTX;
+    const uint32_t X = x0 + col, Y = y0 + (row & 7), Z = z0 + (row >> 3);
+    const bool ok = Y < g.ny && Z < g.nz && X + 4 <= g.nx;
+    const uint64_t fi = ((uint64_t)Z * g.ny + Y) * g.nx + X;
+    cp_async16(&stage[j][tid], ok ? x + fi : x, ok);
+  }
+  asm volatile("cp.async.commit_group;\n" ::: "memory");
+}
 
 template <int MODE>
 __global__ void __launch_bounds__(kSelThreads, (MODE == kSelNet || MODE == kSelReport) ? 2 : FZ_SEL_MINB) k_selquant(const float *__restrict__ x, Geom g, uint32_t R,
@@ -656,12 +686,15 @@ __global__ void __launch_bounds__(kSelThreads, (MODE == kSelNet || MODE == kSelR
     for (int i = tid; i < kNWeights; i += kSelThreads) sm.w[smem_weight_index(i)] = bf16_to_f32(so.weights[i]);
   __syncthreads();
 
+  sel_issue_tile(x, g, blockIdx.x, vec_ok, tid, sm.stage);
   for (uint64_t tile = blockIdx.x; tile < g.n_qtiles; tile += gridDim.x) {
     const uint32_t t32 = (uint32_t)tile;
     const uint32_t tx = t32 % g.tiles_x, rest = t32 / g.tiles_x;
     const uint32_t by = rest % g.nby, bz = rest / g.nby;
     const uint32_t x0 = tx * kTX, y0 = by * 8, z0 = bz * 8;
-    // ---- load + prequantize the tile (row-major, 4 values per thread per step)
+    // ---- prequantize the tile (row-major, 4 values per thread per step) from
+    // the copies issued a tile ahead; then the next tile's copies go out
+    asm volatile("cp.async.wait_all;\n" ::: "memory");
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
       const int e = 4 * (tid + kSelThreads * j);
@@ -671,7 +704,7 @@ __global__ void __launch_bounds__(kSelThreads, (MODE == kSelNet || MODE == kSelR
       const uint64_t fi = ((uint64_t)Z * g.ny + Y) * g.nx + X;
       float xv[4];
       if (inrow && vec_ok && X + 4 <= g.nx) {
-        const float4 f4 = __ldcs(reinterpret_cast<const float4 *>(x + fi));
+        const float4 f4 = sm.stage[j][tid];
         xv[0] = f4.x; xv[1] = f4.y; xv[2] = f4.z; xv[3] = f4.w;
       } else {
 #pragma unroll
@@ -688,6 +721,7 @@ __global__ void __launch_bounds__(kSelThreads, (MODE == kSelNet || MODE == kSelR
       }
       *reinterpret_cast<uint32_t *>(&sm.sexc[e]) = ex;
     }
+    sel_issue_tile(x, g, tile + gridDim.x, vec_ok, tid, sm.stage);
     // ---- corner anchors of every block: q at o + 8 (cx, cy, cz)
     {
       const int wb = warp, c = lane;
