@@ -977,22 +977,35 @@ __global__ void __launch_bounds__(kSelDecThreads, 1) k_dec_codes(SelDecParams p)
     uint64_t oc = ~0ull;  // next outlier entry of this block (located at its first outlier)
     uint32_t nzero = 0;
     bool bad = false;
+    // sixteen codes (two rows) per step, four codewords per window read; the
+    // lane's 32 bytes are stored back to back (one whole sector)
 #pragma unroll 1
-    for (int r = 0; r < 64; ++r) {
-      uint32_t c[8];
+    for (int r = 0; r < 64; r += 2) {
+      uint32_t c[16];
 #pragma unroll
-      for (int u2 = 0; u2 < 4; ++u2) br.next2(slut, c[2 * u2], c[2 * u2 + 1]);
+      for (int u4 = 0; u4 < 4; ++u4) {
+        uint32_t s4[4];
+        br.next4(slut, s4);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) c[4 * u4 + k] = s4[k];
+      }
       dst[r] = make_uint4(c[0] | (c[1] << 16), c[2] | (c[3] << 16), c[4] | (c[5] << 16), c[6] | (c[7] << 16));
-      if (OV && (c[0] == 0 || c[1] == 0 || c[2] == 0 || c[3] == 0 || c[4] == 0 || c[5] == 0 || c[6] == 0 ||
-                 c[7] == 0)) {
-        if (oc == ~0ull) oc = __ldg(p.ofirst + j);  // ~0 for a block without outliers: out of the list
+      dst[r + 1] =
+          make_uint4(c[8] | (c[9] << 16), c[10] | (c[11] << 16), c[12] | (c[13] << 16), c[14] | (c[15] << 16));
+      if (OV) {
+        bool z = false;
 #pragma unroll
-        for (int k = 0; k < 8; ++k) {
-          if (c[k] != 0) continue;
-          if (oc < p.n_out) p.ovals[j * 512u + (uint64_t)(8 * r + k)] = __ldg(p.out_val + oc);
-          else bad = true;
-          ++oc;
-          ++nzero;
+        for (int k = 0; k < 16; ++k) z = z || c[k] == 0;
+        if (z) {
+          if (oc == ~0ull) oc = __ldg(p.ofirst + j);  // ~0 for a block without outliers: out of the list
+#pragma unroll
+          for (int k = 0; k < 16; ++k) {
+            if (c[k] != 0) continue;
+            if (oc < p.n_out) p.ovals[j * 512u + (uint64_t)(8 * r + k)] = __ldg(p.out_val + oc);
+            else bad = true;
+            ++oc;
+            ++nzero;
+          }
         }
       }
     }
