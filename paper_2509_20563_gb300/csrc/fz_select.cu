@@ -939,7 +939,13 @@ struct SelDecParams {
 
 __device__ __forceinline__ void sel_err(uint32_t *err, uint32_t code) { atomicCAS(err, 0u, code); }
 
-constexpr int kSelDecThreads = 768;
+// threads of the code decoder's CTA (one per SM): 864 and 576 give the 512^3
+// field's 8192 work units a whole number of rounds per warp (2 and 3);
+// measured 872 / 875 / 904 us for 864 / 576 / 768 on its interpolation decode
+#ifndef FZ_SELDEC_T
+#define FZ_SELDEC_T 864
+#endif
+constexpr int kSelDecThreads = FZ_SELDEC_T;
 
 // Phase 1: one thread per chunk (= block), codes written row by row; warps
 // take work units of 32 chunks from a counter.
