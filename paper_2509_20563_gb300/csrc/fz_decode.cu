@@ -274,6 +274,7 @@ struct DecParams {
   float *out;
   float ebx2;
   int32_t R;
+  uint32_t gate = 0;      // 0 decode; 1 only if err[4] is clear; 2 only if err[4] is set
 };
 
 // Outliers and exceptions of one block (both lists ascend by code-stream
@@ -368,7 +369,7 @@ __device__ __forceinline__ void store8(float *out, uint64_t f, bool full, bool v
 // 3D: the plane sums P (64 per order), 2D: the column sums Y (32 per order).
 // Words of per-thread prefix state.  NS (narrow state, 3D order 1): the
 // previous plane's values relative to the block's anchor as 16-bit integers,
-// 32 words instead of 64 (see narrow_state_ok).
+// 32 words instead of 64 (see narrow_state_candidate).
 template <int NDIM, int K, bool NS = false>
 struct DecState {
   static constexpr int kWords = NS ? 32 : (NDIM == 3 ? 64 * K : (NDIM == 2 ? 32 * K : 0));
@@ -629,7 +630,7 @@ __device__ __forceinline__ void decode_units(const DecParams &p, const Geom &g, 
       const uint64_t jb = j * k;
       const uint32_t nblk = (uint32_t)(g.n_blocks - jb < k ? g.n_blocks - jb : k);
       int32_t *st = st_thread(sstate, t);
-      if (!NS && p.n_exc) decode_chunk<NDIM, K, true, T>(p, g, slut, st, sring + t, jb, nblk, start, cb, vecbase);
+      if (p.n_exc) decode_chunk<NDIM, K, true, T, NS>(p, g, slut, st, sring + t, jb, nblk, start, cb, vecbase);
       else decode_chunk<NDIM, K, false, T, NS>(p, g, slut, st, sring + t, jb, nblk, start, cb, vecbase);
     }
   }
@@ -1025,10 +1026,17 @@ __global__ void __launch_bounds__(DecCta<NDIM, K, NS>::T, 1) k_decode(DecParams 
   int32_t *sstate = reinterpret_cast<int32_t *>(d_smem + sizeof(uint16_t) * kLutSize);
   uint32_t *sring = reinterpret_cast<uint32_t *>(sstate + DecState<NDIM, K, NS>::kWords * T);
   __shared__ LutBuild lb;
+  // A gated pair (the 16-bit-state decoder, then the 32-bit one) decodes a
+  // stream whose exceptions the offset pass checked: exactly one of the two
+  // runs.  The second is launched once every CTA of the first has ended, so
+  // the offset pass's verdict (err[4]) is final when it starts.
+  const volatile uint32_t *verdict = p.err + 4;
+  if (p.gate == 2 && *verdict == 0) return;
   // every CTA builds the decode table from the 1 KB length table itself (an
   // input of the call: it overlaps the offset pass, launched before)
   const bool ok = build_lut<T>(p.lens, p.nsym, slut, lb);
   dep_wait();  // the unit offsets
+  if (p.gate == 1 && *verdict != 0) return;
   if (ok) {
     __syncthreads();
     decode_units<NDIM, K, NS>(p, g, slut, sstate, sring);
@@ -1141,22 +1149,27 @@ cudaError_t launch_dec_t(const DecParams &p, const Geom &g, int sm_count, cudaSt
   return launch_dep(k_decode<NDIM, K, NS>, (unsigned)grid, (unsigned)T, (size_t)smem, s, p, g);
 }
 
-// Whether the 16-bit relative plane state holds every value of the stream:
-// REL bound eb >= 2^-15 and no exceptions.  Then every quantized value q lies
-// within range * inv2eb + 2 <= 1 / (2 eb) + 2 <= 16386 of its block's
-// anchor: both are prequantized finite values in [lo, hi] (|x * inv2eb| <
-// 2^23, so each product and each rounding to an integer is off by at most
-// 1/2), and inv2eb = 1 / (2 eb (hi - lo)) up to float rounding.
-bool narrow_state_ok(const fz_header &h) {
+}  // namespace
+
+// Whether the 16-bit relative plane state may decode the stream (3D,
+// first-order Lorenzo, chunks of whole blocks, REL bound eb >= 2^-15): every
+// quantized value q then lies within range * inv2eb + 2 <= 1 / (2 eb) + 2 <=
+// 16386 of its block's anchor -- both are prequantized finite values in [lo,
+// hi] (|x * inv2eb| < 2^23, so each product and each rounding to an integer
+// is off by at most 1/2), and inv2eb = 1 / (2 eb (hi - lo)) up to float
+// rounding.  Exceptions whose value was quantized (a rounding check that
+// failed) keep that bound; one that was not (non-finite, or |x * inv2eb| of
+// 2^23 or more) has q = 0, which may lie anywhere relative to its anchor, so
+// a stream with exceptions needs the offset pass's check of their values.
+static bool narrow_state_candidate(const fz_header &h) {
 #if FZ_DEC_NARROW
-  return h.eb_mode == FZ_EB_REL && h.eb >= 1.0 / 32768.0 && h.n_exc == 0;
+  return h.ndim == 3 && h.predictor == FZ_PRED_LORENZO1 && h.flags == 0 && h.chunk >= 512 &&
+         h.eb_mode == FZ_EB_REL && h.eb >= 1.0 / 32768.0;
 #else
   (void)h;
   return false;
 #endif
 }
-
-}  // namespace
 
 cudaError_t launch_decode_prep(const uint8_t *d_in, const fz_header &h, const DecodeWs &ws, cudaStream_t s) {
   const uint64_t n_chunks = h.n_chunks;
@@ -1217,18 +1230,31 @@ constexpr int kOffThreads = 256;  // work units per CTA of k_dec_offsets (one pe
 // range of units is the ticket it draws from a counter (err[3]) when it
 // starts, not its blockIdx: every predecessor in ticket order has started
 // and will publish, whatever order the hardware dispatches the CTAs in.  The
-// status words follow the error word, the work-unit counter, the CTA
-// counter and the ticket; everything starts at zero.
+// control words are err[0] error word, err[1] work-unit counter, err[2] CTA
+// counter, err[3] ticket, err[4] set when an exception is out of the
+// quantizer's range (see below), err[5..7] unused; the status words follow;
+// everything starts at zero.  With n_scan > 0 the pass also checks the
+// stream's n_scan exception values: one that was not quantized (non-finite,
+// or |x * inv2eb| not below 2^23, exactly the quantizer's test) sets err[4]
+// -- its q of 0 may lie far from its block's anchor, which rules out the
+// decoder's 16-bit plane state.
 __global__ void __launch_bounds__(kOffThreads) k_dec_offsets(const uint32_t *__restrict__ chunk_bits,
                                                              uint64_t n_chunks, uint64_t n_units,
                                                              uint64_t total_bits, uint64_t *uoff, uint32_t *err,
-                                                             long long spin) {
+                                                             long long spin, const uint32_t *__restrict__ exc_val,
+                                                             uint64_t n_scan, float inv2eb) {
   dep_trigger();  // the decoder builds its table meanwhile
   __shared__ unsigned long long wsum[kOffThreads / 32];
   __shared__ unsigned long long s_base;
   __shared__ uint32_t s_tile;
   const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
-  uint64_t *status = reinterpret_cast<uint64_t *>(err + 4);
+  uint64_t *status = reinterpret_cast<uint64_t *>(err + kDecCtlWords);
+  if (n_scan) {
+    bool out = false;
+    for (uint64_t i = (uint64_t)blockIdx.x * kOffThreads + t; i < n_scan; i += (uint64_t)gridDim.x * kOffThreads)
+      out |= !(fabsf(__fmul_rn(__uint_as_float(__ldg(exc_val + i)), inv2eb)) < 8388608.0f);
+    if (__any_sync(0xffffffffu, out) && lane == 0) atomicOr(err + 4, 1u);
+  }
   if (t == 0) s_tile = atomicAdd(err + 3, 1u);
   __syncthreads();
   const uint32_t tile = s_tile;
@@ -1288,7 +1314,7 @@ cudaError_t launch_lookback_selftest(uint32_t *scratch, long long spin, cudaStre
 }
 
 uint64_t dec_offset_zero_bytes(const fz_header &h) {
-  return 16 + 8 * ((dec_units_of(h.n_chunks) + kOffThreads - 1) / kOffThreads);
+  return 4 * kDecCtlWords + 8 * ((dec_units_of(h.n_chunks) + kOffThreads - 1) / kOffThreads);
 }
 
 cudaError_t launch_decode_offsets(const uint8_t *d_in, const fz_header &h, const DecodeWs &ws, cudaStream_t s) {
@@ -1296,8 +1322,14 @@ cudaError_t launch_decode_offsets(const uint8_t *d_in, const fz_header &h, const
   const uint64_t n_units = dec_units_of(n_chunks);
   const uint32_t *cbits = reinterpret_cast<const uint32_t *>(d_in + h.off_chunk_bits);
   const uint64_t grid = (n_units + kOffThreads - 1) / kOffThreads;
+  // the exception values are checked for the 16-bit-state decoder's choice
+  const uint64_t n_scan = (narrow_state_candidate(h) && h.flags == 0) ? h.n_exc : 0;
+  float inv2eb;
+  memcpy(&inv2eb, &h.inv2eb_bits, 4);
   k_dec_offsets<<<(unsigned)grid, kOffThreads, 0, s>>>(cbits, n_chunks, n_units, h.total_bits, ws.gsum, ws.err,
-                                                       ws.spin);
+                                                       ws.spin,
+                                                       reinterpret_cast<const uint32_t *>(d_in + h.off_exc_val),
+                                                       n_scan, inv2eb);
   return cudaGetLastError();
 }
 
@@ -1343,9 +1375,18 @@ cudaError_t launch_decode_main(const uint8_t *d_in, const fz_header &h, float *d
   switch (g.ndim) {
     case 1: return k2 ? launch_dec_t<1, 2>(p, g, sm_count, s) : launch_dec_t<1, 1>(p, g, sm_count, s);
     case 2: return k2 ? launch_dec_t<2, 2>(p, g, sm_count, s) : launch_dec_t<2, 1>(p, g, sm_count, s);
-    default:
+    default: {
       if (k2) return launch_dec_t<3, 2>(p, g, sm_count, s);
-      return narrow_state_ok(h) ? launch_dec_t<3, 1, true>(p, g, sm_count, s) : launch_dec_t<3, 1>(p, g, sm_count, s);
+      if (!narrow_state_candidate(h)) return launch_dec_t<3, 1>(p, g, sm_count, s);
+      if (h.n_exc == 0) return launch_dec_t<3, 1, true>(p, g, sm_count, s);
+      // exceptions: the offset pass has checked their values; the 16-bit
+      // decoder runs if all were quantized, else the 32-bit one
+      p.gate = 1;
+      const cudaError_t e = launch_dec_t<3, 1, true>(p, g, sm_count, s);
+      if (e != cudaSuccess) return e;
+      p.gate = 2;
+      return launch_dec_t<3, 1>(p, g, sm_count, s);
+    }
   }
 }
 

@@ -19,6 +19,7 @@ constexpr int kTileElems = 4096;   // elements per quantization tile
 constexpr int kQuantThreads = 256; // 8 warps per quantization tile
 constexpr int kEncWarps = 8;       // chunks per encode tile (one warp per chunk)
 constexpr int kDecUnit = 32;       // chunks per decode work unit (one warp, one chunk per lane)
+constexpr int kDecCtlWords = 8;    // decoder control words ahead of the unit-offset pass's look-back words
 constexpr int kTileGroup = 1024;   // quantization tiles per outlier-offset group
 
 enum Mode : uint32_t { kModeNormal = 0, kModeConst = 1, kModeRaw = 2 };

@@ -29,7 +29,7 @@
 namespace fz {
 namespace {
 
-constexpr size_t kNaErrBytes = 256;  // error word, unit counter, look-back words of the offset pass (<= 30 CTAs)
+constexpr size_t kNaErrBytes = 256;  // decoder control words, look-back words of the offset pass (<= 28 CTAs)
 constexpr size_t kNaUnitBytes = 8 * (FZ_NOALLOC_MAX_CHUNKS / kDecUnit);  // per-unit bit offsets
 constexpr size_t kNaScratchBytes = kNaErrBytes + kNaUnitBytes;
 

@@ -141,6 +141,25 @@ def test_block_spread_at_the_narrow_state_limit(eb, shape):
     _roundtrip_check(f, eb, "rel")
 
 
+@pytest.mark.parametrize("shape", [(40, 48, 72), (24, 40, 520)])
+def test_exceptions_and_the_narrow_state(shape):
+    """Values near 128 with a range of 1 at REL 1e-4: thousands of exceptions
+    whose value was quantized (the float rounding check failed), which the
+    16-bit plane state still decodes; with a NaN at a block origin, or an
+    infinity elsewhere (values that were not quantized, q = 0), the offset
+    pass's check sends the stream to the 32-bit state.  Bit-exact against the
+    oracle in all three cases."""
+    s = synth.smooth_nd(shape, seed=21).numpy()
+    x = (128.0 + (s - s.min()) / (s.max() - s.min())).astype(np.float32)
+    _roundtrip_check(x, 1e-4, "rel")
+    y = x.copy()
+    y[8, 16, 24] = np.nan
+    _roundtrip_check(y, 1e-4, "rel")
+    z = x.copy()
+    z[9, 17, 30] = np.inf
+    _roundtrip_check(z, 1e-4, "rel")
+
+
 def test_deterministic():
     x = torch.from_numpy(synth.grf3d(64, device="cpu").numpy()).cuda()
     a = fz.compress(x, 1e-4).cpu().numpy()
