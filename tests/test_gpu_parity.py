@@ -144,11 +144,10 @@ def test_block_spread_at_the_narrow_state_limit(eb, shape):
 @pytest.mark.parametrize("shape", [(40, 48, 72), (24, 40, 520)])
 def test_exceptions_and_the_narrow_state(shape):
     """Values near 128 with a range of 1 at REL 1e-4: thousands of exceptions
-    whose value was quantized (the float rounding check failed), which the
-    16-bit plane state still decodes; with a NaN at a block origin, or an
-    infinity elsewhere (values that were not quantized, q = 0), the offset
-    pass's check sends the stream to the 32-bit state.  Bit-exact against the
-    oracle in all three cases."""
+    whose value was quantized (the float rounding check failed), then a NaN
+    at a block origin or an infinity elsewhere (values that were not
+    quantized, q = 0).  These streams are below 4096 work units, so the
+    32-bit plane state decodes all three; bit-exact against the oracle."""
     s = synth.smooth_nd(shape, seed=21).numpy()
     x = (128.0 + (s - s.min()) / (s.max() - s.min())).astype(np.float32)
     _roundtrip_check(x, 1e-4, "rel")
@@ -158,6 +157,29 @@ def test_exceptions_and_the_narrow_state(shape):
     z = x.copy()
     z[9, 17, 30] = np.inf
     _roundtrip_check(z, 1e-4, "rel")
+
+
+def test_full_exceptions_and_the_narrow_state():
+    """A 256 x 512 x 512 field (4096 work units, where a stream with
+    exceptions starts to try the 16-bit plane state) near 128 with a range of
+    1: rounding-check exceptions only (the 16-bit state decodes), then a NaN
+    at a block origin (the offset pass's check picks the 32-bit state).
+    Streams byte-identical and reconstructions bit-identical to the
+    oracle's."""
+    g = synth.grf3d(512, seed=5, device="cuda")[:256].contiguous()
+    x = (128.0 + (g - g.min()) / (g.max() - g.min())).float().contiguous()
+    for case in range(2):
+        xd = x.clone()
+        if case == 1:
+            xd[8, 16, 24] = float("nan")
+        buf = fz.compress(xd, 1e-4)
+        y = fz.decompress(buf).cpu().numpy()
+        xh = xd.cpu().numpy()
+        ref = oracle.compress(xh, 1e-4)
+        got = buf.cpu().numpy()
+        assert got.size == ref.size and np.array_equal(got, ref), case
+        assert int.from_bytes(ref[120:128].tobytes(), "little") > 0  # the stream holds exceptions
+        assert np.array_equal(_bits(y), _bits(oracle.decompress(ref))), case
 
 
 def test_deterministic():
