@@ -201,7 +201,7 @@ __device__ __forceinline__ void codebook_body(const Geom &g, uint32_t R, uint32_
     if (t < (int)nsym) {
       uint32_t L = s.len[t];
       ctl->lens[t] = (uint8_t)L;
-      ctl->enc[t] = (L << 24) | code;
+      ctl->enc[t] = L ? (code << (32u - L)) | L : 0u;  // L <= 14
       b = s.cnt[t] * (unsigned long long)L;
     }
     for (int off = 16; off > 0; off >>= 1) b += __shfl_down_sync(0xffffffffu, b, off);

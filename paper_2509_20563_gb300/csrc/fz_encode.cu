@@ -72,6 +72,48 @@ __device__ __forceinline__ void store_multi_chunks(uint32_t *chunk_bits, const u
   if (c < n_chunks) chunk_bits[c] = sum;
 }
 
+// Codeword table entries (Ctl::enc): the codeword left-aligned in the high
+// L bits, L (at most 14) in the low 5 bits.  One lane's PER codewords are
+// packed MSB-first into the tile image lw from tile-local bit rb, two at a
+// time (at most 28 bits: the pair is one left-aligned word, so at most one
+// image word fills per step); the funnel shift gives the pair's bits that
+// spill past the current word.
+template <int PER>
+__device__ __forceinline__ void pack_lane(const uint32_t (&cw)[PER], uint32_t rb, uint32_t *lw) {
+  uint32_t wi = rb >> 5;
+  uint32_t cnt = rb & 31u;  // bits of word wi in front of this lane's next codeword
+  uint32_t cur = 0;         // this lane's bits of word wi
+#pragma unroll
+  for (int k = 0; k < PER; k += 2) {
+    const uint32_t L0 = cw[k] & 31u;
+    const uint32_t v = (cw[k] & ~31u) | ((cw[k + 1] & ~31u) >> L0);
+    cur |= v >> cnt;
+    const uint32_t spill = __funnelshift_r(0u, v, cnt);
+    cnt += L0 + (cw[k + 1] & 31u);
+    if (cnt >= 32) {
+      atomicOr(&lw[wi], cur);
+      ++wi;
+      cur = spill;
+      cnt -= 32;
+    }
+  }
+  if (cnt > 0) atomicOr(&lw[wi], cur);
+}
+
+// The first 32 bits of the codewords of a tile's first 32 codes, one code
+// per lane (entry e of the lane's code): every lane of the warp calls it.
+__device__ __forceinline__ uint32_t head_bits(uint32_t e, int lane) {
+  const uint32_t L = e & 31u;
+  uint32_t p = L;
+#pragma unroll
+  for (int off = 1; off < 32; off <<= 1) {
+    const uint32_t v = __shfl_up_sync(0xffffffffu, p, off);
+    if (lane >= off) p += v;
+  }
+  p -= L;
+  return __reduce_or_sync(0xffffffffu, p < 32 ? (e & ~31u) >> p : 0u);
+}
+
 // One encode tile (kEncWarps chunks) of one field whose codeword table is
 // in sm.senc; all threads of the CTA call it together.
 template <int CH>
@@ -105,7 +147,7 @@ __device__ __forceinline__ void encode_tile(const CompressWs &ws, uint8_t *d_out
       }
     }
 #pragma unroll
-    for (int k = 0; k < PER; ++k) lbits += cw[k] >> 24;
+    for (int k = 0; k < PER; ++k) lbits += cw[k] & 31u;
   } else {
 #pragma unroll
     for (int k = 0; k < PER; ++k) cw[k] = 0;
@@ -137,44 +179,13 @@ __device__ __forceinline__ void encode_tile(const CompressWs &ws, uint8_t *d_out
   __syncthreads();
 
   // ---- pack this lane's codewords MSB-first at its tile-local bit offset
-  if (valid) {
-    const uint32_t rb = sm.woff[warp] + lane_off;
-    uint32_t wi = rb >> 5;
-    int cnt = (int)(rb & 31u);
-    unsigned long long buf = 0;
-    // codewords two at a time (at most 28 bits), so at most one word fills per step
-#pragma unroll
-    for (int k = 0; k < PER; k += 2) {
-      const uint32_t L1 = cw[k + 1] >> 24;
-      const uint32_t v = ((cw[k] & 0xffffffu) << L1) | (cw[k + 1] & 0xffffffu);
-      const int n = (int)((cw[k] >> 24) + L1);
-      buf |= (unsigned long long)v << (64 - cnt - n);
-      cnt += n;
-      if (cnt >= 32) {
-        atomicOr(&lw[wi], (uint32_t)(buf >> 32));
-        ++wi;
-        buf <<= 32;
-        cnt -= 32;
-      }
-    }
-    if (cnt > 0) atomicOr(&lw[wi], (uint32_t)(buf >> 32));
-  }
+  if (valid) pack_lane<PER>(cw, sm.woff[warp] + lane_off, lw);
   __syncthreads();
 
   if (warp == 0) {
     // first 32 bits of the next tile, placed right after this tile's bits
     if (tile + 1 < n_tiles) {
-      const uint32_t e = senc[ws.codes[(tile + 1) * kEncWarps * (uint64_t)CH + lane]];
-      const uint32_t L = e >> 24, c = e & 0xffffffu;
-      uint32_t p = L;
-#pragma unroll
-      for (int off = 1; off < 32; off <<= 1) {
-        const uint32_t v = __shfl_up_sync(0xffffffffu, p, off);
-        if (lane >= off) p += v;
-      }
-      p -= L;
-      const uint32_t contrib = p < 32 ? (uint32_t)(((unsigned long long)c << (64 - p - L)) >> 32) : 0u;
-      const uint32_t head = __reduce_or_sync(0xffffffffu, contrib);
+      const uint32_t head = head_bits(senc[ws.codes[(tile + 1) * kEncWarps * (uint64_t)CH + lane]], lane);
       if (lane == 0) {
         const uint32_t r = tbits & 31u, w0 = tbits >> 5;
         lw[w0] |= head >> r;
@@ -368,7 +379,7 @@ __global__ void __launch_bounds__(kEncThreads, CH == 512 ? FZ_ENC_MINB : FZ_ENC_
         }
       }
 #pragma unroll
-      for (int k = 0; k < PER; ++k) lbits += cw[k] >> 24;
+      for (int k = 0; k < PER; ++k) lbits += cw[k] & 31u;
     } else {
 #pragma unroll
       for (int k = 0; k < PER; ++k) cw[k] = 0;
@@ -406,40 +417,10 @@ __global__ void __launch_bounds__(kEncThreads, CH == 512 ? FZ_ENC_MINB : FZ_ENC_
       }
       if (tid == 0) lookback_publish(ws.estatus, tile, tbits);
       // ---- pack MSB-first at the tile-local bit offset, codewords in pairs
-      if (valid) {
-        const uint32_t rb = woff + incl - lbits;
-        uint32_t wi = rb >> 5;
-        int cnt = (int)(rb & 31u);
-        unsigned long long acc = 0;
-#pragma unroll
-        for (int k = 0; k < PER; k += 2) {
-          const uint32_t L1 = cw[k + 1] >> 24;
-          const uint32_t v = ((cw[k] & 0xffffffu) << L1) | (cw[k + 1] & 0xffffffu);
-          const int n = (int)((cw[k] >> 24) + L1);
-          acc |= (unsigned long long)v << (64 - cnt - n);
-          cnt += n;
-          if (cnt >= 32) {
-            atomicOr(&lw[wi], (uint32_t)(acc >> 32));
-            ++wi;
-            acc <<= 32;
-            cnt -= 32;
-          }
-        }
-        if (cnt > 0) atomicOr(&lw[wi], (uint32_t)(acc >> 32));
-      }
+      if (valid) pack_lane<PER>(cw, woff + incl - lbits, lw);
       // ---- first 32 bits of the next tile, right after this tile's bits
       if (warp == kEncWarps - 1 && tile + 1 < n_tiles) {
-        const uint32_t e = sm.senc[hcode];
-        const uint32_t L = e >> 24, c = e & 0xffffffu;
-        uint32_t p = L;
-#pragma unroll
-        for (int off = 1; off < 32; off <<= 1) {
-          const uint32_t v = __shfl_up_sync(0xffffffffu, p, off);
-          if (lane >= off) p += v;
-        }
-        p -= L;
-        const uint32_t contrib = p < 32 ? (uint32_t)(((unsigned long long)c << (64 - p - L)) >> 32) : 0u;
-        const uint32_t head = __reduce_or_sync(0xffffffffu, contrib);
+        const uint32_t head = head_bits(sm.senc[hcode], lane);
         if (lane == 0) {
           const uint32_t r = tbits & 31u, w0 = tbits >> 5;
           atomicOr(&lw[w0], head >> r);

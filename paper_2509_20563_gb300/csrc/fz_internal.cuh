@@ -171,7 +171,7 @@ struct Ctl {
   uint32_t const_bits;
   uint32_t pad0;
   // codebook results
-  uint32_t enc[kMaxSym];   // (len << 24) | codeword
+  uint32_t enc[kMaxSym];   // codeword left-aligned in the high len bits, len in the low 5 (0: unused)
   uint8_t lens[kMaxSym];
   uint64_t total_bits;
   Result res;
