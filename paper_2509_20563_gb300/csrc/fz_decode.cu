@@ -52,8 +52,9 @@ __global__ void k_dec_gsum(const uint32_t *__restrict__ chunk_bits, uint64_t n_c
 
 __device__ __forceinline__ void dec_scan_body(uint64_t *gsum, uint64_t n_units, uint64_t total_bits, uint32_t *err);
 
-__device__ __forceinline__ void k_dec_prep_body(const uint8_t *__restrict__ lens_in, uint32_t nsym, uint64_t *gsum,
-                                                uint64_t n_units, uint64_t total_bits, uint16_t *lut, uint32_t *err) {
+__device__ __forceinline__ void k_dec_prep_body(const uint8_t *__restrict__ lens_in, uint32_t nsym, int32_t off,
+                                                uint64_t *gsum, uint64_t n_units, uint64_t total_bits, uint16_t *lut,
+                                                uint32_t *err) {
   __shared__ uint32_t first[kLmax + 1], cnt[kLmax + 1], basel[kLmax + 1];
   __shared__ uint32_t wcnt[32][kLmax + 1];
   __shared__ uint32_t wk[32];
@@ -111,12 +112,12 @@ __device__ __forceinline__ void k_dec_prep_body(const uint8_t *__restrict__ lens
   __syncthreads();
   // every table entry: the codeword whose left-aligned range contains it
   for (int e = t; e < kLutSize; e += kPrepThreads) {
-    uint16_t v = 0;
+    uint16_t v = lut_entry(-off, 0);
 #pragma unroll
     for (int l = 1; l <= kLmax; ++l) {
       const uint32_t c = (uint32_t)e >> (kLmax - l);
       if (cnt[l] && c >= first[l] && c - first[l] < cnt[l])
-        v = (uint16_t)((l << kLutLenShift) | sorted[basel[l] + c - first[l]]);
+        v = lut_entry((int32_t)sorted[basel[l] + c - first[l]] - off, (uint32_t)l);
     }
     lut[e] = v;
   }
@@ -160,7 +161,7 @@ __device__ __forceinline__ void dec_scan_body(uint64_t *gsum, uint64_t n_units, 
 __global__ void __launch_bounds__(kPrepThreads) k_dec_prep(const uint8_t *__restrict__ lens_in, uint32_t nsym,
                                                             uint64_t *gsum, uint64_t n_units,
                                                             uint64_t total_bits, uint16_t *lut, uint32_t *err) {
-  k_dec_prep_body(lens_in, nsym, gsum, n_units, total_bits, lut, err);
+  k_dec_prep_body(lens_in, nsym, 0, gsum, n_units, total_bits, lut, err);  // codes, for the code decoder
 }
 
 // Shared memory of the in-kernel decode-table build.
@@ -175,12 +176,13 @@ struct LutBuild {
 // The canonical decode table of the length table lens[0..nsym) built by the
 // T threads of a CTA into slut: codes of length l occupy the contiguous
 // range [first[l], first[l] + cnt[l]) << (14 - l) of the 14-bit window, the
-// ranges follow each other in length order, and entry e holds the symbol of
-// rank (e >> (14 - l)) - first[l] among the symbols of its length l.
-// Windows past the last range (an incomplete code) stay 0.  Returns false
-// (in every thread) for a length above 14 or a Kraft sum outside (0, 1].
+// ranges follow each other in length order, and entry e holds l and the
+// symbol of rank (e >> (14 - l)) - first[l] among the symbols of its length
+// l, minus off.  Windows past the last range (an incomplete code) hold code
+// 0 with length 0.  Returns false (in every thread) for a length above 14 or
+// a Kraft sum outside (0, 1].
 template <int T>
-__device__ bool build_lut(const uint8_t *__restrict__ lens, uint32_t nsym, uint16_t *slut, LutBuild &b) {
+__device__ bool build_lut(const uint8_t *__restrict__ lens, uint32_t nsym, int32_t off, uint16_t *slut, LutBuild &b) {
   constexpr int W = T / 32;
   const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
   for (int grp = warp; grp < 32; grp += W) {
@@ -245,9 +247,9 @@ __device__ bool build_lut(const uint8_t *__restrict__ lens, uint32_t nsym, uint1
     int l = 1;
 #pragma unroll
     for (int k = 1; k < kLmax; ++k) l += (uint32_t)e >= lim[k] ? 1 : 0;
-    uint16_t v = 0;
+    uint16_t v = lut_entry(-off, 0);
     if ((uint32_t)e < lim[kLmax])
-      v = (uint16_t)((l << kLutLenShift) | b.sorted[b.basel[l] + ((uint32_t)e >> (kLmax - l)) - b.first[l]]);
+      v = lut_entry((int32_t)b.sorted[b.basel[l] + ((uint32_t)e >> (kLmax - l)) - b.first[l]] - off, (uint32_t)l);
     slut[e] = v;
   }
   return true;
@@ -768,7 +770,7 @@ __global__ void __launch_bounds__(Sub2d<C>::T) k_decode_sub2d(DecParams p, Geom 
   uint32_t *sring = reinterpret_cast<uint32_t *>(sstate + kSub2dWords * T);
   int4 *sbuf = reinterpret_cast<int4 *>(sring + kRing * T);
   __shared__ LutBuild lb;
-  const bool ok = build_lut<T>(p.lens, p.nsym, slut, lb);
+  const bool ok = build_lut<T>(p.lens, p.nsym, p.R, slut, lb);
   dep_wait();  // the unit offsets
   if (ok) {
     __syncthreads();
@@ -933,7 +935,7 @@ __global__ void __launch_bounds__(kPlaneT, 1) k_decode_planes(DecParams p, Geom 
   int32_t *stile = reinterpret_cast<int32_t *>(sring + kRing * T);
   __shared__ LutBuild lb;
   const int t = threadIdx.x;
-  if (build_lut<T>(p.lens, p.nsym, slut, lb)) {
+  if (build_lut<T>(p.lens, p.nsym, p.R, slut, lb)) {
     __syncthreads();
     int32_t *tile = stile + (t >> 5) * kPlaneTile;
     for (;;) {
@@ -1034,7 +1036,7 @@ __global__ void __launch_bounds__(DecCta<NDIM, K, NS>::T, 1) k_decode(DecParams 
   if (p.gate == 2 && *verdict == 0) return;
   // every CTA builds the decode table from the 1 KB length table itself (an
   // input of the call: it overlaps the offset pass, launched before)
-  const bool ok = build_lut<T>(p.lens, p.nsym, slut, lb);
+  const bool ok = build_lut<T>(p.lens, p.nsym, p.R, slut, lb);
   dep_wait();  // the unit offsets
   if (p.gate == 1 && *verdict != 0) return;
   if (ok) {
@@ -1081,7 +1083,7 @@ __global__ void k_dec_gsum_batch(const DecJob *__restrict__ jobs) {
 // Decode tables and unit offsets: one CTA per field.
 __global__ void __launch_bounds__(kPrepThreads) k_dec_prep_batch(const DecJob *__restrict__ jobs) {
   const DecJob &J = jobs[blockIdx.x];
-  k_dec_prep_body(J.lens, J.nsym, const_cast<uint64_t *>(J.p.goff), J.p.n_units, J.total_bits,
+  k_dec_prep_body(J.lens, J.nsym, J.p.R, const_cast<uint64_t *>(J.p.goff), J.p.n_units, J.total_bits,
                   const_cast<uint16_t *>(J.p.lut), J.p.err);
 }
 

@@ -7,10 +7,16 @@
 namespace fz {
 
 constexpr int kLutSize = 1 << kLutBits;
-// decode-table entry: bits 10..13 codeword length (1..14), bits 0..9 symbol;
-// 0 marks a window that starts no codeword (only in a corrupt stream: the
-// reader then stops advancing and the chunk's bit count check fails)
-constexpr uint32_t kLutLenShift = 10;
+// Decode-table entry, read as a signed 16-bit value e: e >> 4 (arithmetic)
+// is the decoded value v = symbol - offset, e & 15 the codeword length
+// (1..14).  The residual decoders build their table with offset R, so v is
+// the Lorenzo residual and code 0 (an outlier) reads as -R; the code
+// decoder uses offset 0 (v is the code).  A window that starts no codeword
+// (only in a corrupt stream) holds code 0 with length 0: the reader stops
+// advancing there and the chunk's bit count check fails.
+__host__ __device__ constexpr uint16_t lut_entry(int32_t v, uint32_t len) {
+  return (uint16_t)(((uint32_t)v << 4) | len);
+}
 
 __device__ __forceinline__ void prefetch_l2(const void *p) {
   asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
@@ -26,10 +32,9 @@ __device__ __forceinline__ void cp_async4(uint32_t *dst_smem, const uint32_t *sr
 constexpr int kRing = 4;  // stream words in flight per thread (a power of two)
 
 // MSB-first bit reader over one chunk, all 32-bit: a window of three stream
-// words (a, b, c) and a bit offset (< 32) into a.  Codewords are decoded in
-// pairs: both fit in the window (2 x 14 bits from an offset below 32), and
-// afterwards the window slides by at most one word.  The slide is
-// predicated, not branched, so a warp whose lanes slide at different times
+// words (a, b, c) and a bit offset (< 32) into a.  Codewords are decoded
+// four at a time, all within the window, after which the window slides by
+// up to two words.  The slide is predicated, not branched, so a warp whose lanes slide at different times
 // never diverges: the next word comes from a per-thread ring in shared
 // memory that asynchronous copies fill kRing slides ahead, so a slide never
 // waits on memory and no register is read while its load is in flight.
@@ -62,43 +67,11 @@ struct BitReader {
     const uint32_t cw = (off + bits + 31) / 32 + 2;
     for (uint32_t i = 32; i < cw && i < nw; i += 32) prefetch_l2(W + i);
   }
-  // Two symbols.
-  __device__ __forceinline__ void next2(const uint16_t *slut, uint32_t &s0, uint32_t &s1) {
-    const uint32_t e0 = slut[__funnelshift_l(b, a, off) >> (32 - kLutBits)];
-    const uint32_t o1 = off + ((e0 >> kLutLenShift) & 15u);  // < 46
-    const uint32_t w1 = o1 < 32 ? __funnelshift_l(b, a, o1) : __funnelshift_l(c, b, o1);
-    const uint32_t e1 = slut[w1 >> (32 - kLutBits)];
-    const uint32_t o2 = o1 + ((e1 >> kLutLenShift) & 15u);   // < 60
-    s0 = e0 & 1023u;
-    s1 = e1 & 1023u;
-    const uint32_t adv = o2 >> 5;  // 0 or 1
-    off = o2 & 31u;
-    a = adv ? b : a;
-    b = adv ? c : b;
-    // predicated slide: wait for the oldest copy, read its word into c,
-    // refill the slot with the word kRing slides ahead
-    const uint32_t slot = ring_s + rd * (uint32_t)(T * 4);
-    const bool more = wi < nw;
-    const uint32_t *src = W + (more ? wi : 0u);
-    asm volatile(
-        "{\n"
-        " .reg .pred p;\n"
-        " setp.ne.u32 p, %1, 0;\n"
-        " @p cp.async.wait_group %5;\n"
-        " @p ld.shared.u32 %0, [%2];\n"
-        " @p cp.async.ca.shared.global [%2], [%3], 4, %4;\n"
-        " @p cp.async.commit_group;\n"
-        "}\n"
-        : "+r"(c)
-        : "r"(adv), "r"(slot), "l"(src), "r"(more ? 4 : 0), "n"(kRing - 1));
-    rd = (rd + adv) & (kRing - 1);
-    wi += adv;
-  }
   // Four symbols.  They all lie in the window: from an offset below 32,
   // four codewords of at most 14 bits end by bit 87 < 96, and the fourth
   // starts by bit 73, so its 14-bit lookup window needs no fourth word.  The
-  // window then slides by 0, 1 or 2 words (predicated, as in next2).
-  __device__ __forceinline__ void next4(const uint16_t *slut, uint32_t (&s)[4]) {
+  // window then slides by 0, 1 or 2 words, predicated rather than branched.
+  __device__ __forceinline__ void next4(const uint16_t *slut, int32_t (&s)[4]) {
     uint32_t o = off;
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
@@ -106,9 +79,9 @@ struct BitReader {
       if (k == 0) w = __funnelshift_l(b, a, o);                                   // o < 32
       else if (k < 3) w = o < 32 ? __funnelshift_l(b, a, o) : __funnelshift_l(c, b, o);  // o < 60
       else w = o < 32 ? __funnelshift_l(b, a, o) : (o < 64 ? __funnelshift_l(c, b, o) : c << (o & 31u));
-      const uint32_t e = slut[w >> (32 - kLutBits)];
-      s[k] = e & 1023u;
-      o += (e >> kLutLenShift) & 15u;
+      const int32_t e = (int16_t)slut[w >> (32 - kLutBits)];
+      s[k] = e >> 4;
+      o += (uint32_t)e & 15u;
     }
     const uint32_t adv = o >> 5;  // 0, 1 or 2
     off = o & 31u;
@@ -146,18 +119,18 @@ struct BitReader {
     rd = (rd + adv) & (kRing - 1);
     wi += adv;
   }
-  // Eight symbols as residuals sym - R; returns whether any symbol was 0
-  // (an outlier, whose residual is then -R until it is looked up).
+  // Eight residuals from a table built with offset R; returns whether any
+  // is -R (code 0: an outlier, whose residual is looked up afterwards).
   __device__ __forceinline__ bool group8(const uint16_t *slut, int32_t R, int32_t (&d)[8]) {
     bool zero = false;
 #pragma unroll
     for (int k = 0; k < 2; ++k) {
-      uint32_t s[4];
+      int32_t s[4];
       next4(slut, s);
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
-        zero = zero || s[u] == 0;
-        d[4 * k + u] = (int32_t)s[u] - R;
+        zero = zero || s[u] == -R;
+        d[4 * k + u] = s[u];
       }
     }
     return zero;

@@ -990,10 +990,10 @@ __global__ void __launch_bounds__(kSelDecThreads, 1) k_dec_codes(SelDecParams p)
       uint32_t c[16];
 #pragma unroll
       for (int u4 = 0; u4 < 4; ++u4) {
-        uint32_t s4[4];
-        br.next4(slut, s4);
+        int32_t s4[4];
+        br.next4(slut, s4);  // a table of offset 0: the codes themselves
 #pragma unroll
-        for (int k = 0; k < 4; ++k) c[4 * u4 + k] = s4[k];
+        for (int k = 0; k < 4; ++k) c[4 * u4 + k] = (uint32_t)s4[k];
       }
       dst[r] = make_uint4(c[0] | (c[1] << 16), c[2] | (c[3] << 16), c[4] | (c[5] << 16), c[6] | (c[7] << 16));
       dst[r + 1] =
