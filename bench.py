@@ -62,7 +62,7 @@ KERNEL_SOURCES = {
 }
 # kernel -> (dram__bytes_read.sum + dram__bytes_write.sum of one launch at 512^3, digest of the kernel's
 # sources when captured, commit): one-pass ncu capture of the bench's own first decoder launch
-NCU_DRAM_BYTES_512 = {"decode": (251245568 + 478465792, "a3f6ee6f9aa0b292", "db4eda4")}
+NCU_DRAM_BYTES_512 = {"decode": (250551808 + 478513408, "eef5ad757df9bcfb", "dc0e2dd")}
 METRIC = "compress/decompress GB/s vs HBM peak at REL 1e-4; CR learned vs plain"
 PROFILE_EVERY = 8  # timed steps per step that records the library's stage events
 E2E_WORKERS = 4  # host threads (each with its own context and stream) of the end-to-end leg
